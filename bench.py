@@ -1,0 +1,335 @@
+"""Throughput of SDA camera-fingerprint extraction on GB300.
+
+Step = one pass of the whole path over the video-scale workload: 1000 RGB
+1920x1080 uint8 frames of one synthetic camera (drifting scene), SDA groups of
+50 (20 SDA frames, 60 channel denoises), MLE accumulation, finalize (grey,
+zero-mean, DFT Wiener), then 10 same-camera and 10 foreign query frames each
+denoised and matched by PCE.  The metric is frames/s into the fingerprint.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU (torchrun): every rank runs its own camera (independent problems,
+no data-path collective): weak scaling.  --impl reference times the FP64 CPU
+oracle (the only reference this path has) on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames/sec into fingerprint (1080p, SDA vs per-frame) and HBM GB/s % of peak"
+UNIT = "frames/s"
+H, W, C = 1080, 1920, 3
+M_FRAMES, D_SDA, N_QUERY = 1000, 50, 10
+WORKLOAD = "video-1080p-rgb-1000f-sda50"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-perframe", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks --
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max((float(r[2]) for r in rows if r[2].replace(".", "").isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------- CPU oracle --
+def oracle_sample(frames_host, groups: int):
+    """Time the FP64 oracle on `groups` SDA groups of the workload: SDA mean,
+    per-channel residual, MLE sums.  Returns (seconds, frames, cores)."""
+    import numpy as np
+
+    import oracle as O
+    O.build()
+    t0 = time.perf_counter()
+    num = np.zeros((C, H, W))
+    den = np.zeros((C, H, W))
+    O.fingerprint_accumulate(frames_host[: groups * D_SDA], D_SDA, num=num, den=den)
+    t = time.perf_counter() - t0
+    return t, groups * D_SDA, O.threads()
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    import torch
+
+    from paper_1909_04573_gb300 import synth
+    cam = synth.Camera(H=H, W=W, C=C, camera_id=0)
+    fr = synth.frames(cam, D_SDA, device="cpu", drift_px=2.0).numpy()  # one SDA group
+    for _ in range(args.warmup):
+        oracle_sample(fr, 1)
+    ts = []
+    cores = 1
+    for _ in range(args.steps):
+        t, n, cores = oracle_sample(fr, 1)
+        ts.append(t)
+    ms = 1000.0 * sum(ts) / len(ts)
+    value = D_SDA / (ms / 1000.0)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "frames": M_FRAMES, "H": H, "W": W, "C": C, "d": D_SDA,
+                       "parallelism": "oracle on host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"1 SDA group of {D_SDA} frames (1080p RGB) per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    del torch
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- GPU arm ---
+def algorithmic_bytes(name, m, d, G):
+    """Compulsory bytes per step of each kernel family (see the design notes)."""
+    hp, wp = 1088, 1920
+    P = G * C
+    px = H * W
+    if name == "sda_sum":
+        return m * px * C + P * px * 4
+    if name == "analysis_l1":
+        a1 = (hp // 2) * (wp // 2)
+        return P * px * 4 + P * a1 * (8 + 12)
+    if name == "final_mle":
+        a1 = (hp // 2) * (wp // 2)
+        return P * a1 * 16 + P * px * 4 + C * px * 16
+    return None
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    from paper_1909_04573_gb300 import prnu as P
+    from paper_1909_04573_gb300 import synth
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    dev = torch.device("cuda", local)
+    ctx = P.Context(local)
+
+    cam = synth.Camera(H=H, W=W, C=C, camera_id=rank)
+    frames = synth.frames(cam, M_FRAMES, device=dev, drift_px=2.0)        # 6.22 GB resident
+    qf = torch.cat([synth.frames(cam, N_QUERY, stream=1, device=dev),
+                    synth.frames(synth.foreign(cam), N_QUERY, stream=1, device=dev)])
+    qimg = ctx.sda_average(qf, 1)                                         # [20, 3, H, W] float
+    num = torch.zeros((C, H, W), dtype=torch.float32, device=dev)
+    den = torch.zeros_like(num)
+    wq = torch.empty((C, H, W), dtype=torch.float32, device=dev)
+    flags = P.PRNU_TO_GRAY | P.PRNU_ZERO_MEAN | P.PRNU_WIENER_DFT
+    pces = []
+
+    def step(d=D_SDA, images_per_pass=None):
+        num.zero_()
+        den.zero_()
+        ctx.fingerprint_accumulate(frames, d, num, den, images_per_pass=images_per_pass)
+        K = ctx.fingerprint_finalize(num, den, flags)
+        pces.clear()
+        for i in range(2 * N_QUERY):
+            ctx.denoise_residual(qimg[i], out=wq)
+            pces.append(ctx.pce_match(K[0], wq, qimg[i])[0])
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            dist.barrier()
+        return ms
+
+    # ---- SDA path, timed with per-kernel events on the launch stream
+    for _ in range(args.warmup):
+        step()
+    P.prnu_profile_reset(ctx.ctx)
+    P.prnu_profile_enable(ctx.ctx, True)
+    clocks = Clocks(local)
+    clocks.start()
+    ms = timed(step, args.steps, 0)
+    ck = clocks.stop()
+    P.prnu_profile_enable(ctx.ctx, False)
+    prof = P.prnu_profile_read(ctx.ctx)
+    P.prnu_profile_reset(ctx.ctx)
+    value = world * M_FRAMES / (ms / 1000.0)
+    pos = [p for p in pces[:N_QUERY]]
+    neg = [p for p in pces[N_QUERY:]]
+
+    own = {k: v for k, v in prof.items() if not k.startswith("cufft")}
+    launches = sum(v[0] for v in own.values())
+    total_dev = sum(v[1] for v in prof.values())
+    G = math.ceil(M_FRAMES / D_SDA)
+    hbm, peak_kind = peaks()
+    kern = {}
+    for k, (n, t) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
+        ab = algorithmic_bytes(k, M_FRAMES, D_SDA, G)
+        per = n / args.steps
+        e = {"launches_per_step": per, "ms_per_step": t / args.steps, "share": t / total_dev if total_dev else None}
+        if ab is not None and t > 0:
+            e["algorithmic_GBps"] = ab * args.steps / (t / 1000.0) / 1e9
+        kern[k] = e
+    dom = max(own.items(), key=lambda kv: kv[1][1])[0]
+    dom_bytes = algorithmic_bytes(dom, M_FRAMES, D_SDA, G)
+    dom_n, dom_t = own[dom]
+    roof = None
+    if dom_bytes is not None:
+        per_launch_bytes = dom_bytes * args.steps / dom_n
+        ach = per_launch_bytes / (dom_t / dom_n / 1000.0) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "peak_kind": f"{peak_kind} (copy)", "traffic": None,
+                "bytes_per_launch": per_launch_bytes}
+    step_bytes = M_FRAMES * H * W * C
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded sensor model; VISION/NYUAD-MMD absent)",
+            "config": {"workload": WORKLOAD, "frames": M_FRAMES, "H": H, "W": W, "C": C, "d": D_SDA,
+                       "queries": 2 * N_QUERY, "parallelism": f"1 camera per GPU x {world}",
+                       "l2": "inputs 6.22 GB > 129 MB L2 (no flush)"},
+            "frame_GBps": step_bytes / (ms / 1000.0) / 1e9,
+            "frame_frac_of_peak": step_bytes / (ms / 1000.0) / 1e9 / hbm,
+            "roofline": roof, "gpu_launches": int(launches), "kernels": kern,
+            "pce": {"same_camera_min": min(pos), "foreign_max_abs": max(abs(x) for x in neg)}}
+    if ck:
+        line["clocks"] = ck
+
+    # ---- per-frame (ALL-FE) comparison: d = 1, 1000 denoise passes x 3 channels
+    if not args.no_perframe:
+        ms_pf = timed(lambda: step(d=1, images_per_pass=100), 2, 1)
+        line["perframe"] = {"value": world * M_FRAMES / (ms_pf / 1000.0), "unit": UNIT, "ms_per_step": ms_pf,
+                            "sda_speedup": ms_pf / ms}
+
+    # ---- end to end through the host-buffer entry point
+    if not args.no_e2e:
+        host = frames.cpu().pin_memory()
+        qhost = qf.cpu().pin_memory()
+        del frames
+        torch.cuda.empty_cache()
+        qdev = torch.empty_like(qf)
+
+        def step_e2e():
+            num.zero_()
+            den.zero_()
+            ctx.fingerprint_accumulate_host(host, D_SDA, num, den, groups_per_pass=4)
+            K = ctx.fingerprint_finalize(num, den, flags)
+            qdev.copy_(qhost, non_blocking=True)
+            qi = ctx.sda_average(qdev, 1)
+            for i in range(2 * N_QUERY):
+                ctx.denoise_residual(qi[i], out=wq)
+                ctx.pce_match(K[0], wq, qi[i])
+
+        ms_e2e = timed(step_e2e, 3, 1)
+        h2d = host.numel() + qhost.numel()
+        d2h = 2 * N_QUERY * 48
+        line["e2e"] = {"value": world * M_FRAMES / (ms_e2e / 1000.0), "unit": UNIT, "ms_per_step": ms_e2e,
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+        frames_host = host.numpy()
+    else:
+        frames_host = frames.cpu().numpy()
+
+    # ---- CPU baseline: the FP64 oracle on a bounded sample, rank 0 at N = 1
+    if rank == 0 and world == 1 and not args.no_cpu:
+        t, n, cores = oracle_sample(frames_host, 1)
+        line["cpu_baseline"] = {"value": n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"1 SDA group ({D_SDA} frames, 1080p RGB): mean, 3 residuals, MLE",
+                                "seconds": t}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    del np
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * prnu.h -- C ABI of libprnu: GB300 (sm_103a) kernels for PRNU camera-
+ * fingerprint extraction with Spatial Domain Averaged (SDA) frames
+ * (Taspinar, Mohanty, Memon, "Camera Fingerprint Extraction via Spatial
+ * Domain Averaged Frames").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named as device pointers must point to device memory of the
+ *   context's device; the caller owns every buffer.  Entry points that take a
+ *   workspace (`ws`, `ws_bytes`) use only that memory for intermediates and
+ *   call no allocator, except that cuFFT plans are created (and cached in the
+ *   context) on the first FFT of a given size: make that first call before
+ *   any stream capture.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   All work is enqueued asynchronously on it, except prnu_pce_match, which
+ *   synchronises the stream to return its scalars in host memory.
+ * - Arguments are validated on the host before any launch.  Invalid input
+ *   returns PRNU_EINVAL and launches nothing; a workspace that is too small
+ *   returns PRNU_ENOSPC.  A CUDA or cuFFT failure returns PRNU_ECUDA.  The
+ *   message of the last failure on the calling thread is returned by
+ *   prnu_last_error().  No C++ exception crosses this interface.
+ * - Images are planar float32 [C][H][W] in 0..255 units unless stated; frames
+ *   are uint8 interleaved [m][H][W][C] at byte offset
+ *   j*frame_stride + y*row_pitch + x*C + c.
+ * - Limits: 16 <= H, W; H, W <= 16384; C in {1, 3}; 1 <= levels <= 6 with
+ *   H, W >= 2^levels; windows odd in [1, 9]; 1 <= d <= m; d <= 65793 (so that
+ *   a group sum of uint8 frames is an exact float32 integer).
+ */
+#ifndef PRNU_H
+#define PRNU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PRNU_OK = 0,
+    PRNU_EINVAL = -1,      /* invalid argument (nothing launched) */
+    PRNU_ENOSPC = -2,      /* workspace too small (nothing launched) */
+    PRNU_ECUDA = -3,       /* CUDA runtime or cuFFT error */
+    PRNU_ETIMEOUT = -4,    /* a bounded device-side wait gave up */
+    PRNU_EUNSUPPORTED = -5 /* valid but not implemented (e.g. dtype) */
+} prnu_status;
+
+/* Flags of prnu_fingerprint_finalize. */
+#define PRNU_ZERO_MEAN 1u  /* subtract column means, then row means, per plane */
+#define PRNU_WIENER_DFT 2u /* Wiener shrink of |DFT|/sqrt(N) with var(K) noise */
+#define PRNU_TO_GRAY 4u    /* 0.299 R + 0.587 G + 0.114 B before the above */
+
+/* Denoiser parameters.  The paper names the wavelet denoiser of Mihcak et
+ * al. only by citation (Sec. IV-A, Sec. V); these are the build's reading:
+ * orthonormal periodised 8-tap Daubechies DWT, `levels` levels, local
+ * variance = min over the odd windows of the periodic box mean of c^2,
+ * var = max(0, min - sigma0^2), noise coefficient c*sigma0^2/(var+sigma0^2). */
+typedef struct {
+    int levels;      /* 4 */
+    float sigma0;    /* 3.0, in 0..255 pixel units; >= 0 */
+    int n_windows;   /* 4 */
+    int windows[4];  /* 3, 5, 7, 9 */
+    int pad_mode;    /* 0 = mirror with edge repeat to multiples of 2^levels */
+    int dtype;       /* 0 = float32 storage and arithmetic */
+} prnu_params;
+
+typedef struct prnu_ctx prnu_ctx; /* opaque; owns no per-call buffers */
+
+/* Fill *p with the defaults above.  Never fails for non-NULL p. */
+prnu_status prnu_default_params(prnu_params *p);
+
+/* Create a context on CUDA device `device`: derives the filter bank (passed
+ * to the kernels as launch parameters), creates a copy stream and events for
+ * prnu_fingerprint_accumulate_host.  *out is NULL on failure. */
+prnu_status prnu_create(prnu_ctx **out, int device);
+
+/* Destroy a context (NULL allowed).  The caller must have synchronised every
+ * stream that still runs work enqueued through it. */
+void prnu_destroy(prnu_ctx *ctx);
+
+/* Message of the last failure on the calling thread ("" if none).  The
+ * pointer stays valid until the next call on this thread. */
+const char *prnu_last_error(const prnu_ctx *ctx);
+
+/* Bytes of workspace needed by prnu_denoise_residual (images_per_pass = 1
+ * image of C planes), prnu_fingerprint_accumulate (which runs up to
+ * images_per_pass SDA frames, or frames when d = 1, per pass; more workspace
+ * means fewer passes), prnu_fingerprint_finalize and prnu_pce_match for an
+ * H x W x C geometry.  Creates the cuFFT plans of that size in the context. */
+prnu_status prnu_workspace_size(prnu_ctx *ctx, int H, int W, int C, const prnu_params *params,
+                                int images_per_pass, size_t *bytes);
+
+/* Bytes of workspace needed by prnu_fingerprint_accumulate_host for groups
+ * of d frames with groups_per_pass groups copied per chunk (two staging
+ * buffers of groups_per_pass*d packed frames plus the pass intermediates). */
+prnu_status prnu_workspace_size_host(prnu_ctx *ctx, int H, int W, int C, int d, const prnu_params *params,
+                                     int groups_per_pass, size_t *bytes);
+
+/* SDA frames, Sec. IV-B (definition of I_i^SDA): group i holds frames
+ * i*d .. min((i+1)*d, m)-1 and its SDA frame is their arithmetic mean (a
+ * ragged last group is the mean of the frames it holds).
+ * frames: device uint8 [m][H][W][C] (strides in bytes).
+ * sda_out: device float32 [ceil(m/d)][C][H][W], each value the correctly
+ * rounded float32 of the exact mean. */
+prnu_status prnu_sda_average(prnu_ctx *ctx, const uint8_t *frames, int m, int H, int W, int C,
+                             size_t frame_stride, size_t row_pitch, int d, float *sda_out, void *stream);
+
+/* Noise residual, Sec. III-A: W = I - F(I), with F the wavelet denoiser of
+ * `params`, computed as the inverse DWT of the shrunk-away (noise) detail
+ * coefficients of the mirror-padded image, cropped back to H x W.
+ * img, residual_out: device float32 [C][H][W] (may not alias). */
+prnu_status prnu_denoise_residual(prnu_ctx *ctx, const float *img, int H, int W, int C,
+                                  const prnu_params *params, float *residual_out,
+                                  void *ws, size_t ws_bytes, void *stream);
+
+/* MLE fingerprint sums, Sec. IV-A (K-hat = sum W_i I_i / sum I_i^2) over
+ * the SDA frames of Sec. IV-B (d = 1 is the conventional per-frame
+ * estimator): for every group i, I_i = its SDA frame, W_i = I_i - F(I_i), and
+ *     num += W_i * I_i,   den += I_i * I_i   (elementwise, per channel).
+ * frames: device uint8 [m][H][W][C]; num, den: device float32 [C][H][W],
+ * caller-initialised (zero to start); calls accumulate, so a long sequence
+ * may be fed in pieces whose lengths are multiples of d (checkpoint = the
+ * pair num/den plus the count of frames consumed). */
+prnu_status prnu_fingerprint_accumulate(prnu_ctx *ctx, const uint8_t *frames, int m, int H, int W, int C,
+                                        size_t frame_stride, size_t row_pitch, int d,
+                                        const prnu_params *params, float *num, float *den,
+                                        void *ws, size_t ws_bytes, void *stream);
+
+/* Same as prnu_fingerprint_accumulate, but `host_frames` is host memory
+ * (page-locked for overlap; pageable works but serialises the copies).  The
+ * frames are copied in chunks through the workspace, each copy overlapping
+ * the kernels of the previous chunk.  num, den are device pointers. */
+prnu_status prnu_fingerprint_accumulate_host(prnu_ctx *ctx, const uint8_t *host_frames, int m, int H, int W,
+                                             int C, size_t frame_stride, size_t row_pitch, int d,
+                                             const prnu_params *params, float *num, float *den,
+                                             void *ws, size_t ws_bytes, void *stream);
+
+/* Fingerprint from the MLE sums, Sec. IV-A: K = num/den (division in
+ * float64; K = 0 where den == 0), then the optional literature steps named by
+ * `flags` (not defined in the paper): PRNU_TO_GRAY, PRNU_ZERO_MEAN,
+ * PRNU_WIENER_DFT, applied in that order.
+ * num, den: device float32 [C][H][W]; K_out: device float32 [C][H][W], or
+ * [1][H][W] with PRNU_TO_GRAY (requires C == 3). */
+prnu_status prnu_fingerprint_finalize(prnu_ctx *ctx, const float *num, const float *den, int H, int W, int C,
+                                      unsigned flags, const prnu_params *params, float *K_out,
+                                      void *ws, size_t ws_bytes, void *stream);
+
+/* Peak-to-correlation energy of a query against a fingerprint (Sec. V uses
+ * PCE with threshold 60; the paper defines it only by citation).  Reading:
+ * X = W_q - mean(W_q), Y = K*I_q - mean(K*I_q) (grey planes; C == 3 inputs
+ * are converted with the 0.299/0.587/0.114 weights), C(s) = sum_x X(x)
+ * Y(x+s) circular (via cuFFT), peak at zero shift,
+ *     PCE = sign(C0) C0^2 / mean_{s outside the nbhd x nbhd block around 0} C(s)^2,
+ *     NCC = C0 / (|X| |Y|).
+ * K: device float32 [H][W] (grey fingerprint); residual_q, img_q: device
+ * float32 [C][H][W].  pce_out, ncc_out (nullable), peak_yx (nullable, the
+ * (row, col) shift of the maximum of C): host memory, written after this call
+ * synchronises `stream`.  nbhd odd, 1 <= nbhd <= min(H, W). */
+prnu_status prnu_pce_match(prnu_ctx *ctx, const float *K, const float *residual_q, const float *img_q,
+                           int H, int W, int C, int nbhd, double *pce_out, double *ncc_out, int *peak_yx,
+                           void *ws, size_t ws_bytes, void *stream);
+
+/* Per-kernel profiling (not part of the paper's method).  Every kernel launch
+ * is counted per kernel name.  With profiling on, each launch (and each cuFFT
+ * call, named cufft_*) is also bracketed by CUDA events recorded on its
+ * stream; the events are drawn from a pool the context owns. */
+prnu_status prnu_profile_enable(prnu_ctx *ctx, int on);
+
+/* Clear the counters and recorded events (waits for the recorded events). */
+prnu_status prnu_profile_reset(prnu_ctx *ctx);
+
+/* Kernel number `index` (0-based, in order of first launch): its name
+ * (NUL-terminated, truncated to name_len), launches since the last reset and
+ * the summed device time in ms of its launches recorded while profiling was
+ * on (waits for those events).  PRNU_EINVAL past the last kernel. */
+prnu_status prnu_profile_read(prnu_ctx *ctx, int index, char *name, size_t name_len, long long *launches,
+                              double *total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PRNU_H */

@@ -1,0 +1,65 @@
+// common.cuh -- shared device/host helpers of libprnu (GB300, sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/prnu.h"
+
+namespace prnu {
+
+constexpr int kTaps = 8;       // 8-tap Daubechies (4 vanishing moments)
+constexpr int kMaxLevels = 6;
+constexpr int kMaxRadius = 4;  // windows up to 9 x 9
+
+// Filter bank in float32, passed by value to kernels (kernel parameters live
+// in the constant bank).  g[k] = (-1)^k h[7-k].
+struct Filt {
+    float h[kTaps];
+    float g[kTaps];
+};
+
+// Local-variance windows.
+struct Win {
+    int n;
+    int r[4];       // radii (w-1)/2
+    float inv[4];   // 1/w^2
+};
+
+// Per-plane count of frames averaged into the plane: plane p belongs to image
+// g0 + p / C, whose frame count is min(d, m - image*d).  Details are scaled by
+// 1/count (group sums are kept exact, in "sum units", through the LL chain).
+struct PlaneScale {
+    int d, m, g0, C;
+    __device__ __forceinline__ int count(int plane) const {
+        int img = g0 + plane / C;
+        int left = m - img * d;
+        return left < d ? left : d;
+    }
+};
+
+__host__ __device__ __forceinline__ int wrap(int i, int n) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+// Mirror padding with edge repeat: index in [0, 2n) -> [0, n).
+__host__ __device__ __forceinline__ int mirror(int i, int n) { return i < n ? i : 2 * n - 1 - i; }
+
+// ---- error-free float transformations (float-float pairs) -----------------
+// TwoSum (Knuth): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// FastTwoSum (Dekker), requires |a| >= |b| or a == 0.
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace prnu

@@ -1,0 +1,131 @@
+// k_dwt.cu -- one level of the periodised orthonormal 2-D DWT (analysis),
+// rows first then columns: a[n] = sum_k h[k] x[(2n+k) mod N],
+// d[n] = sum_k g[k] x[(2n+k) mod N], g[k] = (-1)^k h[7-k].
+//
+// Difference form.  Input values are 128-ish pixel sums, the detail outputs
+// are O(1) noise, so a plain float32 filter loses the result in the rounding
+// of its large partial sums.  Every output instead works on differences to one
+// reference sample of its own support, using sum_k g[k] = 0 and
+// sum_k h[k] = sqrt(2) exactly:
+//   row pass at (y, q), ref r = v[y][2q], delta_k = v[y][2q+k] - r:
+//       lo = sqrt2 r + s,  s = sum_{k>=1} h[k] delta_k;   hi = t = sum g[k] delta_k
+//   column pass at (p, q), rows y_j = 2p+j, D_j = r_{y_j} - r_{y_0}:
+//       LL = 2 r_{y_0} + sqrt2 sum h_j D_j + sum h_j s_{y_j}
+//       LH = sqrt2 sum g_j D_j + sum g_j s_{y_j}
+//       HL = sum h_j t_{y_j},   HH = sum g_j t_{y_j}
+// The large term 2 r appears only in LL, which is carried to the next level
+// as an unevaluated float-float pair (hi, lo).  At level 1 the inputs are
+// exact integer group sums (or float32 images), so the differences are exact.
+// Details are scaled by 1/count (pixel units) when written; the LL chain stays
+// in sum units.
+#include "kernels.cuh"
+
+namespace prnu {
+
+constexpr float kSqrt2f = 1.41421356237309504880f;
+
+constexpr int TP = 16, TQ = 32;            // output tile: TP rows x TQ cols
+constexpr int IR = 2 * TP + 6, IC = 2 * TQ + 6;  // input tile with the 6-sample halo
+
+template <bool LEVEL1>
+__global__ void __launch_bounds__(256) k_analysis(AnaArgs a) {
+    __shared__ float vh[IR][IC + 1];
+    __shared__ float vl[LEVEL1 ? 1 : IR][LEVEL1 ? 1 : IC + 1];
+    __shared__ float rh[IR][TQ + 1], rl[LEVEL1 ? 1 : IR][LEVEL1 ? 1 : TQ + 1];
+    __shared__ float ss[IR][TQ + 1], tt[IR][TQ + 1];
+
+    const int plane = blockIdx.z;
+    const int p0 = blockIdx.y * TP, q0 = blockIdx.x * TQ;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int R2 = a.R >> 1, C2 = a.Cc >> 1;
+
+    // 1) input tile (periodic wrap in the padded domain; level 1 mirrors into the source)
+    for (int i = tid; i < IR * IC; i += 256) {
+        const int r = i / IC, c = i - r * IC;
+        const int gy = wrap(2 * p0 + r, a.R), gx = wrap(2 * q0 + c, a.Cc);
+        if (LEVEL1) {
+            const int sy = mirror(gy, a.H), sx = mirror(gx, a.W);
+            vh[r][c] = __ldg(a.inh + ((long long)plane * a.H + sy) * a.W + sx);
+        } else {
+            const long long o = ((long long)plane * a.R + gy) * a.Cc + gx;
+            vh[r][c] = __ldg(a.inh + o);
+            vl[r][c] = __ldg(a.inl + o);
+        }
+    }
+    __syncthreads();
+
+    // 2) row pass on differences
+    for (int i = tid; i < IR * TQ; i += 256) {
+        const int r = i / TQ, q = i - r * TQ;
+        const float refh = vh[r][2 * q];
+        const float refl = LEVEL1 ? 0.f : vl[r][2 * q];
+        float s = 0.f, t = 0.f;
+#pragma unroll
+        for (int k = 1; k < kTaps; ++k) {
+            float dlt = __fsub_rn(vh[r][2 * q + k], refh);
+            if (!LEVEL1) dlt = __fadd_rn(dlt, __fsub_rn(vl[r][2 * q + k], refl));
+            s = __fmaf_rn(a.f.h[k], dlt, s);
+            t = __fmaf_rn(a.f.g[k], dlt, t);
+        }
+        rh[r][q] = refh;
+        if (!LEVEL1) rl[r][q] = refl;
+        ss[r][q] = s;
+        tt[r][q] = t;
+    }
+    __syncthreads();
+
+    // 3) column pass
+    const float scale = a.scale_on ? __frcp_rn((float)a.sc.count(plane)) : 1.f;
+    const int q = threadIdx.x;
+    for (int pl = threadIdx.y; pl < TP; pl += blockDim.y) {
+        const int p = p0 + pl, qq = q0 + q;
+        if (p >= R2 || qq >= C2) continue;
+        const int y0 = 2 * pl;
+        const float r0h = rh[y0][q];
+        const float r0l = LEVEL1 ? 0.f : rl[y0][q];
+        float A = 0.f, B = 0.f;
+#pragma unroll
+        for (int j = 1; j < kTaps; ++j) {
+            float D = __fsub_rn(rh[y0 + j][q], r0h);
+            if (!LEVEL1) D = __fadd_rn(D, __fsub_rn(rl[y0 + j][q], r0l));
+            A = __fmaf_rn(a.f.h[j], D, A);
+            B = __fmaf_rn(a.f.g[j], D, B);
+        }
+        float Sh = 0.f, Sg = 0.f, Th = 0.f, Tg = 0.f;
+#pragma unroll
+        for (int j = 0; j < kTaps; ++j) {
+            const float s = ss[y0 + j][q], t = tt[y0 + j][q];
+            Sh = __fmaf_rn(a.f.h[j], s, Sh);
+            Sg = __fmaf_rn(a.f.g[j], s, Sg);
+            Th = __fmaf_rn(a.f.h[j], t, Th);
+            Tg = __fmaf_rn(a.f.g[j], t, Tg);
+        }
+        const float llsmall = __fmaf_rn(kSqrt2f, A, Sh);
+        const float lh = __fmaf_rn(kSqrt2f, B, Sg);
+        const long long o = ((long long)plane * R2 + p) * C2 + qq;
+        if (a.LLh) {
+            float sh, se, lo;
+            two_sum(2.f * r0h, llsmall, sh, se);
+            lo = __fadd_rn(2.f * r0l, se);
+            float hh, ll;
+            fast_two_sum(sh, lo, hh, ll);
+            a.LLh[o] = hh;
+            a.LLl[o] = ll;
+        }
+        a.LH[o] = lh * scale;
+        a.HL[o] = Th * scale;
+        a.HH[o] = Tg * scale;
+    }
+}
+
+cudaError_t launch_analysis(const AnaArgs &a, bool level1, cudaStream_t st) {
+    dim3 block(32, 8);
+    dim3 grid((unsigned)((a.Cc / 2 + TQ - 1) / TQ), (unsigned)((a.R / 2 + TP - 1) / TP), (unsigned)a.P);
+    if (level1)
+        k_analysis<true><<<grid, block, 0, st>>>(a);
+    else
+        k_analysis<false><<<grid, block, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace prnu

@@ -1,0 +1,93 @@
+// kernels.cuh -- argument blocks and launchers of the libprnu kernels.
+#pragma once
+
+#include <cufft.h>
+
+#include "common.cuh"
+
+namespace prnu {
+
+// k_sda.cu
+struct SdaArgs {
+    const uint8_t *frames;
+    long long frame_stride, row_pitch;
+    int m, H, W, C, d;
+    int g0, G;      // groups g0 .. g0+G-1 are produced, output index g - g0
+    float *out;     // [G][C][H][W]
+    int mean;       // 1: write sum/count (correctly rounded), 0: the exact sum
+};
+cudaError_t launch_sda(const SdaArgs &a, int num_sms, cudaStream_t st);
+
+// k_dwt.cu
+struct AnaArgs {
+    const float *inh;   // level 1: planes [P][H][W] virtually mirror-padded to R x Cc
+    const float *inl;   // levels >= 2: low parts [P][R][Cc]; level 1: unused
+    int R, Cc;          // input dims at this level (even)
+    int H, W;           // level 1: unpadded source dims
+    int P;
+    float *LLh, *LLl;   // [P][R/2][Cc/2]; null on the last level
+    float *LH, *HL, *HH;
+    PlaneScale sc;
+    int scale_on;
+    Filt f;
+};
+cudaError_t launch_analysis(const AnaArgs &a, bool level1, cudaStream_t st);
+
+// k_shrink.cu
+struct ShrinkArgs {
+    const float *in;      // [nplanes][R][Cc]
+    float *out;           // [nplanes][R][Cc] (must not alias `in`)
+    int R, Cc, nplanes;
+    float s2;             // sigma0^2, or taken from s2_dev[1] when s2_dev != null
+    const double *s2_dev;
+    Win win;
+};
+cudaError_t launch_shrink(const ShrinkArgs &a, cudaStream_t st);
+
+// k_idwt.cu
+struct SynArgs {
+    const float *LL;   // noise LL at this level [P][Rc][Cc], or null (zero)
+    const float *LH, *HL, *HH;
+    int Rc, Cc, P;     // coefficient dims; output is 2Rc x 2Cc
+    float *out;        // [P][2Rc][2Cc]
+    Filt f;
+};
+struct FinalArgs {
+    const float *LL;   // level-1 noise LL [P][Rc][Cc], or null (one-level transform)
+    const float *LH, *HL, *HH;
+    int Rc, Cc;        // Hp/2, Wp/2
+    int H, W, C, G;    // crop and plane map: image i, channel c -> plane i*C + c
+    const float *X;    // MLE mode: group sums [G][C][H][W]
+    PlaneScale sc;
+    float *res_out;    // residual mode: [C][H][W] (G == 1)
+    float *num, *den;  // MLE mode: [C][H][W]
+    Filt f;
+};
+cudaError_t launch_synthesis(const SynArgs &a, cudaStream_t st);
+cudaError_t launch_final(const FinalArgs &a, bool mle, cudaStream_t st);
+
+// k_fft.cu
+cudaError_t launch_divide(const float *num, const float *den, long long hw, int C, int gray, float *K, int sms,
+                          cudaStream_t st);
+cudaError_t launch_zero_mean(float *K, int H, int W, double *colmean, double *rowmean, int sms, cudaStream_t st);
+cudaError_t launch_mean_var(const float *v, long long n, double *part, int nb, double *tmp, double *out,
+                            cudaStream_t st);
+cudaError_t launch_to_complex(const float *K, long long n, cufftComplex *F, int sms, cudaStream_t st);
+cudaError_t launch_magnitude(const cufftComplex *F, long long n, float inv_sqrt_n, float *M, int sms,
+                             cudaStream_t st);
+cudaError_t launch_apply_ratio(cufftComplex *F, const float *M, const float *Mn, long long n, int sms,
+                               cudaStream_t st);
+cudaError_t launch_real_scaled(const cufftComplex *F, long long n, float scale, float *K, int sms,
+                               cudaStream_t st);
+cudaError_t launch_pce_prep(const float *K, const float *Wq, const float *Iq, long long hw, int C, float *X,
+                            float *Y, int sms, cudaStream_t st);
+cudaError_t launch_sub_center(float *v, long long n, const double *mean, int sms, cudaStream_t st);
+cudaError_t launch_cross_spectrum(const cufftComplex *FX, const cufftComplex *FY, long long n, cufftComplex *Z,
+                                  int sms, cudaStream_t st);
+cudaError_t launch_pce_reduce(const float *Cr, int H, int W, int r, int nb, double *part_e, float *part_v,
+                              long long *part_i, const double *momx, const double *momy, void *out,
+                              cudaStream_t st);
+size_t pce_scalars_bytes();
+void pce_unpack(const void *p, double *c0, double *energy, long long *peak_idx, double *nx2, double *ny2);
+
+}  // namespace prnu

@@ -1,0 +1,946 @@
+// prnu_abi.cu -- host side of libprnu: context, filter bank, argument
+// validation, workspace layout and the extern "C" entry points of prnu.h.
+#include <cufft.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "kernels.cuh"
+
+using namespace prnu;
+
+struct prnu_ctx {
+    int device = 0;
+    int sms = 0;
+    double h64[kTaps];
+    Filt filt;
+    std::mutex mu;
+    std::map<std::tuple<int, int, int>, cufftHandle> plans;  // (H, W, type) -> plan
+    std::map<std::tuple<int, int, int>, size_t> plan_work;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+    // per-kernel launch counters (always) and CUDA-event timing (opt-in)
+    bool prof_on = false;
+    std::vector<std::string> knames;
+    std::vector<long long> klaunches;
+    struct Rec {
+        int kid;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+};
+
+namespace {
+
+thread_local std::string tl_err;
+
+prnu_status fail(prnu_status s, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+prnu_status fail(prnu_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    tl_err = buf;
+    return s;
+}
+
+#define CU(call)                                                                                      \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return fail(PRNU_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define CUFFT(call)                                                                                   \
+    do {                                                                                              \
+        cufftResult r_ = (call);                                                                      \
+        if (r_ != CUFFT_SUCCESS) return fail(PRNU_ECUDA, "%s: cufft error %d", #call, (int)r_);      \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Brackets one kernel (or library call) with CUDA events on its stream when
+// profiling is on; always counts the launch.
+struct Launch {
+    prnu_ctx *ctx;
+    cudaStream_t st;
+    int kid = -1;
+    cudaEvent_t a = nullptr, b = nullptr;
+    Launch(prnu_ctx *c, const char *name, cudaStream_t s, int kernels = 1) : ctx(c), st(s) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (size_t i = 0; i < ctx->knames.size(); ++i)
+            if (ctx->knames[i] == name) kid = (int)i;
+        if (kid < 0) {
+            kid = (int)ctx->knames.size();
+            ctx->knames.push_back(name);
+            ctx->klaunches.push_back(0);
+        }
+        ctx->klaunches[kid] += kernels;
+        if (ctx->prof_on) {
+            a = take();
+            b = take();
+            if (a && b) cudaEventRecord(a, st);
+        }
+    }
+    cudaEvent_t take() {
+        if (!ctx->pool.empty()) {
+            cudaEvent_t e = ctx->pool.back();
+            ctx->pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        return cudaEventCreate(&e) == cudaSuccess ? e : nullptr;
+    }
+    ~Launch() {
+        if (a && b) {
+            cudaEventRecord(b, st);
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            ctx->recs.push_back({kid, a, b});
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Filter bank.  The 8-tap orthonormal Daubechies lowpass (4 vanishing
+// moments) is the solution of eight equations:
+//   sum_k h_k h_{k+2n} = delta_n        (n = 0..3, double-shift orthonormality)
+//   sum_k (-1)^k k^q h_k = 0            (q = 0..3, vanishing moments of g)
+// solved here by Newton's method in double precision, started from the
+// minimum-phase solution rounded to 4 decimals (Daubechies' published table),
+// which selects that solution among the equations' roots.
+// ---------------------------------------------------------------------------
+bool derive_filter(double h[kTaps]) {
+    const double init[kTaps] = {0.2304, 0.7148, 0.6309, -0.0280, -0.1870, 0.0308, 0.0329, -0.0106};
+    for (int k = 0; k < kTaps; ++k) h[k] = init[k];
+    for (int it = 0; it < 30; ++it) {
+        double F[kTaps], J[kTaps][kTaps];
+        for (int n = 0; n < 4; ++n) {
+            double s = 0.0;
+            for (int k = 0; k + 2 * n < kTaps; ++k) s += h[k] * h[k + 2 * n];
+            F[n] = s - (n == 0 ? 1.0 : 0.0);
+            for (int m = 0; m < kTaps; ++m) {
+                double d = 0.0;
+                if (m + 2 * n < kTaps) d += h[m + 2 * n];
+                if (m - 2 * n >= 0) d += h[m - 2 * n];
+                J[n][m] = d;
+            }
+        }
+        for (int q = 0; q < 4; ++q) {
+            double s = 0.0;
+            for (int k = 0; k < kTaps; ++k) {
+                const double c = (k % 2 ? -1.0 : 1.0) * std::pow((double)k, q);
+                s += c * h[k];
+                J[4 + q][k] = c;
+            }
+            F[4 + q] = s;
+        }
+        // solve J dx = F (Gaussian elimination, partial pivoting)
+        double A[kTaps][kTaps + 1];
+        for (int i = 0; i < kTaps; ++i) {
+            for (int j = 0; j < kTaps; ++j) A[i][j] = J[i][j];
+            A[i][kTaps] = F[i];
+        }
+        for (int c = 0; c < kTaps; ++c) {
+            int piv = c;
+            for (int r = c + 1; r < kTaps; ++r)
+                if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+            if (std::fabs(A[piv][c]) < 1e-300) return false;
+            if (piv != c)
+                for (int j = 0; j <= kTaps; ++j) std::swap(A[c][j], A[piv][j]);
+            for (int r = c + 1; r < kTaps; ++r) {
+                const double f = A[r][c] / A[c][c];
+                for (int j = c; j <= kTaps; ++j) A[r][j] -= f * A[c][j];
+            }
+        }
+        double dx[kTaps];
+        for (int r = kTaps - 1; r >= 0; --r) {
+            double s = A[r][kTaps];
+            for (int j = r + 1; j < kTaps; ++j) s -= A[r][j] * dx[j];
+            dx[r] = s / A[r][r];
+        }
+        for (int k = 0; k < kTaps; ++k) h[k] -= dx[k];
+    }
+    // verify: equations, normalisation sum h = sqrt(2), minimum-phase ordering
+    double sum = 0.0, worst = 0.0;
+    for (int k = 0; k < kTaps; ++k) sum += h[k];
+    for (int n = 0; n < 4; ++n) {
+        double s = 0.0;
+        for (int k = 0; k + 2 * n < kTaps; ++k) s += h[k] * h[k + 2 * n];
+        worst = std::fmax(worst, std::fabs(s - (n == 0 ? 1.0 : 0.0)));
+    }
+    for (int q = 0; q < 4; ++q) {
+        double s = 0.0;
+        for (int k = 0; k < kTaps; ++k) s += (k % 2 ? -1.0 : 1.0) * std::pow((double)k, q) * h[k];
+        worst = std::fmax(worst, std::fabs(s) / std::pow(7.0, q));
+    }
+    return worst < 1e-13 && std::fabs(sum - std::sqrt(2.0)) < 1e-12 && h[0] > 0.2 && h[1] > h[0];
+}
+
+prnu_status check_geometry(int H, int W, int C) {
+    if (H < 16 || W < 16 || H > 16384 || W > 16384) return fail(PRNU_EINVAL, "H, W must be in [16, 16384] (got %d x %d)", H, W);
+    if (C != 1 && C != 3) return fail(PRNU_EINVAL, "C must be 1 or 3 (got %d)", C);
+    return PRNU_OK;
+}
+
+prnu_status check_params(const prnu_params *p, int H, int W, Win *win) {
+    if (!p) return fail(PRNU_EINVAL, "params is NULL");
+    if (p->levels < 1 || p->levels > kMaxLevels) return fail(PRNU_EINVAL, "levels must be in [1, %d]", kMaxLevels);
+    if (H < (1 << p->levels) || W < (1 << p->levels)) return fail(PRNU_EINVAL, "H, W must be >= 2^levels");
+    if (!(p->sigma0 >= 0.f) || !std::isfinite(p->sigma0)) return fail(PRNU_EINVAL, "sigma0 must be finite and >= 0");
+    if (p->n_windows < 1 || p->n_windows > 4) return fail(PRNU_EINVAL, "n_windows must be in [1, 4]");
+    if (p->pad_mode != 0) return fail(PRNU_EUNSUPPORTED, "pad_mode %d not supported (0 = mirror)", p->pad_mode);
+    if (p->dtype != 0) return fail(PRNU_EUNSUPPORTED, "dtype %d not supported (0 = float32)", p->dtype);
+    if (win) {
+        win->n = p->n_windows;
+        for (int i = 0; i < 4; ++i) {
+            win->r[i] = 0;
+            win->inv[i] = 1.f;
+        }
+        for (int i = 0; i < p->n_windows; ++i) {
+            const int w = p->windows[i];
+            if (w < 1 || w > 2 * kMaxRadius + 1 || w % 2 == 0) return fail(PRNU_EINVAL, "windows must be odd in [1, 9]");
+            win->r[i] = w / 2;
+            win->inv[i] = (float)(1.0 / ((double)w * w));
+        }
+    }
+    return PRNU_OK;
+}
+
+inline int padded(int n, int levels) {
+    const int m = 1 << levels;
+    return (n + m - 1) / m * m;
+}
+
+// Workspace of the denoise pipeline over P planes of one geometry.
+struct Layout {
+    size_t X = 0;  // group sums [P][H][W] (accumulate only)
+    size_t LLh[kMaxLevels + 1] = {}, LLl[kMaxLevels + 1] = {}, Rn[kMaxLevels + 1] = {};
+    size_t D[kMaxLevels + 1] = {}, N[kMaxLevels + 1] = {};
+    size_t end = 0;
+};
+
+constexpr size_t kAlign = 256;
+
+Layout make_layout(int H, int W, long long P, int L, bool withX) {
+    Layout lo;
+    const long long Hp = padded(H, L), Wp = padded(W, L);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes, kAlign);
+        return o;
+    };
+    if (withX) lo.X = take((size_t)P * H * W * sizeof(float));
+    for (int l = 1; l <= L; ++l) {
+        const size_t A = (size_t)(Hp >> l) * (size_t)(Wp >> l);
+        if (l < L) {
+            lo.LLh[l] = take(P * A * sizeof(float));
+            lo.LLl[l] = take(P * A * sizeof(float));
+            lo.Rn[l] = take(P * A * sizeof(float));
+        }
+        lo.D[l] = take(3 * P * A * sizeof(float));
+        lo.N[l] = take(3 * P * A * sizeof(float));
+    }
+    lo.end = off;
+    return lo;
+}
+
+// Analysis, shrink and synthesis of P planes; the level-1 step (residual or
+// MLE) is described by `fin`, whose coefficient pointers are filled here.
+prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, const prnu_params &prm, const Win &win,
+                        PlaneScale sc, int scale_on, char *ws, const Layout &lo, FinalArgs fin, bool mle,
+                        cudaStream_t st) {
+    const int L = prm.levels;
+    const int Hp = padded(H, L), Wp = padded(W, L);
+    auto F = [&](size_t off) { return reinterpret_cast<float *>(ws + off); };
+    for (int l = 1; l <= L; ++l) {
+        const long long A = (long long)(Hp >> l) * (Wp >> l);
+        AnaArgs a{};
+        a.inh = l == 1 ? in : F(lo.LLh[l - 1]);
+        a.inl = l == 1 ? nullptr : F(lo.LLl[l - 1]);
+        a.R = Hp >> (l - 1);
+        a.Cc = Wp >> (l - 1);
+        a.H = H;
+        a.W = W;
+        a.P = P;
+        a.LLh = l < L ? F(lo.LLh[l]) : nullptr;
+        a.LLl = l < L ? F(lo.LLl[l]) : nullptr;
+        a.LH = F(lo.D[l]);
+        a.HL = F(lo.D[l]) + P * A;
+        a.HH = F(lo.D[l]) + 2 * P * A;
+        a.sc = sc;
+        a.scale_on = scale_on;
+        a.f = ctx->filt;
+        {
+            Launch t(ctx, l == 1 ? "analysis_l1" : "analysis", st);
+            CU(launch_analysis(a, l == 1, st));
+        }
+        ShrinkArgs s{};
+        s.in = F(lo.D[l]);
+        s.out = F(lo.N[l]);
+        s.R = Hp >> l;
+        s.Cc = Wp >> l;
+        s.nplanes = 3 * P;
+        s.s2 = prm.sigma0 * prm.sigma0;
+        s.s2_dev = nullptr;
+        s.win = win;
+        {
+            Launch t(ctx, "shrink", st);
+            CU(launch_shrink(s, st));
+        }
+    }
+    for (int l = L; l >= 2; --l) {
+        const long long A = (long long)(Hp >> l) * (Wp >> l);
+        SynArgs y{};
+        y.LL = l == L ? nullptr : F(lo.Rn[l]);
+        y.LH = F(lo.N[l]);
+        y.HL = F(lo.N[l]) + P * A;
+        y.HH = F(lo.N[l]) + 2 * P * A;
+        y.Rc = Hp >> l;
+        y.Cc = Wp >> l;
+        y.P = P;
+        y.out = F(lo.Rn[l - 1]);
+        y.f = ctx->filt;
+        {
+            Launch t(ctx, "synthesis", st);
+            CU(launch_synthesis(y, st));
+        }
+    }
+    const long long A1 = (long long)(Hp >> 1) * (Wp >> 1);
+    fin.LL = L == 1 ? nullptr : F(lo.Rn[1]);
+    fin.LH = F(lo.N[1]);
+    fin.HL = F(lo.N[1]) + P * A1;
+    fin.HH = F(lo.N[1]) + 2 * P * A1;
+    fin.Rc = Hp >> 1;
+    fin.Cc = Wp >> 1;
+    fin.H = H;
+    fin.W = W;
+    fin.f = ctx->filt;
+    {
+        Launch t(ctx, mle ? "final_mle" : "final_residual", st);
+        CU(launch_final(fin, mle, st));
+    }
+    return PRNU_OK;
+}
+
+prnu_status check_ws(void *ws, size_t ws_bytes, size_t need) {
+    if (need > ws_bytes) return fail(PRNU_ENOSPC, "workspace too small: need %zu bytes, got %zu", need, ws_bytes);
+    if (need > 0 && (reinterpret_cast<uintptr_t>(ws) % kAlign)) return fail(PRNU_EINVAL, "workspace must be 256-byte aligned");
+    return PRNU_OK;
+}
+
+prnu_status check_frames(const uint8_t *frames, int m, int H, int W, int C, size_t frame_stride, size_t row_pitch,
+                         int d) {
+    if (!frames) return fail(PRNU_EINVAL, "frames is NULL");
+    if (m < 1) return fail(PRNU_EINVAL, "m must be >= 1");
+    if (d < 1 || d > m) return fail(PRNU_EINVAL, "d must be in [1, m] (d=%d, m=%d)", d, m);
+    if (d > 65793) return fail(PRNU_EINVAL, "d must be <= 65793 (exact float32 group sums)");
+    if (row_pitch < (size_t)W * C) return fail(PRNU_EINVAL, "row_pitch < W*C");
+    if (m > 1 && frame_stride < (size_t)(H - 1) * row_pitch + (size_t)W * C) return fail(PRNU_EINVAL, "frame_stride too small");
+    return PRNU_OK;
+}
+
+// cuFFT plan cache: (H, W, type) -> plan without auto-allocated work area.
+prnu_status get_plan(prnu_ctx *ctx, int H, int W, cufftType type, cufftHandle *plan, size_t *work) {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    const auto key = std::make_tuple(H, W, (int)type);
+    auto it = ctx->plans.find(key);
+    if (it == ctx->plans.end()) {
+        cufftHandle p;
+        CUFFT(cufftCreate(&p));
+        CUFFT(cufftSetAutoAllocation(p, 0));
+        size_t ws = 0;
+        cufftResult r = cufftMakePlan2d(p, H, W, type, &ws);
+        if (r != CUFFT_SUCCESS) {
+            cufftDestroy(p);
+            return fail(PRNU_ECUDA, "cufftMakePlan2d(%d, %d) failed: %d", H, W, (int)r);
+        }
+        ctx->plans[key] = p;
+        ctx->plan_work[key] = ws;
+        it = ctx->plans.find(key);
+    }
+    *plan = it->second;
+    *work = ctx->plan_work[key];
+    return PRNU_OK;
+}
+
+constexpr int kRedBlocks = 512;
+
+// Workspace of finalize / pce for one plane geometry.
+struct FftLayout {
+    size_t a = 0, b = 0, c = 0;       // float / complex buffers
+    size_t colmean = 0, rowmean = 0;  // doubles
+    size_t part = 0, tmp = 0, mom0 = 0, mom1 = 0, scal = 0;
+    size_t pv = 0, pi = 0;
+    size_t work = 0, end = 0;
+};
+
+prnu_status fft_layout(prnu_ctx *ctx, int H, int W, FftLayout *out) {
+    FftLayout f;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes, kAlign);
+        return o;
+    };
+    const size_t hw = (size_t)H * W;
+    const size_t half = (size_t)H * (W / 2 + 1);
+    const size_t cbytes = std::max(hw, half) * sizeof(cufftComplex);  // a full complex plane
+    f.a = take(cbytes);
+    f.b = take(cbytes);
+    f.c = take(hw * sizeof(float) * 2);
+    f.colmean = take((size_t)W * sizeof(double));
+    f.rowmean = take((size_t)H * sizeof(double));
+    f.part = take((size_t)kRedBlocks * 2 * sizeof(double));
+    f.pv = take((size_t)kRedBlocks * sizeof(float));
+    f.pi = take((size_t)kRedBlocks * sizeof(long long));
+    f.tmp = take(2 * sizeof(double));
+    f.mom0 = take(2 * sizeof(double));
+    f.mom1 = take(2 * sizeof(double));
+    f.scal = take(pce_scalars_bytes());
+    size_t w = 0, wmax = 0;
+    cufftHandle p;
+    prnu_status s;
+    if ((s = get_plan(ctx, H, W, CUFFT_C2C, &p, &w)) != PRNU_OK) return s;
+    wmax = std::max(wmax, w);
+    if ((s = get_plan(ctx, H, W, CUFFT_R2C, &p, &w)) != PRNU_OK) return s;
+    wmax = std::max(wmax, w);
+    if ((s = get_plan(ctx, H, W, CUFFT_C2R, &p, &w)) != PRNU_OK) return s;
+    wmax = std::max(wmax, w);
+    f.work = take(wmax);
+    f.end = off;
+    *out = f;
+    return PRNU_OK;
+}
+
+inline cudaStream_t S(void *p) { return reinterpret_cast<cudaStream_t>(p); }
+
+// Process groups g0 .. g0+G-1 of `frames` (device) into num/den.
+prnu_status accumulate_pass(prnu_ctx *ctx, const uint8_t *frames, int m, int H, int W, int C, size_t fs, size_t rp,
+                            int d, int g0, int G, const prnu_params &prm, const Win &win, float *num, float *den,
+                            char *ws, cudaStream_t st) {
+    const int P = G * C;
+    const Layout lo = make_layout(H, W, P, prm.levels, true);
+    SdaArgs sa{};
+    sa.frames = frames;
+    sa.frame_stride = (long long)fs;
+    sa.row_pitch = (long long)rp;
+    sa.m = m;
+    sa.H = H;
+    sa.W = W;
+    sa.C = C;
+    sa.d = d;
+    sa.g0 = g0;
+    sa.G = G;
+    sa.out = reinterpret_cast<float *>(ws + lo.X);
+    sa.mean = 0;
+    {
+        Launch t(ctx, "sda_sum", st);
+        CU(launch_sda(sa, ctx->sms, st));
+    }
+    const PlaneScale sc{d, m, g0, C};
+    FinalArgs fin{};
+    fin.C = C;
+    fin.G = G;
+    fin.X = reinterpret_cast<const float *>(ws + lo.X);
+    fin.sc = sc;
+    fin.num = num;
+    fin.den = den;
+    return run_denoise(ctx, reinterpret_cast<const float *>(ws + lo.X), H, W, P, prm, win, sc, 1, ws, lo, fin, true, st);
+}
+
+// Largest number of groups per pass whose layout fits in `bytes`.
+int groups_fitting(int H, int W, int C, int L, size_t bytes, int gmax) {
+    int lo = 0, hi = gmax;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (make_layout(H, W, (long long)mid * C, L, true).end <= bytes)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+prnu_status prnu_default_params(prnu_params *p) {
+    if (!p) return fail(PRNU_EINVAL, "params is NULL");
+    p->levels = 4;
+    p->sigma0 = 3.0f;
+    p->n_windows = 4;
+    p->windows[0] = 3;
+    p->windows[1] = 5;
+    p->windows[2] = 7;
+    p->windows[3] = 9;
+    p->pad_mode = 0;
+    p->dtype = 0;
+    return PRNU_OK;
+}
+
+prnu_status prnu_create(prnu_ctx **out, int device) {
+    if (!out) return fail(PRNU_EINVAL, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    CU(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return fail(PRNU_EINVAL, "device %d out of range (%d devices)", device, n);
+    DeviceGuard g(device);
+    if (!g.ok) return fail(PRNU_ECUDA, "cudaSetDevice(%d) failed", device);
+    prnu_ctx *c = new prnu_ctx;
+    c->device = device;
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete c;
+        return fail(PRNU_ECUDA, "cannot query SM count");
+    }
+    if (!derive_filter(c->h64)) {
+        delete c;
+        return fail(PRNU_ECUDA, "filter bank derivation did not converge");
+    }
+    for (int k = 0; k < kTaps; ++k) {
+        c->filt.h[k] = (float)c->h64[k];
+        c->filt.g[k] = (float)((k % 2 ? -1.0 : 1.0) * c->h64[kTaps - 1 - k]);
+    }
+    if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return fail(PRNU_ECUDA, "cannot create copy stream");
+    }
+    for (int i = 0; i < 2; ++i) {
+        cudaEventCreateWithFlags(&c->ev_copied[i], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&c->ev_free[i], cudaEventDisableTiming);
+    }
+    *out = c;
+    return PRNU_OK;
+}
+
+void prnu_destroy(prnu_ctx *ctx) {
+    if (!ctx) return;
+    {
+        DeviceGuard g(ctx->device);
+        for (auto &kv : ctx->plans) cufftDestroy(kv.second);
+        if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+        for (int i = 0; i < 2; ++i) {
+            if (ctx->ev_copied[i]) cudaEventDestroy(ctx->ev_copied[i]);
+            if (ctx->ev_free[i]) cudaEventDestroy(ctx->ev_free[i]);
+        }
+        for (auto &r : ctx->recs) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        for (auto e : ctx->pool) cudaEventDestroy(e);
+    }
+    delete ctx;
+}
+
+const char *prnu_last_error(const prnu_ctx *) { return tl_err.c_str(); }
+
+prnu_status prnu_workspace_size(prnu_ctx *ctx, int H, int W, int C, const prnu_params *params, int images_per_pass,
+                                size_t *bytes) {
+    if (!ctx || !bytes) return fail(PRNU_EINVAL, "ctx/bytes is NULL");
+    prnu_status s;
+    if ((s = check_geometry(H, W, C)) != PRNU_OK) return s;
+    if ((s = check_params(params, H, W, nullptr)) != PRNU_OK) return s;
+    if (images_per_pass < 1) return fail(PRNU_EINVAL, "images_per_pass must be >= 1");
+    DeviceGuard g(ctx->device);
+    size_t need = make_layout(H, W, C, params->levels, false).end;
+    need = std::max(need, make_layout(H, W, (long long)images_per_pass * C, params->levels, true).end);
+    FftLayout f;
+    if ((s = fft_layout(ctx, H, W, &f)) != PRNU_OK) return s;
+    need = std::max(need, f.end);
+    *bytes = need;
+    return PRNU_OK;
+}
+
+prnu_status prnu_workspace_size_host(prnu_ctx *ctx, int H, int W, int C, int d, const prnu_params *params,
+                                     int groups_per_pass, size_t *bytes) {
+    if (!ctx || !bytes) return fail(PRNU_EINVAL, "ctx/bytes is NULL");
+    prnu_status s;
+    if ((s = check_geometry(H, W, C)) != PRNU_OK) return s;
+    if ((s = check_params(params, H, W, nullptr)) != PRNU_OK) return s;
+    if (groups_per_pass < 1 || d < 1) return fail(PRNU_EINVAL, "groups_per_pass and d must be >= 1");
+    const size_t frame = (size_t)H * W * C;
+    const size_t stage = align_up((size_t)groups_per_pass * d * frame, kAlign);
+    *bytes = 2 * stage + make_layout(H, W, (long long)groups_per_pass * C, params->levels, true).end;
+    return PRNU_OK;
+}
+
+prnu_status prnu_sda_average(prnu_ctx *ctx, const uint8_t *frames, int m, int H, int W, int C, size_t frame_stride,
+                             size_t row_pitch, int d, float *sda_out, void *stream) {
+    if (!ctx || !sda_out) return fail(PRNU_EINVAL, "ctx/sda_out is NULL");
+    prnu_status s;
+    if ((s = check_geometry(H, W, C)) != PRNU_OK) return s;
+    if ((s = check_frames(frames, m, H, W, C, frame_stride, row_pitch, d)) != PRNU_OK) return s;
+    DeviceGuard g(ctx->device);
+    SdaArgs a{};
+    a.frames = frames;
+    a.frame_stride = (long long)frame_stride;
+    a.row_pitch = (long long)row_pitch;
+    a.m = m;
+    a.H = H;
+    a.W = W;
+    a.C = C;
+    a.d = d;
+    a.g0 = 0;
+    a.G = (m + d - 1) / d;
+    a.out = sda_out;
+    a.mean = 1;
+    Launch t(ctx, "sda_mean", S(stream));
+    CU(launch_sda(a, ctx->sms, S(stream)));
+    return PRNU_OK;
+}
+
+prnu_status prnu_denoise_residual(prnu_ctx *ctx, const float *img, int H, int W, int C, const prnu_params *params,
+                                  float *residual_out, void *ws, size_t ws_bytes, void *stream) {
+    if (!ctx || !img || !residual_out) return fail(PRNU_EINVAL, "ctx/img/residual_out is NULL");
+    if ((const void *)img == (const void *)residual_out) return fail(PRNU_EINVAL, "img and residual_out alias");
+    prnu_status s;
+    Win win;
+    if ((s = check_geometry(H, W, C)) != PRNU_OK) return s;
+    if ((s = check_params(params, H, W, &win)) != PRNU_OK) return s;
+    const Layout lo = make_layout(H, W, C, params->levels, false);
+    if ((s = check_ws(ws, ws_bytes, lo.end)) != PRNU_OK) return s;
+    DeviceGuard g(ctx->device);
+    FinalArgs fin{};
+    fin.C = C;
+    fin.G = 1;
+    fin.res_out = residual_out;
+    fin.sc = PlaneScale{1, 1, 0, C};
+    return run_denoise(ctx, img, H, W, C, *params, win, fin.sc, 0, static_cast<char *>(ws), lo, fin, false,
+                       S(stream));
+}
+
+prnu_status prnu_fingerprint_accumulate(prnu_ctx *ctx, const uint8_t *frames, int m, int H, int W, int C,
+                                        size_t frame_stride, size_t row_pitch, int d, const prnu_params *params,
+                                        float *num, float *den, void *ws, size_t ws_bytes, void *stream) {
+    if (!ctx || !num || !den) return fail(PRNU_EINVAL, "ctx/num/den is NULL");
+    prnu_status s;
+    Win win;
+    if ((s = check_geometry(H, W, C)) != PRNU_OK) return s;
+    if ((s = check_params(params, H, W, &win)) != PRNU_OK) return s;
+    if ((s = check_frames(frames, m, H, W, C, frame_stride, row_pitch, d)) != PRNU_OK) return s;
+    const int g = (m + d - 1) / d;
+    const int Gp = groups_fitting(H, W, C, params->levels, ws_bytes, g);
+    if (Gp < 1) return check_ws(ws, ws_bytes, make_layout(H, W, C, params->levels, true).end);
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(PRNU_EINVAL, "workspace must be 256-byte aligned");
+    DeviceGuard gd(ctx->device);
+    for (int g0 = 0; g0 < g; g0 += Gp) {
+        const int G = std::min(Gp, g - g0);
+        if ((s = accumulate_pass(ctx, frames, m, H, W, C, frame_stride, row_pitch, d, g0, G, *params, win, num, den,
+                                 static_cast<char *>(ws), S(stream))) != PRNU_OK)
+            return s;
+    }
+    return PRNU_OK;
+}
+
+prnu_status prnu_fingerprint_accumulate_host(prnu_ctx *ctx, const uint8_t *host_frames, int m, int H, int W, int C,
+                                             size_t frame_stride, size_t row_pitch, int d, const prnu_params *params,
+                                             float *num, float *den, void *ws, size_t ws_bytes, void *stream) {
+    if (!ctx || !num || !den) return fail(PRNU_EINVAL, "ctx/num/den is NULL");
+    prnu_status s;
+    Win win;
+    if ((s = check_geometry(H, W, C)) != PRNU_OK) return s;
+    if ((s = check_params(params, H, W, &win)) != PRNU_OK) return s;
+    if ((s = check_frames(host_frames, m, H, W, C, frame_stride, row_pitch, d)) != PRNU_OK) return s;
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(PRNU_EINVAL, "workspace must be 256-byte aligned");
+    const int g = (m + d - 1) / d;
+    const size_t fbytes = (size_t)H * W * C;  // staged frames are packed
+    // largest groups-per-pass with two staging buffers and the pass layout
+    int Gp = 0;
+    for (int lo = 1, hi = g; lo <= hi;) {
+        const int mid = (lo + hi) / 2;
+        const size_t stage = align_up((size_t)mid * d * fbytes, kAlign);
+        const size_t need = 2 * stage + make_layout(H, W, (long long)mid * C, params->levels, true).end;
+        if (need <= ws_bytes) {
+            Gp = mid;
+            lo = mid + 1;
+        } else {
+            hi = mid - 1;
+        }
+    }
+    if (Gp < 1) {
+        const size_t need = 2 * align_up((size_t)d * fbytes, kAlign) + make_layout(H, W, C, params->levels, true).end;
+        return fail(PRNU_ENOSPC, "workspace too small: need %zu bytes, got %zu", need, ws_bytes);
+    }
+    DeviceGuard gd(ctx->device);
+    char *base = static_cast<char *>(ws);
+    const size_t stage = align_up((size_t)Gp * d * fbytes, kAlign);
+    uint8_t *buf[2] = {reinterpret_cast<uint8_t *>(base), reinterpret_cast<uint8_t *>(base + stage)};
+    char *rest = base + 2 * stage;
+    cudaStream_t st = S(stream);
+    const bool packed = row_pitch == (size_t)W * C && (m == 1 || frame_stride == (size_t)H * W * C);
+    int k = 0;
+    for (int g0 = 0; g0 < g; g0 += Gp, ++k) {
+        const int G = std::min(Gp, g - g0);
+        const int j0 = g0 * d, j1 = std::min(m, (g0 + G) * d);
+        const int b = k & 1;
+        CU(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[b], 0));
+        if (packed) {
+            CU(cudaMemcpyAsync(buf[b], host_frames + (size_t)j0 * fbytes, (size_t)(j1 - j0) * fbytes,
+                               cudaMemcpyHostToDevice, ctx->copy_stream));
+        } else {
+            for (int j = j0; j < j1; ++j)
+                CU(cudaMemcpy2DAsync(buf[b] + (size_t)(j - j0) * fbytes, (size_t)W * C,
+                                     host_frames + (size_t)j * frame_stride, row_pitch, (size_t)W * C, H,
+                                     cudaMemcpyHostToDevice, ctx->copy_stream));
+        }
+        CU(cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream));
+        CU(cudaStreamWaitEvent(st, ctx->ev_copied[b], 0));
+        // the staged chunk holds frames j0 .. j1-1, i.e. groups 0..G-1 of a
+        // sequence of (j1 - j0) frames
+        if ((s = accumulate_pass(ctx, buf[b], j1 - j0, H, W, C, fbytes, (size_t)W * C, d, 0, G, *params, win, num,
+                                 den, rest, st)) != PRNU_OK)
+            return s;
+        CU(cudaEventRecord(ctx->ev_free[b], st));
+    }
+    return PRNU_OK;
+}
+
+prnu_status prnu_fingerprint_finalize(prnu_ctx *ctx, const float *num, const float *den, int H, int W, int C,
+                                      unsigned flags, const prnu_params *params, float *K_out, void *ws,
+                                      size_t ws_bytes, void *stream) {
+    if (!ctx || !num || !den || !K_out) return fail(PRNU_EINVAL, "ctx/num/den/K_out is NULL");
+    prnu_status s;
+    Win win;
+    if ((s = check_geometry(H, W, C)) != PRNU_OK) return s;
+    if (flags & ~(PRNU_ZERO_MEAN | PRNU_WIENER_DFT | PRNU_TO_GRAY)) return fail(PRNU_EINVAL, "unknown flags");
+    if ((flags & PRNU_TO_GRAY) && C != 3) return fail(PRNU_EINVAL, "PRNU_TO_GRAY needs C == 3");
+    if ((flags & PRNU_WIENER_DFT) && (s = check_params(params, H, W, &win)) != PRNU_OK) return s;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = S(stream);
+    const long long hw = (long long)H * W;
+    const int Cout = (flags & PRNU_TO_GRAY) ? 1 : C;
+    FftLayout f{};
+    if (flags & (PRNU_ZERO_MEAN | PRNU_WIENER_DFT)) {
+        if ((s = fft_layout(ctx, H, W, &f)) != PRNU_OK) return s;
+        if ((s = check_ws(ws, ws_bytes, f.end)) != PRNU_OK) return s;
+    }
+    char *b = static_cast<char *>(ws);
+    {
+        Launch t(ctx, "finalize_divide", st);
+        CU(launch_divide(num, den, hw, C, (flags & PRNU_TO_GRAY) ? 1 : 0, K_out, ctx->sms, st));
+    }
+    for (int c = 0; c < Cout; ++c) {
+        float *K = K_out + c * hw;
+        if (flags & PRNU_ZERO_MEAN)
+            {
+                Launch t(ctx, "finalize_zero_mean", st, 3);
+                CU(launch_zero_mean(K, H, W, reinterpret_cast<double *>(b + f.colmean),
+                                    reinterpret_cast<double *>(b + f.rowmean), ctx->sms, st));
+            }
+        if (flags & PRNU_WIENER_DFT) {
+            cufftHandle plan;
+            size_t work;
+            if ((s = get_plan(ctx, H, W, CUFFT_C2C, &plan, &work)) != PRNU_OK) return s;
+            cufftComplex *F = reinterpret_cast<cufftComplex *>(b + f.a);
+            float *M = reinterpret_cast<float *>(b + f.c);
+            float *Mn = M + hw;
+            double *mom = reinterpret_cast<double *>(b + f.mom0);
+            {
+                Launch t(ctx, "mean_var", st, 4);
+                CU(launch_mean_var(K, hw, reinterpret_cast<double *>(b + f.part), kRedBlocks,
+                                   reinterpret_cast<double *>(b + f.tmp), mom, st));
+            }
+            {
+                Launch t(ctx, "to_complex", st, 1);
+                CU(launch_to_complex(K, hw, F, ctx->sms, st));
+            }
+            CUFFT(cufftSetStream(plan, st));
+            CUFFT(cufftSetWorkArea(plan, b + f.work));
+            {
+                Launch t(ctx, "cufft_c2c", st, 1);
+                CUFFT(cufftExecC2C(plan, F, F, CUFFT_FORWARD));
+            }
+            {
+                Launch t(ctx, "wiener_magnitude", st, 1);
+                CU(launch_magnitude(F, hw, (float)(1.0 / std::sqrt((double)hw)), M, ctx->sms, st));
+            }
+            ShrinkArgs sa{};
+            sa.in = M;
+            sa.out = Mn;
+            sa.R = H;
+            sa.Cc = W;
+            sa.nplanes = 1;
+            sa.s2 = 0.f;
+            sa.s2_dev = mom;  // variance of K
+            sa.win = win;
+            {
+                Launch t(ctx, "wiener_shrink", st);
+                CU(launch_shrink(sa, st));
+            }
+            {
+                Launch t(ctx, "wiener_ratio", st, 1);
+                CU(launch_apply_ratio(F, M, Mn, hw, ctx->sms, st));
+            }
+            {
+                Launch t(ctx, "cufft_c2c", st, 1);
+                CUFFT(cufftExecC2C(plan, F, F, CUFFT_INVERSE));
+            }
+            {
+                Launch t(ctx, "wiener_real", st, 1);
+                CU(launch_real_scaled(F, hw, (float)(1.0 / (double)hw), K, ctx->sms, st));
+            }
+        }
+    }
+    return PRNU_OK;
+}
+
+prnu_status prnu_pce_match(prnu_ctx *ctx, const float *K, const float *residual_q, const float *img_q, int H, int W,
+                           int C, int nbhd, double *pce_out, double *ncc_out, int *peak_yx, void *ws,
+                           size_t ws_bytes, void *stream) {
+    if (!ctx || !K || !residual_q || !img_q || !pce_out) return fail(PRNU_EINVAL, "NULL argument");
+    prnu_status s;
+    if ((s = check_geometry(H, W, C)) != PRNU_OK) return s;
+    if (nbhd < 1 || nbhd % 2 == 0 || nbhd > H || nbhd > W) return fail(PRNU_EINVAL, "nbhd must be odd and <= min(H, W)");
+    DeviceGuard g(ctx->device);
+    FftLayout f;
+    if ((s = fft_layout(ctx, H, W, &f)) != PRNU_OK) return s;
+    if ((s = check_ws(ws, ws_bytes, f.end)) != PRNU_OK) return s;
+    cudaStream_t st = S(stream);
+    char *b = static_cast<char *>(ws);
+    const long long hw = (long long)H * W;
+    float *X = reinterpret_cast<float *>(b + f.c);
+    float *Y = X + hw;
+    cufftComplex *FX = reinterpret_cast<cufftComplex *>(b + f.a);
+    cufftComplex *FY = reinterpret_cast<cufftComplex *>(b + f.b);
+    double *part = reinterpret_cast<double *>(b + f.part);
+    double *tmp = reinterpret_cast<double *>(b + f.tmp);
+    double *momx = reinterpret_cast<double *>(b + f.mom0);
+    double *momy = reinterpret_cast<double *>(b + f.mom1);
+    {
+        Launch t(ctx, "pce_prep", st, 1);
+        CU(launch_pce_prep(K, residual_q, img_q, hw, C, X, Y, ctx->sms, st));
+    }
+    {
+        Launch t(ctx, "mean_var", st, 4);
+        CU(launch_mean_var(X, hw, part, kRedBlocks, tmp, momx, st));
+    }
+    {
+        Launch t(ctx, "mean_var", st, 4);
+        CU(launch_mean_var(Y, hw, part, kRedBlocks, tmp, momy, st));
+    }
+    {
+        Launch t(ctx, "pce_center", st, 1);
+        CU(launch_sub_center(X, hw, momx, ctx->sms, st));
+    }
+    {
+        Launch t(ctx, "pce_center", st, 1);
+        CU(launch_sub_center(Y, hw, momy, ctx->sms, st));
+    }
+    cufftHandle r2c, c2r;
+    size_t w1, w2;
+    if ((s = get_plan(ctx, H, W, CUFFT_R2C, &r2c, &w1)) != PRNU_OK) return s;
+    if ((s = get_plan(ctx, H, W, CUFFT_C2R, &c2r, &w2)) != PRNU_OK) return s;
+    CUFFT(cufftSetStream(r2c, st));
+    CUFFT(cufftSetWorkArea(r2c, b + f.work));
+    {
+        Launch t(ctx, "cufft_r2c", st, 1);
+        CUFFT(cufftExecR2C(r2c, X, FX));
+    }
+    {
+        Launch t(ctx, "cufft_r2c", st, 1);
+        CUFFT(cufftExecR2C(r2c, Y, FY));
+    }
+    const long long nh = (long long)H * (W / 2 + 1);
+    {
+        Launch t(ctx, "pce_cross_spectrum", st, 1);
+        CU(launch_cross_spectrum(FX, FY, nh, FX, ctx->sms, st));
+    }
+    CUFFT(cufftSetStream(c2r, st));
+    CUFFT(cufftSetWorkArea(c2r, b + f.work));
+    {
+        Launch t(ctx, "cufft_c2r", st, 1);
+        CUFFT(cufftExecC2R(c2r, FX, X));  // X now holds hw * C(s)
+    }
+    {
+        Launch t(ctx, "pce_reduce", st, 2);
+        CU(launch_pce_reduce(X, H, W, nbhd / 2, kRedBlocks, part, reinterpret_cast<float *>(b + f.pv),
+                             reinterpret_cast<long long *>(b + f.pi), momx, momy, b + f.scal, st));
+    }
+    unsigned char host[256];
+    CU(cudaMemcpyAsync(host, b + f.scal, pce_scalars_bytes(), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    double c0, energy, nx2, ny2;
+    long long pidx;
+    pce_unpack(host, &c0, &energy, &pidx, &nx2, &ny2);
+    const double n = (double)hw;
+    const double outside = n - (double)nbhd * nbhd;
+    // c0 and energy carry the unnormalised inverse-FFT factor n (c0) and n^2
+    // (energy); PCE is invariant to it, NCC divides it out.
+    *pce_out = energy > 0.0 ? (c0 >= 0 ? 1.0 : -1.0) * c0 * c0 * outside / energy : 0.0;
+    if (ncc_out) *ncc_out = (nx2 > 0.0 && ny2 > 0.0) ? (c0 / n) / (n * std::sqrt(nx2 * ny2)) : 0.0;
+    if (peak_yx) {
+        peak_yx[0] = (int)(pidx / W);
+        peak_yx[1] = (int)(pidx % W);
+    }
+    return PRNU_OK;
+}
+
+prnu_status prnu_profile_enable(prnu_ctx *ctx, int on) {
+    if (!ctx) return fail(PRNU_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->prof_on = on != 0;
+    return PRNU_OK;
+}
+
+prnu_status prnu_profile_reset(prnu_ctx *ctx) {
+    if (!ctx) return fail(PRNU_EINVAL, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    for (auto &r : ctx->recs) {
+        cudaEventSynchronize(r.b);
+        ctx->pool.push_back(r.a);
+        ctx->pool.push_back(r.b);
+    }
+    ctx->recs.clear();
+    for (auto &n : ctx->klaunches) n = 0;
+    return PRNU_OK;
+}
+
+prnu_status prnu_profile_read(prnu_ctx *ctx, int index, char *name, size_t name_len, long long *launches,
+                              double *total_ms) {
+    if (!ctx) return fail(PRNU_EINVAL, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (index < 0 || index >= (int)ctx->knames.size()) return fail(PRNU_EINVAL, "no kernel with index %d", index);
+    if (name && name_len) {
+        std::strncpy(name, ctx->knames[index].c_str(), name_len - 1);
+        name[name_len - 1] = 0;
+    }
+    if (launches) *launches = ctx->klaunches[index];
+    if (total_ms) {
+        double t = 0.0;
+        for (auto &r : ctx->recs) {
+            if (r.kid != index) continue;
+            float ms = 0.f;
+            CU(cudaEventSynchronize(r.b));
+            CU(cudaEventElapsedTime(&ms, r.a, r.b));
+            t += ms;
+        }
+        *total_ms = t;
+    }
+    return PRNU_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,280 @@
+"""Thin ctypes binding of libprnu (include/prnu.h): same names, argument
+marshalling only.  Every step of the path runs in the library's CUDA kernels;
+there is no CPU fallback, and loading fails loudly when libprnu.so is missing.
+
+The torch-level helpers at the bottom only turn tensors into pointers, sizes,
+strides and the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libprnu.so")
+
+PRNU_OK, PRNU_EINVAL, PRNU_ENOSPC, PRNU_ECUDA, PRNU_ETIMEOUT, PRNU_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+PRNU_ZERO_MEAN, PRNU_WIENER_DFT, PRNU_TO_GRAY = 1, 2, 4
+
+# every symbol declared in include/prnu.h
+EXPORTS = (
+    "prnu_default_params", "prnu_create", "prnu_destroy", "prnu_last_error", "prnu_workspace_size",
+    "prnu_workspace_size_host", "prnu_sda_average", "prnu_denoise_residual", "prnu_fingerprint_accumulate",
+    "prnu_fingerprint_accumulate_host", "prnu_fingerprint_finalize", "prnu_pce_match",
+    "prnu_profile_enable", "prnu_profile_reset", "prnu_profile_read",
+)
+
+
+class PrnuError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libprnu status {status}: {msg}")
+        self.status = status
+
+
+class prnu_params(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("sigma0", ctypes.c_float), ("n_windows", ctypes.c_int),
+                ("windows", ctypes.c_int * 4), ("pad_mode", ctypes.c_int), ("dtype", ctypes.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp, _sz, _i, _u = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint
+_pp = ctypes.POINTER(prnu_params)
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is not built: run __graft_entry__.build() (nvcc, sm_103a)")
+            L = ctypes.CDLL(LIB_PATH)
+            sig = {
+                "prnu_default_params": [_pp],
+                "prnu_create": [ctypes.POINTER(_vp), _i],
+                "prnu_destroy": [_vp],
+                "prnu_last_error": [_vp],
+                "prnu_workspace_size": [_vp, _i, _i, _i, _pp, _i, ctypes.POINTER(_sz)],
+                "prnu_workspace_size_host": [_vp, _i, _i, _i, _i, _pp, _i, ctypes.POINTER(_sz)],
+                "prnu_sda_average": [_vp, _vp, _i, _i, _i, _i, _sz, _sz, _i, _vp, _vp],
+                "prnu_denoise_residual": [_vp, _vp, _i, _i, _i, _pp, _vp, _vp, _sz, _vp],
+                "prnu_fingerprint_accumulate": [_vp, _vp, _i, _i, _i, _i, _sz, _sz, _i, _pp, _vp, _vp, _vp, _sz, _vp],
+                "prnu_fingerprint_accumulate_host": [_vp, _vp, _i, _i, _i, _i, _sz, _sz, _i, _pp, _vp, _vp, _vp,
+                                                     _sz, _vp],
+                "prnu_fingerprint_finalize": [_vp, _vp, _vp, _i, _i, _i, _u, _pp, _vp, _vp, _sz, _vp],
+                "prnu_pce_match": [_vp, _vp, _vp, _vp, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _vp, _sz, _vp],
+                "prnu_profile_enable": [_vp, _i],
+                "prnu_profile_reset": [_vp],
+                "prnu_profile_read": [_vp, _i, ctypes.c_char_p, _sz, ctypes.POINTER(ctypes.c_longlong),
+                                      ctypes.POINTER(ctypes.c_double)],
+            }
+            for name, args in sig.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = None if name == "prnu_destroy" else (ctypes.c_char_p if name == "prnu_last_error"
+                                                                  else ctypes.c_int)
+            _lib = L
+    return _lib
+
+
+def _check(status: int, ctx=None) -> None:
+    if status != PRNU_OK:
+        msg = lib().prnu_last_error(ctx).decode(errors="replace")
+        raise PrnuError(status, msg)
+
+
+def default_params(levels=4, sigma0=3.0, windows=(3, 5, 7, 9)) -> prnu_params:
+    p = prnu_params()
+    _check(lib().prnu_default_params(ctypes.byref(p)))
+    p.levels = levels
+    p.sigma0 = sigma0
+    p.n_windows = len(windows)
+    for i, w in enumerate(windows):
+        p.windows[i] = w
+    return p
+
+
+# ------------------------------------------------------------ raw C names --
+def prnu_create(device: int = 0) -> int:
+    h = _vp()
+    _check(lib().prnu_create(ctypes.byref(h), device))
+    return h.value
+
+
+def prnu_destroy(ctx: int) -> None:
+    lib().prnu_destroy(ctx)
+
+
+def prnu_workspace_size(ctx, H, W, C, params, images_per_pass=1) -> int:
+    n = _sz()
+    _check(lib().prnu_workspace_size(ctx, H, W, C, ctypes.byref(params), images_per_pass, ctypes.byref(n)), ctx)
+    return n.value
+
+
+def prnu_workspace_size_host(ctx, H, W, C, d, params, groups_per_pass=1) -> int:
+    n = _sz()
+    _check(lib().prnu_workspace_size_host(ctx, H, W, C, d, ctypes.byref(params), groups_per_pass,
+                                          ctypes.byref(n)), ctx)
+    return n.value
+
+
+def prnu_sda_average(ctx, frames, m, H, W, C, frame_stride, row_pitch, d, sda_out, stream):
+    _check(lib().prnu_sda_average(ctx, frames, m, H, W, C, frame_stride, row_pitch, d, sda_out, stream), ctx)
+
+
+def prnu_denoise_residual(ctx, img, H, W, C, params, residual_out, ws, ws_bytes, stream):
+    _check(lib().prnu_denoise_residual(ctx, img, H, W, C, ctypes.byref(params), residual_out, ws, ws_bytes,
+                                       stream), ctx)
+
+
+def prnu_fingerprint_accumulate(ctx, frames, m, H, W, C, frame_stride, row_pitch, d, params, num, den, ws,
+                                ws_bytes, stream):
+    _check(lib().prnu_fingerprint_accumulate(ctx, frames, m, H, W, C, frame_stride, row_pitch, d,
+                                             ctypes.byref(params), num, den, ws, ws_bytes, stream), ctx)
+
+
+def prnu_fingerprint_accumulate_host(ctx, host_frames, m, H, W, C, frame_stride, row_pitch, d, params, num, den,
+                                     ws, ws_bytes, stream):
+    _check(lib().prnu_fingerprint_accumulate_host(ctx, host_frames, m, H, W, C, frame_stride, row_pitch, d,
+                                                  ctypes.byref(params), num, den, ws, ws_bytes, stream), ctx)
+
+
+def prnu_fingerprint_finalize(ctx, num, den, H, W, C, flags, params, K_out, ws, ws_bytes, stream):
+    _check(lib().prnu_fingerprint_finalize(ctx, num, den, H, W, C, flags, ctypes.byref(params), K_out, ws,
+                                           ws_bytes, stream), ctx)
+
+
+def prnu_pce_match(ctx, K, residual_q, img_q, H, W, C, nbhd, ws, ws_bytes, stream):
+    pce, ncc = ctypes.c_double(), ctypes.c_double()
+    peak = (ctypes.c_int * 2)()
+    _check(lib().prnu_pce_match(ctx, K, residual_q, img_q, H, W, C, nbhd, ctypes.byref(pce), ctypes.byref(ncc),
+                                peak, ws, ws_bytes, stream), ctx)
+    return pce.value, ncc.value, (peak[0], peak[1])
+
+
+def prnu_profile_enable(ctx, on: bool) -> None:
+    _check(lib().prnu_profile_enable(ctx, 1 if on else 0), ctx)
+
+
+def prnu_profile_reset(ctx) -> None:
+    _check(lib().prnu_profile_reset(ctx), ctx)
+
+
+def prnu_profile_read(ctx) -> dict:
+    """{kernel name: (launches, total device ms)} since the last reset."""
+    out = {}
+    i = 0
+    while True:
+        name = ctypes.create_string_buffer(64)
+        n, ms = ctypes.c_longlong(), ctypes.c_double()
+        st = lib().prnu_profile_read(ctx, i, name, 64, ctypes.byref(n), ctypes.byref(ms))
+        if st == PRNU_EINVAL:
+            break
+        _check(st, ctx)
+        out[name.value.decode()] = (n.value, ms.value)
+        i += 1
+    return out
+
+
+# ------------------------------------------------------- torch marshalling --
+class Context:
+    """One libprnu context on a CUDA device, with a cached workspace tensor.
+
+    Tensors are passed by data pointer on torch's current CUDA stream.
+    """
+
+    def __init__(self, device: int = 0):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.ctx = prnu_create(device)
+        self._ws = None
+
+    def close(self):
+        if self.ctx:
+            self.torch.cuda.synchronize(self.device)
+            prnu_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        return self.torch.cuda.current_stream(self.device).cuda_stream
+
+    def workspace(self, nbytes: int):
+        if self._ws is None or self._ws.numel() < nbytes:
+            self._ws = self.torch.empty(max(nbytes, 256), dtype=self.torch.uint8, device=f"cuda:{self.device}")
+        return self._ws
+
+    @staticmethod
+    def _frames_geometry(frames):
+        if frames.dim() == 3:
+            frames = frames.unsqueeze(-1)
+        m, H, W, C = frames.shape
+        assert frames.dtype.itemsize == 1 and frames.stride(3) == 1 and frames.stride(2) == C, \
+            "frames must be uint8 [m, H, W, C] with interleaved channels"
+        return frames, m, H, W, C, frames.stride(0), frames.stride(1)
+
+    def sda_average(self, frames, d: int):
+        frames, m, H, W, C, fs, rp = self._frames_geometry(frames)
+        out = self.torch.empty(((m + d - 1) // d, C, H, W), dtype=self.torch.float32, device=frames.device)
+        prnu_sda_average(self.ctx, frames.data_ptr(), m, H, W, C, fs, rp, d, out.data_ptr(), self._stream())
+        return out
+
+    def denoise_residual(self, img, params=None, out=None):
+        params = params or default_params()
+        if img.dim() == 2:
+            img = img.unsqueeze(0)
+        img = img.contiguous()
+        C, H, W = img.shape
+        out = self.torch.empty_like(img) if out is None else out
+        n = prnu_workspace_size(self.ctx, H, W, C, params, 1)
+        ws = self.workspace(n)
+        prnu_denoise_residual(self.ctx, img.data_ptr(), H, W, C, params, out.data_ptr(), ws.data_ptr(),
+                              ws.numel(), self._stream())
+        return out
+
+    def fingerprint_accumulate(self, frames, d: int, num, den, params=None, images_per_pass=None):
+        params = params or default_params()
+        frames, m, H, W, C, fs, rp = self._frames_geometry(frames)
+        g = (m + d - 1) // d
+        n = prnu_workspace_size(self.ctx, H, W, C, params, images_per_pass or g)
+        ws = self.workspace(n)
+        prnu_fingerprint_accumulate(self.ctx, frames.data_ptr(), m, H, W, C, fs, rp, d, params, num.data_ptr(),
+                                    den.data_ptr(), ws.data_ptr(), n, self._stream())
+
+    def fingerprint_accumulate_host(self, host_frames, d: int, num, den, params=None, groups_per_pass=1):
+        params = params or default_params()
+        host_frames, m, H, W, C, fs, rp = self._frames_geometry(host_frames)
+        n = prnu_workspace_size_host(self.ctx, H, W, C, d, params, groups_per_pass)
+        ws = self.workspace(n)
+        prnu_fingerprint_accumulate_host(self.ctx, host_frames.data_ptr(), m, H, W, C, fs, rp, d, params,
+                                         num.data_ptr(), den.data_ptr(), ws.data_ptr(), n, self._stream())
+
+    def fingerprint_finalize(self, num, den, flags: int = 0, params=None):
+        params = params or default_params()
+        C, H, W = num.shape
+        Cout = 1 if flags & PRNU_TO_GRAY else C
+        K = self.torch.empty((Cout, H, W), dtype=self.torch.float32, device=num.device)
+        n = prnu_workspace_size(self.ctx, H, W, C, params, 1)
+        ws = self.workspace(n)
+        prnu_fingerprint_finalize(self.ctx, num.data_ptr(), den.data_ptr(), H, W, C, flags, params, K.data_ptr(),
+                                  ws.data_ptr(), ws.numel(), self._stream())
+        return K
+
+    def pce_match(self, K, residual_q, img_q, nbhd: int = 11):
+        if residual_q.dim() == 2:
+            residual_q, img_q = residual_q.unsqueeze(0), img_q.unsqueeze(0)
+        C, H, W = residual_q.shape
+        K = K.reshape(H, W).contiguous()
+        n = prnu_workspace_size(self.ctx, H, W, C, default_params(), 1)
+        ws = self.workspace(n)
+        return prnu_pce_match(self.ctx, K.data_ptr(), residual_q.contiguous().data_ptr(),
+                              img_q.contiguous().data_ptr(), H, W, C, nbhd, ws.data_ptr(), ws.numel(),
+                              self._stream())

@@ -1,0 +1,223 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: SDA mean bit-exact (both sides round the exact mean once);
+residual max-abs <= 1e-3 in 0..255 units; fingerprint relative L2 <= 1e-5;
+PCE within 0.1 %.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1909_04573_gb300 import prnu as P
+from paper_1909_04573_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+RES_TOL = 1e-3
+K_TOL = 1e-5
+PCE_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_04573_gb300 import build
+    build.build()
+    c = P.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a)).cuda()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _frames(H, W, C, m, seed=0, drift=0.0):
+    return synth.frames(synth.Camera(H=H, W=W, C=C, camera_id=seed), m, drift_px=drift).numpy()
+
+
+# ------------------------------------------------------------------- SDA ----
+@pytest.mark.parametrize("H,W,C,m,d", [(16, 16, 1, 5, 2), (37, 50, 3, 11, 4), (64, 80, 3, 20, 20),
+                                       (33, 21, 1, 7, 1), (256, 256, 1, 64, 8)])
+def test_sda_average_bit_exact(ctx, H, W, C, m, d):
+    fr = np.random.default_rng(H * W + m).integers(0, 256, size=(m, H, W, C), dtype=np.uint8)
+    got = ctx.sda_average(_dev(fr), d).cpu().numpy()
+    ref = O.sda_average(fr, d).astype(np.float32)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_sda_average_strided_frames(ctx):
+    rng = np.random.default_rng(5)
+    big = rng.integers(0, 256, size=(9, 40, 70, 3), dtype=np.uint8)
+    view = _dev(big)[:, 2:34, 3:51, :]          # row pitch 210 B, frame stride 8400 B
+    got = ctx.sda_average(view, 3).cpu().numpy()
+    ref = O.sda_average(np.ascontiguousarray(big[:, 2:34, 3:51, :]), 3).astype(np.float32)
+    np.testing.assert_array_equal(got, ref)
+
+
+# -------------------------------------------------------------- residual ----
+@pytest.mark.parametrize("H,W,C", [(16, 16, 1), (37, 50, 1), (64, 64, 3), (100, 300, 1), (256, 256, 1),
+                                   (272, 480, 3)])
+def test_denoise_residual_matches_oracle(ctx, H, W, C):
+    fr = _frames(H, W, C, 1, seed=H + W)
+    img = fr[0].transpose(2, 0, 1).astype(np.float32)
+    got = ctx.denoise_residual(_dev(img)).cpu().numpy()
+    ref = O.residual(img.astype(np.float64))
+    assert np.abs(got - ref).max() <= RES_TOL
+    assert _rel(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("levels,sigma0,windows", [(1, 3.0, (3, 5, 7, 9)), (2, 2.0, (3,)), (5, 3.0, (5, 9)),
+                                                   (4, 0.5, (1, 3)), (3, 6.0, (9, 7, 5, 3))])
+def test_denoise_residual_parameters(ctx, levels, sigma0, windows):
+    img = _frames(64, 96, 1, 1, seed=11)[0].transpose(2, 0, 1).astype(np.float32)
+    got = ctx.denoise_residual(_dev(img), P.default_params(levels, sigma0, windows)).cpu().numpy()
+    ref = O.residual(img.astype(np.float64), O.Params(levels=levels, sigma0=sigma0, windows=tuple(windows)))
+    assert np.abs(got - ref).max() <= RES_TOL
+
+
+def test_denoise_residual_degenerate_cases(ctx):
+    const = np.full((1, 48, 48), 131.0, np.float32)
+    assert np.abs(ctx.denoise_residual(_dev(const)).cpu().numpy()).max() <= 1e-4
+    img = _frames(48, 48, 1, 1, seed=2)[0].transpose(2, 0, 1).astype(np.float32)
+    w0 = ctx.denoise_residual(_dev(img), P.default_params(sigma0=0.0)).cpu().numpy()
+    assert np.all(w0 == 0.0)
+
+
+# ------------------------------------------------------------ fingerprint ---
+def _accumulate(ctx, fr, d, images_per_pass=None):
+    m, H, W, C = fr.shape
+    num = torch.zeros((C, H, W), dtype=torch.float32, device="cuda")
+    den = torch.zeros_like(num)
+    ctx.fingerprint_accumulate(_dev(fr), d, num, den, images_per_pass=images_per_pass)
+    return num.cpu().numpy(), den.cpu().numpy()
+
+
+@pytest.mark.parametrize("H,W,C,m,d,drift", [(256, 256, 1, 64, 8, 0.0),    # small config: 8 SDA groups
+                                              (64, 80, 1, 37, 8, 0.0),      # ragged last group
+                                              (48, 64, 1, 12, 1, 0.0),      # per-frame estimator
+                                              (96, 128, 3, 30, 10, 2.0)])   # RGB, drifting scene
+def test_fingerprint_accumulate_matches_oracle(ctx, H, W, C, m, d, drift):
+    fr = _frames(H, W, C, m, seed=m, drift=drift)
+    num, den = _accumulate(ctx, fr, d)
+    onum, oden = O.fingerprint_accumulate(fr, d)
+    assert _rel(den, oden) <= 1e-6
+    assert _rel(num, onum) <= K_TOL
+    K = ctx.fingerprint_finalize(_dev(num), _dev(den)).cpu().numpy()
+    assert _rel(K, O.fingerprint_finalize(onum, oden)) <= K_TOL
+
+
+def test_multipass_accumulate_and_determinism(ctx):
+    fr = _frames(64, 64, 3, 24, seed=4)
+    n1, d1 = _accumulate(ctx, fr, 4)                      # all six groups in one pass
+    n2, d2 = _accumulate(ctx, fr, 4, images_per_pass=1)   # a smaller workspace: several passes
+    n3, d3 = _accumulate(ctx, fr, 4)
+    np.testing.assert_array_equal(n1, n3)                 # run to run
+    np.testing.assert_array_equal(d1, d3)
+    assert _rel(n2, n1) <= 1e-6 and _rel(d2, d1) <= 1e-6
+
+
+def test_accumulate_host_equals_device(ctx):
+    fr = _frames(48, 64, 3, 20, seed=6)
+    num = torch.zeros((3, 48, 64), dtype=torch.float32, device="cuda")
+    den = torch.zeros_like(num)
+    host = torch.from_numpy(fr).pin_memory()
+    ctx.fingerprint_accumulate_host(host, 5, num, den, groups_per_pass=2)
+    n2, d2 = _accumulate(ctx, fr, 5, images_per_pass=2)
+    torch.cuda.synchronize()
+    assert _rel(num.cpu().numpy(), n2) <= 1e-6
+    assert _rel(den.cpu().numpy(), d2) <= 1e-6
+
+
+@pytest.mark.parametrize("flags", [0, P.PRNU_ZERO_MEAN, P.PRNU_TO_GRAY, P.PRNU_TO_GRAY | P.PRNU_ZERO_MEAN,
+                                   P.PRNU_WIENER_DFT, P.PRNU_TO_GRAY | P.PRNU_ZERO_MEAN | P.PRNU_WIENER_DFT])
+def test_finalize_flags(ctx, flags):
+    rng = np.random.default_rng(flags)
+    C, H, W = 3, 60, 84
+    den = rng.uniform(1e4, 5e4, size=(C, H, W)).astype(np.float32)
+    num = (den * rng.normal(0, 0.01, size=(C, H, W))).astype(np.float32)
+    den[0, 3, 5] = 0.0
+    got = ctx.fingerprint_finalize(_dev(num), _dev(den), flags).cpu().numpy()
+    ref = O.fingerprint_finalize(num.astype(np.float64), den.astype(np.float64), flags)
+    assert got.shape == ref.shape
+    assert _rel(got, ref) <= K_TOL
+
+
+# ------------------------------------------------------------------- PCE ----
+@pytest.mark.parametrize("H,W,C", [(64, 64, 1), (96, 80, 3), (256, 256, 1)])
+def test_pce_matches_oracle(ctx, H, W, C):
+    rng = np.random.default_rng(H * C)
+    K = rng.normal(0, 0.01, size=(H, W))
+    Iq = rng.uniform(40, 220, size=(C, H, W))
+    Wq = K[None] * Iq + rng.normal(0, 0.7, size=(C, H, W))
+    pce, ncc, peak = ctx.pce_match(_dev(K.astype(np.float32)), _dev(Wq.astype(np.float32)),
+                                   _dev(Iq.astype(np.float32)))
+    r = O.pce_match(K, O.to_gray(Wq.astype(np.float32)), O.to_gray(Iq.astype(np.float32)))
+    assert abs(pce - r.pce) <= PCE_TOL * abs(r.pce)
+    assert abs(ncc - r.ncc) <= 1e-4 * abs(r.ncc)
+    assert peak == r.peak == (0, 0)
+
+
+def test_planted_camera_end_to_end(ctx):
+    # 64 grayscale 256x256 frames, SDA groups of 8; one same-camera and one
+    # foreign query; PCE threshold 60 (Sec. V) separates them on both sides
+    cam = synth.Camera(H=256, W=256, C=1, camera_id=21)
+    fr = synth.frames(cam, 64).numpy()
+    num, den = _accumulate(ctx, fr, 8)
+    K = ctx.fingerprint_finalize(_dev(num), _dev(den))
+    onum, oden = O.fingerprint_accumulate(fr, 8)
+    oK = O.fingerprint_finalize(onum, oden)[0]
+    for qcam, positive in ((cam, True), (synth.foreign(cam), False)):
+        q = synth.frames(qcam, 1, stream=1).numpy()[0].transpose(2, 0, 1).astype(np.float32)
+        wq = ctx.denoise_residual(_dev(q))
+        pce, _, _ = ctx.pce_match(K[0], wq, _dev(q))
+        ref = O.pce_match(oK, O.residual(q.astype(np.float64))[0], q[0].astype(np.float64)).pce
+        assert abs(pce - ref) <= PCE_TOL * abs(ref)
+        assert (pce > 60) == positive
+
+
+# ------------------------------------------------------------ full size -----
+@pytest.mark.slow
+def test_full_hd_rgb_sda50_two_groups(ctx):
+    # 1920x1080 RGB with a drifting scene, SDA groups of 50 (the video-scale
+    # geometry: 1080 rows need mirror padding to 1088); two groups
+    cam = synth.Camera(H=1080, W=1920, C=3, camera_id=31)
+    fr = synth.frames(cam, 100, device="cuda", drift_px=2.0)
+    num = torch.zeros((3, 1080, 1920), dtype=torch.float32, device="cuda")
+    den = torch.zeros_like(num)
+    ctx.fingerprint_accumulate(fr, 50, num, den)
+    onum, oden = O.fingerprint_accumulate(fr.cpu().numpy(), 50)
+    assert _rel(den.cpu().numpy(), oden) <= 1e-6
+    assert _rel(num.cpu().numpy(), onum) <= K_TOL
+    # one SDA frame's residual, all three channels
+    sda = ctx.sda_average(fr[:50], 50)[0]
+    got = ctx.denoise_residual(sda).cpu().numpy()
+    ref = O.residual(O.sda_average(fr[:50].cpu().numpy(), 50)[0])
+    assert np.abs(got - ref).max() <= RES_TOL
+
+
+# --------------------------------------------------------------- errors -----
+def test_invalid_arguments_are_rejected(ctx):
+    img = torch.zeros((1, 8, 8), dtype=torch.float32, device="cuda")
+    with pytest.raises(P.PrnuError) as e:
+        ctx.denoise_residual(img)
+    assert e.value.status == P.PRNU_EINVAL
+    fr = torch.zeros((4, 32, 32, 2), dtype=torch.uint8, device="cuda")
+    with pytest.raises(P.PrnuError):
+        ctx.sda_average(fr, 2)
+    with pytest.raises(P.PrnuError):
+        ctx.denoise_residual(torch.zeros((1, 32, 32), device="cuda"), P.default_params(windows=(4,)))
+    p = P.default_params()
+    n = P.prnu_workspace_size(ctx.ctx, 64, 64, 1, p, 1)
+    ws = torch.empty(n, dtype=torch.uint8, device="cuda")
+    x = torch.zeros((1, 64, 64), device="cuda")
+    with pytest.raises(P.PrnuError) as e:
+        P.prnu_denoise_residual(ctx.ctx, x.data_ptr(), 64, 64, 1, p, torch.empty_like(x).data_ptr(),
+                                ws.data_ptr(), 1024, ctx._stream())
+    assert e.value.status == P.PRNU_ENOSPC
