@@ -114,6 +114,26 @@ prnu_status prnu_denoise_residual(prnu_ctx *ctx, const float *img, int H, int W,
                                   const prnu_params *params, float *residual_out,
                                   void *ws, size_t ws_bytes, void *stream);
 
+/* Allocation-free variant of prnu_denoise_residual (the paper has no
+ * counterpart: this is an interface convenience).  For callers that cannot
+ * allocate device memory when they need a residual -- code running inside a
+ * CUDA stream capture, plug-ins whose host application owns every device
+ * allocation, services that fix their memory footprint at start-up -- the
+ * intermediates live in a fixed 64 MiB file-scope device array of the library
+ * instead of a caller workspace.  The caller still passes img and
+ * residual_out (same layout and meaning as prnu_denoise_residual).  Images
+ * whose intermediates exceed 64 MiB (e.g. 1920x1080 RGB; 1920x1080 grey and
+ * 1280x720 RGB fit) return PRNU_ENOSPC with a message and launch nothing.
+ * The first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress, which loads the module that holds the array): make
+ * that first call before any stream capture.  Every GPU on which the array's
+ * module is loaded keeps the 64 MiB until the process exits.  All calls on a
+ * device share the array: calls whose GPU work may overlap (other streams or
+ * threads without ordering) race and corrupt each other's results; calls
+ * ordered on one stream are safe, and no clearing is needed between them. */
+prnu_status prnu_denoise_residual_static(prnu_ctx *ctx, const float *img, int H, int W, int C,
+                                         const prnu_params *params, float *residual_out, void *stream);
+
 /* MLE fingerprint sums, Sec. IV-A (K-hat = sum W_i I_i / sum I_i^2) over
  * the SDA frames of Sec. IV-B (d = 1 is the conventional per-frame
  * estimator): for every group i, I_i = its SDA frame, W_i = I_i - F(I_i), and

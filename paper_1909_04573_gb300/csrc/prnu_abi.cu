@@ -484,6 +484,13 @@ int groups_fitting(int H, int W, int C, int L, size_t bytes, int gmax) {
 
 }  // namespace
 
+// Accessors for the allocation-free entry point (prnu_static.cu).
+namespace prnu {
+int ctx_device(const prnu_ctx *ctx) { return ctx->device; }
+size_t denoise_scratch_bytes(int H, int W, int C, int levels) { return make_layout(H, W, C, levels, false).end; }
+prnu_status set_last_error(prnu_status s, const char *msg) { return fail(s, "%s", msg); }
+}  // namespace prnu
+
 // ===========================================================================
 extern "C" {
 

@@ -22,7 +22,7 @@ EXPORTS = (
     "prnu_default_params", "prnu_create", "prnu_destroy", "prnu_last_error", "prnu_workspace_size",
     "prnu_workspace_size_host", "prnu_sda_average", "prnu_denoise_residual", "prnu_fingerprint_accumulate",
     "prnu_fingerprint_accumulate_host", "prnu_fingerprint_finalize", "prnu_pce_match",
-    "prnu_profile_enable", "prnu_profile_reset", "prnu_profile_read",
+    "prnu_profile_enable", "prnu_profile_reset", "prnu_profile_read", "prnu_denoise_residual_static",
 )
 
 
@@ -65,6 +65,7 @@ def lib() -> ctypes.CDLL:
                 "prnu_fingerprint_finalize": [_vp, _vp, _vp, _i, _i, _i, _u, _pp, _vp, _vp, _sz, _vp],
                 "prnu_pce_match": [_vp, _vp, _vp, _vp, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _vp, _sz, _vp],
+                "prnu_denoise_residual_static": [_vp, _vp, _i, _i, _i, _pp, _vp, _vp],
                 "prnu_profile_enable": [_vp, _i],
                 "prnu_profile_reset": [_vp],
                 "prnu_profile_read": [_vp, _i, ctypes.c_char_p, _sz, ctypes.POINTER(ctypes.c_longlong),
@@ -152,6 +153,12 @@ def prnu_pce_match(ctx, K, residual_q, img_q, H, W, C, nbhd, ws, ws_bytes, strea
     _check(lib().prnu_pce_match(ctx, K, residual_q, img_q, H, W, C, nbhd, ctypes.byref(pce), ctypes.byref(ncc),
                                 peak, ws, ws_bytes, stream), ctx)
     return pce.value, ncc.value, (peak[0], peak[1])
+
+
+def prnu_denoise_residual_static(ctx, img, H, W, C, params, residual_out, stream):
+    """prnu_denoise_residual with the library's fixed static scratch: no
+    workspace argument and no allocation (for callers that cannot allocate)."""
+    _check(lib().prnu_denoise_residual_static(ctx, img, H, W, C, ctypes.byref(params), residual_out, stream), ctx)
 
 
 def prnu_profile_enable(ctx, on: bool) -> None:
