@@ -16,7 +16,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
@@ -145,22 +144,6 @@ def reference_arm(args, rank):
 
 
 # --------------------------------------------------------------- GPU arm ---
-def algorithmic_bytes(name, m, d, G):
-    """Compulsory bytes per step of each kernel family (see the design notes)."""
-    hp, wp = 1088, 1920
-    P = G * C
-    px = H * W
-    if name == "sda_sum":
-        return m * px * C + P * px * 4
-    if name == "analysis_l1":
-        a1 = (hp // 2) * (wp // 2)
-        return P * px * 4 + P * a1 * (8 + 12)
-    if name == "final_mle":
-        a1 = (hp // 2) * (wp // 2)
-        return P * a1 * 16 + P * px * 4 + C * px * 16
-    return None
-
-
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -195,7 +178,7 @@ def main():
     qimg = ctx.sda_average(qf, 1)                                         # [20, 3, H, W] float
     num = torch.zeros((C, H, W), dtype=torch.float32, device=dev)
     den = torch.zeros_like(num)
-    wq = torch.empty((C, H, W), dtype=torch.float32, device=dev)
+    wq = torch.empty_like(qimg)
     flags = P.PRNU_TO_GRAY | P.PRNU_ZERO_MEAN | P.PRNU_WIENER_DFT
     pces = []
 
@@ -204,10 +187,8 @@ def main():
         den.zero_()
         ctx.fingerprint_accumulate(frames, d, num, den, images_per_pass=images_per_pass)
         K = ctx.fingerprint_finalize(num, den, flags)
-        pces.clear()
-        for i in range(2 * N_QUERY):
-            ctx.denoise_residual(qimg[i], out=wq)
-            pces.append(ctx.pce_match(K[0], wq, qimg[i])[0])
+        ctx.denoise_residual_batch(qimg, out=wq)
+        pces[:] = [r[0] for r in ctx.pce_match_batch(K[0], wq, qimg)]
 
     def timed(fn, steps, warmup):
         for _ in range(warmup):
@@ -249,26 +230,22 @@ def main():
     own = {k: v for k, v in prof.items() if not k.startswith("cufft")}
     launches = sum(v[0] for v in own.values())
     total_dev = sum(v[1] for v in prof.values())
-    G = math.ceil(M_FRAMES / D_SDA)
     hbm, peak_kind = peaks()
     kern = {}
-    for k, (n, t) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
-        ab = algorithmic_bytes(k, M_FRAMES, D_SDA, G)
-        per = n / args.steps
-        e = {"launches_per_step": per, "ms_per_step": t / args.steps, "share": t / total_dev if total_dev else None}
-        if ab is not None and t > 0:
-            e["algorithmic_GBps"] = ab * args.steps / (t / 1000.0) / 1e9
+    for k, (n, t, nbytes) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
+        e = {"launches_per_step": n / args.steps, "ms_per_step": t / args.steps,
+             "share": t / total_dev if total_dev else None}
+        if nbytes > 0 and t > 0:
+            e["algorithmic_GBps"] = nbytes / (t / 1000.0) / 1e9
         kern[k] = e
     dom = max(own.items(), key=lambda kv: kv[1][1])[0]
-    dom_bytes = algorithmic_bytes(dom, M_FRAMES, D_SDA, G)
-    dom_n, dom_t = own[dom]
+    dom_n, dom_t, dom_b = own[dom]
     roof = None
-    if dom_bytes is not None:
-        per_launch_bytes = dom_bytes * args.steps / dom_n
-        ach = per_launch_bytes / (dom_t / dom_n / 1000.0) / 1e9
+    if dom_b > 0 and dom_n > 0:
+        ach = (dom_b / dom_n) / (dom_t / dom_n / 1000.0) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "peak_kind": f"{peak_kind} (copy)", "traffic": None,
-                "bytes_per_launch": per_launch_bytes}
+                "frac": ach / hbm, "peak_kind": f"{peak_kind} copy bandwidth", "traffic": None,
+                "bytes_per_launch": dom_b / dom_n, "launches": dom_n, "ms_per_launch": dom_t / dom_n}
     step_bytes = M_FRAMES * H * W * C
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -304,15 +281,27 @@ def main():
             K = ctx.fingerprint_finalize(num, den, flags)
             qdev.copy_(qhost, non_blocking=True)
             qi = ctx.sda_average(qdev, 1)
-            for i in range(2 * N_QUERY):
-                ctx.denoise_residual(qi[i], out=wq)
-                ctx.pce_match(K[0], wq, qi[i])
+            ctx.denoise_residual_batch(qi, out=wq)
+            ctx.pce_match_batch(K[0], wq, qi)
 
         ms_e2e = timed(step_e2e, 3, 1)
+        # raw pinned H2D bandwidth of one 1 GiB copy, for context
+        probe = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
+        src = host.view(-1)[: 1 << 30]
+        probe.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        probe.copy_(src, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        h2d_gbps = (1 << 30) / (e0.elapsed_time(e1) / 1000.0) / 1e9
+        del probe
         h2d = host.numel() + qhost.numel()
         d2h = 2 * N_QUERY * 48
         line["e2e"] = {"value": world * M_FRAMES / (ms_e2e / 1000.0), "unit": UNIT, "ms_per_step": ms_e2e,
-                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                       "pinned_h2d_GBps": h2d_gbps}
         frames_host = host.numpy()
     else:
         frames_host = frames.cpu().numpy()

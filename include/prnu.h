@@ -83,11 +83,12 @@ void prnu_destroy(prnu_ctx *ctx);
  * pointer stays valid until the next call on this thread. */
 const char *prnu_last_error(const prnu_ctx *ctx);
 
-/* Bytes of workspace needed by prnu_denoise_residual (images_per_pass = 1
- * image of C planes), prnu_fingerprint_accumulate (which runs up to
- * images_per_pass SDA frames, or frames when d = 1, per pass; more workspace
- * means fewer passes), prnu_fingerprint_finalize and prnu_pce_match for an
- * H x W x C geometry.  Creates the cuFFT plans of that size in the context. */
+/* Bytes of workspace needed, for an H x W x C geometry, by
+ * prnu_denoise_residual_batch and prnu_pce_match_batch with n <=
+ * images_per_pass, by prnu_fingerprint_accumulate running up to
+ * images_per_pass SDA frames (frames when d = 1) per pass (a larger workspace
+ * means fewer passes), and by prnu_fingerprint_finalize.  Creates the cuFFT
+ * plans of that size and batch in the context. */
 prnu_status prnu_workspace_size(prnu_ctx *ctx, int H, int W, int C, const prnu_params *params,
                                 int images_per_pass, size_t *bytes);
 
@@ -113,6 +114,13 @@ prnu_status prnu_sda_average(prnu_ctx *ctx, const uint8_t *frames, int m, int H,
 prnu_status prnu_denoise_residual(prnu_ctx *ctx, const float *img, int H, int W, int C,
                                   const prnu_params *params, float *residual_out,
                                   void *ws, size_t ws_bytes, void *stream);
+
+/* Batched residuals, Sec. III-A: n independent images img [n][C][H][W] ->
+ * residual_out [n][C][H][W] in one pass of the kernels (same semantics as n
+ * calls of prnu_denoise_residual). */
+prnu_status prnu_denoise_residual_batch(prnu_ctx *ctx, const float *img, int n, int H, int W, int C,
+                                        const prnu_params *params, float *residual_out,
+                                        void *ws, size_t ws_bytes, void *stream);
 
 /* Allocation-free variant of prnu_denoise_residual (the paper has no
  * counterpart: this is an interface convenience).  For callers that cannot
@@ -181,6 +189,14 @@ prnu_status prnu_pce_match(prnu_ctx *ctx, const float *K, const float *residual_
                            int H, int W, int C, int nbhd, double *pce_out, double *ncc_out, int *peak_yx,
                            void *ws, size_t ws_bytes, void *stream);
 
+/* PCE of n queries against one grey fingerprint K (same semantics as n
+ * calls of prnu_pce_match, one stream synchronisation): residual_q and img_q
+ * are device float32 [n][C][H][W]; pce_out[n], ncc_out[n] (nullable) and
+ * peak_yx[2n] (nullable) are host memory. */
+prnu_status prnu_pce_match_batch(prnu_ctx *ctx, const float *K, const float *residual_q, const float *img_q, int n,
+                                 int H, int W, int C, int nbhd, double *pce_out, double *ncc_out, int *peak_yx,
+                                 void *ws, size_t ws_bytes, void *stream);
+
 /* Per-kernel profiling (not part of the paper's method).  Every kernel launch
  * is counted per kernel name.  With profiling on, each launch (and each cuFFT
  * call, named cufft_*) is also bracketed by CUDA events recorded on its
@@ -191,11 +207,13 @@ prnu_status prnu_profile_enable(prnu_ctx *ctx, int on);
 prnu_status prnu_profile_reset(prnu_ctx *ctx);
 
 /* Kernel number `index` (0-based, in order of first launch): its name
- * (NUL-terminated, truncated to name_len), launches since the last reset and
- * the summed device time in ms of its launches recorded while profiling was
- * on (waits for those events).  PRNU_EINVAL past the last kernel. */
+ * (NUL-terminated, truncated to name_len), launches since the last reset, the
+ * summed device time in ms of its launches recorded while profiling was on
+ * (waits for those events) and the algorithmic bytes of the counted launches
+ * (each input byte read once, each output byte written once; 0 for cuFFT).
+ * Any output pointer may be NULL.  PRNU_EINVAL past the last kernel. */
 prnu_status prnu_profile_read(prnu_ctx *ctx, int index, char *name, size_t name_len, long long *launches,
-                              double *total_ms);
+                              double *total_ms, double *bytes);
 
 #ifdef __cplusplus
 }

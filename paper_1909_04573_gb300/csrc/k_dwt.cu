@@ -24,60 +24,92 @@ namespace prnu {
 
 constexpr float kSqrt2f = 1.41421356237309504880f;
 
-constexpr int TP = 16, TQ = 32;            // output tile: TP rows x TQ cols
+constexpr int TP = 16, TQ = 32;                 // output tile: TP rows x TQ cols
 constexpr int IR = 2 * TP + 6, IC = 2 * TQ + 6;  // input tile with the 6-sample halo
+constexpr int ICS = IC + 2;                      // even row stride: float2-aligned rows
+constexpr int NCOL = (IC + 31) / 32;             // input columns per thread
 
 template <bool LEVEL1>
 __global__ void __launch_bounds__(256) k_analysis(AnaArgs a) {
-    __shared__ float vh[IR][IC + 1];
-    __shared__ float vl[LEVEL1 ? 1 : IR][LEVEL1 ? 1 : IC + 1];
+    __shared__ __align__(16) float vh[IR][ICS];
+    __shared__ __align__(16) float vl[LEVEL1 ? 1 : IR][LEVEL1 ? 2 : ICS];
     __shared__ float rh[IR][TQ + 1], rl[LEVEL1 ? 1 : IR][LEVEL1 ? 1 : TQ + 1];
     __shared__ float ss[IR][TQ + 1], tt[IR][TQ + 1];
 
     const int plane = blockIdx.z;
     const int p0 = blockIdx.y * TP, q0 = blockIdx.x * TQ;
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int tx = threadIdx.x, ty = threadIdx.y;
     const int R2 = a.R >> 1, C2 = a.Cc >> 1;
 
-    // 1) input tile (periodic wrap in the padded domain; level 1 mirrors into the source)
-    for (int i = tid; i < IR * IC; i += 256) {
-        const int r = i / IC, c = i - r * IC;
-        const int gy = wrap(2 * p0 + r, a.R), gx = wrap(2 * q0 + c, a.Cc);
-        if (LEVEL1) {
-            const int sy = mirror(gy, a.H), sx = mirror(gx, a.W);
-            vh[r][c] = __ldg(a.inh + ((long long)plane * a.H + sy) * a.W + sx);
-        } else {
-            const long long o = ((long long)plane * a.R + gy) * a.Cc + gx;
-            vh[r][c] = __ldg(a.inh + o);
-            vl[r][c] = __ldg(a.inl + o);
+    // 1) input tile: periodic wrap in the (padded) domain; level 1 mirrors the
+    //    padded index into the unpadded source.  Column sources are computed
+    //    once per thread, row sources once per row.
+    int srcx[NCOL];
+#pragma unroll
+    for (int k = 0; k < NCOL; ++k) {
+        const int c = tx + 32 * k;
+        const int gx = wrap(2 * q0 + c, a.Cc);
+        srcx[k] = LEVEL1 ? mirror(gx, a.W) : gx;
+    }
+    const int srcH = LEVEL1 ? a.H : a.R, srcW = LEVEL1 ? a.W : a.Cc;
+    for (int r = ty; r < IR; r += 8) {
+        const int gy = wrap(2 * p0 + r, a.R);
+        const int sy = LEVEL1 ? mirror(gy, a.H) : gy;
+        const long long rowoff = ((long long)plane * srcH + sy) * srcW;
+#pragma unroll
+        for (int k = 0; k < NCOL; ++k) {
+            const int c = tx + 32 * k;
+            if (c < IC) {
+                vh[r][c] = __ldg(a.inh + rowoff + srcx[k]);
+                if (!LEVEL1) vl[r][c] = __ldg(a.inl + rowoff + srcx[k]);
+            }
         }
     }
     __syncthreads();
 
-    // 2) row pass on differences
-    for (int i = tid; i < IR * TQ; i += 256) {
-        const int r = i / TQ, q = i - r * TQ;
-        const float refh = vh[r][2 * q];
-        const float refl = LEVEL1 ? 0.f : vl[r][2 * q];
-        float s = 0.f, t = 0.f;
+    // 2) row pass on differences; thread tx owns output column q = tx and reads
+    //    the 8 input samples 2q..2q+7 as four float2 (conflict-free)
+    {
+        const int q = tx;
+        for (int r = ty; r < IR; r += 8) {
+            float v[8], w[8];
+            const float2 *row = reinterpret_cast<const float2 *>(&vh[r][0]);
 #pragma unroll
-        for (int k = 1; k < kTaps; ++k) {
-            float dlt = __fsub_rn(vh[r][2 * q + k], refh);
-            if (!LEVEL1) dlt = __fadd_rn(dlt, __fsub_rn(vl[r][2 * q + k], refl));
-            s = __fmaf_rn(a.f.h[k], dlt, s);
-            t = __fmaf_rn(a.f.g[k], dlt, t);
+            for (int j = 0; j < 4; ++j) {
+                const float2 t = row[q + j];
+                v[2 * j] = t.x;
+                v[2 * j + 1] = t.y;
+            }
+            if (!LEVEL1) {
+                const float2 *rowl = reinterpret_cast<const float2 *>(&vl[r][0]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float2 t = rowl[q + j];
+                    w[2 * j] = t.x;
+                    w[2 * j + 1] = t.y;
+                }
+            }
+            float s = 0.f, t = 0.f;
+#pragma unroll
+            for (int k = 1; k < kTaps; ++k) {
+                float dlt = __fsub_rn(v[k], v[0]);
+                if (!LEVEL1) dlt = __fadd_rn(dlt, __fsub_rn(w[k], w[0]));
+                s = __fmaf_rn(a.f.h[k], dlt, s);
+                t = __fmaf_rn(a.f.g[k], dlt, t);
+            }
+            rh[r][q] = v[0];
+            if (!LEVEL1) rl[r][q] = w[0];
+            ss[r][q] = s;
+            tt[r][q] = t;
         }
-        rh[r][q] = refh;
-        if (!LEVEL1) rl[r][q] = refl;
-        ss[r][q] = s;
-        tt[r][q] = t;
     }
     __syncthreads();
 
     // 3) column pass
     const float scale = a.scale_on ? __frcp_rn((float)a.sc.count(plane)) : 1.f;
-    const int q = threadIdx.x;
-    for (int pl = threadIdx.y; pl < TP; pl += blockDim.y) {
+    const int q = tx;
+#pragma unroll
+    for (int pl = ty; pl < TP; pl += 8) {
         const int p = p0 + pl, qq = q0 + q;
         if (p >= R2 || qq >= C2) continue;
         const int y0 = 2 * pl;

@@ -138,64 +138,105 @@ __global__ void k_real_scaled(const cufftComplex *F, long long n, float scale, f
 }
 
 // -------------------------------------------------------------------- PCE --
-// X = grey(residual_q), Y = K * grey(img_q)
+// Batched over n queries (grid y = query).  X_i = grey(residual_i),
+// Y_i = K * grey(img_i); the block partials carry sum and sum of squares of
+// X_i and Y_i in float64.  The means are removed exactly by zeroing the DC
+// bin of the cross spectrum: sum_x (X-mx)(Y(x+s)-my) = sum_x X Y(x+s) - N mx my.
 __global__ void k_pce_prep(const float *K, const float *Wq, const float *Iq, long long hw, int C, float *X,
-                           float *Y) {
+                           float *Y, double *part) {
+    __shared__ double sh[32];
+    const int q = blockIdx.y;
+    const float *w = Wq + (long long)q * C * hw;
+    const float *im = Iq + (long long)q * C * hw;
+    float *xo = X + (long long)q * hw;
+    float *yo = Y + (long long)q * hw;
+    // per-thread float32 partials over a short run, then float64 across threads
+    double sx = 0.0, sxx = 0.0, sy = 0.0, syy = 0.0;
+    float fx = 0.f, fxx = 0.f, fy = 0.f, fyy = 0.f;
+    int run = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < hw;
          i += (long long)gridDim.x * blockDim.x) {
-        float w, im;
+        float a, b;
         if (C == 3) {
-            w = (float)(0.299 * Wq[i] + 0.587 * Wq[hw + i] + 0.114 * Wq[2 * hw + i]);
-            im = (float)(0.299 * Iq[i] + 0.587 * Iq[hw + i] + 0.114 * Iq[2 * hw + i]);
+            a = __fmaf_rn(0.114f, w[2 * hw + i], __fmaf_rn(0.587f, w[hw + i], 0.299f * w[i]));
+            b = __fmaf_rn(0.114f, im[2 * hw + i], __fmaf_rn(0.587f, im[hw + i], 0.299f * im[i]));
         } else {
-            w = Wq[i];
-            im = Iq[i];
+            a = w[i];
+            b = im[i];
         }
-        X[i] = w;
-        Y[i] = K[i] * im;
+        const float yv = K[i] * b;
+        xo[i] = a;
+        yo[i] = yv;
+        fx += a;
+        fxx = __fmaf_rn(a, a, fxx);
+        fy += yv;
+        fyy = __fmaf_rn(yv, yv, fyy);
+        if (++run == 16) {
+            sx += fx; sxx += fxx; sy += fy; syy += fyy;
+            fx = fxx = fy = fyy = 0.f;
+            run = 0;
+        }
+    }
+    sx += fx; sxx += fxx; sy += fy; syy += fyy;
+    sx = block_sum(sx, sh);
+    sxx = block_sum(sxx, sh);
+    sy = block_sum(sy, sh);
+    syy = block_sum(syy, sh);
+    if (threadIdx.x == 0) {
+        double *o = part + ((long long)q * gridDim.x + blockIdx.x) * 4;
+        o[0] = sx;
+        o[1] = sxx;
+        o[2] = sy;
+        o[3] = syy;
     }
 }
 
-__global__ void k_sub_center(float *v, long long n, const double *mean) {
-    const double m = mean[0];
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        v[i] = (float)((double)v[i] - m);
-}
-
-// Z = conj(FX) * FY  (C(s) = sum_x X(x) Y(x+s))
-__global__ void k_cross_spectrum(const cufftComplex *FX, const cufftComplex *FY, long long n, cufftComplex *Z) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+// Z_i = conj(FX_i) * FY_i with the DC bin set to 0 (C(s) = sum_x X(x) Y(x+s))
+__global__ void k_cross_spectrum(const cufftComplex *FX, const cufftComplex *FY, long long nh, int n,
+                                 cufftComplex *Z) {
+    const long long tot = nh * n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
          i += (long long)gridDim.x * blockDim.x) {
         const cufftComplex a = FX[i], b = FY[i];
-        Z[i] = make_cuFloatComplex(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+        Z[i] = (i % nh == 0) ? make_cuFloatComplex(0.f, 0.f)
+                             : make_cuFloatComplex(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
     }
 }
 
 struct PceScalars {
-    double c0, energy, peak_val;
+    double c0, energy;
     long long peak_idx;
-    double nx2, ny2;
+    double sx, sxx, sy, syy;
 };
 
-// stage 1: energy outside the neighbourhood and argmax (first index on ties)
+// energy outside the neighbourhood of zero shift and argmax (first index on ties)
 __global__ void k_pce_energy(const float *Cr, int H, int W, int r, double *part_e, float *part_v,
                              long long *part_i) {
     __shared__ double sh[32];
     __shared__ float sv[RB];
     __shared__ long long si[RB];
+    const int q = blockIdx.y;
     const long long n = (long long)H * W;
+    const float *c = Cr + (long long)q * n;
     double e = 0.0;
+    float fe = 0.f;
+    int run = 0;
     float bv = -__int_as_float(0x7f800000);
     long long bi = 0x7fffffffffffffffLL;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(i / W), x = (int)(i - (long long)y * W);
-        const float v = Cr[i];
+        const float v = c[i];
         const int dy = min(y, H - y), dx = min(x, W - x);  // wrapped distance to zero shift
-        if (dy > r || dx > r) e += (double)v * (double)v;
+        if (dy > r || dx > r) fe = __fmaf_rn(v, v, fe);
+        if (++run == 16) {
+            e += fe;
+            fe = 0.f;
+            run = 0;
+        }
         if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
     }
+    e += fe;
     e = block_sum(e, sh);
     sv[threadIdx.x] = bv;
     si[threadIdx.x] = bi;
@@ -212,29 +253,39 @@ __global__ void k_pce_energy(const float *Cr, int H, int W, int r, double *part_
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        part_e[blockIdx.x] = e;
-        part_v[blockIdx.x] = sv[0];
-        part_i[blockIdx.x] = si[0];
+        const long long o = (long long)q * gridDim.x + blockIdx.x;
+        part_e[o] = e;
+        part_v[o] = sv[0];
+        part_i[o] = si[0];
     }
 }
 
-__global__ void k_pce_final(const float *Cr, const double *part_e, const float *part_v, const long long *part_i,
-                            int nb, const double *momx, const double *momy, PceScalars *out) {
+// one block per query
+__global__ void k_pce_final(const float *Cr, long long n, const double *part_e, const float *part_v,
+                            const long long *part_i, int nb, const double *part_m, int nbm, PceScalars *out) {
     __shared__ double sh[32];
-    double e = 0.0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) e += part_e[i];
+    const int q = blockIdx.x;
+    double e = 0.0, m[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) e += part_e[(long long)q * nb + i];
+    for (int i = threadIdx.x; i < nbm; i += blockDim.x)
+        for (int k = 0; k < 4; ++k) m[k] += part_m[((long long)q * nbm + i) * 4 + k];
     e = block_sum(e, sh);
+    for (int k = 0; k < 4; ++k) m[k] = block_sum(m[k], sh);
     if (threadIdx.x == 0) {
-        float bv = part_v[0];
-        long long bi = part_i[0];
-        for (int i = 1; i < nb; ++i)
-            if (part_v[i] > bv || (part_v[i] == bv && part_i[i] < bi)) { bv = part_v[i]; bi = part_i[i]; }
-        out->c0 = (double)Cr[0];
-        out->energy = e;
-        out->peak_val = bv;
-        out->peak_idx = bi;
-        out->nx2 = momx[1];
-        out->ny2 = momy[1];
+        float bv = part_v[(long long)q * nb];
+        long long bi = part_i[(long long)q * nb];
+        for (int i = 1; i < nb; ++i) {
+            const float v = part_v[(long long)q * nb + i];
+            const long long ix = part_i[(long long)q * nb + i];
+            if (v > bv || (v == bv && ix < bi)) { bv = v; bi = ix; }
+        }
+        out[q].c0 = (double)Cr[(long long)q * n];
+        out[q].energy = e;
+        out[q].peak_idx = bi;
+        out[q].sx = m[0];
+        out[q].sxx = m[1];
+        out[q].sy = m[2];
+        out[q].syy = m[3];
     }
 }
 
@@ -288,37 +339,36 @@ cudaError_t launch_real_scaled(const cufftComplex *F, long long n, float scale, 
     k_real_scaled<<<ew_blocks(n, sms), 256, 0, st>>>(F, n, scale, K);
     return cudaGetLastError();
 }
-cudaError_t launch_pce_prep(const float *K, const float *Wq, const float *Iq, long long hw, int C, float *X,
-                            float *Y, int sms, cudaStream_t st) {
-    k_pce_prep<<<ew_blocks(hw, sms), 256, 0, st>>>(K, Wq, Iq, hw, C, X, Y);
+cudaError_t launch_pce_prep(const float *K, const float *Wq, const float *Iq, long long hw, int C, int n, int nb,
+                            float *X, float *Y, double *part, cudaStream_t st) {
+    k_pce_prep<<<dim3(nb, n), RB, 0, st>>>(K, Wq, Iq, hw, C, X, Y, part);
     return cudaGetLastError();
 }
-cudaError_t launch_sub_center(float *v, long long n, const double *mean, int sms, cudaStream_t st) {
-    k_sub_center<<<ew_blocks(n, sms), 256, 0, st>>>(v, n, mean);
+cudaError_t launch_cross_spectrum(const cufftComplex *FX, const cufftComplex *FY, long long nh, int n,
+                                  cufftComplex *Z, int sms, cudaStream_t st) {
+    k_cross_spectrum<<<ew_blocks(nh * n, sms), 256, 0, st>>>(FX, FY, nh, n, Z);
     return cudaGetLastError();
 }
-cudaError_t launch_cross_spectrum(const cufftComplex *FX, const cufftComplex *FY, long long n, cufftComplex *Z,
-                                  int sms, cudaStream_t st) {
-    k_cross_spectrum<<<ew_blocks(n, sms), 256, 0, st>>>(FX, FY, n, Z);
-    return cudaGetLastError();
-}
-cudaError_t launch_pce_reduce(const float *Cr, int H, int W, int r, int nb, double *part_e, float *part_v,
-                              long long *part_i, const double *momx, const double *momy, void *out,
-                              cudaStream_t st) {
-    k_pce_energy<<<nb, RB, 0, st>>>(Cr, H, W, r, part_e, part_v, part_i);
-    k_pce_final<<<1, RB, 0, st>>>(Cr, part_e, part_v, part_i, nb, momx, momy, (PceScalars *)out);
+cudaError_t launch_pce_reduce(const float *Cr, int H, int W, int r, int n, int nb, double *part_e, float *part_v,
+                              long long *part_i, const double *part_m, int nbm, void *out, cudaStream_t st) {
+    k_pce_energy<<<dim3(nb, n), RB, 0, st>>>(Cr, H, W, r, part_e, part_v, part_i);
+    k_pce_final<<<n, RB, 0, st>>>(Cr, (long long)H * W, part_e, part_v, part_i, nb, part_m, nbm,
+                                  (PceScalars *)out);
     return cudaGetLastError();
 }
 
 size_t pce_scalars_bytes() { return sizeof(PceScalars); }
 
-void pce_unpack(const void *p, double *c0, double *energy, long long *peak_idx, double *nx2, double *ny2) {
-    const PceScalars *s = (const PceScalars *)p;
+void pce_unpack(const void *p, int q, double *c0, double *energy, long long *peak_idx, double *sx, double *sxx,
+                double *sy, double *syy) {
+    const PceScalars *s = (const PceScalars *)p + q;
     *c0 = s->c0;
     *energy = s->energy;
     *peak_idx = s->peak_idx;
-    *nx2 = s->nx2;
-    *ny2 = s->ny2;
+    *sx = s->sx;
+    *sxx = s->sxx;
+    *sy = s->sy;
+    *syy = s->syy;
 }
 
 }  // namespace prnu

@@ -13,55 +13,80 @@
 namespace prnu {
 
 constexpr int OT = 32, CT = OT / 2 + 3;  // output tile, coefficient tile
+constexpr int NPAIR = OT / 2;              // output pairs per tile row / column
 
 struct SynTile {
     float c[4][CT][CT + 1];
     float lo[OT][CT + 1], hi[OT][CT + 1];
 };
 
-// Stage the four coefficient tiles of output tile (y0, x0) of one plane.
+// Stage the four coefficient tiles of output tile (y0, x0) of one plane:
+// coefficient rows m0-3 .. m0+15 and columns n0-3 .. n0+15 (periodic).
 __device__ __forceinline__ void load_coeffs(SynTile &s, const float *LL, const float *LH, const float *HL,
-                                            const float *HH, long long poff, int Rc, int Cc, int y0, int x0,
-                                            int tid) {
-    const int m0 = (y0 >> 1) - 3, n0 = (x0 >> 1) - 3;
-    for (int i = tid; i < CT * CT; i += 256) {
-        const int r = i / CT, c = i - r * CT;
-        const long long o = poff + (long long)wrap(m0 + r, Rc) * Cc + wrap(n0 + c, Cc);
-        s.c[0][r][c] = LL ? __ldg(LL + o) : 0.f;
-        s.c[1][r][c] = __ldg(LH + o);
-        s.c[2][r][c] = __ldg(HL + o);
-        s.c[3][r][c] = __ldg(HH + o);
+                                            const float *HH, long long poff, int Rc, int Cc, int y0, int x0) {
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    if (tx < CT) {
+        const int sx = wrap((x0 >> 1) - 3 + tx, Cc);
+        for (int r = ty; r < CT; r += 8) {
+            const long long o = poff + (long long)wrap((y0 >> 1) - 3 + r, Rc) * Cc + sx;
+            s.c[0][r][tx] = LL ? __ldg(LL + o) : 0.f;
+            s.c[1][r][tx] = __ldg(LH + o);
+            s.c[2][r][tx] = __ldg(HL + o);
+            s.c[3][r][tx] = __ldg(HH + o);
+        }
     }
 }
 
-// Column synthesis into lo/hi, then row synthesis of one output sample.
+// Column synthesis: item (coefficient column c, output row pair m) makes
+// rows 2m and 2m+1 of lo/hi from coefficient rows m..m+3 of the tile.
 __device__ __forceinline__ void synth_cols(SynTile &s, const Filt &f, int tid) {
-    for (int i = tid; i < OT * CT; i += 256) {
-        const int y = i / CT, c = i - y * CT;
-        const int e = y & 1, mr = (y >> 1) + 3;
-        float lo = 0.f, hi = 0.f;
+    for (int it = tid; it < NPAIR * CT; it += 256) {
+        const int m = it / CT, c = it - m * CT;
+        float a[4], b[4], u[4], v[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-            const float hk = f.h[e + 2 * t], gk = f.g[e + 2 * t];
-            lo = __fmaf_rn(hk, s.c[0][mr - t][c], lo);
-            lo = __fmaf_rn(gk, s.c[1][mr - t][c], lo);
-            hi = __fmaf_rn(hk, s.c[2][mr - t][c], hi);
-            hi = __fmaf_rn(gk, s.c[3][mr - t][c], hi);
+            a[t] = s.c[0][m + 3 - t][c];
+            b[t] = s.c[1][m + 3 - t][c];
+            u[t] = s.c[2][m + 3 - t][c];
+            v[t] = s.c[3][m + 3 - t][c];
         }
-        s.lo[y][c] = lo;
-        s.hi[y][c] = hi;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            float lo = 0.f, hi = 0.f;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const float hk = f.h[e + 2 * t], gk = f.g[e + 2 * t];
+                lo = __fmaf_rn(hk, a[t], lo);
+                lo = __fmaf_rn(gk, b[t], lo);
+                hi = __fmaf_rn(hk, u[t], hi);
+                hi = __fmaf_rn(gk, v[t], hi);
+            }
+            s.lo[2 * m + e][c] = lo;
+            s.hi[2 * m + e][c] = hi;
+        }
     }
 }
 
-__device__ __forceinline__ float synth_row(const SynTile &s, const Filt &f, int y, int x) {
-    const int e = x & 1, nr = (x >> 1) + 3;
-    float v = 0.f;
+// Row synthesis of the output pair (y, 2n), (y, 2n+1).
+__device__ __forceinline__ float2 synth_pair(const SynTile &s, const Filt &f, int y, int n) {
+    float l[4], h[4];
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-        v = __fmaf_rn(f.h[e + 2 * t], s.lo[y][nr - t], v);
-        v = __fmaf_rn(f.g[e + 2 * t], s.hi[y][nr - t], v);
+        l[t] = s.lo[y][n + 3 - t];
+        h[t] = s.hi[y][n + 3 - t];
     }
-    return v;
+    float o[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        float v = 0.f;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            v = __fmaf_rn(f.h[e + 2 * t], l[t], v);
+            v = __fmaf_rn(f.g[e + 2 * t], h[t], v);
+        }
+        o[e] = v;
+    }
+    return make_float2(o[0], o[1]);
 }
 
 __global__ void __launch_bounds__(256) k_synthesis(SynArgs a) {
@@ -70,64 +95,83 @@ __global__ void __launch_bounds__(256) k_synthesis(SynArgs a) {
     const int y0 = blockIdx.y * OT, x0 = blockIdx.x * OT;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const long long poff = (long long)plane * a.Rc * a.Cc;
-    load_coeffs(s, a.LL, a.LH, a.HL, a.HH, poff, a.Rc, a.Cc, y0, x0, tid);
+    load_coeffs(s, a.LL, a.LH, a.HL, a.HH, poff, a.Rc, a.Cc, y0, x0);
     __syncthreads();
     synth_cols(s, a.f, tid);
     __syncthreads();
-    const int Ro = 2 * a.Rc, Co = 2 * a.Cc;
-    const int x = threadIdx.x;
-    for (int yl = threadIdx.y; yl < OT; yl += blockDim.y) {
-        const int gy = y0 + yl, gx = x0 + x;
-        if (gy < Ro && gx < Co) a.out[((long long)plane * Ro + gy) * Co + gx] = synth_row(s, a.f, yl, x);
+    const int Ro = 2 * a.Rc, Co = 2 * a.Cc;  // even, so a pair is in range or out together
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int it = tid + 256 * k;
+        const int y = it >> 4, n = it & 15;
+        const int gy = y0 + y, gx = x0 + 2 * n;
+        if (gy < Ro && gx < Co) {
+            const float2 v = synth_pair(s, a.f, y, n);
+            *reinterpret_cast<float2 *>(a.out + ((long long)plane * Ro + gy) * Co + gx) = v;
+        }
     }
 }
 
-// Level 1: W for the cropped H x W region; residual or MLE accumulation.
+// Level 1: W for the cropped H x W region.  Residual mode: one plane per
+// grid z, W stored at res_out[plane].  MLE mode: grid z is the channel and
+// the block walks the pass's G images, summing W*I and I*I in registers
+// before one read-modify-write of num/den.
 template <bool MLE>
 __global__ void __launch_bounds__(256) k_final(FinalArgs a) {
     __shared__ SynTile s;
-    const int c = blockIdx.z;
     const int y0 = blockIdx.y * OT, x0 = blockIdx.x * OT;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int x = threadIdx.x;
-    constexpr int PER = OT / 8;  // rows per thread
-    float an[PER], ad[PER];
+    float an[4], ad[4];
 #pragma unroll
-    for (int k = 0; k < PER; ++k) { an[k] = 0.f; ad[k] = 0.f; }
+    for (int k = 0; k < 4; ++k) { an[k] = 0.f; ad[k] = 0.f; }
     const long long hw = (long long)a.H * a.W;
-    for (int i = 0; i < a.G; ++i) {
-        const int plane = i * a.C + c;
+    const int nimg = MLE ? a.G : 1;
+    for (int i = 0; i < nimg; ++i) {
+        const int plane = MLE ? i * a.C + (int)blockIdx.z : (int)blockIdx.z;
         const long long poff = (long long)plane * a.Rc * a.Cc;
         if (i > 0) __syncthreads();
-        load_coeffs(s, a.LL, a.LH, a.HL, a.HH, poff, a.Rc, a.Cc, y0, x0, tid);
+        load_coeffs(s, a.LL, a.LH, a.HL, a.HH, poff, a.Rc, a.Cc, y0, x0);
         __syncthreads();
         synth_cols(s, a.f, tid);
         __syncthreads();
         const float fn = MLE ? (float)a.sc.count(plane) : 1.f;
 #pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int yl = threadIdx.y + 8 * k;
-            const int gy = y0 + yl, gx = x0 + x;
-            if (gy < a.H && gx < a.W) {
-                const float w = synth_row(s, a.f, yl, x);
-                if (MLE) {
-                    const float I = __fdiv_rn(__ldg(a.X + (long long)plane * hw + (long long)gy * a.W + gx), fn);
-                    an[k] = __fmaf_rn(w, I, an[k]);
-                    ad[k] = __fmaf_rn(I, I, ad[k]);
-                } else {
-                    a.res_out[(long long)c * hw + (long long)gy * a.W + gx] = w;
+        for (int k = 0; k < 2; ++k) {
+            const int it = tid + 256 * k;
+            const int y = it >> 4, n = it & 15;
+            const int gy = y0 + y, gx = x0 + 2 * n;
+            if (gy >= a.H || gx >= a.W) continue;
+            const float2 w = synth_pair(s, a.f, y, n);
+            const long long o = (long long)plane * hw + (long long)gy * a.W + gx;
+            const bool two = gx + 1 < a.W;
+            if (MLE) {
+                const float I0 = __fdiv_rn(__ldg(a.X + o), fn);
+                an[2 * k] = __fmaf_rn(w.x, I0, an[2 * k]);
+                ad[2 * k] = __fmaf_rn(I0, I0, ad[2 * k]);
+                if (two) {
+                    const float I1 = __fdiv_rn(__ldg(a.X + o + 1), fn);
+                    an[2 * k + 1] = __fmaf_rn(w.y, I1, an[2 * k + 1]);
+                    ad[2 * k + 1] = __fmaf_rn(I1, I1, ad[2 * k + 1]);
                 }
+            } else {
+                a.res_out[o] = w.x;
+                if (two) a.res_out[o + 1] = w.y;
             }
         }
     }
     if (MLE) {
 #pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int gy = y0 + threadIdx.y + 8 * k, gx = x0 + x;
-            if (gy < a.H && gx < a.W) {
-                const long long o = (long long)c * hw + (long long)gy * a.W + gx;
-                a.num[o] += an[k];
-                a.den[o] += ad[k];
+        for (int k = 0; k < 2; ++k) {
+            const int it = tid + 256 * k;
+            const int y = it >> 4, n = it & 15;
+            const int gy = y0 + y, gx = x0 + 2 * n;
+            if (gy >= a.H || gx >= a.W) continue;
+            const long long o = (long long)blockIdx.z * hw + (long long)gy * a.W + gx;
+            a.num[o] += an[2 * k];
+            a.den[o] += ad[2 * k];
+            if (gx + 1 < a.W) {
+                a.num[o + 1] += an[2 * k + 1];
+                a.den[o + 1] += ad[2 * k + 1];
             }
         }
     }
@@ -142,7 +186,7 @@ cudaError_t launch_synthesis(const SynArgs &a, cudaStream_t st) {
 
 cudaError_t launch_final(const FinalArgs &a, bool mle, cudaStream_t st) {
     dim3 block(32, 8);
-    dim3 grid((unsigned)((a.W + OT - 1) / OT), (unsigned)((a.H + OT - 1) / OT), (unsigned)a.C);
+    dim3 grid((unsigned)((a.W + OT - 1) / OT), (unsigned)((a.H + OT - 1) / OT), (unsigned)(mle ? a.C : a.C * a.G));
     if (mle)
         k_final<true><<<grid, block, 0, st>>>(a);
     else

@@ -59,7 +59,7 @@ struct FinalArgs {
     int H, W, C, G;    // crop and plane map: image i, channel c -> plane i*C + c
     const float *X;    // MLE mode: group sums [G][C][H][W]
     PlaneScale sc;
-    float *res_out;    // residual mode: [C][H][W] (G == 1)
+    float *res_out;    // residual mode: [G*C][H][W]
     float *num, *den;  // MLE mode: [C][H][W]
     Filt f;
 };
@@ -79,15 +79,14 @@ cudaError_t launch_apply_ratio(cufftComplex *F, const float *M, const float *Mn,
                                cudaStream_t st);
 cudaError_t launch_real_scaled(const cufftComplex *F, long long n, float scale, float *K, int sms,
                                cudaStream_t st);
-cudaError_t launch_pce_prep(const float *K, const float *Wq, const float *Iq, long long hw, int C, float *X,
-                            float *Y, int sms, cudaStream_t st);
-cudaError_t launch_sub_center(float *v, long long n, const double *mean, int sms, cudaStream_t st);
-cudaError_t launch_cross_spectrum(const cufftComplex *FX, const cufftComplex *FY, long long n, cufftComplex *Z,
-                                  int sms, cudaStream_t st);
-cudaError_t launch_pce_reduce(const float *Cr, int H, int W, int r, int nb, double *part_e, float *part_v,
-                              long long *part_i, const double *momx, const double *momy, void *out,
-                              cudaStream_t st);
+cudaError_t launch_pce_prep(const float *K, const float *Wq, const float *Iq, long long hw, int C, int n, int nb,
+                            float *X, float *Y, double *part, cudaStream_t st);
+cudaError_t launch_cross_spectrum(const cufftComplex *FX, const cufftComplex *FY, long long nh, int n,
+                                  cufftComplex *Z, int sms, cudaStream_t st);
+cudaError_t launch_pce_reduce(const float *Cr, int H, int W, int r, int n, int nb, double *part_e, float *part_v,
+                              long long *part_i, const double *part_m, int nbm, void *out, cudaStream_t st);
 size_t pce_scalars_bytes();
-void pce_unpack(const void *p, double *c0, double *energy, long long *peak_idx, double *nx2, double *ny2);
+void pce_unpack(const void *p, int q, double *c0, double *energy, long long *peak_idx, double *sx, double *sxx,
+                double *sy, double *syy);
 
 }  // namespace prnu

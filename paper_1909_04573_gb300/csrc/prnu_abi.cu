@@ -22,14 +22,15 @@ struct prnu_ctx {
     double h64[kTaps];
     Filt filt;
     std::mutex mu;
-    std::map<std::tuple<int, int, int>, cufftHandle> plans;  // (H, W, type) -> plan
-    std::map<std::tuple<int, int, int>, size_t> plan_work;
+    std::map<std::tuple<int, int, int, int>, cufftHandle> plans;  // (H, W, type, batch) -> plan
+    std::map<std::tuple<int, int, int, int>, size_t> plan_work;
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
     // per-kernel launch counters (always) and CUDA-event timing (opt-in)
     bool prof_on = false;
     std::vector<std::string> knames;
     std::vector<long long> klaunches;
+    std::vector<double> kbytes;  // algorithmic bytes of the counted launches
     struct Rec {
         int kid;
         cudaEvent_t a, b;
@@ -86,7 +87,7 @@ struct Launch {
     cudaStream_t st;
     int kid = -1;
     cudaEvent_t a = nullptr, b = nullptr;
-    Launch(prnu_ctx *c, const char *name, cudaStream_t s, int kernels = 1) : ctx(c), st(s) {
+    Launch(prnu_ctx *c, const char *name, cudaStream_t s, int kernels = 1, double bytes = 0.0) : ctx(c), st(s) {
         std::lock_guard<std::mutex> lk(ctx->mu);
         for (size_t i = 0; i < ctx->knames.size(); ++i)
             if (ctx->knames[i] == name) kid = (int)i;
@@ -94,8 +95,10 @@ struct Launch {
             kid = (int)ctx->knames.size();
             ctx->knames.push_back(name);
             ctx->klaunches.push_back(0);
+            ctx->kbytes.push_back(0.0);
         }
         ctx->klaunches[kid] += kernels;
+        ctx->kbytes[kid] += bytes;
         if (ctx->prof_on) {
             a = take();
             b = take();
@@ -292,7 +295,9 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
         a.scale_on = scale_on;
         a.f = ctx->filt;
         {
-            Launch t(ctx, l == 1 ? "analysis_l1" : "analysis", st);
+            const double in_b = l == 1 ? (double)P * H * W * 4 : (double)P * a.R * a.Cc * 8;
+            const double out_b = (double)P * A * (12 + (l < L ? 8 : 0));
+            Launch t(ctx, l == 1 ? "analysis_l1" : "analysis", st, 1, in_b + out_b);
             CU(launch_analysis(a, l == 1, st));
         }
         ShrinkArgs s{};
@@ -305,7 +310,7 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
         s.s2_dev = nullptr;
         s.win = win;
         {
-            Launch t(ctx, "shrink", st);
+            Launch t(ctx, "shrink", st, 1, 2.0 * s.nplanes * s.R * s.Cc * 4);
             CU(launch_shrink(s, st));
         }
     }
@@ -322,7 +327,7 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
         y.out = F(lo.Rn[l - 1]);
         y.f = ctx->filt;
         {
-            Launch t(ctx, "synthesis", st);
+            Launch t(ctx, "synthesis", st, 1, (double)P * A * 4 * (y.LL ? 4 : 3) + (double)P * A * 16);
             CU(launch_synthesis(y, st));
         }
     }
@@ -337,7 +342,9 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
     fin.W = W;
     fin.f = ctx->filt;
     {
-        Launch t(ctx, mle ? "final_mle" : "final_residual", st);
+        const double cin = (double)P * A1 * 4 * (fin.LL ? 4 : 3);
+        const double io = mle ? (double)P * H * W * 4 + (double)fin.C * H * W * 16 : (double)P * H * W * 4;
+        Launch t(ctx, mle ? "final_mle" : "final_residual", st, 1, cin + io);
         CU(launch_final(fin, mle, st));
     }
     return PRNU_OK;
@@ -360,20 +367,22 @@ prnu_status check_frames(const uint8_t *frames, int m, int H, int W, int C, size
     return PRNU_OK;
 }
 
-// cuFFT plan cache: (H, W, type) -> plan without auto-allocated work area.
-prnu_status get_plan(prnu_ctx *ctx, int H, int W, cufftType type, cufftHandle *plan, size_t *work) {
+// cuFFT plan cache: (H, W, type, batch) -> plan without an auto-allocated
+// work area; batched planes are contiguous with the default distances.
+prnu_status get_plan(prnu_ctx *ctx, int H, int W, cufftType type, int batch, cufftHandle *plan, size_t *work) {
     std::lock_guard<std::mutex> lk(ctx->mu);
-    const auto key = std::make_tuple(H, W, (int)type);
+    const auto key = std::make_tuple(H, W, (int)type, batch);
     auto it = ctx->plans.find(key);
     if (it == ctx->plans.end()) {
         cufftHandle p;
         CUFFT(cufftCreate(&p));
         CUFFT(cufftSetAutoAllocation(p, 0));
         size_t ws = 0;
-        cufftResult r = cufftMakePlan2d(p, H, W, type, &ws);
+        int dims[2] = {H, W};
+        cufftResult r = cufftMakePlanMany(p, 2, dims, nullptr, 1, 0, nullptr, 1, 0, type, batch, &ws);
         if (r != CUFFT_SUCCESS) {
             cufftDestroy(p);
-            return fail(PRNU_ECUDA, "cufftMakePlan2d(%d, %d) failed: %d", H, W, (int)r);
+            return fail(PRNU_ECUDA, "cufftMakePlanMany(%d x %d, batch %d) failed: %d", H, W, batch, (int)r);
         }
         ctx->plans[key] = p;
         ctx->plan_work[key] = ws;
@@ -386,16 +395,18 @@ prnu_status get_plan(prnu_ctx *ctx, int H, int W, cufftType type, cufftHandle *p
 
 constexpr int kRedBlocks = 512;
 
-// Workspace of finalize / pce for one plane geometry.
+// Workspace of finalize (one plane at a time) and of a PCE batch of n queries.
 struct FftLayout {
-    size_t a = 0, b = 0, c = 0;       // float / complex buffers
+    size_t cplx = 0;                  // complex: max(2n half spectra, one full plane)
+    size_t real = 0;                  // float: 2n planes (X_i, Y_i) or (M, Mn)
     size_t colmean = 0, rowmean = 0;  // doubles
-    size_t part = 0, tmp = 0, mom0 = 0, mom1 = 0, scal = 0;
-    size_t pv = 0, pi = 0;
+    size_t part = 0, tmp = 0, mom0 = 0;
+    size_t pm = 0, pe = 0, pv = 0, pi = 0, scal = 0;
     size_t work = 0, end = 0;
+    int nb = 0, nbm = 0;              // reduction blocks per query
 };
 
-prnu_status fft_layout(prnu_ctx *ctx, int H, int W, FftLayout *out) {
+prnu_status fft_layout(prnu_ctx *ctx, int H, int W, int n, FftLayout *out) {
     FftLayout f;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -404,28 +415,29 @@ prnu_status fft_layout(prnu_ctx *ctx, int H, int W, FftLayout *out) {
         return o;
     };
     const size_t hw = (size_t)H * W;
-    const size_t half = (size_t)H * (W / 2 + 1);
-    const size_t cbytes = std::max(hw, half) * sizeof(cufftComplex);  // a full complex plane
-    f.a = take(cbytes);
-    f.b = take(cbytes);
-    f.c = take(hw * sizeof(float) * 2);
+    const size_t nh = (size_t)H * (W / 2 + 1);
+    f.nb = (int)std::min<size_t>(256, std::max<size_t>(1, hw / (256 * 16)));
+    f.nbm = f.nb;
+    f.cplx = take(std::max(2 * (size_t)n * nh, hw) * sizeof(cufftComplex));
+    f.real = take(2 * (size_t)std::max(n, 1) * hw * sizeof(float));
     f.colmean = take((size_t)W * sizeof(double));
     f.rowmean = take((size_t)H * sizeof(double));
     f.part = take((size_t)kRedBlocks * 2 * sizeof(double));
-    f.pv = take((size_t)kRedBlocks * sizeof(float));
-    f.pi = take((size_t)kRedBlocks * sizeof(long long));
     f.tmp = take(2 * sizeof(double));
     f.mom0 = take(2 * sizeof(double));
-    f.mom1 = take(2 * sizeof(double));
-    f.scal = take(pce_scalars_bytes());
+    f.pm = take((size_t)n * f.nbm * 4 * sizeof(double));
+    f.pe = take((size_t)n * f.nb * sizeof(double));
+    f.pv = take((size_t)n * f.nb * sizeof(float));
+    f.pi = take((size_t)n * f.nb * sizeof(long long));
+    f.scal = take((size_t)n * pce_scalars_bytes());
     size_t w = 0, wmax = 0;
     cufftHandle p;
     prnu_status s;
-    if ((s = get_plan(ctx, H, W, CUFFT_C2C, &p, &w)) != PRNU_OK) return s;
+    if ((s = get_plan(ctx, H, W, CUFFT_C2C, 1, &p, &w)) != PRNU_OK) return s;
     wmax = std::max(wmax, w);
-    if ((s = get_plan(ctx, H, W, CUFFT_R2C, &p, &w)) != PRNU_OK) return s;
+    if ((s = get_plan(ctx, H, W, CUFFT_R2C, 2 * n, &p, &w)) != PRNU_OK) return s;
     wmax = std::max(wmax, w);
-    if ((s = get_plan(ctx, H, W, CUFFT_C2R, &p, &w)) != PRNU_OK) return s;
+    if ((s = get_plan(ctx, H, W, CUFFT_C2R, n, &p, &w)) != PRNU_OK) return s;
     wmax = std::max(wmax, w);
     f.work = take(wmax);
     f.end = off;
@@ -455,7 +467,8 @@ prnu_status accumulate_pass(prnu_ctx *ctx, const uint8_t *frames, int m, int H, 
     sa.out = reinterpret_cast<float *>(ws + lo.X);
     sa.mean = 0;
     {
-        Launch t(ctx, "sda_sum", st);
+        const double fr = (double)(std::min(m, (g0 + G) * d) - g0 * d) * H * W * C;
+        Launch t(ctx, "sda_sum", st, 1, fr + (double)P * H * W * 4);
         CU(launch_sda(sa, ctx->sms, st));
     }
     const PlaneScale sc{d, m, g0, C};
@@ -571,10 +584,9 @@ prnu_status prnu_workspace_size(prnu_ctx *ctx, int H, int W, int C, const prnu_p
     if ((s = check_params(params, H, W, nullptr)) != PRNU_OK) return s;
     if (images_per_pass < 1) return fail(PRNU_EINVAL, "images_per_pass must be >= 1");
     DeviceGuard g(ctx->device);
-    size_t need = make_layout(H, W, C, params->levels, false).end;
-    need = std::max(need, make_layout(H, W, (long long)images_per_pass * C, params->levels, true).end);
+    size_t need = make_layout(H, W, (long long)images_per_pass * C, params->levels, true).end;
     FftLayout f;
-    if ((s = fft_layout(ctx, H, W, &f)) != PRNU_OK) return s;
+    if ((s = fft_layout(ctx, H, W, images_per_pass, &f)) != PRNU_OK) return s;
     need = std::max(need, f.end);
     *bytes = need;
     return PRNU_OK;
@@ -613,29 +625,36 @@ prnu_status prnu_sda_average(prnu_ctx *ctx, const uint8_t *frames, int m, int H,
     a.G = (m + d - 1) / d;
     a.out = sda_out;
     a.mean = 1;
-    Launch t(ctx, "sda_mean", S(stream));
+    Launch t(ctx, "sda_mean", S(stream), 1, (double)m * H * W * C + (double)a.G * C * H * W * 4);
     CU(launch_sda(a, ctx->sms, S(stream)));
     return PRNU_OK;
 }
 
-prnu_status prnu_denoise_residual(prnu_ctx *ctx, const float *img, int H, int W, int C, const prnu_params *params,
-                                  float *residual_out, void *ws, size_t ws_bytes, void *stream) {
+prnu_status prnu_denoise_residual_batch(prnu_ctx *ctx, const float *img, int n, int H, int W, int C,
+                                        const prnu_params *params, float *residual_out, void *ws, size_t ws_bytes,
+                                        void *stream) {
     if (!ctx || !img || !residual_out) return fail(PRNU_EINVAL, "ctx/img/residual_out is NULL");
     if ((const void *)img == (const void *)residual_out) return fail(PRNU_EINVAL, "img and residual_out alias");
+    if (n < 1) return fail(PRNU_EINVAL, "n must be >= 1");
     prnu_status s;
     Win win;
     if ((s = check_geometry(H, W, C)) != PRNU_OK) return s;
     if ((s = check_params(params, H, W, &win)) != PRNU_OK) return s;
-    const Layout lo = make_layout(H, W, C, params->levels, false);
+    const Layout lo = make_layout(H, W, (long long)n * C, params->levels, false);
     if ((s = check_ws(ws, ws_bytes, lo.end)) != PRNU_OK) return s;
     DeviceGuard g(ctx->device);
     FinalArgs fin{};
     fin.C = C;
-    fin.G = 1;
+    fin.G = n;
     fin.res_out = residual_out;
     fin.sc = PlaneScale{1, 1, 0, C};
-    return run_denoise(ctx, img, H, W, C, *params, win, fin.sc, 0, static_cast<char *>(ws), lo, fin, false,
+    return run_denoise(ctx, img, H, W, n * C, *params, win, fin.sc, 0, static_cast<char *>(ws), lo, fin, false,
                        S(stream));
+}
+
+prnu_status prnu_denoise_residual(prnu_ctx *ctx, const float *img, int H, int W, int C, const prnu_params *params,
+                                  float *residual_out, void *ws, size_t ws_bytes, void *stream) {
+    return prnu_denoise_residual_batch(ctx, img, 1, H, W, C, params, residual_out, ws, ws_bytes, stream);
 }
 
 prnu_status prnu_fingerprint_accumulate(prnu_ctx *ctx, const uint8_t *frames, int m, int H, int W, int C,
@@ -740,12 +759,12 @@ prnu_status prnu_fingerprint_finalize(prnu_ctx *ctx, const float *num, const flo
     const int Cout = (flags & PRNU_TO_GRAY) ? 1 : C;
     FftLayout f{};
     if (flags & (PRNU_ZERO_MEAN | PRNU_WIENER_DFT)) {
-        if ((s = fft_layout(ctx, H, W, &f)) != PRNU_OK) return s;
+        if ((s = fft_layout(ctx, H, W, 1, &f)) != PRNU_OK) return s;
         if ((s = check_ws(ws, ws_bytes, f.end)) != PRNU_OK) return s;
     }
     char *b = static_cast<char *>(ws);
     {
-        Launch t(ctx, "finalize_divide", st);
+        Launch t(ctx, "finalize_divide", st, 1, (double)hw * 4 * (2 * C + Cout));
         CU(launch_divide(num, den, hw, C, (flags & PRNU_TO_GRAY) ? 1 : 0, K_out, ctx->sms, st));
     }
     for (int c = 0; c < Cout; ++c) {
@@ -759,9 +778,9 @@ prnu_status prnu_fingerprint_finalize(prnu_ctx *ctx, const float *num, const flo
         if (flags & PRNU_WIENER_DFT) {
             cufftHandle plan;
             size_t work;
-            if ((s = get_plan(ctx, H, W, CUFFT_C2C, &plan, &work)) != PRNU_OK) return s;
-            cufftComplex *F = reinterpret_cast<cufftComplex *>(b + f.a);
-            float *M = reinterpret_cast<float *>(b + f.c);
+            if ((s = get_plan(ctx, H, W, CUFFT_C2C, 1, &plan, &work)) != PRNU_OK) return s;
+            cufftComplex *F = reinterpret_cast<cufftComplex *>(b + f.cplx);
+            float *M = reinterpret_cast<float *>(b + f.real);
             float *Mn = M + hw;
             double *mom = reinterpret_cast<double *>(b + f.mom0);
             {
@@ -813,95 +832,84 @@ prnu_status prnu_fingerprint_finalize(prnu_ctx *ctx, const float *num, const flo
     return PRNU_OK;
 }
 
-prnu_status prnu_pce_match(prnu_ctx *ctx, const float *K, const float *residual_q, const float *img_q, int H, int W,
-                           int C, int nbhd, double *pce_out, double *ncc_out, int *peak_yx, void *ws,
-                           size_t ws_bytes, void *stream) {
+prnu_status prnu_pce_match_batch(prnu_ctx *ctx, const float *K, const float *residual_q, const float *img_q, int n,
+                                 int H, int W, int C, int nbhd, double *pce_out, double *ncc_out, int *peak_yx,
+                                 void *ws, size_t ws_bytes, void *stream) {
     if (!ctx || !K || !residual_q || !img_q || !pce_out) return fail(PRNU_EINVAL, "NULL argument");
+    if (n < 1) return fail(PRNU_EINVAL, "n must be >= 1");
     prnu_status s;
     if ((s = check_geometry(H, W, C)) != PRNU_OK) return s;
     if (nbhd < 1 || nbhd % 2 == 0 || nbhd > H || nbhd > W) return fail(PRNU_EINVAL, "nbhd must be odd and <= min(H, W)");
     DeviceGuard g(ctx->device);
     FftLayout f;
-    if ((s = fft_layout(ctx, H, W, &f)) != PRNU_OK) return s;
+    if ((s = fft_layout(ctx, H, W, n, &f)) != PRNU_OK) return s;
     if ((s = check_ws(ws, ws_bytes, f.end)) != PRNU_OK) return s;
     cudaStream_t st = S(stream);
     char *b = static_cast<char *>(ws);
     const long long hw = (long long)H * W;
-    float *X = reinterpret_cast<float *>(b + f.c);
-    float *Y = X + hw;
-    cufftComplex *FX = reinterpret_cast<cufftComplex *>(b + f.a);
-    cufftComplex *FY = reinterpret_cast<cufftComplex *>(b + f.b);
-    double *part = reinterpret_cast<double *>(b + f.part);
-    double *tmp = reinterpret_cast<double *>(b + f.tmp);
-    double *momx = reinterpret_cast<double *>(b + f.mom0);
-    double *momy = reinterpret_cast<double *>(b + f.mom1);
+    const long long nh = (long long)H * (W / 2 + 1);
+    float *X = reinterpret_cast<float *>(b + f.real);  // X_0..X_{n-1}, then Y_0..Y_{n-1}
+    float *Y = X + n * hw;
+    cufftComplex *FX = reinterpret_cast<cufftComplex *>(b + f.cplx);
     {
-        Launch t(ctx, "pce_prep", st, 1);
-        CU(launch_pce_prep(K, residual_q, img_q, hw, C, X, Y, ctx->sms, st));
-    }
-    {
-        Launch t(ctx, "mean_var", st, 4);
-        CU(launch_mean_var(X, hw, part, kRedBlocks, tmp, momx, st));
-    }
-    {
-        Launch t(ctx, "mean_var", st, 4);
-        CU(launch_mean_var(Y, hw, part, kRedBlocks, tmp, momy, st));
-    }
-    {
-        Launch t(ctx, "pce_center", st, 1);
-        CU(launch_sub_center(X, hw, momx, ctx->sms, st));
-    }
-    {
-        Launch t(ctx, "pce_center", st, 1);
-        CU(launch_sub_center(Y, hw, momy, ctx->sms, st));
+        Launch t(ctx, "pce_prep", st, 1, (double)n * hw * 4 * (2 * C + 2) + (double)hw * 4);
+        CU(launch_pce_prep(K, residual_q, img_q, hw, C, n, f.nbm, X, Y, reinterpret_cast<double *>(b + f.pm), st));
     }
     cufftHandle r2c, c2r;
     size_t w1, w2;
-    if ((s = get_plan(ctx, H, W, CUFFT_R2C, &r2c, &w1)) != PRNU_OK) return s;
-    if ((s = get_plan(ctx, H, W, CUFFT_C2R, &c2r, &w2)) != PRNU_OK) return s;
-    CUFFT(cufftSetStream(r2c, st));
-    CUFFT(cufftSetWorkArea(r2c, b + f.work));
+    if ((s = get_plan(ctx, H, W, CUFFT_R2C, 2 * n, &r2c, &w1)) != PRNU_OK) return s;
+    if ((s = get_plan(ctx, H, W, CUFFT_C2R, n, &c2r, &w2)) != PRNU_OK) return s;
     {
-        Launch t(ctx, "cufft_r2c", st, 1);
-        CUFFT(cufftExecR2C(r2c, X, FX));
+        Launch t(ctx, "cufft_r2c", st);
+        CUFFT(cufftSetStream(r2c, st));
+        CUFFT(cufftSetWorkArea(r2c, b + f.work));
+        CUFFT(cufftExecR2C(r2c, X, FX));  // 2n half spectra: FX_i, then FY_i
     }
     {
-        Launch t(ctx, "cufft_r2c", st, 1);
-        CUFFT(cufftExecR2C(r2c, Y, FY));
-    }
-    const long long nh = (long long)H * (W / 2 + 1);
-    {
-        Launch t(ctx, "pce_cross_spectrum", st, 1);
-        CU(launch_cross_spectrum(FX, FY, nh, FX, ctx->sms, st));
-    }
-    CUFFT(cufftSetStream(c2r, st));
-    CUFFT(cufftSetWorkArea(c2r, b + f.work));
-    {
-        Launch t(ctx, "cufft_c2r", st, 1);
-        CUFFT(cufftExecC2R(c2r, FX, X));  // X now holds hw * C(s)
+        Launch t(ctx, "pce_cross_spectrum", st, 1, (double)n * nh * 24);
+        CU(launch_cross_spectrum(FX, FX + n * nh, nh, n, FX, ctx->sms, st));
     }
     {
-        Launch t(ctx, "pce_reduce", st, 2);
-        CU(launch_pce_reduce(X, H, W, nbhd / 2, kRedBlocks, part, reinterpret_cast<float *>(b + f.pv),
-                             reinterpret_cast<long long *>(b + f.pi), momx, momy, b + f.scal, st));
+        Launch t(ctx, "cufft_c2r", st);
+        CUFFT(cufftSetStream(c2r, st));
+        CUFFT(cufftSetWorkArea(c2r, b + f.work));
+        CUFFT(cufftExecC2R(c2r, FX, X));  // X_i now holds hw * C_i(s)
     }
-    unsigned char host[256];
-    CU(cudaMemcpyAsync(host, b + f.scal, pce_scalars_bytes(), cudaMemcpyDeviceToHost, st));
+    {
+        Launch t(ctx, "pce_reduce", st, 2, (double)n * hw * 4);
+        CU(launch_pce_reduce(X, H, W, nbhd / 2, n, f.nb, reinterpret_cast<double *>(b + f.pe),
+                             reinterpret_cast<float *>(b + f.pv), reinterpret_cast<long long *>(b + f.pi),
+                             reinterpret_cast<double *>(b + f.pm), f.nbm, b + f.scal, st));
+    }
+    std::vector<unsigned char> host((size_t)n * pce_scalars_bytes());
+    CU(cudaMemcpyAsync(host.data(), b + f.scal, host.size(), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
-    double c0, energy, nx2, ny2;
-    long long pidx;
-    pce_unpack(host, &c0, &energy, &pidx, &nx2, &ny2);
-    const double n = (double)hw;
-    const double outside = n - (double)nbhd * nbhd;
-    // c0 and energy carry the unnormalised inverse-FFT factor n (c0) and n^2
-    // (energy); PCE is invariant to it, NCC divides it out.
-    *pce_out = energy > 0.0 ? (c0 >= 0 ? 1.0 : -1.0) * c0 * c0 * outside / energy : 0.0;
-    if (ncc_out) *ncc_out = (nx2 > 0.0 && ny2 > 0.0) ? (c0 / n) / (n * std::sqrt(nx2 * ny2)) : 0.0;
-    if (peak_yx) {
-        peak_yx[0] = (int)(pidx / W);
-        peak_yx[1] = (int)(pidx % W);
+    const double N = (double)hw;
+    const double outside = N - (double)nbhd * nbhd;
+    for (int q = 0; q < n; ++q) {
+        double c0, energy, sx, sxx, sy, syy;
+        long long pidx;
+        pce_unpack(host.data(), q, &c0, &energy, &pidx, &sx, &sxx, &sy, &syy);
+        // c0 and energy carry the unnormalised inverse-FFT factor N (c0) and
+        // N^2 (energy): PCE is invariant to it, NCC divides it out.
+        pce_out[q] = energy > 0.0 ? (c0 >= 0 ? 1.0 : -1.0) * c0 * c0 * outside / energy : 0.0;
+        if (ncc_out) {
+            const double nx2 = sxx - sx * sx / N, ny2 = syy - sy * sy / N;
+            ncc_out[q] = (nx2 > 0.0 && ny2 > 0.0) ? (c0 / N) / std::sqrt(nx2 * ny2) : 0.0;
+        }
+        if (peak_yx) {
+            peak_yx[2 * q] = (int)(pidx / W);
+            peak_yx[2 * q + 1] = (int)(pidx % W);
+        }
     }
     return PRNU_OK;
+}
+
+prnu_status prnu_pce_match(prnu_ctx *ctx, const float *K, const float *residual_q, const float *img_q, int H, int W,
+                           int C, int nbhd, double *pce_out, double *ncc_out, int *peak_yx, void *ws,
+                           size_t ws_bytes, void *stream) {
+    return prnu_pce_match_batch(ctx, K, residual_q, img_q, 1, H, W, C, nbhd, pce_out, ncc_out, peak_yx, ws,
+                                ws_bytes, stream);
 }
 
 prnu_status prnu_profile_enable(prnu_ctx *ctx, int on) {
@@ -922,11 +930,12 @@ prnu_status prnu_profile_reset(prnu_ctx *ctx) {
     }
     ctx->recs.clear();
     for (auto &n : ctx->klaunches) n = 0;
+    for (auto &b : ctx->kbytes) b = 0.0;
     return PRNU_OK;
 }
 
 prnu_status prnu_profile_read(prnu_ctx *ctx, int index, char *name, size_t name_len, long long *launches,
-                              double *total_ms) {
+                              double *total_ms, double *bytes) {
     if (!ctx) return fail(PRNU_EINVAL, "ctx is NULL");
     DeviceGuard g(ctx->device);
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -936,6 +945,7 @@ prnu_status prnu_profile_read(prnu_ctx *ctx, int index, char *name, size_t name_
         name[name_len - 1] = 0;
     }
     if (launches) *launches = ctx->klaunches[index];
+    if (bytes) *bytes = ctx->kbytes[index];
     if (total_ms) {
         double t = 0.0;
         for (auto &r : ctx->recs) {

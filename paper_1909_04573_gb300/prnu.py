@@ -23,6 +23,7 @@ EXPORTS = (
     "prnu_workspace_size_host", "prnu_sda_average", "prnu_denoise_residual", "prnu_fingerprint_accumulate",
     "prnu_fingerprint_accumulate_host", "prnu_fingerprint_finalize", "prnu_pce_match",
     "prnu_profile_enable", "prnu_profile_reset", "prnu_profile_read", "prnu_denoise_residual_static",
+    "prnu_denoise_residual_batch", "prnu_pce_match_batch",
 )
 
 
@@ -66,10 +67,14 @@ def lib() -> ctypes.CDLL:
                 "prnu_pce_match": [_vp, _vp, _vp, _vp, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _vp, _sz, _vp],
                 "prnu_denoise_residual_static": [_vp, _vp, _i, _i, _i, _pp, _vp, _vp],
+                "prnu_denoise_residual_batch": [_vp, _vp, _i, _i, _i, _i, _pp, _vp, _vp, _sz, _vp],
+                "prnu_pce_match_batch": [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _vp, _sz,
+                                         _vp],
                 "prnu_profile_enable": [_vp, _i],
                 "prnu_profile_reset": [_vp],
                 "prnu_profile_read": [_vp, _i, ctypes.c_char_p, _sz, ctypes.POINTER(ctypes.c_longlong),
-                                      ctypes.POINTER(ctypes.c_double)],
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -130,6 +135,11 @@ def prnu_denoise_residual(ctx, img, H, W, C, params, residual_out, ws, ws_bytes,
                                        stream), ctx)
 
 
+def prnu_denoise_residual_batch(ctx, img, n, H, W, C, params, residual_out, ws, ws_bytes, stream):
+    _check(lib().prnu_denoise_residual_batch(ctx, img, n, H, W, C, ctypes.byref(params), residual_out, ws,
+                                             ws_bytes, stream), ctx)
+
+
 def prnu_fingerprint_accumulate(ctx, frames, m, H, W, C, frame_stride, row_pitch, d, params, num, den, ws,
                                 ws_bytes, stream):
     _check(lib().prnu_fingerprint_accumulate(ctx, frames, m, H, W, C, frame_stride, row_pitch, d,
@@ -155,6 +165,15 @@ def prnu_pce_match(ctx, K, residual_q, img_q, H, W, C, nbhd, ws, ws_bytes, strea
     return pce.value, ncc.value, (peak[0], peak[1])
 
 
+def prnu_pce_match_batch(ctx, K, residual_q, img_q, n, H, W, C, nbhd, ws, ws_bytes, stream):
+    pce = (ctypes.c_double * n)()
+    ncc = (ctypes.c_double * n)()
+    peak = (ctypes.c_int * (2 * n))()
+    _check(lib().prnu_pce_match_batch(ctx, K, residual_q, img_q, n, H, W, C, nbhd, pce, ncc, peak, ws, ws_bytes,
+                                      stream), ctx)
+    return [(pce[i], ncc[i], (peak[2 * i], peak[2 * i + 1])) for i in range(n)]
+
+
 def prnu_denoise_residual_static(ctx, img, H, W, C, params, residual_out, stream):
     """prnu_denoise_residual with the library's fixed static scratch: no
     workspace argument and no allocation (for callers that cannot allocate)."""
@@ -170,17 +189,17 @@ def prnu_profile_reset(ctx) -> None:
 
 
 def prnu_profile_read(ctx) -> dict:
-    """{kernel name: (launches, total device ms)} since the last reset."""
+    """{kernel name: (launches, total device ms, algorithmic bytes)} since the last reset."""
     out = {}
     i = 0
     while True:
         name = ctypes.create_string_buffer(64)
-        n, ms = ctypes.c_longlong(), ctypes.c_double()
-        st = lib().prnu_profile_read(ctx, i, name, 64, ctypes.byref(n), ctypes.byref(ms))
+        n, ms, nb = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+        st = lib().prnu_profile_read(ctx, i, name, 64, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(nb))
         if st == PRNU_EINVAL:
             break
         _check(st, ctx)
-        out[name.value.decode()] = (n.value, ms.value)
+        out[name.value.decode()] = (n.value, ms.value, nb.value)
         i += 1
     return out
 
@@ -246,6 +265,28 @@ class Context:
         prnu_denoise_residual(self.ctx, img.data_ptr(), H, W, C, params, out.data_ptr(), ws.data_ptr(),
                               ws.numel(), self._stream())
         return out
+
+    def denoise_residual_batch(self, imgs, params=None, out=None):
+        """imgs float32 [n, C, H, W] on the device -> residuals [n, C, H, W]."""
+        params = params or default_params()
+        imgs = imgs.contiguous()
+        n, C, H, W = imgs.shape
+        out = self.torch.empty_like(imgs) if out is None else out
+        nb = prnu_workspace_size(self.ctx, H, W, C, params, n)
+        ws = self.workspace(nb)
+        prnu_denoise_residual_batch(self.ctx, imgs.data_ptr(), n, H, W, C, params, out.data_ptr(), ws.data_ptr(),
+                                    ws.numel(), self._stream())
+        return out
+
+    def pce_match_batch(self, K, residual_q, img_q, nbhd: int = 11):
+        """K [H, W]; residual_q, img_q [n, C, H, W] -> [(pce, ncc, (dy, dx))] * n."""
+        n, C, H, W = residual_q.shape
+        K = K.reshape(H, W).contiguous()
+        nb = prnu_workspace_size(self.ctx, H, W, C, default_params(), n)
+        ws = self.workspace(nb)
+        return prnu_pce_match_batch(self.ctx, K.data_ptr(), residual_q.contiguous().data_ptr(),
+                                    img_q.contiguous().data_ptr(), n, H, W, C, nbhd, ws.data_ptr(), ws.numel(),
+                                    self._stream())
 
     def fingerprint_accumulate(self, frames, d: int, num, den, params=None, images_per_pass=None):
         params = params or default_params()

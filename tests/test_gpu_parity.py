@@ -221,3 +221,30 @@ def test_invalid_arguments_are_rejected(ctx):
         P.prnu_denoise_residual(ctx.ctx, x.data_ptr(), 64, 64, 1, p, torch.empty_like(x).data_ptr(),
                                 ws.data_ptr(), 1024, ctx._stream())
     assert e.value.status == P.PRNU_ENOSPC
+
+
+# --------------------------------------------------------------- batches ----
+def test_denoise_residual_batch_matches_oracle(ctx):
+    imgs = np.stack([_frames(72, 104, 3, 1, seed=40 + i)[0].transpose(2, 0, 1) for i in range(5)]).astype(np.float32)
+    got = ctx.denoise_residual_batch(_dev(imgs)).cpu().numpy()
+    for i in range(5):
+        ref = O.residual(imgs[i].astype(np.float64))
+        assert np.abs(got[i] - ref).max() <= RES_TOL
+
+
+def test_pce_match_batch_matches_single_queries_and_oracle(ctx):
+    rng = np.random.default_rng(77)
+    n, C, H, W = 6, 3, 80, 112
+    K = rng.normal(0, 0.01, size=(H, W))
+    Iq = rng.uniform(40, 220, size=(n, C, H, W)).astype(np.float32)
+    Wq = (K[None, None] * Iq * (np.arange(n) % 2)[:, None, None, None] +
+          rng.normal(0, 0.7, size=(n, C, H, W))).astype(np.float32)  # odd queries carry K
+    Kd = _dev(K.astype(np.float32))
+    batch = ctx.pce_match_batch(Kd, _dev(Wq), _dev(Iq))
+    for i in range(n):
+        single = ctx.pce_match(Kd, _dev(Wq[i]), _dev(Iq[i]))
+        r = O.pce_match(K, O.to_gray(Wq[i]), O.to_gray(Iq[i]))
+        assert abs(batch[i][0] - r.pce) <= PCE_TOL * max(abs(r.pce), 1.0)
+        assert abs(single[0] - batch[i][0]) <= 1e-6 * max(abs(batch[i][0]), 1.0)
+        assert abs(batch[i][1] - r.ncc) <= 1e-4 * max(abs(r.ncc), 1e-3)
+        assert (batch[i][0] > 60) == bool(i % 2)
