@@ -41,6 +41,10 @@ def parse():
     ap.add_argument("--no-perframe", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--frames", type=int, default=M_FRAMES,
+                    help="frames of the workload (default 1000; smaller values are for profiling captures)")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the timed SDA region with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
 
 
@@ -67,7 +71,7 @@ class Clocks:
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                       "--format=csv,noheader,nounits", "-lms", "20"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -171,8 +175,9 @@ def main():
     dev = torch.device("cuda", local)
     ctx = P.Context(local)
 
+    m_frames = args.frames
     cam = synth.Camera(H=H, W=W, C=C, camera_id=rank)
-    frames = synth.frames(cam, M_FRAMES, device=dev, drift_px=2.0)        # 6.22 GB resident
+    frames = synth.frames(cam, m_frames, device=dev, drift_px=2.0)        # 6.22 GB resident at 1000 frames
     qf = torch.cat([synth.frames(cam, N_QUERY, stream=1, device=dev),
                     synth.frames(synth.foreign(cam), N_QUERY, stream=1, device=dev)])
     qimg = ctx.sda_average(qf, 1)                                         # [20, 3, H, W] float
@@ -218,12 +223,17 @@ def main():
     P.prnu_profile_enable(ctx.ctx, True)
     clocks = Clocks(local)
     clocks.start()
+    if args.profile_range:
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
     ms = timed(step, args.steps, 0)
+    if args.profile_range:
+        torch.cuda.profiler.stop()
     ck = clocks.stop()
     P.prnu_profile_enable(ctx.ctx, False)
     prof = P.prnu_profile_read(ctx.ctx)
     P.prnu_profile_reset(ctx.ctx)
-    value = world * M_FRAMES / (ms / 1000.0)
+    value = world * m_frames / (ms / 1000.0)
     pos = [p for p in pces[:N_QUERY]]
     neg = [p for p in pces[N_QUERY:]]
 
@@ -246,11 +256,12 @@ def main():
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "peak_kind": f"{peak_kind} copy bandwidth", "traffic": None,
                 "bytes_per_launch": dom_b / dom_n, "launches": dom_n, "ms_per_launch": dom_t / dom_n}
-    step_bytes = M_FRAMES * H * W * C
+    step_bytes = m_frames * H * W * C
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded sensor model; VISION/NYUAD-MMD absent)",
-            "config": {"workload": WORKLOAD, "frames": M_FRAMES, "H": H, "W": W, "C": C, "d": D_SDA,
+            "config": {"workload": WORKLOAD if m_frames == M_FRAMES else f"video-1080p-rgb-{m_frames}f-sda50",
+                       "frames": m_frames, "H": H, "W": W, "C": C, "d": D_SDA,
                        "queries": 2 * N_QUERY, "parallelism": f"1 camera per GPU x {world}",
                        "l2": "inputs 6.22 GB > 129 MB L2 (no flush)"},
             "frame_GBps": step_bytes / (ms / 1000.0) / 1e9,
@@ -263,7 +274,7 @@ def main():
     # ---- per-frame (ALL-FE) comparison: d = 1, 1000 denoise passes x 3 channels
     if not args.no_perframe:
         ms_pf = timed(lambda: step(d=1, images_per_pass=100), 2, 1)
-        line["perframe"] = {"value": world * M_FRAMES / (ms_pf / 1000.0), "unit": UNIT, "ms_per_step": ms_pf,
+        line["perframe"] = {"value": world * m_frames / (ms_pf / 1000.0), "unit": UNIT, "ms_per_step": ms_pf,
                             "sda_speedup": ms_pf / ms}
 
     # ---- end to end through the host-buffer entry point
@@ -299,7 +310,7 @@ def main():
         del probe
         h2d = host.numel() + qhost.numel()
         d2h = 2 * N_QUERY * 48
-        line["e2e"] = {"value": world * M_FRAMES / (ms_e2e / 1000.0), "unit": UNIT, "ms_per_step": ms_e2e,
+        line["e2e"] = {"value": world * m_frames / (ms_e2e / 1000.0), "unit": UNIT, "ms_per_step": ms_e2e,
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                        "pinned_h2d_GBps": h2d_gbps}
         frames_host = host.numpy()

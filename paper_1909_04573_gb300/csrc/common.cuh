@@ -43,6 +43,16 @@ __host__ __device__ __forceinline__ int wrap(int i, int n) {
     return r < 0 ? r + n : r;
 }
 
+// Periodic index for i within one period of [0, n) (the common case of a
+// tile's halo): two compare-and-adds; falls back to a modulo otherwise
+// (planes smaller than a tile's reach).
+__host__ __device__ __forceinline__ int wrap_near(int i, int n) {
+    if (i < 0) i += n;
+    if (i >= n) i -= n;
+    if (i < 0 || i >= n) i = wrap(i, n);
+    return i;
+}
+
 // Mirror padding with edge repeat: index in [0, 2n) -> [0, n).
 __host__ __device__ __forceinline__ int mirror(int i, int n) { return i < n ? i : 2 * n - 1 - i; }
 

@@ -18,11 +18,170 @@
 // exact integer group sums (or float32 images), so the differences are exact.
 // Details are scaled by 1/count (pixel units) when written; the LL chain stays
 // in sum units.
+//
+// Two launch shapes: level 1 (the full-resolution planes) streams down strips
+// with the row pass held in registers; levels >= 2 (a quarter of the samples
+// or fewer, too few strips to keep the GPU busy) use shared-memory tiles.
 #include "kernels.cuh"
 
 namespace prnu {
 
 constexpr float kSqrt2f = 1.41421356237309504880f;
+
+// Streaming layout: a warp owns 32 consecutive output columns q and a strip
+// of SP output rows; each lane walks down its column.  The row pass of an
+// input row y (ref, s, t) goes into a ring of the last 8 input rows held in
+// registers; every two new input rows complete one output row (rows
+// 2p..2p+7).  The ring slot of input row y is (y - 2p0) mod 8, so an unrolled
+// body of 4 output rows uses fixed slots.  Inputs come from global memory
+// through L1 (interior warps read four float2 per row and part); no shared
+// memory and no barriers.
+constexpr int SP = 32;        // output rows per strip (multiple of 4)
+constexpr int WARPS = 4;      // warps per block, side by side in q
+
+struct RowIn {
+    const float *h, *l;       // row base of the high / low parts (l unused at level 1)
+};
+
+template <bool LEVEL1>
+struct Lane {
+    int col[8];               // source column of input samples 2q..2q+7
+    bool fast;                // warp-uniform: columns are 2q..2q+7 directly, float2-aligned
+};
+
+// row pass of one input row: ref, s = sum_{k>=1} h_k (v_k - v_0), t = sum g_k (v_k - v_0)
+template <bool LEVEL1>
+__device__ __forceinline__ void row_item(const AnaArgs &a, const RowIn &row, const Lane<LEVEL1> &L, int q2,
+                                         float &rh, float &rl, float &s, float &t) {
+    float v[8], w[8];
+    if (L.fast) {
+        const float2 *ph = reinterpret_cast<const float2 *>(row.h + q2);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float2 u = __ldg(ph + j);
+            v[2 * j] = u.x;
+            v[2 * j + 1] = u.y;
+        }
+        if (!LEVEL1) {
+            const float2 *pl = reinterpret_cast<const float2 *>(row.l + q2);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float2 u = __ldg(pl + j);
+                w[2 * j] = u.x;
+                w[2 * j + 1] = u.y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            v[k] = __ldg(row.h + L.col[k]);
+            if (!LEVEL1) w[k] = __ldg(row.l + L.col[k]);
+        }
+    }
+    float ss = 0.f, tt = 0.f;
+#pragma unroll
+    for (int k = 1; k < kTaps; ++k) {
+        float dlt = __fsub_rn(v[k], v[0]);
+        if (!LEVEL1) dlt = __fadd_rn(dlt, __fsub_rn(w[k], w[0]));
+        ss = __fmaf_rn(a.f.h[k], dlt, ss);
+        tt = __fmaf_rn(a.f.g[k], dlt, tt);
+    }
+    rh = v[0];
+    rl = LEVEL1 ? 0.f : w[0];
+    s = ss;
+    t = tt;
+}
+
+template <bool LEVEL1>
+__global__ void __launch_bounds__(32 * WARPS, 6) k_analysis_stream(AnaArgs a) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int plane = blockIdx.z;
+    const int R2 = a.R >> 1, C2 = a.Cc >> 1;
+    const int cq0 = (blockIdx.x * WARPS + warp) * 32;  // first output column of this warp
+    if (cq0 >= C2) return;                             // whole warp past the plane
+    const int p0 = blockIdx.y * SP;
+    const int q = min(cq0 + lane, C2 - 1);             // lanes past the edge recompute the last column
+    const bool store_q = cq0 + lane < C2;
+    const int srcH = LEVEL1 ? a.H : a.R, srcW = LEVEL1 ? a.W : a.Cc;
+    const long long pbase = (long long)plane * srcH * srcW;
+
+    Lane<LEVEL1> L;
+    {
+        const int qmax = min(cq0 + 31, C2 - 1);
+        const bool aligned8 = ((reinterpret_cast<uintptr_t>(a.inh) |
+                                (LEVEL1 ? (uintptr_t)0 : reinterpret_cast<uintptr_t>(a.inl))) & 7u) == 0;
+        L.fast = (2 * qmax + 7 < srcW) && ((srcW & 1) == 0) && aligned8;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int gx = wrap_near(2 * q + k, a.Cc);
+            L.col[k] = LEVEL1 ? mirror(gx, a.W) : gx;
+        }
+    }
+    auto row_at = [&](int y) {
+        const int gy = wrap_near(y, a.R);
+        const int sy = LEVEL1 ? mirror(gy, a.H) : gy;
+        RowIn r;
+        r.h = a.inh + pbase + (long long)sy * srcW;
+        r.l = LEVEL1 ? nullptr : a.inl + pbase + (long long)sy * srcW;
+        return r;
+    };
+    const float scale = a.scale_on ? __frcp_rn((float)a.sc.count(plane)) : 1.f;
+
+    float rh[8], rl[8], rs[8], rt[8];
+    const int y0 = 2 * p0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) row_item<LEVEL1>(a, row_at(y0 + k), L, 2 * q, rh[k], rl[k], rs[k], rt[k]);
+
+    const int pend = min(p0 + SP, R2);
+    for (int pb = p0; pb < pend; pb += 4) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int p = pb + j;
+            // input rows 2p+6, 2p+7 go to slots (2j+6) mod 8, (2j+7) mod 8
+            const int s6 = (2 * j + 6) & 7, s7 = (2 * j + 7) & 7;
+            row_item<LEVEL1>(a, row_at(2 * p + 6), L, 2 * q, rh[s6], rl[s6], rs[s6], rt[s6]);
+            row_item<LEVEL1>(a, row_at(2 * p + 7), L, 2 * q, rh[s7], rl[s7], rs[s7], rt[s7]);
+            // column pass over rows 2p..2p+7 = slots 2j .. 2j+7 (mod 8)
+            const int b0 = (2 * j) & 7;
+            const float r0h = rh[b0], r0l = rl[b0];
+            float A = 0.f, B = 0.f;
+#pragma unroll
+            for (int k = 1; k < kTaps; ++k) {
+                const int sl = (b0 + k) & 7;
+                float D = __fsub_rn(rh[sl], r0h);
+                if (!LEVEL1) D = __fadd_rn(D, __fsub_rn(rl[sl], r0l));
+                A = __fmaf_rn(a.f.h[k], D, A);
+                B = __fmaf_rn(a.f.g[k], D, B);
+            }
+            float Sh = 0.f, Sg = 0.f, Th = 0.f, Tg = 0.f;
+#pragma unroll
+            for (int k = 0; k < kTaps; ++k) {
+                const int sl = (b0 + k) & 7;
+                Sh = __fmaf_rn(a.f.h[k], rs[sl], Sh);
+                Sg = __fmaf_rn(a.f.g[k], rs[sl], Sg);
+                Th = __fmaf_rn(a.f.h[k], rt[sl], Th);
+                Tg = __fmaf_rn(a.f.g[k], rt[sl], Tg);
+            }
+            if (p < pend && store_q) {
+                const float llsmall = __fmaf_rn(kSqrt2f, A, Sh);
+                const float lh = __fmaf_rn(kSqrt2f, B, Sg);
+                const long long o = ((long long)plane * R2 + p) * C2 + q;
+                if (a.LLh) {
+                    float sh, se;
+                    two_sum(2.f * r0h, llsmall, sh, se);
+                    const float lo = __fadd_rn(2.f * r0l, se);
+                    float hh, ll;
+                    fast_two_sum(sh, lo, hh, ll);
+                    a.LLh[o] = hh;
+                    a.LLl[o] = ll;
+                }
+                a.LH[o] = lh * scale;
+                a.HL[o] = Th * scale;
+                a.HH[o] = Tg * scale;
+            }
+        }
+    }
+}
 
 constexpr int TP = 16, TQ = 32;                 // output tile: TP rows x TQ cols
 constexpr int IR = 2 * TP + 6, IC = 2 * TQ + 6;  // input tile with the 6-sample halo
@@ -48,12 +207,12 @@ __global__ void __launch_bounds__(256) k_analysis(AnaArgs a) {
 #pragma unroll
     for (int k = 0; k < NCOL; ++k) {
         const int c = tx + 32 * k;
-        const int gx = wrap(2 * q0 + c, a.Cc);
+        const int gx = wrap_near(2 * q0 + c, a.Cc);
         srcx[k] = LEVEL1 ? mirror(gx, a.W) : gx;
     }
     const int srcH = LEVEL1 ? a.H : a.R, srcW = LEVEL1 ? a.W : a.Cc;
     for (int r = ty; r < IR; r += 8) {
-        const int gy = wrap(2 * p0 + r, a.R);
+        const int gy = wrap_near(2 * p0 + r, a.R);
         const int sy = LEVEL1 ? mirror(gy, a.H) : gy;
         const long long rowoff = ((long long)plane * srcH + sy) * srcW;
 #pragma unroll
@@ -151,12 +310,16 @@ __global__ void __launch_bounds__(256) k_analysis(AnaArgs a) {
 }
 
 cudaError_t launch_analysis(const AnaArgs &a, bool level1, cudaStream_t st) {
-    dim3 block(32, 8);
-    dim3 grid((unsigned)((a.Cc / 2 + TQ - 1) / TQ), (unsigned)((a.R / 2 + TP - 1) / TP), (unsigned)a.P);
-    if (level1)
-        k_analysis<true><<<grid, block, 0, st>>>(a);
-    else
+    if (level1) {
+        dim3 block(32 * WARPS);
+        dim3 grid((unsigned)((a.Cc / 2 + 32 * WARPS - 1) / (32 * WARPS)), (unsigned)((a.R / 2 + SP - 1) / SP),
+                  (unsigned)a.P);
+        k_analysis_stream<true><<<grid, block, 0, st>>>(a);
+    } else {
+        dim3 block(32, 8);
+        dim3 grid((unsigned)((a.Cc / 2 + TQ - 1) / TQ), (unsigned)((a.R / 2 + TP - 1) / TP), (unsigned)a.P);
         k_analysis<false><<<grid, block, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -44,12 +44,26 @@ __global__ void k_divide(const float *num, const float *den, long long hw, int C
     }
 }
 
-// column means of one plane: one thread per column (coalesced across threads)
-__global__ void k_colmean(const float *K, int H, int W, double *colmean) {
+// column means of one plane in two passes: a 2-D grid of partial column
+// sums over row bands (coalesced across threads), then one thread per column
+// sums its bands in order.
+constexpr int CM_BAND = 64;
+__global__ void k_colsum_part(const float *K, int H, int W, double *part) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int band = blockIdx.y;
+    if (x >= W) return;
+    const int y0 = band * CM_BAND, y1 = min(H, y0 + CM_BAND);
+    double s = 0.0;
+    for (int y = y0; y < y1; ++y) s += (double)K[(long long)y * W + x];
+    part[(long long)band * W + x] = s;
+}
+
+__global__ void k_colmean(const double *part, int H, int W, double *colmean) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= W) return;
+    const int nb = (H + CM_BAND - 1) / CM_BAND;
     double s = 0.0;
-    for (int y = 0; y < H; ++y) s += (double)K[(long long)y * W + x];
+    for (int b = 0; b < nb; ++b) s += part[(long long)b * W + x];
     colmean[x] = s / H;
 }
 
@@ -150,34 +164,64 @@ __global__ void k_pce_prep(const float *K, const float *Wq, const float *Iq, lon
     const float *im = Iq + (long long)q * C * hw;
     float *xo = X + (long long)q * hw;
     float *yo = Y + (long long)q * hw;
-    // per-thread float32 partials over a short run, then float64 across threads
+    // per-thread float32 partials over 4 samples, then float64 across
     double sx = 0.0, sxx = 0.0, sy = 0.0, syy = 0.0;
-    float fx = 0.f, fxx = 0.f, fy = 0.f, fyy = 0.f;
-    int run = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < hw;
-         i += (long long)gridDim.x * blockDim.x) {
-        float a, b;
+    auto one = [&](float w0, float w1, float w2, float i0, float i1, float i2, float k, float &a, float &yv) {
+        float b;
         if (C == 3) {
-            a = __fmaf_rn(0.114f, w[2 * hw + i], __fmaf_rn(0.587f, w[hw + i], 0.299f * w[i]));
-            b = __fmaf_rn(0.114f, im[2 * hw + i], __fmaf_rn(0.587f, im[hw + i], 0.299f * im[i]));
+            a = __fmaf_rn(0.114f, w2, __fmaf_rn(0.587f, w1, 0.299f * w0));
+            b = __fmaf_rn(0.114f, i2, __fmaf_rn(0.587f, i1, 0.299f * i0));
         } else {
-            a = w[i];
-            b = im[i];
+            a = w0;
+            b = i0;
         }
-        const float yv = K[i] * b;
-        xo[i] = a;
-        yo[i] = yv;
-        fx += a;
-        fxx = __fmaf_rn(a, a, fxx);
-        fy += yv;
-        fyy = __fmaf_rn(yv, yv, fyy);
-        if (++run == 16) {
-            sx += fx; sxx += fxx; sy += fy; syy += fyy;
-            fx = fxx = fy = fyy = 0.f;
-            run = 0;
+        yv = k * b;
+    };
+    const bool vec = ((hw & 3) == 0) && (((reinterpret_cast<uintptr_t>(Wq) | reinterpret_cast<uintptr_t>(Iq) |
+                                           reinterpret_cast<uintptr_t>(K) | reinterpret_cast<uintptr_t>(X) |
+                                           reinterpret_cast<uintptr_t>(Y)) & 15u) == 0);
+    if (vec) {
+        const long long n4 = hw >> 2;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
+             i += (long long)gridDim.x * blockDim.x) {
+            const float4 k4 = __ldg(reinterpret_cast<const float4 *>(K) + i);
+            const float4 w0 = __ldg(reinterpret_cast<const float4 *>(w) + i);
+            const float4 i0 = __ldg(reinterpret_cast<const float4 *>(im) + i);
+            float4 w1 = w0, w2 = w0, i1 = i0, i2 = i0;
+            if (C == 3) {
+                w1 = __ldg(reinterpret_cast<const float4 *>(w + hw) + i);
+                w2 = __ldg(reinterpret_cast<const float4 *>(w + 2 * hw) + i);
+                i1 = __ldg(reinterpret_cast<const float4 *>(im + hw) + i);
+                i2 = __ldg(reinterpret_cast<const float4 *>(im + 2 * hw) + i);
+            }
+            float4 xa, ya;
+            one(w0.x, w1.x, w2.x, i0.x, i1.x, i2.x, k4.x, xa.x, ya.x);
+            one(w0.y, w1.y, w2.y, i0.y, i1.y, i2.y, k4.y, xa.y, ya.y);
+            one(w0.z, w1.z, w2.z, i0.z, i1.z, i2.z, k4.z, xa.z, ya.z);
+            one(w0.w, w1.w, w2.w, i0.w, i1.w, i2.w, k4.w, xa.w, ya.w);
+            reinterpret_cast<float4 *>(xo)[i] = xa;
+            reinterpret_cast<float4 *>(yo)[i] = ya;
+            sx += (xa.x + xa.y) + (xa.z + xa.w);
+            sxx += __fmaf_rn(xa.x, xa.x, xa.y * xa.y) + __fmaf_rn(xa.z, xa.z, xa.w * xa.w);
+            sy += (ya.x + ya.y) + (ya.z + ya.w);
+            syy += __fmaf_rn(ya.x, ya.x, ya.y * ya.y) + __fmaf_rn(ya.z, ya.z, ya.w * ya.w);
+        }
+    } else {
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < hw;
+             i += (long long)gridDim.x * blockDim.x) {
+            float xa, ya;
+            if (C == 3)
+                one(w[i], w[hw + i], w[2 * hw + i], im[i], im[hw + i], im[2 * hw + i], K[i], xa, ya);
+            else
+                one(w[i], 0.f, 0.f, im[i], 0.f, 0.f, K[i], xa, ya);
+            xo[i] = xa;
+            yo[i] = ya;
+            sx += xa;
+            sxx += (double)xa * xa;
+            sy += ya;
+            syy += (double)ya * ya;
         }
     }
-    sx += fx; sxx += fxx; sy += fy; syy += fyy;
     sx = block_sum(sx, sh);
     sxx = block_sum(sxx, sh);
     sy = block_sum(sy, sh);
@@ -302,8 +346,11 @@ cudaError_t launch_divide(const float *num, const float *den, long long hw, int 
     return cudaGetLastError();
 }
 
-cudaError_t launch_zero_mean(float *K, int H, int W, double *colmean, double *rowmean, int sms, cudaStream_t st) {
-    k_colmean<<<(W + 255) / 256, 256, 0, st>>>(K, H, W, colmean);
+cudaError_t launch_zero_mean(float *K, int H, int W, double *colmean, double *rowmean, double *part, int sms,
+                             cudaStream_t st) {
+    const int nb = (H + CM_BAND - 1) / CM_BAND;
+    k_colsum_part<<<dim3((W + 127) / 128, nb), 128, 0, st>>>(K, H, W, part);
+    k_colmean<<<(W + 255) / 256, 256, 0, st>>>(part, H, W, colmean);
     k_rowmean<<<H, RB, 0, st>>>(K, H, W, colmean, rowmean);
     k_sub_means<<<ew_blocks((long long)H * W, sms), 256, 0, st>>>(K, H, W, colmean, rowmean);
     return cudaGetLastError();

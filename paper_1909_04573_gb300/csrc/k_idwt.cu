@@ -26,9 +26,9 @@ __device__ __forceinline__ void load_coeffs(SynTile &s, const float *LL, const f
                                             const float *HH, long long poff, int Rc, int Cc, int y0, int x0) {
     const int tx = threadIdx.x, ty = threadIdx.y;
     if (tx < CT) {
-        const int sx = wrap((x0 >> 1) - 3 + tx, Cc);
+        const int sx = wrap_near((x0 >> 1) - 3 + tx, Cc);
         for (int r = ty; r < CT; r += 8) {
-            const long long o = poff + (long long)wrap((y0 >> 1) - 3 + r, Rc) * Cc + sx;
+            const long long o = poff + (long long)wrap_near((y0 >> 1) - 3 + r, Rc) * Cc + sx;
             s.c[0][r][tx] = LL ? __ldg(LL + o) : 0.f;
             s.c[1][r][tx] = __ldg(LH + o);
             s.c[2][r][tx] = __ldg(HL + o);
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256) k_final(FinalArgs a) {
         __syncthreads();
         synth_cols(s, a.f, tid);
         __syncthreads();
-        const float fn = MLE ? (float)a.sc.count(plane) : 1.f;
+        const float inv_n = MLE ? __frcp_rn((float)a.sc.count(plane)) : 1.f;
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int it = tid + 256 * k;
@@ -145,11 +145,11 @@ __global__ void __launch_bounds__(256) k_final(FinalArgs a) {
             const long long o = (long long)plane * hw + (long long)gy * a.W + gx;
             const bool two = gx + 1 < a.W;
             if (MLE) {
-                const float I0 = __fdiv_rn(__ldg(a.X + o), fn);
+                const float I0 = __ldg(a.X + o) * inv_n;
                 an[2 * k] = __fmaf_rn(w.x, I0, an[2 * k]);
                 ad[2 * k] = __fmaf_rn(I0, I0, ad[2 * k]);
                 if (two) {
-                    const float I1 = __fdiv_rn(__ldg(a.X + o + 1), fn);
+                    const float I1 = __ldg(a.X + o + 1) * inv_n;
                     an[2 * k + 1] = __fmaf_rn(w.y, I1, an[2 * k + 1]);
                     ad[2 * k + 1] = __fmaf_rn(I1, I1, ad[2 * k + 1]);
                 }

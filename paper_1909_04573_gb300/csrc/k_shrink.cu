@@ -33,9 +33,9 @@ __global__ void __launch_bounds__(256) k_shrink(ShrinkArgs a) {
 
     int srcx[2];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) srcx[k] = wrap(x0 + tx + 32 * k - SH, a.Cc);
+    for (int k = 0; k < 2; ++k) srcx[k] = wrap_near(x0 + tx + 32 * k - SH, a.Cc);
     for (int r = ty; r < SE; r += 8) {
-        const long long rowoff = (long long)wrap(y0 + r - SH, a.R) * a.Cc;
+        const long long rowoff = (long long)wrap_near(y0 + r - SH, a.R) * a.Cc;
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int c = tx + 32 * k;
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(256) k_shrink(ShrinkArgs a) {
             const float c = in[(long long)gy * a.Cc + gx];
             const float var = fmaxf(0.f, m[k] - s2);
             const float den = var + s2;
-            a.out[(long long)plane * a.R * a.Cc + (long long)gy * a.Cc + gx] = den > 0.f ? __fdiv_rn(c * s2, den) : 0.f;
+            a.out[(long long)plane * a.R * a.Cc + (long long)gy * a.Cc + gx] = den > 0.f ? __fdividef(c * s2, den) : 0.f;
         }
     } else {
         for (int yl = ty; yl < ST; yl += 8) {
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(256) k_shrink(ShrinkArgs a) {
             const float c = in[(long long)gy * a.Cc + gx];
             const float var = fmaxf(0.f, vmin - s2);
             const float den = var + s2;
-            a.out[(long long)plane * a.R * a.Cc + (long long)gy * a.Cc + gx] = den > 0.f ? __fdiv_rn(c * s2, den) : 0.f;
+            a.out[(long long)plane * a.R * a.Cc + (long long)gy * a.Cc + gx] = den > 0.f ? __fdividef(c * s2, den) : 0.f;
         }
     }
 }

@@ -69,7 +69,8 @@ cudaError_t launch_final(const FinalArgs &a, bool mle, cudaStream_t st);
 // k_fft.cu
 cudaError_t launch_divide(const float *num, const float *den, long long hw, int C, int gray, float *K, int sms,
                           cudaStream_t st);
-cudaError_t launch_zero_mean(float *K, int H, int W, double *colmean, double *rowmean, int sms, cudaStream_t st);
+cudaError_t launch_zero_mean(float *K, int H, int W, double *colmean, double *rowmean, double *part, int sms,
+                             cudaStream_t st);
 cudaError_t launch_mean_var(const float *v, long long n, double *part, int nb, double *tmp, double *out,
                             cudaStream_t st);
 cudaError_t launch_to_complex(const float *K, long long n, cufftComplex *F, int sms, cudaStream_t st);

@@ -400,6 +400,7 @@ struct FftLayout {
     size_t cplx = 0;                  // complex: max(2n half spectra, one full plane)
     size_t real = 0;                  // float: 2n planes (X_i, Y_i) or (M, Mn)
     size_t colmean = 0, rowmean = 0;  // doubles
+    size_t colpart = 0;               // doubles: partial column sums per 64-row band
     size_t part = 0, tmp = 0, mom0 = 0;
     size_t pm = 0, pe = 0, pv = 0, pi = 0, scal = 0;
     size_t work = 0, end = 0;
@@ -421,6 +422,7 @@ prnu_status fft_layout(prnu_ctx *ctx, int H, int W, int n, FftLayout *out) {
     f.cplx = take(std::max(2 * (size_t)n * nh, hw) * sizeof(cufftComplex));
     f.real = take(2 * (size_t)std::max(n, 1) * hw * sizeof(float));
     f.colmean = take((size_t)W * sizeof(double));
+    f.colpart = take((size_t)((H + 63) / 64) * W * sizeof(double));
     f.rowmean = take((size_t)H * sizeof(double));
     f.part = take((size_t)kRedBlocks * 2 * sizeof(double));
     f.tmp = take(2 * sizeof(double));
@@ -771,9 +773,10 @@ prnu_status prnu_fingerprint_finalize(prnu_ctx *ctx, const float *num, const flo
         float *K = K_out + c * hw;
         if (flags & PRNU_ZERO_MEAN)
             {
-                Launch t(ctx, "finalize_zero_mean", st, 3);
+                Launch t(ctx, "finalize_zero_mean", st, 4, (double)hw * 4 * 4);
                 CU(launch_zero_mean(K, H, W, reinterpret_cast<double *>(b + f.colmean),
-                                    reinterpret_cast<double *>(b + f.rowmean), ctx->sms, st));
+                                    reinterpret_cast<double *>(b + f.rowmean),
+                                    reinterpret_cast<double *>(b + f.colpart), ctx->sms, st));
             }
         if (flags & PRNU_WIENER_DFT) {
             cufftHandle plan;

@@ -248,3 +248,13 @@ def test_pce_match_batch_matches_single_queries_and_oracle(ctx):
         assert abs(single[0] - batch[i][0]) <= 1e-6 * max(abs(batch[i][0]), 1.0)
         assert abs(batch[i][1] - r.ncc) <= 1e-4 * max(abs(r.ncc), 1e-3)
         assert (batch[i][0] > 60) == bool(i % 2)
+
+
+def test_residual_of_an_unaligned_image_view(ctx):
+    # a float image starting at an odd element offset (no 8-byte alignment)
+    img = _frames(64, 96, 1, 1, seed=13)[0].transpose(2, 0, 1).astype(np.float32)
+    buf = torch.zeros(img.size + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = _dev(img).reshape(-1)
+    view = buf[1:].view(1, 64, 96)
+    got = ctx.denoise_residual(view).cpu().numpy()
+    assert np.abs(got - O.residual(img.astype(np.float64))).max() <= RES_TOL
