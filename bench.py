@@ -57,6 +57,38 @@ def peaks():
     return 6800.0, "fallback"
 
 
+# Kernels bound by FP32 arithmetic issue rather than HBM, with their
+# algorithmic FP32 operations per algorithmic byte the profiler records.
+# shrink: per coefficient 8 bytes (read + write) and 41 operations: c^2 (1),
+# nested horizontal sums (8), vertical sums of 3/5/7/9 terms (20), four
+# 1/w^2 scalings (4), three minima (3), max(0, v - s0^2) (2), + s0^2 (1),
+# c s0^2 / den (2).
+ALU_OPS_PER_BYTE = {"shrink": 41.0 / 8.0}
+FP32_LANES_PER_SM = 128
+
+# profiler name -> kernel symbol in the ncu captures (profiles/)
+NCU_NAME = {"shrink": "k_shrink<1, 0>", "sda_sum": "k_sda_sum<3, 1024>", "analysis_l1": "k_analysis_stream<1>",
+            "analysis": "k_analysis<0>", "synthesis": "k_synthesis", "final_mle": "k_final<1>",
+            "final_residual": "k_final<0>", "pce_prep": "k_pce_prep"}
+
+def dram_traffic(kernel_symbol):
+    """DRAM bytes per launch of a kernel from the committed ncu capture, or
+    None when the capture is missing or the kernel source changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "dram_traffic_video-1080p-rgb-1000f-sda50.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = line.split("\t")
+        if len(parts) == 5 and parts[0] == kernel_symbol:
+            src = os.path.join(ROOT, "paper_1909_04573_gb300", "csrc", parts[3])
+            if not os.path.exists(src):
+                return None
+            sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+            return float(parts[2]) if sha == parts[4].strip() else None
+    return None
+
+
 # ------------------------------------------------------------------ clocks --
 class Clocks:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -252,10 +284,32 @@ def main():
     dom_n, dom_t, dom_b = own[dom]
     roof = None
     if dom_b > 0 and dom_n > 0:
-        ach = (dom_b / dom_n) / (dom_t / dom_n / 1000.0) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "peak_kind": f"{peak_kind} copy bandwidth", "traffic": None,
-                "bytes_per_launch": dom_b / dom_n, "launches": dom_n, "ms_per_launch": dom_t / dom_n}
+        sec = dom_t / dom_n / 1000.0
+        gbps = (dom_b / dom_n) / sec / 1e9
+        sym = NCU_NAME.get(dom)
+        traffic = dram_traffic(sym) if sym else None
+        if dom in ALU_OPS_PER_BYTE:
+            sm_mhz = (ck or {}).get("sm_mhz") or 2070.0
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            peak_tops = sms * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+            ach = ALU_OPS_PER_BYTE[dom] * (dom_b / dom_n) / sec / 1e12
+            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak_tops, "unit": "TOP/s (FP32)",
+                    "frac": ach / peak_tops,
+                    "peak_kind": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz",
+                    "traffic": traffic, "bytes_per_launch": dom_b / dom_n, "launches": dom_n,
+                    "ms_per_launch": dom_t / dom_n, "hbm_achieved_GBps": gbps, "hbm_frac": gbps / hbm}
+        else:
+            roof = {"kernel": dom, "bound": "hbm", "achieved": gbps, "peak": hbm, "unit": "GB/s",
+                    "frac": gbps / hbm, "peak_kind": f"{peak_kind} copy bandwidth", "traffic": traffic,
+                    "bytes_per_launch": dom_b / dom_n, "launches": dom_n, "ms_per_launch": dom_t / dom_n}
+    # the HBM-bound streaming kernel of the path, for reference
+    if "sda_sum" in own and own["sda_sum"][1] > 0:
+        n_, t_, b_ = own["sda_sum"]
+        g_ = (b_ / n_) / (t_ / n_ / 1000.0) / 1e9
+        sda_roof = {"kernel": "sda_sum", "bound": "hbm", "achieved": g_, "peak": hbm, "unit": "GB/s",
+                    "frac": g_ / hbm, "traffic": dram_traffic(NCU_NAME["sda_sum"]), "bytes_per_launch": b_ / n_}
+    else:
+        sda_roof = None
     step_bytes = m_frames * H * W * C
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -266,7 +320,7 @@ def main():
                        "l2": "inputs 6.22 GB > 129 MB L2 (no flush)"},
             "frame_GBps": step_bytes / (ms / 1000.0) / 1e9,
             "frame_frac_of_peak": step_bytes / (ms / 1000.0) / 1e9 / hbm,
-            "roofline": roof, "gpu_launches": int(launches), "kernels": kern,
+            "roofline": roof, "roofline_sda_sum": sda_roof, "gpu_launches": int(launches), "kernels": kern,
             "pce": {"same_camera_min": min(pos), "foreign_max_abs": max(abs(x) for x in neg)}}
     if ck:
         line["clocks"] = ck

@@ -28,16 +28,26 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 }
 
 // ---------------------------------------------------------------- finalize --
+// K = num/den to float64 accuracy without a float64 divide: q0 is the float32
+// IEEE quotient, then one float64 residual step q = q0 + (num - q0 den) / den
+// (the residual is O(2^-24 num), so its float32-reciprocal scaling leaves an
+// error O(2^-48)).
+__device__ __forceinline__ double div64(float n, float d) {
+    const double q0 = (double)__fdiv_rn(n, d);
+    const double r = fma(-q0, (double)d, (double)n);
+    return fma(r, (double)__frcp_rn(d), q0);
+}
+
 __global__ void k_divide(const float *num, const float *den, long long hw, int C, int gray, float *K) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < hw;
          i += (long long)gridDim.x * blockDim.x) {
         double k[3];
         for (int c = 0; c < C; ++c) {
-            const double d = (double)den[c * hw + i];
-            k[c] = d != 0.0 ? (double)num[c * hw + i] / d : 0.0;
+            const float d = den[c * hw + i];
+            k[c] = d != 0.f ? div64(num[c * hw + i], d) : 0.0;
         }
         if (gray) {
-            K[i] = (float)(0.299 * k[0] + 0.587 * k[1] + 0.114 * k[2]);
+            K[i] = (float)fma(0.114, k[2], fma(0.587, k[1], 0.299 * k[0]));
         } else {
             for (int c = 0; c < C; ++c) K[c * hw + i] = (float)k[c];
         }
@@ -253,7 +263,8 @@ struct PceScalars {
     double sx, sxx, sy, syy;
 };
 
-// energy outside the neighbourhood of zero shift and argmax (first index on ties)
+// energy outside the neighbourhood of zero shift and argmax (first index on
+// ties); one row segment per iteration so the row index is known
 __global__ void k_pce_energy(const float *Cr, int H, int W, int r, double *part_e, float *part_v,
                              long long *part_i) {
     __shared__ double sh[32];
@@ -263,24 +274,21 @@ __global__ void k_pce_energy(const float *Cr, int H, int W, int r, double *part_
     const long long n = (long long)H * W;
     const float *c = Cr + (long long)q * n;
     double e = 0.0;
-    float fe = 0.f;
-    int run = 0;
     float bv = -__int_as_float(0x7f800000);
     long long bi = 0x7fffffffffffffffLL;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(i / W), x = (int)(i - (long long)y * W);
-        const float v = c[i];
-        const int dy = min(y, H - y), dx = min(x, W - x);  // wrapped distance to zero shift
-        if (dy > r || dx > r) fe = __fmaf_rn(v, v, fe);
-        if (++run == 16) {
-            e += fe;
-            fe = 0.f;
-            run = 0;
+    // rows are distributed over blocks, columns over threads
+    for (int y = blockIdx.x; y < H; y += gridDim.x) {
+        const bool ynear = min(y, H - y) <= r;
+        const float *row = c + (long long)y * W;
+        float fe = 0.f;
+        for (int x = threadIdx.x; x < W; x += blockDim.x) {
+            const float v = row[x];
+            const bool near = ynear && min(x, W - x) <= r;
+            if (!near) fe = __fmaf_rn(v, v, fe);
+            if (v > bv) { bv = v; bi = (long long)y * W + x; }  // scan order is increasing per thread
         }
-        if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+        e += fe;
     }
-    e += fe;
     e = block_sum(e, sh);
     sv[threadIdx.x] = bv;
     si[threadIdx.x] = bi;

@@ -20,8 +20,10 @@ constexpr int C2S = SE + 4;                                 // c^2 row stride (f
 // output rows of one column (the 12 row sums of each radius it needs are read
 // once).  Every window sum is a direct sum of its terms (no running
 // subtraction, so a large coefficient leaving a window cannot cancel the small
-// ones).  Other window sets take the generic path.
-template <bool STD>
+// ones).  Other window sets take the generic path.  S2DEV: sigma0^2 is read
+// from device memory (the DFT-domain Wiener filter, whose noise variance is
+// computed on the device).
+template <bool STD, bool S2DEV>
 __global__ void __launch_bounds__(256) k_shrink(ShrinkArgs a) {
     __shared__ __align__(16) float c2[SE][C2S];
     __shared__ float rs[4][SE][ST + 1];
@@ -81,7 +83,7 @@ __global__ void __launch_bounds__(256) k_shrink(ShrinkArgs a) {
     }
     __syncthreads();
 
-    const float s2 = a.s2_dev ? (float)a.s2_dev[1] : a.s2;
+    const float s2 = S2DEV ? (float)a.s2_dev[1] : a.s2;
     const int gx = x0 + tx;
     if (STD) {
         // column sums: thread (tx, ty) owns output rows 4ty .. 4ty+3
@@ -135,10 +137,14 @@ cudaError_t launch_shrink(const ShrinkArgs &a, cudaStream_t st) {
     dim3 block(32, 8);
     dim3 grid((unsigned)((a.Cc + ST - 1) / ST), (unsigned)((a.R + ST - 1) / ST), (unsigned)a.nplanes);
     const bool std4 = a.win.n == 4 && a.win.r[0] == 1 && a.win.r[1] == 2 && a.win.r[2] == 3 && a.win.r[3] == 4;
-    if (std4)
-        k_shrink<true><<<grid, block, 0, st>>>(a);
+    if (std4 && !a.s2_dev)
+        k_shrink<true, false><<<grid, block, 0, st>>>(a);
+    else if (std4)
+        k_shrink<true, true><<<grid, block, 0, st>>>(a);
+    else if (!a.s2_dev)
+        k_shrink<false, false><<<grid, block, 0, st>>>(a);
     else
-        k_shrink<false><<<grid, block, 0, st>>>(a);
+        k_shrink<false, true><<<grid, block, 0, st>>>(a);
     return cudaGetLastError();
 }
 
