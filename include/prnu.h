@@ -51,6 +51,15 @@ typedef enum {
 #define PRNU_WIENER_DFT 2u /* Wiener shrink of |DFT|/sqrt(N) with var(K) noise */
 #define PRNU_TO_GRAY 4u    /* 0.299 R + 0.587 G + 0.114 B before the above */
 
+/* Storage of the intermediate detail / noise subbands (arithmetic is always
+ * float32; the lowpass chain is always a float32 float-float pair). */
+#define PRNU_DTYPE_F32 0
+#define PRNU_DTYPE_F16 1
+#define PRNU_DTYPE_BF16 2
+/* Element type of the input frames of the accumulate calls. */
+#define PRNU_FRAMES_U8 0
+#define PRNU_FRAMES_F16 1
+
 /* Denoiser parameters.  The paper names the wavelet denoiser of Mihcak et
  * al. only by citation (Sec. IV-A, Sec. V); these are the build's reading:
  * orthonormal periodised 8-tap Daubechies DWT, `levels` levels, local
@@ -62,7 +71,12 @@ typedef struct {
     int n_windows;   /* 4 */
     int windows[4];  /* 3, 5, 7, 9 */
     int pad_mode;    /* 0 = mirror with edge repeat to multiples of 2^levels */
-    int dtype;       /* 0 = float32 storage and arithmetic */
+    int dtype;       /* subband storage: PRNU_DTYPE_F32 (default), _F16 or _BF16 */
+    int frame_dtype; /* accumulate input frames: PRNU_FRAMES_U8 (default) or _F16 (values in 0..255 units;
+                        frame_stride and row_pitch stay in bytes) */
+    int compensated; /* 0: num/den are float32 [C][H][W];  1: compensated sums, num and den each point to
+                        [2][C][H][W] float32 (the float-float pair hi, then lo, both zero-initialised by the
+                        caller), accumulated with TwoSum error terms; finalize then reads both parts */
 } prnu_params;
 
 typedef struct prnu_ctx prnu_ctx; /* opaque; owns no per-call buffers */

@@ -1,6 +1,8 @@
 // common.cuh -- shared device/host helpers of libprnu (GB300, sm_103a).
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -69,6 +71,35 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &
     s = __fadd_rn(a, b);
     e = __fsub_rn(b, __fsub_rn(s, a));
 }
+
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float v) {
+    float s, e;
+    two_sum(hi, v, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+// ---- storage types of the detail / noise subbands (arithmetic is float32) --
+enum SubbandType : int { SB_F32 = 0, SB_F16 = 1, SB_BF16 = 2 };
+
+__host__ __device__ inline size_t subband_bytes(int sdt) { return sdt == SB_F32 ? 4 : 2; }
+
+template <class T> __device__ __forceinline__ float ldf(const T *p);
+template <> __device__ __forceinline__ float ldf<float>(const float *p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ldf<__half>(const __half *p) { return __half2float(__ldg(p)); }
+template <> __device__ __forceinline__ float ldf<__nv_bfloat16>(const __nv_bfloat16 *p) {
+    return __bfloat162float(__ldg(p));
+}
+template <class T> __device__ __forceinline__ void stf(T *p, float v);
+template <> __device__ __forceinline__ void stf<float>(float *p, float v) { *p = v; }
+template <> __device__ __forceinline__ void stf<__half>(__half *p, float v) { *p = __float2half_rn(v); }
+template <> __device__ __forceinline__ void stf<__nv_bfloat16>(__nv_bfloat16 *p, float v) {
+    *p = __float2bfloat16_rn(v);
+}
+
+// float-float accumulation (compensated, Neumaier form via TwoSum):
+// (hi, lo) += v with the rounding error of the add kept in lo.
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float v);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

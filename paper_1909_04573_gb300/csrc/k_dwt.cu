@@ -92,7 +92,7 @@ __device__ __forceinline__ void row_item(const AnaArgs &a, const RowIn &row, con
     t = tt;
 }
 
-template <bool LEVEL1>
+template <bool LEVEL1, class T>
 __global__ void __launch_bounds__(32 * WARPS, 6) k_analysis_stream(AnaArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int plane = blockIdx.z;
@@ -175,9 +175,9 @@ __global__ void __launch_bounds__(32 * WARPS, 6) k_analysis_stream(AnaArgs a) {
                     a.LLh[o] = hh;
                     a.LLl[o] = ll;
                 }
-                a.LH[o] = lh * scale;
-                a.HL[o] = Th * scale;
-                a.HH[o] = Tg * scale;
+                stf<T>(static_cast<T *>(a.LH) + o, lh * scale);
+                stf<T>(static_cast<T *>(a.HL) + o, Th * scale);
+                stf<T>(static_cast<T *>(a.HH) + o, Tg * scale);
             }
         }
     }
@@ -188,7 +188,7 @@ constexpr int IR = 2 * TP + 6, IC = 2 * TQ + 6;  // input tile with the 6-sample
 constexpr int ICS = IC + 2;                      // even row stride: float2-aligned rows
 constexpr int NCOL = (IC + 31) / 32;             // input columns per thread
 
-template <bool LEVEL1>
+template <bool LEVEL1, class T>
 __global__ void __launch_bounds__(256) k_analysis(AnaArgs a) {
     __shared__ __align__(16) float vh[IR][ICS];
     __shared__ __align__(16) float vl[LEVEL1 ? 1 : IR][LEVEL1 ? 2 : ICS];
@@ -303,23 +303,33 @@ __global__ void __launch_bounds__(256) k_analysis(AnaArgs a) {
             a.LLh[o] = hh;
             a.LLl[o] = ll;
         }
-        a.LH[o] = lh * scale;
-        a.HL[o] = Th * scale;
-        a.HH[o] = Tg * scale;
+        stf<T>(static_cast<T *>(a.LH) + o, lh * scale);
+        stf<T>(static_cast<T *>(a.HL) + o, Th * scale);
+        stf<T>(static_cast<T *>(a.HH) + o, Tg * scale);
     }
 }
 
-cudaError_t launch_analysis(const AnaArgs &a, bool level1, cudaStream_t st) {
+template <class T>
+static void launch_analysis_t(const AnaArgs &a, bool level1, cudaStream_t st) {
     if (level1) {
         dim3 block(32 * WARPS);
         dim3 grid((unsigned)((a.Cc / 2 + 32 * WARPS - 1) / (32 * WARPS)), (unsigned)((a.R / 2 + SP - 1) / SP),
                   (unsigned)a.P);
-        k_analysis_stream<true><<<grid, block, 0, st>>>(a);
+        k_analysis_stream<true, T><<<grid, block, 0, st>>>(a);
     } else {
         dim3 block(32, 8);
         dim3 grid((unsigned)((a.Cc / 2 + TQ - 1) / TQ), (unsigned)((a.R / 2 + TP - 1) / TP), (unsigned)a.P);
-        k_analysis<false><<<grid, block, 0, st>>>(a);
+        k_analysis<false, T><<<grid, block, 0, st>>>(a);
     }
+}
+
+cudaError_t launch_analysis(const AnaArgs &a, bool level1, cudaStream_t st) {
+    if (a.sdt == SB_F16)
+        launch_analysis_t<__half>(a, level1, st);
+    else if (a.sdt == SB_BF16)
+        launch_analysis_t<__nv_bfloat16>(a, level1, st);
+    else
+        launch_analysis_t<float>(a, level1, st);
     return cudaGetLastError();
 }
 

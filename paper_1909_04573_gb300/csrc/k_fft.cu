@@ -38,13 +38,23 @@ __device__ __forceinline__ double div64(float n, float d) {
     return fma(r, (double)__frcp_rn(d), q0);
 }
 
-__global__ void k_divide(const float *num, const float *den, long long hw, int C, int gray, float *K) {
+// num_lo / den_lo (nullable): low parts of compensated float-float sums, so
+// that the quotient is (num + num_lo) / (den + den_lo) formed in float64.
+__global__ void k_divide(const float *num, const float *den, const float *num_lo, const float *den_lo, long long hw,
+                         int C, int gray, float *K) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < hw;
          i += (long long)gridDim.x * blockDim.x) {
         double k[3];
         for (int c = 0; c < C; ++c) {
-            const float d = den[c * hw + i];
-            k[c] = d != 0.f ? div64(num[c * hw + i], d) : 0.0;
+            const long long o = c * hw + i;
+            if (num_lo) {
+                const double n = (double)num[o] + (double)num_lo[o];
+                const double d = (double)den[o] + (double)den_lo[o];
+                k[c] = d != 0.0 ? n / d : 0.0;
+            } else {
+                const float d = den[o];
+                k[c] = d != 0.f ? div64(num[o], d) : 0.0;
+            }
         }
         if (gray) {
             K[i] = (float)fma(0.114, k[2], fma(0.587, k[1], 0.299 * k[0]));
@@ -348,9 +358,9 @@ static inline unsigned ew_blocks(long long n, int num_sms) {
     return (unsigned)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
-cudaError_t launch_divide(const float *num, const float *den, long long hw, int C, int gray, float *K, int sms,
-                          cudaStream_t st) {
-    k_divide<<<ew_blocks(hw, sms), 256, 0, st>>>(num, den, hw, C, gray, K);
+cudaError_t launch_divide(const float *num, const float *den, const float *num_lo, const float *den_lo, long long hw,
+                          int C, int gray, float *K, int sms, cudaStream_t st) {
+    k_divide<<<ew_blocks(hw, sms), 256, 0, st>>>(num, den, num_lo, den_lo, hw, C, gray, K);
     return cudaGetLastError();
 }
 

@@ -22,17 +22,18 @@ struct SynTile {
 
 // Stage the four coefficient tiles of output tile (y0, x0) of one plane:
 // coefficient rows m0-3 .. m0+15 and columns n0-3 .. n0+15 (periodic).
-__device__ __forceinline__ void load_coeffs(SynTile &s, const float *LL, const float *LH, const float *HL,
-                                            const float *HH, long long poff, int Rc, int Cc, int y0, int x0) {
+template <class T>
+__device__ __forceinline__ void load_coeffs(SynTile &s, const T *LL, const T *LH, const T *HL, const T *HH,
+                                            long long poff, int Rc, int Cc, int y0, int x0) {
     const int tx = threadIdx.x, ty = threadIdx.y;
     if (tx < CT) {
         const int sx = wrap_near((x0 >> 1) - 3 + tx, Cc);
         for (int r = ty; r < CT; r += 8) {
             const long long o = poff + (long long)wrap_near((y0 >> 1) - 3 + r, Rc) * Cc + sx;
-            s.c[0][r][tx] = LL ? __ldg(LL + o) : 0.f;
-            s.c[1][r][tx] = __ldg(LH + o);
-            s.c[2][r][tx] = __ldg(HL + o);
-            s.c[3][r][tx] = __ldg(HH + o);
+            s.c[0][r][tx] = LL ? ldf<T>(LL + o) : 0.f;
+            s.c[1][r][tx] = ldf<T>(LH + o);
+            s.c[2][r][tx] = ldf<T>(HL + o);
+            s.c[3][r][tx] = ldf<T>(HH + o);
         }
     }
 }
@@ -89,13 +90,15 @@ __device__ __forceinline__ float2 synth_pair(const SynTile &s, const Filt &f, in
     return make_float2(o[0], o[1]);
 }
 
+template <class T>
 __global__ void __launch_bounds__(256) k_synthesis(SynArgs a) {
     __shared__ SynTile s;
     const int plane = blockIdx.z;
     const int y0 = blockIdx.y * OT, x0 = blockIdx.x * OT;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const long long poff = (long long)plane * a.Rc * a.Cc;
-    load_coeffs(s, a.LL, a.LH, a.HL, a.HH, poff, a.Rc, a.Cc, y0, x0);
+    load_coeffs<T>(s, static_cast<const T *>(a.LL), static_cast<const T *>(a.LH), static_cast<const T *>(a.HL),
+                   static_cast<const T *>(a.HH), poff, a.Rc, a.Cc, y0, x0);
     __syncthreads();
     synth_cols(s, a.f, tid);
     __syncthreads();
@@ -107,7 +110,9 @@ __global__ void __launch_bounds__(256) k_synthesis(SynArgs a) {
         const int gy = y0 + y, gx = x0 + 2 * n;
         if (gy < Ro && gx < Co) {
             const float2 v = synth_pair(s, a.f, y, n);
-            *reinterpret_cast<float2 *>(a.out + ((long long)plane * Ro + gy) * Co + gx) = v;
+            T *o = static_cast<T *>(a.out) + ((long long)plane * Ro + gy) * Co + gx;
+            stf<T>(o, v.x);
+            stf<T>(o + 1, v.y);
         }
     }
 }
@@ -116,21 +121,24 @@ __global__ void __launch_bounds__(256) k_synthesis(SynArgs a) {
 // grid z, W stored at res_out[plane].  MLE mode: grid z is the channel and
 // the block walks the pass's G images, summing W*I and I*I in registers
 // before one read-modify-write of num/den.
-template <bool MLE>
+template <bool MLE, class T, bool COMP>
 __global__ void __launch_bounds__(256) k_final(FinalArgs a) {
     __shared__ SynTile s;
     const int y0 = blockIdx.y * OT, x0 = blockIdx.x * OT;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    float an[4], ad[4];
+    // MLE sums of the 4 outputs this thread owns; with COMP a float-float
+    // pair each (compensated summation across the pass's images)
+    float an[4], ad[4], anl[4], adl[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) { an[k] = 0.f; ad[k] = 0.f; }
+    for (int k = 0; k < 4; ++k) { an[k] = 0.f; ad[k] = 0.f; anl[k] = 0.f; adl[k] = 0.f; }
     const long long hw = (long long)a.H * a.W;
     const int nimg = MLE ? a.G : 1;
     for (int i = 0; i < nimg; ++i) {
         const int plane = MLE ? i * a.C + (int)blockIdx.z : (int)blockIdx.z;
         const long long poff = (long long)plane * a.Rc * a.Cc;
         if (i > 0) __syncthreads();
-        load_coeffs(s, a.LL, a.LH, a.HL, a.HH, poff, a.Rc, a.Cc, y0, x0);
+        load_coeffs<T>(s, static_cast<const T *>(a.LL), static_cast<const T *>(a.LH), static_cast<const T *>(a.HL),
+                       static_cast<const T *>(a.HH), poff, a.Rc, a.Cc, y0, x0);
         __syncthreads();
         synth_cols(s, a.f, tid);
         __syncthreads();
@@ -146,12 +154,21 @@ __global__ void __launch_bounds__(256) k_final(FinalArgs a) {
             const bool two = gx + 1 < a.W;
             if (MLE) {
                 const float I0 = __ldg(a.X + o) * inv_n;
-                an[2 * k] = __fmaf_rn(w.x, I0, an[2 * k]);
-                ad[2 * k] = __fmaf_rn(I0, I0, ad[2 * k]);
-                if (two) {
-                    const float I1 = __ldg(a.X + o + 1) * inv_n;
-                    an[2 * k + 1] = __fmaf_rn(w.y, I1, an[2 * k + 1]);
-                    ad[2 * k + 1] = __fmaf_rn(I1, I1, ad[2 * k + 1]);
+                const float I1 = two ? __ldg(a.X + o + 1) * inv_n : 0.f;
+                if (COMP) {
+                    ff_add(an[2 * k], anl[2 * k], w.x * I0);
+                    ff_add(ad[2 * k], adl[2 * k], I0 * I0);
+                    if (two) {
+                        ff_add(an[2 * k + 1], anl[2 * k + 1], w.y * I1);
+                        ff_add(ad[2 * k + 1], adl[2 * k + 1], I1 * I1);
+                    }
+                } else {
+                    an[2 * k] = __fmaf_rn(w.x, I0, an[2 * k]);
+                    ad[2 * k] = __fmaf_rn(I0, I0, ad[2 * k]);
+                    if (two) {
+                        an[2 * k + 1] = __fmaf_rn(w.y, I1, an[2 * k + 1]);
+                        ad[2 * k + 1] = __fmaf_rn(I1, I1, ad[2 * k + 1]);
+                    }
                 }
             } else {
                 a.res_out[o] = w.x;
@@ -160,6 +177,7 @@ __global__ void __launch_bounds__(256) k_final(FinalArgs a) {
         }
     }
     if (MLE) {
+        const long long chw = (long long)a.C * hw;  // offset of the low parts when COMP
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int it = tid + 256 * k;
@@ -167,11 +185,25 @@ __global__ void __launch_bounds__(256) k_final(FinalArgs a) {
             const int gy = y0 + y, gx = x0 + 2 * n;
             if (gy >= a.H || gx >= a.W) continue;
             const long long o = (long long)blockIdx.z * hw + (long long)gy * a.W + gx;
-            a.num[o] += an[2 * k];
-            a.den[o] += ad[2 * k];
-            if (gx + 1 < a.W) {
-                a.num[o + 1] += an[2 * k + 1];
-                a.den[o + 1] += ad[2 * k + 1];
+            const int cnt = gx + 1 < a.W ? 2 : 1;
+            for (int e = 0; e < cnt; ++e) {
+                const int j = 2 * k + e;
+                if (COMP) {
+                    float h = a.num[o + e], l = a.num[chw + o + e];
+                    ff_add(h, l, an[j]);
+                    l = __fadd_rn(l, anl[j]);
+                    a.num[o + e] = h;
+                    a.num[chw + o + e] = l;
+                    h = a.den[o + e];
+                    l = a.den[chw + o + e];
+                    ff_add(h, l, ad[j]);
+                    l = __fadd_rn(l, adl[j]);
+                    a.den[o + e] = h;
+                    a.den[chw + o + e] = l;
+                } else {
+                    a.num[o + e] += an[j];
+                    a.den[o + e] += ad[j];
+                }
             }
         }
     }
@@ -180,17 +212,34 @@ __global__ void __launch_bounds__(256) k_final(FinalArgs a) {
 cudaError_t launch_synthesis(const SynArgs &a, cudaStream_t st) {
     dim3 block(32, 8);
     dim3 grid((unsigned)((2 * a.Cc + OT - 1) / OT), (unsigned)((2 * a.Rc + OT - 1) / OT), (unsigned)a.P);
-    k_synthesis<<<grid, block, 0, st>>>(a);
+    if (a.sdt == SB_F16)
+        k_synthesis<__half><<<grid, block, 0, st>>>(a);
+    else if (a.sdt == SB_BF16)
+        k_synthesis<__nv_bfloat16><<<grid, block, 0, st>>>(a);
+    else
+        k_synthesis<float><<<grid, block, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_final(const FinalArgs &a, bool mle, cudaStream_t st) {
+template <class T>
+static void launch_final_t(const FinalArgs &a, bool mle, cudaStream_t st) {
     dim3 block(32, 8);
     dim3 grid((unsigned)((a.W + OT - 1) / OT), (unsigned)((a.H + OT - 1) / OT), (unsigned)(mle ? a.C : a.C * a.G));
-    if (mle)
-        k_final<true><<<grid, block, 0, st>>>(a);
+    if (!mle)
+        k_final<false, T, false><<<grid, block, 0, st>>>(a);
+    else if (a.compensated)
+        k_final<true, T, true><<<grid, block, 0, st>>>(a);
     else
-        k_final<false><<<grid, block, 0, st>>>(a);
+        k_final<true, T, false><<<grid, block, 0, st>>>(a);
+}
+
+cudaError_t launch_final(const FinalArgs &a, bool mle, cudaStream_t st) {
+    if (a.sdt == SB_F16)
+        launch_final_t<__half>(a, mle, st);
+    else if (a.sdt == SB_BF16)
+        launch_final_t<__nv_bfloat16>(a, mle, st);
+    else
+        launch_final_t<float>(a, mle, st);
     return cudaGetLastError();
 }
 

@@ -12,7 +12,9 @@
 // threads on consecutive pixels.  Output: float32 (exact below 2^24, i.e.
 // groups of up to 65793 frames), planar [group][C][H][W], as sums (the
 // fingerprint pipeline stays in "sum units" until the details are formed) or
-// as correctly rounded means.
+// as correctly rounded means.  Frames may also be float16 (one 16-byte load
+// per frame then carries 8 values, summed in float32; such sums are not exact
+// integers, but the same pipeline applies).
 #include <algorithm>
 
 #include "kernels.cuh"
@@ -97,7 +99,84 @@ __global__ void __launch_bounds__(SEGPX * C / 16) k_sda_sum(SdaArgs a) {
     }
 }
 
+// float16 frames: a thread owns 8 consecutive values (16 bytes) of a row
+// segment and sums them in float32 over the group's frames.
+template <int C, int SEGPX>
+__global__ void __launch_bounds__(SEGPX * C / 8) k_sda_sum_f16(SdaArgs a) {
+    constexpr int NT = SEGPX * C / 8;
+    __shared__ float sbuf[SEGPX * C];
+    const int rowvals = a.W * C;
+    const int nseg = (a.W + SEGPX - 1) / SEGPX;
+    const long long units = (long long)a.G * a.H * nseg;
+    const bool aligned16 = ((reinterpret_cast<uintptr_t>(a.frames) | (uintptr_t)a.frame_stride |
+                             (uintptr_t)a.row_pitch) & 15u) == 0;
+    const long long plane = (long long)a.H * a.W;
+    const int k = threadIdx.x;
+    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+        const int seg = (int)(u % nseg);
+        const long long r = u / nseg;
+        const int y = (int)(r % a.H);
+        const int gi = (int)(r / a.H);
+        const int g = a.g0 + gi;
+        const int j0 = g * a.d;
+        const int j1 = min(a.m, j0 + a.d);
+        const int x0 = seg * SEGPX;
+        const int npx = min(SEGPX, a.W - x0);
+        const int e0 = x0 * C + 8 * k;  // first value of this thread's chunk
+        const int ne = min(8, rowvals - e0);
+        float tot[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) tot[i] = 0.f;
+        if (ne > 0) {
+            const uint8_t *base = a.frames + (long long)y * a.row_pitch + 2LL * e0;
+            if (aligned16 && ne == 8) {
+#pragma unroll 4
+                for (int j = j0; j < j1; ++j) {
+                    const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(base + (long long)j * a.frame_stride));
+                    const __half2 *h2 = reinterpret_cast<const __half2 *>(&v);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float2 f = __half22float2(h2[i]);
+                        tot[2 * i] += f.x;
+                        tot[2 * i + 1] += f.y;
+                    }
+                }
+            } else {
+                for (int j = j0; j < j1; ++j) {
+                    const __half *p = reinterpret_cast<const __half *>(base + (long long)j * a.frame_stride);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (i < ne) tot[i] += __half2float(p[i]);
+                }
+            }
+        }
+        const float fn = (float)(j1 - j0);
+        if (u != blockIdx.x) __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) sbuf[8 * k + i] = a.mean ? __fdiv_rn(tot[i], fn) : tot[i];
+        __syncthreads();
+        float *o = a.out + (long long)gi * C * plane + (long long)y * a.W + x0;
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+            for (int x = k; x < npx; x += NT) o[(long long)c * plane + x] = sbuf[x * C + c];
+    }
+}
+
 cudaError_t launch_sda(const SdaArgs &a, int num_sms, cudaStream_t st) {
+    if (a.frame_half) {
+        constexpr int SEG = 1024;
+        const long long units = (long long)a.G * a.H * ((a.W + SEG - 1) / SEG);
+        if (a.C == 3) {
+            constexpr int NT = SEG * 3 / 8;
+            const long long blocks = std::min<long long>(units, (long long)num_sms * (2048 / NT));
+            k_sda_sum_f16<3, SEG><<<(unsigned)std::max<long long>(blocks, 1), NT, 0, st>>>(a);
+        } else {
+            constexpr int NT = SEG / 8;
+            const long long blocks = std::min<long long>(units, (long long)num_sms * (2048 / NT));
+            k_sda_sum_f16<1, SEG><<<(unsigned)std::max<long long>(blocks, 1), NT, 0, st>>>(a);
+        }
+        return cudaGetLastError();
+    }
     if (a.C == 3) {
         constexpr int SEG = 1024, NT = SEG * 3 / 16;
         const long long units = (long long)a.G * a.H * ((a.W + SEG - 1) / SEG);

@@ -23,7 +23,7 @@ constexpr int C2S = SE + 4;                                 // c^2 row stride (f
 // ones).  Other window sets take the generic path.  S2DEV: sigma0^2 is read
 // from device memory (the DFT-domain Wiener filter, whose noise variance is
 // computed on the device).
-template <bool STD, bool S2DEV>
+template <bool STD, bool S2DEV, class T>
 __global__ void __launch_bounds__(256) k_shrink(ShrinkArgs a) {
     __shared__ __align__(16) float c2[SE][C2S];
     __shared__ float rs[4][SE][ST + 1];
@@ -31,7 +31,8 @@ __global__ void __launch_bounds__(256) k_shrink(ShrinkArgs a) {
     const int y0 = blockIdx.y * ST, x0 = blockIdx.x * ST;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * 32 + tx;
-    const float *in = a.in + (long long)plane * a.R * a.Cc;
+    const T *in = static_cast<const T *>(a.in) + (long long)plane * a.R * a.Cc;
+    T *out = static_cast<T *>(a.out) + (long long)plane * a.R * a.Cc;
 
     int srcx[2];
 #pragma unroll
@@ -42,7 +43,7 @@ __global__ void __launch_bounds__(256) k_shrink(ShrinkArgs a) {
         for (int k = 0; k < 2; ++k) {
             const int c = tx + 32 * k;
             if (c < SE) {
-                const float v = __ldg(in + rowoff + srcx[k]);
+                const float v = ldf<T>(in + rowoff + srcx[k]);
                 c2[r][c] = v * v;
             }
         }
@@ -108,10 +109,10 @@ __global__ void __launch_bounds__(256) k_shrink(ShrinkArgs a) {
         for (int k = 0; k < 4; ++k) {
             const int gy = y0 + yb + k;
             if (gy >= a.R || gx >= a.Cc) continue;
-            const float c = in[(long long)gy * a.Cc + gx];
+            const float c = ldf<T>(in + (long long)gy * a.Cc + gx);
             const float var = fmaxf(0.f, m[k] - s2);
             const float den = var + s2;
-            a.out[(long long)plane * a.R * a.Cc + (long long)gy * a.Cc + gx] = den > 0.f ? __fdividef(c * s2, den) : 0.f;
+            stf<T>(out + (long long)gy * a.Cc + gx, den > 0.f ? __fdividef(c * s2, den) : 0.f);
         }
     } else {
         for (int yl = ty; yl < ST; yl += 8) {
@@ -125,26 +126,36 @@ __global__ void __launch_bounds__(256) k_shrink(ShrinkArgs a) {
                 for (int dy = -rad; dy <= rad; ++dy) s += rs[w][yc + dy][tx];
                 vmin = fminf(vmin, s * a.win.inv[w]);
             }
-            const float c = in[(long long)gy * a.Cc + gx];
+            const float c = ldf<T>(in + (long long)gy * a.Cc + gx);
             const float var = fmaxf(0.f, vmin - s2);
             const float den = var + s2;
-            a.out[(long long)plane * a.R * a.Cc + (long long)gy * a.Cc + gx] = den > 0.f ? __fdividef(c * s2, den) : 0.f;
+            stf<T>(out + (long long)gy * a.Cc + gx, den > 0.f ? __fdividef(c * s2, den) : 0.f);
         }
     }
 }
 
-cudaError_t launch_shrink(const ShrinkArgs &a, cudaStream_t st) {
+template <class T>
+static void launch_shrink_t(const ShrinkArgs &a, cudaStream_t st) {
     dim3 block(32, 8);
     dim3 grid((unsigned)((a.Cc + ST - 1) / ST), (unsigned)((a.R + ST - 1) / ST), (unsigned)a.nplanes);
     const bool std4 = a.win.n == 4 && a.win.r[0] == 1 && a.win.r[1] == 2 && a.win.r[2] == 3 && a.win.r[3] == 4;
     if (std4 && !a.s2_dev)
-        k_shrink<true, false><<<grid, block, 0, st>>>(a);
+        k_shrink<true, false, T><<<grid, block, 0, st>>>(a);
     else if (std4)
-        k_shrink<true, true><<<grid, block, 0, st>>>(a);
+        k_shrink<true, true, T><<<grid, block, 0, st>>>(a);
     else if (!a.s2_dev)
-        k_shrink<false, false><<<grid, block, 0, st>>>(a);
+        k_shrink<false, false, T><<<grid, block, 0, st>>>(a);
     else
-        k_shrink<false, true><<<grid, block, 0, st>>>(a);
+        k_shrink<false, true, T><<<grid, block, 0, st>>>(a);
+}
+
+cudaError_t launch_shrink(const ShrinkArgs &a, cudaStream_t st) {
+    if (a.sdt == SB_F16)
+        launch_shrink_t<__half>(a, st);
+    else if (a.sdt == SB_BF16)
+        launch_shrink_t<__nv_bfloat16>(a, st);
+    else
+        launch_shrink_t<float>(a, st);
     return cudaGetLastError();
 }
 

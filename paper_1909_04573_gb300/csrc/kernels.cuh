@@ -9,7 +9,8 @@ namespace prnu {
 
 // k_sda.cu
 struct SdaArgs {
-    const uint8_t *frames;
+    const uint8_t *frames;  // uint8 frames, or fp16 frames when frame_half (byte pointer)
+    int frame_half;
     long long frame_stride, row_pitch;
     int m, H, W, C, d;
     int g0, G;      // groups g0 .. g0+G-1 are produced, output index g - g0
@@ -26,7 +27,8 @@ struct AnaArgs {
     int H, W;           // level 1: unpadded source dims
     int P;
     float *LLh, *LLl;   // [P][R/2][Cc/2]; null on the last level
-    float *LH, *HL, *HH;
+    void *LH, *HL, *HH;  // detail subbands, storage type sdt
+    int sdt;
     PlaneScale sc;
     int scale_on;
     Filt f;
@@ -35,8 +37,9 @@ cudaError_t launch_analysis(const AnaArgs &a, bool level1, cudaStream_t st);
 
 // k_shrink.cu
 struct ShrinkArgs {
-    const float *in;      // [nplanes][R][Cc]
-    float *out;           // [nplanes][R][Cc] (must not alias `in`)
+    const void *in;       // [nplanes][R][Cc], storage type sdt
+    void *out;            // [nplanes][R][Cc] (must not alias `in`)
+    int sdt;
     int R, Cc, nplanes;
     float s2;             // sigma0^2, or taken from s2_dev[1] when s2_dev != null
     const double *s2_dev;
@@ -46,15 +49,18 @@ cudaError_t launch_shrink(const ShrinkArgs &a, cudaStream_t st);
 
 // k_idwt.cu
 struct SynArgs {
-    const float *LL;   // noise LL at this level [P][Rc][Cc], or null (zero)
-    const float *LH, *HL, *HH;
+    const void *LL;    // noise LL at this level [P][Rc][Cc], or null (zero); storage type sdt
+    const void *LH, *HL, *HH;
     int Rc, Cc, P;     // coefficient dims; output is 2Rc x 2Cc
-    float *out;        // [P][2Rc][2Cc]
+    void *out;         // [P][2Rc][2Cc]
+    int sdt;
     Filt f;
 };
 struct FinalArgs {
-    const float *LL;   // level-1 noise LL [P][Rc][Cc], or null (one-level transform)
-    const float *LH, *HL, *HH;
+    const void *LL;    // level-1 noise LL [P][Rc][Cc], or null (one-level transform); storage type sdt
+    const void *LH, *HL, *HH;
+    int sdt;
+    int compensated;   // MLE mode: num, den are [2][C][H][W] float-float pairs (hi, then lo)
     int Rc, Cc;        // Hp/2, Wp/2
     int H, W, C, G;    // crop and plane map: image i, channel c -> plane i*C + c
     const float *X;    // MLE mode: group sums [G][C][H][W]
@@ -67,8 +73,8 @@ cudaError_t launch_synthesis(const SynArgs &a, cudaStream_t st);
 cudaError_t launch_final(const FinalArgs &a, bool mle, cudaStream_t st);
 
 // k_fft.cu
-cudaError_t launch_divide(const float *num, const float *den, long long hw, int C, int gray, float *K, int sms,
-                          cudaStream_t st);
+cudaError_t launch_divide(const float *num, const float *den, const float *num_lo, const float *den_lo, long long hw,
+                          int C, int gray, float *K, int sms, cudaStream_t st);
 cudaError_t launch_zero_mean(float *K, int H, int W, double *colmean, double *rowmean, double *part, int sms,
                              cudaStream_t st);
 cudaError_t launch_mean_var(const float *v, long long n, double *part, int nb, double *tmp, double *out,

@@ -212,7 +212,11 @@ prnu_status check_params(const prnu_params *p, int H, int W, Win *win) {
     if (!(p->sigma0 >= 0.f) || !std::isfinite(p->sigma0)) return fail(PRNU_EINVAL, "sigma0 must be finite and >= 0");
     if (p->n_windows < 1 || p->n_windows > 4) return fail(PRNU_EINVAL, "n_windows must be in [1, 4]");
     if (p->pad_mode != 0) return fail(PRNU_EUNSUPPORTED, "pad_mode %d not supported (0 = mirror)", p->pad_mode);
-    if (p->dtype != 0) return fail(PRNU_EUNSUPPORTED, "dtype %d not supported (0 = float32)", p->dtype);
+    if (p->dtype < PRNU_DTYPE_F32 || p->dtype > PRNU_DTYPE_BF16)
+        return fail(PRNU_EINVAL, "dtype %d invalid (0 = float32, 1 = float16, 2 = bfloat16 subbands)", p->dtype);
+    if (p->frame_dtype != PRNU_FRAMES_U8 && p->frame_dtype != PRNU_FRAMES_F16)
+        return fail(PRNU_EINVAL, "frame_dtype %d invalid (0 = uint8, 1 = float16)", p->frame_dtype);
+    if (p->compensated != 0 && p->compensated != 1) return fail(PRNU_EINVAL, "compensated must be 0 or 1");
     if (win) {
         win->n = p->n_windows;
         for (int i = 0; i < 4; ++i) {
@@ -244,8 +248,9 @@ struct Layout {
 
 constexpr size_t kAlign = 256;
 
-Layout make_layout(int H, int W, long long P, int L, bool withX) {
+Layout make_layout(int H, int W, long long P, int L, bool withX, int sdt = SB_F32) {
     Layout lo;
+    const size_t es = subband_bytes(sdt);  // detail, noise and noise-LL storage
     const long long Hp = padded(H, L), Wp = padded(W, L);
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -259,10 +264,10 @@ Layout make_layout(int H, int W, long long P, int L, bool withX) {
         if (l < L) {
             lo.LLh[l] = take(P * A * sizeof(float));
             lo.LLl[l] = take(P * A * sizeof(float));
-            lo.Rn[l] = take(P * A * sizeof(float));
+            lo.Rn[l] = take(P * A * es);
         }
-        lo.D[l] = take(3 * P * A * sizeof(float));
-        lo.N[l] = take(3 * P * A * sizeof(float));
+        lo.D[l] = take(3 * P * A * es);
+        lo.N[l] = take(3 * P * A * es);
     }
     lo.end = off;
     return lo;
@@ -276,6 +281,10 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
     const int L = prm.levels;
     const int Hp = padded(H, L), Wp = padded(W, L);
     auto F = [&](size_t off) { return reinterpret_cast<float *>(ws + off); };
+    const int sdt = prm.dtype;
+    const size_t es = subband_bytes(sdt);
+    // typed subband k of a region holding 3 (or 1) planes groups of P planes
+    auto SB = [&](size_t off, long long A, int k) { return static_cast<void *>(ws + off + (size_t)k * P * A * es); };
     for (int l = 1; l <= L; ++l) {
         const long long A = (long long)(Hp >> l) * (Wp >> l);
         AnaArgs a{};
@@ -288,21 +297,23 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
         a.P = P;
         a.LLh = l < L ? F(lo.LLh[l]) : nullptr;
         a.LLl = l < L ? F(lo.LLl[l]) : nullptr;
-        a.LH = F(lo.D[l]);
-        a.HL = F(lo.D[l]) + P * A;
-        a.HH = F(lo.D[l]) + 2 * P * A;
+        a.LH = SB(lo.D[l], A, 0);
+        a.HL = SB(lo.D[l], A, 1);
+        a.HH = SB(lo.D[l], A, 2);
+        a.sdt = sdt;
         a.sc = sc;
         a.scale_on = scale_on;
         a.f = ctx->filt;
         {
             const double in_b = l == 1 ? (double)P * H * W * 4 : (double)P * a.R * a.Cc * 8;
-            const double out_b = (double)P * A * (12 + (l < L ? 8 : 0));
+            const double out_b = (double)P * A * (3.0 * es + (l < L ? 8 : 0));
             Launch t(ctx, l == 1 ? "analysis_l1" : "analysis", st, 1, in_b + out_b);
             CU(launch_analysis(a, l == 1, st));
         }
         ShrinkArgs s{};
-        s.in = F(lo.D[l]);
-        s.out = F(lo.N[l]);
+        s.in = SB(lo.D[l], A, 0);
+        s.out = SB(lo.N[l], A, 0);
+        s.sdt = sdt;
         s.R = Hp >> l;
         s.Cc = Wp >> l;
         s.nplanes = 3 * P;
@@ -310,40 +321,44 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
         s.s2_dev = nullptr;
         s.win = win;
         {
-            Launch t(ctx, "shrink", st, 1, 2.0 * s.nplanes * s.R * s.Cc * 4);
+            Launch t(ctx, "shrink", st, 1, 2.0 * s.nplanes * s.R * s.Cc * es);
             CU(launch_shrink(s, st));
         }
     }
     for (int l = L; l >= 2; --l) {
         const long long A = (long long)(Hp >> l) * (Wp >> l);
         SynArgs y{};
-        y.LL = l == L ? nullptr : F(lo.Rn[l]);
-        y.LH = F(lo.N[l]);
-        y.HL = F(lo.N[l]) + P * A;
-        y.HH = F(lo.N[l]) + 2 * P * A;
+        y.LL = l == L ? nullptr : SB(lo.Rn[l], A, 0);
+        y.LH = SB(lo.N[l], A, 0);
+        y.HL = SB(lo.N[l], A, 1);
+        y.HH = SB(lo.N[l], A, 2);
+        y.sdt = sdt;
         y.Rc = Hp >> l;
         y.Cc = Wp >> l;
         y.P = P;
-        y.out = F(lo.Rn[l - 1]);
+        y.out = SB(lo.Rn[l - 1], 0, 0);
         y.f = ctx->filt;
         {
-            Launch t(ctx, "synthesis", st, 1, (double)P * A * 4 * (y.LL ? 4 : 3) + (double)P * A * 16);
+            Launch t(ctx, "synthesis", st, 1, (double)P * A * es * (y.LL ? 4 : 3) + (double)P * A * 4 * es);
             CU(launch_synthesis(y, st));
         }
     }
     const long long A1 = (long long)(Hp >> 1) * (Wp >> 1);
-    fin.LL = L == 1 ? nullptr : F(lo.Rn[1]);
-    fin.LH = F(lo.N[1]);
-    fin.HL = F(lo.N[1]) + P * A1;
-    fin.HH = F(lo.N[1]) + 2 * P * A1;
+    fin.LL = L == 1 ? nullptr : SB(lo.Rn[1], A1, 0);
+    fin.LH = SB(lo.N[1], A1, 0);
+    fin.HL = SB(lo.N[1], A1, 1);
+    fin.HH = SB(lo.N[1], A1, 2);
+    fin.sdt = sdt;
+    fin.compensated = prm.compensated;
     fin.Rc = Hp >> 1;
     fin.Cc = Wp >> 1;
     fin.H = H;
     fin.W = W;
     fin.f = ctx->filt;
     {
-        const double cin = (double)P * A1 * 4 * (fin.LL ? 4 : 3);
-        const double io = mle ? (double)P * H * W * 4 + (double)fin.C * H * W * 16 : (double)P * H * W * 4;
+        const double cin = (double)P * A1 * es * (fin.LL ? 4 : 3);
+        const double io = mle ? (double)P * H * W * 4 + (double)fin.C * H * W * 16 * (prm.compensated ? 2 : 1)
+                              : (double)P * H * W * 4;
         Launch t(ctx, mle ? "final_mle" : "final_residual", st, 1, cin + io);
         CU(launch_final(fin, mle, st));
     }
@@ -357,13 +372,16 @@ prnu_status check_ws(void *ws, size_t ws_bytes, size_t need) {
 }
 
 prnu_status check_frames(const uint8_t *frames, int m, int H, int W, int C, size_t frame_stride, size_t row_pitch,
-                         int d) {
+                         int d, int fes = 1) {
     if (!frames) return fail(PRNU_EINVAL, "frames is NULL");
     if (m < 1) return fail(PRNU_EINVAL, "m must be >= 1");
     if (d < 1 || d > m) return fail(PRNU_EINVAL, "d must be in [1, m] (d=%d, m=%d)", d, m);
     if (d > 65793) return fail(PRNU_EINVAL, "d must be <= 65793 (exact float32 group sums)");
-    if (row_pitch < (size_t)W * C) return fail(PRNU_EINVAL, "row_pitch < W*C");
-    if (m > 1 && frame_stride < (size_t)(H - 1) * row_pitch + (size_t)W * C) return fail(PRNU_EINVAL, "frame_stride too small");
+    if (row_pitch < (size_t)W * C * fes) return fail(PRNU_EINVAL, "row_pitch < W*C*element size");
+    if (m > 1 && frame_stride < (size_t)(H - 1) * row_pitch + (size_t)W * C * fes)
+        return fail(PRNU_EINVAL, "frame_stride too small");
+    if (fes == 2 && ((reinterpret_cast<uintptr_t>(frames) | frame_stride | row_pitch) & 1u))
+        return fail(PRNU_EINVAL, "float16 frames need 2-byte aligned pointer and strides");
     return PRNU_OK;
 }
 
@@ -454,7 +472,7 @@ prnu_status accumulate_pass(prnu_ctx *ctx, const uint8_t *frames, int m, int H, 
                             int d, int g0, int G, const prnu_params &prm, const Win &win, float *num, float *den,
                             char *ws, cudaStream_t st) {
     const int P = G * C;
-    const Layout lo = make_layout(H, W, P, prm.levels, true);
+    const Layout lo = make_layout(H, W, P, prm.levels, true, prm.dtype);
     SdaArgs sa{};
     sa.frames = frames;
     sa.frame_stride = (long long)fs;
@@ -468,8 +486,10 @@ prnu_status accumulate_pass(prnu_ctx *ctx, const uint8_t *frames, int m, int H, 
     sa.G = G;
     sa.out = reinterpret_cast<float *>(ws + lo.X);
     sa.mean = 0;
+    sa.frame_half = prm.frame_dtype == PRNU_FRAMES_F16;
     {
-        const double fr = (double)(std::min(m, (g0 + G) * d) - g0 * d) * H * W * C;
+        const double fr = (double)(std::min(m, (g0 + G) * d) - g0 * d) * H * W * C *
+                          (prm.frame_dtype == PRNU_FRAMES_F16 ? 2 : 1);
         Launch t(ctx, "sda_sum", st, 1, fr + (double)P * H * W * 4);
         CU(launch_sda(sa, ctx->sms, st));
     }
@@ -485,11 +505,11 @@ prnu_status accumulate_pass(prnu_ctx *ctx, const uint8_t *frames, int m, int H, 
 }
 
 // Largest number of groups per pass whose layout fits in `bytes`.
-int groups_fitting(int H, int W, int C, int L, size_t bytes, int gmax) {
+int groups_fitting(int H, int W, int C, int L, size_t bytes, int gmax, int sdt) {
     int lo = 0, hi = gmax;
     while (lo < hi) {
         const int mid = (lo + hi + 1) / 2;
-        if (make_layout(H, W, (long long)mid * C, L, true).end <= bytes)
+        if (make_layout(H, W, (long long)mid * C, L, true, sdt).end <= bytes)
             lo = mid;
         else
             hi = mid - 1;
@@ -519,7 +539,9 @@ prnu_status prnu_default_params(prnu_params *p) {
     p->windows[2] = 7;
     p->windows[3] = 9;
     p->pad_mode = 0;
-    p->dtype = 0;
+    p->dtype = PRNU_DTYPE_F32;
+    p->frame_dtype = PRNU_FRAMES_U8;
+    p->compensated = 0;
     return PRNU_OK;
 }
 
@@ -586,7 +608,7 @@ prnu_status prnu_workspace_size(prnu_ctx *ctx, int H, int W, int C, const prnu_p
     if ((s = check_params(params, H, W, nullptr)) != PRNU_OK) return s;
     if (images_per_pass < 1) return fail(PRNU_EINVAL, "images_per_pass must be >= 1");
     DeviceGuard g(ctx->device);
-    size_t need = make_layout(H, W, (long long)images_per_pass * C, params->levels, true).end;
+    size_t need = make_layout(H, W, (long long)images_per_pass * C, params->levels, true, params->dtype).end;
     FftLayout f;
     if ((s = fft_layout(ctx, H, W, images_per_pass, &f)) != PRNU_OK) return s;
     need = std::max(need, f.end);
@@ -603,7 +625,7 @@ prnu_status prnu_workspace_size_host(prnu_ctx *ctx, int H, int W, int C, int d, 
     if (groups_per_pass < 1 || d < 1) return fail(PRNU_EINVAL, "groups_per_pass and d must be >= 1");
     const size_t frame = (size_t)H * W * C;
     const size_t stage = align_up((size_t)groups_per_pass * d * frame, kAlign);
-    *bytes = 2 * stage + make_layout(H, W, (long long)groups_per_pass * C, params->levels, true).end;
+    *bytes = 2 * stage + make_layout(H, W, (long long)groups_per_pass * C, params->levels, true, params->dtype).end;
     return PRNU_OK;
 }
 
@@ -627,6 +649,7 @@ prnu_status prnu_sda_average(prnu_ctx *ctx, const uint8_t *frames, int m, int H,
     a.G = (m + d - 1) / d;
     a.out = sda_out;
     a.mean = 1;
+    a.frame_half = 0;
     Launch t(ctx, "sda_mean", S(stream), 1, (double)m * H * W * C + (double)a.G * C * H * W * 4);
     CU(launch_sda(a, ctx->sms, S(stream)));
     return PRNU_OK;
@@ -642,7 +665,7 @@ prnu_status prnu_denoise_residual_batch(prnu_ctx *ctx, const float *img, int n, 
     Win win;
     if ((s = check_geometry(H, W, C)) != PRNU_OK) return s;
     if ((s = check_params(params, H, W, &win)) != PRNU_OK) return s;
-    const Layout lo = make_layout(H, W, (long long)n * C, params->levels, false);
+    const Layout lo = make_layout(H, W, (long long)n * C, params->levels, false, params->dtype);
     if ((s = check_ws(ws, ws_bytes, lo.end)) != PRNU_OK) return s;
     DeviceGuard g(ctx->device);
     FinalArgs fin{};
@@ -667,10 +690,11 @@ prnu_status prnu_fingerprint_accumulate(prnu_ctx *ctx, const uint8_t *frames, in
     Win win;
     if ((s = check_geometry(H, W, C)) != PRNU_OK) return s;
     if ((s = check_params(params, H, W, &win)) != PRNU_OK) return s;
-    if ((s = check_frames(frames, m, H, W, C, frame_stride, row_pitch, d)) != PRNU_OK) return s;
+    const int fes = params->frame_dtype == PRNU_FRAMES_F16 ? 2 : 1;
+    if ((s = check_frames(frames, m, H, W, C, frame_stride, row_pitch, d, fes)) != PRNU_OK) return s;
     const int g = (m + d - 1) / d;
-    const int Gp = groups_fitting(H, W, C, params->levels, ws_bytes, g);
-    if (Gp < 1) return check_ws(ws, ws_bytes, make_layout(H, W, C, params->levels, true).end);
+    const int Gp = groups_fitting(H, W, C, params->levels, ws_bytes, g, params->dtype);
+    if (Gp < 1) return check_ws(ws, ws_bytes, make_layout(H, W, C, params->levels, true, params->dtype).end);
     if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(PRNU_EINVAL, "workspace must be 256-byte aligned");
     DeviceGuard gd(ctx->device);
     for (int g0 = 0; g0 < g; g0 += Gp) {
@@ -690,16 +714,17 @@ prnu_status prnu_fingerprint_accumulate_host(prnu_ctx *ctx, const uint8_t *host_
     Win win;
     if ((s = check_geometry(H, W, C)) != PRNU_OK) return s;
     if ((s = check_params(params, H, W, &win)) != PRNU_OK) return s;
-    if ((s = check_frames(host_frames, m, H, W, C, frame_stride, row_pitch, d)) != PRNU_OK) return s;
+    const int fes = params->frame_dtype == PRNU_FRAMES_F16 ? 2 : 1;
+    if ((s = check_frames(host_frames, m, H, W, C, frame_stride, row_pitch, d, fes)) != PRNU_OK) return s;
     if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(PRNU_EINVAL, "workspace must be 256-byte aligned");
     const int g = (m + d - 1) / d;
-    const size_t fbytes = (size_t)H * W * C;  // staged frames are packed
+    const size_t fbytes = (size_t)H * W * C * fes;  // staged frames are packed
     // largest groups-per-pass with two staging buffers and the pass layout
     int Gp = 0;
     for (int lo = 1, hi = g; lo <= hi;) {
         const int mid = (lo + hi) / 2;
         const size_t stage = align_up((size_t)mid * d * fbytes, kAlign);
-        const size_t need = 2 * stage + make_layout(H, W, (long long)mid * C, params->levels, true).end;
+        const size_t need = 2 * stage + make_layout(H, W, (long long)mid * C, params->levels, true, params->dtype).end;
         if (need <= ws_bytes) {
             Gp = mid;
             lo = mid + 1;
@@ -708,7 +733,8 @@ prnu_status prnu_fingerprint_accumulate_host(prnu_ctx *ctx, const uint8_t *host_
         }
     }
     if (Gp < 1) {
-        const size_t need = 2 * align_up((size_t)d * fbytes, kAlign) + make_layout(H, W, C, params->levels, true).end;
+        const size_t need =
+            2 * align_up((size_t)d * fbytes, kAlign) + make_layout(H, W, C, params->levels, true, params->dtype).end;
         return fail(PRNU_ENOSPC, "workspace too small: need %zu bytes, got %zu", need, ws_bytes);
     }
     DeviceGuard gd(ctx->device);
@@ -717,7 +743,8 @@ prnu_status prnu_fingerprint_accumulate_host(prnu_ctx *ctx, const uint8_t *host_
     uint8_t *buf[2] = {reinterpret_cast<uint8_t *>(base), reinterpret_cast<uint8_t *>(base + stage)};
     char *rest = base + 2 * stage;
     cudaStream_t st = S(stream);
-    const bool packed = row_pitch == (size_t)W * C && (m == 1 || frame_stride == (size_t)H * W * C);
+    const size_t rowb = (size_t)W * C * fes;
+    const bool packed = row_pitch == rowb && (m == 1 || frame_stride == (size_t)H * rowb);
     int k = 0;
     for (int g0 = 0; g0 < g; g0 += Gp, ++k) {
         const int G = std::min(Gp, g - g0);
@@ -729,15 +756,15 @@ prnu_status prnu_fingerprint_accumulate_host(prnu_ctx *ctx, const uint8_t *host_
                                cudaMemcpyHostToDevice, ctx->copy_stream));
         } else {
             for (int j = j0; j < j1; ++j)
-                CU(cudaMemcpy2DAsync(buf[b] + (size_t)(j - j0) * fbytes, (size_t)W * C,
-                                     host_frames + (size_t)j * frame_stride, row_pitch, (size_t)W * C, H,
+                CU(cudaMemcpy2DAsync(buf[b] + (size_t)(j - j0) * fbytes, rowb,
+                                     host_frames + (size_t)j * frame_stride, row_pitch, rowb, H,
                                      cudaMemcpyHostToDevice, ctx->copy_stream));
         }
         CU(cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream));
         CU(cudaStreamWaitEvent(st, ctx->ev_copied[b], 0));
         // the staged chunk holds frames j0 .. j1-1, i.e. groups 0..G-1 of a
         // sequence of (j1 - j0) frames
-        if ((s = accumulate_pass(ctx, buf[b], j1 - j0, H, W, C, fbytes, (size_t)W * C, d, 0, G, *params, win, num,
+        if ((s = accumulate_pass(ctx, buf[b], j1 - j0, H, W, C, fbytes, rowb, d, 0, G, *params, win, num,
                                  den, rest, st)) != PRNU_OK)
             return s;
         CU(cudaEventRecord(ctx->ev_free[b], st));
@@ -767,7 +794,9 @@ prnu_status prnu_fingerprint_finalize(prnu_ctx *ctx, const float *num, const flo
     char *b = static_cast<char *>(ws);
     {
         Launch t(ctx, "finalize_divide", st, 1, (double)hw * 4 * (2 * C + Cout));
-        CU(launch_divide(num, den, hw, C, (flags & PRNU_TO_GRAY) ? 1 : 0, K_out, ctx->sms, st));
+        const bool comp = params && params->compensated;
+        CU(launch_divide(num, den, comp ? num + C * hw : nullptr, comp ? den + C * hw : nullptr, hw, C,
+                         (flags & PRNU_TO_GRAY) ? 1 : 0, K_out, ctx->sms, st));
     }
     for (int c = 0; c < Cout; ++c) {
         float *K = K_out + c * hw;

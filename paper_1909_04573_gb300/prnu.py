@@ -33,9 +33,14 @@ class PrnuError(RuntimeError):
         self.status = status
 
 
+PRNU_DTYPE_F32, PRNU_DTYPE_F16, PRNU_DTYPE_BF16 = 0, 1, 2
+PRNU_FRAMES_U8, PRNU_FRAMES_F16 = 0, 1
+
+
 class prnu_params(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("sigma0", ctypes.c_float), ("n_windows", ctypes.c_int),
-                ("windows", ctypes.c_int * 4), ("pad_mode", ctypes.c_int), ("dtype", ctypes.c_int)]
+                ("windows", ctypes.c_int * 4), ("pad_mode", ctypes.c_int), ("dtype", ctypes.c_int),
+                ("frame_dtype", ctypes.c_int), ("compensated", ctypes.c_int)]
 
 
 _lib = None
@@ -91,9 +96,13 @@ def _check(status: int, ctx=None) -> None:
         raise PrnuError(status, msg)
 
 
-def default_params(levels=4, sigma0=3.0, windows=(3, 5, 7, 9)) -> prnu_params:
+def default_params(levels=4, sigma0=3.0, windows=(3, 5, 7, 9), dtype=PRNU_DTYPE_F32, frame_dtype=PRNU_FRAMES_U8,
+                   compensated=False) -> prnu_params:
     p = prnu_params()
     _check(lib().prnu_default_params(ctypes.byref(p)))
+    p.dtype = dtype
+    p.frame_dtype = frame_dtype
+    p.compensated = 1 if compensated else 0
     p.levels = levels
     p.sigma0 = sigma0
     p.n_windows = len(windows)
@@ -243,9 +252,10 @@ class Context:
         if frames.dim() == 3:
             frames = frames.unsqueeze(-1)
         m, H, W, C = frames.shape
-        assert frames.dtype.itemsize == 1 and frames.stride(3) == 1 and frames.stride(2) == C, \
-            "frames must be uint8 [m, H, W, C] with interleaved channels"
-        return frames, m, H, W, C, frames.stride(0), frames.stride(1)
+        es = frames.dtype.itemsize
+        assert es in (1, 2) and frames.stride(3) == 1 and frames.stride(2) == C, \
+            "frames must be uint8 or float16 [m, H, W, C] with interleaved channels"
+        return frames, m, H, W, C, frames.stride(0) * es, frames.stride(1) * es
 
     def sda_average(self, frames, d: int):
         frames, m, H, W, C, fs, rp = self._frames_geometry(frames)
@@ -289,7 +299,8 @@ class Context:
                                     self._stream())
 
     def fingerprint_accumulate(self, frames, d: int, num, den, params=None, images_per_pass=None):
-        params = params or default_params()
+        """num, den: float32 [C, H, W] ([2, C, H, W] with params.compensated)."""
+        params = params or default_params(frame_dtype=PRNU_FRAMES_F16 if frames.dtype.itemsize == 2 else 0)
         frames, m, H, W, C, fs, rp = self._frames_geometry(frames)
         g = (m + d - 1) // d
         n = prnu_workspace_size(self.ctx, H, W, C, params, images_per_pass or g)
@@ -298,7 +309,7 @@ class Context:
                                     den.data_ptr(), ws.data_ptr(), n, self._stream())
 
     def fingerprint_accumulate_host(self, host_frames, d: int, num, den, params=None, groups_per_pass=1):
-        params = params or default_params()
+        params = params or default_params(frame_dtype=PRNU_FRAMES_F16 if host_frames.dtype.itemsize == 2 else 0)
         host_frames, m, H, W, C, fs, rp = self._frames_geometry(host_frames)
         n = prnu_workspace_size_host(self.ctx, H, W, C, d, params, groups_per_pass)
         ws = self.workspace(n)
@@ -307,7 +318,7 @@ class Context:
 
     def fingerprint_finalize(self, num, den, flags: int = 0, params=None):
         params = params or default_params()
-        C, H, W = num.shape
+        C, H, W = num.shape[-3:]
         Cout = 1 if flags & PRNU_TO_GRAY else C
         K = self.torch.empty((Cout, H, W), dtype=self.torch.float32, device=num.device)
         n = prnu_workspace_size(self.ctx, H, W, C, params, 1)

@@ -30,15 +30,17 @@ def partition_groups(m: int, d: int, world: int):
     return out
 
 
-def accumulate_sharded(accumulate, frames, d: int, num, den, rank: int, world: int, group=None):
+def accumulate_sharded(accumulate, frames, d: int, num, den, rank: int, world: int, group=None,
+                       reduce: bool = True):
     """Each rank accumulates its run of groups with ``accumulate(frames_slice,
-    d, num, den)`` into its own num/den (zero-initialised by the caller), then
-    num and den are summed across ranks with torch.distributed.all_reduce
-    (world > 1).  Returns the (f0, f1) run this rank processed."""
+    d, num, den)`` into its own num/den (zero-initialised by the caller), then,
+    with ``reduce`` and world > 1, num and den are summed across ranks with
+    torch.distributed.all_reduce.  Returns the (f0, f1) run this rank
+    processed."""
     f0, f1 = partition_groups(len(frames), d, world)[rank]
     if f1 > f0:
         accumulate(frames[f0:f1], d, num, den)
-    if world > 1:
+    if reduce and world > 1:
         import torch.distributed as dist
         dist.all_reduce(num, op=dist.ReduceOp.SUM, group=group)
         dist.all_reduce(den, op=dist.ReduceOp.SUM, group=group)

@@ -89,7 +89,7 @@ def test_virtual_ranks_on_one_gpu_sum_to_single_call():
             n = torch.zeros_like(full_n)
             dd = torch.zeros_like(full_n)
             shard.accumulate_sharded(lambda f, d_, a, b: ctx.fingerprint_accumulate(f, d_, a, b), fr, 5, n, dd,
-                                     rank, world)
+                                     rank, world, reduce=False)
             sum_n += n      # the host-side sum stands in for the all-reduce
             sum_d += dd
         torch.cuda.synchronize()
