@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--frames", type=int, default=M_FRAMES,
                     help="frames of the workload (default 1000; smaller values are for profiling captures)")
+    ap.add_argument("--config", default="video", choices=["video", "precision", "depth"],
+                    help="video: 1000 RGB 1920x1080 frames, SDA-50 (the headline); precision: 500 RGB 4032x3024 "
+                         "frames, SDA-25, per storage type throughput and error against the FP64 oracle")
     ap.add_argument("--mode", default="weak", choices=["weak", "shard"],
                     help="weak: one camera per GPU (no exchange); shard: one camera's groups split over the GPUs, "
                          "num/den summed with one all-reduce (strong scaling)")
@@ -182,6 +185,161 @@ def reference_arm(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------- precision config --
+def precision_config(args, rank, world, local):
+    """500 RGB 4032x3024 frames (sigma_read 3), SDA groups of 25.  For each
+    storage variant: step time of accumulate + finalize over all frames, and
+    the error of the residual (one SDA frame), the fingerprint and the PCE of
+    a same-camera query against the FP64 oracle on the first two groups."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import oracle as O
+    from paper_1909_04573_gb300 import prnu as P
+    from paper_1909_04573_gb300 import synth
+
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    dev = torch.device("cuda", local)
+    Hh, Ww, Cc, m, d = 3024, 4032, 3, args.frames if args.frames != M_FRAMES else 500, 25
+    cam = synth.Camera(H=Hh, W=Ww, C=Cc, camera_id=rank, sigma_read=3.0)
+    frames = synth.frames(cam, m, device=dev, drift_px=2.0)
+    q = synth.frames(cam, 1, stream=1, device=dev)
+    ctx = P.Context(local)
+    qimg = ctx.sda_average(q, 1)
+    # oracle on the first two groups
+    sample = frames[: 2 * d].cpu().numpy()
+    t0 = time.perf_counter()
+    onum, oden = O.fingerprint_accumulate(sample, d)
+    oK = O.fingerprint_finalize(onum, oden, O.TO_GRAY)[0]
+    oimg = O.sda_average(sample[:d], d)[0]
+    ores = O.residual(oimg)
+    qh = qimg[0].cpu().numpy().astype(np.float64)
+    oq = O.residual(qh)
+    opce = O.pce_match(oK, O.to_gray(oq), O.to_gray(qh)).pce
+    t_oracle = time.perf_counter() - t0
+    frames16 = frames.to(torch.float16)
+    variants = [("u8-f32", P.PRNU_FRAMES_U8, P.PRNU_DTYPE_F32, False),
+                ("u8-f32-compensated", P.PRNU_FRAMES_U8, P.PRNU_DTYPE_F32, True),
+                ("u8-f16", P.PRNU_FRAMES_U8, P.PRNU_DTYPE_F16, False),
+                ("u8-bf16", P.PRNU_FRAMES_U8, P.PRNU_DTYPE_BF16, False),
+                ("f16-f16", P.PRNU_FRAMES_F16, P.PRNU_DTYPE_F16, False)]
+    out = {}
+    for name, fdt, sdt, comp in variants:
+        prm = P.default_params(dtype=sdt, frame_dtype=fdt, compensated=comp)
+        src = frames16 if fdt == P.PRNU_FRAMES_F16 else frames
+        shape = (2, Cc, Hh, Ww) if comp else (Cc, Hh, Ww)
+        num = torch.zeros(shape, device=dev)
+        den = torch.zeros_like(num)
+
+        def step():
+            num.zero_()
+            den.zero_()
+            ctx.fingerprint_accumulate(src, d, num, den, params=prm)
+            ctx.fingerprint_finalize(num, den, P.PRNU_TO_GRAY, params=prm)
+
+        for _ in range(max(1, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        # errors on the two-group sample
+        num.zero_()
+        den.zero_()
+        ctx.fingerprint_accumulate(src[: 2 * d], d, num, den, params=prm)
+        K = ctx.fingerprint_finalize(num, den, P.PRNU_TO_GRAY, params=prm)
+        res = ctx.denoise_residual(torch.as_tensor(oimg.astype(np.float32), device=dev), params=prm)
+        wq = ctx.denoise_residual(qimg[0], params=prm)
+        pce = ctx.pce_match(K[0], wq, qimg[0])[0]
+        Kc = K[0].cpu().numpy()
+        out[name] = {"frames_per_s": m / (ms / 1000.0), "ms_per_step": ms,
+                     "residual_maxabs": float(np.abs(res.cpu().numpy() - ores).max()),
+                     "fingerprint_relL2": float(np.linalg.norm(Kc - oK) / np.linalg.norm(oK)),
+                     "pce_rel": abs(pce - opce) / abs(opce), "pce": pce}
+    line = {"metric": "precision: error vs FP64 oracle and frames/s per storage type", "unit": "frames/s",
+            "config": {"workload": f"precision-4032x3024-rgb-{m}f-sda25", "frames": m, "H": Hh, "W": Ww, "C": Cc,
+                       "d": d, "sigma_read": 3.0, "error_sample": "first 2 SDA groups (50 frames) + 1 query"},
+            "oracle_pce": opce, "oracle_seconds": t_oracle, "variants": out, "steps": args.steps}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+# ----------------------------------------------------------- depth study --
+def depth_config(args, rank, world, local):
+    """Synthetic analogue of the paper's SDA-depth experiment (Sec. V-C): per
+    camera 50 frames give fingerprints at d = 1, 2, 5, 10, 25, 50 (50 .. 1
+    denoise calls); 8 queries per camera are matched block-wise (disjoint
+    500 x 500 blocks, Sec. V-A) against their own camera's fingerprint (true
+    cases) and the next camera's (false cases); PCE threshold 60 (Sec. V).
+    Flat scenes (low-pass sigma 8 px) against textured ones (sigma 1.5 px)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_1909_04573_gb300 import prnu as P
+    from paper_1909_04573_gb300 import synth
+
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    dev = torch.device("cuda", local)
+    ctx = P.Context(local)
+    Hh = Ww = 1000
+    Cc, n_cam, m, n_q, blk = 3, 4, 50, 8, 500
+    depths = [1, 2, 5, 10, 25, 50]
+    flags = P.PRNU_TO_GRAY | P.PRNU_ZERO_MEAN | P.PRNU_WIENER_DFT
+    result = {}
+    for label, sig in (("flat", 8.0), ("textured", 1.5)):
+        cams = [synth.Camera(H=Hh, W=Ww, C=Cc, camera_id=700 + i, scene_sigma=sig) for i in range(n_cam)]
+        frames = [synth.frames(c, m, device=dev) for c in cams]
+        qimg = [ctx.sda_average(synth.frames(c, n_q, stream=1, device=dev), 1) for c in cams]
+        qres = [ctx.denoise_residual_batch(q).clone() for q in qimg]
+        rows = {}
+        for d in depths:
+            Ks = []
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for i in range(n_cam):
+                num = torch.zeros((Cc, Hh, Ww), device=dev)
+                den = torch.zeros_like(num)
+                ctx.fingerprint_accumulate(frames[i], d, num, den)
+                Ks.append(ctx.fingerprint_finalize(num, den, flags)[0].clone())
+            e1.record()
+            torch.cuda.synchronize()
+            fe_ms = e0.elapsed_time(e1) / n_cam
+            pos, neg = [], []
+            for i in range(n_cam):
+                for j, tgt in ((i, pos), ((i + 1) % n_cam, neg)):
+                    Kb, Wb, Ib = [], [], []
+                    for by in range(Hh // blk):
+                        for bx in range(Ww // blk):
+                            ys, xs = slice(by * blk, (by + 1) * blk), slice(bx * blk, (bx + 1) * blk)
+                            for k in range(n_q):
+                                Kb.append(Ks[i][ys, xs])
+                                Wb.append(qres[j][k][:, ys, xs])
+                                Ib.append(qimg[j][k][:, ys, xs])
+                    res = ctx.pce_match_pairs(torch.stack(Kb), torch.stack(Wb), torch.stack(Ib))
+                    tgt.extend(r[0] for r in res)
+            pos, neg = np.array(pos), np.array(neg)
+            rows[str(d)] = {"denoise_calls": (m + d - 1) // d, "fe_ms_per_camera": fe_ms,
+                            "pce_mean_true": float(pos.mean()), "pce_median_true": float(np.median(pos)),
+                            "tpr": float((pos > 60).mean()), "fpr": float((neg > 60).mean()),
+                            "blocks_true": int(pos.size), "blocks_false": int(neg.size)}
+        result[label] = rows
+    line = {"metric": "SDA depth study: block-wise PCE / TPR at threshold 60 vs SDA depth",
+            "config": {"workload": "depth-1000x1000-rgb-50f", "cameras": n_cam, "frames": m, "queries": n_q,
+                       "block": blk, "depths": depths, "finalize": "grey, zero-mean, DFT Wiener"},
+            "result": result}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 # --------------------------------------------------------------- GPU arm ---
 def main():
     args = parse()
@@ -190,6 +348,12 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         reference_arm(args, rank)
+        return
+    if args.config == "precision":
+        precision_config(args, rank, world, local)
+        return
+    if args.config == "depth":
+        depth_config(args, rank, world, local)
         return
 
     import numpy as np

@@ -211,6 +211,15 @@ prnu_status prnu_pce_match_batch(prnu_ctx *ctx, const float *K, const float *res
                                  int H, int W, int C, int nbhd, double *pce_out, double *ncc_out, int *peak_yx,
                                  void *ws, size_t ws_bytes, void *stream);
 
+/* PCE of n (fingerprint, query) pairs, each query against its own grey
+ * fingerprint plane: K is device float32 [n][H][W]; otherwise as
+ * prnu_pce_match_batch.  Used for block-wise matching (Sec. V: fingerprints
+ * split into disjoint 500 x 500 blocks, each correlated with the same block of
+ * the query) and for matrices of fingerprints against queries. */
+prnu_status prnu_pce_match_pairs(prnu_ctx *ctx, const float *K, const float *residual_q, const float *img_q, int n,
+                                 int H, int W, int C, int nbhd, double *pce_out, double *ncc_out, int *peak_yx,
+                                 void *ws, size_t ws_bytes, void *stream);
+
 /* Per-kernel profiling (not part of the paper's method).  Every kernel launch
  * is counted per kernel name.  With profiling on, each launch (and each cuFFT
  * call, named cufft_*) is also bracketed by CUDA events recorded on its

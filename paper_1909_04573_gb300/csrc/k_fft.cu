@@ -176,10 +176,11 @@ __global__ void k_real_scaled(const cufftComplex *F, long long n, float scale, f
 // Y_i = K * grey(img_i); the block partials carry sum and sum of squares of
 // X_i and Y_i in float64.  The means are removed exactly by zeroing the DC
 // bin of the cross spectrum: sum_x (X-mx)(Y(x+s)-my) = sum_x X Y(x+s) - N mx my.
-__global__ void k_pce_prep(const float *K, const float *Wq, const float *Iq, long long hw, int C, float *X,
-                           float *Y, double *part) {
+__global__ void k_pce_prep(const float *Kbase, long long k_stride, const float *Wq, const float *Iq, long long hw,
+                           int C, float *X, float *Y, double *part) {
     __shared__ double sh[32];
     const int q = blockIdx.y;
+    const float *K = Kbase + (long long)q * k_stride;  // one fingerprint for all queries, or one per query
     const float *w = Wq + (long long)q * C * hw;
     const float *im = Iq + (long long)q * C * hw;
     float *xo = X + (long long)q * hw;
@@ -404,9 +405,9 @@ cudaError_t launch_real_scaled(const cufftComplex *F, long long n, float scale, 
     k_real_scaled<<<ew_blocks(n, sms), 256, 0, st>>>(F, n, scale, K);
     return cudaGetLastError();
 }
-cudaError_t launch_pce_prep(const float *K, const float *Wq, const float *Iq, long long hw, int C, int n, int nb,
-                            float *X, float *Y, double *part, cudaStream_t st) {
-    k_pce_prep<<<dim3(nb, n), RB, 0, st>>>(K, Wq, Iq, hw, C, X, Y, part);
+cudaError_t launch_pce_prep(const float *K, long long k_stride, const float *Wq, const float *Iq, long long hw, int C,
+                            int n, int nb, float *X, float *Y, double *part, cudaStream_t st) {
+    k_pce_prep<<<dim3(nb, n), RB, 0, st>>>(K, k_stride, Wq, Iq, hw, C, X, Y, part);
     return cudaGetLastError();
 }
 cudaError_t launch_cross_spectrum(const cufftComplex *FX, const cufftComplex *FY, long long nh, int n,

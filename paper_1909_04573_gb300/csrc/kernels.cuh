@@ -86,8 +86,8 @@ cudaError_t launch_apply_ratio(cufftComplex *F, const float *M, const float *Mn,
                                cudaStream_t st);
 cudaError_t launch_real_scaled(const cufftComplex *F, long long n, float scale, float *K, int sms,
                                cudaStream_t st);
-cudaError_t launch_pce_prep(const float *K, const float *Wq, const float *Iq, long long hw, int C, int n, int nb,
-                            float *X, float *Y, double *part, cudaStream_t st);
+cudaError_t launch_pce_prep(const float *K, long long k_stride, const float *Wq, const float *Iq, long long hw, int C,
+                            int n, int nb, float *X, float *Y, double *part, cudaStream_t st);
 cudaError_t launch_cross_spectrum(const cufftComplex *FX, const cufftComplex *FY, long long nh, int n,
                                   cufftComplex *Z, int sms, cudaStream_t st);
 cudaError_t launch_pce_reduce(const float *Cr, int H, int W, int r, int n, int nb, double *part_e, float *part_v,

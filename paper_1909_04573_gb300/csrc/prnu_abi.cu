@@ -864,9 +864,10 @@ prnu_status prnu_fingerprint_finalize(prnu_ctx *ctx, const float *num, const flo
     return PRNU_OK;
 }
 
-prnu_status prnu_pce_match_batch(prnu_ctx *ctx, const float *K, const float *residual_q, const float *img_q, int n,
-                                 int H, int W, int C, int nbhd, double *pce_out, double *ncc_out, int *peak_yx,
-                                 void *ws, size_t ws_bytes, void *stream) {
+namespace {
+prnu_status pce_impl(prnu_ctx *ctx, const float *K, long long k_stride, const float *residual_q, const float *img_q,
+                     int n, int H, int W, int C, int nbhd, double *pce_out, double *ncc_out, int *peak_yx, void *ws,
+                     size_t ws_bytes, void *stream) {
     if (!ctx || !K || !residual_q || !img_q || !pce_out) return fail(PRNU_EINVAL, "NULL argument");
     if (n < 1) return fail(PRNU_EINVAL, "n must be >= 1");
     prnu_status s;
@@ -885,7 +886,8 @@ prnu_status prnu_pce_match_batch(prnu_ctx *ctx, const float *K, const float *res
     cufftComplex *FX = reinterpret_cast<cufftComplex *>(b + f.cplx);
     {
         Launch t(ctx, "pce_prep", st, 1, (double)n * hw * 4 * (2 * C + 2) + (double)hw * 4);
-        CU(launch_pce_prep(K, residual_q, img_q, hw, C, n, f.nbm, X, Y, reinterpret_cast<double *>(b + f.pm), st));
+        CU(launch_pce_prep(K, k_stride, residual_q, img_q, hw, C, n, f.nbm, X, Y,
+                           reinterpret_cast<double *>(b + f.pm), st));
     }
     cufftHandle r2c, c2r;
     size_t w1, w2;
@@ -935,6 +937,21 @@ prnu_status prnu_pce_match_batch(prnu_ctx *ctx, const float *K, const float *res
         }
     }
     return PRNU_OK;
+}
+
+}  // namespace
+
+prnu_status prnu_pce_match_batch(prnu_ctx *ctx, const float *K, const float *residual_q, const float *img_q, int n,
+                                 int H, int W, int C, int nbhd, double *pce_out, double *ncc_out, int *peak_yx,
+                                 void *ws, size_t ws_bytes, void *stream) {
+    return pce_impl(ctx, K, 0, residual_q, img_q, n, H, W, C, nbhd, pce_out, ncc_out, peak_yx, ws, ws_bytes, stream);
+}
+
+prnu_status prnu_pce_match_pairs(prnu_ctx *ctx, const float *K, const float *residual_q, const float *img_q, int n,
+                                 int H, int W, int C, int nbhd, double *pce_out, double *ncc_out, int *peak_yx,
+                                 void *ws, size_t ws_bytes, void *stream) {
+    return pce_impl(ctx, K, (long long)H * W, residual_q, img_q, n, H, W, C, nbhd, pce_out, ncc_out, peak_yx, ws,
+                    ws_bytes, stream);
 }
 
 prnu_status prnu_pce_match(prnu_ctx *ctx, const float *K, const float *residual_q, const float *img_q, int H, int W,

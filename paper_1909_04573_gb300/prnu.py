@@ -23,7 +23,7 @@ EXPORTS = (
     "prnu_workspace_size_host", "prnu_sda_average", "prnu_denoise_residual", "prnu_fingerprint_accumulate",
     "prnu_fingerprint_accumulate_host", "prnu_fingerprint_finalize", "prnu_pce_match",
     "prnu_profile_enable", "prnu_profile_reset", "prnu_profile_read", "prnu_denoise_residual_static",
-    "prnu_denoise_residual_batch", "prnu_pce_match_batch",
+    "prnu_denoise_residual_batch", "prnu_pce_match_batch", "prnu_pce_match_pairs",
 )
 
 
@@ -74,6 +74,9 @@ def lib() -> ctypes.CDLL:
                 "prnu_denoise_residual_static": [_vp, _vp, _i, _i, _i, _pp, _vp, _vp],
                 "prnu_denoise_residual_batch": [_vp, _vp, _i, _i, _i, _i, _pp, _vp, _vp, _sz, _vp],
                 "prnu_pce_match_batch": [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _vp, _sz,
+                                         _vp],
+                "prnu_pce_match_pairs": [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _vp, _sz,
                                          _vp],
                 "prnu_profile_enable": [_vp, _i],
@@ -179,6 +182,15 @@ def prnu_pce_match_batch(ctx, K, residual_q, img_q, n, H, W, C, nbhd, ws, ws_byt
     ncc = (ctypes.c_double * n)()
     peak = (ctypes.c_int * (2 * n))()
     _check(lib().prnu_pce_match_batch(ctx, K, residual_q, img_q, n, H, W, C, nbhd, pce, ncc, peak, ws, ws_bytes,
+                                      stream), ctx)
+    return [(pce[i], ncc[i], (peak[2 * i], peak[2 * i + 1])) for i in range(n)]
+
+
+def prnu_pce_match_pairs(ctx, K, residual_q, img_q, n, H, W, C, nbhd, ws, ws_bytes, stream):
+    pce = (ctypes.c_double * n)()
+    ncc = (ctypes.c_double * n)()
+    peak = (ctypes.c_int * (2 * n))()
+    _check(lib().prnu_pce_match_pairs(ctx, K, residual_q, img_q, n, H, W, C, nbhd, pce, ncc, peak, ws, ws_bytes,
                                       stream), ctx)
     return [(pce[i], ncc[i], (peak[2 * i], peak[2 * i + 1])) for i in range(n)]
 
@@ -295,6 +307,15 @@ class Context:
         nb = prnu_workspace_size(self.ctx, H, W, C, default_params(), n)
         ws = self.workspace(nb)
         return prnu_pce_match_batch(self.ctx, K.data_ptr(), residual_q.contiguous().data_ptr(),
+                                    img_q.contiguous().data_ptr(), n, H, W, C, nbhd, ws.data_ptr(), ws.numel(),
+                                    self._stream())
+
+    def pce_match_pairs(self, K, residual_q, img_q, nbhd: int = 11):
+        """K [n, H, W]; residual_q, img_q [n, C, H, W]: query i against fingerprint i."""
+        n, C, H, W = residual_q.shape
+        nb = prnu_workspace_size(self.ctx, H, W, C, default_params(), n)
+        ws = self.workspace(nb)
+        return prnu_pce_match_pairs(self.ctx, K.contiguous().data_ptr(), residual_q.contiguous().data_ptr(),
                                     img_q.contiguous().data_ptr(), n, H, W, C, nbhd, ws.data_ptr(), ws.numel(),
                                     self._stream())
 
