@@ -178,6 +178,35 @@ prnu_status prnu_fingerprint_accumulate_host(prnu_ctx *ctx, const uint8_t *host_
                                              const prnu_params *params, float *num, float *den,
                                              void *ws, size_t ws_bytes, void *stream);
 
+/* One camera of a multi-camera batch: its frames (device; uint8 or float16 per
+ * params->frame_dtype), frame count, geometry, byte strides, SDA group size
+ * (ragged last group) and its own MLE sums (device float32 [C][H][W], or
+ * [2][C][H][W] with params->compensated; accumulated into, as for
+ * prnu_fingerprint_accumulate).  Cameras must not share num/den. */
+typedef struct {
+    const uint8_t *frames;
+    int m, H, W, C;
+    size_t frame_stride, row_pitch;
+    int d;
+    float *num, *den;
+} prnu_camera;
+
+/* Workspace for prnu_fingerprint_accumulate_multi running up to
+ * groups_per_pass SDA groups (1..192) of one geometry per pass. */
+prnu_status prnu_workspace_size_multi(prnu_ctx *ctx, const prnu_camera *cams, int ncams, const prnu_params *params,
+                                      int groups_per_pass, size_t *bytes);
+
+/* MLE fingerprint sums (Sec. IV-A / IV-B) of many cameras with uneven frame
+ * counts, resolutions and SDA group sizes in one call: cameras are grouped by
+ * geometry and their groups packed into passes that mix cameras (each pass is
+ * one launch of every kernel of the pipeline, with a per-group table of frame
+ * pointers, counts and destination camera).  `cams` is a host array.  Same
+ * results as one prnu_fingerprint_accumulate per camera.  Allocates nothing,
+ * synchronises nothing: the call can be captured in a CUDA graph once the
+ * workspace exists. */
+prnu_status prnu_fingerprint_accumulate_multi(prnu_ctx *ctx, const prnu_camera *cams, int ncams,
+                                              const prnu_params *params, void *ws, size_t ws_bytes, void *stream);
+
 /* Fingerprint from the MLE sums, Sec. IV-A: K = num/den (division in
  * float64; K = 0 where den == 0), then the optional literature steps named by
  * `flags` (not defined in the paper): PRNU_TO_GRAY, PRNU_ZERO_MEAN,

@@ -28,12 +28,35 @@ struct Win {
     float inv[4];   // 1/w^2
 };
 
+// One SDA group of a multi-camera pass: its first frame, strides, frame
+// count and camera index.
+struct GroupDesc {
+    const uint8_t *frames;
+    long long frame_stride, row_pitch;
+    int n, cam;
+};
+struct CamDesc {
+    float *num, *den;
+};
+constexpr int kMaxPassGroups = 192;
+constexpr int kMaxPassCams = 64;
+// Passed to one small kernel by value (graph-capturable), which writes it to
+// the workspace for the kernels of the pass.
+struct PassDesc {
+    int G, ncam;
+    GroupDesc g[kMaxPassGroups];
+    CamDesc cam[kMaxPassCams];
+};
+
 // Per-plane count of frames averaged into the plane: plane p belongs to image
-// g0 + p / C, whose frame count is min(d, m - image*d).  Details are scaled by
-// 1/count (group sums are kept exact, in "sum units", through the LL chain).
+// g0 + p / C, whose frame count is min(d, m - image*d), or, in a
+// multi-camera pass, the count recorded for that group.  Details are scaled
+// by 1/count (group sums are kept exact, in "sum units", through the LL chain).
 struct PlaneScale {
     int d, m, g0, C;
+    const GroupDesc *gd;  // null: single sequence
     __device__ __forceinline__ int count(int plane) const {
+        if (gd) return gd[plane / C].n;
         int img = g0 + plane / C;
         int left = m - img * d;
         return left < d ? left : d;

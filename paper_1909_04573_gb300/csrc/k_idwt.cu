@@ -121,6 +121,42 @@ __global__ void __launch_bounds__(256) k_synthesis(SynArgs a) {
 // grid z, W stored at res_out[plane].  MLE mode: grid z is the channel and
 // the block walks the pass's G images, summing W*I and I*I in registers
 // before one read-modify-write of num/den.
+// Add a thread's 4 MLE sums (plain or float-float pairs) into num/den.
+template <bool COMP>
+__device__ __forceinline__ void mle_flush(const FinalArgs &a, float *num, float *den, float *an, float *ad,
+                                          float *anl, float *adl, int y0, int x0, int tid) {
+    const long long hw = (long long)a.H * a.W;
+    const long long chw = (long long)a.C * hw;  // offset of the low parts when COMP
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int it = tid + 256 * k;
+        const int y = it >> 4, n = it & 15;
+        const int gy = y0 + y, gx = x0 + 2 * n;
+        if (gy >= a.H || gx >= a.W) continue;
+        const long long o = (long long)blockIdx.z * hw + (long long)gy * a.W + gx;
+        const int cnt = gx + 1 < a.W ? 2 : 1;
+        for (int e = 0; e < cnt; ++e) {
+            const int j = 2 * k + e;
+            if (COMP) {
+                float h = num[o + e], l = num[chw + o + e];
+                ff_add(h, l, an[j]);
+                l = __fadd_rn(l, anl[j]);
+                num[o + e] = h;
+                num[chw + o + e] = l;
+                h = den[o + e];
+                l = den[chw + o + e];
+                ff_add(h, l, ad[j]);
+                l = __fadd_rn(l, adl[j]);
+                den[o + e] = h;
+                den[chw + o + e] = l;
+            } else {
+                num[o + e] += an[j];
+                den[o + e] += ad[j];
+            }
+        }
+    }
+}
+
 template <bool MLE, class T, bool COMP>
 __global__ void __launch_bounds__(256) k_final(FinalArgs a) {
     __shared__ SynTile s;
@@ -133,8 +169,15 @@ __global__ void __launch_bounds__(256) k_final(FinalArgs a) {
     for (int k = 0; k < 4; ++k) { an[k] = 0.f; ad[k] = 0.f; anl[k] = 0.f; adl[k] = 0.f; }
     const long long hw = (long long)a.H * a.W;
     const int nimg = MLE ? a.G : 1;
+    int cam = (MLE && a.gd) ? a.gd[0].cam : -1;  // multi-camera pass: current camera
     for (int i = 0; i < nimg; ++i) {
         const int plane = MLE ? i * a.C + (int)blockIdx.z : (int)blockIdx.z;
+        if (MLE && a.gd && a.gd[i].cam != cam) {  // block-uniform: the camera changes
+            mle_flush<COMP>(a, a.cams[cam].num, a.cams[cam].den, an, ad, anl, adl, y0, x0, tid);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) { an[k] = 0.f; ad[k] = 0.f; anl[k] = 0.f; adl[k] = 0.f; }
+            cam = a.gd[i].cam;
+        }
         const long long poff = (long long)plane * a.Rc * a.Cc;
         if (i > 0) __syncthreads();
         load_coeffs<T>(s, static_cast<const T *>(a.LL), static_cast<const T *>(a.LH), static_cast<const T *>(a.HL),
@@ -177,35 +220,10 @@ __global__ void __launch_bounds__(256) k_final(FinalArgs a) {
         }
     }
     if (MLE) {
-        const long long chw = (long long)a.C * hw;  // offset of the low parts when COMP
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int it = tid + 256 * k;
-            const int y = it >> 4, n = it & 15;
-            const int gy = y0 + y, gx = x0 + 2 * n;
-            if (gy >= a.H || gx >= a.W) continue;
-            const long long o = (long long)blockIdx.z * hw + (long long)gy * a.W + gx;
-            const int cnt = gx + 1 < a.W ? 2 : 1;
-            for (int e = 0; e < cnt; ++e) {
-                const int j = 2 * k + e;
-                if (COMP) {
-                    float h = a.num[o + e], l = a.num[chw + o + e];
-                    ff_add(h, l, an[j]);
-                    l = __fadd_rn(l, anl[j]);
-                    a.num[o + e] = h;
-                    a.num[chw + o + e] = l;
-                    h = a.den[o + e];
-                    l = a.den[chw + o + e];
-                    ff_add(h, l, ad[j]);
-                    l = __fadd_rn(l, adl[j]);
-                    a.den[o + e] = h;
-                    a.den[chw + o + e] = l;
-                } else {
-                    a.num[o + e] += an[j];
-                    a.den[o + e] += ad[j];
-                }
-            }
-        }
+        if (a.gd)
+            mle_flush<COMP>(a, a.cams[cam].num, a.cams[cam].den, an, ad, anl, adl, y0, x0, tid);
+        else
+            mle_flush<COMP>(a, a.num, a.den, an, ad, anl, adl, y0, x0, tid);
     }
 }
 

@@ -26,15 +26,13 @@ __device__ __forceinline__ void acc_word(uint32_t v, uint32_t &ev, uint32_t &od)
     od += (v >> 8) & 0x00FF00FFu;
 }
 
-template <int C, int SEGPX>
+template <int C, int SEGPX, bool MULTI>
 __global__ void __launch_bounds__(SEGPX * C / 16) k_sda_sum(SdaArgs a) {
     constexpr int NT = SEGPX * C / 16;  // threads = 16-byte chunks per segment
     __shared__ float sbuf[SEGPX * C];
     const int rowbytes = a.W * C;
     const int nseg = (a.W + SEGPX - 1) / SEGPX;
     const long long units = (long long)a.G * a.H * nseg;
-    const bool aligned16 = ((reinterpret_cast<uintptr_t>(a.frames) | (uintptr_t)a.frame_stride |
-                             (uintptr_t)a.row_pitch) & 15u) == 0;
     const long long plane = (long long)a.H * a.W;
     const int k = threadIdx.x;
     for (long long u = blockIdx.x; u < units; u += gridDim.x) {
@@ -42,9 +40,22 @@ __global__ void __launch_bounds__(SEGPX * C / 16) k_sda_sum(SdaArgs a) {
         const long long r = u / nseg;
         const int y = (int)(r % a.H);
         const int gi = (int)(r / a.H);
-        const int g = a.g0 + gi;
-        const int j0 = g * a.d;
-        const int j1 = min(a.m, j0 + a.d);
+        int j0, j1;
+        const uint8_t *fr = a.frames;
+        long long fstride = a.frame_stride, rpitch = a.row_pitch;
+        if (MULTI) {  // multi-camera pass: the group's own frames
+            const GroupDesc &gdesc = a.gd[gi];
+            fr = gdesc.frames;
+            fstride = gdesc.frame_stride;
+            rpitch = gdesc.row_pitch;
+            j0 = 0;
+            j1 = gdesc.n;
+        } else {
+            const int g = a.g0 + gi;
+            j0 = g * a.d;
+            j1 = min(a.m, j0 + a.d);
+        }
+        const bool al16 = ((reinterpret_cast<uintptr_t>(fr) | (uintptr_t)fstride | (uintptr_t)rpitch) & 15u) == 0;
         const int x0 = seg * SEGPX;
         const int npx = min(SEGPX, a.W - x0);
         const int b0 = x0 * C + 16 * k;
@@ -53,14 +64,14 @@ __global__ void __launch_bounds__(SEGPX * C / 16) k_sda_sum(SdaArgs a) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) tot[i] = 0;
         if (nb > 0) {
-            const uint8_t *base = a.frames + (long long)y * a.row_pitch + b0;
-            if (aligned16 && nb == 16) {
+            const uint8_t *base = fr + (long long)y * rpitch + b0;
+            if (al16 && nb == 16) {
                 for (int jb = j0; jb < j1; jb += 256) {
                     const int je = min(j1, jb + 256);
                     uint32_t ev[4] = {0, 0, 0, 0}, od[4] = {0, 0, 0, 0};
-                    const uint8_t *p = base + (long long)jb * a.frame_stride;
+                    const uint8_t *p = base + (long long)jb * fstride;
 #pragma unroll 4
-                    for (int j = jb; j < je; ++j, p += a.frame_stride) {
+                    for (int j = jb; j < je; ++j, p += fstride) {
                         const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(p));
                         acc_word(v.x, ev[0], od[0]);
                         acc_word(v.y, ev[1], od[1]);
@@ -77,7 +88,7 @@ __global__ void __launch_bounds__(SEGPX * C / 16) k_sda_sum(SdaArgs a) {
                 }
             } else {
                 for (int j = j0; j < j1; ++j) {
-                    const uint8_t *p = base + (long long)j * a.frame_stride;
+                    const uint8_t *p = base + (long long)j * fstride;
 #pragma unroll
                     for (int i = 0; i < 16; ++i)
                         if (i < nb) tot[i] += p[i];
@@ -101,15 +112,13 @@ __global__ void __launch_bounds__(SEGPX * C / 16) k_sda_sum(SdaArgs a) {
 
 // float16 frames: a thread owns 8 consecutive values (16 bytes) of a row
 // segment and sums them in float32 over the group's frames.
-template <int C, int SEGPX>
+template <int C, int SEGPX, bool MULTI>
 __global__ void __launch_bounds__(SEGPX * C / 8) k_sda_sum_f16(SdaArgs a) {
     constexpr int NT = SEGPX * C / 8;
     __shared__ float sbuf[SEGPX * C];
     const int rowvals = a.W * C;
     const int nseg = (a.W + SEGPX - 1) / SEGPX;
     const long long units = (long long)a.G * a.H * nseg;
-    const bool aligned16 = ((reinterpret_cast<uintptr_t>(a.frames) | (uintptr_t)a.frame_stride |
-                             (uintptr_t)a.row_pitch) & 15u) == 0;
     const long long plane = (long long)a.H * a.W;
     const int k = threadIdx.x;
     for (long long u = blockIdx.x; u < units; u += gridDim.x) {
@@ -117,9 +126,22 @@ __global__ void __launch_bounds__(SEGPX * C / 8) k_sda_sum_f16(SdaArgs a) {
         const long long r = u / nseg;
         const int y = (int)(r % a.H);
         const int gi = (int)(r / a.H);
-        const int g = a.g0 + gi;
-        const int j0 = g * a.d;
-        const int j1 = min(a.m, j0 + a.d);
+        int j0, j1;
+        const uint8_t *fr = a.frames;
+        long long fstride = a.frame_stride, rpitch = a.row_pitch;
+        if (MULTI) {
+            const GroupDesc &gdesc = a.gd[gi];
+            fr = gdesc.frames;
+            fstride = gdesc.frame_stride;
+            rpitch = gdesc.row_pitch;
+            j0 = 0;
+            j1 = gdesc.n;
+        } else {
+            const int g = a.g0 + gi;
+            j0 = g * a.d;
+            j1 = min(a.m, j0 + a.d);
+        }
+        const bool al16 = ((reinterpret_cast<uintptr_t>(fr) | (uintptr_t)fstride | (uintptr_t)rpitch) & 15u) == 0;
         const int x0 = seg * SEGPX;
         const int npx = min(SEGPX, a.W - x0);
         const int e0 = x0 * C + 8 * k;  // first value of this thread's chunk
@@ -128,11 +150,11 @@ __global__ void __launch_bounds__(SEGPX * C / 8) k_sda_sum_f16(SdaArgs a) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) tot[i] = 0.f;
         if (ne > 0) {
-            const uint8_t *base = a.frames + (long long)y * a.row_pitch + 2LL * e0;
-            if (aligned16 && ne == 8) {
+            const uint8_t *base = fr + (long long)y * rpitch + 2LL * e0;
+            if (al16 && ne == 8) {
 #pragma unroll 4
                 for (int j = j0; j < j1; ++j) {
-                    const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(base + (long long)j * a.frame_stride));
+                    const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(base + (long long)j * fstride));
                     const __half2 *h2 = reinterpret_cast<const __half2 *>(&v);
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
@@ -143,7 +165,7 @@ __global__ void __launch_bounds__(SEGPX * C / 8) k_sda_sum_f16(SdaArgs a) {
                 }
             } else {
                 for (int j = j0; j < j1; ++j) {
-                    const __half *p = reinterpret_cast<const __half *>(base + (long long)j * a.frame_stride);
+                    const __half *p = reinterpret_cast<const __half *>(base + (long long)j * fstride);
 #pragma unroll
                     for (int i = 0; i < 8; ++i)
                         if (i < ne) tot[i] += __half2float(p[i]);
@@ -162,6 +184,18 @@ __global__ void __launch_bounds__(SEGPX * C / 8) k_sda_sum_f16(SdaArgs a) {
     }
 }
 
+__global__ void k_put_desc(PassDesc pd, PassDesc *dst) {
+    // one block copies the by-value descriptor into device memory
+    const int *src = reinterpret_cast<const int *>(&pd);
+    int *out = reinterpret_cast<int *>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(PassDesc) / sizeof(int)); i += blockDim.x) out[i] = src[i];
+}
+
+cudaError_t launch_put_desc(const PassDesc &pd, PassDesc *dst, cudaStream_t st) {
+    k_put_desc<<<1, 256, 0, st>>>(pd, dst);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sda(const SdaArgs &a, int num_sms, cudaStream_t st) {
     if (a.frame_half) {
         constexpr int SEG = 1024;
@@ -169,11 +203,17 @@ cudaError_t launch_sda(const SdaArgs &a, int num_sms, cudaStream_t st) {
         if (a.C == 3) {
             constexpr int NT = SEG * 3 / 8;
             const long long blocks = std::min<long long>(units, (long long)num_sms * (2048 / NT));
-            k_sda_sum_f16<3, SEG><<<(unsigned)std::max<long long>(blocks, 1), NT, 0, st>>>(a);
+            if (a.gd)
+                k_sda_sum_f16<3, SEG, true><<<(unsigned)std::max<long long>(blocks, 1), NT, 0, st>>>(a);
+            else
+                k_sda_sum_f16<3, SEG, false><<<(unsigned)std::max<long long>(blocks, 1), NT, 0, st>>>(a);
         } else {
             constexpr int NT = SEG / 8;
             const long long blocks = std::min<long long>(units, (long long)num_sms * (2048 / NT));
-            k_sda_sum_f16<1, SEG><<<(unsigned)std::max<long long>(blocks, 1), NT, 0, st>>>(a);
+            if (a.gd)
+                k_sda_sum_f16<1, SEG, true><<<(unsigned)std::max<long long>(blocks, 1), NT, 0, st>>>(a);
+            else
+                k_sda_sum_f16<1, SEG, false><<<(unsigned)std::max<long long>(blocks, 1), NT, 0, st>>>(a);
         }
         return cudaGetLastError();
     }
@@ -181,12 +221,18 @@ cudaError_t launch_sda(const SdaArgs &a, int num_sms, cudaStream_t st) {
         constexpr int SEG = 1024, NT = SEG * 3 / 16;
         const long long units = (long long)a.G * a.H * ((a.W + SEG - 1) / SEG);
         const long long blocks = std::min<long long>(units, (long long)num_sms * (2048 / NT));
-        k_sda_sum<3, SEG><<<(unsigned)std::max<long long>(blocks, 1), NT, 0, st>>>(a);
+        if (a.gd)
+            k_sda_sum<3, SEG, true><<<(unsigned)std::max<long long>(blocks, 1), NT, 0, st>>>(a);
+        else
+            k_sda_sum<3, SEG, false><<<(unsigned)std::max<long long>(blocks, 1), NT, 0, st>>>(a);
     } else {
         constexpr int SEG = 4096, NT = SEG / 16;
         const long long units = (long long)a.G * a.H * ((a.W + SEG - 1) / SEG);
         const long long blocks = std::min<long long>(units, (long long)num_sms * (2048 / NT));
-        k_sda_sum<1, SEG><<<(unsigned)std::max<long long>(blocks, 1), NT, 0, st>>>(a);
+        if (a.gd)
+            k_sda_sum<1, SEG, true><<<(unsigned)std::max<long long>(blocks, 1), NT, 0, st>>>(a);
+        else
+            k_sda_sum<1, SEG, false><<<(unsigned)std::max<long long>(blocks, 1), NT, 0, st>>>(a);
     }
     return cudaGetLastError();
 }

@@ -16,7 +16,9 @@ struct SdaArgs {
     int g0, G;      // groups g0 .. g0+G-1 are produced, output index g - g0
     float *out;     // [G][C][H][W]
     int mean;       // 1: write sum/count (correctly rounded), 0: the exact sum
+    const GroupDesc *gd;  // multi-camera pass: per-group frames/strides/count (frames..d, g0 unused)
 };
+cudaError_t launch_put_desc(const PassDesc &pd, PassDesc *dst, cudaStream_t st);
 cudaError_t launch_sda(const SdaArgs &a, int num_sms, cudaStream_t st);
 
 // k_dwt.cu
@@ -67,6 +69,8 @@ struct FinalArgs {
     PlaneScale sc;
     float *res_out;    // residual mode: [G*C][H][W]
     float *num, *den;  // MLE mode: [C][H][W]
+    const GroupDesc *gd;    // multi-camera MLE: group -> camera (groups of a camera are consecutive)
+    const CamDesc *cams;    // multi-camera MLE: per-camera num/den
     Filt f;
 };
 cudaError_t launch_synthesis(const SynArgs &a, cudaStream_t st);

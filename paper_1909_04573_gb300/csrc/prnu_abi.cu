@@ -493,7 +493,7 @@ prnu_status accumulate_pass(prnu_ctx *ctx, const uint8_t *frames, int m, int H, 
         Launch t(ctx, "sda_sum", st, 1, fr + (double)P * H * W * 4);
         CU(launch_sda(sa, ctx->sms, st));
     }
-    const PlaneScale sc{d, m, g0, C};
+    const PlaneScale sc{d, m, g0, C, nullptr};
     FinalArgs fin{};
     fin.C = C;
     fin.G = G;
@@ -515,6 +515,64 @@ int groups_fitting(int H, int W, int C, int L, size_t bytes, int gmax, int sdt) 
             hi = mid - 1;
     }
     return lo;
+}
+
+}  // namespace
+
+namespace {
+
+// One pass over G groups of several cameras of one geometry: the group and
+// camera table goes to the device through one small kernel (by value, so the
+// sequence stays capturable in a CUDA graph), then the usual kernels run with
+// per-group frame pointers, counts and camera routing.
+prnu_status accumulate_pass_multi(prnu_ctx *ctx, const PassDesc &pd, int H, int W, int C, const prnu_params &prm,
+                                  const Win &win, char *ws, cudaStream_t st) {
+    const int G = pd.G, P = G * C;
+    const Layout lo = make_layout(H, W, P, prm.levels, true, prm.dtype);
+    PassDesc *dpd = reinterpret_cast<PassDesc *>(ws + lo.end);
+    {
+        Launch t(ctx, "put_desc", st, 1, 0.0);
+        CU(launch_put_desc(pd, dpd, st));
+    }
+    SdaArgs sa{};
+    sa.H = H;
+    sa.W = W;
+    sa.C = C;
+    sa.G = G;
+    sa.out = reinterpret_cast<float *>(ws + lo.X);
+    sa.mean = 0;
+    sa.frame_half = prm.frame_dtype == PRNU_FRAMES_F16;
+    sa.gd = dpd->g;
+    {
+        double fr = 0.0;
+        for (int i = 0; i < G; ++i) fr += (double)pd.g[i].n;
+        Launch t(ctx, "sda_sum", st, 1, fr * H * W * C * (sa.frame_half ? 2 : 1) + (double)P * H * W * 4);
+        CU(launch_sda(sa, ctx->sms, st));
+    }
+    const PlaneScale sc{1, 1, 0, C, dpd->g};
+    FinalArgs fin{};
+    fin.C = C;
+    fin.G = G;
+    fin.X = reinterpret_cast<const float *>(ws + lo.X);
+    fin.sc = sc;
+    fin.gd = dpd->g;
+    fin.cams = dpd->cam;
+    return run_denoise(ctx, reinterpret_cast<const float *>(ws + lo.X), H, W, P, prm, win, sc, 1, ws, lo, fin, true,
+                       st);
+}
+
+prnu_status check_camera(const prnu_camera &c, const prnu_params *params) {
+    prnu_status s;
+    if ((s = check_geometry(c.H, c.W, c.C)) != PRNU_OK) return s;
+    if ((s = check_params(params, c.H, c.W, nullptr)) != PRNU_OK) return s;
+    if (!c.num || !c.den) return fail(PRNU_EINVAL, "camera num/den is NULL");
+    const int fes = params->frame_dtype == PRNU_FRAMES_F16 ? 2 : 1;
+    return check_frames(c.frames, c.m, c.H, c.W, c.C, c.frame_stride, c.row_pitch, c.d, fes);
+}
+
+size_t multi_layout_bytes(int H, int W, int C, const prnu_params *p, int groups) {
+    return align_up(make_layout(H, W, (long long)groups * C, p->levels, true, p->dtype).end, kAlign) +
+           sizeof(PassDesc);
 }
 
 }  // namespace
@@ -672,7 +730,7 @@ prnu_status prnu_denoise_residual_batch(prnu_ctx *ctx, const float *img, int n, 
     fin.C = C;
     fin.G = n;
     fin.res_out = residual_out;
-    fin.sc = PlaneScale{1, 1, 0, C};
+    fin.sc = PlaneScale{1, 1, 0, C, nullptr};
     return run_denoise(ctx, img, H, W, n * C, *params, win, fin.sc, 0, static_cast<char *>(ws), lo, fin, false,
                        S(stream));
 }
@@ -959,6 +1017,91 @@ prnu_status prnu_pce_match(prnu_ctx *ctx, const float *K, const float *residual_
                            size_t ws_bytes, void *stream) {
     return prnu_pce_match_batch(ctx, K, residual_q, img_q, 1, H, W, C, nbhd, pce_out, ncc_out, peak_yx, ws,
                                 ws_bytes, stream);
+}
+
+prnu_status prnu_workspace_size_multi(prnu_ctx *ctx, const prnu_camera *cams, int ncams, const prnu_params *params,
+                                      int groups_per_pass, size_t *bytes) {
+    if (!ctx || !cams || !bytes || ncams < 1) return fail(PRNU_EINVAL, "NULL argument or ncams < 1");
+    if (groups_per_pass < 1 || groups_per_pass > kMaxPassGroups)
+        return fail(PRNU_EINVAL, "groups_per_pass must be in [1, %d]", kMaxPassGroups);
+    size_t need = 0;
+    for (int i = 0; i < ncams; ++i) {
+        prnu_status s = check_camera(cams[i], params);
+        if (s != PRNU_OK) return s;
+        need = std::max(need, multi_layout_bytes(cams[i].H, cams[i].W, cams[i].C, params, groups_per_pass));
+    }
+    *bytes = need;
+    return PRNU_OK;
+}
+
+prnu_status prnu_fingerprint_accumulate_multi(prnu_ctx *ctx, const prnu_camera *cams, int ncams,
+                                              const prnu_params *params, void *ws, size_t ws_bytes, void *stream) {
+    if (!ctx || !cams || ncams < 1) return fail(PRNU_EINVAL, "NULL argument or ncams < 1");
+    prnu_status s;
+    Win win;
+    for (int i = 0; i < ncams; ++i)
+        if ((s = check_camera(cams[i], params)) != PRNU_OK) return s;
+    if ((s = check_params(params, cams[0].H, cams[0].W, &win)) != PRNU_OK) return s;
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(PRNU_EINVAL, "workspace must be 256-byte aligned");
+    DeviceGuard gd(ctx->device);
+    cudaStream_t st = S(stream);
+    // geometry classes in order of first appearance
+    std::vector<int> done(ncams, 0);
+    for (int i0 = 0; i0 < ncams; ++i0) {
+        if (done[i0]) continue;
+        const int H = cams[i0].H, W = cams[i0].W, C = cams[i0].C;
+        std::vector<int> members;
+        for (int i = i0; i < ncams; ++i)
+            if (!done[i] && cams[i].H == H && cams[i].W == W && cams[i].C == C) {
+                members.push_back(i);
+                done[i] = 1;
+            }
+        // largest pass that fits the workspace and the descriptor table
+        int Gp = 0;
+        for (int g = kMaxPassGroups; g >= 1; g = g > 8 ? g * 3 / 4 : g - 1)
+            if (multi_layout_bytes(H, W, C, params, g) <= ws_bytes) {
+                Gp = g;
+                break;
+            }
+        if (Gp < 1) {
+            return fail(PRNU_ENOSPC, "workspace too small: need %zu bytes, got %zu",
+                        multi_layout_bytes(H, W, C, params, 1), ws_bytes);
+        }
+        // walk the groups of the class's cameras, in camera order
+        PassDesc pd;
+        pd.G = 0;
+        pd.ncam = 0;
+        auto flush = [&]() -> prnu_status {
+            if (pd.G == 0) return PRNU_OK;
+            prnu_status r = accumulate_pass_multi(ctx, pd, H, W, C, *params, win, static_cast<char *>(ws), st);
+            pd.G = 0;
+            pd.ncam = 0;
+            return r;
+        };
+        for (int ci : members) {
+            const prnu_camera &c = cams[ci];
+            const int g = (c.m + c.d - 1) / c.d;
+            for (int k = 0; k < g; ++k) {
+                if (pd.G == Gp || (pd.ncam == kMaxPassCams && (pd.ncam == 0 || pd.cam[pd.ncam - 1].num != c.num))) {
+                    if ((s = flush()) != PRNU_OK) return s;
+                }
+                if (pd.ncam == 0 || pd.cam[pd.ncam - 1].num != c.num) {
+                    pd.cam[pd.ncam].num = c.num;
+                    pd.cam[pd.ncam].den = c.den;
+                    ++pd.ncam;
+                }
+                GroupDesc &gdesc = pd.g[pd.G++];
+                const int j0 = k * c.d, j1 = std::min(c.m, j0 + c.d);
+                gdesc.frames = c.frames + (size_t)j0 * c.frame_stride;
+                gdesc.frame_stride = (long long)c.frame_stride;
+                gdesc.row_pitch = (long long)c.row_pitch;
+                gdesc.n = j1 - j0;
+                gdesc.cam = pd.ncam - 1;
+            }
+        }
+        if ((s = flush()) != PRNU_OK) return s;
+    }
+    return PRNU_OK;
 }
 
 prnu_status prnu_profile_enable(prnu_ctx *ctx, int on) {

@@ -24,6 +24,7 @@ EXPORTS = (
     "prnu_fingerprint_accumulate_host", "prnu_fingerprint_finalize", "prnu_pce_match",
     "prnu_profile_enable", "prnu_profile_reset", "prnu_profile_read", "prnu_denoise_residual_static",
     "prnu_denoise_residual_batch", "prnu_pce_match_batch", "prnu_pce_match_pairs",
+    "prnu_workspace_size_multi", "prnu_fingerprint_accumulate_multi",
 )
 
 
@@ -41,6 +42,12 @@ class prnu_params(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("sigma0", ctypes.c_float), ("n_windows", ctypes.c_int),
                 ("windows", ctypes.c_int * 4), ("pad_mode", ctypes.c_int), ("dtype", ctypes.c_int),
                 ("frame_dtype", ctypes.c_int), ("compensated", ctypes.c_int)]
+
+
+class prnu_camera(ctypes.Structure):
+    _fields_ = [("frames", ctypes.c_void_p), ("m", ctypes.c_int), ("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("C", ctypes.c_int), ("frame_stride", ctypes.c_size_t), ("row_pitch", ctypes.c_size_t),
+                ("d", ctypes.c_int), ("num", ctypes.c_void_p), ("den", ctypes.c_void_p)]
 
 
 _lib = None
@@ -79,6 +86,8 @@ def lib() -> ctypes.CDLL:
                 "prnu_pce_match_pairs": [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _vp, _sz,
                                          _vp],
+                "prnu_workspace_size_multi": [_vp, ctypes.POINTER(prnu_camera), _i, _pp, _i, ctypes.POINTER(_sz)],
+                "prnu_fingerprint_accumulate_multi": [_vp, ctypes.POINTER(prnu_camera), _i, _pp, _vp, _sz, _vp],
                 "prnu_profile_enable": [_vp, _i],
                 "prnu_profile_reset": [_vp],
                 "prnu_profile_read": [_vp, _i, ctypes.c_char_p, _sz, ctypes.POINTER(ctypes.c_longlong),
@@ -199,6 +208,20 @@ def prnu_denoise_residual_static(ctx, img, H, W, C, params, residual_out, stream
     """prnu_denoise_residual with the library's fixed static scratch: no
     workspace argument and no allocation (for callers that cannot allocate)."""
     _check(lib().prnu_denoise_residual_static(ctx, img, H, W, C, ctypes.byref(params), residual_out, stream), ctx)
+
+
+def prnu_workspace_size_multi(ctx, cams, params, groups_per_pass) -> int:
+    arr = (prnu_camera * len(cams))(*cams)
+    n = _sz()
+    _check(lib().prnu_workspace_size_multi(ctx, arr, len(cams), ctypes.byref(params), groups_per_pass,
+                                           ctypes.byref(n)), ctx)
+    return n.value
+
+
+def prnu_fingerprint_accumulate_multi(ctx, cams, params, ws, ws_bytes, stream):
+    arr = (prnu_camera * len(cams))(*cams)
+    _check(lib().prnu_fingerprint_accumulate_multi(ctx, arr, len(cams), ctypes.byref(params), ws, ws_bytes, stream),
+           ctx)
 
 
 def prnu_profile_enable(ctx, on: bool) -> None:
@@ -336,6 +359,22 @@ class Context:
         ws = self.workspace(n)
         prnu_fingerprint_accumulate_host(self.ctx, host_frames.data_ptr(), m, H, W, C, fs, rp, d, params,
                                          num.data_ptr(), den.data_ptr(), ws.data_ptr(), n, self._stream())
+
+    def cameras(self, items):
+        """[(frames [m, H, W, C] tensor, d, num, den)] -> prnu_camera structs."""
+        out = []
+        for frames, d, num, den in items:
+            frames, m, H, W, C, fs, rp = self._frames_geometry(frames)
+            out.append(prnu_camera(frames.data_ptr(), m, H, W, C, fs, rp, d, num.data_ptr(), den.data_ptr()))
+        return out
+
+    def fingerprint_accumulate_multi(self, items, params=None, groups_per_pass=64, ws_bytes=None):
+        """items: [(frames, d, num, den)] of several cameras (any geometries)."""
+        params = params or default_params(frame_dtype=PRNU_FRAMES_F16 if items[0][0].dtype.itemsize == 2 else 0)
+        cams = self.cameras(items)
+        n = ws_bytes or prnu_workspace_size_multi(self.ctx, cams, params, groups_per_pass)
+        ws = self.workspace(n)
+        prnu_fingerprint_accumulate_multi(self.ctx, cams, params, ws.data_ptr(), n, self._stream())
 
     def fingerprint_finalize(self, num, den, flags: int = 0, params=None):
         params = params or default_params()
