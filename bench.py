@@ -43,9 +43,13 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--frames", type=int, default=M_FRAMES,
                     help="frames of the workload (default 1000; smaller values are for profiling captures)")
-    ap.add_argument("--config", default="video", choices=["video", "precision", "depth"],
+    ap.add_argument("--config", default="video", choices=["video", "precision", "depth", "batch"],
                     help="video: 1000 RGB 1920x1080 frames, SDA-50 (the headline); precision: 500 RGB 4032x3024 "
-                         "frames, SDA-25, per storage type throughput and error against the FP64 oracle")
+                         "frames, SDA-25, per storage type throughput and error against the FP64 oracle; depth: "
+                         "SDA-depth study; batch: 32 cameras of mixed resolutions, frame counts and SDA groups")
+    ap.add_argument("--cameras", type=int, default=32, help="batch config: number of cameras")
+    ap.add_argument("--chunk-gb", type=float, default=96.0, help="batch config: frame buffer per chunk (GiB)")
+    ap.add_argument("--groups-per-pass", type=int, default=32, help="batch config: SDA groups per pass")
     ap.add_argument("--mode", default="weak", choices=["weak", "shard"],
                     help="weak: one camera per GPU (no exchange); shard: one camera's groups split over the GPUs, "
                          "num/den summed with one all-reduce (strong scaling)")
@@ -138,6 +142,53 @@ class Clocks:
         reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
         return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
                 "samples": len(rows)}
+
+
+def kernel_report(prof, steps, ck, dev):
+    """Per-kernel table and rooflines from the library's event profile of
+    `steps` steps: (roofline of the dominant kernel, roofline of sda_sum,
+    per-kernel table, launches of the library's own kernels)."""
+    import torch
+    own = {k: v for k, v in prof.items() if not k.startswith("cufft")}
+    launches = sum(v[0] for v in own.values())
+    total_dev = sum(v[1] for v in prof.values())
+    hbm, peak_kind = peaks()
+    kern = {}
+    for k, (n, t, nbytes) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
+        e = {"launches_per_step": n / steps, "ms_per_step": t / steps,
+             "share": t / total_dev if total_dev else None}
+        if nbytes > 0 and t > 0:
+            e["algorithmic_GBps"] = nbytes / (t / 1000.0) / 1e9
+        kern[k] = e
+    dom = max(own.items(), key=lambda kv: kv[1][1])[0]
+    dom_n, dom_t, dom_b = own[dom]
+    roof = None
+    if dom_b > 0 and dom_n > 0:
+        sec = dom_t / dom_n / 1000.0
+        gbps = (dom_b / dom_n) / sec / 1e9
+        sym = NCU_NAME.get(dom)
+        traffic = dram_traffic(sym) if sym else None
+        if dom in ALU_OPS_PER_BYTE:
+            sm_mhz = (ck or {}).get("sm_mhz") or 2070.0
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            peak_tops = sms * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+            ach = ALU_OPS_PER_BYTE[dom] * (dom_b / dom_n) / sec / 1e12
+            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak_tops, "unit": "TOP/s (FP32)",
+                    "frac": ach / peak_tops,
+                    "peak_kind": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz",
+                    "traffic": traffic, "bytes_per_launch": dom_b / dom_n, "launches": dom_n,
+                    "ms_per_launch": dom_t / dom_n, "hbm_achieved_GBps": gbps, "hbm_frac": gbps / hbm}
+        else:
+            roof = {"kernel": dom, "bound": "hbm", "achieved": gbps, "peak": hbm, "unit": "GB/s",
+                    "frac": gbps / hbm, "peak_kind": f"{peak_kind} copy bandwidth", "traffic": traffic,
+                    "bytes_per_launch": dom_b / dom_n, "launches": dom_n, "ms_per_launch": dom_t / dom_n}
+    sda_roof = None
+    if "sda_sum" in own and own["sda_sum"][1] > 0:
+        n_, t_, b_ = own["sda_sum"]
+        g_ = (b_ / n_) / (t_ / n_ / 1000.0) / 1e9
+        sda_roof = {"kernel": "sda_sum", "bound": "hbm", "achieved": g_, "peak": hbm, "unit": "GB/s",
+                    "frac": g_ / hbm, "traffic": dram_traffic(NCU_NAME["sda_sum"]), "bytes_per_launch": b_ / n_}
+    return roof, sda_roof, kern, launches
 
 
 # ------------------------------------------------------------- CPU oracle --
@@ -340,6 +391,183 @@ def depth_config(args, rank, world, local):
     ctx.close()
 
 
+# ------------------------------------------------------ multi-camera batch --
+def batch_config(args, rank, world, local):
+    """32 synthetic cameras (own K each) with frame counts uniform in
+    100..2000, resolutions from {1280x720, 1920x1080, 4032x3024} RGB and SDA
+    group sizes uniform in 10..100 (ragged last groups): 32,282 frames, 453 GB.
+    The frames do not fit in HBM, so they are produced chunk by chunk into one
+    reusable buffer (generation is outside the timed region); each chunk is one
+    multi-camera accumulate call, captured once in a CUDA graph and replayed.
+    Then the 32 fingerprints are finalised (grey, zero-mean, DFT Wiener) and
+    matched in a 32 x 32 PCE matrix on the common top-left 1280 x 720 window
+    (one query frame per camera).  Every rank runs the whole batch (weak)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_1909_04573_gb300 import batch as B
+    from paper_1909_04573_gb300 import prnu as P
+    from paper_1909_04573_gb300 import synth
+
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    dev = torch.device("cuda", local)
+    ctx = P.Context(local)
+    specs = synth.batch_cameras(args.cameras)
+    ncam = len(specs)
+    budget = int(args.chunk_gb * (1 << 30))
+    fbytes = [c.H * c.W * c.C for c, _, _ in specs]
+    chunks = B.plan_chunks([(fb, m, d) for fb, (_, m, d) in zip(fbytes, specs)], budget)
+    total_frames = sum(m for _, m, _ in specs)
+    total_bytes = sum(fb * m for fb, (_, m, _) in zip(fbytes, specs))
+    buf = torch.empty(max(B._align(p.offset + (p.f1 - p.f0) * fbytes[p.cam]) for ch in chunks for p in ch),
+                      dtype=torch.uint8, device=dev)
+    nums = [torch.zeros((c.C, c.H, c.W), device=dev) for c, _, _ in specs]
+    dens = [torch.zeros_like(n) for n in nums]
+    prm = P.default_params()
+    gpp = args.groups_per_pass
+
+    def items_of(ch):
+        out = []
+        for p in ch:
+            c, _, d = specs[p.cam]
+            n = p.f1 - p.f0
+            v = buf[p.offset: p.offset + n * fbytes[p.cam]].view(n, c.H, c.W, c.C)
+            out.append((v, d, nums[p.cam], dens[p.cam]))
+        return out
+
+    chunk_items = [items_of(ch) for ch in chunks]
+    chunk_cams = [ctx.cameras(it) for it in chunk_items]
+    # queries: one frame per camera, cropped to the common top-left window
+    Hq, Wq = min(c.H for c, _, _ in specs), min(c.W for c, _, _ in specs)
+    qimg = torch.empty((ncam, 3, Hq, Wq), device=dev)
+    for i, (c, _, _) in enumerate(specs):
+        q = ctx.sda_average(synth.frames_fast(c, 1, stream=1, device=dev), 1)
+        qimg[i].copy_(q[0, :, :Hq, :Wq])
+    wq = torch.empty_like(qimg)
+    Kc = torch.empty((ncam, Hq, Wq), device=dev)
+    flags = P.PRNU_TO_GRAY | P.PRNU_ZERO_MEAN | P.PRNU_WIENER_DFT
+    # autotuned level-1 analysis shapes, one per geometry (outside the timed region)
+    tuned = {}
+    for geo in sorted({(c.H, c.W) for c, _, _ in specs}):
+        shape, t = ctx.autotune(geo[0], geo[1], 3, prm, images=8)
+        tuned[f"{geo[1]}x{geo[0]}"] = {"strip_rows": shape[0], "warps": shape[1], "ms": t}
+    need = max(P.prnu_workspace_size_multi(ctx.ctx, cc, prm, gpp) for cc in chunk_cams)
+    for c, _, _ in specs:
+        need = max(need, P.prnu_workspace_size(ctx.ctx, c.H, c.W, c.C, prm, 1))
+    need = max(need, P.prnu_workspace_size(ctx.ctx, Hq, Wq, 3, prm, ncam))
+    ws = ctx.workspace(need)
+    gen_s = [0.0]
+
+    def generate(ci):
+        t0 = time.perf_counter()
+        for p, it in zip(chunks[ci], chunk_items[ci]):
+            synth.frames_fast(specs[p.cam][0], p.f1 - p.f0, device=dev, out=it[0], start=p.f0)
+        torch.cuda.synchronize()
+        gen_s[0] += time.perf_counter() - t0
+
+    def accumulate(ci):
+        P.prnu_fingerprint_accumulate_multi(ctx.ctx, chunk_cams[ci], prm, ws.data_ptr(), ws.numel(),
+                                            ctx._stream())
+
+    pce = np.zeros((ncam, ncam))
+
+    def tail():
+        for i, (c, _, _) in enumerate(specs):
+            K = ctx.fingerprint_finalize(nums[i], dens[i], flags)
+            Kc[i].copy_(K[0, :Hq, :Wq])
+        ctx.denoise_residual_batch(qimg, out=wq)
+        for i in range(ncam):
+            pce[i] = [r[0] for r in ctx.pce_match_batch(Kc[i], wq, qimg)]
+
+    graphs = [None] * len(chunks)
+
+    def run_step(use_graphs, times):
+        for n_, d_ in zip(nums, dens):
+            n_.zero_()
+            d_.zero_()
+        for ci in range(len(chunks)):
+            generate(ci)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            if use_graphs:
+                graphs[ci].replay()
+            else:
+                accumulate(ci)
+            e1.record()
+            times.append((e0, e1))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        tail()
+        e1.record()
+        times.append((e0, e1))
+
+    # warm-up 1 (eager, also creates the cuFFT plans), then capture one graph per chunk
+    run_step(False, [])
+    side = torch.cuda.Stream()
+    for ci in range(len(chunks)):
+        g = torch.cuda.CUDAGraph()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g, stream=side):
+                P.prnu_fingerprint_accumulate_multi(ctx.ctx, chunk_cams[ci], prm, ws.data_ptr(), ws.numel(),
+                                                    side.cuda_stream)
+        torch.cuda.current_stream().wait_stream(side)
+        graphs[ci] = g
+    for _ in range(max(0, args.warmup - 1)):
+        run_step(True, [])
+    # per-kernel profile of one eager step (the graphs replay the same launches)
+    P.prnu_profile_reset(ctx.ctx)
+    P.prnu_profile_enable(ctx.ctx, True)
+    run_step(False, [])
+    torch.cuda.synchronize()
+    P.prnu_profile_enable(ctx.ctx, False)
+    prof = P.prnu_profile_read(ctx.ctx)
+    P.prnu_profile_reset(ctx.ctx)
+    # timed steps: graph replays; only the device time between generation gaps counts
+    gen_s[0] = 0.0
+    clocks = Clocks(local)
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        run_step(True, times)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in times)
+    tail_ms = sum(times[i][0].elapsed_time(times[i][1]) for i in range(len(chunks), len(times), len(chunks) + 1))
+    ms = total_ms / args.steps
+    roof, sda_roof, kern, launches = kernel_report(prof, 1, ck, dev)
+    hbm, _ = peaks()
+    diag = np.diag(pce)
+    off = pce[~np.eye(ncam, dtype=bool)]
+    res = sorted({(c.W, c.H) for c, _, _ in specs})
+    line = {"metric": "multi-camera batch: frames/sec into 32 fingerprints + 32x32 PCE matrix",
+            "value": world * total_frames / (ms / 1000.0), "unit": "frames/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded sensor model, whole-pixel drift; VISION/NYUAD-MMD absent)",
+            "config": {"workload": f"batch-{ncam}cam-{total_frames}f", "cameras": ncam, "frames": total_frames,
+                       "frame_GB": total_bytes / 1e9, "resolutions": [f"{w}x{h}" for w, h in res],
+                       "chunks": len(chunks), "chunk_GB": args.chunk_gb, "groups_per_pass": gpp,
+                       "groups": sum((m + d - 1) // d for _, m, d in specs), "cuda_graphs": len(chunks),
+                       "pce_window": f"{Wq}x{Hq}", "parallelism": f"whole batch per GPU x {world}",
+                       "l2": "inputs 453 GB > 129 MB L2 (no flush)"},
+            "tail_ms_per_step": tail_ms / args.steps, "generation_s_per_step_untimed": gen_s[0] / args.steps,
+            "frame_GBps": total_bytes / (ms / 1000.0) / 1e9,
+            "frame_frac_of_peak": total_bytes / (ms / 1000.0) / 1e9 / hbm,
+            "autotune": tuned, "roofline": roof, "roofline_sda_sum": sda_roof, "gpu_launches": int(launches),
+            "kernels": kern,
+            "pce_matrix": {"diag_min": float(diag.min()), "diag_median": float(np.median(diag)),
+                           "offdiag_max": float(off.max()), "offdiag_max_abs": float(np.abs(off).max()),
+                           "diag_above_60": int((diag > 60).sum()), "offdiag_above_60": int((off > 60).sum())}}
+    if ck:
+        line["clocks"] = ck
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 # --------------------------------------------------------------- GPU arm ---
 def main():
     args = parse()
@@ -354,6 +582,9 @@ def main():
         return
     if args.config == "depth":
         depth_config(args, rank, world, local)
+        return
+    if args.config == "batch":
+        batch_config(args, rank, world, local)
         return
 
     import numpy as np
@@ -423,6 +654,11 @@ def main():
             dist.barrier()
         return ms
 
+    # ---- level-1 analysis launch shape for this geometry (outside the timed region)
+    g_pass = (m_frames + D_SDA - 1) // D_SDA
+    shape, t_shape = ctx.autotune(H, W, C, images=min(g_pass, 20))
+    tuned = {f"{W}x{H}": {"strip_rows": shape[0], "warps": shape[1], "ms": t_shape}}
+
     # ---- SDA path, timed with per-kernel events on the launch stream
     for _ in range(args.warmup):
         step()
@@ -445,47 +681,8 @@ def main():
     pos = [p for p in pces[:N_QUERY]]
     neg = [p for p in pces[N_QUERY:]]
 
-    own = {k: v for k, v in prof.items() if not k.startswith("cufft")}
-    launches = sum(v[0] for v in own.values())
-    total_dev = sum(v[1] for v in prof.values())
-    hbm, peak_kind = peaks()
-    kern = {}
-    for k, (n, t, nbytes) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
-        e = {"launches_per_step": n / args.steps, "ms_per_step": t / args.steps,
-             "share": t / total_dev if total_dev else None}
-        if nbytes > 0 and t > 0:
-            e["algorithmic_GBps"] = nbytes / (t / 1000.0) / 1e9
-        kern[k] = e
-    dom = max(own.items(), key=lambda kv: kv[1][1])[0]
-    dom_n, dom_t, dom_b = own[dom]
-    roof = None
-    if dom_b > 0 and dom_n > 0:
-        sec = dom_t / dom_n / 1000.0
-        gbps = (dom_b / dom_n) / sec / 1e9
-        sym = NCU_NAME.get(dom)
-        traffic = dram_traffic(sym) if sym else None
-        if dom in ALU_OPS_PER_BYTE:
-            sm_mhz = (ck or {}).get("sm_mhz") or 2070.0
-            sms = torch.cuda.get_device_properties(dev).multi_processor_count
-            peak_tops = sms * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
-            ach = ALU_OPS_PER_BYTE[dom] * (dom_b / dom_n) / sec / 1e12
-            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak_tops, "unit": "TOP/s (FP32)",
-                    "frac": ach / peak_tops,
-                    "peak_kind": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz",
-                    "traffic": traffic, "bytes_per_launch": dom_b / dom_n, "launches": dom_n,
-                    "ms_per_launch": dom_t / dom_n, "hbm_achieved_GBps": gbps, "hbm_frac": gbps / hbm}
-        else:
-            roof = {"kernel": dom, "bound": "hbm", "achieved": gbps, "peak": hbm, "unit": "GB/s",
-                    "frac": gbps / hbm, "peak_kind": f"{peak_kind} copy bandwidth", "traffic": traffic,
-                    "bytes_per_launch": dom_b / dom_n, "launches": dom_n, "ms_per_launch": dom_t / dom_n}
-    # the HBM-bound streaming kernel of the path, for reference
-    if "sda_sum" in own and own["sda_sum"][1] > 0:
-        n_, t_, b_ = own["sda_sum"]
-        g_ = (b_ / n_) / (t_ / n_ / 1000.0) / 1e9
-        sda_roof = {"kernel": "sda_sum", "bound": "hbm", "achieved": g_, "peak": hbm, "unit": "GB/s",
-                    "frac": g_ / hbm, "traffic": dram_traffic(NCU_NAME["sda_sum"]), "bytes_per_launch": b_ / n_}
-    else:
-        sda_roof = None
+    roof, sda_roof, kern, launches = kernel_report(prof, args.steps, ck, dev)
+    hbm, _ = peaks()
     step_bytes = m_frames * H * W * C
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -500,6 +697,7 @@ def main():
             "frame_GBps": step_bytes / (ms / 1000.0) / 1e9,
             "frame_frac_of_peak": step_bytes / (ms / 1000.0) / 1e9 / hbm,
             "roofline": roof, "roofline_sda_sum": sda_roof, "gpu_launches": int(launches), "kernels": kern,
+            "autotune": tuned,
             "pce": {"same_camera_min": min(pos), "foreign_max_abs": max(abs(x) for x in neg)}}
     if ck:
         line["clocks"] = ck

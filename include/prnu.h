@@ -249,6 +249,23 @@ prnu_status prnu_pce_match_pairs(prnu_ctx *ctx, const float *K, const float *res
                                  int H, int W, int C, int nbhd, double *pce_out, double *ncc_out, int *peak_yx,
                                  void *ws, size_t ws_bytes, void *stream);
 
+/* Autotuner (not part of the paper's method): times every launch shape
+ * (strip rows x warps per block) of the level-1 analysis kernel on `images`
+ * images of this geometry and storage type, in the workspace (which must hold
+ * prnu_workspace_size(..., images) bytes; its contents are overwritten), and
+ * keeps the fastest in the context for all later calls with that geometry.
+ * All shapes compute the same results.  Synchronises `stream` (not
+ * capturable).  shape_out / ms_out (nullable, host) receive the chosen shape
+ * index and its time per launch. */
+prnu_status prnu_autotune(prnu_ctx *ctx, int H, int W, int C, const prnu_params *params, int images, void *ws,
+                          size_t ws_bytes, void *stream, int *shape_out, float *ms_out);
+
+/* Pins the level-1 analysis launch shape (index into the tuner's list:
+ * 0..5 = 16x4, 32x4, 64x4, 32x2, 32x8, 64x2 strip rows x warps) for this
+ * padded geometry and storage type, or with shape = -1 returns it to the
+ * default (32x4).  Host only; EINVAL for an index out of range. */
+prnu_status prnu_autotune_set(prnu_ctx *ctx, int H, int W, const prnu_params *params, int shape);
+
 /* Per-kernel profiling (not part of the paper's method).  Every kernel launch
  * is counted per kernel name.  With profiling on, each launch (and each cuFFT
  * call, named cufft_*) is also bracketed by CUDA events recorded on its

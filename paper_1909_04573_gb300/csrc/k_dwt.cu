@@ -36,8 +36,9 @@ constexpr float kSqrt2f = 1.41421356237309504880f;
 // body of 4 output rows uses fixed slots.  Inputs come from global memory
 // through L1 (interior warps read four float2 per row and part); no shared
 // memory and no barriers.
-constexpr int SP = 32;        // output rows per strip (multiple of 4)
-constexpr int WARPS = 4;      // warps per block, side by side in q
+// Launch shapes (output rows per strip SP, a multiple of 4, and warps per
+// block side by side in q) are template parameters; prnu_autotune picks one
+// per geometry among kStreamShapes.
 
 struct RowIn {
     const float *h, *l;       // row base of the high / low parts (l unused at level 1)
@@ -92,8 +93,8 @@ __device__ __forceinline__ void row_item(const AnaArgs &a, const RowIn &row, con
     t = tt;
 }
 
-template <bool LEVEL1, class T>
-__global__ void __launch_bounds__(32 * WARPS, 6) k_analysis_stream(AnaArgs a) {
+template <bool LEVEL1, class T, int SP, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS, 24 / WARPS) k_analysis_stream(AnaArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int plane = blockIdx.z;
     const int R2 = a.R >> 1, C2 = a.Cc >> 1;
@@ -309,13 +310,25 @@ __global__ void __launch_bounds__(256) k_analysis(AnaArgs a) {
     }
 }
 
+template <class T, int SP, int WARPS>
+static void launch_stream(const AnaArgs &a, cudaStream_t st) {
+    dim3 block(32 * WARPS);
+    dim3 grid((unsigned)((a.Cc / 2 + 32 * WARPS - 1) / (32 * WARPS)), (unsigned)((a.R / 2 + SP - 1) / SP),
+              (unsigned)a.P);
+    k_analysis_stream<true, T, SP, WARPS><<<grid, block, 0, st>>>(a);
+}
+
 template <class T>
-static void launch_analysis_t(const AnaArgs &a, bool level1, cudaStream_t st) {
+static void launch_analysis_t(const AnaArgs &a, bool level1, int shape, cudaStream_t st) {
     if (level1) {
-        dim3 block(32 * WARPS);
-        dim3 grid((unsigned)((a.Cc / 2 + 32 * WARPS - 1) / (32 * WARPS)), (unsigned)((a.R / 2 + SP - 1) / SP),
-                  (unsigned)a.P);
-        k_analysis_stream<true, T><<<grid, block, 0, st>>>(a);
+        switch (shape) {
+            case 0: launch_stream<T, 16, 4>(a, st); break;
+            case 2: launch_stream<T, 64, 4>(a, st); break;
+            case 3: launch_stream<T, 32, 2>(a, st); break;
+            case 4: launch_stream<T, 32, 8>(a, st); break;
+            case 5: launch_stream<T, 64, 2>(a, st); break;
+            default: launch_stream<T, 32, 4>(a, st); break;
+        }
     } else {
         dim3 block(32, 8);
         dim3 grid((unsigned)((a.Cc / 2 + TQ - 1) / TQ), (unsigned)((a.R / 2 + TP - 1) / TP), (unsigned)a.P);
@@ -323,13 +336,13 @@ static void launch_analysis_t(const AnaArgs &a, bool level1, cudaStream_t st) {
     }
 }
 
-cudaError_t launch_analysis(const AnaArgs &a, bool level1, cudaStream_t st) {
+cudaError_t launch_analysis(const AnaArgs &a, bool level1, cudaStream_t st, int shape) {
     if (a.sdt == SB_F16)
-        launch_analysis_t<__half>(a, level1, st);
+        launch_analysis_t<__half>(a, level1, shape, st);
     else if (a.sdt == SB_BF16)
-        launch_analysis_t<__nv_bfloat16>(a, level1, st);
+        launch_analysis_t<__nv_bfloat16>(a, level1, shape, st);
     else
-        launch_analysis_t<float>(a, level1, st);
+        launch_analysis_t<float>(a, level1, shape, st);
     return cudaGetLastError();
 }
 

@@ -35,7 +35,11 @@ struct AnaArgs {
     int scale_on;
     Filt f;
 };
-cudaError_t launch_analysis(const AnaArgs &a, bool level1, cudaStream_t st);
+// level-1 launch shapes (strip rows x warps per block) of the autotuner
+constexpr int kStreamShapes = 6;
+constexpr int kStreamShapeDefault = 1;  // 32 rows x 4 warps
+constexpr int kStreamShapeDims[kStreamShapes][2] = {{16, 4}, {32, 4}, {64, 4}, {32, 2}, {32, 8}, {64, 2}};
+cudaError_t launch_analysis(const AnaArgs &a, bool level1, cudaStream_t st, int shape = kStreamShapeDefault);
 
 // k_shrink.cu
 struct ShrinkArgs {

@@ -37,6 +37,8 @@ struct prnu_ctx {
     };
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> pool;
+    // autotuned level-1 analysis shape per (padded H, padded W, subband type)
+    std::map<std::tuple<int, int, int>, int> tuned;
 };
 
 namespace {
@@ -308,7 +310,13 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
             const double in_b = l == 1 ? (double)P * H * W * 4 : (double)P * a.R * a.Cc * 8;
             const double out_b = (double)P * A * (3.0 * es + (l < L ? 8 : 0));
             Launch t(ctx, l == 1 ? "analysis_l1" : "analysis", st, 1, in_b + out_b);
-            CU(launch_analysis(a, l == 1, st));
+            int shape = kStreamShapeDefault;
+            if (l == 1) {
+                std::lock_guard<std::mutex> lk(ctx->mu);
+                auto it = ctx->tuned.find(std::make_tuple(Hp, Wp, sdt));
+                if (it != ctx->tuned.end()) shape = it->second;
+            }
+            CU(launch_analysis(a, l == 1, st, shape));
         }
         ShrinkArgs s{};
         s.in = SB(lo.D[l], A, 0);
@@ -1101,6 +1109,85 @@ prnu_status prnu_fingerprint_accumulate_multi(prnu_ctx *ctx, const prnu_camera *
         }
         if ((s = flush()) != PRNU_OK) return s;
     }
+    return PRNU_OK;
+}
+
+prnu_status prnu_autotune(prnu_ctx *ctx, int H, int W, int C, const prnu_params *params, int images, void *ws,
+                          size_t ws_bytes, void *stream, int *shape_out, float *ms_out) {
+    if (!ctx) return fail(PRNU_EINVAL, "ctx is NULL");
+    prnu_status s;
+    if ((s = check_geometry(H, W, C)) != PRNU_OK) return s;
+    if ((s = check_params(params, H, W, nullptr)) != PRNU_OK) return s;
+    if (images < 1) return fail(PRNU_EINVAL, "images must be >= 1");
+    const int P = images * C;
+    const Layout lo = make_layout(H, W, P, params->levels, true, params->dtype);
+    if ((s = check_ws(ws, ws_bytes, lo.end)) != PRNU_OK) return s;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = S(stream);
+    char *b = static_cast<char *>(ws);
+    const int L = params->levels, Hp = padded(H, L), Wp = padded(W, L);
+    const long long A = (long long)(Hp >> 1) * (Wp >> 1);
+    const size_t es = subband_bytes(params->dtype);
+    CU(cudaMemsetAsync(b + lo.X, 0, (size_t)P * H * W * sizeof(float), st));
+    AnaArgs a{};
+    a.inh = reinterpret_cast<const float *>(b + lo.X);
+    a.R = Hp;
+    a.Cc = Wp;
+    a.H = H;
+    a.W = W;
+    a.P = P;
+    a.LLh = L > 1 ? reinterpret_cast<float *>(b + lo.LLh[1]) : nullptr;
+    a.LLl = L > 1 ? reinterpret_cast<float *>(b + lo.LLl[1]) : nullptr;
+    a.LH = b + lo.D[1];
+    a.HL = b + lo.D[1] + (size_t)P * A * es;
+    a.HH = b + lo.D[1] + 2 * (size_t)P * A * es;
+    a.sdt = params->dtype;
+    a.sc = PlaneScale{1, 1, 0, C, nullptr};
+    a.scale_on = 0;
+    a.f = ctx->filt;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    int best = kStreamShapeDefault;
+    float best_ms = 1e30f;
+    for (int shape = 0; shape < kStreamShapes; ++shape) {
+        CU(launch_analysis(a, true, st, shape));  // warm
+        CU(cudaEventRecord(e0, st));
+        for (int r = 0; r < 3; ++r) CU(launch_analysis(a, true, st, shape));
+        CU(cudaEventRecord(e1, st));
+        CU(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, e0, e1));
+        ms /= 3.f;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = shape;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->tuned[std::make_tuple(Hp, Wp, (int)params->dtype)] = best;
+    }
+    if (shape_out) *shape_out = best;
+    if (ms_out) *ms_out = best_ms;
+    return PRNU_OK;
+}
+
+prnu_status prnu_autotune_set(prnu_ctx *ctx, int H, int W, const prnu_params *params, int shape) {
+    if (!ctx) return fail(PRNU_EINVAL, "ctx is NULL");
+    prnu_status s;
+    if ((s = check_geometry(H, W, 1)) != PRNU_OK) return s;
+    if ((s = check_params(params, H, W, nullptr)) != PRNU_OK) return s;
+    if (shape < -1 || shape >= kStreamShapes) return fail(PRNU_EINVAL, "shape must be in [-1, %d)", kStreamShapes);
+    const int L = params->levels;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    const auto key = std::make_tuple(padded(H, L), padded(W, L), (int)params->dtype);
+    if (shape < 0)
+        ctx->tuned.erase(key);
+    else
+        ctx->tuned[key] = shape;
     return PRNU_OK;
 }
 

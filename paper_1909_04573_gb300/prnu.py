@@ -24,7 +24,8 @@ EXPORTS = (
     "prnu_fingerprint_accumulate_host", "prnu_fingerprint_finalize", "prnu_pce_match",
     "prnu_profile_enable", "prnu_profile_reset", "prnu_profile_read", "prnu_denoise_residual_static",
     "prnu_denoise_residual_batch", "prnu_pce_match_batch", "prnu_pce_match_pairs",
-    "prnu_workspace_size_multi", "prnu_fingerprint_accumulate_multi",
+    "prnu_workspace_size_multi", "prnu_fingerprint_accumulate_multi", "prnu_autotune",
+    "prnu_autotune_set",
 )
 
 
@@ -88,6 +89,9 @@ def lib() -> ctypes.CDLL:
                                          _vp],
                 "prnu_workspace_size_multi": [_vp, ctypes.POINTER(prnu_camera), _i, _pp, _i, ctypes.POINTER(_sz)],
                 "prnu_fingerprint_accumulate_multi": [_vp, ctypes.POINTER(prnu_camera), _i, _pp, _vp, _sz, _vp],
+                "prnu_autotune": [_vp, _i, _i, _i, _pp, _i, _vp, _sz, _vp, ctypes.POINTER(_i),
+                                  ctypes.POINTER(ctypes.c_float)],
+                "prnu_autotune_set": [_vp, _i, _i, _pp, _i],
                 "prnu_profile_enable": [_vp, _i],
                 "prnu_profile_reset": [_vp],
                 "prnu_profile_read": [_vp, _i, ctypes.c_char_p, _sz, ctypes.POINTER(ctypes.c_longlong),
@@ -222,6 +226,16 @@ def prnu_fingerprint_accumulate_multi(ctx, cams, params, ws, ws_bytes, stream):
     arr = (prnu_camera * len(cams))(*cams)
     _check(lib().prnu_fingerprint_accumulate_multi(ctx, arr, len(cams), ctypes.byref(params), ws, ws_bytes, stream),
            ctx)
+
+
+STREAM_SHAPES = [(16, 4), (32, 4), (64, 4), (32, 2), (32, 8), (64, 2)]  # (strip rows, warps per block)
+
+
+def prnu_autotune(ctx, H, W, C, params, images, ws, ws_bytes, stream):
+    shape, ms = _i(), ctypes.c_float()
+    _check(lib().prnu_autotune(ctx, H, W, C, ctypes.byref(params), images, ws, ws_bytes, stream, ctypes.byref(shape),
+                               ctypes.byref(ms)), ctx)
+    return shape.value, ms.value
 
 
 def prnu_profile_enable(ctx, on: bool) -> None:
@@ -359,6 +373,19 @@ class Context:
         ws = self.workspace(n)
         prnu_fingerprint_accumulate_host(self.ctx, host_frames.data_ptr(), m, H, W, C, fs, rp, d, params,
                                          num.data_ptr(), den.data_ptr(), ws.data_ptr(), n, self._stream())
+
+    def autotune(self, H, W, C, params=None, images=4):
+        """Pick the level-1 analysis launch shape for this geometry; returns
+        ((strip rows, warps), ms per launch)."""
+        params = params or default_params()
+        n = prnu_workspace_size(self.ctx, H, W, C, params, images)
+        ws = self.workspace(n)
+        shape, ms = prnu_autotune(self.ctx, H, W, C, params, images, ws.data_ptr(), n, self._stream())
+        return STREAM_SHAPES[shape], ms
+
+    def autotune_set(self, H, W, shape, params=None):
+        """Pin the level-1 analysis shape (index into STREAM_SHAPES; -1 = default)."""
+        _check(lib().prnu_autotune_set(self.ctx, H, W, ctypes.byref(params or default_params()), shape), self.ctx)
 
     def cameras(self, items):
         """[(frames [m, H, W, C] tensor, d, num, den)] -> prnu_camera structs."""

@@ -122,3 +122,53 @@ def foreign(cam: Camera, offset: int = 1000) -> Camera:
     return Camera(H=cam.H, W=cam.W, C=cam.C, camera_id=cam.camera_id + offset, k_std=cam.k_std,
                   scene_sigma=cam.scene_sigma, scene_mean=cam.scene_mean, scene_std=cam.scene_std,
                   sigma_read=cam.sigma_read)
+
+
+def frames_fast(cam: Camera, m: int, stream: int = 0, device="cpu", drift_px: int = 2,
+                out: torch.Tensor | None = None, start: int = 0) -> torch.Tensor:
+    """m uint8 frames [m, H, W, C] for large batches: the same sensor model as
+    ``frames`` with a drifting scene, but the drift is a random walk of whole
+    pixels (steps uniform in {-drift_px .. drift_px} per axis), so a frame's
+    scene is an index roll of the camera's base scene instead of a Fourier
+    shift, and the read noise is drawn in float32.  Frames start..start+m-1 of
+    the stream; each frame's noise comes from its own seeded generator, so
+    chunked generation gives the same bytes."""
+    H, W, C = cam.H, cam.W, cam.C
+    if out is None:
+        out = torch.empty((m, H, W, C), dtype=torch.uint8, device=device)
+    gain = 1.0 + k_true(cam, device)                                  # [C, H, W] float32
+    gb = _gen(device, 7, cam.camera_id, stream)
+    base = torch.stack([torch.fft.irfft2(_lowpass_spectrum(cam, gb, device), s=(H, W)) for _ in range(C)])
+    base = base.to(torch.float32)
+    steps = torch.randint(-drift_px, drift_px + 1, (start + m, 2), generator=_gen("cpu", 8, cam.camera_id, stream))
+    offsets = torch.cumsum(steps, dim=0)
+    for j in range(m):
+        idx = start + j
+        v = torch.randn((C, H, W), generator=_gen(device, 9, cam.camera_id, stream, idx), device=device,
+                        dtype=torch.float32)
+        v.mul_(cam.sigma_read)
+        v.addcmul_(torch.roll(base, shifts=(int(offsets[idx, 0]), int(offsets[idx, 1])), dims=(1, 2)), gain)
+        v.round_().clamp_(0, 255)
+        out[j].copy_(v.permute(1, 2, 0))
+    return out
+
+
+BATCH_RESOLUTIONS = ((720, 1280), (1080, 1920), (3024, 4032))
+
+
+def batch_cameras(n: int = 32, seed: int = 2, m_range=(100, 2000), d_range=(10, 100),
+                  resolutions=BATCH_RESOLUTIONS, C: int = 3):
+    """A seeded multi-camera workload: n cameras (camera_id 2000 + i, each with
+    its own K), each with a resolution drawn from ``resolutions``, a frame
+    count uniform in m_range and an SDA group size uniform in d_range (both
+    inclusive).  Returns [(Camera, m, d)]."""
+    g = torch.Generator()
+    g.manual_seed(BASE_SEED + seed)
+    out = []
+    for i in range(n):
+        r = int(torch.randint(len(resolutions), (1,), generator=g))
+        m = int(torch.randint(m_range[0], m_range[1] + 1, (1,), generator=g))
+        d = int(torch.randint(d_range[0], d_range[1] + 1, (1,), generator=g))
+        H, W = resolutions[r]
+        out.append((Camera(H=H, W=W, C=C, camera_id=2000 + i), m, d))
+    return out

@@ -1,0 +1,58 @@
+"""Level-1 analysis launch shapes: every shape the tuner may pick gives
+bit-identical results, and the tuner's choice is cached and used (GPU)."""
+import pytest
+import torch
+
+from paper_1909_04573_gb300 import prnu as P
+from paper_1909_04573_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_04573_gb300 import build
+    build.build()
+    c = P.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("H,W,C,dtype", [(200, 328, 3, P.PRNU_DTYPE_F32), (1080, 1920, 3, P.PRNU_DTYPE_F32),
+                                         (97, 250, 1, P.PRNU_DTYPE_F16), (256, 256, 1, P.PRNU_DTYPE_BF16)])
+def test_every_shape_gives_identical_residuals(ctx, H, W, C, dtype):
+    prm = P.default_params(dtype=dtype)
+    img = ctx.sda_average(synth.frames(synth.Camera(H=H, W=W, C=C, camera_id=41), 3, device="cuda"), 3)[0]
+    ctx.autotune_set(H, W, -1, prm)
+    ref = ctx.denoise_residual(img, params=prm).clone()
+    for s in range(len(P.STREAM_SHAPES)):
+        ctx.autotune_set(H, W, s, prm)
+        out = ctx.denoise_residual(img, params=prm)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref), f"shape {P.STREAM_SHAPES[s]}"
+    ctx.autotune_set(H, W, -1, prm)
+
+
+def test_tuner_picks_a_shape_and_keeps_results(ctx):
+    H, W, C = 1080, 1920, 3
+    fr = synth.frames(synth.Camera(H=H, W=W, C=C, camera_id=42), 20, device="cuda")
+    num0, den0 = torch.zeros((C, H, W), device="cuda"), torch.zeros((C, H, W), device="cuda")
+    ctx.autotune_set(H, W, -1)
+    ctx.fingerprint_accumulate(fr, 5, num0, den0)
+    shape, ms = ctx.autotune(H, W, C, images=4)
+    assert shape in P.STREAM_SHAPES and 0 < ms < 100
+    num1, den1 = torch.zeros_like(num0), torch.zeros_like(den0)
+    ctx.fingerprint_accumulate(fr, 5, num1, den1)
+    torch.cuda.synchronize()
+    assert torch.equal(num0, num1) and torch.equal(den0, den1)
+    ctx.autotune_set(H, W, -1)
+
+
+def test_invalid_shape_is_rejected(ctx):
+    with pytest.raises(P.PrnuError) as e:
+        ctx.autotune_set(64, 64, len(P.STREAM_SHAPES))
+    assert e.value.status == P.PRNU_EINVAL
+    with pytest.raises(P.PrnuError):
+        ctx.autotune(64, 64, 2)                                   # C must be 1 or 3

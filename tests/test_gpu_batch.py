@@ -104,3 +104,50 @@ def test_cuda_graph_capture_and_replay(ctx, cams):
         for K, e in zip(Ks, eager):
             assert torch.isfinite(K).all()
             assert _rel(K, e) <= 1e-6
+
+
+def test_batch_resolutions_full_size_match_oracle(ctx):
+    """The three resolutions of the 32-camera workload at full size, with the
+    bench's launch configuration (32 groups per pass, autotuned level-1
+    shapes, accumulate captured in a CUDA graph and replayed), against the
+    oracle; then the PCE of one camera on the common 1280x720 window."""
+    specs = [(synth.Camera(H=720, W=1280, C=3, camera_id=2900), 23, 10),
+             (synth.Camera(H=1080, W=1920, C=3, camera_id=2901), 25, 12),
+             (synth.Camera(H=3024, W=4032, C=3, camera_id=2902), 12, 10)]
+    prm = P.default_params()
+    for c, _, _ in specs:
+        ctx.autotune(c.H, c.W, 3, prm, images=2)
+    items = []
+    for c, m, d in specs:
+        fr = synth.frames_fast(c, m, device="cuda")
+        items.append((fr, d, *_zeros(fr)))
+    cams_c = ctx.cameras(items)
+    nbytes = P.prnu_workspace_size_multi(ctx.ctx, cams_c, prm, 32)
+    ws = ctx.workspace(nbytes)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            P.prnu_fingerprint_accumulate_multi(ctx.ctx, cams_c, prm, ws.data_ptr(), ws.numel(), side.cuda_stream)
+    torch.cuda.current_stream().wait_stream(side)
+    g.replay()
+    torch.cuda.synchronize()
+    for fr, d, n, dd in items:
+        onum, oden = O.fingerprint_accumulate(fr.cpu().numpy(), d)
+        assert float(np.linalg.norm(n.cpu().numpy() - onum) / np.linalg.norm(onum)) <= 1e-5
+        assert float(np.linalg.norm(dd.cpu().numpy() - oden) / np.linalg.norm(oden)) <= 1e-6
+    # PCE of the 4032x3024 camera's fingerprint against its own query, top-left 1280x720
+    c, _, _ = specs[2]
+    fr, d, n, dd = items[2]
+    K = ctx.fingerprint_finalize(n, dd, P.PRNU_TO_GRAY)[0, :720, :1280].contiguous()
+    qf = synth.frames_fast(c, 1, stream=1, device="cuda")
+    q = ctx.sda_average(qf, 1)[0, :, :720, :1280].contiguous()
+    wq = ctx.denoise_residual(q)
+    pce = ctx.pce_match(K, wq, q)[0]
+    onum, oden = O.fingerprint_accumulate(fr.cpu().numpy(), d)
+    oK = O.fingerprint_finalize(onum, oden, O.TO_GRAY)[0, :720, :1280]
+    qh = O.sda_average(qf.cpu().numpy(), 1)[0][:, :720, :1280]
+    opce = O.pce_match(oK, O.to_gray(O.residual(qh)), O.to_gray(qh)).pce
+    assert opce > 60
+    assert abs(pce - opce) <= 1e-3 * abs(opce)
