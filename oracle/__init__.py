@@ -11,6 +11,8 @@ Contents:
   prnu_oracle.c    literal FP64 loops: SDA mean, mirror pad, periodised DWT /
                    IDWT, local-variance Wiener shrink, residual, MLE
   pipeline.py      the Python API over the C core, finalize and PCE (numpy FFT)
+  grad.py          FP64 vector-Jacobian products of weighted SDA, residual,
+                   MLE and PCE, and of the whole chain (mean PCE of queries)
 
 Parity unpinned: the exact denoiser output on natural-looking content is fixed
 only by this literal restatement; the tests pin every invariant around it.
@@ -22,3 +24,4 @@ from .pipeline import (DEFAULT, TO_GRAY, WIENER_DFT, ZERO_MEAN, Params, PCEResul
                        wavedec2, waverec2, wiener_dft, zero_mean)
 from .wavelet import daubechies_lowpass, dwt_matrix_1d, highpass  # noqa: F401
 from .native import build, threads  # noqa: F401
+from . import grad  # noqa: F401

@@ -12,36 +12,13 @@
 #include <tuple>
 #include <vector>
 
-#include "kernels.cuh"
+#include "abi_internal.cuh"
 
 using namespace prnu;
+using namespace prnu::abi;
 
-struct prnu_ctx {
-    int device = 0;
-    int sms = 0;
-    double h64[kTaps];
-    Filt filt;
-    std::mutex mu;
-    std::map<std::tuple<int, int, int, int>, cufftHandle> plans;  // (H, W, type, batch) -> plan
-    std::map<std::tuple<int, int, int, int>, size_t> plan_work;
-    cudaStream_t copy_stream = nullptr;
-    cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
-    // per-kernel launch counters (always) and CUDA-event timing (opt-in)
-    bool prof_on = false;
-    std::vector<std::string> knames;
-    std::vector<long long> klaunches;
-    std::vector<double> kbytes;  // algorithmic bytes of the counted launches
-    struct Rec {
-        int kid;
-        cudaEvent_t a, b;
-    };
-    std::vector<Rec> recs;
-    std::vector<cudaEvent_t> pool;
-    // autotuned level-1 analysis shape per (padded H, padded W, subband type)
-    std::map<std::tuple<int, int, int>, int> tuned;
-};
-
-namespace {
+namespace prnu {
+namespace abi {
 
 thread_local std::string tl_err;
 
@@ -56,74 +33,8 @@ prnu_status fail(prnu_status s, const char *fmt, ...) {
     return s;
 }
 
-#define CU(call)                                                                                      \
-    do {                                                                                              \
-        cudaError_t e_ = (call);                                                                      \
-        if (e_ != cudaSuccess)                                                                        \
-            return fail(PRNU_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
-    } while (0)
 
-#define CUFFT(call)                                                                                   \
-    do {                                                                                              \
-        cufftResult r_ = (call);                                                                      \
-        if (r_ != CUFFT_SUCCESS) return fail(PRNU_ECUDA, "%s: cufft error %d", #call, (int)r_);      \
-    } while (0)
 
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
-// Brackets one kernel (or library call) with CUDA events on its stream when
-// profiling is on; always counts the launch.
-struct Launch {
-    prnu_ctx *ctx;
-    cudaStream_t st;
-    int kid = -1;
-    cudaEvent_t a = nullptr, b = nullptr;
-    Launch(prnu_ctx *c, const char *name, cudaStream_t s, int kernels = 1, double bytes = 0.0) : ctx(c), st(s) {
-        std::lock_guard<std::mutex> lk(ctx->mu);
-        for (size_t i = 0; i < ctx->knames.size(); ++i)
-            if (ctx->knames[i] == name) kid = (int)i;
-        if (kid < 0) {
-            kid = (int)ctx->knames.size();
-            ctx->knames.push_back(name);
-            ctx->klaunches.push_back(0);
-            ctx->kbytes.push_back(0.0);
-        }
-        ctx->klaunches[kid] += kernels;
-        ctx->kbytes[kid] += bytes;
-        if (ctx->prof_on) {
-            a = take();
-            b = take();
-            if (a && b) cudaEventRecord(a, st);
-        }
-    }
-    cudaEvent_t take() {
-        if (!ctx->pool.empty()) {
-            cudaEvent_t e = ctx->pool.back();
-            ctx->pool.pop_back();
-            return e;
-        }
-        cudaEvent_t e = nullptr;
-        return cudaEventCreate(&e) == cudaSuccess ? e : nullptr;
-    }
-    ~Launch() {
-        if (a && b) {
-            cudaEventRecord(b, st);
-            std::lock_guard<std::mutex> lk(ctx->mu);
-            ctx->recs.push_back({kid, a, b});
-        }
-    }
-};
 
 // ---------------------------------------------------------------------------
 // Filter bank.  The 8-tap orthonormal Daubechies lowpass (4 vanishing
@@ -235,22 +146,9 @@ prnu_status check_params(const prnu_params *p, int H, int W, Win *win) {
     return PRNU_OK;
 }
 
-inline int padded(int n, int levels) {
-    const int m = 1 << levels;
-    return (n + m - 1) / m * m;
-}
 
-// Workspace of the denoise pipeline over P planes of one geometry.
-struct Layout {
-    size_t X = 0;  // group sums [P][H][W] (accumulate only)
-    size_t LLh[kMaxLevels + 1] = {}, LLl[kMaxLevels + 1] = {}, Rn[kMaxLevels + 1] = {};
-    size_t D[kMaxLevels + 1] = {}, N[kMaxLevels + 1] = {};
-    size_t end = 0;
-};
 
-constexpr size_t kAlign = 256;
-
-Layout make_layout(int H, int W, long long P, int L, bool withX, int sdt = SB_F32) {
+Layout make_layout(int H, int W, long long P, int L, bool withX, int sdt) {
     Layout lo;
     const size_t es = subband_bytes(sdt);  // detail, noise and noise-LL storage
     const long long Hp = padded(H, L), Wp = padded(W, L);
@@ -419,19 +317,7 @@ prnu_status get_plan(prnu_ctx *ctx, int H, int W, cufftType type, int batch, cuf
     return PRNU_OK;
 }
 
-constexpr int kRedBlocks = 512;
 
-// Workspace of finalize (one plane at a time) and of a PCE batch of n queries.
-struct FftLayout {
-    size_t cplx = 0;                  // complex: max(2n half spectra, one full plane)
-    size_t real = 0;                  // float: 2n planes (X_i, Y_i) or (M, Mn)
-    size_t colmean = 0, rowmean = 0;  // doubles
-    size_t colpart = 0;               // doubles: partial column sums per 64-row band
-    size_t part = 0, tmp = 0, mom0 = 0;
-    size_t pm = 0, pe = 0, pv = 0, pi = 0, scal = 0;
-    size_t work = 0, end = 0;
-    int nb = 0, nbm = 0;              // reduction blocks per query
-};
 
 prnu_status fft_layout(prnu_ctx *ctx, int H, int W, int n, FftLayout *out) {
     FftLayout f;
@@ -473,7 +359,6 @@ prnu_status fft_layout(prnu_ctx *ctx, int H, int W, int n, FftLayout *out) {
     return PRNU_OK;
 }
 
-inline cudaStream_t S(void *p) { return reinterpret_cast<cudaStream_t>(p); }
 
 // Process groups g0 .. g0+G-1 of `frames` (device) into num/den.
 prnu_status accumulate_pass(prnu_ctx *ctx, const uint8_t *frames, int m, int H, int W, int C, size_t fs, size_t rp,
@@ -525,7 +410,8 @@ int groups_fitting(int H, int W, int C, int L, size_t bytes, int gmax, int sdt) 
     return lo;
 }
 
-}  // namespace
+}  // namespace abi
+}  // namespace prnu
 
 namespace {
 
