@@ -249,6 +249,73 @@ prnu_status prnu_pce_match_pairs(prnu_ctx *ctx, const float *K, const float *res
                                  int H, int W, int C, int nbhd, double *pce_out, double *ncc_out, int *peak_yx,
                                  void *ws, size_t ws_bytes, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Differentiation.  The chain of Sec. IV-A / IV-B with the SDA weights made
+ * free (the paper's SDA frame is the equal-weight case w_j = 1/d) and sigma0
+ * differentiable:
+ *   S_i = sum_{j in group i} w_j I_j,   W_i = residual(S_i; sigma0),
+ *   K = sum_i W_i S_i / sum_i S_i^2,    PCE of each query against K.
+ * Each forward step below has an adjoint ("_backward") that maps the
+ * gradient of its outputs to the gradient of its inputs.  The residual's
+ * forward keeps every level's detail coefficients (a checkpoint, float32) and
+ * its adjoint recomputes the local variances from them.  Requirements: float32
+ * subbands (EUNSUPPORTED otherwise) and H, W multiples of 2^levels (no
+ * padding; EUNSUPPORTED otherwise).  The derivative is the one of the active
+ * branch: away from ties between window means and from min-mean == sigma0^2.
+ * All pointers are device pointers unless stated; nothing synchronises.
+ * ------------------------------------------------------------------------- */
+
+/* S [g][C][H][W] float32 with S_i = sum_{j in group i} weights[j] * frame_j
+ * (uint8 frames as in prnu_sda_average; weights: device float32 [m]). */
+prnu_status prnu_sda_weighted(prnu_ctx *ctx, const uint8_t *frames, int m, int H, int W, int C, size_t frame_stride,
+                              size_t row_pitch, int d, const float *weights, float *sda_out, void *stream);
+
+/* g_weights[j] = <g_sda[group(j)], frame_j> (written, float32 [m]); the
+ * workspace holds at least m * min(H, 64) * 8 bytes (256-byte aligned). */
+prnu_status prnu_sda_weighted_backward(prnu_ctx *ctx, const uint8_t *frames, int m, int H, int W, int C,
+                                       size_t frame_stride, size_t row_pitch, int d, const float *g_sda,
+                                       float *g_weights, void *ws, size_t ws_bytes, void *stream);
+
+/* Workspace of prnu_denoise_residual_ckpt / _backward for n images, and the
+ * checkpoint size (bytes of float32 detail coefficients of n images). */
+prnu_status prnu_workspace_size_grad(prnu_ctx *ctx, int H, int W, int C, const prnu_params *params, int n,
+                                     size_t *ws_bytes, size_t *ckpt_bytes);
+
+/* prnu_denoise_residual_batch that also writes the checkpoint `ckpt`. */
+prnu_status prnu_denoise_residual_ckpt(prnu_ctx *ctx, const float *img, int n, int H, int W, int C,
+                                       const prnu_params *params, float *residual_out, float *ckpt, void *ws,
+                                       size_t ws_bytes, void *stream);
+
+/* Adjoint of the residual: g_img += d<g_residual, W>/d img ([n][C][H][W]),
+ * *g_sigma0 += d<g_residual, W>/d sigma0 (device float64, nullable).  ckpt is
+ * the forward's checkpoint with the same params. */
+prnu_status prnu_denoise_residual_backward(prnu_ctx *ctx, const float *ckpt, int n, int H, int W, int C,
+                                           const prnu_params *params, const float *g_residual, float *g_img,
+                                           double *g_sigma0, void *ws, size_t ws_bytes, void *stream);
+
+/* MLE fingerprint of n residual/image pairs ([n][C][H][W]), Sec. IV-A:
+ * num = sum W S, den = sum S^2 ([C][H][W], written), K = num/den (0 where
+ * den == 0): [C][H][W], or [H][W] grey (0.299/0.587/0.114) with gray = 1. */
+prnu_status prnu_mle_images(prnu_ctx *ctx, const float *residual, const float *img, int n, int H, int W, int C,
+                            int gray, float *num, float *den, float *K, void *stream);
+
+/* Adjoint of prnu_mle_images: g_residual, g_img [n][C][H][W] written from
+ * g_K (shape of K) and the forward's num, den. */
+prnu_status prnu_mle_images_backward(prnu_ctx *ctx, const float *residual, const float *img, int n, int H, int W,
+                                     int C, int gray, const float *num, const float *den, const float *g_K,
+                                     float *g_residual, float *g_img, void *stream);
+
+prnu_status prnu_workspace_size_pce_backward(prnu_ctx *ctx, int H, int W, int n, size_t *bytes);
+
+/* Adjoint of prnu_pce_match_batch (per_query = 0: one K [H][W]) or of
+ * prnu_pce_match_pairs (per_query = 1: K [n][H][W]) with respect to K and the
+ * query residuals; g_pce: device float64 [n] (the gradient of each PCE).
+ * g_K (written): the shape of K, summed over queries when K is shared;
+ * g_residual_q (written): [n][C][H][W].  The queries' images are data. */
+prnu_status prnu_pce_backward(prnu_ctx *ctx, const float *K, int per_query, const float *residual_q, const float *img_q,
+                              int n, int H, int W, int C, int nbhd, const double *g_pce, float *g_K,
+                              float *g_residual_q, void *ws, size_t ws_bytes, void *stream);
+
 /* Autotuner (not part of the paper's method): times every launch shape
  * (strip rows x warps per block) of the level-1 analysis kernel on `images`
  * images of this geometry and storage type, in the workspace (which must hold

@@ -138,9 +138,13 @@ Layout make_layout(int H, int W, long long P, int L, bool withX, int sdt = SB_F3
 
 // Analysis, shrink and synthesis of P planes; the level-1 step (residual or
 // MLE) is described by `fin`, whose coefficient pointers are filled here.
+// With `ckpt` (the forward's detail coefficients of all levels, float32, level
+// after level, each [3][P][Hp/2^l][Wp/2^l]) the shrink is replaced by its
+// adjoint: `in` is then a residual gradient and the result (accumulated into
+// fin.res_out) the gradient of the input; dL/dsigma0 is added to *g_sigma.
 prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, const prnu_params &prm, const Win &win,
                         PlaneScale sc, int scale_on, char *ws, const Layout &lo, FinalArgs fin, bool mle,
-                        cudaStream_t st);
+                        cudaStream_t st, const float *ckpt = nullptr, double *g_sigma = nullptr);
 
 // cuFFT plan cache: (H, W, type, batch) -> plan without an auto-allocated
 // work area; batched planes are contiguous with the default distances.

@@ -268,11 +268,6 @@ __global__ void k_cross_spectrum(const cufftComplex *FX, const cufftComplex *FY,
     }
 }
 
-struct PceScalars {
-    double c0, energy;
-    long long peak_idx;
-    double sx, sxx, sy, syy;
-};
 
 // energy outside the neighbourhood of zero shift and argmax (first index on
 // ties); one row segment per iteration so the row index is known

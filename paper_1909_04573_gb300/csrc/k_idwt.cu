@@ -214,8 +214,13 @@ __global__ void __launch_bounds__(256) k_final(FinalArgs a) {
                     }
                 }
             } else {
-                a.res_out[o] = w.x;
-                if (two) a.res_out[o + 1] = w.y;
+                if (a.accumulate) {
+                    a.res_out[o] += w.x;
+                    if (two) a.res_out[o + 1] += w.y;
+                } else {
+                    a.res_out[o] = w.x;
+                    if (two) a.res_out[o + 1] = w.y;
+                }
             }
         }
     }

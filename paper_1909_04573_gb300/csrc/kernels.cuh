@@ -72,6 +72,7 @@ struct FinalArgs {
     const float *X;    // MLE mode: group sums [G][C][H][W]
     PlaneScale sc;
     float *res_out;    // residual mode: [G*C][H][W]
+    int accumulate;    // residual mode: res_out += W instead of res_out = W
     float *num, *den;  // MLE mode: [C][H][W]
     const GroupDesc *gd;    // multi-camera MLE: group -> camera (groups of a camera are consecutive)
     const CamDesc *cams;    // multi-camera MLE: per-camera num/den
@@ -100,7 +101,39 @@ cudaError_t launch_cross_spectrum(const cufftComplex *FX, const cufftComplex *FY
                                   cufftComplex *Z, int sms, cudaStream_t st);
 cudaError_t launch_pce_reduce(const float *Cr, int H, int W, int r, int n, int nb, double *part_e, float *part_v,
                               long long *part_i, const double *part_m, int nbm, void *out, cudaStream_t st);
+// per-query PCE scalars written by the reduction (device)
+struct PceScalars {
+    double c0, energy;
+    long long peak_idx;
+    double sx, sxx, sy, syy;
+};
 size_t pce_scalars_bytes();
+
+// k_grad.cu -- adjoints
+struct ShrinkBwdArgs {
+    const float *c;    // forward detail coefficients (checkpoint) [nplanes][R][Cc]
+    const float *gn;   // gradient of the noise coefficients
+    float *gc;         // gradient of the coefficients (written)
+    int R, Cc, nplanes;
+    float s2, two_sigma0;
+    Win win;
+    double *g_sigma;   // += dL/dsigma0 (nullable)
+};
+cudaError_t launch_sda_weighted(const SdaArgs &a, const float *wts, int num_sms, cudaStream_t st);
+int sda_wgrad_blocks(int H);
+cudaError_t launch_sda_wgrad(const SdaArgs &a, const float *gS, double *part, float *gw, cudaStream_t st);
+cudaError_t launch_mle_images(const float *res, const float *img, int n, int C, long long hw, int gray, float *num,
+                              float *den, float *K, int sms, cudaStream_t st);
+cudaError_t launch_mle_images_bwd(const float *res, const float *img, int n, int C, long long hw, int gray,
+                                  const float *num, const float *den, const float *gK, float *gres, float *gimg,
+                                  int sms, cudaStream_t st);
+cudaError_t launch_shrink_bwd(const ShrinkBwdArgs &a, cudaStream_t st);
+cudaError_t launch_pce_gfield(float *Cr, int H, int W, int r, int n, const void *scal, const double *g,
+                              cudaStream_t st);
+cudaError_t launch_pce_spectra_bwd(cufftComplex *FX, cufftComplex *FY, const cufftComplex *FG, long long nh, int n,
+                                   int sms, cudaStream_t st);
+cudaError_t launch_pce_bwd_out(const float *gYraw, const float *gXraw, const float *Iq, int n, int C, long long hw,
+                               float inv_n, int per_query, float *gK, float *gres, int sms, cudaStream_t st);
 void pce_unpack(const void *p, int q, double *c0, double *energy, long long *peak_idx, double *sx, double *sxx,
                 double *sy, double *syy);
 

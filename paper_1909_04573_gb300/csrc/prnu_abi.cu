@@ -177,7 +177,8 @@ Layout make_layout(int H, int W, long long P, int L, bool withX, int sdt) {
 // MLE) is described by `fin`, whose coefficient pointers are filled here.
 prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, const prnu_params &prm, const Win &win,
                         PlaneScale sc, int scale_on, char *ws, const Layout &lo, FinalArgs fin, bool mle,
-                        cudaStream_t st) {
+                        cudaStream_t st, const float *ckpt, double *g_sigma) {
+    size_t ckpt_off = 0;  // floats of the levels before l in the checkpoint
     const int L = prm.levels;
     const int Hp = padded(H, L), Wp = padded(W, L);
     auto F = [&](size_t off) { return reinterpret_cast<float *>(ws + off); };
@@ -215,6 +216,23 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
                 if (it != ctx->tuned.end()) shape = it->second;
             }
             CU(launch_analysis(a, l == 1, st, shape));
+        }
+        if (ckpt) {  // adjoint: D holds the gradient of the noise coefficients
+            ShrinkBwdArgs b{};
+            b.c = ckpt + ckpt_off;
+            b.gn = static_cast<const float *>(SB(lo.D[l], A, 0));
+            b.gc = static_cast<float *>(SB(lo.N[l], A, 0));
+            b.R = Hp >> l;
+            b.Cc = Wp >> l;
+            b.nplanes = 3 * P;
+            b.s2 = prm.sigma0 * prm.sigma0;
+            b.two_sigma0 = 2.f * prm.sigma0;
+            b.win = win;
+            b.g_sigma = g_sigma;
+            ckpt_off += (size_t)3 * P * A;
+            Launch t(ctx, "shrink_bwd", st, 1, 3.0 * b.nplanes * b.R * b.Cc * 4);
+            CU(launch_shrink_bwd(b, st));
+            continue;
         }
         ShrinkArgs s{};
         s.in = SB(lo.D[l], A, 0);
@@ -265,7 +283,7 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
         const double cin = (double)P * A1 * es * (fin.LL ? 4 : 3);
         const double io = mle ? (double)P * H * W * 4 + (double)fin.C * H * W * 16 * (prm.compensated ? 2 : 1)
                               : (double)P * H * W * 4;
-        Launch t(ctx, mle ? "final_mle" : "final_residual", st, 1, cin + io);
+        Launch t(ctx, mle ? "final_mle" : "final_residual", st, 1, cin + io * (fin.accumulate ? 2 : 1));
         CU(launch_final(fin, mle, st));
     }
     return PRNU_OK;

@@ -25,7 +25,9 @@ EXPORTS = (
     "prnu_profile_enable", "prnu_profile_reset", "prnu_profile_read", "prnu_denoise_residual_static",
     "prnu_denoise_residual_batch", "prnu_pce_match_batch", "prnu_pce_match_pairs",
     "prnu_workspace_size_multi", "prnu_fingerprint_accumulate_multi", "prnu_autotune",
-    "prnu_autotune_set",
+    "prnu_autotune_set", "prnu_sda_weighted", "prnu_sda_weighted_backward", "prnu_workspace_size_grad",
+    "prnu_denoise_residual_ckpt", "prnu_denoise_residual_backward", "prnu_mle_images", "prnu_mle_images_backward",
+    "prnu_workspace_size_pce_backward", "prnu_pce_backward",
 )
 
 
@@ -92,6 +94,15 @@ def lib() -> ctypes.CDLL:
                 "prnu_autotune": [_vp, _i, _i, _i, _pp, _i, _vp, _sz, _vp, ctypes.POINTER(_i),
                                   ctypes.POINTER(ctypes.c_float)],
                 "prnu_autotune_set": [_vp, _i, _i, _pp, _i],
+                "prnu_sda_weighted": [_vp, _vp, _i, _i, _i, _i, _sz, _sz, _i, _vp, _vp, _vp],
+                "prnu_sda_weighted_backward": [_vp, _vp, _i, _i, _i, _i, _sz, _sz, _i, _vp, _vp, _vp, _sz, _vp],
+                "prnu_workspace_size_grad": [_vp, _i, _i, _i, _pp, _i, ctypes.POINTER(_sz), ctypes.POINTER(_sz)],
+                "prnu_denoise_residual_ckpt": [_vp, _vp, _i, _i, _i, _i, _pp, _vp, _vp, _vp, _sz, _vp],
+                "prnu_denoise_residual_backward": [_vp, _vp, _i, _i, _i, _i, _pp, _vp, _vp, _vp, _vp, _sz, _vp],
+                "prnu_mle_images": [_vp, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp],
+                "prnu_mle_images_backward": [_vp, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp],
+                "prnu_workspace_size_pce_backward": [_vp, _i, _i, _i, ctypes.POINTER(_sz)],
+                "prnu_pce_backward": [_vp, _vp, _i, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _sz, _vp],
                 "prnu_profile_enable": [_vp, _i],
                 "prnu_profile_reset": [_vp],
                 "prnu_profile_read": [_vp, _i, ctypes.c_char_p, _sz, ctypes.POINTER(ctypes.c_longlong),
@@ -236,6 +247,24 @@ def prnu_autotune(ctx, H, W, C, params, images, ws, ws_bytes, stream):
     _check(lib().prnu_autotune(ctx, H, W, C, ctypes.byref(params), images, ws, ws_bytes, stream, ctypes.byref(shape),
                                ctypes.byref(ms)), ctx)
     return shape.value, ms.value
+
+
+def prnu_workspace_size_grad(ctx, H, W, C, params, n):
+    ws, ck = _sz(), _sz()
+    _check(lib().prnu_workspace_size_grad(ctx, H, W, C, ctypes.byref(params), n, ctypes.byref(ws), ctypes.byref(ck)),
+           ctx)
+    return ws.value, ck.value
+
+
+def prnu_workspace_size_pce_backward(ctx, H, W, n):
+    b = _sz()
+    _check(lib().prnu_workspace_size_pce_backward(ctx, H, W, n, ctypes.byref(b)), ctx)
+    return b.value
+
+
+def call(name, ctx, *args):
+    """Call a status-returning entry point of libprnu; raise PrnuError on failure."""
+    _check(getattr(lib(), name)(ctx, *args), ctx)
 
 
 def prnu_profile_enable(ctx, on: bool) -> None:
