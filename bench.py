@@ -43,10 +43,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--frames", type=int, default=M_FRAMES,
                     help="frames of the workload (default 1000; smaller values are for profiling captures)")
-    ap.add_argument("--config", default="video", choices=["video", "precision", "depth", "batch"],
+    ap.add_argument("--config", default="video", choices=["video", "precision", "depth", "batch", "grad"],
                     help="video: 1000 RGB 1920x1080 frames, SDA-50 (the headline); precision: 500 RGB 4032x3024 "
                          "frames, SDA-25, per storage type throughput and error against the FP64 oracle; depth: "
-                         "SDA-depth study; batch: 32 cameras of mixed resolutions, frame counts and SDA groups")
+                         "SDA-depth study; batch: 32 cameras of mixed resolutions, frame counts and SDA groups; "
+                         "grad: forward + adjoint of the chain on 256 grey 512x512 frames and 50 PCE ascent steps")
     ap.add_argument("--cameras", type=int, default=32, help="batch config: number of cameras")
     ap.add_argument("--chunk-gb", type=float, default=96.0, help="batch config: frame buffer per chunk (GiB)")
     ap.add_argument("--groups-per-pass", type=int, default=32, help="batch config: SDA groups per pass")
@@ -568,6 +569,120 @@ def batch_config(args, rank, world, local):
     ctx.close()
 
 
+# ------------------------------------------------------- differentiation --
+def grad_config(args, rank, world, local):
+    """256 grey 512x512 frames (independent scenes), SDA groups of 16 with
+    learnable per-frame weights (init 1/16) and a learnable sigma0 (init 3).
+    Step = forward (weighted SDA, residuals with checkpoint, MLE, PCE of 8
+    held-out query frames) plus the adjoint of all of it; value = frames/s
+    through forward + adjoint.  Then 50 Adam steps maximising the queries'
+    mean PCE, with 8 further queries as an evaluation set; the FP64 oracle's
+    gradient at the start is timed beside it (one evaluation, 2 queries)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_1909_04573_gb300 import grad as G
+    from paper_1909_04573_gb300 import prnu as P
+    from paper_1909_04573_gb300 import synth
+
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    dev = torch.device("cuda", local)
+    ctx = P.Context(local)
+    m, Hh, Ww, d, nq = 256, 512, 512, 16, 8
+    cam = synth.Camera(H=Hh, W=Ww, C=1, camera_id=900 + rank)
+    frames = synth.frames(cam, m, device=dev)
+    q_train = ctx.sda_average(synth.frames(cam, nq, stream=1, device=dev), 1)
+    q_eval = ctx.sda_average(synth.frames(cam, nq, stream=2, device=dev), 1)
+    w = torch.full((m,), 1.0 / d, device=dev, requires_grad=True)
+    sig = torch.tensor(3.0, dtype=torch.float64, requires_grad=True)
+
+    def step():
+        w.grad = None
+        sig.grad = None
+        J = G.mean_pce(frames, w, d, sig, q_train, ctx)
+        J.backward()
+        return J
+
+    for _ in range(args.warmup):
+        step()
+    P.prnu_profile_reset(ctx.ctx)
+    P.prnu_profile_enable(ctx.ctx, True)
+    clocks = Clocks(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record()
+    for _ in range(args.steps):
+        J0 = step()
+    e1.record()
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) / args.steps * 1000.0
+    ck = clocks.stop()
+    P.prnu_profile_enable(ctx.ctx, False)
+    prof = P.prnu_profile_read(ctx.ctx)
+    P.prnu_profile_reset(ctx.ctx)
+    ms = e0.elapsed_time(e1) / args.steps
+    roof, _, kern, launches = kernel_report(prof, args.steps, ck, dev)
+    g_w0, g_s0 = w.grad.detach().clone(), float(sig.grad)
+    out = {"metric": "differentiation: frames/s through forward + adjoint (weighted SDA, residual, MLE, PCE)",
+           "value": world * m / (ms / 1000.0), "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "wall_ms_per_step": wall, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded sensor model)",
+           "config": {"workload": "grad-512x512-gray-256f-sda16", "frames": m, "H": Hh, "W": Ww, "C": 1, "d": d,
+                      "queries_train": nq, "queries_eval": nq, "l2": "inputs 67 MB < L2; residual and PCE "
+                      "intermediates ~0.4 GB per step (no flush)"},
+           "roofline": roof, "gpu_launches": int(launches), "kernels": kern,
+           "grad_at_start": {"J": J0.item(), "g_sigma0": g_s0, "g_w_norm": float(g_w0.norm()),
+                             "g_w_mean": float(g_w0.mean())}}
+    if ck:
+        out["clocks"] = ck
+    # FP64 oracle gradient at the start (bounded: 2 queries), timed on the host
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle as O
+        from oracle import grad as OG
+        O.build()
+        t0 = time.perf_counter()
+        oJ, ogw, ogs = OG.objective_and_grad(frames.cpu().numpy(), d, np.full(m, 1.0 / d), 3.0,
+                                             q_train[:2].double().cpu().numpy())
+        t_or = time.perf_counter() - t0
+        with torch.no_grad():
+            w2 = torch.full((m,), 1.0 / d, device=dev, requires_grad=True)
+            s2 = torch.tensor(3.0, dtype=torch.float64, requires_grad=True)
+        J2 = G.mean_pce(frames, w2, d, s2, q_train[:2], ctx)
+        J2.backward()
+        gw2 = w2.grad.double().cpu().numpy()
+        out["cpu_baseline"] = {"value": m / t_or, "unit": "frames/s", "cores": O.threads(), "kind": "oracle",
+                               "sample": "one forward + adjoint of the whole workload with 2 queries",
+                               "seconds": t_or}
+        out["oracle_parity"] = {"J_rel": abs(J2.item() - oJ) / abs(oJ),
+                                "g_w_relL2": float(np.linalg.norm(gw2 - ogw) / np.linalg.norm(ogw)),
+                                "g_sigma0_rel": abs(float(s2.grad) - ogs) / abs(ogs)}
+    # 50 ascent steps on the training queries' mean PCE
+    opt = torch.optim.Adam([{"params": [w], "lr": 2e-3}, {"params": [sig], "lr": 5e-2}])
+    with torch.no_grad():
+        ev0 = G.mean_pce(frames, w, d, sig, q_eval, ctx).item()
+    traj = []
+    for it in range(50):
+        opt.zero_grad()
+        J = G.mean_pce(frames, w, d, sig, q_train, ctx)
+        (-J).backward()
+        opt.step()
+        traj.append(J.item())
+    with torch.no_grad():
+        J_end = G.mean_pce(frames, w, d, sig, q_train, ctx).item()
+        ev1 = G.mean_pce(frames, w, d, sig, q_eval, ctx).item()
+    out["ascent"] = {"steps": 50, "optimizer": "Adam (lr 2e-3 weights, 5e-2 sigma0)",
+                     "pce_train_start": traj[0], "pce_train_end": J_end, "pce_eval_start": ev0, "pce_eval_end": ev1,
+                     "sigma0_end": float(sig), "w_min": float(w.min()), "w_max": float(w.max()),
+                     "w_mean": float(w.mean()), "trajectory_every_10": traj[::10]}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 # --------------------------------------------------------------- GPU arm ---
 def main():
     args = parse()
@@ -585,6 +700,9 @@ def main():
         return
     if args.config == "batch":
         batch_config(args, rank, world, local)
+        return
+    if args.config == "grad":
+        grad_config(args, rank, world, local)
         return
 
     import numpy as np
