@@ -232,6 +232,261 @@ __global__ void __launch_bounds__(256) k_final(FinalArgs a) {
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// MLE mode with float32 subbands: the same level-1 step as k_final with the
+// next image's coefficient tiles and image tile fetched by cp.async into a
+// second buffer while the current image is synthesised.
+
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+struct AsyncTile {
+    float c[2][4][CT][CT + 1];  // LL, LH, HL, HH coefficient tiles, double-buffered
+    float x[2][OT][OT];         // MLE mode: the image tile (group sums)
+    float lo[OT][CT + 1], hi[OT][CT + 1];
+};
+
+template <bool COMP>
+__global__ void __launch_bounds__(256) k_final_async(FinalArgs a) {
+    constexpr bool MLE = true;
+    __shared__ __align__(16) AsyncTile s;
+    const int y0 = blockIdx.y * OT, x0 = blockIdx.x * OT;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * 32 + tx;
+    const long long hw = (long long)a.H * a.W;
+    const float *LL = static_cast<const float *>(a.LL), *LH = static_cast<const float *>(a.LH);
+    const float *HL = static_cast<const float *>(a.HL), *HH = static_cast<const float *>(a.HH);
+    const int nimg = a.G;
+    auto plane_of = [&](int i) { return i * a.C + (int)blockIdx.z; };
+    const int sx = wrap_near((x0 >> 1) - 3 + tx, a.Cc);
+    auto issue = [&](int plane, int b) {
+        const long long poff = (long long)plane * a.Rc * a.Cc;
+        if (tx < CT) {
+            for (int r = ty; r < CT; r += 8) {
+                const long long o = poff + (long long)wrap_near((y0 >> 1) - 3 + r, a.Rc) * a.Cc + sx;
+                if (LL)
+                    cp_async4(&s.c[b][0][r][tx], LL + o);
+                else
+                    s.c[b][0][r][tx] = 0.f;
+                cp_async4(&s.c[b][1][r][tx], LH + o);
+                cp_async4(&s.c[b][2][r][tx], HL + o);
+                cp_async4(&s.c[b][3][r][tx], HH + o);
+            }
+        }
+        if (MLE) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int it = tid + 256 * k;
+                const int y = it >> 5, xx = it & 31;
+                const int gy = y0 + y, gx = x0 + xx;
+                if (gy < a.H && gx < a.W) cp_async4(&s.x[b][y][xx], a.X + (long long)plane * hw + (long long)gy * a.W + gx);
+            }
+        }
+    };
+    float an[4], ad[4], anl[4], adl[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { an[k] = 0.f; ad[k] = 0.f; anl[k] = 0.f; adl[k] = 0.f; }
+    int cam = (MLE && a.gd) ? a.gd[0].cam : -1;
+    issue(plane_of(0), 0);
+    cp_commit();
+    for (int i = 0; i < nimg; ++i) {
+        const int b = i & 1;
+        const int plane = plane_of(i);
+        cp_wait_all();
+        __syncthreads();  // image i landed; every reader of the other buffer and of lo/hi is done
+        if (i + 1 < nimg) issue(plane_of(i + 1), b ^ 1);
+        cp_commit();
+        if (MLE && a.gd && a.gd[i].cam != cam) {  // block-uniform: the camera changes
+            mle_flush<COMP>(a, a.cams[cam].num, a.cams[cam].den, an, ad, anl, adl, y0, x0, tid);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) { an[k] = 0.f; ad[k] = 0.f; anl[k] = 0.f; adl[k] = 0.f; }
+            cam = a.gd[i].cam;
+        }
+        // column synthesis from buffer b
+        for (int it = tid; it < NPAIR * CT; it += 256) {
+            const int m = it / CT, c = it - m * CT;
+            float q[4][4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) q[k][t] = s.c[b][k][m + 3 - t][c];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                float lo = 0.f, hi = 0.f;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const float hk = a.f.h[e + 2 * t], gk = a.f.g[e + 2 * t];
+                    lo = __fmaf_rn(hk, q[0][t], lo);
+                    lo = __fmaf_rn(gk, q[1][t], lo);
+                    hi = __fmaf_rn(hk, q[2][t], hi);
+                    hi = __fmaf_rn(gk, q[3][t], hi);
+                }
+                s.lo[2 * m + e][c] = lo;
+                s.hi[2 * m + e][c] = hi;
+            }
+        }
+        __syncthreads();
+        const float inv_n = MLE ? __frcp_rn((float)a.sc.count(plane)) : 1.f;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int it = tid + 256 * k;
+            const int y = it >> 4, n = it & 15;
+            const int gy = y0 + y, gx = x0 + 2 * n;
+            if (gy >= a.H || gx >= a.W) continue;
+            const bool two = gx + 1 < a.W;
+            float l[4], h[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                l[t] = s.lo[y][n + 3 - t];
+                h[t] = s.hi[y][n + 3 - t];
+            }
+            float w[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                float v = 0.f;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    v = __fmaf_rn(a.f.h[e + 2 * t], l[t], v);
+                    v = __fmaf_rn(a.f.g[e + 2 * t], h[t], v);
+                }
+                w[e] = v;
+            }
+            if (MLE) {
+                const float I0 = s.x[b][y][2 * n] * inv_n;
+                const float I1 = two ? s.x[b][y][2 * n + 1] * inv_n : 0.f;
+                if (COMP) {
+                    ff_add(an[2 * k], anl[2 * k], w[0] * I0);
+                    ff_add(ad[2 * k], adl[2 * k], I0 * I0);
+                    if (two) {
+                        ff_add(an[2 * k + 1], anl[2 * k + 1], w[1] * I1);
+                        ff_add(ad[2 * k + 1], adl[2 * k + 1], I1 * I1);
+                    }
+                } else {
+                    an[2 * k] = __fmaf_rn(w[0], I0, an[2 * k]);
+                    ad[2 * k] = __fmaf_rn(I0, I0, ad[2 * k]);
+                    if (two) {
+                        an[2 * k + 1] = __fmaf_rn(w[1], I1, an[2 * k + 1]);
+                        ad[2 * k + 1] = __fmaf_rn(I1, I1, ad[2 * k + 1]);
+                    }
+                }
+            }
+        }
+    }
+    if (MLE) {
+        if (a.gd)
+            mle_flush<COMP>(a, a.cams[cam].num, a.cams[cam].den, an, ad, anl, adl, y0, x0, tid);
+        else
+            mle_flush<COMP>(a, a.num, a.den, an, ad, anl, adl, y0, x0, tid);
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Residual mode with float32 subbands, streaming: a warp owns 32 coefficient
+// columns n0 .. n0+31 of one plane and walks a strip of coefficient rows,
+// keeping the last four rows of the four subbands in a register ring for the
+// column synthesis.  Lanes 3..31 produce output columns 2n, 2n+1; lanes 0..2
+// only supply the row synthesis' left neighbours (taken with shuffles), so
+// consecutive warps start 29 columns apart.  Three rows above the strip prime
+// the ring.
+constexpr int FS_ROWS = 32;  // coefficient rows per strip (64 output rows)
+constexpr int FS_WARPS = 4;
+constexpr int FS_COLS = 29;  // output coefficient columns per warp
+
+__global__ void __launch_bounds__(32 * FS_WARPS) k_final_stream(FinalArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int cg = blockIdx.x * FS_WARPS + (threadIdx.x >> 5);
+    if (cg * FS_COLS >= a.Cc) return;  // warp-uniform
+    const int n = cg * FS_COLS - 3 + lane;  // coefficient column (unwrapped)
+    const int nw = wrap_near(n, a.Cc);
+    const bool out_lane = lane >= 3 && n < a.Cc;
+    const int plane = blockIdx.z;
+    const long long poff = (long long)plane * a.Rc * a.Cc + nw;
+    const float *LL = static_cast<const float *>(a.LL), *LH = static_cast<const float *>(a.LH);
+    const float *HL = static_cast<const float *>(a.HL), *HH = static_cast<const float *>(a.HH);
+    const int m0 = blockIdx.y * FS_ROWS, m1 = min(a.Rc, m0 + FS_ROWS);
+    const long long hw = (long long)a.H * a.W;
+    float *outp = a.res_out + (long long)plane * hw;
+    // ring slot of coefficient row m is (m - m0 + 3) & 3
+    float q[4][4];  // [slot][subband]
+    auto load = [&](int m, float *d) {
+        const long long o = poff + (long long)wrap_near(m, a.Rc) * a.Cc;
+        d[0] = LL ? __ldg(LL + o) : 0.f;
+        d[1] = __ldg(LH + o);
+        d[2] = __ldg(HL + o);
+        d[3] = __ldg(HH + o);
+    };
+#pragma unroll
+    for (int t = 1; t <= 3; ++t) load(m0 - t, q[(3 - t) & 3]);
+    for (int mb = m0; mb < m1; mb += 4) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = mb + j;
+            if (m >= m1) break;
+            load(m, q[(j + 3) & 3]);
+            // column synthesis: rows 2m + e of lo (LL, LH) and hi (HL, HH)
+            float lo[2], hi[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                float l = 0.f, h = 0.f;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const float *r = q[(j + 3 - t) & 3];
+                    const float hk = a.f.h[e + 2 * t], gk = a.f.g[e + 2 * t];
+                    l = __fmaf_rn(hk, r[0], l);
+                    l = __fmaf_rn(gk, r[1], l);
+                    h = __fmaf_rn(hk, r[2], h);
+                    h = __fmaf_rn(gk, r[3], h);
+                }
+                lo[e] = l;
+                hi[e] = h;
+            }
+            // row synthesis of output rows 2m + e, columns 2n + f
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                float L[4], Hh[4];
+                L[0] = lo[e];
+                Hh[0] = hi[e];
+#pragma unroll
+                for (int t = 1; t < 4; ++t) {
+                    L[t] = __shfl_up_sync(0xffffffffu, lo[e], t);
+                    Hh[t] = __shfl_up_sync(0xffffffffu, hi[e], t);
+                }
+                float w[2];
+#pragma unroll
+                for (int f = 0; f < 2; ++f) {
+                    float v = 0.f;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        v = __fmaf_rn(a.f.h[f + 2 * t], L[t], v);
+                        v = __fmaf_rn(a.f.g[f + 2 * t], Hh[t], v);
+                    }
+                    w[f] = v;
+                }
+                const int y = 2 * m + e, x = 2 * n;
+                if (out_lane && y < a.H && x < a.W) {
+                    float *o = outp + (long long)y * a.W + x;
+                    const bool two = x + 1 < a.W;
+                    if (a.accumulate) {
+                        o[0] += w[0];
+                        if (two) o[1] += w[1];
+                    } else if (two && ((reinterpret_cast<uintptr_t>(o) & 7u) == 0)) {
+                        *reinterpret_cast<float2 *>(o) = make_float2(w[0], w[1]);
+                    } else {
+                        o[0] = w[0];
+                        if (two) o[1] = w[1];
+                    }
+                }
+            }
+        }
+    }
+}
+
 cudaError_t launch_synthesis(const SynArgs &a, cudaStream_t st) {
     dim3 block(32, 8);
     dim3 grid((unsigned)((2 * a.Cc + OT - 1) / OT), (unsigned)((2 * a.Rc + OT - 1) / OT), (unsigned)a.P);
@@ -256,7 +511,27 @@ static void launch_final_t(const FinalArgs &a, bool mle, cudaStream_t st) {
         k_final<true, T, false><<<grid, block, 0, st>>>(a);
 }
 
+static void launch_final_async_mle(const FinalArgs &a, cudaStream_t st) {
+    dim3 block(32, 8);
+    dim3 grid((unsigned)((a.W + OT - 1) / OT), (unsigned)((a.H + OT - 1) / OT), (unsigned)a.C);
+    if (a.compensated)
+        k_final_async<true><<<grid, block, 0, st>>>(a);
+    else
+        k_final_async<false><<<grid, block, 0, st>>>(a);
+}
+
 cudaError_t launch_final(const FinalArgs &a, bool mle, cudaStream_t st) {
+    if (a.sdt == SB_F32 && mle) {
+        launch_final_async_mle(a, st);
+        return cudaGetLastError();
+    }
+    if (a.sdt == SB_F32) {
+        const int groups = (a.Cc + FS_COLS - 1) / FS_COLS;
+        dim3 grid((unsigned)((groups + FS_WARPS - 1) / FS_WARPS), (unsigned)((a.Rc + FS_ROWS - 1) / FS_ROWS),
+                  (unsigned)(a.C * a.G));
+        k_final_stream<<<grid, 32 * FS_WARPS, 0, st>>>(a);
+        return cudaGetLastError();
+    }
     if (a.sdt == SB_F16)
         launch_final_t<__half>(a, mle, st);
     else if (a.sdt == SB_BF16)
