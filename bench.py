@@ -732,7 +732,6 @@ def main():
     qimg = ctx.sda_average(qf, 1)                                         # [20, 3, H, W] float
     num = torch.zeros((C, H, W), dtype=torch.float32, device=dev)
     den = torch.zeros_like(num)
-    wq = torch.empty_like(qimg)
     flags = P.PRNU_TO_GRAY | P.PRNU_ZERO_MEAN | P.PRNU_WIENER_DFT
     pces = []
 
@@ -748,8 +747,7 @@ def main():
         else:
             ctx.fingerprint_accumulate(frames, d, num, den, images_per_pass=images_per_pass)
         K = ctx.fingerprint_finalize(num, den, flags)
-        ctx.denoise_residual_batch(qimg, out=wq)
-        pces[:] = [r[0] for r in ctx.pce_match_batch(K[0], wq, qimg)]
+        pces[:] = [r[0] for r in ctx.pce_match_images(K[0], qimg)]
 
     def timed(fn, steps, warmup):
         for _ in range(warmup):
@@ -841,8 +839,7 @@ def main():
             K = ctx.fingerprint_finalize(num, den, flags)
             qdev.copy_(qhost, non_blocking=True)
             qi = ctx.sda_average(qdev, 1)
-            ctx.denoise_residual_batch(qi, out=wq)
-            ctx.pce_match_batch(K[0], wq, qi)
+            ctx.pce_match_images(K[0], qi)
 
         ms_e2e = timed(step_e2e, 3, 1)
         # raw pinned H2D bandwidth of one 1 GiB copy, for context

@@ -249,6 +249,21 @@ prnu_status prnu_pce_match_pairs(prnu_ctx *ctx, const float *K, const float *res
                                  int H, int W, int C, int nbhd, double *pce_out, double *ncc_out, int *peak_yx,
                                  void *ws, size_t ws_bytes, void *stream);
 
+/* Queries straight from their images: the residual of each query image
+ * (the denoiser of prnu_denoise_residual_batch with `params`) matched against
+ * K as in prnu_pce_match_batch, without storing the per-channel residuals.
+ * Because everything after the shrink is linear, the grey residual of a
+ * three-channel query is synthesised once from the 0.299/0.587/0.114
+ * combination of the channels' noise coefficients (the same value up to
+ * float32 rounding order).  img_q: device float32 [n][C][H][W]; K: device
+ * float32 [H][W]; outputs as in prnu_pce_match_batch (host, after a stream
+ * synchronisation).  float32 subbands only (EUNSUPPORTED otherwise). */
+prnu_status prnu_workspace_size_pce_images(prnu_ctx *ctx, int H, int W, int C, const prnu_params *params, int n,
+                                           size_t *bytes);
+prnu_status prnu_pce_match_images(prnu_ctx *ctx, const float *K, const float *img_q, int n, int H, int W, int C,
+                                  const prnu_params *params, int nbhd, double *pce_out, double *ncc_out,
+                                  int *peak_yx, void *ws, size_t ws_bytes, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Differentiation.  The chain of Sec. IV-A / IV-B with the SDA weights made
  * free (the paper's SDA frame is the equal-weight case w_j = 1/d) and sigma0

@@ -398,28 +398,33 @@ constexpr int FS_ROWS = 32;  // coefficient rows per strip (64 output rows)
 constexpr int FS_WARPS = 4;
 constexpr int FS_COLS = 29;  // output coefficient columns per warp
 
-__global__ void __launch_bounds__(32 * FS_WARPS) k_final_stream(FinalArgs a) {
+// One warp's strip: coefficient planes [Rc][Cc] (LL may be null: zero).
+// With GRAY3 each detail value is 0.299 / 0.587 / 0.114 of the planes at
+// offsets 0, cs, 2 cs (the synthesis is linear, so this synthesises the grey
+// combination of three channels' noise).  Each output pair (y, x), (y, x+1)
+// of the first outH x outW samples goes to epi(y, x, w0, w1, two).
+template <bool GRAY3, class Epi>
+__device__ __forceinline__ void stream_synth(const float *LL, const float *LH, const float *HL, const float *HH,
+                                             long long cs, int Rc, int Cc, const Filt &f, int cg, int m0, int outH,
+                                             int outW, Epi &epi) {
     const int lane = threadIdx.x & 31;
-    const int cg = blockIdx.x * FS_WARPS + (threadIdx.x >> 5);
-    if (cg * FS_COLS >= a.Cc) return;  // warp-uniform
     const int n = cg * FS_COLS - 3 + lane;  // coefficient column (unwrapped)
-    const int nw = wrap_near(n, a.Cc);
-    const bool out_lane = lane >= 3 && n < a.Cc;
-    const int plane = blockIdx.z;
-    const long long poff = (long long)plane * a.Rc * a.Cc + nw;
-    const float *LL = static_cast<const float *>(a.LL), *LH = static_cast<const float *>(a.LH);
-    const float *HL = static_cast<const float *>(a.HL), *HH = static_cast<const float *>(a.HH);
-    const int m0 = blockIdx.y * FS_ROWS, m1 = min(a.Rc, m0 + FS_ROWS);
-    const long long hw = (long long)a.H * a.W;
-    float *outp = a.res_out + (long long)plane * hw;
+    const int nw = wrap_near(n, Cc);
+    const bool out_lane = lane >= 3 && n < Cc;
+    const int m1 = min(Rc, m0 + FS_ROWS);
     // ring slot of coefficient row m is (m - m0 + 3) & 3
     float q[4][4];  // [slot][subband]
+    auto ld = [&](const float *p, long long o) {
+        if (GRAY3)
+            return __fmaf_rn(0.114f, __ldg(p + o + 2 * cs), __fmaf_rn(0.587f, __ldg(p + o + cs), 0.299f * __ldg(p + o)));
+        return __ldg(p + o);
+    };
     auto load = [&](int m, float *d) {
-        const long long o = poff + (long long)wrap_near(m, a.Rc) * a.Cc;
+        const long long o = (long long)wrap_near(m, Rc) * Cc + nw;
         d[0] = LL ? __ldg(LL + o) : 0.f;
-        d[1] = __ldg(LH + o);
-        d[2] = __ldg(HL + o);
-        d[3] = __ldg(HH + o);
+        d[1] = ld(LH, o);
+        d[2] = ld(HL, o);
+        d[3] = ld(HH, o);
     };
 #pragma unroll
     for (int t = 1; t <= 3; ++t) load(m0 - t, q[(3 - t) & 3]);
@@ -437,7 +442,7 @@ __global__ void __launch_bounds__(32 * FS_WARPS) k_final_stream(FinalArgs a) {
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     const float *r = q[(j + 3 - t) & 3];
-                    const float hk = a.f.h[e + 2 * t], gk = a.f.g[e + 2 * t];
+                    const float hk = f.h[e + 2 * t], gk = f.g[e + 2 * t];
                     l = __fmaf_rn(hk, r[0], l);
                     l = __fmaf_rn(gk, r[1], l);
                     h = __fmaf_rn(hk, r[2], h);
@@ -459,35 +464,167 @@ __global__ void __launch_bounds__(32 * FS_WARPS) k_final_stream(FinalArgs a) {
                 }
                 float w[2];
 #pragma unroll
-                for (int f = 0; f < 2; ++f) {
+                for (int fi = 0; fi < 2; ++fi) {
                     float v = 0.f;
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
-                        v = __fmaf_rn(a.f.h[f + 2 * t], L[t], v);
-                        v = __fmaf_rn(a.f.g[f + 2 * t], Hh[t], v);
+                        v = __fmaf_rn(f.h[fi + 2 * t], L[t], v);
+                        v = __fmaf_rn(f.g[fi + 2 * t], Hh[t], v);
                     }
-                    w[f] = v;
+                    w[fi] = v;
                 }
                 const int y = 2 * m + e, x = 2 * n;
-                if (out_lane && y < a.H && x < a.W) {
-                    float *o = outp + (long long)y * a.W + x;
-                    const bool two = x + 1 < a.W;
-                    if (a.accumulate) {
-                        o[0] += w[0];
-                        if (two) o[1] += w[1];
-                    } else if (two && ((reinterpret_cast<uintptr_t>(o) & 7u) == 0)) {
-                        *reinterpret_cast<float2 *>(o) = make_float2(w[0], w[1]);
-                    } else {
-                        o[0] = w[0];
-                        if (two) o[1] = w[1];
-                    }
-                }
+                if (out_lane && y < outH && x < outW) epi(y, x, w[0], w[1], x + 1 < outW);
             }
         }
     }
 }
 
+// store (ACC: add) an output pair into a row-major plane of width W
+template <bool ACC>
+struct StoreEpi {
+    float *p;
+    int W;
+    __device__ __forceinline__ void operator()(int y, int x, float w0, float w1, bool two) const {
+        float *o = p + (long long)y * W + x;
+        if (ACC) {
+            o[0] += w0;
+            if (two) o[1] += w1;
+        } else if (two && ((reinterpret_cast<uintptr_t>(o) & 7u) == 0)) {
+            *reinterpret_cast<float2 *>(o) = make_float2(w0, w1);
+        } else {
+            o[0] = w0;
+            if (two) o[1] = w1;
+        }
+    }
+};
+
+// Level 1, residual mode: W cropped to H x W, stored (ACC: added) at res_out[plane].
+template <bool ACC>
+__global__ void __launch_bounds__(32 * FS_WARPS) k_final_stream(FinalArgs a) {
+    const int cg = blockIdx.x * FS_WARPS + (threadIdx.x >> 5);
+    if (cg * FS_COLS >= a.Cc) return;  // warp-uniform
+    const long long off = (long long)blockIdx.z * a.Rc * a.Cc;
+    const float *LL = a.LL ? static_cast<const float *>(a.LL) + off : nullptr;
+    StoreEpi<ACC> epi{a.res_out + (long long)blockIdx.z * a.H * a.W, a.W};
+    stream_synth<false>(LL, static_cast<const float *>(a.LH) + off, static_cast<const float *>(a.HL) + off,
+                        static_cast<const float *>(a.HH) + off, 0, a.Rc, a.Cc, a.f, cg, blockIdx.y * FS_ROWS, a.H,
+                        a.W, epi);
+}
+
+// Levels 2..L: the 2Rc x 2Cc noise LL of the level below (grey with gray3).
+template <bool GRAY3>
+__global__ void __launch_bounds__(32 * FS_WARPS) k_synthesis_stream(SynArgs a) {
+    const int cg = blockIdx.x * FS_WARPS + (threadIdx.x >> 5);
+    if (cg * FS_COLS >= a.Cc) return;  // warp-uniform
+    const long long A = (long long)a.Rc * a.Cc;
+    const long long off = (long long)blockIdx.z * A, doff = GRAY3 ? 3 * off : off;
+    const float *LL = a.LL ? static_cast<const float *>(a.LL) + off : nullptr;
+    StoreEpi<false> epi{static_cast<float *>(a.out) + 4 * off, 2 * a.Cc};
+    stream_synth<GRAY3>(LL, static_cast<const float *>(a.LH) + doff, static_cast<const float *>(a.HL) + doff,
+                        static_cast<const float *>(a.HH) + doff, A, a.Rc, a.Cc, a.f, cg, blockIdx.y * FS_ROWS,
+                        2 * a.Rc, 2 * a.Cc, epi);
+}
+
+// Level 1, PCE mode: X = grey W, Y = K grey(I), and the lane's sums of X,
+// X^2, Y, Y^2 as float-float pairs (no float64 arithmetic per pixel).
+struct PceEpi {
+    float *X, *Y;
+    const float *K, *I;
+    long long hw;
+    int W, C;
+    bool vec;  // W even and every base 8-byte aligned: pairs move as float2
+    float m[4] = {0.f, 0.f, 0.f, 0.f}, mlo[4] = {0.f, 0.f, 0.f, 0.f};
+    __device__ __forceinline__ float2 ld2(const float *p, bool two) const {
+        if (vec && two) return __ldg(reinterpret_cast<const float2 *>(p));
+        return make_float2(__ldg(p), two ? __ldg(p + 1) : 0.f);
+    }
+    __device__ __forceinline__ void st2(float *p, float a, float b, bool two) const {
+        if (vec && two) {
+            *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+        } else {
+            p[0] = a;
+            if (two) p[1] = b;
+        }
+    }
+    __device__ __forceinline__ void operator()(int y, int x, float w0, float w1, bool two) {
+        const long long o = (long long)y * W + x;
+        float2 g = ld2(I + o, two);
+        if (C == 3) {
+            const float2 i1 = ld2(I + hw + o, two), i2 = ld2(I + 2 * hw + o, two);
+            g.x = __fmaf_rn(0.114f, i2.x, __fmaf_rn(0.587f, i1.x, 0.299f * g.x));
+            g.y = __fmaf_rn(0.114f, i2.y, __fmaf_rn(0.587f, i1.y, 0.299f * g.y));
+        }
+        const float2 k = ld2(K + o, two);
+        const float y0 = k.x * g.x, y1 = two ? k.y * g.y : 0.f;
+        if (!two) w1 = 0.f;
+        st2(X + o, w0, w1, two);
+        st2(Y + o, y0, y1, two);
+        ff_add(m[0], mlo[0], w0 + w1);
+        ff_add(m[1], mlo[1], __fmaf_rn(w0, w0, w1 * w1));
+        ff_add(m[2], mlo[2], y0 + y1);
+        ff_add(m[3], mlo[3], __fmaf_rn(y0, y0, y1 * y1));
+    }
+};
+
+template <bool GRAY3>
+__global__ void __launch_bounds__(32 * FS_WARPS, 8) k_final_pce(FinalArgs a) {
+    __shared__ double sh[FS_WARPS][4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cg = blockIdx.x * FS_WARPS + warp;
+    const int z = blockIdx.z;
+    const long long hw = (long long)a.H * a.W;
+    const long long A = (long long)a.Rc * a.Cc;
+    const bool vec = (a.W % 2 == 0) && (((reinterpret_cast<uintptr_t>(a.Xo) | reinterpret_cast<uintptr_t>(a.Yo) |
+                                          reinterpret_cast<uintptr_t>(a.Kq) | reinterpret_cast<uintptr_t>(a.Iq)) &
+                                         7u) == 0) && (a.k_stride % 2 == 0);
+    PceEpi epi{a.Xo + z * hw, a.Yo + z * hw, a.Kq + z * a.k_stride, a.Iq + (long long)z * a.C * hw, hw, a.W, a.C,
+               vec};
+    if (cg * FS_COLS < a.Cc) {  // warp-uniform
+        const long long doff = (GRAY3 ? 3LL : 1LL) * z * A;
+        const float *LL = a.LL ? static_cast<const float *>(a.LL) + z * A : nullptr;
+        stream_synth<GRAY3>(LL, static_cast<const float *>(a.LH) + doff, static_cast<const float *>(a.HL) + doff,
+                            static_cast<const float *>(a.HH) + doff, A, a.Rc, a.Cc, a.f, cg, blockIdx.y * FS_ROWS,
+                            a.H, a.W, epi);
+    }
+    double v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = (double)epi.m[k] + (double)epi.mlo[k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sh[warp][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double t = 0.0;
+        for (int w = 0; w < FS_WARPS; ++w) t += sh[w][threadIdx.x];
+        const long long blk = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+        a.part_m[((long long)z * gridDim.x * gridDim.y + blk) * 4 + threadIdx.x] = t;
+    }
+}
+
+static dim3 stream_grid(int Rc, int Cc, int planes) {
+    const int groups = (Cc + FS_COLS - 1) / FS_COLS;
+    return dim3((unsigned)((groups + FS_WARPS - 1) / FS_WARPS), (unsigned)((Rc + FS_ROWS - 1) / FS_ROWS),
+                (unsigned)planes);
+}
+
+int final_pce_blocks(int Rc, int Cc) {
+    const dim3 g = stream_grid(Rc, Cc, 1);
+    return (int)(g.x * g.y);
+}
+
 cudaError_t launch_synthesis(const SynArgs &a, cudaStream_t st) {
+    if (a.sdt == SB_F32) {
+        if (a.gray3)
+            k_synthesis_stream<true><<<stream_grid(a.Rc, a.Cc, a.P), 32 * FS_WARPS, 0, st>>>(a);
+        else
+            k_synthesis_stream<false><<<stream_grid(a.Rc, a.Cc, a.P), 32 * FS_WARPS, 0, st>>>(a);
+        return cudaGetLastError();
+    }
     dim3 block(32, 8);
     dim3 grid((unsigned)((2 * a.Cc + OT - 1) / OT), (unsigned)((2 * a.Rc + OT - 1) / OT), (unsigned)a.P);
     if (a.sdt == SB_F16)
@@ -525,11 +662,18 @@ cudaError_t launch_final(const FinalArgs &a, bool mle, cudaStream_t st) {
         launch_final_async_mle(a, st);
         return cudaGetLastError();
     }
+    if (a.pce) {  // float32 subbands only (checked by the caller)
+        if (a.C == 3)
+            k_final_pce<true><<<stream_grid(a.Rc, a.Cc, a.G), 32 * FS_WARPS, 0, st>>>(a);
+        else
+            k_final_pce<false><<<stream_grid(a.Rc, a.Cc, a.G), 32 * FS_WARPS, 0, st>>>(a);
+        return cudaGetLastError();
+    }
     if (a.sdt == SB_F32) {
-        const int groups = (a.Cc + FS_COLS - 1) / FS_COLS;
-        dim3 grid((unsigned)((groups + FS_WARPS - 1) / FS_WARPS), (unsigned)((a.Rc + FS_ROWS - 1) / FS_ROWS),
-                  (unsigned)(a.C * a.G));
-        k_final_stream<<<grid, 32 * FS_WARPS, 0, st>>>(a);
+        if (a.accumulate)
+            k_final_stream<true><<<stream_grid(a.Rc, a.Cc, a.C * a.G), 32 * FS_WARPS, 0, st>>>(a);
+        else
+            k_final_stream<false><<<stream_grid(a.Rc, a.Cc, a.C * a.G), 32 * FS_WARPS, 0, st>>>(a);
         return cudaGetLastError();
     }
     if (a.sdt == SB_F16)

@@ -60,6 +60,8 @@ struct SynArgs {
     int Rc, Cc, P;     // coefficient dims; output is 2Rc x 2Cc
     void *out;         // [P][2Rc][2Cc]
     int sdt;
+    int gray3;         // float32 only: output plane z synthesises 0.299/0.587/0.114 of detail
+                       // planes 3z, 3z+1, 3z+2 (LL is already grey: plane z)
     Filt f;
 };
 struct FinalArgs {
@@ -76,8 +78,19 @@ struct FinalArgs {
     float *num, *den;  // MLE mode: [C][H][W]
     const GroupDesc *gd;    // multi-camera MLE: group -> camera (groups of a camera are consecutive)
     const CamDesc *cams;    // multi-camera MLE: per-camera num/den
+    // PCE mode (float32 subbands): per query z, X = grey W (the grey synthesis
+    // of the detail planes, as in gray3), Y = K grey(I); block partial sums of
+    // X, X^2, Y, Y^2 (float64) at part_m[z][block][4]
+    int pce;
+    const float *Kq;        // [H][W], or one per query at stride k_stride
+    long long k_stride;
+    const float *Iq;        // query images [G][C][H][W]
+    float *Xo, *Yo;         // [G][H][W]
+    double *part_m;
     Filt f;
 };
+// blocks per query of the PCE-mode level-1 kernel (its partial-sum count)
+int final_pce_blocks(int Rc, int Cc);
 cudaError_t launch_synthesis(const SynArgs &a, cudaStream_t st);
 cudaError_t launch_final(const FinalArgs &a, bool mle, cudaStream_t st);
 

@@ -249,6 +249,10 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
             CU(launch_shrink(s, st));
         }
     }
+    // PCE mode with three channels: the synthesis is linear, so levels L..1
+    // synthesise the grey combination of the channels' noise, one plane per image
+    const bool grey = fin.pce && fin.C == 3;
+    const int Ps = grey ? P / 3 : P;
     for (int l = L; l >= 2; --l) {
         const long long A = (long long)(Hp >> l) * (Wp >> l);
         SynArgs y{};
@@ -259,11 +263,12 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
         y.sdt = sdt;
         y.Rc = Hp >> l;
         y.Cc = Wp >> l;
-        y.P = P;
+        y.P = Ps;
+        y.gray3 = grey;
         y.out = SB(lo.Rn[l - 1], 0, 0);
         y.f = ctx->filt;
         {
-            Launch t(ctx, "synthesis", st, 1, (double)P * A * es * (y.LL ? 4 : 3) + (double)P * A * 4 * es);
+            Launch t(ctx, "synthesis", st, 1, (double)P * A * es * 3 + (double)Ps * A * es * (y.LL ? 5 : 4));
             CU(launch_synthesis(y, st));
         }
     }
@@ -280,10 +285,11 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
     fin.W = W;
     fin.f = ctx->filt;
     {
-        const double cin = (double)P * A1 * es * (fin.LL ? 4 : 3);
+        const double cin = (double)P * A1 * es * 3 + (fin.LL ? (double)Ps * A1 * es : 0.0);
         const double io = mle ? (double)P * H * W * 4 + (double)fin.C * H * W * 16 * (prm.compensated ? 2 : 1)
-                              : (double)P * H * W * 4;
-        Launch t(ctx, mle ? "final_mle" : "final_residual", st, 1, cin + io * (fin.accumulate ? 2 : 1));
+                        : fin.pce ? (double)fin.G * H * W * 4 * (fin.C + 3)
+                                  : (double)P * H * W * 4 * (fin.accumulate ? 2 : 1);
+        Launch t(ctx, mle ? "final_mle" : fin.pce ? "final_pce" : "final_residual", st, 1, cin + io);
         CU(launch_final(fin, mle, st));
     }
     return PRNU_OK;
@@ -835,30 +841,17 @@ prnu_status prnu_fingerprint_finalize(prnu_ctx *ctx, const float *num, const flo
 }
 
 namespace {
-prnu_status pce_impl(prnu_ctx *ctx, const float *K, long long k_stride, const float *residual_q, const float *img_q,
-                     int n, int H, int W, int C, int nbhd, double *pce_out, double *ncc_out, int *peak_yx, void *ws,
-                     size_t ws_bytes, void *stream) {
-    if (!ctx || !K || !residual_q || !img_q || !pce_out) return fail(PRNU_EINVAL, "NULL argument");
-    if (n < 1) return fail(PRNU_EINVAL, "n must be >= 1");
+// From X, Y in f.real (X_0..X_{n-1}, then Y_0..Y_{n-1}) and the moment
+// partials (nbm per query at part_m): cross-correlation, energy, PCE / NCC
+// / peak to the host.  Synchronises the stream.
+prnu_status pce_finish(prnu_ctx *ctx, int n, int H, int W, int nbhd, const FftLayout &f, char *b,
+                       const double *part_m, int nbm, double *pce_out, double *ncc_out, int *peak_yx,
+                       cudaStream_t st) {
     prnu_status s;
-    if ((s = check_geometry(H, W, C)) != PRNU_OK) return s;
-    if (nbhd < 1 || nbhd % 2 == 0 || nbhd > H || nbhd > W) return fail(PRNU_EINVAL, "nbhd must be odd and <= min(H, W)");
-    DeviceGuard g(ctx->device);
-    FftLayout f;
-    if ((s = fft_layout(ctx, H, W, n, &f)) != PRNU_OK) return s;
-    if ((s = check_ws(ws, ws_bytes, f.end)) != PRNU_OK) return s;
-    cudaStream_t st = S(stream);
-    char *b = static_cast<char *>(ws);
     const long long hw = (long long)H * W;
     const long long nh = (long long)H * (W / 2 + 1);
-    float *X = reinterpret_cast<float *>(b + f.real);  // X_0..X_{n-1}, then Y_0..Y_{n-1}
-    float *Y = X + n * hw;
+    float *X = reinterpret_cast<float *>(b + f.real);
     cufftComplex *FX = reinterpret_cast<cufftComplex *>(b + f.cplx);
-    {
-        Launch t(ctx, "pce_prep", st, 1, (double)n * hw * 4 * (2 * C + 2) + (double)hw * 4);
-        CU(launch_pce_prep(K, k_stride, residual_q, img_q, hw, C, n, f.nbm, X, Y,
-                           reinterpret_cast<double *>(b + f.pm), st));
-    }
     cufftHandle r2c, c2r;
     size_t w1, w2;
     if ((s = get_plan(ctx, H, W, CUFFT_R2C, 2 * n, &r2c, &w1)) != PRNU_OK) return s;
@@ -882,8 +875,8 @@ prnu_status pce_impl(prnu_ctx *ctx, const float *K, long long k_stride, const fl
     {
         Launch t(ctx, "pce_reduce", st, 2, (double)n * hw * 4);
         CU(launch_pce_reduce(X, H, W, nbhd / 2, n, f.nb, reinterpret_cast<double *>(b + f.pe),
-                             reinterpret_cast<float *>(b + f.pv), reinterpret_cast<long long *>(b + f.pi),
-                             reinterpret_cast<double *>(b + f.pm), f.nbm, b + f.scal, st));
+                             reinterpret_cast<float *>(b + f.pv), reinterpret_cast<long long *>(b + f.pi), part_m,
+                             nbm, b + f.scal, st));
     }
     std::vector<unsigned char> host((size_t)n * pce_scalars_bytes());
     CU(cudaMemcpyAsync(host.data(), b + f.scal, host.size(), cudaMemcpyDeviceToHost, st));
@@ -909,7 +902,108 @@ prnu_status pce_impl(prnu_ctx *ctx, const float *K, long long k_stride, const fl
     return PRNU_OK;
 }
 
+prnu_status pce_impl(prnu_ctx *ctx, const float *K, long long k_stride, const float *residual_q, const float *img_q,
+                     int n, int H, int W, int C, int nbhd, double *pce_out, double *ncc_out, int *peak_yx, void *ws,
+                     size_t ws_bytes, void *stream) {
+    if (!ctx || !K || !residual_q || !img_q || !pce_out) return fail(PRNU_EINVAL, "NULL argument");
+    if (n < 1) return fail(PRNU_EINVAL, "n must be >= 1");
+    prnu_status s;
+    if ((s = check_geometry(H, W, C)) != PRNU_OK) return s;
+    if (nbhd < 1 || nbhd % 2 == 0 || nbhd > H || nbhd > W) return fail(PRNU_EINVAL, "nbhd must be odd and <= min(H, W)");
+    DeviceGuard g(ctx->device);
+    FftLayout f;
+    if ((s = fft_layout(ctx, H, W, n, &f)) != PRNU_OK) return s;
+    if ((s = check_ws(ws, ws_bytes, f.end)) != PRNU_OK) return s;
+    cudaStream_t st = S(stream);
+    char *b = static_cast<char *>(ws);
+    const long long hw = (long long)H * W;
+    float *X = reinterpret_cast<float *>(b + f.real);  // X_0..X_{n-1}, then Y_0..Y_{n-1}
+    float *Y = X + n * hw;
+    {
+        Launch t(ctx, "pce_prep", st, 1, (double)n * hw * 4 * (2 * C + 2) + (double)hw * 4);
+        CU(launch_pce_prep(K, k_stride, residual_q, img_q, hw, C, n, f.nbm, X, Y,
+                           reinterpret_cast<double *>(b + f.pm), st));
+    }
+    return pce_finish(ctx, n, H, W, nbhd, f, b, reinterpret_cast<double *>(b + f.pm), f.nbm, pce_out, ncc_out,
+                      peak_yx, st);
+}
+
+// Workspace of prnu_pce_match_images: the denoise layout of n*C planes, then
+// the FFT layout of n queries, then the moment partials of the fused kernel.
+struct PceImagesLayout {
+    Layout den;
+    FftLayout fft;
+    size_t fft_off = 0, pm = 0, end = 0;
+    int nbm = 0;
+};
+
+prnu_status pce_images_layout(prnu_ctx *ctx, int H, int W, int C, const prnu_params *params, int n,
+                              PceImagesLayout *out) {
+    PceImagesLayout p;
+    prnu_status s;
+    p.den = make_layout(H, W, (long long)n * C, params->levels, false, PRNU_DTYPE_F32);
+    p.fft_off = align_up(p.den.end, kAlign);
+    if ((s = fft_layout(ctx, H, W, n, &p.fft)) != PRNU_OK) return s;
+    const int L = params->levels;
+    p.nbm = final_pce_blocks(padded(H, L) / 2, padded(W, L) / 2);
+    p.pm = align_up(p.fft_off + p.fft.end, kAlign);
+    p.end = p.pm + (size_t)n * p.nbm * 4 * sizeof(double);
+    *out = p;
+    return PRNU_OK;
+}
+
 }  // namespace
+
+prnu_status prnu_workspace_size_pce_images(prnu_ctx *ctx, int H, int W, int C, const prnu_params *params, int n,
+                                           size_t *bytes) {
+    if (!ctx || !bytes) return fail(PRNU_EINVAL, "NULL argument");
+    if (n < 1) return fail(PRNU_EINVAL, "n must be >= 1");
+    prnu_status s;
+    if ((s = check_geometry(H, W, C)) != PRNU_OK) return s;
+    if ((s = check_params(params, H, W, nullptr)) != PRNU_OK) return s;
+    DeviceGuard g(ctx->device);
+    PceImagesLayout p;
+    if ((s = pce_images_layout(ctx, H, W, C, params, n, &p)) != PRNU_OK) return s;
+    *bytes = p.end;
+    return PRNU_OK;
+}
+
+prnu_status prnu_pce_match_images(prnu_ctx *ctx, const float *K, const float *img_q, int n, int H, int W, int C,
+                                  const prnu_params *params, int nbhd, double *pce_out, double *ncc_out,
+                                  int *peak_yx, void *ws, size_t ws_bytes, void *stream) {
+    if (!ctx || !K || !img_q || !pce_out) return fail(PRNU_EINVAL, "NULL argument");
+    if (n < 1) return fail(PRNU_EINVAL, "n must be >= 1");
+    prnu_status s;
+    Win win;
+    if ((s = check_geometry(H, W, C)) != PRNU_OK) return s;
+    if ((s = check_params(params, H, W, &win)) != PRNU_OK) return s;
+    if (params->dtype != PRNU_DTYPE_F32)
+        return fail(PRNU_EUNSUPPORTED, "prnu_pce_match_images needs float32 subbands (use prnu_denoise_residual_batch "
+                                       "and prnu_pce_match_batch)");
+    if (nbhd < 1 || nbhd % 2 == 0 || nbhd > H || nbhd > W) return fail(PRNU_EINVAL, "nbhd must be odd and <= min(H, W)");
+    DeviceGuard g(ctx->device);
+    PceImagesLayout p;
+    if ((s = pce_images_layout(ctx, H, W, C, params, n, &p)) != PRNU_OK) return s;
+    if ((s = check_ws(ws, ws_bytes, p.end)) != PRNU_OK) return s;
+    cudaStream_t st = S(stream);
+    char *b = static_cast<char *>(ws);
+    const long long hw = (long long)H * W;
+    float *X = reinterpret_cast<float *>(b + p.fft_off + p.fft.real);
+    FinalArgs fin{};
+    fin.C = C;
+    fin.G = n;
+    fin.sc = PlaneScale{1, 1, 0, C, nullptr};
+    fin.pce = 1;
+    fin.Kq = K;
+    fin.k_stride = 0;
+    fin.Iq = img_q;
+    fin.Xo = X;
+    fin.Yo = X + n * hw;
+    fin.part_m = reinterpret_cast<double *>(b + p.pm);
+    if ((s = run_denoise(ctx, img_q, H, W, n * C, *params, win, fin.sc, 0, b, p.den, fin, false, st)) != PRNU_OK)
+        return s;
+    return pce_finish(ctx, n, H, W, nbhd, p.fft, b + p.fft_off, fin.part_m, p.nbm, pce_out, ncc_out, peak_yx, st);
+}
 
 prnu_status prnu_pce_match_batch(prnu_ctx *ctx, const float *K, const float *residual_q, const float *img_q, int n,
                                  int H, int W, int C, int nbhd, double *pce_out, double *ncc_out, int *peak_yx,

@@ -27,7 +27,8 @@ EXPORTS = (
     "prnu_workspace_size_multi", "prnu_fingerprint_accumulate_multi", "prnu_autotune",
     "prnu_autotune_set", "prnu_sda_weighted", "prnu_sda_weighted_backward", "prnu_workspace_size_grad",
     "prnu_denoise_residual_ckpt", "prnu_denoise_residual_backward", "prnu_mle_images", "prnu_mle_images_backward",
-    "prnu_workspace_size_pce_backward", "prnu_pce_backward",
+    "prnu_workspace_size_pce_backward", "prnu_pce_backward", "prnu_workspace_size_pce_images",
+    "prnu_pce_match_images",
 )
 
 
@@ -94,6 +95,9 @@ def lib() -> ctypes.CDLL:
                 "prnu_autotune": [_vp, _i, _i, _i, _pp, _i, _vp, _sz, _vp, ctypes.POINTER(_i),
                                   ctypes.POINTER(ctypes.c_float)],
                 "prnu_autotune_set": [_vp, _i, _i, _pp, _i],
+                "prnu_workspace_size_pce_images": [_vp, _i, _i, _i, _pp, _i, ctypes.POINTER(_sz)],
+                "prnu_pce_match_images": [_vp, _vp, _vp, _i, _i, _i, _i, _pp, _i, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i), _vp, _sz, _vp],
                 "prnu_sda_weighted": [_vp, _vp, _i, _i, _i, _i, _sz, _sz, _i, _vp, _vp, _vp],
                 "prnu_sda_weighted_backward": [_vp, _vp, _i, _i, _i, _i, _sz, _sz, _i, _vp, _vp, _vp, _sz, _vp],
                 "prnu_workspace_size_grad": [_vp, _i, _i, _i, _pp, _i, ctypes.POINTER(_sz), ctypes.POINTER(_sz)],
@@ -207,6 +211,21 @@ def prnu_pce_match_batch(ctx, K, residual_q, img_q, n, H, W, C, nbhd, ws, ws_byt
     peak = (ctypes.c_int * (2 * n))()
     _check(lib().prnu_pce_match_batch(ctx, K, residual_q, img_q, n, H, W, C, nbhd, pce, ncc, peak, ws, ws_bytes,
                                       stream), ctx)
+    return [(pce[i], ncc[i], (peak[2 * i], peak[2 * i + 1])) for i in range(n)]
+
+
+def prnu_workspace_size_pce_images(ctx, H, W, C, params, n):
+    b = _sz()
+    _check(lib().prnu_workspace_size_pce_images(ctx, H, W, C, ctypes.byref(params), n, ctypes.byref(b)), ctx)
+    return b.value
+
+
+def prnu_pce_match_images(ctx, K, img_q, n, H, W, C, params, nbhd, ws, ws_bytes, stream):
+    pce = (ctypes.c_double * n)()
+    ncc = (ctypes.c_double * n)()
+    peak = (ctypes.c_int * (2 * n))()
+    _check(lib().prnu_pce_match_images(ctx, K, img_q, n, H, W, C, ctypes.byref(params), nbhd, pce, ncc, peak, ws,
+                                       ws_bytes, stream), ctx)
     return [(pce[i], ncc[i], (peak[2 * i], peak[2 * i + 1])) for i in range(n)]
 
 
@@ -375,6 +394,18 @@ class Context:
         return prnu_pce_match_batch(self.ctx, K.data_ptr(), residual_q.contiguous().data_ptr(),
                                     img_q.contiguous().data_ptr(), n, H, W, C, nbhd, ws.data_ptr(), ws.numel(),
                                     self._stream())
+
+    def pce_match_images(self, K, img_q, nbhd: int = 11, params=None):
+        """K [H, W]; query images [n, C, H, W] -> [(pce, ncc, (dy, dx))] * n, the
+        residuals computed inside without being stored."""
+        params = params or default_params()
+        n, C, H, W = img_q.shape
+        K = K.reshape(H, W).contiguous()
+        img_q = img_q.contiguous()
+        nb = prnu_workspace_size_pce_images(self.ctx, H, W, C, params, n)
+        ws = self.workspace(nb)
+        return prnu_pce_match_images(self.ctx, K.data_ptr(), img_q.data_ptr(), n, H, W, C, params, nbhd,
+                                     ws.data_ptr(), ws.numel(), self._stream())
 
     def pce_match_pairs(self, K, residual_q, img_q, nbhd: int = 11):
         """K [n, H, W]; residual_q, img_q [n, C, H, W]: query i against fingerprint i."""

@@ -258,3 +258,30 @@ def test_residual_of_an_unaligned_image_view(ctx):
     view = buf[1:].view(1, 64, 96)
     got = ctx.denoise_residual(view).cpu().numpy()
     assert np.abs(got - O.residual(img.astype(np.float64))).max() <= RES_TOL
+
+
+@pytest.mark.parametrize("H,W,C,n", [(1080, 1920, 3, 4), (200, 328, 3, 3), (97, 250, 1, 2), (256, 256, 1, 1)])
+def test_pce_from_images_matches_two_step_path_and_oracle(ctx, H, W, C, n):
+    """prnu_pce_match_images (residuals never stored; grey synthesis of the
+    combined noise for C = 3) against residual + pce_match_batch and, for the
+    first query, the oracle."""
+    cam = synth.Camera(H=H, W=W, C=C, camera_id=77)
+    fr = synth.frames(cam, 16, device="cuda")
+    num = torch.zeros((C, H, W), device="cuda")
+    den = torch.zeros_like(num)
+    ctx.fingerprint_accumulate(fr, 8, num, den)
+    K = ctx.fingerprint_finalize(num, den, P.PRNU_TO_GRAY if C == 3 else 0)[0].clone()
+    qf = torch.cat([synth.frames(cam, n - 1, stream=1, device="cuda"),
+                    synth.frames(synth.foreign(cam), 1, stream=1, device="cuda")])
+    q = ctx.sda_average(qf, 1)
+    fused = ctx.pce_match_images(K, q)
+    two = ctx.pce_match_batch(K, ctx.denoise_residual_batch(q), q)
+    for (p1, c1, k1), (p2, c2, k2) in zip(fused, two):
+        assert abs(p1 - p2) <= 1e-4 * max(abs(p2), 1.0)
+        assert abs(c1 - c2) <= 1e-5 * max(abs(c2), 1e-3)
+        assert k1 == k2 or abs(p2) < 60
+    onum, oden = O.fingerprint_accumulate(fr.cpu().numpy(), 8)
+    oK = O.fingerprint_finalize(onum, oden, O.TO_GRAY if C == 3 else 0)[0]
+    qh = O.sda_average(qf[:1].cpu().numpy(), 1)[0]
+    opce = O.pce_match(oK, O.to_gray(O.residual(qh)), O.to_gray(qh)).pce
+    assert abs(fused[0][0] - opce) <= 1e-3 * abs(opce)
