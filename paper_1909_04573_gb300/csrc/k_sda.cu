@@ -26,6 +26,15 @@ __device__ __forceinline__ void acc_word(uint32_t v, uint32_t &ev, uint32_t &od)
     od += (v >> 8) & 0x00FF00FFu;
 }
 
+// Frames ahead whose row segment thread 0 of a block requests into L2 with a
+// bulk prefetch (fire and forget: no completion, no wait), so that the
+// block's 16-byte loads find their data in L2.  Sizes are rounded down to 16
+// bytes, so a prefetch never reaches past the segment.
+constexpr int kPrefetch = 8;
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <int C, int SEGPX, bool MULTI>
 __global__ void __launch_bounds__(SEGPX * C / 16) k_sda_sum(SdaArgs a) {
     constexpr int NT = SEGPX * C / 16;  // threads = 16-byte chunks per segment
@@ -66,12 +75,16 @@ __global__ void __launch_bounds__(SEGPX * C / 16) k_sda_sum(SdaArgs a) {
         if (nb > 0) {
             const uint8_t *base = fr + (long long)y * rpitch + b0;
             if (al16 && nb == 16) {
+                // thread 0 asks L2 for the segment kPrefetch frames ahead
+                const uint8_t *seg = fr + (long long)y * rpitch + (long long)x0 * C;
+                const unsigned segb = (unsigned)(min(SEGPX * C, rowbytes - x0 * C) & ~15);
                 for (int jb = j0; jb < j1; jb += 256) {
                     const int je = min(j1, jb + 256);
                     uint32_t ev[4] = {0, 0, 0, 0}, od[4] = {0, 0, 0, 0};
                     const uint8_t *p = base + (long long)jb * fstride;
 #pragma unroll 4
                     for (int j = jb; j < je; ++j, p += fstride) {
+                        if (k == 0 && j + kPrefetch < j1 && segb) prefetch_l2(seg + (long long)(j + kPrefetch) * fstride, segb);
                         const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(p));
                         acc_word(v.x, ev[0], od[0]);
                         acc_word(v.y, ev[1], od[1]);
@@ -152,8 +165,11 @@ __global__ void __launch_bounds__(SEGPX * C / 8) k_sda_sum_f16(SdaArgs a) {
         if (ne > 0) {
             const uint8_t *base = fr + (long long)y * rpitch + 2LL * e0;
             if (al16 && ne == 8) {
+                const uint8_t *seg = fr + (long long)y * rpitch + 2LL * x0 * C;
+                const unsigned segb = (unsigned)(min(SEGPX * C, rowvals - x0 * C) * 2 & ~15);
 #pragma unroll 4
                 for (int j = j0; j < j1; ++j) {
+                    if (k == 0 && j + kPrefetch < j1 && segb) prefetch_l2(seg + (long long)(j + kPrefetch) * fstride, segb);
                     const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(base + (long long)j * fstride));
                     const __half2 *h2 = reinterpret_cast<const __half2 *>(&v);
 #pragma unroll
@@ -195,6 +211,7 @@ cudaError_t launch_put_desc(const PassDesc &pd, PassDesc *dst, cudaStream_t st) 
     k_put_desc<<<1, 256, 0, st>>>(pd, dst);
     return cudaGetLastError();
 }
+
 
 cudaError_t launch_sda(const SdaArgs &a, int num_sms, cudaStream_t st) {
     if (a.frame_half) {

@@ -52,6 +52,18 @@ def test_sda_average_bit_exact(ctx, H, W, C, m, d):
     np.testing.assert_array_equal(got, ref)
 
 
+@pytest.mark.parametrize("H,W,C,m,d", [(64, 80, 3, 600, 300), (40, 52, 3, 70, 9), (96, 100, 3, 40, 40), (17, 35, 3, 30, 7),
+                                       (1080, 1920, 3, 12, 5)])
+def test_sda_long_groups_and_segment_tails(ctx, H, W, C, m, d):
+    """Row segments that end mid-chunk, groups longer than 256 frames (the
+    16-bit lanes are flushed), ragged last groups, L2 prefetches that reach
+    the last frame; exact sums (as means, bit for bit)."""
+    fr = np.random.default_rng(H * W * C + m).integers(0, 256, size=(m, H, W, C), dtype=np.uint8)
+    got = ctx.sda_average(_dev(fr), d).cpu().numpy()
+    ref = O.sda_average(fr, d).astype(np.float32)
+    np.testing.assert_array_equal(got, ref)
+
+
 def test_sda_average_strided_frames(ctx):
     rng = np.random.default_rng(5)
     big = rng.integers(0, 256, size=(9, 40, 70, 3), dtype=np.uint8)
