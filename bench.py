@@ -78,9 +78,9 @@ ALU_OPS_PER_BYTE = {"shrink": 41.0 / 8.0}
 FP32_LANES_PER_SM = 128
 
 # profiler name -> kernel symbol in the ncu captures (profiles/)
-NCU_NAME = {"shrink": "k_shrink<1, 0>", "sda_sum": "k_sda_sum<3, 1024>", "analysis_l1": "k_analysis_stream<1>",
-            "analysis": "k_analysis<0>", "synthesis": "k_synthesis", "final_mle": "k_final<1>",
-            "final_residual": "k_final<0>", "pce_prep": "k_pce_prep"}
+NCU_NAME = {"shrink": "k_shrink_x2<0, float>", "sda_sum": "k_sda_sum<3, 1024, 0>",
+            "analysis_l1": "k_analysis_stream<1, float, 32, 2>", "analysis": "k_analysis<0, float>",
+            "synthesis": "k_synthesis_stream<0>", "final_mle": "k_final_async<0>", "final_pce": "k_final_pce<1>"}
 
 def dram_traffic(kernel_symbol):
     """DRAM bytes per launch of a kernel from the committed ncu capture, or
@@ -324,11 +324,11 @@ def precision_config(args, rank, world, local):
 
 # ----------------------------------------------------------- depth study --
 def depth_config(args, rank, world, local):
-    """Synthetic analogue of the paper's SDA-depth experiment (Sec. V-C): per
+    """Synthetic analogue of the paper's SDA-depth experiment (Sec. IV-C): per
     camera 50 frames give fingerprints at d = 1, 2, 5, 10, 25, 50 (50 .. 1
     denoise calls); 8 queries per camera are matched block-wise (disjoint
-    500 x 500 blocks, Sec. V-A) against their own camera's fingerprint (true
-    cases) and the next camera's (false cases); PCE threshold 60 (Sec. V).
+    500 x 500 blocks, Sec. IV-A) against their own camera's fingerprint (true
+    cases) and the next camera's (false cases); PCE threshold 60 (Sec. IV).
     Flat scenes (low-pass sigma 8 px) against textured ones (sigma 1.5 px)."""
     import numpy as np
     import torch

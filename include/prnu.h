@@ -61,7 +61,7 @@ typedef enum {
 #define PRNU_FRAMES_F16 1
 
 /* Denoiser parameters.  The paper names the wavelet denoiser of Mihcak et
- * al. only by citation (Sec. IV-A, Sec. V); these are the build's reading:
+ * al. only by citation (Sec. III-A, Sec. IV); these are the build's reading:
  * orthonormal periodised 8-tap Daubechies DWT, `levels` levels, local
  * variance = min over the odd windows of the periodic box mean of c^2,
  * var = max(0, min - sigma0^2), noise coefficient c*sigma0^2/(var+sigma0^2). */
@@ -112,7 +112,7 @@ prnu_status prnu_workspace_size(prnu_ctx *ctx, int H, int W, int C, const prnu_p
 prnu_status prnu_workspace_size_host(prnu_ctx *ctx, int H, int W, int C, int d, const prnu_params *params,
                                      int groups_per_pass, size_t *bytes);
 
-/* SDA frames, Sec. IV-B (definition of I_i^SDA): group i holds frames
+/* SDA frames, Sec. III-B (definition of I_i^SDA): group i holds frames
  * i*d .. min((i+1)*d, m)-1 and its SDA frame is their arithmetic mean (a
  * ragged last group is the mean of the frames it holds).
  * frames: device uint8 [m][H][W][C] (strides in bytes).
@@ -121,7 +121,7 @@ prnu_status prnu_workspace_size_host(prnu_ctx *ctx, int H, int W, int C, int d, 
 prnu_status prnu_sda_average(prnu_ctx *ctx, const uint8_t *frames, int m, int H, int W, int C,
                              size_t frame_stride, size_t row_pitch, int d, float *sda_out, void *stream);
 
-/* Noise residual, Sec. III-A: W = I - F(I), with F the wavelet denoiser of
+/* Noise residual, Sec. II-A: W = I - F(I), with F the wavelet denoiser of
  * `params`, computed as the inverse DWT of the shrunk-away (noise) detail
  * coefficients of the mirror-padded image, cropped back to H x W.
  * img, residual_out: device float32 [C][H][W] (may not alias). */
@@ -129,7 +129,7 @@ prnu_status prnu_denoise_residual(prnu_ctx *ctx, const float *img, int H, int W,
                                   const prnu_params *params, float *residual_out,
                                   void *ws, size_t ws_bytes, void *stream);
 
-/* Batched residuals, Sec. III-A: n independent images img [n][C][H][W] ->
+/* Batched residuals, Sec. II-A: n independent images img [n][C][H][W] ->
  * residual_out [n][C][H][W] in one pass of the kernels (same semantics as n
  * calls of prnu_denoise_residual). */
 prnu_status prnu_denoise_residual_batch(prnu_ctx *ctx, const float *img, int n, int H, int W, int C,
@@ -156,8 +156,8 @@ prnu_status prnu_denoise_residual_batch(prnu_ctx *ctx, const float *img, int n, 
 prnu_status prnu_denoise_residual_static(prnu_ctx *ctx, const float *img, int H, int W, int C,
                                          const prnu_params *params, float *residual_out, void *stream);
 
-/* MLE fingerprint sums, Sec. IV-A (K-hat = sum W_i I_i / sum I_i^2) over
- * the SDA frames of Sec. IV-B (d = 1 is the conventional per-frame
+/* MLE fingerprint sums, Sec. III-A (K-hat = sum W_i I_i / sum I_i^2) over
+ * the SDA frames of Sec. III-B (d = 1 is the conventional per-frame
  * estimator): for every group i, I_i = its SDA frame, W_i = I_i - F(I_i), and
  *     num += W_i * I_i,   den += I_i * I_i   (elementwise, per channel).
  * frames: device uint8 [m][H][W][C]; num, den: device float32 [C][H][W],
@@ -196,7 +196,7 @@ typedef struct {
 prnu_status prnu_workspace_size_multi(prnu_ctx *ctx, const prnu_camera *cams, int ncams, const prnu_params *params,
                                       int groups_per_pass, size_t *bytes);
 
-/* MLE fingerprint sums (Sec. IV-A / IV-B) of many cameras with uneven frame
+/* MLE fingerprint sums (Sec. III-A / III-B) of many cameras with uneven frame
  * counts, resolutions and SDA group sizes in one call: cameras are grouped by
  * geometry and their groups packed into passes that mix cameras (each pass is
  * one launch of every kernel of the pipeline, with a per-group table of frame
@@ -207,7 +207,7 @@ prnu_status prnu_workspace_size_multi(prnu_ctx *ctx, const prnu_camera *cams, in
 prnu_status prnu_fingerprint_accumulate_multi(prnu_ctx *ctx, const prnu_camera *cams, int ncams,
                                               const prnu_params *params, void *ws, size_t ws_bytes, void *stream);
 
-/* Fingerprint from the MLE sums, Sec. IV-A: K = num/den (division in
+/* Fingerprint from the MLE sums, Sec. III-A: K = num/den (division in
  * float64; K = 0 where den == 0), then the optional literature steps named by
  * `flags` (not defined in the paper): PRNU_TO_GRAY, PRNU_ZERO_MEAN,
  * PRNU_WIENER_DFT, applied in that order.
@@ -217,7 +217,7 @@ prnu_status prnu_fingerprint_finalize(prnu_ctx *ctx, const float *num, const flo
                                       unsigned flags, const prnu_params *params, float *K_out,
                                       void *ws, size_t ws_bytes, void *stream);
 
-/* Peak-to-correlation energy of a query against a fingerprint (Sec. V uses
+/* Peak-to-correlation energy of a query against a fingerprint (Sec. IV uses
  * PCE with threshold 60; the paper defines it only by citation).  Reading:
  * X = W_q - mean(W_q), Y = K*I_q - mean(K*I_q) (grey planes; C == 3 inputs
  * are converted with the 0.299/0.587/0.114 weights), C(s) = sum_x X(x)
@@ -242,7 +242,7 @@ prnu_status prnu_pce_match_batch(prnu_ctx *ctx, const float *K, const float *res
 
 /* PCE of n (fingerprint, query) pairs, each query against its own grey
  * fingerprint plane: K is device float32 [n][H][W]; otherwise as
- * prnu_pce_match_batch.  Used for block-wise matching (Sec. V: fingerprints
+ * prnu_pce_match_batch.  Used for block-wise matching (Sec. IV: fingerprints
  * split into disjoint 500 x 500 blocks, each correlated with the same block of
  * the query) and for matrices of fingerprints against queries. */
 prnu_status prnu_pce_match_pairs(prnu_ctx *ctx, const float *K, const float *residual_q, const float *img_q, int n,
@@ -265,7 +265,7 @@ prnu_status prnu_pce_match_images(prnu_ctx *ctx, const float *K, const float *im
                                   int *peak_yx, void *ws, size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------------------------
- * Differentiation.  The chain of Sec. IV-A / IV-B with the SDA weights made
+ * Differentiation.  The chain of Sec. III-A / III-B with the SDA weights made
  * free (the paper's SDA frame is the equal-weight case w_j = 1/d) and sigma0
  * differentiable:
  *   S_i = sum_{j in group i} w_j I_j,   W_i = residual(S_i; sigma0),
@@ -308,7 +308,7 @@ prnu_status prnu_denoise_residual_backward(prnu_ctx *ctx, const float *ckpt, int
                                            const prnu_params *params, const float *g_residual, float *g_img,
                                            double *g_sigma0, void *ws, size_t ws_bytes, void *stream);
 
-/* MLE fingerprint of n residual/image pairs ([n][C][H][W]), Sec. IV-A:
+/* MLE fingerprint of n residual/image pairs ([n][C][H][W]), Sec. III-A:
  * num = sum W S, den = sum S^2 ([C][H][W], written), K = num/den (0 where
  * den == 0): [C][H][W], or [H][W] grey (0.299/0.587/0.114) with gray = 1. */
 prnu_status prnu_mle_images(prnu_ctx *ctx, const float *residual, const float *img, int n, int H, int W, int C,

@@ -5,12 +5,12 @@ never by the CUDA product path.
 
 The chain, for one camera (all steps of the extraction method, with the SDA
 weights made free parameters):
-  S_i = sum_{j in group i} w_j I_j      Sec. IV-B (w_j = 1/d gives the SDA frame)
-  W_i = residual(S_i; sigma0)           Sec. III-A / IV-A, noise form of the
+  S_i = sum_{j in group i} w_j I_j      Sec. III-B (w_j = 1/d gives the SDA frame)
+  W_i = residual(S_i; sigma0)           Sec. II-A / III-A, noise form of the
                                         wavelet denoiser (IDWT of the shrunk
                                         detail coefficients' noise part)
-  K   = sum_i W_i S_i / sum_i S_i^2     Sec. IV-A (MLE), grey for C = 3
-  PCE of each query (W_q = residual(I_q; sigma0), I_q) against K   Sec. V
+  K   = sum_i W_i S_i / sum_i S_i^2     Sec. III-A (MLE), grey for C = 3
+  PCE of each query (W_q = residual(I_q; sigma0), I_q) against K   Sec. IV
 Every function below restates one step's forward in the order of the method
 and its exact derivative; the DWT levels are the oracle's own dwt2_level /
 idwt2_level, whose orthonormality (the transpose of one is the other) is pinned
@@ -26,7 +26,7 @@ from . import pipeline as P
 
 
 # --------------------------------------------------------------------------
-# weighted SDA frames (Sec. IV-B with free per-frame weights)
+# weighted SDA frames (Sec. III-B with free per-frame weights)
 # --------------------------------------------------------------------------
 def sda_weighted(frames: np.ndarray, w: np.ndarray, d: int) -> np.ndarray:
     """uint8 frames [m, H, W, C] (or [m, H, W]), weights [m] -> S [g, C, H, W]:
@@ -51,7 +51,7 @@ def sda_weighted_vjp(frames: np.ndarray, d: int, gS: np.ndarray) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
-# local-variance Wiener shrink, noise part (denoiser of Sec. IV-A / V)
+# local-variance Wiener shrink, noise part (denoiser of Sec. III-A / IV)
 # --------------------------------------------------------------------------
 def _box_sum(a: np.ndarray, w: int) -> np.ndarray:
     """Periodic w x w box sum centred on each sample."""
@@ -94,7 +94,7 @@ def shrink_vjp(cache, gn: np.ndarray):
 
 
 # --------------------------------------------------------------------------
-# residual W = IDWT(0, noise(details(pad(S))))[:H, :W]   (Sec. III-A)
+# residual W = IDWT(0, noise(details(pad(S))))[:H, :W]   (Sec. II-A)
 # --------------------------------------------------------------------------
 def _mirror_index(n: int, npad: int) -> np.ndarray:
     i = np.arange(npad)
@@ -158,7 +158,7 @@ def residual_vjp(cache, gW: np.ndarray):
 
 
 # --------------------------------------------------------------------------
-# MLE fingerprint K = sum W S / sum S^2   (Sec. IV-A)
+# MLE fingerprint K = sum W S / sum S^2   (Sec. III-A)
 # --------------------------------------------------------------------------
 def mle_forward(Wr: np.ndarray, S: np.ndarray, gray: bool = False):
     """Wr, S [n, C, H, W] -> K [C, H, W] (or [H, W] grey when gray), cache."""
@@ -184,7 +184,7 @@ def mle_vjp(cache, gK: np.ndarray):
 
 
 # --------------------------------------------------------------------------
-# PCE against K (Sec. V; same reading as pipeline.pce_match)
+# PCE against K (Sec. IV; same reading as pipeline.pce_match)
 # --------------------------------------------------------------------------
 def pce_forward(K: np.ndarray, Wq: np.ndarray, Iq: np.ndarray, nbhd: int = 11):
     """K [H, W]; Wq, Iq [C, H, W] (or [H, W]) -> (pce, cache)."""

@@ -4,14 +4,14 @@ TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and the
 CPU legs of bench.py, never by the CUDA product path.
 
 Steps, in the paper's order:
-  sda_average            Sec. IV-B, definition of I_i^SDA (mean of d frames)
-  residual               Sec. III-A, W = I - F(I); F = the wavelet denoiser
-  fingerprint_accumulate Sec. IV-A equation for K-hat / Sec. IV-B K-hat^SDA:
+  sda_average            Sec. III-B, definition of I_i^SDA (mean of d frames)
+  residual               Sec. II-A, W = I - F(I); F = the wavelet denoiser
+  fingerprint_accumulate Sec. III-A equation for K-hat / Sec. III-B K-hat^SDA:
                          num = sum W.I, den = sum I^2
-  fingerprint_finalize   K = num/den (Sec. IV-A); zero-mean, DFT-domain Wiener
+  fingerprint_finalize   K = num/den (Sec. III-A); zero-mean, DFT-domain Wiener
                          and grey conversion are literature steps the paper
                          does not define (optional flags)
-  pce_match              Sec. V: PCE with threshold 60 (definition by
+  pce_match              Sec. IV: PCE with threshold 60 (definition by
                          citation only; the reading used is stated below)
 
 Readings where the paper is silent (all listed in the design notes): 8-tap
@@ -56,7 +56,7 @@ def padded_size(n: int, levels: int) -> int:
 
 
 # --------------------------------------------------------------------------
-# SDA frames (Sec. IV-B)
+# SDA frames (Sec. III-B)
 # --------------------------------------------------------------------------
 def sda_average(frames: np.ndarray, d: int) -> np.ndarray:
     """frames uint8 [m, H, W, C] (or [m, H, W]) -> float64 [g, C, H, W].
@@ -155,7 +155,7 @@ def denoise_plane(xp: np.ndarray, params: Params = DEFAULT):
 
 
 # --------------------------------------------------------------------------
-# Residual W = I - F(I)  (Sec. III-A)
+# Residual W = I - F(I)  (Sec. II-A)
 # --------------------------------------------------------------------------
 def residual(img: np.ndarray, params: Params = DEFAULT) -> np.ndarray:
     """img float [C, H, W] or [H, W] (0..255 units) -> W of the same shape."""
@@ -191,7 +191,7 @@ def residual_noise_form(img: np.ndarray, params: Params = DEFAULT) -> np.ndarray
 
 
 # --------------------------------------------------------------------------
-# MLE fingerprint (Sec. IV-A, Sec. IV-B)
+# MLE fingerprint (Sec. III-A, Sec. III-B)
 # --------------------------------------------------------------------------
 def fingerprint_accumulate(frames: np.ndarray, d: int, params: Params = DEFAULT,
                            num: np.ndarray | None = None, den: np.ndarray | None = None,
@@ -221,7 +221,7 @@ def fingerprint_accumulate(frames: np.ndarray, d: int, params: Params = DEFAULT,
 
 def mle_accumulate(Wr: np.ndarray, I: np.ndarray, num: np.ndarray, den: np.ndarray) -> None:
     """num += W.I and den += I.I elementwise (in place), the sums of the MLE
-    estimator K-hat = sum W_i I_i / sum I_i^2 (Sec. IV-A)."""
+    estimator K-hat = sum W_i I_i / sum I_i^2 (Sec. III-A)."""
     Wr = np.ascontiguousarray(Wr, dtype=np.float64)
     I = np.ascontiguousarray(I, dtype=np.float64)
     assert Wr.shape == I.shape == num.shape == den.shape
@@ -281,7 +281,7 @@ def fingerprint_finalize(num: np.ndarray, den: np.ndarray, flags: int = 0,
 
 
 # --------------------------------------------------------------------------
-# PCE (Sec. V; definition by citation only)
+# PCE (Sec. IV; definition by citation only)
 # --------------------------------------------------------------------------
 @dataclass
 class PCEResult:

@@ -10,10 +10,10 @@
  * Every routine restates one step literally, in double precision, with no
  * blocking, fusion or reordering beyond what the definition states:
  *
- *   SDA frame (Sec. IV-B, definition of I_i^SDA): mean of the frames of each
+ *   SDA frame (Sec. III-B, definition of I_i^SDA): mean of the frames of each
  *       disjoint group of d consecutive frames; a ragged last group is the mean
  *       of the frames it actually holds.
- *   Denoiser F (Sec. III-A / IV-A cite the wavelet filter of Mihcak et al.;
+ *   Denoiser F (Sec. II-A / III-A cite the wavelet filter of Mihcak et al.;
  *       its parameters are the build's reading): L-level periodised orthonormal
  *       DWT with an 8-tap Daubechies lowpass h and highpass g[k]=(-1)^k h[7-k],
  *       a[n] = sum_k h[k] x[(2n+k) mod N], d[n] = sum_k g[k] x[(2n+k) mod N],
@@ -21,8 +21,8 @@
  *       minimum over the w x w windows (w in {3,5,7,9}, periodic wrap) of the
  *       mean of c^2: var = max(0, min_w mean_w - s0^2), clean = c var/(var+s0^2),
  *       noise = c s0^2/(var+s0^2); F(I) = IDWT(LL_L, clean details).
- *   Residual (Sec. III-A, W = I - F(I)) on the mirror-padded image, cropped.
- *   MLE (Sec. IV-A equation for K-hat, and its SDA form in Sec. IV-B):
+ *   Residual (Sec. II-A, W = I - F(I)) on the mirror-padded image, cropped.
+ *   MLE (Sec. III-A equation for K-hat, and its SDA form in Sec. III-B):
  *       num += W.I, den += I.I accumulated over the frames (or SDA frames).
  *
  * The parity-unpinned part (the exact denoiser output on natural-looking
@@ -44,7 +44,7 @@ static long wrap_index(long i, long n)
 }
 
 /* ------------------------------------------------------------------------ */
-/* SDA frames, Sec. IV-B: I_i^SDA = (1/n_i) sum of the frames of group i.   */
+/* SDA frames, Sec. III-B: I_i^SDA = (1/n_i) sum of the frames of group i.   */
 /* frames: uint8 [m][H][W][C] at byte offsets j*frame_stride + y*row_pitch  */
 /* + x*C + c.  out: [g][C][H][W] doubles, g = ceil(m/d).                    */
 /* ------------------------------------------------------------------------ */
@@ -290,7 +290,7 @@ done:
 }
 
 /* ------------------------------------------------------------------------ */
-/* Noise residual of one plane, Sec. III-A: W = I - F(I).  img: H x W.      */
+/* Noise residual of one plane, Sec. II-A: W = I - F(I).  img: H x W.      */
 /* The plane is mirror-padded to Hp x Wp, denoised, subtracted, cropped.    */
 /* ------------------------------------------------------------------------ */
 int orc_residual_plane(const double *img, int H, int W, int levels,
@@ -314,7 +314,7 @@ int orc_residual_plane(const double *img, int H, int W, int levels,
 }
 
 /* ------------------------------------------------------------------------ */
-/* MLE accumulation, Sec. IV-A/IV-B: num += W.I, den += I.I (elementwise).  */
+/* MLE accumulation, Sec. III-A/III-B: num += W.I, den += I.I (elementwise).  */
 /* ------------------------------------------------------------------------ */
 void orc_mle_accumulate(const double *Wr, const double *I, long n, double *num, double *den)
 {

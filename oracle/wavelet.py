@@ -2,8 +2,9 @@
 
 TEST INFRASTRUCTURE ONLY.
 
-The paper names the denoiser only by citation (Sec. IV-A: "such as [Mihcak et
-al.]"; Sec. V: "the wavelet denoising algorithm").  The build reads it as an
+The paper names the denoiser only by citation (Sec. II-A and III-A point to the
+wavelet filter of Mihcak et al.; Sec. IV says a wavelet denoiser was used).  The
+build reads it as an
 orthonormal 8-tap Daubechies wavelet (4 vanishing moments).  The lowpass filter
 is derived here from Daubechies' construction rather than typed in:
 

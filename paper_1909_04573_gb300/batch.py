@@ -1,6 +1,6 @@
 """Host-side planning for multi-camera workloads larger than device memory.
 
-The fingerprint sums of Sec. IV-A / IV-B run over independent SDA groups, so a
+The fingerprint sums of Sec. III-A / III-B run over independent SDA groups, so a
 camera's frames can be processed in several calls as long as no group is split
 (each call accumulates whole groups into the camera's num/den).  plan_chunks
 packs the cameras' groups, in order, into chunks of at most ``budget`` bytes of

@@ -1,8 +1,8 @@
 // k_fft.cu -- once-per-fingerprint and once-per-query steps:
-//   finalize: K = num/den (Sec. IV-A) in float64, optional grey conversion,
+//   finalize: K = num/den (Sec. III-A) in float64, optional grey conversion,
 //             zero-mean (column means, then row means) and DFT-domain Wiener
 //             filter (literature steps the paper does not define);
-//   PCE:      peak-to-correlation energy of a query (Sec. V, threshold 60;
+//   PCE:      peak-to-correlation energy of a query (Sec. IV, threshold 60;
 //             defined there by citation only).
 // The DFTs go through cuFFT (float32); every sum that decides a result (means,
 // variance, correlation energy) is accumulated in float64 with a fixed

@@ -1,9 +1,9 @@
 // k_grad.cu -- adjoint (vector-Jacobian) kernels of the extraction chain with
 // free per-frame SDA weights and a differentiable sigma0:
-//   S_i = sum_{j in group i} w_j I_j                 (Sec. IV-B)
-//   W_i = residual(S_i; sigma0)                      (Sec. III-A / IV-A)
-//   K   = sum_i W_i S_i / sum_i S_i^2                (Sec. IV-A)
-//   PCE of queries against K                         (Sec. V)
+//   S_i = sum_{j in group i} w_j I_j                 (Sec. III-B)
+//   W_i = residual(S_i; sigma0)                      (Sec. II-A / III-A)
+//   K   = sum_i W_i S_i / sum_i S_i^2                (Sec. III-A)
+//   PCE of queries against K                         (Sec. IV)
 // The residual's adjoint reuses the forward DWT kernels (the periodised
 // orthonormal transform's transpose is its inverse); the shrink's adjoint and
 // the other steps are here.

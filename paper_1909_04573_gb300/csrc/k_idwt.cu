@@ -1,8 +1,8 @@
 // k_idwt.cu -- inverse DWT of the noise coefficients (synthesis, the
 // transpose of the periodised analysis) and the fused level-1 step that forms
-// the residual W = I - F(I) = IDWT(0, noise details) (Sec. III-A), crops the
+// the residual W = I - F(I) = IDWT(0, noise details) (Sec. II-A), crops the
 // padding and either stores W or accumulates the MLE sums
-// num += W I, den += I^2 (Sec. IV-A / IV-B).
+// num += W I, den += I^2 (Sec. III-A / III-B).
 //
 // Gather form of x[(2n+k) mod N] += h[k] a[n] + g[k] b[n]: output sample
 // j = 2m + e (e in {0, 1}) takes k = e + 2t, n = m - t for t = 0..3.

@@ -1,4 +1,4 @@
-// k_sda.cu -- SDA frames (Sec. IV-B): exact per-group sums of uint8 frames.
+// k_sda.cu -- SDA frames (Sec. III-B): exact per-group sums of uint8 frames.
 //
 // A frame row is W*C interleaved bytes.  A block owns a segment of SEGPX
 // pixels of one row of one group (SEGPX*C bytes, a multiple of 16) and each

@@ -1,5 +1,5 @@
 // k_shrink.cu -- local-variance Wiener shrink of detail coefficients (the
-// denoiser of Mihcak et al., cited in Sec. IV-A and Sec. V; parameters are the
+// denoiser of Mihcak et al., cited in Sec. III-A and Sec. IV; parameters are the
 // build's reading).  For each coefficient c of a subband and each window w:
 //   mean_w = (1/w^2) sum of c^2 over the w x w window (periodic wrap),
 //   var = max(0, min_w mean_w - s0^2),   noise = c s0^2 / (var + s0^2)

@@ -1,10 +1,10 @@
 """torch.autograd bindings of the differentiable chain (marshalling only:
 every forward and adjoint step runs in libprnu's kernels).
 
-  S = sda_weighted(frames, w, d)        Sec. IV-B with free per-frame weights
-  W = residual(S, sigma0)               Sec. III-A, noise-form wavelet denoiser
-  K = mle(W, S, gray=True)              Sec. IV-A
-  p = pce(K, Wq, Iq)                    Sec. V (one value per query)
+  S = sda_weighted(frames, w, d)        Sec. III-B with free per-frame weights
+  W = residual(S, sigma0)               Sec. II-A, noise-form wavelet denoiser
+  K = mle(W, S, gray=True)              Sec. III-A
+  p = pce(K, Wq, Iq)                    Sec. IV (one value per query)
 
 sigma0 is a 0-d CPU tensor (its value is a kernel parameter); frames are
 uint8 [m, H, W, C] device tensors.  The residual keeps its detail

@@ -1,6 +1,6 @@
 """Sharding one camera's fingerprint across ranks (one process per GPU).
 
-The MLE sums of Sec. IV-A / IV-B, num = sum_i W_i I_i and den = sum_i I_i^2,
+The MLE sums of Sec. III-A / III-B, num = sum_i W_i I_i and den = sum_i I_i^2,
 run over independent SDA groups, so ranks can take disjoint, contiguous runs
 of whole groups and one sum all-reduce of num/den (2 * 4 B per pixel-channel)
 completes the fingerprint.  Group boundaries stay at multiples of d, so every

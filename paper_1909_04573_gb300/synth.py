@@ -1,7 +1,7 @@
 """Seeded synthetic cameras and frames (the stand-in for the paper's datasets).
 
 The paper's experiments use the VISION and NYUAD-MMD datasets, which are not
-available; frames here follow the sensor model of Sec. III-A, Eq. (1):
+available; frames here follow the sensor model of Sec. II-A, Eq. (1):
 
     I = I0 + I0 K + psi
 

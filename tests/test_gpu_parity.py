@@ -178,7 +178,7 @@ def test_pce_matches_oracle(ctx, H, W, C):
 
 def test_planted_camera_end_to_end(ctx):
     # 64 grayscale 256x256 frames, SDA groups of 8; one same-camera and one
-    # foreign query; PCE threshold 60 (Sec. V) separates them on both sides
+    # foreign query; PCE threshold 60 (Sec. IV) separates them on both sides
     cam = synth.Camera(H=256, W=256, C=1, camera_id=21)
     fr = synth.frames(cam, 64).numpy()
     num, den = _accumulate(ctx, fr, 8)

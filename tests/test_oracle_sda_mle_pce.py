@@ -18,7 +18,7 @@ def test_sda_average_equals_brute_force_mean_with_ragged_group():
 
 
 def test_sda_noise_variance_drops_by_d():
-    # Sec. IV-B: Var(psi^SDA) = sigma1^2 / d for i.i.d. noise.  Pure-noise
+    # Sec. III-B: Var(psi^SDA) = sigma1^2 / d for i.i.d. noise.  Pure-noise
     # frames (mean 128, sigma 8, quantised) averaged in groups of d.
     rng = np.random.default_rng(1)
     m, d, H, W = 64, 16, 64, 64
@@ -32,7 +32,7 @@ def test_sda_noise_variance_drops_by_d():
 
 
 def test_mle_recovers_planted_fingerprint_exactly():
-    # Sec. IV-A: with W_i = I_i K exactly, K-hat = sum W I / sum I^2 = K.
+    # Sec. III-A: with W_i = I_i K exactly, K-hat = sum W I / sum I^2 = K.
     rng = np.random.default_rng(2)
     K = rng.normal(0, 0.005, size=(2, 16, 16))
     num = np.zeros_like(K)
@@ -133,7 +133,7 @@ def test_pce_of_independent_white_signals_is_order_one():
 @pytest.mark.slow
 def test_planted_camera_end_to_end_small():
     # 64 grayscale 256x256 frames, SDA groups of 8 (8 denoise calls); one query
-    # frame from the same camera and one from a foreign camera (Sec. V
+    # frame from the same camera and one from a foreign camera (Sec. IV
     # threshold 60 separates them)
     cam = synth.Camera(H=256, W=256, C=1, camera_id=7)
     fr = synth.frames(cam, 64).numpy()
@@ -159,5 +159,5 @@ def test_more_groups_give_a_better_fingerprint_and_sda_costs_little_on_smooth_sc
         return np.corrcoef(O.fingerprint_finalize(num, den)[0].ravel(), Kt.ravel())[0, 1]
 
     assert corr(16, 4) < corr(64, 4)                    # more frames, better K
-    # smooth scenes: the SDA estimator is close to the per-frame one (Sec. IV remarks)
+    # smooth scenes: the SDA estimator is close to the per-frame one (Sec. III remarks)
     assert corr(64, 4) > 0.8 * corr(64, 1)
