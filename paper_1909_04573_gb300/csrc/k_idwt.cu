@@ -612,13 +612,20 @@ static dim3 stream_grid(int Rc, int Cc, int planes) {
                 (unsigned)planes);
 }
 
+// The streaming form pays off when its grid fills the GPU; small planes
+// (deep levels, small images) keep the tiled kernels.
+static bool stream_pays(int Rc, int Cc, int planes) {
+    const dim3 g = stream_grid(Rc, Cc, planes);
+    return (long long)g.x * g.y * g.z * FS_WARPS >= 3648;  // half of 152 SMs x 48 warps
+}
+
 int final_pce_blocks(int Rc, int Cc) {
     const dim3 g = stream_grid(Rc, Cc, 1);
     return (int)(g.x * g.y);
 }
 
 cudaError_t launch_synthesis(const SynArgs &a, cudaStream_t st) {
-    if (a.sdt == SB_F32) {
+    if (a.sdt == SB_F32 && (a.gray3 || stream_pays(a.Rc, a.Cc, a.P))) {
         if (a.gray3)
             k_synthesis_stream<true><<<stream_grid(a.Rc, a.Cc, a.P), 32 * FS_WARPS, 0, st>>>(a);
         else
@@ -669,7 +676,7 @@ cudaError_t launch_final(const FinalArgs &a, bool mle, cudaStream_t st) {
             k_final_pce<false><<<stream_grid(a.Rc, a.Cc, a.G), 32 * FS_WARPS, 0, st>>>(a);
         return cudaGetLastError();
     }
-    if (a.sdt == SB_F32) {
+    if (a.sdt == SB_F32 && stream_pays(a.Rc, a.Cc, a.C * a.G)) {
         if (a.accumulate)
             k_final_stream<true><<<stream_grid(a.Rc, a.Cc, a.C * a.G), 32 * FS_WARPS, 0, st>>>(a);
         else
