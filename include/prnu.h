@@ -169,10 +169,14 @@ prnu_status prnu_fingerprint_accumulate(prnu_ctx *ctx, const uint8_t *frames, in
                                         const prnu_params *params, float *num, float *den,
                                         void *ws, size_t ws_bytes, void *stream);
 
-/* Same as prnu_fingerprint_accumulate, but `host_frames` is host memory
- * (page-locked for overlap; pageable works but serialises the copies).  The
- * frames are copied in chunks through the workspace, each copy overlapping
- * the kernels of the previous chunk.  num, den are device pointers. */
+/* Same as prnu_fingerprint_accumulate, but `host_frames` is host memory.
+ * Page-locked frames (cudaHostAlloc / cudaHostRegister) are read in place by
+ * the kernels through their device-visible address (no staging copy; the
+ * whole workspace holds pass intermediates).  Pageable frames are copied in
+ * chunks through two staging buffers in the workspace, each copy overlapping
+ * the kernels of the previous chunk.  Either way the frames must stay
+ * unchanged until the stream has run the work.  num, den are device
+ * pointers. */
 prnu_status prnu_fingerprint_accumulate_host(prnu_ctx *ctx, const uint8_t *host_frames, int m, int H, int W,
                                              int C, size_t frame_stride, size_t row_pitch, int d,
                                              const prnu_params *params, float *num, float *den,

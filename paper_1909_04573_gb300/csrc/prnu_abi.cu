@@ -694,6 +694,26 @@ prnu_status prnu_fingerprint_accumulate_host(prnu_ctx *ctx, const uint8_t *host_
     if ((s = check_frames(host_frames, m, H, W, C, frame_stride, row_pitch, d, fes)) != PRNU_OK) return s;
     if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(PRNU_EINVAL, "workspace must be 256-byte aligned");
     const int g = (m + d - 1) / d;
+    DeviceGuard gd(ctx->device);
+    cudaStream_t st = S(stream);
+    {
+        // Page-locked host frames are read in place by the kernels (through
+        // their device-visible address over the host link): no staging copy,
+        // and the whole workspace holds pass layouts.
+        cudaPointerAttributes attr{};
+        if (cudaPointerGetAttributes(&attr, host_frames) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+            attr.devicePointer) {
+            const uint8_t *dev = static_cast<const uint8_t *>(attr.devicePointer);
+            const int Gp = groups_fitting(H, W, C, params->levels, ws_bytes, g, params->dtype);
+            if (Gp < 1) return check_ws(ws, ws_bytes, make_layout(H, W, C, params->levels, true, params->dtype).end);
+            for (int g0 = 0; g0 < g; g0 += Gp)
+                if ((s = accumulate_pass(ctx, dev, m, H, W, C, frame_stride, row_pitch, d, g0, std::min(Gp, g - g0),
+                                         *params, win, num, den, static_cast<char *>(ws), st)) != PRNU_OK)
+                    return s;
+            return PRNU_OK;
+        }
+        cudaGetLastError();  // pageable memory: clear the query's error state, stage through the device
+    }
     const size_t fbytes = (size_t)H * W * C * fes;  // staged frames are packed
     // largest groups-per-pass with two staging buffers and the pass layout
     int Gp = 0;
@@ -713,12 +733,10 @@ prnu_status prnu_fingerprint_accumulate_host(prnu_ctx *ctx, const uint8_t *host_
             2 * align_up((size_t)d * fbytes, kAlign) + make_layout(H, W, C, params->levels, true, params->dtype).end;
         return fail(PRNU_ENOSPC, "workspace too small: need %zu bytes, got %zu", need, ws_bytes);
     }
-    DeviceGuard gd(ctx->device);
     char *base = static_cast<char *>(ws);
     const size_t stage = align_up((size_t)Gp * d * fbytes, kAlign);
     uint8_t *buf[2] = {reinterpret_cast<uint8_t *>(base), reinterpret_cast<uint8_t *>(base + stage)};
     char *rest = base + 2 * stage;
-    cudaStream_t st = S(stream);
     const size_t rowb = (size_t)W * C * fes;
     const bool packed = row_pitch == rowb && (m == 1 || frame_stride == (size_t)H * rowb);
     int k = 0;

@@ -135,11 +135,14 @@ def test_multipass_accumulate_and_determinism(ctx):
     assert _rel(n2, n1) <= 1e-6 and _rel(d2, d1) <= 1e-6
 
 
-def test_accumulate_host_equals_device(ctx):
+@pytest.mark.parametrize("pinned", [True, False])
+def test_accumulate_host_equals_device(ctx, pinned):
+    """Page-locked frames are read in place (zero copy), pageable ones are
+    staged through the workspace; both equal the device path."""
     fr = _frames(48, 64, 3, 20, seed=6)
     num = torch.zeros((3, 48, 64), dtype=torch.float32, device="cuda")
     den = torch.zeros_like(num)
-    host = torch.from_numpy(fr).pin_memory()
+    host = torch.from_numpy(fr).pin_memory() if pinned else torch.from_numpy(fr.copy())
     ctx.fingerprint_accumulate_host(host, 5, num, den, groups_per_pass=2)
     n2, d2 = _accumulate(ctx, fr, 5, images_per_pass=2)
     torch.cuda.synchronize()
