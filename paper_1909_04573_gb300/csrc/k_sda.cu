@@ -219,14 +219,14 @@ cudaError_t launch_sda(const SdaArgs &a, int num_sms, cudaStream_t st) {
         const long long units = (long long)a.G * a.H * ((a.W + SEG - 1) / SEG);
         if (a.C == 3) {
             constexpr int NT = SEG * 3 / 8;
-            const long long blocks = std::min<long long>(units, (long long)num_sms * (2048 / NT));
+            const long long blocks = std::min<long long>(units, (long long)num_sms * (a.blocks_per_sm > 0 ? a.blocks_per_sm : 2048 / NT));
             if (a.gd)
                 k_sda_sum_f16<3, SEG, true><<<(unsigned)std::max<long long>(blocks, 1), NT, 0, st>>>(a);
             else
                 k_sda_sum_f16<3, SEG, false><<<(unsigned)std::max<long long>(blocks, 1), NT, 0, st>>>(a);
         } else {
             constexpr int NT = SEG / 8;
-            const long long blocks = std::min<long long>(units, (long long)num_sms * (2048 / NT));
+            const long long blocks = std::min<long long>(units, (long long)num_sms * (a.blocks_per_sm > 0 ? a.blocks_per_sm : 2048 / NT));
             if (a.gd)
                 k_sda_sum_f16<1, SEG, true><<<(unsigned)std::max<long long>(blocks, 1), NT, 0, st>>>(a);
             else
@@ -237,7 +237,7 @@ cudaError_t launch_sda(const SdaArgs &a, int num_sms, cudaStream_t st) {
     if (a.C == 3) {
         constexpr int SEG = 1024, NT = SEG * 3 / 16;
         const long long units = (long long)a.G * a.H * ((a.W + SEG - 1) / SEG);
-        const long long blocks = std::min<long long>(units, (long long)num_sms * (2048 / NT));
+        const long long blocks = std::min<long long>(units, (long long)num_sms * (a.blocks_per_sm > 0 ? a.blocks_per_sm : 2048 / NT));
         if (a.gd)
             k_sda_sum<3, SEG, true><<<(unsigned)std::max<long long>(blocks, 1), NT, 0, st>>>(a);
         else
@@ -245,7 +245,7 @@ cudaError_t launch_sda(const SdaArgs &a, int num_sms, cudaStream_t st) {
     } else {
         constexpr int SEG = 4096, NT = SEG / 16;
         const long long units = (long long)a.G * a.H * ((a.W + SEG - 1) / SEG);
-        const long long blocks = std::min<long long>(units, (long long)num_sms * (2048 / NT));
+        const long long blocks = std::min<long long>(units, (long long)num_sms * (a.blocks_per_sm > 0 ? a.blocks_per_sm : 2048 / NT));
         if (a.gd)
             k_sda_sum<1, SEG, true><<<(unsigned)std::max<long long>(blocks, 1), NT, 0, st>>>(a);
         else

@@ -17,6 +17,7 @@ struct SdaArgs {
     float *out;     // [G][C][H][W]
     int mean;       // 1: write sum/count (correctly rounded), 0: the exact sum
     const GroupDesc *gd;  // multi-camera pass: per-group frames/strides/count (frames..d, g0 unused)
+    int blocks_per_sm;    // grid cap (0: fill the SMs); frames read over the host link need few blocks
 };
 cudaError_t launch_put_desc(const PassDesc &pd, PassDesc *dst, cudaStream_t st);
 cudaError_t launch_sda(const SdaArgs &a, int num_sms, cudaStream_t st);

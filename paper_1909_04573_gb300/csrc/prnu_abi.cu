@@ -384,10 +384,9 @@ prnu_status fft_layout(prnu_ctx *ctx, int H, int W, int n, FftLayout *out) {
 }
 
 
-// Process groups g0 .. g0+G-1 of `frames` (device) into num/den.
-prnu_status accumulate_pass(prnu_ctx *ctx, const uint8_t *frames, int m, int H, int W, int C, size_t fs, size_t rp,
-                            int d, int g0, int G, const prnu_params &prm, const Win &win, float *num, float *den,
-                            char *ws, cudaStream_t st) {
+// Group sums of groups g0 .. g0+G-1 of `frames` into the pass layout's X.
+prnu_status sda_pass(prnu_ctx *ctx, const uint8_t *frames, int m, int H, int W, int C, size_t fs, size_t rp, int d,
+                     int g0, int G, const prnu_params &prm, char *ws, cudaStream_t st, int blocks_per_sm = 0) {
     const int P = G * C;
     const Layout lo = make_layout(H, W, P, prm.levels, true, prm.dtype);
     SdaArgs sa{};
@@ -404,12 +403,19 @@ prnu_status accumulate_pass(prnu_ctx *ctx, const uint8_t *frames, int m, int H, 
     sa.out = reinterpret_cast<float *>(ws + lo.X);
     sa.mean = 0;
     sa.frame_half = prm.frame_dtype == PRNU_FRAMES_F16;
-    {
-        const double fr = (double)(std::min(m, (g0 + G) * d) - g0 * d) * H * W * C *
-                          (prm.frame_dtype == PRNU_FRAMES_F16 ? 2 : 1);
-        Launch t(ctx, "sda_sum", st, 1, fr + (double)P * H * W * 4);
-        CU(launch_sda(sa, ctx->sms, st));
-    }
+    sa.blocks_per_sm = blocks_per_sm;
+    const double fr = (double)(std::min(m, (g0 + G) * d) - g0 * d) * H * W * C *
+                      (prm.frame_dtype == PRNU_FRAMES_F16 ? 2 : 1);
+    Launch t(ctx, "sda_sum", st, 1, fr + (double)P * H * W * 4);
+    CU(launch_sda(sa, ctx->sms, st));
+    return PRNU_OK;
+}
+
+// Denoise + MLE of the G group sums in the pass layout's X into num/den.
+prnu_status denoise_pass(prnu_ctx *ctx, int m, int H, int W, int C, int d, int g0, int G, const prnu_params &prm,
+                         const Win &win, float *num, float *den, char *ws, cudaStream_t st) {
+    const int P = G * C;
+    const Layout lo = make_layout(H, W, P, prm.levels, true, prm.dtype);
     const PlaneScale sc{d, m, g0, C, nullptr};
     FinalArgs fin{};
     fin.C = C;
@@ -419,6 +425,15 @@ prnu_status accumulate_pass(prnu_ctx *ctx, const uint8_t *frames, int m, int H, 
     fin.num = num;
     fin.den = den;
     return run_denoise(ctx, reinterpret_cast<const float *>(ws + lo.X), H, W, P, prm, win, sc, 1, ws, lo, fin, true, st);
+}
+
+// Process groups g0 .. g0+G-1 of `frames` (device) into num/den.
+prnu_status accumulate_pass(prnu_ctx *ctx, const uint8_t *frames, int m, int H, int W, int C, size_t fs, size_t rp,
+                            int d, int g0, int G, const prnu_params &prm, const Win &win, float *num, float *den,
+                            char *ws, cudaStream_t st) {
+    prnu_status s = sda_pass(ctx, frames, m, H, W, C, fs, rp, d, g0, G, prm, ws, st);
+    if (s != PRNU_OK) return s;
+    return denoise_pass(ctx, m, H, W, C, d, g0, G, prm, win, num, den, ws, st);
 }
 
 // Largest number of groups per pass whose layout fits in `bytes`.
@@ -704,6 +719,33 @@ prnu_status prnu_fingerprint_accumulate_host(prnu_ctx *ctx, const uint8_t *host_
         if (cudaPointerGetAttributes(&attr, host_frames) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
             attr.devicePointer) {
             const uint8_t *dev = static_cast<const uint8_t *>(attr.devicePointer);
+            // Two pass layouts: the sums of pass k+1 are read over the link (on the
+            // context's side stream, two blocks per SM are enough for its bandwidth)
+            // while pass k is denoised on `stream`.
+            // at least four passes, so that all but the last pass's denoise hides behind the reads
+            const int Gp2 = groups_fitting(H, W, C, params->levels, ws_bytes / 2 / kAlign * kAlign,
+                                           std::max(1, (g + 3) / 4), params->dtype);
+            if (Gp2 >= 1 && g > Gp2) {
+                const size_t half =
+                    align_up(make_layout(H, W, (long long)Gp2 * C, params->levels, true, params->dtype).end, kAlign);
+                char *wsb[2] = {static_cast<char *>(ws), static_cast<char *>(ws) + half};
+                cudaStream_t side = ctx->copy_stream;
+                for (int b = 0; b < 2; ++b) CU(cudaEventRecord(ctx->ev_free[b], st));  // after prior work on st
+                int k = 0;
+                for (int g0 = 0; g0 < g; g0 += Gp2, ++k) {
+                    const int G = std::min(Gp2, g - g0), b = k & 1;
+                    CU(cudaStreamWaitEvent(side, ctx->ev_free[b], 0));
+                    if ((s = sda_pass(ctx, dev, m, H, W, C, frame_stride, row_pitch, d, g0, G, *params, wsb[b], side,
+                                      2)) != PRNU_OK)
+                        return s;
+                    CU(cudaEventRecord(ctx->ev_copied[b], side));
+                    CU(cudaStreamWaitEvent(st, ctx->ev_copied[b], 0));
+                    if ((s = denoise_pass(ctx, m, H, W, C, d, g0, G, *params, win, num, den, wsb[b], st)) != PRNU_OK)
+                        return s;
+                    CU(cudaEventRecord(ctx->ev_free[b], st));
+                }
+                return PRNU_OK;
+            }
             const int Gp = groups_fitting(H, W, C, params->levels, ws_bytes, g, params->dtype);
             if (Gp < 1) return check_ws(ws, ws_bytes, make_layout(H, W, C, params->levels, true, params->dtype).end);
             for (int g0 = 0; g0 < g; g0 += Gp)
