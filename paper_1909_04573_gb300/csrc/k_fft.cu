@@ -9,6 +9,8 @@
 // two-stage reduction, so results do not change from run to run.
 #include <cufft.h>
 
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace prnu {
@@ -28,40 +30,95 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 }
 
 // ---------------------------------------------------------------- finalize --
-// K = num/den to float64 accuracy without a float64 divide: q0 is the float32
-// IEEE quotient, then one float64 residual step q = q0 + (num - q0 den) / den
-// (the residual is O(2^-24 num), so its float32-reciprocal scaling leaves an
-// error O(2^-48)).
-__device__ __forceinline__ double div64(float n, float d) {
-    const double q0 = (double)__fdiv_rn(n, d);
-    const double r = fma(-q0, (double)d, (double)n);
-    return fma(r, (double)__frcp_rn(d), q0);
+// K = num/den to float64 accuracy in float32 arithmetic (GB300's float64 rate
+// is a small fraction of its float32 rate): q0 is the float32 IEEE quotient,
+// r = num - q0 den is exact (one FMA), and q0 + r/den is carried as an
+// unevaluated float-float pair (hi, lo), accurate to O(2^-46) relative.
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF div_ff(float n, float d) {
+    const float q0 = __fdiv_rn(n, d);
+    const float r = __fmaf_rn(-q0, d, n);
+    return FF{q0, __fmul_rn(r, __frcp_rn(d))};
+}
+// a * (hi, lo) + (s, t) in float-float: TwoProd by FMA, then TwoSum
+__device__ __forceinline__ FF ff_fma(float a, FF x, FF acc) {
+    const float p = __fmul_rn(a, x.hi);
+    const float pe = __fmaf_rn(a, x.hi, -p);  // exact error of the product
+    float sh, se;
+    two_sum(acc.hi, p, sh, se);
+    const float lo = __fadd_rn(__fadd_rn(acc.lo, se), __fmaf_rn(a, x.lo, pe));
+    float h, l;
+    fast_two_sum(sh, lo, h, l);
+    return FF{h, l};
 }
 
+// The grey weights as float-float pairs of 0.299, 0.587, 0.114.
+__constant__ float kGrayHi[3] = {0.299f, 0.587f, 0.114f};
+__constant__ float kGrayLo[3] = {(float)(0.299 - (double)0.299f), (float)(0.587 - (double)0.587f),
+                                 (float)(0.114 - (double)0.114f)};
+
 // num_lo / den_lo (nullable): low parts of compensated float-float sums, so
-// that the quotient is (num + num_lo) / (den + den_lo) formed in float64.
+// that the quotient is (num + num_lo) / (den + den_lo).
 __global__ void k_divide(const float *num, const float *den, const float *num_lo, const float *den_lo, long long hw,
                          int C, int gray, float *K) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < hw;
          i += (long long)gridDim.x * blockDim.x) {
-        double k[3];
-        for (int c = 0; c < C; ++c) {
+        FF k[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (c >= C) break;
             const long long o = c * hw + i;
+            const float d = den[o];
             if (num_lo) {
-                const double n = (double)num[o] + (double)num_lo[o];
-                const double d = (double)den[o] + (double)den_lo[o];
-                k[c] = d != 0.0 ? n / d : 0.0;
+                // (n + nl) / (d + dl): q0 from the high parts, then the exact residual of the pair
+                const float dl = den_lo[o];
+                if (d == 0.f && dl == 0.f) {
+                    k[c] = FF{0.f, 0.f};
+                    continue;
+                }
+                float dh, dlo;
+                fast_two_sum(d, dl, dh, dlo);
+                const float n = num[o], nl = num_lo[o];
+                const float q0 = __fdiv_rn(__fadd_rn(n, nl), dh);
+                // r = (n + nl) - q0 (dh + dlo), accurate to the float-float level
+                const float p = __fmul_rn(q0, dh), pe = __fmaf_rn(q0, dh, -p);
+                const float r = __fadd_rn(__fadd_rn(__fsub_rn(n, p), nl), -__fmaf_rn(q0, dlo, pe));
+                k[c] = FF{q0, __fmul_rn(r, __frcp_rn(dh))};
             } else {
-                const float d = den[o];
-                k[c] = d != 0.f ? div64(num[o], d) : 0.0;
+                k[c] = d != 0.f ? div_ff(num[o], d) : FF{0.f, 0.f};
             }
         }
         if (gray) {
-            K[i] = (float)fma(0.114, k[2], fma(0.587, k[1], 0.299 * k[0]));
+            FF acc{0.f, 0.f};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                acc = ff_fma(kGrayHi[c], k[c], acc);
+                acc = ff_fma(kGrayLo[c], FF{k[c].hi, 0.f}, acc);
+            }
+            K[i] = __fadd_rn(acc.hi, acc.lo);
         } else {
-            for (int c = 0; c < C; ++c) K[c * hw + i] = (float)k[c];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                if (c < C) K[c * hw + i] = __fadd_rn(k[c].hi, k[c].lo);
         }
     }
+}
+
+// Float-float helpers: sums kept as (hi, lo) pairs with TwoSum (no float64
+// arithmetic per element; float64 only for the few per-block partials).
+__device__ __forceinline__ void ffa(FF &a, float v) { ff_add(a.hi, a.lo, v); }
+__device__ __forceinline__ double ffd(const FF &a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ FF ff_of(double v) {
+    const float h = (float)v;
+    return FF{h, (float)(v - (double)h)};
+}
+// (x - m) for a float x and a float-float m, as a float-float value
+__device__ __forceinline__ FF ff_sub(float x, FF m) {
+    float s, e;
+    two_sum(x, -m.hi, s, e);
+    return FF{s, __fsub_rn(e, m.lo)};
 }
 
 // column means of one plane in two passes: a 2-D grid of partial column
@@ -73,55 +130,70 @@ __global__ void k_colsum_part(const float *K, int H, int W, double *part) {
     const int band = blockIdx.y;
     if (x >= W) return;
     const int y0 = band * CM_BAND, y1 = min(H, y0 + CM_BAND);
-    double s = 0.0;
-    for (int y = y0; y < y1; ++y) s += (double)K[(long long)y * W + x];
-    part[(long long)band * W + x] = s;
+    FF s{0.f, 0.f};
+    for (int y = y0; y < y1; ++y) ffa(s, K[(long long)y * W + x]);
+    part[(long long)band * W + x] = ffd(s);
 }
 
-__global__ void k_colmean(const double *part, int H, int W, double *colmean) {
+// column means as float-float pairs (each in its 8-byte slot)
+__global__ void k_colmean(const double *part, int H, int W, FF *colmean) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= W) return;
     const int nb = (H + CM_BAND - 1) / CM_BAND;
     double s = 0.0;
     for (int b = 0; b < nb; ++b) s += part[(long long)b * W + x];
-    colmean[x] = s / H;
+    colmean[x] = ff_of(s / H);
 }
 
-// row means of K - colmean: one block per row
-__global__ void k_rowmean(const float *K, int H, int W, const double *colmean, double *rowmean) {
+// row means of K - colmean (float-float pairs): one block per row
+__global__ void k_rowmean(const float *K, int H, int W, const FF *colmean, FF *rowmean) {
     __shared__ double sh[32];
     const int y = blockIdx.x;
-    double s = 0.0;
-    for (int x = threadIdx.x; x < W; x += blockDim.x) s += (double)K[(long long)y * W + x] - colmean[x];
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) rowmean[y] = s / W;
+    FF acc{0.f, 0.f};
+    for (int x = threadIdx.x; x < W; x += blockDim.x) {
+        const FF d = ff_sub(K[(long long)y * W + x], colmean[x]);
+        ffa(acc, d.hi);
+        ffa(acc, d.lo);
+    }
+    const double s = block_sum(ffd(acc), sh);
+    if (threadIdx.x == 0) rowmean[y] = ff_of(s / W);
 }
 
-__global__ void k_sub_means(float *K, int H, int W, const double *colmean, const double *rowmean) {
-    const long long hw = (long long)H * W;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < hw;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(i / W), x = (int)(i - (long long)y * W);
-        K[i] = (float)((double)K[i] - colmean[x] - rowmean[y]);
+// K - colmean - rowmean, rounded once; rows over blocks, columns over threads
+__global__ void k_sub_means(float *K, int H, int W, const FF *colmean, const FF *rowmean) {
+    for (int y = blockIdx.x; y < H; y += gridDim.x) {
+        const FF rm = rowmean[y];
+        float *row = K + (long long)y * W;
+        for (int x = threadIdx.x; x < W; x += blockDim.x) {
+            const FF cm = colmean[x];
+            const FF a = ff_sub(row[x], cm);  // a.hi + a.lo = K - colmean
+            float s, e;
+            two_sum(a.hi, -rm.hi, s, e);
+            row[x] = __fadd_rn(s, __fadd_rn(__fsub_rn(e, rm.lo), a.lo));
+        }
     }
 }
 
 // stage 1 of sum and sum of squares about `center` (nullable => 0)
 __global__ void k_moments(const float *v, long long n, const double *center, double *part) {
     __shared__ double sh[32];
-    const double c = center ? center[0] : 0.0;
-    double s = 0.0, q = 0.0;
+    const FF c = ff_of(center ? center[0] : 0.0);
+    FF s{0.f, 0.f}, q{0.f, 0.f};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const double d = (double)v[i] - c;
-        s += d;
-        q += d * d;
+        const FF d = ff_sub(v[i], c);
+        ffa(s, d.hi);
+        ffa(s, d.lo);
+        // d^2 with the product error of hi^2 (TwoProd by FMA); the lo terms are far below it
+        const float p = __fmul_rn(d.hi, d.hi);
+        ffa(q, p);
+        ffa(q, __fmaf_rn(d.hi, d.hi, -p) + 2.f * d.hi * d.lo);
     }
-    s = block_sum(s, sh);
-    q = block_sum(q, sh);
+    const double ss = block_sum(ffd(s), sh);
+    const double qq = block_sum(ffd(q), sh);
     if (threadIdx.x == 0) {
-        part[2 * blockIdx.x] = s;
-        part[2 * blockIdx.x + 1] = q;
+        part[2 * blockIdx.x] = ss;
+        part[2 * blockIdx.x + 1] = qq;
     }
 }
 
@@ -364,9 +436,10 @@ cudaError_t launch_zero_mean(float *K, int H, int W, double *colmean, double *ro
                              cudaStream_t st) {
     const int nb = (H + CM_BAND - 1) / CM_BAND;
     k_colsum_part<<<dim3((W + 127) / 128, nb), 128, 0, st>>>(K, H, W, part);
-    k_colmean<<<(W + 255) / 256, 256, 0, st>>>(part, H, W, colmean);
-    k_rowmean<<<H, RB, 0, st>>>(K, H, W, colmean, rowmean);
-    k_sub_means<<<ew_blocks((long long)H * W, sms), 256, 0, st>>>(K, H, W, colmean, rowmean);
+    FF *cm = reinterpret_cast<FF *>(colmean), *rm = reinterpret_cast<FF *>(rowmean);  // 8-byte slots
+    k_colmean<<<(W + 255) / 256, 256, 0, st>>>(part, H, W, cm);
+    k_rowmean<<<H, RB, 0, st>>>(K, H, W, cm, rm);
+    k_sub_means<<<(unsigned)std::min(H, sms * 8), 256, 0, st>>>(K, H, W, cm, rm);
     return cudaGetLastError();
 }
 
