@@ -328,18 +328,20 @@ __global__ void k_pce_prep(const float *Kbase, long long k_stride, const float *
     }
 }
 
-// Z_i = conj(FX_i) * FY_i with the DC bin set to 0 (C(s) = sum_x X(x) Y(x+s))
+// Z_i = conj(FX_i) * FY_i with the DC bin set to 0 (C(s) = sum_x X(x) Y(x+s));
+// grid y = query
 __global__ void k_cross_spectrum(const cufftComplex *FX, const cufftComplex *FY, long long nh, int n,
                                  cufftComplex *Z) {
-    const long long tot = nh * n;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+    const long long off = (long long)blockIdx.y * nh;
+    const cufftComplex *fx = FX + off, *fy = FY + off;
+    cufftComplex *z = Z + off;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nh;
          i += (long long)gridDim.x * blockDim.x) {
-        const cufftComplex a = FX[i], b = FY[i];
-        Z[i] = (i % nh == 0) ? make_cuFloatComplex(0.f, 0.f)
-                             : make_cuFloatComplex(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+        const cufftComplex a = fx[i], b = fy[i];
+        z[i] = i == 0 ? make_cuFloatComplex(0.f, 0.f)
+                      : make_cuFloatComplex(__fmaf_rn(a.x, b.x, a.y * b.y), __fmaf_rn(a.x, b.y, -a.y * b.x));
     }
 }
-
 
 // energy outside the neighbourhood of zero shift and argmax (first index on
 // ties); one row segment per iteration so the row index is known
@@ -351,23 +353,34 @@ __global__ void k_pce_energy(const float *Cr, int H, int W, int r, double *part_
     const int q = blockIdx.y;
     const long long n = (long long)H * W;
     const float *c = Cr + (long long)q * n;
-    double e = 0.0;
+    FF acc{0.f, 0.f};  // float-float energy (no float64 per row)
     float bv = -__int_as_float(0x7f800000);
     long long bi = 0x7fffffffffffffffLL;
+    const bool vec = (W % 4 == 0) && ((reinterpret_cast<uintptr_t>(c) & 15u) == 0);
+    auto one = [&](float v, int y, int x, bool ynear, float &fe) {
+        const bool near = ynear && min(x, W - x) <= r;
+        if (!near) fe = __fmaf_rn(v, v, fe);
+        if (v > bv) { bv = v; bi = (long long)y * W + x; }  // scan order is increasing per thread
+    };
     // rows are distributed over blocks, columns over threads
     for (int y = blockIdx.x; y < H; y += gridDim.x) {
         const bool ynear = min(y, H - y) <= r;
         const float *row = c + (long long)y * W;
         float fe = 0.f;
-        for (int x = threadIdx.x; x < W; x += blockDim.x) {
-            const float v = row[x];
-            const bool near = ynear && min(x, W - x) <= r;
-            if (!near) fe = __fmaf_rn(v, v, fe);
-            if (v > bv) { bv = v; bi = (long long)y * W + x; }  // scan order is increasing per thread
+        if (vec) {
+            for (int x4 = threadIdx.x; x4 < W / 4; x4 += blockDim.x) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(row) + x4);
+                one(v.x, y, 4 * x4, ynear, fe);
+                one(v.y, y, 4 * x4 + 1, ynear, fe);
+                one(v.z, y, 4 * x4 + 2, ynear, fe);
+                one(v.w, y, 4 * x4 + 3, ynear, fe);
+            }
+        } else {
+            for (int x = threadIdx.x; x < W; x += blockDim.x) one(row[x], y, x, ynear, fe);
         }
-        e += fe;
+        ffa(acc, fe);
     }
-    e = block_sum(e, sh);
+    const double e = block_sum(ffd(acc), sh);
     sv[threadIdx.x] = bv;
     si[threadIdx.x] = bi;
     __syncthreads();
@@ -480,7 +493,7 @@ cudaError_t launch_pce_prep(const float *K, long long k_stride, const float *Wq,
 }
 cudaError_t launch_cross_spectrum(const cufftComplex *FX, const cufftComplex *FY, long long nh, int n,
                                   cufftComplex *Z, int sms, cudaStream_t st) {
-    k_cross_spectrum<<<ew_blocks(nh * n, sms), 256, 0, st>>>(FX, FY, nh, n, Z);
+    k_cross_spectrum<<<dim3(ew_blocks(nh, sms), n), 256, 0, st>>>(FX, FY, nh, n, Z);
     return cudaGetLastError();
 }
 cudaError_t launch_pce_reduce(const float *Cr, int H, int W, int r, int n, int nb, double *part_e, float *part_v,
