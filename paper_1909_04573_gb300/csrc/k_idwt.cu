@@ -252,7 +252,7 @@ struct AsyncTile {
 };
 
 template <bool COMP>
-__global__ void __launch_bounds__(256) k_final_async(FinalArgs a) {
+__global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
     constexpr bool MLE = true;
     __shared__ __align__(16) AsyncTile s;
     const int y0 = blockIdx.y * OT, x0 = blockIdx.x * OT;
