@@ -214,33 +214,35 @@ __global__ void k_moments_final(const double *part, int nb, long long n, const d
     }
 }
 
-__global__ void k_to_complex(const float *K, long long n, cufftComplex *F) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        F[i] = make_cuFloatComplex(K[i], 0.f);
-}
-
-__global__ void k_magnitude(const cufftComplex *F, long long n, float inv_sqrt_n, float *M) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        M[i] = hypotf(F[i].x, F[i].y) * inv_sqrt_n;
-}
-
-// F *= Mn/M (0 where M == 0)
-__global__ void k_apply_ratio(cufftComplex *F, const float *M, const float *Mn, long long n) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const float m = M[i];
-        const float r = m > 0.f ? __fdiv_rn(Mn[i], m) : 0.f;
-        F[i].x *= r;
-        F[i].y *= r;
+// DFT-domain Wiener on the half spectrum of a real plane.  |F| is point
+// symmetric (F(-k) = conj F(k)) and so are the windows, so the shrunk
+// magnitudes and the ratio Mn/M are too: the full magnitude plane is built
+// from the half spectrum, and the ratio is applied to the half spectrum
+// before a complex-to-real inverse.
+__global__ void k_magnitude_half(const cufftComplex *Fh, int H, int W, float inv_sqrt_n, float *M) {
+    const int W2 = W / 2 + 1;
+    for (int y = blockIdx.x; y < H; y += gridDim.x) {
+        const cufftComplex *row = Fh + (long long)y * W2;
+        const cufftComplex *mrow = Fh + (long long)((H - y) % H) * W2;  // row of -ky
+        for (int x = threadIdx.x; x < W; x += blockDim.x) {
+            const cufftComplex v = x < W2 ? row[x] : mrow[W - x];
+            M[(long long)y * W + x] = hypotf(v.x, v.y) * inv_sqrt_n;
+        }
     }
 }
 
-__global__ void k_real_scaled(const cufftComplex *F, long long n, float scale, float *K) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        K[i] = F[i].x * scale;
+// Fh *= scale * Mn/M (0 where M == 0) over the half spectrum
+__global__ void k_apply_ratio_half(cufftComplex *Fh, const float *M, const float *Mn, int H, int W, float scale) {
+    const int W2 = W / 2 + 1;
+    for (int y = blockIdx.x; y < H; y += gridDim.x)
+        for (int x = threadIdx.x; x < W2; x += blockDim.x) {
+            const long long o = (long long)y * W + x;
+            const float m = M[o];
+            const float r = m > 0.f ? __fdiv_rn(Mn[o], m) * scale : 0.f;
+            cufftComplex &f = Fh[(long long)y * W2 + x];
+            f.x *= r;
+            f.y *= r;
+        }
 }
 
 // -------------------------------------------------------------------- PCE --
@@ -257,8 +259,8 @@ __global__ void k_pce_prep(const float *Kbase, long long k_stride, const float *
     const float *im = Iq + (long long)q * C * hw;
     float *xo = X + (long long)q * hw;
     float *yo = Y + (long long)q * hw;
-    // per-thread float32 partials over 4 samples, then float64 across
-    double sx = 0.0, sxx = 0.0, sy = 0.0, syy = 0.0;
+    // per-thread float-float sums (float32 partials over 4 samples), float64 only across the block
+    FF sx{0.f, 0.f}, sxx{0.f, 0.f}, sy{0.f, 0.f}, syy{0.f, 0.f};
     auto one = [&](float w0, float w1, float w2, float i0, float i1, float i2, float k, float &a, float &yv) {
         float b;
         if (C == 3) {
@@ -294,10 +296,10 @@ __global__ void k_pce_prep(const float *Kbase, long long k_stride, const float *
             one(w0.w, w1.w, w2.w, i0.w, i1.w, i2.w, k4.w, xa.w, ya.w);
             reinterpret_cast<float4 *>(xo)[i] = xa;
             reinterpret_cast<float4 *>(yo)[i] = ya;
-            sx += (xa.x + xa.y) + (xa.z + xa.w);
-            sxx += __fmaf_rn(xa.x, xa.x, xa.y * xa.y) + __fmaf_rn(xa.z, xa.z, xa.w * xa.w);
-            sy += (ya.x + ya.y) + (ya.z + ya.w);
-            syy += __fmaf_rn(ya.x, ya.x, ya.y * ya.y) + __fmaf_rn(ya.z, ya.z, ya.w * ya.w);
+            ffa(sx, (xa.x + xa.y) + (xa.z + xa.w));
+            ffa(sxx, __fmaf_rn(xa.x, xa.x, xa.y * xa.y) + __fmaf_rn(xa.z, xa.z, xa.w * xa.w));
+            ffa(sy, (ya.x + ya.y) + (ya.z + ya.w));
+            ffa(syy, __fmaf_rn(ya.x, ya.x, ya.y * ya.y) + __fmaf_rn(ya.z, ya.z, ya.w * ya.w));
         }
     } else {
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < hw;
@@ -309,22 +311,22 @@ __global__ void k_pce_prep(const float *Kbase, long long k_stride, const float *
                 one(w[i], 0.f, 0.f, im[i], 0.f, 0.f, K[i], xa, ya);
             xo[i] = xa;
             yo[i] = ya;
-            sx += xa;
-            sxx += (double)xa * xa;
-            sy += ya;
-            syy += (double)ya * ya;
+            ffa(sx, xa);
+            ffa(sxx, xa * xa);
+            ffa(sy, ya);
+            ffa(syy, ya * ya);
         }
     }
-    sx = block_sum(sx, sh);
-    sxx = block_sum(sxx, sh);
-    sy = block_sum(sy, sh);
-    syy = block_sum(syy, sh);
+    const double bx = block_sum(ffd(sx), sh);
+    const double bxx = block_sum(ffd(sxx), sh);
+    const double by = block_sum(ffd(sy), sh);
+    const double byy = block_sum(ffd(syy), sh);
     if (threadIdx.x == 0) {
         double *o = part + ((long long)q * gridDim.x + blockIdx.x) * 4;
-        o[0] = sx;
-        o[1] = sxx;
-        o[2] = sy;
-        o[3] = syy;
+        o[0] = bx;
+        o[1] = bxx;
+        o[2] = by;
+        o[3] = byy;
     }
 }
 
@@ -467,23 +469,14 @@ cudaError_t launch_mean_var(const float *v, long long n, double *part, int nb, d
     return cudaGetLastError();
 }
 
-cudaError_t launch_to_complex(const float *K, long long n, cufftComplex *F, int sms, cudaStream_t st) {
-    k_to_complex<<<ew_blocks(n, sms), 256, 0, st>>>(K, n, F);
+cudaError_t launch_magnitude_half(const cufftComplex *Fh, int H, int W, float inv_sqrt_n, float *M, int sms,
+                                  cudaStream_t st) {
+    k_magnitude_half<<<(unsigned)std::min(H, sms * 8), 256, 0, st>>>(Fh, H, W, inv_sqrt_n, M);
     return cudaGetLastError();
 }
-cudaError_t launch_magnitude(const cufftComplex *F, long long n, float inv_sqrt_n, float *M, int sms,
-                             cudaStream_t st) {
-    k_magnitude<<<ew_blocks(n, sms), 256, 0, st>>>(F, n, inv_sqrt_n, M);
-    return cudaGetLastError();
-}
-cudaError_t launch_apply_ratio(cufftComplex *F, const float *M, const float *Mn, long long n, int sms,
-                               cudaStream_t st) {
-    k_apply_ratio<<<ew_blocks(n, sms), 256, 0, st>>>(F, M, Mn, n);
-    return cudaGetLastError();
-}
-cudaError_t launch_real_scaled(const cufftComplex *F, long long n, float scale, float *K, int sms,
-                               cudaStream_t st) {
-    k_real_scaled<<<ew_blocks(n, sms), 256, 0, st>>>(F, n, scale, K);
+cudaError_t launch_apply_ratio_half(cufftComplex *Fh, const float *M, const float *Mn, int H, int W, float scale,
+                                    int sms, cudaStream_t st) {
+    k_apply_ratio_half<<<(unsigned)std::min(H, sms * 8), 256, 0, st>>>(Fh, M, Mn, H, W, scale);
     return cudaGetLastError();
 }
 cudaError_t launch_pce_prep(const float *K, long long k_stride, const float *Wq, const float *Iq, long long hw, int C,

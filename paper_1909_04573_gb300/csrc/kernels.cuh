@@ -102,13 +102,10 @@ cudaError_t launch_zero_mean(float *K, int H, int W, double *colmean, double *ro
                              cudaStream_t st);
 cudaError_t launch_mean_var(const float *v, long long n, double *part, int nb, double *tmp, double *out,
                             cudaStream_t st);
-cudaError_t launch_to_complex(const float *K, long long n, cufftComplex *F, int sms, cudaStream_t st);
-cudaError_t launch_magnitude(const cufftComplex *F, long long n, float inv_sqrt_n, float *M, int sms,
-                             cudaStream_t st);
-cudaError_t launch_apply_ratio(cufftComplex *F, const float *M, const float *Mn, long long n, int sms,
-                               cudaStream_t st);
-cudaError_t launch_real_scaled(const cufftComplex *F, long long n, float scale, float *K, int sms,
-                               cudaStream_t st);
+cudaError_t launch_magnitude_half(const cufftComplex *Fh, int H, int W, float inv_sqrt_n, float *M, int sms,
+                                  cudaStream_t st);
+cudaError_t launch_apply_ratio_half(cufftComplex *Fh, const float *M, const float *Mn, int H, int W, float scale,
+                                    int sms, cudaStream_t st);
 cudaError_t launch_pce_prep(const float *K, long long k_stride, const float *Wq, const float *Iq, long long hw, int C,
                             int n, int nb, float *X, float *Y, double *part, cudaStream_t st);
 cudaError_t launch_cross_spectrum(const cufftComplex *FX, const cufftComplex *FY, long long nh, int n,

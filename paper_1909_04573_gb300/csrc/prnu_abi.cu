@@ -355,7 +355,7 @@ prnu_status fft_layout(prnu_ctx *ctx, int H, int W, int n, FftLayout *out) {
     const size_t nh = (size_t)H * (W / 2 + 1);
     f.nb = (int)std::min<size_t>(256, std::max<size_t>(1, hw / (256 * 16)));
     f.nbm = f.nb;
-    f.cplx = take(std::max(2 * (size_t)n * nh, hw) * sizeof(cufftComplex));
+    f.cplx = take(2 * (size_t)std::max(n, 1) * nh * sizeof(cufftComplex));
     f.real = take(2 * (size_t)std::max(n, 1) * hw * sizeof(float));
     f.colmean = take((size_t)W * sizeof(double));
     f.colpart = take((size_t)((H + 63) / 64) * W * sizeof(double));
@@ -371,7 +371,9 @@ prnu_status fft_layout(prnu_ctx *ctx, int H, int W, int n, FftLayout *out) {
     size_t w = 0, wmax = 0;
     cufftHandle p;
     prnu_status s;
-    if ((s = get_plan(ctx, H, W, CUFFT_C2C, 1, &p, &w)) != PRNU_OK) return s;
+    if ((s = get_plan(ctx, H, W, CUFFT_R2C, 1, &p, &w)) != PRNU_OK) return s;  // finalize's Wiener step
+    wmax = std::max(wmax, w);
+    if ((s = get_plan(ctx, H, W, CUFFT_C2R, 1, &p, &w)) != PRNU_OK) return s;
     wmax = std::max(wmax, w);
     if ((s = get_plan(ctx, H, W, CUFFT_R2C, 2 * n, &p, &w)) != PRNU_OK) return s;
     wmax = std::max(wmax, w);
@@ -844,10 +846,11 @@ prnu_status prnu_fingerprint_finalize(prnu_ctx *ctx, const float *num, const flo
                                     reinterpret_cast<double *>(b + f.colpart), ctx->sms, st));
             }
         if (flags & PRNU_WIENER_DFT) {
-            cufftHandle plan;
+            cufftHandle r2c, c2r;
             size_t work;
-            if ((s = get_plan(ctx, H, W, CUFFT_C2C, 1, &plan, &work)) != PRNU_OK) return s;
-            cufftComplex *F = reinterpret_cast<cufftComplex *>(b + f.cplx);
+            if ((s = get_plan(ctx, H, W, CUFFT_R2C, 1, &r2c, &work)) != PRNU_OK) return s;
+            if ((s = get_plan(ctx, H, W, CUFFT_C2R, 1, &c2r, &work)) != PRNU_OK) return s;
+            cufftComplex *F = reinterpret_cast<cufftComplex *>(b + f.cplx);  // half spectrum
             float *M = reinterpret_cast<float *>(b + f.real);
             float *Mn = M + hw;
             double *mom = reinterpret_cast<double *>(b + f.mom0);
@@ -857,18 +860,14 @@ prnu_status prnu_fingerprint_finalize(prnu_ctx *ctx, const float *num, const flo
                                    reinterpret_cast<double *>(b + f.tmp), mom, st));
             }
             {
-                Launch t(ctx, "to_complex", st, 1);
-                CU(launch_to_complex(K, hw, F, ctx->sms, st));
-            }
-            CUFFT(cufftSetStream(plan, st));
-            CUFFT(cufftSetWorkArea(plan, b + f.work));
-            {
-                Launch t(ctx, "cufft_c2c", st, 1);
-                CUFFT(cufftExecC2C(plan, F, F, CUFFT_FORWARD));
+                Launch t(ctx, "cufft_r2c", st, 1);
+                CUFFT(cufftSetStream(r2c, st));
+                CUFFT(cufftSetWorkArea(r2c, b + f.work));
+                CUFFT(cufftExecR2C(r2c, K, F));
             }
             {
                 Launch t(ctx, "wiener_magnitude", st, 1);
-                CU(launch_magnitude(F, hw, (float)(1.0 / std::sqrt((double)hw)), M, ctx->sms, st));
+                CU(launch_magnitude_half(F, H, W, (float)(1.0 / std::sqrt((double)hw)), M, ctx->sms, st));
             }
             ShrinkArgs sa{};
             sa.in = M;
@@ -884,16 +883,14 @@ prnu_status prnu_fingerprint_finalize(prnu_ctx *ctx, const float *num, const flo
                 CU(launch_shrink(sa, st));
             }
             {
-                Launch t(ctx, "wiener_ratio", st, 1);
-                CU(launch_apply_ratio(F, M, Mn, hw, ctx->sms, st));
+                Launch t(ctx, "wiener_ratio", st, 1);  // with the inverse transform's 1/N
+                CU(launch_apply_ratio_half(F, M, Mn, H, W, (float)(1.0 / (double)hw), ctx->sms, st));
             }
             {
-                Launch t(ctx, "cufft_c2c", st, 1);
-                CUFFT(cufftExecC2C(plan, F, F, CUFFT_INVERSE));
-            }
-            {
-                Launch t(ctx, "wiener_real", st, 1);
-                CU(launch_real_scaled(F, hw, (float)(1.0 / (double)hw), K, ctx->sms, st));
+                Launch t(ctx, "cufft_c2r", st, 1);
+                CUFFT(cufftSetStream(c2r, st));
+                CUFFT(cufftSetWorkArea(c2r, b + f.work));
+                CUFFT(cufftExecC2R(c2r, F, K));
             }
         }
     }
