@@ -23,5 +23,5 @@ from .pipeline import (DEFAULT, TO_GRAY, WIENER_DFT, ZERO_MEAN, Params, PCEResul
                        residual, residual_noise_form, sda_average, shrink_subband, to_gray,
                        wavedec2, waverec2, wiener_dft, zero_mean)
 from .wavelet import daubechies_lowpass, dwt_matrix_1d, highpass  # noqa: F401
-from .native import build, threads  # noqa: F401
+from .native import build, set_threads, threads  # noqa: F401
 from . import grad  # noqa: F401

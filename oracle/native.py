@@ -82,11 +82,16 @@ def lib() -> ctypes.CDLL:
     return _lib
 
 
+_threads_set = None
+
+
 def threads() -> int:
     """Threads the C core runs with (1 when built without OpenMP)."""
     lib()
     if not _openmp:
         return 1
+    if _threads_set:
+        return _threads_set
     n = os.environ.get("OMP_NUM_THREADS")
     if n:
         return int(n)
@@ -94,6 +99,25 @@ def threads() -> int:
         return len(os.sched_getaffinity(0))
     except AttributeError:  # pragma: no cover
         return os.cpu_count() or 1
+
+
+def set_threads(n: int | None) -> int:
+    """Run the C core's parallel loops on n threads (None: back to the
+    default, all cores of the affinity mask); returns the count in effect.
+    Results do not depend on it (every parallel loop writes disjoint
+    outputs)."""
+    global _threads_set
+    L = lib()
+    if not _openmp:
+        return 1
+    fn = getattr(L, "omp_set_num_threads", None)  # from the OpenMP runtime the library links
+    if fn is None:  # pragma: no cover
+        return threads()
+    _threads_set = None
+    want = int(n) if n else threads()
+    fn(ctypes.c_int(want))
+    _threads_set = int(n) if n else None
+    return threads()
 
 
 def dptr(a: np.ndarray):

@@ -161,3 +161,16 @@ def test_more_groups_give_a_better_fingerprint_and_sda_costs_little_on_smooth_sc
     assert corr(16, 4) < corr(64, 4)                    # more frames, better K
     # smooth scenes: the SDA estimator is close to the per-frame one (Sec. III remarks)
     assert corr(64, 4) > 0.8 * corr(64, 1)
+
+
+def test_oracle_results_do_not_depend_on_the_thread_count():
+    rng = np.random.default_rng(11)
+    frames = rng.integers(0, 256, size=(6, 40, 56, 3), dtype=np.uint8)
+    ref = O.fingerprint_accumulate(frames, 3)
+    try:
+        assert O.set_threads(1) == 1
+        one = O.fingerprint_accumulate(frames, 3)
+    finally:
+        O.set_threads(None)
+    np.testing.assert_array_equal(one[0], ref[0])
+    np.testing.assert_array_equal(one[1], ref[1])
