@@ -169,10 +169,10 @@ __global__ void __launch_bounds__(256) k_final(FinalArgs a) {
     for (int k = 0; k < 4; ++k) { an[k] = 0.f; ad[k] = 0.f; anl[k] = 0.f; adl[k] = 0.f; }
     const long long hw = (long long)a.H * a.W;
     const int nimg = MLE ? a.G : 1;
-    int cam = (MLE && a.gd) ? a.gd[0].cam : -1;  // multi-camera pass: current camera
+    int cam = a.gd ? a.gd[0].cam : -1;  // multi-camera pass: current camera
     for (int i = 0; i < nimg; ++i) {
         const int plane = MLE ? i * a.C + (int)blockIdx.z : (int)blockIdx.z;
-        if (MLE && a.gd && a.gd[i].cam != cam) {  // block-uniform: the camera changes
+        if (a.gd && a.gd[i].cam != cam) {  // block-uniform: the camera changes
             mle_flush<COMP>(a, a.cams[cam].num, a.cams[cam].den, an, ad, anl, adl, y0, x0, tid);
 #pragma unroll
             for (int k = 0; k < 4; ++k) { an[k] = 0.f; ad[k] = 0.f; anl[k] = 0.f; adl[k] = 0.f; }
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256) k_final(FinalArgs a) {
         __syncthreads();
         synth_cols(s, a.f, tid);
         __syncthreads();
-        const float inv_n = MLE ? __frcp_rn((float)a.sc.count(plane)) : 1.f;
+        const float inv_n = __frcp_rn((float)a.sc.count(plane));
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int it = tid + 256 * k;
@@ -247,13 +247,12 @@ __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_grou
 
 struct AsyncTile {
     float c[2][4][CT][CT + 1];  // LL, LH, HL, HH coefficient tiles, double-buffered
-    float x[2][OT][OT];         // MLE mode: the image tile (group sums)
+    float x[2][OT][OT];         // the image tile (group sums)
     float lo[OT][CT + 1], hi[OT][CT + 1];
 };
 
 template <bool COMP>
 __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
-    constexpr bool MLE = true;
     __shared__ __align__(16) AsyncTile s;
     const int y0 = blockIdx.y * OT, x0 = blockIdx.x * OT;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -278,20 +277,18 @@ __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
                 cp_async4(&s.c[b][3][r][tx], HH + o);
             }
         }
-        if (MLE) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int it = tid + 256 * k;
-                const int y = it >> 5, xx = it & 31;
-                const int gy = y0 + y, gx = x0 + xx;
-                if (gy < a.H && gx < a.W) cp_async4(&s.x[b][y][xx], a.X + (long long)plane * hw + (long long)gy * a.W + gx);
-            }
+        for (int k = 0; k < 4; ++k) {
+            const int it = tid + 256 * k;
+            const int y = it >> 5, xx = it & 31;
+            const int gy = y0 + y, gx = x0 + xx;
+            if (gy < a.H && gx < a.W) cp_async4(&s.x[b][y][xx], a.X + (long long)plane * hw + (long long)gy * a.W + gx);
         }
     };
     float an[4], ad[4], anl[4], adl[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) { an[k] = 0.f; ad[k] = 0.f; anl[k] = 0.f; adl[k] = 0.f; }
-    int cam = (MLE && a.gd) ? a.gd[0].cam : -1;
+    int cam = a.gd ? a.gd[0].cam : -1;
     issue(plane_of(0), 0);
     cp_commit();
     for (int i = 0; i < nimg; ++i) {
@@ -301,7 +298,7 @@ __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
         __syncthreads();  // image i landed; every reader of the other buffer and of lo/hi is done
         if (i + 1 < nimg) issue(plane_of(i + 1), b ^ 1);
         cp_commit();
-        if (MLE && a.gd && a.gd[i].cam != cam) {  // block-uniform: the camera changes
+        if (a.gd && a.gd[i].cam != cam) {  // block-uniform: the camera changes
             mle_flush<COMP>(a, a.cams[cam].num, a.cams[cam].den, an, ad, anl, adl, y0, x0, tid);
 #pragma unroll
             for (int k = 0; k < 4; ++k) { an[k] = 0.f; ad[k] = 0.f; anl[k] = 0.f; adl[k] = 0.f; }
@@ -331,7 +328,7 @@ __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
             }
         }
         __syncthreads();
-        const float inv_n = MLE ? __frcp_rn((float)a.sc.count(plane)) : 1.f;
+        const float inv_n = __frcp_rn((float)a.sc.count(plane));
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int it = tid + 256 * k;
@@ -356,33 +353,29 @@ __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
                 }
                 w[e] = v;
             }
-            if (MLE) {
-                const float I0 = s.x[b][y][2 * n] * inv_n;
-                const float I1 = two ? s.x[b][y][2 * n + 1] * inv_n : 0.f;
-                if (COMP) {
-                    ff_add(an[2 * k], anl[2 * k], w[0] * I0);
-                    ff_add(ad[2 * k], adl[2 * k], I0 * I0);
-                    if (two) {
-                        ff_add(an[2 * k + 1], anl[2 * k + 1], w[1] * I1);
-                        ff_add(ad[2 * k + 1], adl[2 * k + 1], I1 * I1);
-                    }
-                } else {
-                    an[2 * k] = __fmaf_rn(w[0], I0, an[2 * k]);
-                    ad[2 * k] = __fmaf_rn(I0, I0, ad[2 * k]);
-                    if (two) {
-                        an[2 * k + 1] = __fmaf_rn(w[1], I1, an[2 * k + 1]);
-                        ad[2 * k + 1] = __fmaf_rn(I1, I1, ad[2 * k + 1]);
-                    }
+            const float I0 = s.x[b][y][2 * n] * inv_n;
+            const float I1 = two ? s.x[b][y][2 * n + 1] * inv_n : 0.f;
+            if (COMP) {
+                ff_add(an[2 * k], anl[2 * k], w[0] * I0);
+                ff_add(ad[2 * k], adl[2 * k], I0 * I0);
+                if (two) {
+                    ff_add(an[2 * k + 1], anl[2 * k + 1], w[1] * I1);
+                    ff_add(ad[2 * k + 1], adl[2 * k + 1], I1 * I1);
+                }
+            } else {
+                an[2 * k] = __fmaf_rn(w[0], I0, an[2 * k]);
+                ad[2 * k] = __fmaf_rn(I0, I0, ad[2 * k]);
+                if (two) {
+                    an[2 * k + 1] = __fmaf_rn(w[1], I1, an[2 * k + 1]);
+                    ad[2 * k + 1] = __fmaf_rn(I1, I1, ad[2 * k + 1]);
                 }
             }
         }
     }
-    if (MLE) {
-        if (a.gd)
-            mle_flush<COMP>(a, a.cams[cam].num, a.cams[cam].den, an, ad, anl, adl, y0, x0, tid);
-        else
-            mle_flush<COMP>(a, a.num, a.den, an, ad, anl, adl, y0, x0, tid);
-    }
+    if (a.gd)
+        mle_flush<COMP>(a, a.cams[cam].num, a.cams[cam].den, an, ad, anl, adl, y0, x0, tid);
+    else
+        mle_flush<COMP>(a, a.num, a.den, an, ad, anl, adl, y0, x0, tid);
 }
 
 
