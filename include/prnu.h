@@ -268,6 +268,15 @@ prnu_status prnu_pce_match_images(prnu_ctx *ctx, const float *K, const float *im
                                   const prnu_params *params, int nbhd, double *pce_out, double *ncc_out,
                                   int *peak_yx, void *ws, size_t ws_bytes, void *stream);
 
+/* prnu_pce_match_images with its outputs left on the device: pce_dev[n],
+ * ncc_dev[n] (nullable) and peak_dev[2n] (nullable) are device pointers,
+ * written by the last kernel of the call.  Nothing synchronises, so the call
+ * can be captured in a CUDA graph once the workspace and the cuFFT plans exist
+ * (after one uncaptured call with the same geometry). */
+prnu_status prnu_pce_match_images_async(prnu_ctx *ctx, const float *K, const float *img_q, int n, int H, int W,
+                                        int C, const prnu_params *params, int nbhd, double *pce_dev, double *ncc_dev,
+                                        int *peak_dev, void *ws, size_t ws_bytes, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Differentiation.  The chain of Sec. III-A / III-B with the SDA weights made
  * free (the paper's SDA frame is the equal-weight case w_j = 1/d) and sigma0
@@ -355,8 +364,18 @@ prnu_status prnu_autotune_set(prnu_ctx *ctx, int H, int W, const prnu_params *pa
 /* Per-kernel profiling (not part of the paper's method).  Every kernel launch
  * is counted per kernel name.  With profiling on, each launch (and each cuFFT
  * call, named cufft_*) is also bracketed by CUDA events recorded on its
- * stream; the events are drawn from a pool the context owns. */
+ * stream; the events are drawn from a pool the context owns.  Under stream
+ * capture the events become event-record nodes of the graph (launches are
+ * counted once, at capture), so prnu_profile_read then reports the device time
+ * of the graph's latest replay.  Destroy such a graph before
+ * prnu_profile_reset, which returns its events to the pool. */
 prnu_status prnu_profile_enable(prnu_ctx *ctx, int on);
+
+/* Restricts the event timing of prnu_profile_enable to the kernels named in
+ * `names`, a comma-separated list of profile names ("shrink,sda_sum"); the
+ * other launches are still counted.  NULL or "" times every launch again.
+ * Host only; the string is copied. */
+prnu_status prnu_profile_select(prnu_ctx *ctx, const char *names);
 
 /* Clear the counters and recorded events (waits for the recorded events). */
 prnu_status prnu_profile_reset(prnu_ctx *ctx);

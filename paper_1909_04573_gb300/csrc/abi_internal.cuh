@@ -25,6 +25,7 @@ struct prnu_ctx {
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
     // per-kernel launch counters (always) and CUDA-event timing (opt-in)
     bool prof_on = false;
+    std::vector<std::string> prof_sel;  // kernels to time (empty: all)
     std::vector<std::string> knames;
     std::vector<long long> klaunches;
     std::vector<double> kbytes;  // algorithmic bytes of the counted launches
@@ -89,10 +90,12 @@ struct Launch {
         }
         ctx->klaunches[kid] += kernels;
         ctx->kbytes[kid] += bytes;
-        if (ctx->prof_on) {
+        bool timed = ctx->prof_on && ctx->prof_sel.empty();
+        for (size_t i = 0; ctx->prof_on && !timed && i < ctx->prof_sel.size(); ++i) timed = ctx->prof_sel[i] == name;
+        if (timed) {
             a = take();
             b = take();
-            if (a && b) cudaEventRecord(a, st);
+            if (a && b) record(a);
         }
     }
     cudaEvent_t take() {
@@ -104,9 +107,19 @@ struct Launch {
         cudaEvent_t e = nullptr;
         return cudaEventCreate(&e) == cudaSuccess ? e : nullptr;
     }
+    // Under stream capture the record becomes an event node of the graph, so
+    // that each replay re-times the launch; the events stay checked out of the
+    // pool until prnu_profile_reset.
+    void record(cudaEvent_t e) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+            cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+        else
+            cudaEventRecord(e, st);
+    }
     ~Launch() {
         if (a && b) {
-            cudaEventRecord(b, st);
+            record(b);
             std::lock_guard<std::mutex> lk(ctx->mu);
             ctx->recs.push_back({kid, a, b});
         }
@@ -160,6 +173,8 @@ struct FftLayout {
     size_t colpart = 0;               // doubles: partial column sums per 64-row band
     size_t part = 0, tmp = 0, mom0 = 0;
     size_t pm = 0, pe = 0, pv = 0, pi = 0, scal = 0;
+    size_t tw = 0, c0 = 0;            // own-FFT correlation: twiddles, C(0, 0) per query
+    bool own_fft = false;             // PCE correlation by k_corr.cu instead of cuFFT
     size_t work = 0, end = 0;
     int nb = 0, nbm = 0;              // reduction blocks per query
 };

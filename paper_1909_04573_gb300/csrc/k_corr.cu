@@ -1,0 +1,574 @@
+// Circular cross-correlation of the PCE test (Sec. IV) by our own mixed-radix
+// FFTs, fused so that the spectra pass through HBM as few times as possible:
+//
+//   1. k_rfft_rows     one real FFT per row of X_i and Y_i (length W, as a
+//                      complex FFT of length W/2 plus the split step), half
+//                      spectra to a padded complex workspace;
+//   2. k_corr_columns  per query and tile of spectrum columns: the column FFTs
+//                      of X^ and Y^, the cross spectrum conj(X^) Y^ with its
+//                      DC bin zeroed (the means removed), and the inverse
+//                      column FFT, all in shared memory; the result replaces X^;
+//   3. k_corr_rows     per row: the inverse real FFT (the split step, then a
+//                      complex FFT of length W/2) and, on the correlation row
+//                      it leaves in shared memory, the PCE reductions: energy
+//                      outside the (2r+1)^2 neighbourhood of zero shift, the
+//                      argmax (first index on ties) and C(0, 0).
+//
+// The correlation plane itself is never written.  All transforms are
+// unnormalised (the result is H*W times the correlation), like cuFFT's.
+//
+// Each 1-D transform is a Stockham autosort FFT over the factors 8, 4, 2, 3,
+// 5, 7 of its length; one pass per factor, ping-ponging between two shared
+// buffers.  Several sequences are interleaved element by element (element j of
+// sequence g at j*G + g) and consecutive threads take consecutive sequences,
+// so every shared-memory access of a pass is conflict-free.  Twiddles are
+// computed once per call in float64 (k_twiddles) and rounded to float.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+
+#include "kernels.cuh"
+
+namespace prnu {
+namespace {
+
+constexpr int CT = 256;  // threads per block of the three kernels
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(__fmaf_rn(a.x, b.x, -a.y * b.y), __fmaf_rn(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmi(float2 a) { return make_float2(a.y, -a.x); }  // -i a
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// ---------------------------------------------------------- small DFTs ---
+// Forward (exponent sign -1), in registers.
+template <int R>
+struct Dft;
+
+template <>
+struct Dft<2> {
+    static __device__ __forceinline__ void run(float2 *v) {
+        const float2 t = v[0];
+        v[0] = cadd(t, v[1]);
+        v[1] = csub(t, v[1]);
+    }
+};
+
+template <>
+struct Dft<4> {
+    static __device__ __forceinline__ void run(float2 *v) {
+        const float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+        const float2 s13 = cadd(v[1], v[3]), d13 = cmi(csub(v[1], v[3]));
+        v[0] = cadd(s02, s13);
+        v[2] = csub(s02, s13);
+        v[1] = cadd(d02, d13);
+        v[3] = csub(d02, d13);
+    }
+};
+
+template <>
+struct Dft<8> {
+    static __device__ __forceinline__ void run(float2 *v) {
+        constexpr float h = 0.70710678118654752f;  // sqrt(1/2)
+        float2 e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+        Dft<4>::run(e);
+        Dft<4>::run(o);
+        o[1] = make_float2((o[1].x + o[1].y) * h, (o[1].y - o[1].x) * h);   // * e^{-i pi/4}
+        o[2] = cmi(o[2]);                                                   // * e^{-i pi/2}
+        o[3] = make_float2((o[3].y - o[3].x) * h, -(o[3].x + o[3].y) * h);  // * e^{-3i pi/4}
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = cadd(e[k], o[k]);
+            v[k + 4] = csub(e[k], o[k]);
+        }
+    }
+};
+
+template <>
+struct Dft<3> {
+    static __device__ __forceinline__ void run(float2 *v) {
+        constexpr float c = 0.86602540378443865f;  // sin(2 pi / 3)
+        const float2 s = cadd(v[1], v[2]), d = cmi(csub(v[1], v[2]));
+        const float2 t = make_float2(__fmaf_rn(-0.5f, s.x, v[0].x), __fmaf_rn(-0.5f, s.y, v[0].y));
+        v[0] = cadd(v[0], s);
+        v[1] = make_float2(__fmaf_rn(c, d.x, t.x), __fmaf_rn(c, d.y, t.y));
+        v[2] = make_float2(__fmaf_rn(-c, d.x, t.x), __fmaf_rn(-c, d.y, t.y));
+    }
+};
+
+// odd prime R: y_k = v_0 + sum_{m=1}^{(R-1)/2} [(v_m + v_{R-m}) cos(2 pi m k / R)
+//                                             - i (v_m - v_{R-m}) sin(2 pi m k / R)]
+// and y_{R-k} the same with +i; cos/sin of 2 pi q / R for q = 0..(R-1)/2.
+template <int R>
+struct OddConst;
+template <>
+struct OddConst<5> {
+    static __device__ __forceinline__ float c(int q) {
+        return q == 0 ? 1.f : (q == 1 ? 0.30901699437494742f : -0.80901699437494742f);
+    }
+    static __device__ __forceinline__ float s(int q) {
+        return q == 0 ? 0.f : (q == 1 ? 0.95105651629515357f : 0.58778525229247313f);
+    }
+};
+template <>
+struct OddConst<7> {
+    static __device__ __forceinline__ float c(int q) {
+        return q == 0 ? 1.f
+                      : (q == 1 ? 0.62348980185873353f : (q == 2 ? -0.22252093395631440f : -0.90096886790241913f));
+    }
+    static __device__ __forceinline__ float s(int q) {
+        return q == 0 ? 0.f : (q == 1 ? 0.78183148246802981f : (q == 2 ? 0.97492791218182361f : 0.43388373911755812f));
+    }
+};
+
+template <int R>
+struct DftOdd {
+    static __device__ __forceinline__ void run(float2 *v) {
+        constexpr int H = (R - 1) / 2;
+        float2 A[H + 1], B[H + 1];
+#pragma unroll
+        for (int m = 1; m <= H; ++m) {
+            A[m] = cadd(v[m], v[R - m]);
+            B[m] = cmi(csub(v[m], v[R - m]));  // -i (v_m - v_{R-m})
+        }
+        float2 y0 = v[0];
+#pragma unroll
+        for (int m = 1; m <= H; ++m) y0 = cadd(y0, A[m]);
+        float2 out[R];
+        out[0] = y0;
+#pragma unroll
+        for (int k = 1; k <= H; ++k) {
+            float2 re = v[0], im = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int m = 1; m <= H; ++m) {
+                const int idx = (m * k) % R;
+                const int q = idx <= H ? idx : R - idx;
+                const float cs = OddConst<R>::c(q);
+                const float sn = idx <= H ? OddConst<R>::s(q) : -OddConst<R>::s(q);
+                re = make_float2(__fmaf_rn(cs, A[m].x, re.x), __fmaf_rn(cs, A[m].y, re.y));
+                im = make_float2(__fmaf_rn(sn, B[m].x, im.x), __fmaf_rn(sn, B[m].y, im.y));
+            }
+            out[k] = cadd(re, im);
+            out[R - k] = csub(re, im);
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[k] = out[k];
+    }
+};
+template <>
+struct Dft<5> : DftOdd<5> {};
+template <>
+struct Dft<7> : DftOdd<7> {};
+
+// ------------------------------------------------------ Stockham passes ---
+// One radix-R pass over NA sequences of length L laid out with stride G
+// (element j of sequence g at j*G + g), from a to b; Ns = product of the
+// radices already applied.  INV: exponent sign +1.
+template <int R, int G, int NA, bool INV>
+__device__ __forceinline__ void fft_pass(const float2 *__restrict__ a, float2 *__restrict__ b, int L, int Ns,
+                                         const float2 *__restrict__ tw) {
+    const int nb = L / R;
+    const int step = L / (Ns * R);
+    for (int u = threadIdx.x; u < nb * NA; u += blockDim.x) {
+        const int g = u % NA, j = u / NA;
+        const int k = j % Ns;
+        float2 v[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = a[(j + m * nb) * G + g];
+        if (k) {
+            const int ts = k * step;  // twiddle of element m: w_L^{m k step}, m k step < L
+#pragma unroll
+            for (int m = 1; m < R; ++m) {
+                float2 t = tw[m * ts];
+                if (INV) t.y = -t.y;
+                v[m] = cmul(v[m], t);
+            }
+        }
+        if (INV) {
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[m] = cconj(v[m]);
+        }
+        Dft<R>::run(v);
+        if (INV) {
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[m] = cconj(v[m]);
+        }
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int m = 0; m < R; ++m) b[(base + m * Ns) * G + g] = v[m];
+    }
+}
+
+// All passes; the input is in a (visible to the block), the result in the
+// returned buffer (a or b), visible to the block on return.
+template <int G, int NA, bool INV>
+__device__ float2 *fft_run(float2 *a, float2 *b, const FftSteps &p, const float2 *tw) {
+    int Ns = 1;
+    for (int i = 0; i < p.np; ++i) {
+        const int R = p.r(i);
+        switch (R) {
+            case 8: fft_pass<8, G, NA, INV>(a, b, p.L, Ns, tw); break;
+            case 4: fft_pass<4, G, NA, INV>(a, b, p.L, Ns, tw); break;
+            case 2: fft_pass<2, G, NA, INV>(a, b, p.L, Ns, tw); break;
+            case 3: fft_pass<3, G, NA, INV>(a, b, p.L, Ns, tw); break;
+            case 5: fft_pass<5, G, NA, INV>(a, b, p.L, Ns, tw); break;
+            default: fft_pass<7, G, NA, INV>(a, b, p.L, Ns, tw); break;
+        }
+        __syncthreads();
+        float2 *t = a;
+        a = b;
+        b = t;
+        Ns *= R;
+    }
+    return a;
+}
+
+// 8-byte global -> shared copies in flight together (cp.async groups)
+__device__ __forceinline__ void cp_async8(float2 *dst, const float2 *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void load_table(float2 *dst, const float2 *__restrict__ src, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+// ------------------------------------------------------------- kernels ---
+// tw_m[i] = e^{-2 pi i i / M} (i < M), tw_h[k] = e^{-2 pi i k / W} (k <= M),
+// tw_c[i] = e^{-2 pi i i / H} (i < H), M = W / 2; float64 then rounded.
+__global__ void k_twiddles(float2 *tw, int M, int H) {
+    const int n = M + (M + 1) + H;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double a;  // angle / (-pi)
+        if (i < M)
+            a = 2.0 * i / M;
+        else if (i < 2 * M + 1)
+            a = (double)(i - M) / M;
+        else
+            a = 2.0 * (i - 2 * M - 1) / H;
+        double s, c;
+        sincospi(-a, &s, &c);
+        tw[i] = make_float2((float)c, (float)s);
+    }
+}
+
+// Real FFT of nrows rows of length W (pitch W floats) to half spectra of
+// M + 1 bins (pitch ldo complex); G rows per block iteration.  Three buffers
+// rotate: the next rows are staged (cp.async) while the current ones are
+// transformed in the other two.
+template <int G>
+__global__ void __launch_bounds__(CT) k_rfft_rows(const float *__restrict__ x, float2 *__restrict__ out,
+                                                  long long nrows, int W, int ldo, FftSteps p,
+                                                  const float2 *__restrict__ twg) {
+    extern __shared__ float2 sm[];
+    const int M = W >> 1;
+    float2 *tw = sm, *twh = sm + M;
+    float2 *const buf0 = twh + M + 1;  // three buffers of G * M
+    load_table(tw, twg, 2 * M + 1);
+    auto stage = [&](long long r0, float2 *dst) {
+        for (int u = threadIdx.x; u < G * M; u += blockDim.x) {
+            const int g = u % G, m = u / G;
+            const long long r = r0 + g;
+            if (r < nrows)
+                cp_async8(dst + m * G + g, reinterpret_cast<const float2 *>(x + r * W) + m);
+            else
+                dst[m * G + g] = make_float2(0.f, 0.f);
+        }
+    };
+    const long long stride = (long long)gridDim.x * G;
+    long long r0 = (long long)blockIdx.x * G;
+    if (r0 < nrows) stage(r0, buf0);
+    cp_async_commit();
+    for (int i = 0; r0 < nrows; r0 += stride, ++i) {
+        float2 *cur = buf0 + (i % 3) * G * M, *nxt = buf0 + ((i + 1) % 3) * G * M,
+               *scr = buf0 + ((i + 2) % 3) * G * M;
+        if (r0 + stride < nrows) stage(r0 + stride, nxt);
+        cp_async_commit();
+        cp_async_wait<1>();  // this iteration's rows have landed
+        __syncthreads();
+        const float2 *Z = fft_run<G, G, false>(cur, scr, p, tw);
+        // split step: X_k = (Z_k + conj Z_{M-k}) / 2 - i w_W^k (Z_k - conj Z_{M-k}) / 2
+        for (int u = threadIdx.x; u < G * (M + 1); u += blockDim.x) {
+            const int g = u % G, k = u / G;
+            const long long r = r0 + g;
+            if (r >= nrows) continue;
+            const float2 zk = Z[(k == M ? 0 : k) * G + g];
+            const float2 zc = cconj(Z[(k == 0 ? 0 : M - k) * G + g]);
+            const float2 s = cadd(zk, zc), wd = cmul(twh[k], csub(zk, zc));
+            out[r * ldo + k] = make_float2(0.5f * (s.x + wd.y), 0.5f * (s.y - wd.x));
+        }
+        __syncthreads();  // cur / scr are restaged from the next iteration on
+    }
+    cp_async_wait<0>();
+}
+
+// Per query q (grid y) and tile of TC spectrum columns (grid x): column FFTs
+// of X^_q and Y^_q (F + q*H*ld and F + (n+q)*H*ld, pitch ld), Z = conj(X^) Y^
+// with Z(0, 0) = 0, inverse column FFT of Z, written over X^_q.
+template <int TC>
+__global__ void __launch_bounds__(CT) k_corr_columns(float2 *F, int n, int H, int Wh, int ld, FftSteps p,
+                                                     const float2 *__restrict__ twg) {
+    extern __shared__ float2 sm[];
+    constexpr int G = 2 * TC;
+    float2 *tw = sm, *A = sm + H, *B = A + G * H;
+    const int q = blockIdx.y, c0 = blockIdx.x * TC;
+    float2 *FX = F + (long long)q * H * ld;
+    const float2 *FY = F + (long long)(n + q) * H * ld;
+    load_table(tw, twg, H);
+    for (int u = threadIdx.x; u < G * H; u += blockDim.x) {
+        const int s = u % G, y = u / G, c = c0 + (s < TC ? s : s - TC);
+        const float2 *src = s < TC ? FX : FY;
+        if (c < Wh)
+            cp_async8(A + y * G + s, src + (long long)y * ld + c);
+        else
+            A[y * G + s] = make_float2(0.f, 0.f);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    float2 *S = fft_run<G, G, false>(A, B, p, tw);
+    float2 *T = S == A ? B : A;
+    for (int u = threadIdx.x; u < TC * H; u += blockDim.x) {
+        const int s = u % TC, y = u / TC;
+        const float2 a = S[y * G + s], b = S[y * G + TC + s];
+        float2 z = make_float2(__fmaf_rn(a.x, b.x, a.y * b.y), __fmaf_rn(a.x, b.y, -a.y * b.x));
+        if (y == 0 && c0 + s == 0) z = make_float2(0.f, 0.f);
+        S[y * G + s] = z;
+    }
+    __syncthreads();
+    const float2 *Z = fft_run<G, TC, true>(S, T, p, tw);
+    for (int u = threadIdx.x; u < TC * H; u += blockDim.x) {
+        const int s = u % TC, y = u / TC, c = c0 + s;
+        if (c < Wh) FX[(long long)y * ld + c] = Z[y * G + s];
+    }
+}
+
+__device__ __forceinline__ double block_sum_d(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+    __syncthreads();
+    return t;  // valid in thread 0
+}
+
+// Per query q (grid y): inverse real FFT of rows y = blockIdx.x*G + ... of
+// Z_q (pitch ld, M + 1 bins) and the PCE partials of this block: energy
+// outside the neighbourhood |dy|, |dx| <= r of zero shift (circular), the
+// maximum and its first flat index, and C(0, 0) to c0[q].  The rows are
+// staged (cp.async) into one of two buffers while the previous ones are
+// transformed in the work buffer and the other.
+template <int G>
+__global__ void __launch_bounds__(CT) k_corr_rows(const float2 *__restrict__ Zall, int H, int W, int ld, int r,
+                                                  FftSteps p, const float2 *__restrict__ twg, double *part_e,
+                                                  float *part_v, long long *part_i, float *c0) {
+    extern __shared__ float2 sm[];
+    __shared__ double sh[32];
+    __shared__ float sv[CT];
+    __shared__ long long si[CT];
+    const int M = W >> 1, Wh = M + 1;
+    float2 *tw = sm, *twh = sm + M, *Wk = twh + M + 1;
+    float2 *const S0 = Wk + G * Wh;  // two staging buffers of G * Wh
+    const int q = blockIdx.y;
+    const float2 *Z = Zall + (long long)q * H * ld;
+    load_table(tw, twg, 2 * M + 1);
+    auto stage = [&](int y0, float2 *dst) {
+        for (int g = 0; g < G; ++g) {
+            const int y = y0 + g;
+            for (int k = threadIdx.x; k < Wh; k += blockDim.x) {
+                if (y < H)
+                    cp_async8(dst + g * Wh + k, Z + (long long)y * ld + k);
+                else
+                    dst[g * Wh + k] = make_float2(0.f, 0.f);
+            }
+        }
+    };
+    double acc = 0.0;
+    float bv = -__int_as_float(0x7f800000);
+    long long bi = LLONG_MAX;
+    const int stride = gridDim.x * G;
+    int y0 = blockIdx.x * G;
+    if (y0 < H) stage(y0, S0);
+    cp_async_commit();
+    for (int i = 0; y0 < H; y0 += stride, ++i) {
+        float2 *cur = S0 + (i & 1) * G * Wh, *nxt = S0 + ((i + 1) & 1) * G * Wh;
+        if (y0 + stride < H) stage(y0 + stride, nxt);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        // split step: Z'_k = E_k + i O_k, E_k = X_k + conj X_{M-k},
+        // O_k = (X_k - conj X_{M-k}) e^{+2 pi i k / W}  (gives W * x after the length-M inverse)
+        for (int u = threadIdx.x; u < G * M; u += blockDim.x) {
+            const int g = u % G, k = u / G;
+            const float2 a = cur[g * Wh + k], b = cconj(cur[g * Wh + M - k]);
+            const float2 e = cadd(a, b), o = cmul(csub(a, b), cconj(twh[k]));
+            Wk[k * G + g] = make_float2(e.x - o.y, e.y + o.x);
+        }
+        __syncthreads();
+        const float2 *z = fft_run<G, G, true>(Wk, cur, p, tw);
+        float fe = 0.f;
+        for (int u = threadIdx.x; u < G * M; u += blockDim.x) {
+            const int g = u % G, m = u / G, y = y0 + g;
+            if (y >= H) continue;
+            const float2 v = z[m * G + g];  // C(y, 2m), C(y, 2m + 1)
+            const bool ynear = min(y, H - y) <= r;
+            const int x0 = 2 * m, x1 = 2 * m + 1;
+            if (!(ynear && min(x0, W - x0) <= r)) fe = __fmaf_rn(v.x, v.x, fe);
+            if (!(ynear && min(x1, W - x1) <= r)) fe = __fmaf_rn(v.y, v.y, fe);
+            const long long i0 = (long long)y * W + x0;
+            if (v.x > bv || (v.x == bv && i0 < bi)) { bv = v.x; bi = i0; }
+            if (v.y > bv || (v.y == bv && i0 + 1 < bi)) { bv = v.y; bi = i0 + 1; }
+            if (y == 0 && m == 0) c0[q] = v.x;
+        }
+        acc += (double)fe;
+        __syncthreads();  // Wk / cur are reused by the next iteration
+    }
+    cp_async_wait<0>();
+    const double e = block_sum_d(acc, sh);
+    sv[threadIdx.x] = bv;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            const float ov = sv[threadIdx.x + s];
+            const long long oi = si[threadIdx.x + s];
+            if (ov > sv[threadIdx.x] || (ov == sv[threadIdx.x] && oi < si[threadIdx.x])) {
+                sv[threadIdx.x] = ov;
+                si[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const long long o = (long long)q * gridDim.x + blockIdx.x;
+        part_e[o] = e;
+        part_v[o] = sv[0];
+        part_i[o] = si[0];
+    }
+}
+
+// Opts each kernel instance, once per device, into the largest dynamic shared
+// memory the device allows next to its static shared memory (a host-side
+// attribute; each launch still asks only for what it uses, checked against
+// that limit).  Repeating it from another thread is harmless.
+template <auto Kern>
+cudaError_t smem_attr(size_t bytes) {
+    static int limit[64] = {};  // per device: 0 unset, else limit + 1
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (limit[dev] == 0) {
+        int optin = 0;
+        cudaFuncAttributes fa{};
+        cudaError_t e;
+        if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+        if ((e = cudaFuncGetAttributes(&fa, Kern)) != cudaSuccess) return e;
+        const int dyn = optin - (int)fa.sharedSizeBytes;
+        if ((e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)) != cudaSuccess) return e;
+        limit[dev] = dyn + 1;
+    }
+    return bytes < (size_t)limit[dev] ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
+int rows_per_block(int M) { return M <= 1024 ? 4 : 2; }
+// twiddles (2M + 1) and three buffers of G rows (G*M forward, G*(M+1) inverse)
+size_t rows_smem(int M) { return (size_t)(2 * M + 1 + 3 * rows_per_block(M) * (M + 1)) * sizeof(float2); }
+size_t cols_smem(int H, int tc) { return (size_t)(H + 2 * 2 * tc * H) * sizeof(float2); }
+// widest column tile whose block still fits twice per SM, else once
+int cols_tile(int H) {
+    for (int tc : {4, 2, 1})
+        if (cols_smem(H, tc) <= 113 * 1024) return tc;
+    for (int tc : {4, 2, 1})
+        if (cols_smem(H, tc) <= 220 * 1024) return tc;
+    return 0;
+}
+
+}  // namespace
+
+bool fft_steps(int L, FftSteps *p) {
+    FftSteps s{};
+    s.L = L;
+    if (L < 2) return false;
+    int x = L;
+    for (int r : {8, 4, 2, 3, 5, 7})
+        while (x % r == 0 && s.np < kMaxFftPasses) {
+            s.radix |= (unsigned long long)r << (4 * s.np++);
+            x /= r;
+        }
+    if (x != 1) return false;
+    *p = s;
+    return true;
+}
+
+bool corr_fft_supported(int H, int W) {
+    FftSteps a, b;
+    if (W % 2 || W < 4 || H < 2) return false;
+    if (!fft_steps(W / 2, &a) || !fft_steps(H, &b)) return false;
+    return rows_smem(W / 2) <= 220 * 1024 && cols_tile(H) > 0;
+}
+
+size_t corr_twiddle_count(int H, int W) { return (size_t)(W / 2) * 2 + 1 + H; }
+int corr_pitch(int W) { return (W / 2 + 1 + 3) / 4 * 4; }
+
+cudaError_t launch_corr_fft(const float *XY, float2 *F, float2 *tw, int n, int H, int W, int r, int nb,
+                            double *part_e, float *part_v, long long *part_i, float *c0, int sms, cudaStream_t st,
+                            int stage) {
+    const int M = W / 2, Wh = M + 1, ld = corr_pitch(W);
+    FftSteps pm, ph;
+    if (!fft_steps(M, &pm) || !fft_steps(H, &ph)) return cudaErrorInvalidValue;
+    const int G = rows_per_block(M);
+    const size_t rs = rows_smem(M);
+    cudaError_t e;
+    if (stage == 0) {
+        const int nt = corr_twiddle_count(H, W);
+        k_twiddles<<<(nt + 255) / 256, 256, 0, st>>>(tw, M, H);
+        const long long nrows = 2LL * n * H;
+        const long long blocks = std::min<long long>((nrows + G - 1) / G, (long long)sms * (rs <= 113 * 1024 ? 2 : 1));
+        if (G == 4) {
+            if ((e = smem_attr<k_rfft_rows<4>>(rs)) != cudaSuccess) return e;
+            k_rfft_rows<4><<<(unsigned)blocks, CT, rs, st>>>(XY, F, nrows, W, ld, pm, tw);
+        } else {
+            if ((e = smem_attr<k_rfft_rows<2>>(rs)) != cudaSuccess) return e;
+            k_rfft_rows<2><<<(unsigned)blocks, CT, rs, st>>>(XY, F, nrows, W, ld, pm, tw);
+        }
+    } else if (stage == 1) {
+        const int tc = cols_tile(H);
+        const size_t cs = cols_smem(H, tc);
+        const dim3 grid((Wh + tc - 1) / tc, n);
+        const float2 *twc = tw + 2 * M + 1;
+        if (tc == 4) {
+            if ((e = smem_attr<k_corr_columns<4>>(cs)) != cudaSuccess) return e;
+            k_corr_columns<4><<<grid, CT, cs, st>>>(F, n, H, Wh, ld, ph, twc);
+        } else if (tc == 2) {
+            if ((e = smem_attr<k_corr_columns<2>>(cs)) != cudaSuccess) return e;
+            k_corr_columns<2><<<grid, CT, cs, st>>>(F, n, H, Wh, ld, ph, twc);
+        } else {
+            if ((e = smem_attr<k_corr_columns<1>>(cs)) != cudaSuccess) return e;
+            k_corr_columns<1><<<grid, CT, cs, st>>>(F, n, H, Wh, ld, ph, twc);
+        }
+    } else {
+        const dim3 grid((unsigned)std::min(nb, (H + G - 1) / G), n);
+        if (G == 4) {
+            if ((e = smem_attr<k_corr_rows<4>>(rs)) != cudaSuccess) return e;
+            k_corr_rows<4><<<grid, CT, rs, st>>>(F, H, W, ld, r, pm, tw, part_e, part_v, part_i, c0);
+        } else {
+            if ((e = smem_attr<k_corr_rows<2>>(rs)) != cudaSuccess) return e;
+            k_corr_rows<2><<<grid, CT, rs, st>>>(F, H, W, ld, r, pm, tw, part_e, part_v, part_i, c0);
+        }
+    }
+    return cudaGetLastError();
+}
+
+int corr_rows_blocks(int H, int W, int nb) { return std::min(nb, (H + rows_per_block(W / 2) - 1) / rows_per_block(W / 2)); }
+
+}  // namespace prnu

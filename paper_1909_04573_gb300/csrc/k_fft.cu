@@ -405,8 +405,8 @@ __global__ void k_pce_energy(const float *Cr, int H, int W, int r, double *part_
     }
 }
 
-// one block per query
-__global__ void k_pce_final(const float *Cr, long long n, const double *part_e, const float *part_v,
+// one block per query; C(0, 0) of query q at c0[q * c0_stride]
+__global__ void k_pce_final(const float *c0, long long c0_stride, const double *part_e, const float *part_v,
                             const long long *part_i, int nb, const double *part_m, int nbm, PceScalars *out) {
     __shared__ double sh[32];
     const int q = blockIdx.x;
@@ -424,7 +424,7 @@ __global__ void k_pce_final(const float *Cr, long long n, const double *part_e, 
             const long long ix = part_i[(long long)q * nb + i];
             if (v > bv || (v == bv && ix < bi)) { bv = v; bi = ix; }
         }
-        out[q].c0 = (double)Cr[(long long)q * n];
+        out[q].c0 = (double)c0[(long long)q * c0_stride];
         out[q].energy = e;
         out[q].peak_idx = bi;
         out[q].sx = m[0];
@@ -494,6 +494,41 @@ cudaError_t launch_pce_reduce(const float *Cr, int H, int W, int r, int n, int n
     k_pce_energy<<<dim3(nb, n), RB, 0, st>>>(Cr, H, W, r, part_e, part_v, part_i);
     k_pce_final<<<n, RB, 0, st>>>(Cr, (long long)H * W, part_e, part_v, part_i, nb, part_m, nbm,
                                   (PceScalars *)out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pce_final(const float *c0, long long c0_stride, int n, const double *part_e, const float *part_v,
+                             const long long *part_i, int nb, const double *part_m, int nbm, void *out,
+                             cudaStream_t st) {
+    k_pce_final<<<n, RB, 0, st>>>(c0, c0_stride, part_e, part_v, part_i, nb, part_m, nbm, (PceScalars *)out);
+    return cudaGetLastError();
+}
+
+// PCE, NCC and peak of each query from its reduction scalars, on the device
+// (the same formulas the host applies after a copy): c0 and energy carry the
+// unnormalised inverse-FFT factors N and N^2; PCE is invariant to them, NCC
+// divides them out.
+__global__ void k_pce_outputs(const PceScalars *sc, int n, long long hw, int W, int nbhd, double *pce, double *ncc,
+                              int *peak) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const PceScalars s = sc[q];
+    const double N = (double)hw, outside = N - (double)nbhd * nbhd;
+    pce[q] = s.energy > 0.0 ? (s.c0 >= 0 ? 1.0 : -1.0) * s.c0 * s.c0 * outside / s.energy : 0.0;
+    if (ncc) {
+        const double nx2 = s.sxx - s.sx * s.sx / N, ny2 = s.syy - s.sy * s.sy / N;
+        ncc[q] = (nx2 > 0.0 && ny2 > 0.0) ? (s.c0 / N) / sqrt(nx2 * ny2) : 0.0;
+    }
+    if (peak) {
+        peak[2 * q] = (int)(s.peak_idx / W);
+        peak[2 * q + 1] = (int)(s.peak_idx % W);
+    }
+}
+
+cudaError_t launch_pce_outputs(const void *sc, int n, long long hw, int W, int nbhd, double *pce, double *ncc,
+                               int *peak, cudaStream_t st) {
+    k_pce_outputs<<<(n + 127) / 128, 128, 0, st>>>(static_cast<const PceScalars *>(sc), n, hw, W, nbhd, pce, ncc,
+                                                   peak);
     return cudaGetLastError();
 }
 

@@ -119,6 +119,32 @@ struct PceScalars {
     double sx, sxx, sy, syy;
 };
 size_t pce_scalars_bytes();
+cudaError_t launch_pce_final(const float *c0, long long c0_stride, int n, const double *part_e, const float *part_v,
+                             const long long *part_i, int nb, const double *part_m, int nbm, void *out,
+                             cudaStream_t st);
+
+// k_corr.cu -- PCE correlation by our own mixed-radix FFTs
+constexpr int kMaxFftPasses = 16;
+struct FftSteps {
+    int L = 0, np = 0;
+    unsigned long long radix = 0;  // radix of pass i (8, 4, 2, 3, 5 or 7) in bits 4i..4i+3
+    __host__ __device__ int r(int i) const { return (int)((radix >> (4 * i)) & 15u); }
+};
+bool fft_steps(int L, FftSteps *p);
+// true when W is even and W/2 and H factor into 2, 3, 5, 7 within the
+// shared-memory limits of the kernels
+bool corr_fft_supported(int H, int W);
+size_t corr_twiddle_count(int H, int W);  // float2 entries
+int corr_pitch(int W);                    // complex bins per half-spectrum row (W/2 + 1, padded to 4)
+int corr_rows_blocks(int H, int W, int nb);
+// stage 0: twiddles + row FFTs of the 2n planes XY into F; 1: column FFTs,
+// cross spectrum and inverse column FFTs (in place over the X half of F);
+// 2: inverse row FFTs and the PCE partials (corr_rows_blocks per query).
+cudaError_t launch_corr_fft(const float *XY, float2 *F, float2 *tw, int n, int H, int W, int r, int nb,
+                            double *part_e, float *part_v, long long *part_i, float *c0, int sms, cudaStream_t st,
+                            int stage);
+cudaError_t launch_pce_outputs(const void *sc, int n, long long hw, int W, int nbhd, double *pce, double *ncc,
+                               int *peak, cudaStream_t st);
 
 // k_grad.cu -- adjoints
 struct ShrinkBwdArgs {

@@ -355,7 +355,9 @@ prnu_status fft_layout(prnu_ctx *ctx, int H, int W, int n, FftLayout *out) {
     const size_t nh = (size_t)H * (W / 2 + 1);
     f.nb = (int)std::min<size_t>(256, std::max<size_t>(1, hw / (256 * 16)));
     f.nbm = f.nb;
-    f.cplx = take(2 * (size_t)std::max(n, 1) * nh * sizeof(cufftComplex));
+    f.own_fft = corr_fft_supported(H, W);
+    const size_t nh_pce = f.own_fft ? (size_t)H * corr_pitch(W) : nh;  // padded rows for the own FFT
+    f.cplx = take(2 * (size_t)std::max(n, 1) * std::max(nh, nh_pce) * sizeof(cufftComplex));
     f.real = take(2 * (size_t)std::max(n, 1) * hw * sizeof(float));
     f.colmean = take((size_t)W * sizeof(double));
     f.colpart = take((size_t)((H + 63) / 64) * W * sizeof(double));
@@ -368,6 +370,8 @@ prnu_status fft_layout(prnu_ctx *ctx, int H, int W, int n, FftLayout *out) {
     f.pv = take((size_t)n * f.nb * sizeof(float));
     f.pi = take((size_t)n * f.nb * sizeof(long long));
     f.scal = take((size_t)n * pce_scalars_bytes());
+    f.tw = take(f.own_fft ? corr_twiddle_count(H, W) * sizeof(float2) : 0);
+    f.c0 = take((size_t)std::max(n, 1) * sizeof(float));
     size_t w = 0, wmax = 0;
     cufftHandle p;
     prnu_status s;
@@ -375,10 +379,12 @@ prnu_status fft_layout(prnu_ctx *ctx, int H, int W, int n, FftLayout *out) {
     wmax = std::max(wmax, w);
     if ((s = get_plan(ctx, H, W, CUFFT_C2R, 1, &p, &w)) != PRNU_OK) return s;
     wmax = std::max(wmax, w);
-    if ((s = get_plan(ctx, H, W, CUFFT_R2C, 2 * n, &p, &w)) != PRNU_OK) return s;
-    wmax = std::max(wmax, w);
-    if ((s = get_plan(ctx, H, W, CUFFT_C2R, n, &p, &w)) != PRNU_OK) return s;
-    wmax = std::max(wmax, w);
+    if (!f.own_fft) {  // batched plans of the PCE correlation
+        if ((s = get_plan(ctx, H, W, CUFFT_R2C, 2 * n, &p, &w)) != PRNU_OK) return s;
+        wmax = std::max(wmax, w);
+        if ((s = get_plan(ctx, H, W, CUFFT_C2R, n, &p, &w)) != PRNU_OK) return s;
+        wmax = std::max(wmax, w);
+    }
     f.work = take(wmax);
     f.end = off;
     *out = f;
@@ -898,12 +904,60 @@ prnu_status prnu_fingerprint_finalize(prnu_ctx *ctx, const float *num, const flo
 }
 
 namespace {
+prnu_status pce_correlate_cufft(prnu_ctx *ctx, int n, int H, int W, int nbhd, const FftLayout &f, char *b,
+                                const double *part_m, int nbm, cudaStream_t st);
+prnu_status pce_to_host(int n, int W, long long hw, int nbhd, const char *scal, double *pce_out, double *ncc_out,
+                        int *peak_yx, cudaStream_t st);
+
 // From X, Y in f.real (X_0..X_{n-1}, then Y_0..Y_{n-1}) and the moment
 // partials (nbm per query at part_m): cross-correlation, energy, PCE / NCC
-// / peak to the host.  Synchronises the stream.
+// / peak, to the host (synchronising the stream) or, with device_out, to the
+// device pointers.
 prnu_status pce_finish(prnu_ctx *ctx, int n, int H, int W, int nbhd, const FftLayout &f, char *b,
                        const double *part_m, int nbm, double *pce_out, double *ncc_out, int *peak_yx,
-                       cudaStream_t st) {
+                       cudaStream_t st, bool device_out = false) {
+    prnu_status s;
+    const long long hw = (long long)H * W;
+    const long long nh = (long long)H * (W / 2 + 1);
+    const float *X = reinterpret_cast<const float *>(b + f.real);
+    if (f.own_fft) {
+        // correlation by our own row / column FFTs; the plane is never stored
+        float2 *F = reinterpret_cast<float2 *>(b + f.cplx);
+        float2 *tw = reinterpret_cast<float2 *>(b + f.tw);
+        double *pe = reinterpret_cast<double *>(b + f.pe);
+        float *pv = reinterpret_cast<float *>(b + f.pv), *c0 = reinterpret_cast<float *>(b + f.c0);
+        long long *pi = reinterpret_cast<long long *>(b + f.pi);
+        const int nbr = corr_rows_blocks(H, W, f.nb);
+        {
+            Launch t(ctx, "pce_fft_rows", st, 2, (double)n * (2.0 * hw * 4 + 2.0 * nh * 8));
+            CU(launch_corr_fft(X, F, tw, n, H, W, nbhd / 2, nbr, pe, pv, pi, c0, ctx->sms, st, 0));
+        }
+        {
+            Launch t(ctx, "pce_fft_columns", st, 1, (double)n * 3.0 * nh * 8);
+            CU(launch_corr_fft(X, F, tw, n, H, W, nbhd / 2, nbr, pe, pv, pi, c0, ctx->sms, st, 1));
+        }
+        {
+            Launch t(ctx, "pce_fft_rows_inverse", st, 1, (double)n * nh * 8);
+            CU(launch_corr_fft(X, F, tw, n, H, W, nbhd / 2, nbr, pe, pv, pi, c0, ctx->sms, st, 2));
+        }
+        {
+            Launch t(ctx, "pce_final", st);
+            CU(launch_pce_final(c0, 1, n, pe, pv, pi, nbr, part_m, nbm, b + f.scal, st));
+        }
+    } else {
+        if ((s = pce_correlate_cufft(ctx, n, H, W, nbhd, f, b, part_m, nbm, st)) != PRNU_OK) return s;
+    }
+    if (device_out) {  // outputs stay on the device: nothing synchronises (graph-capturable)
+        Launch t(ctx, "pce_outputs", st);
+        CU(launch_pce_outputs(b + f.scal, n, hw, W, nbhd, pce_out, ncc_out, peak_yx, st));
+        return PRNU_OK;
+    }
+    return pce_to_host(n, W, hw, nbhd, b + f.scal, pce_out, ncc_out, peak_yx, st);
+}
+
+// cuFFT correlation for geometries the own FFT does not cover
+prnu_status pce_correlate_cufft(prnu_ctx *ctx, int n, int H, int W, int nbhd, const FftLayout &f, char *b,
+                                const double *part_m, int nbm, cudaStream_t st) {
     prnu_status s;
     const long long hw = (long long)H * W;
     const long long nh = (long long)H * (W / 2 + 1);
@@ -935,8 +989,14 @@ prnu_status pce_finish(prnu_ctx *ctx, int n, int H, int W, int nbhd, const FftLa
                              reinterpret_cast<float *>(b + f.pv), reinterpret_cast<long long *>(b + f.pi), part_m,
                              nbm, b + f.scal, st));
     }
+    return PRNU_OK;
+}
+
+// PCE / NCC / peak of the n queries to the host (synchronises the stream)
+prnu_status pce_to_host(int n, int W, long long hw, int nbhd, const char *scal, double *pce_out, double *ncc_out,
+                        int *peak_yx, cudaStream_t st) {
     std::vector<unsigned char> host((size_t)n * pce_scalars_bytes());
-    CU(cudaMemcpyAsync(host.data(), b + f.scal, host.size(), cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(host.data(), scal, host.size(), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     const double N = (double)hw;
     const double outside = N - (double)nbhd * nbhd;
@@ -1025,9 +1085,10 @@ prnu_status prnu_workspace_size_pce_images(prnu_ctx *ctx, int H, int W, int C, c
     return PRNU_OK;
 }
 
-prnu_status prnu_pce_match_images(prnu_ctx *ctx, const float *K, const float *img_q, int n, int H, int W, int C,
-                                  const prnu_params *params, int nbhd, double *pce_out, double *ncc_out,
-                                  int *peak_yx, void *ws, size_t ws_bytes, void *stream) {
+namespace {
+prnu_status pce_images_impl(prnu_ctx *ctx, const float *K, const float *img_q, int n, int H, int W, int C,
+                            const prnu_params *params, int nbhd, double *pce_out, double *ncc_out, int *peak_yx,
+                            void *ws, size_t ws_bytes, void *stream, bool device_out) {
     if (!ctx || !K || !img_q || !pce_out) return fail(PRNU_EINVAL, "NULL argument");
     if (n < 1) return fail(PRNU_EINVAL, "n must be >= 1");
     prnu_status s;
@@ -1059,7 +1120,23 @@ prnu_status prnu_pce_match_images(prnu_ctx *ctx, const float *K, const float *im
     fin.part_m = reinterpret_cast<double *>(b + p.pm);
     if ((s = run_denoise(ctx, img_q, H, W, n * C, *params, win, fin.sc, 0, b, p.den, fin, false, st)) != PRNU_OK)
         return s;
-    return pce_finish(ctx, n, H, W, nbhd, p.fft, b + p.fft_off, fin.part_m, p.nbm, pce_out, ncc_out, peak_yx, st);
+    return pce_finish(ctx, n, H, W, nbhd, p.fft, b + p.fft_off, fin.part_m, p.nbm, pce_out, ncc_out, peak_yx, st,
+                      device_out);
+}
+}  // namespace
+
+prnu_status prnu_pce_match_images(prnu_ctx *ctx, const float *K, const float *img_q, int n, int H, int W, int C,
+                                  const prnu_params *params, int nbhd, double *pce_out, double *ncc_out,
+                                  int *peak_yx, void *ws, size_t ws_bytes, void *stream) {
+    return pce_images_impl(ctx, K, img_q, n, H, W, C, params, nbhd, pce_out, ncc_out, peak_yx, ws, ws_bytes, stream,
+                           false);
+}
+
+prnu_status prnu_pce_match_images_async(prnu_ctx *ctx, const float *K, const float *img_q, int n, int H, int W,
+                                        int C, const prnu_params *params, int nbhd, double *pce_dev, double *ncc_dev,
+                                        int *peak_dev, void *ws, size_t ws_bytes, void *stream) {
+    return pce_images_impl(ctx, K, img_q, n, H, W, C, params, nbhd, pce_dev, ncc_dev, peak_dev, ws, ws_bytes, stream,
+                           true);
 }
 
 prnu_status prnu_pce_match_batch(prnu_ctx *ctx, const float *K, const float *residual_q, const float *img_q, int n,
@@ -1250,6 +1327,19 @@ prnu_status prnu_profile_enable(prnu_ctx *ctx, int on) {
     if (!ctx) return fail(PRNU_EINVAL, "ctx is NULL");
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->prof_on = on != 0;
+    return PRNU_OK;
+}
+
+prnu_status prnu_profile_select(prnu_ctx *ctx, const char *names) {
+    if (!ctx) return fail(PRNU_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->prof_sel.clear();
+    for (const char *p = names; p && *p;) {
+        const char *e = std::strchr(p, ',');
+        const size_t len = e ? (size_t)(e - p) : std::strlen(p);
+        if (len) ctx->prof_sel.emplace_back(p, len);
+        p = e ? e + 1 : p + len;
+    }
     return PRNU_OK;
 }
 

@@ -22,13 +22,13 @@ EXPORTS = (
     "prnu_default_params", "prnu_create", "prnu_destroy", "prnu_last_error", "prnu_workspace_size",
     "prnu_workspace_size_host", "prnu_sda_average", "prnu_denoise_residual", "prnu_fingerprint_accumulate",
     "prnu_fingerprint_accumulate_host", "prnu_fingerprint_finalize", "prnu_pce_match",
-    "prnu_profile_enable", "prnu_profile_reset", "prnu_profile_read", "prnu_denoise_residual_static",
+    "prnu_profile_enable", "prnu_profile_select", "prnu_profile_reset", "prnu_profile_read", "prnu_denoise_residual_static",
     "prnu_denoise_residual_batch", "prnu_pce_match_batch", "prnu_pce_match_pairs",
     "prnu_workspace_size_multi", "prnu_fingerprint_accumulate_multi", "prnu_autotune",
     "prnu_autotune_set", "prnu_sda_weighted", "prnu_sda_weighted_backward", "prnu_workspace_size_grad",
     "prnu_denoise_residual_ckpt", "prnu_denoise_residual_backward", "prnu_mle_images", "prnu_mle_images_backward",
     "prnu_workspace_size_pce_backward", "prnu_pce_backward", "prnu_workspace_size_pce_images",
-    "prnu_pce_match_images",
+    "prnu_pce_match_images", "prnu_pce_match_images_async",
 )
 
 
@@ -96,6 +96,8 @@ def lib() -> ctypes.CDLL:
                                   ctypes.POINTER(ctypes.c_float)],
                 "prnu_autotune_set": [_vp, _i, _i, _pp, _i],
                 "prnu_workspace_size_pce_images": [_vp, _i, _i, _i, _pp, _i, ctypes.POINTER(_sz)],
+                "prnu_pce_match_images_async": [_vp, _vp, _vp, _i, _i, _i, _i, _pp, _i, _vp, _vp, _vp, _vp, _sz,
+                                                _vp],
                 "prnu_pce_match_images": [_vp, _vp, _vp, _i, _i, _i, _i, _pp, _i, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i), _vp, _sz, _vp],
                 "prnu_sda_weighted": [_vp, _vp, _i, _i, _i, _i, _sz, _sz, _i, _vp, _vp, _vp],
@@ -109,6 +111,7 @@ def lib() -> ctypes.CDLL:
                 "prnu_pce_backward": [_vp, _vp, _i, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _sz, _vp],
                 "prnu_profile_enable": [_vp, _i],
                 "prnu_profile_reset": [_vp],
+                "prnu_profile_select": [_vp, ctypes.c_char_p],
                 "prnu_profile_read": [_vp, _i, ctypes.c_char_p, _sz, ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
             }
@@ -290,6 +293,11 @@ def prnu_profile_enable(ctx, on: bool) -> None:
     _check(lib().prnu_profile_enable(ctx, 1 if on else 0), ctx)
 
 
+def prnu_profile_select(ctx, names=None) -> None:
+    """Time only the named kernels (an iterable of profile names; None: all)."""
+    _check(lib().prnu_profile_select(ctx, ",".join(names).encode() if names else None), ctx)
+
+
 def prnu_profile_reset(ctx) -> None:
     _check(lib().prnu_profile_reset(ctx), ctx)
 
@@ -406,6 +414,25 @@ class Context:
         ws = self.workspace(nb)
         return prnu_pce_match_images(self.ctx, K.data_ptr(), img_q.data_ptr(), n, H, W, C, params, nbhd,
                                      ws.data_ptr(), ws.numel(), self._stream())
+
+    def pce_match_images_async(self, K, img_q, out=None, nbhd: int = 11, params=None):
+        """Like pce_match_images, with the results left on the device (no
+        synchronisation; capturable in a CUDA graph after one eager call):
+        returns (pce float64 [n], ncc float64 [n], peak int32 [n, 2])."""
+        params = params or default_params()
+        n, C, H, W = img_q.shape
+        K = K.reshape(H, W)
+        if out is None:
+            out = (self.torch.empty(n, dtype=self.torch.float64, device=img_q.device),
+                   self.torch.empty(n, dtype=self.torch.float64, device=img_q.device),
+                   self.torch.empty((n, 2), dtype=self.torch.int32, device=img_q.device))
+        nb = prnu_workspace_size_pce_images(self.ctx, H, W, C, params, n)
+        ws = self.workspace(nb)
+        _check(lib().prnu_pce_match_images_async(self.ctx, K.data_ptr(), img_q.data_ptr(), n, H, W, C,
+                                                 ctypes.byref(params), nbhd, out[0].data_ptr(), out[1].data_ptr(),
+                                                 out[2].data_ptr(), ws.data_ptr(), ws.numel(), self._stream()),
+               self.ctx)
+        return out
 
     def pce_match_pairs(self, K, residual_q, img_q, nbhd: int = 11):
         """K [n, H, W]; residual_q, img_q [n, C, H, W]: query i against fingerprint i."""

@@ -300,3 +300,103 @@ def test_pce_from_images_matches_two_step_path_and_oracle(ctx, H, W, C, n):
     qh = O.sda_average(qf[:1].cpu().numpy(), 1)[0]
     opce = O.pce_match(oK, O.to_gray(O.residual(qh)), O.to_gray(qh)).pce
     assert abs(fused[0][0] - opce) <= 1e-3 * abs(opce)
+
+
+def test_pce_images_async_equals_sync_and_replays_in_a_graph(ctx):
+    """prnu_pce_match_images_async leaves the same PCE / NCC / peak on the
+    device as the synchronous call returns, and the whole step (accumulate,
+    finalize, PCE) captured in a CUDA graph reproduces them on replay, also
+    after its input frames are changed in place."""
+    H, W, C, n = 136, 200, 3, 4
+    cam = synth.Camera(H=H, W=W, C=C, camera_id=81)
+    fr = synth.frames(cam, 12, device="cuda")
+    qf = torch.cat([synth.frames(cam, n - 1, stream=1, device="cuda"),
+                    synth.frames(synth.foreign(cam), 1, stream=1, device="cuda")])
+    q = ctx.sda_average(qf, 1)
+    num = torch.zeros((C, H, W), device="cuda")
+    den = torch.zeros_like(num)
+    flags = P.PRNU_TO_GRAY | P.PRNU_ZERO_MEAN | P.PRNU_WIENER_DFT
+    out = (torch.full((n,), -1.0, dtype=torch.float64, device="cuda"),
+           torch.full((n,), -1.0, dtype=torch.float64, device="cuda"),
+           torch.full((n, 2), -1, dtype=torch.int32, device="cuda"))
+
+    def step():
+        num.zero_()
+        den.zero_()
+        ctx.fingerprint_accumulate(fr, 4, num, den)
+        K = ctx.fingerprint_finalize(num, den, flags)
+        ctx.pce_match_images_async(K[0], q, out=out)
+        return K
+
+    def sync_reference():
+        num.zero_()
+        den.zero_()
+        ctx.fingerprint_accumulate(fr, 4, num, den)
+        K = ctx.fingerprint_finalize(num, den, flags)
+        return ctx.pce_match_images(K[0], q)
+
+    def check(ref):
+        pce, ncc, peak = out[0].cpu(), out[1].cpu(), out[2].cpu()
+        for i, (p, c, k) in enumerate(ref):
+            # same formula in double on the device and on the host
+            assert abs(pce[i].item() - p) <= 1e-12 * max(abs(p), 1.0)
+            assert abs(ncc[i].item() - c) <= 1e-12 * max(abs(c), 1e-6)
+            assert tuple(peak[i].tolist()) == tuple(k)
+
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        step()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    check(sync_reference())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        step()
+    for v in out:
+        v.fill_(-1)
+    g.replay()
+    torch.cuda.synchronize()
+    check(sync_reference())
+    fr.copy_(synth.frames(synth.foreign(cam), 12, device="cuda"))   # new frames, same buffer
+    g.replay()
+    torch.cuda.synchronize()
+    ref = sync_reference()
+    check(ref)
+    assert abs(ref[0][0]) < 60 and abs(ref[-1][0]) > 60        # the foreign fingerprint now matches query n-1
+
+    # the profiler's events inside a captured graph time each replay
+    P.prnu_profile_reset(ctx.ctx)
+    P.prnu_profile_enable(ctx.ctx, True)
+    step()
+    torch.cuda.synchronize()
+    eager = {k: v for k, v in P.prnu_profile_read(ctx.ctx).items() if v[0] > 0}
+    P.prnu_profile_reset(ctx.ctx)
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g2, stream=s):
+        step()
+        step()
+    P.prnu_profile_enable(ctx.ctx, False)
+    g2.replay()
+    torch.cuda.synchronize()
+    captured = {k: v for k, v in P.prnu_profile_read(ctx.ctx).items() if v[0] > 0}
+    del g2
+    torch.cuda.synchronize()
+    P.prnu_profile_reset(ctx.ctx)
+    assert set(captured) == set(eager)
+    for k, (nl, ms, nb) in captured.items():
+        assert nl == 2 * eager[k][0] and nb == 2 * eager[k][2]
+        assert ms > 0.0, k
+    # with a selection only the named kernels are timed; all are counted
+    P.prnu_profile_select(ctx.ctx, ["shrink", "sda_sum"])
+    P.prnu_profile_enable(ctx.ctx, True)
+    step()
+    torch.cuda.synchronize()
+    P.prnu_profile_enable(ctx.ctx, False)
+    sel = {k: v for k, v in P.prnu_profile_read(ctx.ctx).items() if v[0] > 0}
+    P.prnu_profile_reset(ctx.ctx)
+    P.prnu_profile_select(ctx.ctx, None)
+    assert set(sel) == set(eager)
+    for k, (nl, ms, nb) in sel.items():
+        assert nl == eager[k][0]
+        assert (ms > 0.0) == (k in ("shrink", "sda_sum")), k
