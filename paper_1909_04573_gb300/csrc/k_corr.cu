@@ -164,9 +164,43 @@ template <>
 struct Dft<7> : DftOdd<7> {};
 
 // ------------------------------------------------------ Stockham passes ---
-// One radix-R pass over NA sequences of length L laid out with stride G
-// (element j of sequence g at j*G + g), from a to b; Ns = product of the
-// radices already applied.  INV: exponent sign +1.
+// Element j of interleaved sequence g sits at at<G>(j, g): rows of G
+// elements with one row of padding after every 16, so that the strided
+// writes of the early passes (stride R rows) spread over the banks as the
+// contiguous reads do; the offsets stay linear in the butterfly's element
+// index wherever the stride is a multiple of 16.
+template <int G>
+__device__ __forceinline__ int at(int j, int g) {
+    return (j + (j >> 4)) * G + g;
+}
+__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4) + 1; }
+
+// twiddles w_L^{m ts} (exponent sign -1, or +1 with INV), then the radix-R DFT
+template <int R, bool INV>
+__device__ __forceinline__ void butterfly(float2 *v, const float2 *__restrict__ tw, int ts) {
+    if (ts) {
+#pragma unroll
+        for (int m = 1; m < R; ++m) {
+            float2 t = tw[m * ts];
+            if (INV) t.y = -t.y;
+            v[m] = cmul(v[m], t);
+        }
+    }
+    if (INV) {
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = cconj(v[m]);
+    }
+    Dft<R>::run(v);
+    if (INV) {
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = cconj(v[m]);
+    }
+}
+
+// One radix-R pass over NA sequences of length L in a layout of G
+// interleaved sequences, from a to b; Ns = product of the radices already
+// applied.  Butterfly j reads elements j + m L/R and writes
+// (j - j%Ns) R + j%Ns + m Ns (Stockham autosort).
 template <int R, int G, int NA, bool INV>
 __device__ __forceinline__ void fft_pass(const float2 *__restrict__ a, float2 *__restrict__ b, int L, int Ns,
                                          const float2 *__restrict__ tw) {
@@ -177,33 +211,16 @@ __device__ __forceinline__ void fft_pass(const float2 *__restrict__ a, float2 *_
         const int k = j % Ns;
         float2 v[R];
 #pragma unroll
-        for (int m = 0; m < R; ++m) v[m] = a[(j + m * nb) * G + g];
-        if (k) {
-            const int ts = k * step;  // twiddle of element m: w_L^{m k step}, m k step < L
-#pragma unroll
-            for (int m = 1; m < R; ++m) {
-                float2 t = tw[m * ts];
-                if (INV) t.y = -t.y;
-                v[m] = cmul(v[m], t);
-            }
-        }
-        if (INV) {
-#pragma unroll
-            for (int m = 0; m < R; ++m) v[m] = cconj(v[m]);
-        }
-        Dft<R>::run(v);
-        if (INV) {
-#pragma unroll
-            for (int m = 0; m < R; ++m) v[m] = cconj(v[m]);
-        }
+        for (int m = 0; m < R; ++m) v[m] = a[at<G>(j + m * nb, g)];
+        butterfly<R, INV>(v, tw, k * step);
         const int base = (j - k) * R + k;
 #pragma unroll
-        for (int m = 0; m < R; ++m) b[(base + m * Ns) * G + g] = v[m];
+        for (int m = 0; m < R; ++m) b[at<G>(base + m * Ns, g)] = v[m];
     }
 }
 
-// All passes; the input is in a (visible to the block), the result in the
-// returned buffer (a or b), visible to the block on return.
+// All passes for a length known at run time; the input is in a (visible to
+// the block), the result in the returned buffer, visible to the block.
 template <int G, int NA, bool INV>
 __device__ float2 *fft_run(float2 *a, float2 *b, const FftSteps &p, const float2 *tw) {
     int Ns = 1;
@@ -224,6 +241,71 @@ __device__ float2 *fft_run(float2 *a, float2 *b, const FftSteps &p, const float2
         Ns *= R;
     }
     return a;
+}
+
+// The same with the length fixed at compile time: the pass sequence, strides
+// and loop trip counts are constants (the block has CT threads).
+struct StaticPlan {
+    int np = 0;
+    int r[kMaxFftPasses] = {}, ns[kMaxFftPasses] = {};
+};
+__host__ __device__ constexpr StaticPlan static_plan(int L) {
+    StaticPlan p{};
+    const int rs[6] = {8, 4, 2, 3, 5, 7};
+    int x = L, ns = 1;
+    for (int i = 0; i < 6; ++i)
+        while (x % rs[i] == 0 && p.np < kMaxFftPasses) {
+            p.r[p.np] = rs[i];
+            p.ns[p.np] = ns;
+            ns *= rs[i];
+            x /= rs[i];
+            ++p.np;
+        }
+    if (x != 1) p.np = -1;
+    return p;
+}
+
+template <int R, int L, int Ns, int G, int NA, bool INV>
+__device__ __forceinline__ void fft_pass_s(const float2 *__restrict__ a, float2 *__restrict__ b,
+                                           const float2 *__restrict__ tw) {
+    constexpr int nb = L / R, step = L / (Ns * R), total = nb * NA;
+#pragma unroll
+    for (int it = 0; it < (total + CT - 1) / CT; ++it) {
+        const int u = (int)threadIdx.x + it * CT;
+        if (total % CT == 0 || u < total) {
+            const int g = u % NA, j = u / NA;
+            const int k = Ns == 1 ? 0 : j % Ns;
+            float2 v[R];
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[m] = a[at<G>(j + m * nb, g)];
+            butterfly<R, INV>(v, tw, k * step);
+            const int base = (j - k) * R + k;
+#pragma unroll
+            for (int m = 0; m < R; ++m) b[at<G>(base + m * Ns, g)] = v[m];
+        }
+    }
+}
+
+template <int L, int G, int NA, bool INV, int P = 0>
+__device__ __forceinline__ float2 *fft_run_s(float2 *a, float2 *b, const float2 *tw) {
+    constexpr StaticPlan pl = static_plan(L);
+    static_assert(pl.np > 0, "length must factor into 2, 3, 5, 7");
+    if constexpr (P == pl.np) {
+        return a;
+    } else {
+        fft_pass_s<pl.r[P], L, pl.ns[P], G, NA, INV>(a, b, tw);
+        __syncthreads();
+        return fft_run_s<L, G, NA, INV, P + 1>(b, a, tw);
+    }
+}
+
+// LS > 0: the length is LS (compile time); else p.L
+template <int LS, int G, int NA, bool INV>
+__device__ __forceinline__ float2 *fft_any(float2 *a, float2 *b, const FftSteps &p, const float2 *tw) {
+    if constexpr (LS > 0)
+        return fft_run_s<LS, G, NA, INV>(a, b, tw);
+    else
+        return fft_run<G, NA, INV>(a, b, p, tw);
 }
 
 // 8-byte global -> shared copies in flight together (cp.async groups)
@@ -264,23 +346,25 @@ __global__ void k_twiddles(float2 *tw, int M, int H) {
 // M + 1 bins (pitch ldo complex); G rows per block iteration.  Three buffers
 // rotate: the next rows are staged (cp.async) while the current ones are
 // transformed in the other two.
-template <int G>
+template <int G, int MS>
 __global__ void __launch_bounds__(CT) k_rfft_rows(const float *__restrict__ x, float2 *__restrict__ out,
                                                   long long nrows, int W, int ldo, FftSteps p,
                                                   const float2 *__restrict__ twg) {
     extern __shared__ float2 sm[];
-    const int M = W >> 1;
-    float2 *tw = sm, *twh = sm + M;
-    float2 *const buf0 = twh + M + 1;  // three buffers of G * M
-    load_table(tw, twg, 2 * M + 1);
+    const int M = MS > 0 ? MS : W >> 1;
+    float2 *tw = sm;  // w_M^i; the split step's w_W^k are read through L1 (once per element)
+    const float2 *__restrict__ twh = twg + M;
+    const int BS = G * padded_len(M + 1);
+    float2 *const buf0 = sm + M;  // three buffers of BS
+    load_table(tw, twg, M);
     auto stage = [&](long long r0, float2 *dst) {
         for (int u = threadIdx.x; u < G * M; u += blockDim.x) {
             const int g = u % G, m = u / G;
             const long long r = r0 + g;
             if (r < nrows)
-                cp_async8(dst + m * G + g, reinterpret_cast<const float2 *>(x + r * W) + m);
+                cp_async8(dst + at<G>(m, g), reinterpret_cast<const float2 *>(x + r * W) + m);
             else
-                dst[m * G + g] = make_float2(0.f, 0.f);
+                dst[at<G>(m, g)] = make_float2(0.f, 0.f);
         }
     };
     const long long stride = (long long)gridDim.x * G;
@@ -288,21 +372,20 @@ __global__ void __launch_bounds__(CT) k_rfft_rows(const float *__restrict__ x, f
     if (r0 < nrows) stage(r0, buf0);
     cp_async_commit();
     for (int i = 0; r0 < nrows; r0 += stride, ++i) {
-        float2 *cur = buf0 + (i % 3) * G * M, *nxt = buf0 + ((i + 1) % 3) * G * M,
-               *scr = buf0 + ((i + 2) % 3) * G * M;
+        float2 *cur = buf0 + (i % 3) * BS, *nxt = buf0 + ((i + 1) % 3) * BS, *scr = buf0 + ((i + 2) % 3) * BS;
         if (r0 + stride < nrows) stage(r0 + stride, nxt);
         cp_async_commit();
         cp_async_wait<1>();  // this iteration's rows have landed
         __syncthreads();
-        const float2 *Z = fft_run<G, G, false>(cur, scr, p, tw);
+        const float2 *Z = fft_any<MS, G, G, false>(cur, scr, p, tw);
         // split step: X_k = (Z_k + conj Z_{M-k}) / 2 - i w_W^k (Z_k - conj Z_{M-k}) / 2
         for (int u = threadIdx.x; u < G * (M + 1); u += blockDim.x) {
             const int g = u % G, k = u / G;
             const long long r = r0 + g;
             if (r >= nrows) continue;
-            const float2 zk = Z[(k == M ? 0 : k) * G + g];
-            const float2 zc = cconj(Z[(k == 0 ? 0 : M - k) * G + g]);
-            const float2 s = cadd(zk, zc), wd = cmul(twh[k], csub(zk, zc));
+            const float2 zk = Z[at<G>(k == M ? 0 : k, g)];
+            const float2 zc = cconj(Z[at<G>(k == 0 ? 0 : M - k, g)]);
+            const float2 s = cadd(zk, zc), wd = cmul(__ldg(twh + k), csub(zk, zc));
             out[r * ldo + k] = make_float2(0.5f * (s.x + wd.y), 0.5f * (s.y - wd.x));
         }
         __syncthreads();  // cur / scr are restaged from the next iteration on
@@ -313,12 +396,12 @@ __global__ void __launch_bounds__(CT) k_rfft_rows(const float *__restrict__ x, f
 // Per query q (grid y) and tile of TC spectrum columns (grid x): column FFTs
 // of X^_q and Y^_q (F + q*H*ld and F + (n+q)*H*ld, pitch ld), Z = conj(X^) Y^
 // with Z(0, 0) = 0, inverse column FFT of Z, written over X^_q.
-template <int TC>
+template <int TC, int HS>
 __global__ void __launch_bounds__(CT) k_corr_columns(float2 *F, int n, int H, int Wh, int ld, FftSteps p,
                                                      const float2 *__restrict__ twg) {
     extern __shared__ float2 sm[];
     constexpr int G = 2 * TC;
-    float2 *tw = sm, *A = sm + H, *B = A + G * H;
+    float2 *tw = sm, *A = sm + H, *B = A + G * padded_len(H);
     const int q = blockIdx.y, c0 = blockIdx.x * TC;
     float2 *FX = F + (long long)q * H * ld;
     const float2 *FY = F + (long long)(n + q) * H * ld;
@@ -327,27 +410,29 @@ __global__ void __launch_bounds__(CT) k_corr_columns(float2 *F, int n, int H, in
         const int s = u % G, y = u / G, c = c0 + (s < TC ? s : s - TC);
         const float2 *src = s < TC ? FX : FY;
         if (c < Wh)
-            cp_async8(A + y * G + s, src + (long long)y * ld + c);
+            cp_async8(A + at<G>(y, s), src + (long long)y * ld + c);
         else
-            A[y * G + s] = make_float2(0.f, 0.f);
+            A[at<G>(y, s)] = make_float2(0.f, 0.f);
     }
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    float2 *S = fft_run<G, G, false>(A, B, p, tw);
+    float2 *S = fft_any<HS, G, G, false>(A, B, p, tw);
     float2 *T = S == A ? B : A;
+    // Z into T in its own layout of TC sequences (the inverse then touches
+    // whole rows of that layout)
     for (int u = threadIdx.x; u < TC * H; u += blockDim.x) {
         const int s = u % TC, y = u / TC;
-        const float2 a = S[y * G + s], b = S[y * G + TC + s];
+        const float2 a = S[at<G>(y, s)], b = S[at<G>(y, TC + s)];
         float2 z = make_float2(__fmaf_rn(a.x, b.x, a.y * b.y), __fmaf_rn(a.x, b.y, -a.y * b.x));
         if (y == 0 && c0 + s == 0) z = make_float2(0.f, 0.f);
-        S[y * G + s] = z;
+        T[at<TC>(y, s)] = z;
     }
     __syncthreads();
-    const float2 *Z = fft_run<G, TC, true>(S, T, p, tw);
+    const float2 *Z = fft_any<HS, TC, TC, true>(T, S, p, tw);
     for (int u = threadIdx.x; u < TC * H; u += blockDim.x) {
         const int s = u % TC, y = u / TC, c = c0 + s;
-        if (c < Wh) FX[(long long)y * ld + c] = Z[y * G + s];
+        if (c < Wh) FX[(long long)y * ld + c] = Z[at<TC>(y, s)];
     }
 }
 
@@ -369,7 +454,7 @@ __device__ __forceinline__ double block_sum_d(double v, double *sh) {
 // maximum and its first flat index, and C(0, 0) to c0[q].  The rows are
 // staged (cp.async) into one of two buffers while the previous ones are
 // transformed in the work buffer and the other.
-template <int G>
+template <int G, int MS>
 __global__ void __launch_bounds__(CT) k_corr_rows(const float2 *__restrict__ Zall, int H, int W, int ld, int r,
                                                   FftSteps p, const float2 *__restrict__ twg, double *part_e,
                                                   float *part_v, long long *part_i, float *c0) {
@@ -377,12 +462,14 @@ __global__ void __launch_bounds__(CT) k_corr_rows(const float2 *__restrict__ Zal
     __shared__ double sh[32];
     __shared__ float sv[CT];
     __shared__ long long si[CT];
-    const int M = W >> 1, Wh = M + 1;
-    float2 *tw = sm, *twh = sm + M, *Wk = twh + M + 1;
-    float2 *const S0 = Wk + G * Wh;  // two staging buffers of G * Wh
+    const int M = MS > 0 ? MS : W >> 1, Wh = M + 1;
+    float2 *tw = sm, *Wk = sm + M;  // w_M^i; the split step's w_W^k are read through L1
+    const float2 *__restrict__ twh = twg + M;
+    const int BS = G * padded_len(Wh);
+    float2 *const S0 = Wk + BS;  // two staging buffers of BS (G raw rows of Wh bins)
     const int q = blockIdx.y;
     const float2 *Z = Zall + (long long)q * H * ld;
-    load_table(tw, twg, 2 * M + 1);
+    load_table(tw, twg, M);
     auto stage = [&](int y0, float2 *dst) {
         for (int g = 0; g < G; ++g) {
             const int y = y0 + g;
@@ -402,7 +489,7 @@ __global__ void __launch_bounds__(CT) k_corr_rows(const float2 *__restrict__ Zal
     if (y0 < H) stage(y0, S0);
     cp_async_commit();
     for (int i = 0; y0 < H; y0 += stride, ++i) {
-        float2 *cur = S0 + (i & 1) * G * Wh, *nxt = S0 + ((i + 1) & 1) * G * Wh;
+        float2 *cur = S0 + (i & 1) * BS, *nxt = S0 + ((i + 1) & 1) * BS;
         if (y0 + stride < H) stage(y0 + stride, nxt);
         cp_async_commit();
         cp_async_wait<1>();
@@ -412,16 +499,16 @@ __global__ void __launch_bounds__(CT) k_corr_rows(const float2 *__restrict__ Zal
         for (int u = threadIdx.x; u < G * M; u += blockDim.x) {
             const int g = u % G, k = u / G;
             const float2 a = cur[g * Wh + k], b = cconj(cur[g * Wh + M - k]);
-            const float2 e = cadd(a, b), o = cmul(csub(a, b), cconj(twh[k]));
-            Wk[k * G + g] = make_float2(e.x - o.y, e.y + o.x);
+            const float2 e = cadd(a, b), o = cmul(csub(a, b), cconj(__ldg(twh + k)));
+            Wk[at<G>(k, g)] = make_float2(e.x - o.y, e.y + o.x);
         }
         __syncthreads();
-        const float2 *z = fft_run<G, G, true>(Wk, cur, p, tw);
+        const float2 *z = fft_any<MS, G, G, true>(Wk, cur, p, tw);
         float fe = 0.f;
         for (int u = threadIdx.x; u < G * M; u += blockDim.x) {
             const int g = u % G, m = u / G, y = y0 + g;
             if (y >= H) continue;
-            const float2 v = z[m * G + g];  // C(y, 2m), C(y, 2m + 1)
+            const float2 v = z[at<G>(m, g)];  // C(y, 2m), C(y, 2m + 1)
             const bool ynear = min(y, H - y) <= r;
             const int x0 = 2 * m, x1 = 2 * m + 1;
             if (!(ynear && min(x0, W - x0) <= r)) fe = __fmaf_rn(v.x, v.x, fe);
@@ -481,9 +568,10 @@ cudaError_t smem_attr(size_t bytes) {
 }
 
 int rows_per_block(int M) { return M <= 1024 ? 4 : 2; }
-// twiddles (2M + 1) and three buffers of G rows (G*M forward, G*(M+1) inverse)
-size_t rows_smem(int M) { return (size_t)(2 * M + 1 + 3 * rows_per_block(M) * (M + 1)) * sizeof(float2); }
-size_t cols_smem(int H, int tc) { return (size_t)(H + 2 * 2 * tc * H) * sizeof(float2); }
+// twiddles (M) and three buffers of G padded rows
+size_t rows_buf(int M) { return (size_t)rows_per_block(M) * padded_len(M + 1); }
+size_t rows_smem(int M) { return ((size_t)M + 3 * rows_buf(M)) * sizeof(float2); }
+size_t cols_smem(int H, int tc) { return ((size_t)H + 2 * 2 * tc * (size_t)padded_len(H)) * sizeof(float2); }
 // widest column tile whose block still fits twice per SM, else once
 int cols_tile(int H) {
     for (int tc : {4, 2, 1})
@@ -520,6 +608,19 @@ bool corr_fft_supported(int H, int W) {
 size_t corr_twiddle_count(int H, int W) { return (size_t)(W / 2) * 2 + 1 + H; }
 int corr_pitch(int W) { return (W / 2 + 1 + 3) / 4 * 4; }
 
+namespace {
+template <auto Kern, typename... Args>
+cudaError_t launch(dim3 grid, size_t smem, cudaStream_t st, Args... args) {
+    cudaError_t e = smem_attr<Kern>(smem);
+    if (e != cudaSuccess) return e;
+    Kern<<<grid, CT, smem, st>>>(args...);
+    return cudaGetLastError();
+}
+// lengths with compiled-in pass plans (1920 x 1080 frames); others run the
+// same passes with run-time strides
+constexpr int kStaticM = 960, kStaticH = 1080;
+}  // namespace
+
 cudaError_t launch_corr_fft(const float *XY, float2 *F, float2 *tw, int n, int H, int W, int r, int nb,
                             double *part_e, float *part_v, long long *part_i, float *c0, int sms, cudaStream_t st,
                             int stage) {
@@ -528,45 +629,31 @@ cudaError_t launch_corr_fft(const float *XY, float2 *F, float2 *tw, int n, int H
     if (!fft_steps(M, &pm) || !fft_steps(H, &ph)) return cudaErrorInvalidValue;
     const int G = rows_per_block(M);
     const size_t rs = rows_smem(M);
-    cudaError_t e;
     if (stage == 0) {
         const int nt = corr_twiddle_count(H, W);
         k_twiddles<<<(nt + 255) / 256, 256, 0, st>>>(tw, M, H);
         const long long nrows = 2LL * n * H;
-        const long long blocks = std::min<long long>((nrows + G - 1) / G, (long long)sms * (rs <= 113 * 1024 ? 2 : 1));
-        if (G == 4) {
-            if ((e = smem_attr<k_rfft_rows<4>>(rs)) != cudaSuccess) return e;
-            k_rfft_rows<4><<<(unsigned)blocks, CT, rs, st>>>(XY, F, nrows, W, ld, pm, tw);
-        } else {
-            if ((e = smem_attr<k_rfft_rows<2>>(rs)) != cudaSuccess) return e;
-            k_rfft_rows<2><<<(unsigned)blocks, CT, rs, st>>>(XY, F, nrows, W, ld, pm, tw);
-        }
-    } else if (stage == 1) {
+        const dim3 grid((unsigned)std::min<long long>((nrows + G - 1) / G, (long long)sms * (rs <= 113 * 1024 ? 2 : 1)));
+        if (M == kStaticM) return launch<k_rfft_rows<4, kStaticM>>(grid, rs, st, XY, F, nrows, W, ld, pm, (const float2 *)tw);
+        if (G == 4) return launch<k_rfft_rows<4, 0>>(grid, rs, st, XY, F, nrows, W, ld, pm, (const float2 *)tw);
+        return launch<k_rfft_rows<2, 0>>(grid, rs, st, XY, F, nrows, W, ld, pm, (const float2 *)tw);
+    }
+    if (stage == 1) {
         const int tc = cols_tile(H);
         const size_t cs = cols_smem(H, tc);
         const dim3 grid((Wh + tc - 1) / tc, n);
         const float2 *twc = tw + 2 * M + 1;
-        if (tc == 4) {
-            if ((e = smem_attr<k_corr_columns<4>>(cs)) != cudaSuccess) return e;
-            k_corr_columns<4><<<grid, CT, cs, st>>>(F, n, H, Wh, ld, ph, twc);
-        } else if (tc == 2) {
-            if ((e = smem_attr<k_corr_columns<2>>(cs)) != cudaSuccess) return e;
-            k_corr_columns<2><<<grid, CT, cs, st>>>(F, n, H, Wh, ld, ph, twc);
-        } else {
-            if ((e = smem_attr<k_corr_columns<1>>(cs)) != cudaSuccess) return e;
-            k_corr_columns<1><<<grid, CT, cs, st>>>(F, n, H, Wh, ld, ph, twc);
-        }
-    } else {
-        const dim3 grid((unsigned)std::min(nb, (H + G - 1) / G), n);
-        if (G == 4) {
-            if ((e = smem_attr<k_corr_rows<4>>(rs)) != cudaSuccess) return e;
-            k_corr_rows<4><<<grid, CT, rs, st>>>(F, H, W, ld, r, pm, tw, part_e, part_v, part_i, c0);
-        } else {
-            if ((e = smem_attr<k_corr_rows<2>>(rs)) != cudaSuccess) return e;
-            k_corr_rows<2><<<grid, CT, rs, st>>>(F, H, W, ld, r, pm, tw, part_e, part_v, part_i, c0);
-        }
+        if (H == kStaticH && tc == 2) return launch<k_corr_columns<2, kStaticH>>(grid, cs, st, F, n, H, Wh, ld, ph, twc);
+        if (tc == 4) return launch<k_corr_columns<4, 0>>(grid, cs, st, F, n, H, Wh, ld, ph, twc);
+        if (tc == 2) return launch<k_corr_columns<2, 0>>(grid, cs, st, F, n, H, Wh, ld, ph, twc);
+        return launch<k_corr_columns<1, 0>>(grid, cs, st, F, n, H, Wh, ld, ph, twc);
     }
-    return cudaGetLastError();
+    const dim3 grid((unsigned)std::min(nb, (H + G - 1) / G), n);
+    const float2 *Fc = F, *twc = tw;
+    if (M == kStaticM)
+        return launch<k_corr_rows<4, kStaticM>>(grid, rs, st, Fc, H, W, ld, r, pm, twc, part_e, part_v, part_i, c0);
+    if (G == 4) return launch<k_corr_rows<4, 0>>(grid, rs, st, Fc, H, W, ld, r, pm, twc, part_e, part_v, part_i, c0);
+    return launch<k_corr_rows<2, 0>>(grid, rs, st, Fc, H, W, ld, r, pm, twc, part_e, part_v, part_i, c0);
 }
 
 int corr_rows_blocks(int H, int W, int nb) { return std::min(nb, (H + rows_per_block(W / 2) - 1) / rows_per_block(W / 2)); }
