@@ -165,7 +165,10 @@ def test_finalize_flags(ctx, flags):
 
 
 # ------------------------------------------------------------------- PCE ----
-@pytest.mark.parametrize("H,W,C", [(64, 64, 1), (96, 80, 3), (256, 256, 1)])
+# own-FFT geometries (radix 8/4/2/3/5/7 factors, column tiles with a ragged
+# tail, two-row blocks for W/2 > 1024) and cuFFT ones (prime factors)
+@pytest.mark.parametrize("H,W,C", [(64, 64, 1), (96, 80, 3), (256, 256, 1), (84, 140, 1), (50, 2240, 1),
+                                   (74, 94, 1), (1080, 1920, 1)])
 def test_pce_matches_oracle(ctx, H, W, C):
     rng = np.random.default_rng(H * C)
     K = rng.normal(0, 0.01, size=(H, W))
@@ -177,6 +180,23 @@ def test_pce_matches_oracle(ctx, H, W, C):
     assert abs(pce - r.pce) <= PCE_TOL * abs(r.pce)
     assert abs(ncc - r.ncc) <= 1e-4 * abs(r.ncc)
     assert peak == r.peak == (0, 0)
+
+
+@pytest.mark.parametrize("H,W,dy,dx", [(84, 140, 5, -9), (96, 80, -30, 17), (74, 94, 3, 40)])
+def test_pce_peak_follows_a_circular_shift(ctx, H, W, dy, dx):
+    """The query's noise is the fingerprint pattern shifted circularly by
+    (dy, dx): the correlation peak moves to that shift (bit-exact index
+    against the oracle) and the PCE at zero shift collapses."""
+    rng = np.random.default_rng(H + W)
+    K = rng.normal(0, 0.01, size=(H, W))
+    Iq = rng.uniform(40, 220, size=(1, H, W))
+    Wq = np.roll(K[None] * Iq, (-dy, -dx), axis=(1, 2)) + rng.normal(0, 0.3, size=(1, H, W))
+    pce, ncc, peak = ctx.pce_match(_dev(K.astype(np.float32)), _dev(Wq.astype(np.float32)),
+                                   _dev(Iq.astype(np.float32)))
+    r = O.pce_match(K, O.to_gray(Wq.astype(np.float32)), O.to_gray(Iq.astype(np.float32)))
+    assert peak == r.peak == (dy % H, dx % W)
+    assert abs(pce - r.pce) <= PCE_TOL * max(abs(r.pce), 1.0)
+    assert abs(pce) < 60
 
 
 def test_planted_camera_end_to_end(ctx):
