@@ -17,9 +17,9 @@
 // The correlation plane itself is never written.  All transforms are
 // unnormalised (the result is H*W times the correlation), like cuFFT's.
 //
-// Each 1-D transform is a Stockham autosort FFT over the factors 8, 4, 2, 3,
-// 5, 7 of its length; one pass per factor, ping-ponging between two shared
-// buffers.  Several sequences are interleaved element by element (element j of
+// Each 1-D transform is a Stockham autosort FFT over the factors 8, 4, 2, 9,
+// 15, 3, 5, 7 of its length (9 and 15 as register-resident composite
+// butterflies); one pass per factor, ping-ponging between two shared buffers.  Several sequences are interleaved element by element (element j of
 // sequence g at j*G + g) and consecutive threads take consecutive sequences,
 // so every shared-memory access of a pass is conflict-free.  Twiddles are
 // computed once per call in float64 (k_twiddles) and rounded to float.
@@ -163,6 +163,56 @@ struct Dft<5> : DftOdd<5> {};
 template <>
 struct Dft<7> : DftOdd<7> {};
 
+// 9 = 3 x 3 (Cooley-Tukey, twiddles w_9^{n2 k1} as constants):
+// X[k1 + 3 k2] = sum_n2 w_3^{n2 k2} w_9^{n2 k1} sum_n1 x[3 n1 + n2] w_3^{n1 k1}
+template <>
+struct Dft<9> {
+    static __device__ __forceinline__ void run(float2 *v) {
+        // w_9^j = (cos 2 pi j / 9, -sin 2 pi j / 9), j = 1, 2, 4
+        const float2 w1 = make_float2(0.76604444311897804f, -0.64278760968653933f);
+        const float2 w2 = make_float2(0.17364817766693035f, -0.98480775301220806f);
+        const float2 w4 = make_float2(-0.93969262078590838f, -0.34202014332566873f);
+        float2 y[3][3];
+#pragma unroll
+        for (int n2 = 0; n2 < 3; ++n2) {
+            float2 a[3] = {v[n2], v[3 + n2], v[6 + n2]};
+            Dft<3>::run(a);
+            y[n2][0] = a[0];
+            y[n2][1] = n2 == 0 ? a[1] : cmul(a[1], n2 == 1 ? w1 : w2);
+            y[n2][2] = n2 == 0 ? a[2] : cmul(a[2], n2 == 1 ? w2 : w4);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < 3; ++k1) {
+            float2 b[3] = {y[0][k1], y[1][k1], y[2][k1]};
+            Dft<3>::run(b);
+#pragma unroll
+            for (int k2 = 0; k2 < 3; ++k2) v[k1 + 3 * k2] = b[k2];
+        }
+    }
+};
+
+// 15 = 3 x 5 by the prime-factor (Good-Thomas) map, no twiddles:
+// input n = (5 n1 + 3 n2) mod 15, output k = (10 k1 + 6 k2) mod 15
+template <>
+struct Dft<15> {
+    static __device__ __forceinline__ void run(float2 *v) {
+        float2 b[3][5];
+#pragma unroll
+        for (int n2 = 0; n2 < 5; ++n2) {
+            float2 c[3] = {v[(3 * n2) % 15], v[(5 + 3 * n2) % 15], v[(10 + 3 * n2) % 15]};
+            Dft<3>::run(c);
+#pragma unroll
+            for (int k1 = 0; k1 < 3; ++k1) b[k1][n2] = c[k1];
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < 3; ++k1) {
+            Dft<5>::run(b[k1]);
+#pragma unroll
+            for (int k2 = 0; k2 < 5; ++k2) v[(10 * k1 + 6 * k2) % 15] = b[k1][k2];
+        }
+    }
+};
+
 // ------------------------------------------------------ Stockham passes ---
 // Element j of interleaved sequence g sits at at<G>(j, g): rows of G
 // elements with one row of padding after every 16, so that the strided
@@ -232,6 +282,8 @@ __device__ float2 *fft_run(float2 *a, float2 *b, const FftSteps &p, const float2
             case 2: fft_pass<2, G, NA, INV>(a, b, p.L, Ns, tw); break;
             case 3: fft_pass<3, G, NA, INV>(a, b, p.L, Ns, tw); break;
             case 5: fft_pass<5, G, NA, INV>(a, b, p.L, Ns, tw); break;
+            case 9: fft_pass<9, G, NA, INV>(a, b, p.L, Ns, tw); break;
+            case 15: fft_pass<15, G, NA, INV>(a, b, p.L, Ns, tw); break;
             default: fft_pass<7, G, NA, INV>(a, b, p.L, Ns, tw); break;
         }
         __syncthreads();
@@ -249,11 +301,13 @@ struct StaticPlan {
     int np = 0;
     int r[kMaxFftPasses] = {}, ns[kMaxFftPasses] = {};
 };
+// Powers of two first (8, 4, 2), then the odd part in register radices 9
+// and 15 where they divide it, then 3, 5, 7: 960 = 8.8.15, 1080 = 8.9.15.
 __host__ __device__ constexpr StaticPlan static_plan(int L) {
     StaticPlan p{};
-    const int rs[6] = {8, 4, 2, 3, 5, 7};
+    const int rs[8] = {8, 4, 2, 9, 15, 3, 5, 7};
     int x = L, ns = 1;
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < 8; ++i)
         while (x % rs[i] == 0 && p.np < kMaxFftPasses) {
             p.r[p.np] = rs[i];
             p.ns[p.np] = ns;
@@ -584,16 +638,12 @@ int cols_tile(int H) {
 }  // namespace
 
 bool fft_steps(int L, FftSteps *p) {
+    if (L < 2) return false;
+    const StaticPlan sp = static_plan(L);
+    if (sp.np <= 0) return false;
     FftSteps s{};
     s.L = L;
-    if (L < 2) return false;
-    int x = L;
-    for (int r : {8, 4, 2, 3, 5, 7})
-        while (x % r == 0 && s.np < kMaxFftPasses) {
-            s.radix |= (unsigned long long)r << (4 * s.np++);
-            x /= r;
-        }
-    if (x != 1) return false;
+    for (int i = 0; i < sp.np; ++i) s.radix |= (unsigned long long)sp.r[i] << (4 * s.np++);
     *p = s;
     return true;
 }
