@@ -215,15 +215,17 @@ struct Dft<15> {
 
 // ------------------------------------------------------ Stockham passes ---
 // Element j of interleaved sequence g sits at at<G>(j, g): rows of G
-// elements with one row of padding after every 16, so that the strided
+// elements with one row of padding after every 8, so that the strided
 // writes of the early passes (stride R rows) spread over the banks as the
-// contiguous reads do; the offsets stay linear in the butterfly's element
-// index wherever the stride is a multiple of 16.
+// contiguous reads do; padded row prow(j + 8c) = prow(j) + 9c, so offsets
+// stay linear in the butterfly's element index wherever the stride is a
+// multiple of 8.
+__host__ __device__ constexpr int prow(int j) { return j + (j >> 3); }
 template <int G>
 __device__ __forceinline__ int at(int j, int g) {
-    return (j + (j >> 4)) * G + g;
+    return prow(j) * G + g;
 }
-__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4) + 1; }
+__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 3) + 1; }
 
 // twiddles w_L^{m ts} (exponent sign -1, or +1 with INV), then the radix-R DFT
 template <int R, bool INV>
@@ -323,6 +325,11 @@ template <int R, int L, int Ns, int G, int NA, bool INV>
 __device__ __forceinline__ void fft_pass_s(const float2 *__restrict__ a, float2 *__restrict__ b,
                                            const float2 *__restrict__ tw) {
     constexpr int nb = L / R, step = L / (Ns * R), total = nb * NA;
+    // element offsets linear in m: loads when nb is a multiple of 8; stores
+    // when Ns is, or when Ns = 1 and R divides 8 (base = j R, m < R)
+    constexpr bool ld_lin = nb % 8 == 0;
+    constexpr bool st_lin = Ns % 8 == 0 || (Ns == 1 && 8 % R == 0);
+    constexpr int ld_step = prow(nb), st_step = Ns == 1 ? 1 : prow(Ns);
 #pragma unroll
     for (int it = 0; it < (total + CT - 1) / CT; ++it) {
         const int u = (int)threadIdx.x + it * CT;
@@ -330,12 +337,24 @@ __device__ __forceinline__ void fft_pass_s(const float2 *__restrict__ a, float2 
             const int g = u % NA, j = u / NA;
             const int k = Ns == 1 ? 0 : j % Ns;
             float2 v[R];
+            if constexpr (ld_lin) {
+                const float2 *src = a + at<G>(j, g);
 #pragma unroll
-            for (int m = 0; m < R; ++m) v[m] = a[at<G>(j + m * nb, g)];
+                for (int m = 0; m < R; ++m) v[m] = src[m * ld_step * G];
+            } else {
+#pragma unroll
+                for (int m = 0; m < R; ++m) v[m] = a[at<G>(j + m * nb, g)];
+            }
             butterfly<R, INV>(v, tw, k * step);
             const int base = (j - k) * R + k;
+            if constexpr (st_lin) {
+                float2 *dst = b + at<G>(base, g);
 #pragma unroll
-            for (int m = 0; m < R; ++m) b[at<G>(base + m * Ns, g)] = v[m];
+                for (int m = 0; m < R; ++m) dst[m * st_step * G] = v[m];
+            } else {
+#pragma unroll
+                for (int m = 0; m < R; ++m) b[at<G>(base + m * Ns, g)] = v[m];
+            }
         }
     }
 }
@@ -513,9 +532,6 @@ __global__ void __launch_bounds__(CT) k_corr_rows(const float2 *__restrict__ Zal
                                                   FftSteps p, const float2 *__restrict__ twg, double *part_e,
                                                   float *part_v, long long *part_i, float *c0) {
     extern __shared__ float2 sm[];
-    __shared__ double sh[32];
-    __shared__ float sv[CT];
-    __shared__ long long si[CT];
     const int M = MS > 0 ? MS : W >> 1, Wh = M + 1;
     float2 *tw = sm, *Wk = sm + M;  // w_M^i; the split step's w_W^k are read through L1
     const float2 *__restrict__ twh = twg + M;
@@ -576,6 +592,11 @@ __global__ void __launch_bounds__(CT) k_corr_rows(const float2 *__restrict__ Zal
         __syncthreads();  // Wk / cur are reused by the next iteration
     }
     cp_async_wait<0>();
+    __syncthreads();
+    // block reduction scratch in the now idle work buffer
+    double *sh = reinterpret_cast<double *>(Wk);
+    float *sv = reinterpret_cast<float *>(sh + 32);
+    long long *si = reinterpret_cast<long long *>(sv + CT);
     const double e = block_sum_d(acc, sh);
     sv[threadIdx.x] = bv;
     si[threadIdx.x] = bi;
@@ -624,7 +645,10 @@ cudaError_t smem_attr(size_t bytes) {
 int rows_per_block(int M) { return M <= 1024 ? 4 : 2; }
 // twiddles (M) and three buffers of G padded rows
 size_t rows_buf(int M) { return (size_t)rows_per_block(M) * padded_len(M + 1); }
-size_t rows_smem(int M) { return ((size_t)M + 3 * rows_buf(M)) * sizeof(float2); }
+// (k_corr_rows reuses its work buffer as 3328 bytes of reduction scratch)
+size_t rows_smem(int M) {
+    return std::max(((size_t)M + 3 * rows_buf(M)) * sizeof(float2), (size_t)M * sizeof(float2) + 3328);
+}
 size_t cols_smem(int H, int tc) { return ((size_t)H + 2 * 2 * tc * (size_t)padded_len(H)) * sizeof(float2); }
 // widest column tile whose block still fits twice per SM, else once
 int cols_tile(int H) {
