@@ -77,6 +77,9 @@ typedef struct {
     int compensated; /* 0: num/den are float32 [C][H][W];  1: compensated sums, num and den each point to
                         [2][C][H][W] float32 (the float-float pair hi, then lo, both zero-initialised by the
                         caller), accumulated with TwoSum error terms; finalize then reads both parts */
+    int sda_blocks_per_sm; /* 0 (default): the SDA group-sum kernel fills every SM; 1..32: at most that many
+                              of its 1024-thread blocks per SM, leaving room for kernels that run concurrently
+                              on other streams (e.g. prnu_pce_images_prepare) */
 } prnu_params;
 
 typedef struct prnu_ctx prnu_ctx; /* opaque; owns no per-call buffers */
@@ -276,6 +279,23 @@ prnu_status prnu_pce_match_images(prnu_ctx *ctx, const float *K, const float *im
 prnu_status prnu_pce_match_images_async(prnu_ctx *ctx, const float *K, const float *img_q, int n, int H, int W,
                                         int C, const prnu_params *params, int nbhd, double *pce_dev, double *ncc_dev,
                                         int *peak_dev, void *ws, size_t ws_bytes, void *stream);
+
+/* prnu_pce_match_images_async in two halves, so that the queries' denoising
+ * (which does not involve K) can run on another stream while the fingerprint
+ * is extracted.  prnu_pce_images_prepare takes the query images through the
+ * wavelet analysis, the shrink and the synthesis down to level 2 and leaves
+ * the subbands in ws (size from prnu_workspace_size_pce_images);
+ * prnu_pce_images_finish_async, called later (stream-ordered after it) with
+ * the same img_q, n, geometry, params and ws, synthesises the grey level-1
+ * residual against K and writes the PCE / NCC / peak outputs to the device
+ * like prnu_pce_match_images_async.  The results equal those of
+ * prnu_pce_match_images.  ws must not be used in between; float32 subbands
+ * only (PRNU_EUNSUPPORTED otherwise).  Neither call synchronises. */
+prnu_status prnu_pce_images_prepare(prnu_ctx *ctx, const float *img_q, int n, int H, int W, int C,
+                                    const prnu_params *params, void *ws, size_t ws_bytes, void *stream);
+prnu_status prnu_pce_images_finish_async(prnu_ctx *ctx, const float *K, const float *img_q, int n, int H, int W,
+                                         int C, const prnu_params *params, int nbhd, double *pce_dev,
+                                         double *ncc_dev, int *peak_dev, void *ws, size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Differentiation.  The chain of Sec. III-A / III-B with the SDA weights made

@@ -155,9 +155,14 @@ Layout make_layout(int H, int W, long long P, int L, bool withX, int sdt = SB_F3
 // after level, each [3][P][Hp/2^l][Wp/2^l]) the shrink is replaced by its
 // adjoint: `in` is then a residual gradient and the result (accumulated into
 // fin.res_out) the gradient of the input; dL/dsigma0 is added to *g_sigma.
+// run_denoise phases: everything; analysis, shrink and synthesis down to
+// level 2 only; the level-1 synthesis (and its epilogue) only, from subbands a
+// kDenoiseUpToLevel2 call left in the same workspace.
+constexpr int kDenoiseAll = 0, kDenoiseUpToLevel2 = 1, kDenoiseLevel1 = 2;
 prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, const prnu_params &prm, const Win &win,
                         PlaneScale sc, int scale_on, char *ws, const Layout &lo, FinalArgs fin, bool mle,
-                        cudaStream_t st, const float *ckpt = nullptr, double *g_sigma = nullptr);
+                        cudaStream_t st, const float *ckpt = nullptr, double *g_sigma = nullptr,
+                        int phase = kDenoiseAll);
 
 // cuFFT plan cache: (H, W, type, batch) -> plan without an auto-allocated
 // work area; batched planes are contiguous with the default distances.

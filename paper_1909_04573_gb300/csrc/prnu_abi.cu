@@ -130,6 +130,8 @@ prnu_status check_params(const prnu_params *p, int H, int W, Win *win) {
     if (p->frame_dtype != PRNU_FRAMES_U8 && p->frame_dtype != PRNU_FRAMES_F16)
         return fail(PRNU_EINVAL, "frame_dtype %d invalid (0 = uint8, 1 = float16)", p->frame_dtype);
     if (p->compensated != 0 && p->compensated != 1) return fail(PRNU_EINVAL, "compensated must be 0 or 1");
+    if (p->sda_blocks_per_sm < 0 || p->sda_blocks_per_sm > 32)
+        return fail(PRNU_EINVAL, "sda_blocks_per_sm must be in 0..32");
     if (win) {
         win->n = p->n_windows;
         for (int i = 0; i < 4; ++i) {
@@ -177,7 +179,7 @@ Layout make_layout(int H, int W, long long P, int L, bool withX, int sdt) {
 // MLE) is described by `fin`, whose coefficient pointers are filled here.
 prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, const prnu_params &prm, const Win &win,
                         PlaneScale sc, int scale_on, char *ws, const Layout &lo, FinalArgs fin, bool mle,
-                        cudaStream_t st, const float *ckpt, double *g_sigma) {
+                        cudaStream_t st, const float *ckpt, double *g_sigma, int phase) {
     size_t ckpt_off = 0;  // floats of the levels before l in the checkpoint
     const int L = prm.levels;
     const int Hp = padded(H, L), Wp = padded(W, L);
@@ -186,7 +188,7 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
     const size_t es = subband_bytes(sdt);
     // typed subband k of a region holding 3 (or 1) planes groups of P planes
     auto SB = [&](size_t off, long long A, int k) { return static_cast<void *>(ws + off + (size_t)k * P * A * es); };
-    for (int l = 1; l <= L; ++l) {
+    for (int l = 1; l <= L && phase != kDenoiseLevel1; ++l) {
         const long long A = (long long)(Hp >> l) * (Wp >> l);
         AnaArgs a{};
         a.inh = l == 1 ? in : F(lo.LLh[l - 1]);
@@ -253,7 +255,7 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
     // synthesise the grey combination of the channels' noise, one plane per image
     const bool grey = fin.pce && fin.C == 3;
     const int Ps = grey ? P / 3 : P;
-    for (int l = L; l >= 2; --l) {
+    for (int l = L; l >= 2 && phase != kDenoiseLevel1; --l) {
         const long long A = (long long)(Hp >> l) * (Wp >> l);
         SynArgs y{};
         y.LL = l == L ? nullptr : SB(lo.Rn[l], A, 0);
@@ -272,6 +274,7 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
             CU(launch_synthesis(y, st));
         }
     }
+    if (phase == kDenoiseUpToLevel2) return PRNU_OK;
     const long long A1 = (long long)(Hp >> 1) * (Wp >> 1);
     fin.LL = L == 1 ? nullptr : SB(lo.Rn[1], A1, 0);
     fin.LH = SB(lo.N[1], A1, 0);
@@ -411,7 +414,7 @@ prnu_status sda_pass(prnu_ctx *ctx, const uint8_t *frames, int m, int H, int W, 
     sa.out = reinterpret_cast<float *>(ws + lo.X);
     sa.mean = 0;
     sa.frame_half = prm.frame_dtype == PRNU_FRAMES_F16;
-    sa.blocks_per_sm = blocks_per_sm;
+    sa.blocks_per_sm = blocks_per_sm > 0 ? blocks_per_sm : prm.sda_blocks_per_sm;
     const double fr = (double)(std::min(m, (g0 + G) * d) - g0 * d) * H * W * C *
                       (prm.frame_dtype == PRNU_FRAMES_F16 ? 2 : 1);
     Launch t(ctx, "sda_sum", st, 1, fr + (double)P * H * W * 4);
@@ -541,6 +544,7 @@ prnu_status prnu_default_params(prnu_params *p) {
     p->dtype = PRNU_DTYPE_F32;
     p->frame_dtype = PRNU_FRAMES_U8;
     p->compensated = 0;
+    p->sda_blocks_per_sm = 0;
     return PRNU_OK;
 }
 
@@ -1088,8 +1092,8 @@ prnu_status prnu_workspace_size_pce_images(prnu_ctx *ctx, int H, int W, int C, c
 namespace {
 prnu_status pce_images_impl(prnu_ctx *ctx, const float *K, const float *img_q, int n, int H, int W, int C,
                             const prnu_params *params, int nbhd, double *pce_out, double *ncc_out, int *peak_yx,
-                            void *ws, size_t ws_bytes, void *stream, bool device_out) {
-    if (!ctx || !K || !img_q || !pce_out) return fail(PRNU_EINVAL, "NULL argument");
+                            void *ws, size_t ws_bytes, void *stream, bool device_out, int phase = kDenoiseAll) {
+    if (!ctx || !img_q || (phase != kDenoiseUpToLevel2 && (!K || !pce_out))) return fail(PRNU_EINVAL, "NULL argument");
     if (n < 1) return fail(PRNU_EINVAL, "n must be >= 1");
     prnu_status s;
     Win win;
@@ -1118,12 +1122,27 @@ prnu_status pce_images_impl(prnu_ctx *ctx, const float *K, const float *img_q, i
     fin.Xo = X;
     fin.Yo = X + n * hw;
     fin.part_m = reinterpret_cast<double *>(b + p.pm);
-    if ((s = run_denoise(ctx, img_q, H, W, n * C, *params, win, fin.sc, 0, b, p.den, fin, false, st)) != PRNU_OK)
+    if ((s = run_denoise(ctx, img_q, H, W, n * C, *params, win, fin.sc, 0, b, p.den, fin, false, st, nullptr,
+                         nullptr, phase)) != PRNU_OK)
         return s;
+    if (phase == kDenoiseUpToLevel2) return PRNU_OK;
     return pce_finish(ctx, n, H, W, nbhd, p.fft, b + p.fft_off, fin.part_m, p.nbm, pce_out, ncc_out, peak_yx, st,
                       device_out);
 }
 }  // namespace
+
+prnu_status prnu_pce_images_prepare(prnu_ctx *ctx, const float *img_q, int n, int H, int W, int C,
+                                    const prnu_params *params, void *ws, size_t ws_bytes, void *stream) {
+    return pce_images_impl(ctx, nullptr, img_q, n, H, W, C, params, 1, nullptr, nullptr, nullptr, ws, ws_bytes,
+                           stream, true, kDenoiseUpToLevel2);
+}
+
+prnu_status prnu_pce_images_finish_async(prnu_ctx *ctx, const float *K, const float *img_q, int n, int H, int W,
+                                         int C, const prnu_params *params, int nbhd, double *pce_dev,
+                                         double *ncc_dev, int *peak_dev, void *ws, size_t ws_bytes, void *stream) {
+    return pce_images_impl(ctx, K, img_q, n, H, W, C, params, nbhd, pce_dev, ncc_dev, peak_dev, ws, ws_bytes, stream,
+                           true, kDenoiseLevel1);
+}
 
 prnu_status prnu_pce_match_images(prnu_ctx *ctx, const float *K, const float *img_q, int n, int H, int W, int C,
                                   const prnu_params *params, int nbhd, double *pce_out, double *ncc_out,

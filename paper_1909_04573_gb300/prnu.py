@@ -28,7 +28,8 @@ EXPORTS = (
     "prnu_autotune_set", "prnu_sda_weighted", "prnu_sda_weighted_backward", "prnu_workspace_size_grad",
     "prnu_denoise_residual_ckpt", "prnu_denoise_residual_backward", "prnu_mle_images", "prnu_mle_images_backward",
     "prnu_workspace_size_pce_backward", "prnu_pce_backward", "prnu_workspace_size_pce_images",
-    "prnu_pce_match_images", "prnu_pce_match_images_async",
+    "prnu_pce_match_images", "prnu_pce_match_images_async", "prnu_pce_images_prepare",
+    "prnu_pce_images_finish_async",
 )
 
 
@@ -45,7 +46,7 @@ PRNU_FRAMES_U8, PRNU_FRAMES_F16 = 0, 1
 class prnu_params(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("sigma0", ctypes.c_float), ("n_windows", ctypes.c_int),
                 ("windows", ctypes.c_int * 4), ("pad_mode", ctypes.c_int), ("dtype", ctypes.c_int),
-                ("frame_dtype", ctypes.c_int), ("compensated", ctypes.c_int)]
+                ("frame_dtype", ctypes.c_int), ("compensated", ctypes.c_int), ("sda_blocks_per_sm", ctypes.c_int)]
 
 
 class prnu_camera(ctypes.Structure):
@@ -98,6 +99,9 @@ def lib() -> ctypes.CDLL:
                 "prnu_workspace_size_pce_images": [_vp, _i, _i, _i, _pp, _i, ctypes.POINTER(_sz)],
                 "prnu_pce_match_images_async": [_vp, _vp, _vp, _i, _i, _i, _i, _pp, _i, _vp, _vp, _vp, _vp, _sz,
                                                 _vp],
+                "prnu_pce_images_prepare": [_vp, _vp, _i, _i, _i, _i, _pp, _vp, _sz, _vp],
+                "prnu_pce_images_finish_async": [_vp, _vp, _vp, _i, _i, _i, _i, _pp, _i, _vp, _vp, _vp, _vp, _sz,
+                                                 _vp],
                 "prnu_pce_match_images": [_vp, _vp, _vp, _i, _i, _i, _i, _pp, _i, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i), _vp, _sz, _vp],
                 "prnu_sda_weighted": [_vp, _vp, _i, _i, _i, _i, _sz, _sz, _i, _vp, _vp, _vp],
@@ -131,12 +135,13 @@ def _check(status: int, ctx=None) -> None:
 
 
 def default_params(levels=4, sigma0=3.0, windows=(3, 5, 7, 9), dtype=PRNU_DTYPE_F32, frame_dtype=PRNU_FRAMES_U8,
-                   compensated=False) -> prnu_params:
+                   compensated=False, sda_blocks_per_sm=0) -> prnu_params:
     p = prnu_params()
     _check(lib().prnu_default_params(ctypes.byref(p)))
     p.dtype = dtype
     p.frame_dtype = frame_dtype
     p.compensated = 1 if compensated else 0
+    p.sda_blocks_per_sm = sda_blocks_per_sm
     p.levels = levels
     p.sigma0 = sigma0
     p.n_windows = len(windows)
@@ -431,6 +436,35 @@ class Context:
         _check(lib().prnu_pce_match_images_async(self.ctx, K.data_ptr(), img_q.data_ptr(), n, H, W, C,
                                                  ctypes.byref(params), nbhd, out[0].data_ptr(), out[1].data_ptr(),
                                                  out[2].data_ptr(), ws.data_ptr(), ws.numel(), self._stream()),
+               self.ctx)
+        return out
+
+    def pce_images_prepare(self, img_q, params=None):
+        """First half of pce_match_images_async: denoise the queries [n, C, H, W]
+        down to level 2 into this context's workspace (no K needed)."""
+        params = params or default_params()
+        n, C, H, W = img_q.shape
+        nb = prnu_workspace_size_pce_images(self.ctx, H, W, C, params, n)
+        ws = self.workspace(nb)
+        _check(lib().prnu_pce_images_prepare(self.ctx, img_q.data_ptr(), n, H, W, C, ctypes.byref(params),
+                                             ws.data_ptr(), ws.numel(), self._stream()), self.ctx)
+
+    def pce_images_finish_async(self, K, img_q, out=None, nbhd: int = 11, params=None):
+        """Second half: grey level-1 synthesis against K and PCE, results on the
+        device (pce float64 [n], ncc float64 [n], peak int32 [n, 2]); same
+        img_q and the same context (workspace) as pce_images_prepare."""
+        params = params or default_params()
+        n, C, H, W = img_q.shape
+        K = K.reshape(H, W)
+        if out is None:
+            out = (self.torch.empty(n, dtype=self.torch.float64, device=img_q.device),
+                   self.torch.empty(n, dtype=self.torch.float64, device=img_q.device),
+                   self.torch.empty((n, 2), dtype=self.torch.int32, device=img_q.device))
+        nb = prnu_workspace_size_pce_images(self.ctx, H, W, C, params, n)
+        ws = self.workspace(nb)
+        _check(lib().prnu_pce_images_finish_async(self.ctx, K.data_ptr(), img_q.data_ptr(), n, H, W, C,
+                                                  ctypes.byref(params), nbhd, out[0].data_ptr(), out[1].data_ptr(),
+                                                  out[2].data_ptr(), ws.data_ptr(), ws.numel(), self._stream()),
                self.ctx)
         return out
 

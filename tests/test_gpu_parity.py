@@ -182,6 +182,37 @@ def test_pce_matches_oracle(ctx, H, W, C):
     assert peak == r.peak == (0, 0)
 
 
+def test_pce_images_prepare_then_finish_overlapping_an_extraction(ctx):
+    """The query half split in two (prepare on a side stream in its own
+    context while the fingerprint is accumulated, finish after the join)
+    gives the PCE / NCC / peak of prnu_pce_match_images."""
+    H, W, C, n = 200, 320, 3, 3
+    cam = synth.Camera(H=H, W=W, C=C, camera_id=91)
+    fr = synth.frames(cam, 24, device="cuda")
+    qf = torch.cat([synth.frames(cam, n - 1, stream=1, device="cuda"),
+                    synth.frames(synth.foreign(cam), 1, stream=1, device="cuda")])
+    q = ctx.sda_average(qf, 1)
+    flags = P.PRNU_TO_GRAY | P.PRNU_ZERO_MEAN | P.PRNU_WIENER_DFT
+    num = torch.zeros((C, H, W), device="cuda")
+    den = torch.zeros_like(num)
+    qctx = P.Context(0)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        qctx.pce_images_prepare(q)
+    ctx.fingerprint_accumulate(fr, 8, num, den)
+    K = ctx.fingerprint_finalize(num, den, flags)
+    torch.cuda.current_stream().wait_stream(side)
+    out = qctx.pce_images_finish_async(K[0], q)
+    ref = ctx.pce_match_images(K[0], q)
+    torch.cuda.synchronize()
+    for i, (p, c, k) in enumerate(ref):
+        assert out[0][i].item() == p and out[1][i].item() == c
+        assert tuple(out[2][i].tolist()) == tuple(k)
+    assert ref[0][0] > 60 and abs(ref[-1][0]) < 60
+    qctx.close()
+
+
 @pytest.mark.parametrize("H,W,dy,dx", [(84, 140, 5, -9), (96, 80, -30, 17), (74, 94, 3, 40)])
 def test_pce_peak_follows_a_circular_shift(ctx, H, W, dy, dx):
     """The query's noise is the fingerprint pattern shifted circularly by
