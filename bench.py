@@ -698,8 +698,8 @@ def grad_config(args, rank, world, local):
         ev1 = G.mean_pce(frames, w, d, sig, q_eval, ctx).item()
     out["ascent"] = {"steps": 50, "optimizer": "Adam (lr 2e-3 weights, 5e-2 sigma0)",
                      "pce_train_start": traj[0], "pce_train_end": J_end, "pce_eval_start": ev0, "pce_eval_end": ev1,
-                     "sigma0_end": float(sig), "w_min": float(w.min()), "w_max": float(w.max()),
-                     "w_mean": float(w.mean()), "trajectory_every_10": traj[::10]}
+                     "sigma0_end": float(sig.detach()), "w_min": float(w.detach().min()),
+                     "w_max": float(w.detach().max()), "w_mean": float(w.detach().mean()), "trajectory_every_10": traj[::10]}
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.close()
