@@ -79,7 +79,7 @@ ALU_OPS_PER_BYTE = {"shrink": 41.0 / 8.0}
 FP32_LANES_PER_SM = 128
 
 # profiler name -> kernel symbol in the ncu captures (profiles/)
-NCU_NAME = {"shrink": "k_shrink_x2<0, float>", "sda_sum": "k_sda_sum<3, 1024, 0>",
+NCU_NAME = {"shrink": "k_shrink_strip<0, float>", "sda_sum": "k_sda_sum<3, 1024, 0>",
             "analysis_l1": "k_analysis_stream<1, float, 32, 2>", "analysis": "k_analysis<0, float>",
             "synthesis": "k_synthesis_stream<0>", "final_mle": "k_final_async<0>", "final_pce": "k_final_pce<1>",
             "pce_outputs": "k_pce_outputs"}

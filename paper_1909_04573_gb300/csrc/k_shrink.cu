@@ -5,8 +5,10 @@
 //   var = max(0, min_w mean_w - s0^2),   noise = c s0^2 / (var + s0^2)
 // (0 when var + s0^2 == 0, which forces c == 0).
 //
-// A 32 x 32 output tile stages c^2 with a 4-sample halo in shared memory; the
-// box sums are separable: per-window row sums, then column sums.
+// The box sums are separable: per-window row sums, then column sums.  The
+// standard windows on widths that are multiples of 4 take k_shrink_strip
+// (register column sums down a strip); other window sets and widths take
+// k_shrink (a 32 x 32 tile with both sums through shared memory).
 #include "kernels.cuh"
 
 namespace prnu {
@@ -136,18 +138,8 @@ __global__ void __launch_bounds__(256) k_shrink(ShrinkArgs a) {
 
 
 // ---------------------------------------------------------------------------
-// Packed variant for the standard windows {3, 5, 7, 9} on subbands whose width
-// is a multiple of 4.  Same arithmetic per coefficient (direct sums of c^2,
-// nested in the row direction), issued as float32x2 operations: a thread's
-// values come in pairs of adjacent columns, so every shared-memory load of
-// the box sums is an aligned 64-bit load and every add a packed add.
-//   staging: the extended tile (40 x 40) of c^2 is loaded as 4-wide groups
-//            (periodic wrap per group) and kept twice, as is and shifted left
-//            by one column, so the pair starting at any column is aligned;
-//   rows:    an item is one extended row and 4 output columns: 11 pair loads
-//            give the nested row sums of radii 1..4 for both column pairs;
-//   columns: a thread owns 2 output rows x 2 columns; per radius the two rows
-//            share the 2d middle terms of their column sums.
+// float32x2 helpers: two adjacent columns' values in one 64-bit register,
+// added and multiplied with the packed Blackwell instructions.
 using f2 = unsigned long long;  // two float32 in one 64-bit register
 
 __device__ __forceinline__ f2 pk2(float a, float b) {
@@ -189,116 +181,93 @@ template <> struct Vec4<__nv_bfloat16> {
     }
 };
 
-constexpr int XS = 42;  // row stride of the staged c^2 (even: 8-byte pairs; 2 mod 4: no bank overlap of rows)
+// ---------------------------------------------------------------------------
+// Standard windows {3, 5, 7, 9} on subbands whose width is a multiple of 4.  A tile of 64 columns x SS_H rows is staged once (the
+// coefficients with a 4-sample periodic halo); then each thread owns two
+// adjacent columns and walks down a strip of SS_SL rows without further
+// barriers: per staged row, five aligned pair loads give the nested row sums
+// of c^2 for radii 1..4 (as float32x2), and the box sums of each radius are
+// direct sums over the last 2d+1 rows' row sums, held in registers.  No
+// row-sum array goes through shared memory.
+constexpr int SS_W = 64, SS_WARPS = 4, SS_SL = 34;  // 544 = 4 x 136: level-1 subbands of 1088-row frames
+constexpr int SS_H = SS_WARPS * SS_SL;
+constexpr int SS_XS = SS_W + 2 * SH;  // 72 staged columns (float4-aligned rows)
 
 template <bool S2DEV, class T>
-__global__ void __launch_bounds__(256) k_shrink_x2(ShrinkArgs a) {
-    __shared__ __align__(16) float c2[SE][XS];   // c^2, extended columns 0..39
-    __shared__ __align__(16) float c2s[SE][XS];  // c2s[r][k] = c2[r][k + 1]
-    __shared__ __align__(16) float rs[4][SE][ST];
+__global__ void __launch_bounds__(32 * SS_WARPS) k_shrink_strip(ShrinkArgs a) {
+    __shared__ __align__(16) float cs[SS_H + 2 * SH][SS_XS];
     const int plane = blockIdx.z;
-    const int y0 = blockIdx.y * ST, x0 = blockIdx.x * ST;
-    const int tid = threadIdx.x;
+    const int y0 = blockIdx.y * SS_H, x0 = blockIdx.x * SS_W;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const T *in = static_cast<const T *>(a.in) + (long long)plane * a.R * a.Cc;
     T *out = static_cast<T *>(a.out) + (long long)plane * a.R * a.Cc;
 
-    // staging: 40 rows x 10 groups of 4 columns, both loads of a thread first
+    // staging: (SS_H + 8) rows x 18 groups of 4 columns (periodic wrap per group)
     const int nq = a.Cc >> 2;
-    constexpr int NI = SE * (SE / 4);  // 400 groups: items tid and tid + 256
-    float4 v[2];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int it = tid + 256 * k;
-        if (it < NI) {
-            const int r = it / (SE / 4), j = it - r * (SE / 4);
-            v[k] = Vec4<T>::ld(in + (long long)wrap_near(y0 + r - SH, a.R) * a.Cc +
-                               4 * wrap_near((x0 >> 2) - 1 + j, nq));
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int it = tid + 256 * k;
-        if (it < NI) {
-            const int r = it / (SE / 4), j = it - r * (SE / 4);
-            const float q0 = v[k].x * v[k].x, q1 = v[k].y * v[k].y, q2 = v[k].z * v[k].z, q3 = v[k].w * v[k].w;
-            *reinterpret_cast<float2 *>(&c2[r][4 * j]) = make_float2(q0, q1);
-            *reinterpret_cast<float2 *>(&c2[r][4 * j + 2]) = make_float2(q2, q3);
-            if (j > 0) c2s[r][4 * j - 1] = q0;
-            *reinterpret_cast<float2 *>(&c2s[r][4 * j]) = make_float2(q1, q2);
-            c2s[r][4 * j + 2] = q3;
-        }
+    constexpr int GPR = SS_XS / 4, NG = (SS_H + 2 * SH) * GPR;
+#pragma unroll 4
+    for (int it = tid; it < NG; it += 32 * SS_WARPS) {
+        const int r = it / GPR, j = it - r * GPR;
+        const float4 v = Vec4<T>::ld(in + (long long)wrap_near(y0 + r - SH, a.R) * a.Cc +
+                                     4 * wrap_near((x0 >> 2) - 1 + j, nq));
+        *reinterpret_cast<float4 *>(&cs[r][4 * j]) = v;
     }
     __syncthreads();
 
-    // rows: item = (extended row r, output columns 4g .. 4g+3)
-    for (int it = tid; it < SE * (ST / 4); it += 256) {
-        const int r = it >> 3, g = it & 7;
-        const int xc = 4 * g + SH;  // extended column of output column 4g
-        // P[i + 4] = (c2[xc + i], c2[xc + i + 1]), i = -4 .. 6
-        f2 P[11];
-#pragma unroll
-        for (int i = -4; i <= 6; ++i)
-            P[i + 4] = (i & 1) ? lds2(&c2s[r][xc + i - 1]) : lds2(&c2[r][xc + i]);
-        f2 s = add2(P[4], add2(P[3], P[5]));  // columns (4g, 4g+1)
-        f2 t = add2(P[6], add2(P[5], P[7]));  // columns (4g+2, 4g+3)
-#pragma unroll
-        for (int d = 1; d <= 4; ++d) {
-            if (d > 1) {
-                s = add2(s, add2(P[4 - d], P[4 + d]));
-                t = add2(t, add2(P[6 - d], P[6 + d]));
-            }
-            float s0, s1, t0, t1;
-            up2(s, s0, s1);
-            up2(t, t0, t1);
-            *reinterpret_cast<float4 *>(&rs[d - 1][r][4 * g]) = make_float4(s0, s1, t0, t1);
-        }
-    }
-    __syncthreads();
-
-    // columns: thread = (column pair p, row pair rp); its coefficients are
-    // loaded first so the loads overlap the sums
-    const int p = tid & 15, rp = tid >> 4;
-    const int yb = 2 * rp;  // output rows yb, yb+1
-    const int gx = x0 + 2 * p;
-    float cv[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int gy = y0 + yb + k;
-        if (gy < a.R && gx < a.Cc) {
-            cv[2 * k] = ldf<T>(in + (long long)gy * a.Cc + gx);
-            cv[2 * k + 1] = ldf<T>(in + (long long)gy * a.Cc + gx + 1);
-        }
-    }
-    f2 m0 = pk2(__int_as_float(0x7f800000), __int_as_float(0x7f800000)), m1 = m0;
-#pragma unroll
-    for (int d = 1; d <= 4; ++d) {
-        // rows yb - d .. yb + 1 + d of rs (extended row = output row + SH)
-        f2 core = lds2(&rs[d - 1][yb + SH - d + 1][2 * p]);
-#pragma unroll
-        for (int j = 2 - d; j <= d; ++j) core = add2(core, lds2(&rs[d - 1][yb + SH + j][2 * p]));
-        const f2 b0 = add2(lds2(&rs[d - 1][yb + SH - d][2 * p]), core);
-        const f2 b1 = add2(core, lds2(&rs[d - 1][yb + SH + d + 1][2 * p]));
-        const f2 iw = pk2(a.win.inv[d - 1], a.win.inv[d - 1]);
-        const f2 v0 = mul2(b0, iw), v1 = mul2(b1, iw);
-        float u0, u1, w0, w1, n0, n1, o0, o1;
-        up2(v0, u0, u1);
-        up2(v1, w0, w1);
-        up2(m0, n0, n1);
-        up2(m1, o0, o1);
-        m0 = pk2(fminf(n0, u0), fminf(n1, u1));
-        m1 = pk2(fminf(o0, w0), fminf(o1, w1));
-    }
+    const int ys = y0 + warp * SS_SL;  // first output row of this warp's strip
+    if (ys >= a.R) return;             // whole strip past the plane (no barrier follows)
+    const int gx = x0 + 2 * lane;
     const float s2 = S2DEV ? (float)a.s2_dev[1] : a.s2;
+    const f2 iw1 = pk2(a.win.inv[0], a.win.inv[0]), iw2 = pk2(a.win.inv[1], a.win.inv[1]);
+    const f2 iw3 = pk2(a.win.inv[2], a.win.inv[2]), iw4 = pk2(a.win.inv[3], a.win.inv[3]);
+    // staged row of strip row i: warp * SS_SL + i; lane's pairs start at column 2 lane
+    const float *base = &cs[warp * SS_SL][2 * lane];
+    f2 R1[SS_SL + 8], R2[SS_SL + 8], R3[SS_SL + 8], R4[SS_SL + 8];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int gy = y0 + yb + k;
-        if (gy >= a.R || gx >= a.Cc) continue;
-        float mA, mB;
-        up2(k ? m1 : m0, mA, mB);
-        T *dst = out + (long long)gy * a.Cc + gx;
-        const float denA = fmaxf(0.f, mA - s2) + s2, denB = fmaxf(0.f, mB - s2) + s2;
-        stf<T>(dst, denA > 0.f ? __fdividef(cv[2 * k] * s2, denA) : 0.f);
-        stf<T>(dst + 1, denB > 0.f ? __fdividef(cv[2 * k + 1] * s2, denB) : 0.f);
+    for (int i = 0; i < SS_SL + 8; ++i) {
+        const float *row = base + i * SS_XS;
+        const f2 e0 = lds2(row), e1 = lds2(row + 2), e2 = lds2(row + 4), e3 = lds2(row + 6), e4 = lds2(row + 8);
+        const f2 q0 = mul2(e0, e0), q1 = mul2(e1, e1), q2 = mul2(e2, e2), q3 = mul2(e3, e3), q4 = mul2(e4, e4);
+        float a0, a1, b0, b1, c0, c1, d0, d1, g0, g1;
+        up2(q0, a0, a1);
+        up2(q1, b0, b1);
+        up2(q2, c0, c1);
+        up2(q3, d0, d1);
+        up2(q4, g0, g1);
+        // columns (x, x+1): q_k = c^2 at (x-4+2k, x-3+2k); odd pairs straddle them
+        const f2 om3 = pk2(a1, b0), om1 = pk2(b1, c0), op1 = pk2(c1, d0), op3 = pk2(d1, g0);
+        R1[i] = add2(q2, add2(om1, op1));
+        R2[i] = add2(R1[i], add2(q1, q3));
+        R3[i] = add2(R2[i], add2(om3, op3));
+        R4[i] = add2(R3[i], add2(q0, q4));
+        if (i >= 8) {
+            const int o = i - 8, c = i - 4;  // output row of the strip, its staged row (strip-relative)
+            f2 b1s = R1[c - 1], b2s = R2[c - 2], b3s = R3[c - 3], b4s = R4[c - 4];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) b1s = add2(b1s, R1[c + j]);
+#pragma unroll
+            for (int j = -1; j < 3; ++j) b2s = add2(b2s, R2[c + j]);
+#pragma unroll
+            for (int j = -2; j < 4; ++j) b3s = add2(b3s, R3[c + j]);
+#pragma unroll
+            for (int j = -3; j < 5; ++j) b4s = add2(b4s, R4[c + j]);
+            float m1a, m1b, m2a, m2b, m3a, m3b, m4a, m4b;
+            up2(mul2(b1s, iw1), m1a, m1b);
+            up2(mul2(b2s, iw2), m2a, m2b);
+            up2(mul2(b3s, iw3), m3a, m3b);
+            up2(mul2(b4s, iw4), m4a, m4b);
+            const float mA = fminf(fminf(m1a, m2a), fminf(m3a, m4a));
+            const float mB = fminf(fminf(m1b, m2b), fminf(m3b, m4b));
+            const int gy = ys + o;
+            if (gy < a.R && gx < a.Cc) {
+                float cA, cB;
+                up2(lds2(base + c * SS_XS + 4), cA, cB);
+                const float denA = fmaxf(0.f, mA - s2) + s2, denB = fmaxf(0.f, mB - s2) + s2;
+                T *dst = out + (long long)gy * a.Cc + gx;
+                stf<T>(dst, denA > 0.f ? __fdividef(cA * s2, denA) : 0.f);
+                stf<T>(dst + 1, denB > 0.f ? __fdividef(cB * s2, denB) : 0.f);
+            }
+        }
     }
 }
 
@@ -307,11 +276,12 @@ static void launch_shrink_t(const ShrinkArgs &a, cudaStream_t st) {
     dim3 block(32, 8);
     dim3 grid((unsigned)((a.Cc + ST - 1) / ST), (unsigned)((a.R + ST - 1) / ST), (unsigned)a.nplanes);
     const bool std4 = a.win.n == 4 && a.win.r[0] == 1 && a.win.r[1] == 2 && a.win.r[2] == 3 && a.win.r[3] == 4;
-    if (std4 && a.Cc % 4 == 0) {  // packed path (aligned 4-wide groups)
+    if (std4 && a.Cc % 4 == 0) {  // strip path (aligned 4-wide groups)
+        dim3 g2((unsigned)((a.Cc + SS_W - 1) / SS_W), (unsigned)((a.R + SS_H - 1) / SS_H), (unsigned)a.nplanes);
         if (a.s2_dev)
-            k_shrink_x2<true, T><<<grid, 256, 0, st>>>(a);
+            k_shrink_strip<true, T><<<g2, 32 * SS_WARPS, 0, st>>>(a);
         else
-            k_shrink_x2<false, T><<<grid, 256, 0, st>>>(a);
+            k_shrink_strip<false, T><<<g2, 32 * SS_WARPS, 0, st>>>(a);
     } else if (std4 && !a.s2_dev)
         k_shrink<true, false, T><<<grid, block, 0, st>>>(a);
     else if (std4)
