@@ -9,6 +9,8 @@
 // standard windows on widths that are multiples of 4 take k_shrink_strip
 // (register column sums down a strip); other window sets and widths take
 // k_shrink (a 32 x 32 tile with both sums through shared memory).
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace prnu {
@@ -193,38 +195,73 @@ constexpr int SS_W = 64, SS_WARPS = 4, SS_SL = 34;  // 544 = 4 x 136: level-1 su
 constexpr int SS_H = SS_WARPS * SS_SL;
 constexpr int SS_XS = SS_W + 2 * SH;  // 72 staged columns (float4-aligned rows)
 
+__device__ __forceinline__ void cp_async16(float *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// float32 subbands (WS): each warp stages its own strip (SS_SL + 8 rows) with
+// cp.async in three row groups and starts on the first while the others are
+// in flight -- no block barrier; 16-bit subbands share one converted tile.
 template <bool S2DEV, class T>
 __global__ void __launch_bounds__(32 * SS_WARPS) k_shrink_strip(ShrinkArgs a) {
-    __shared__ __align__(16) float cs[SS_H + 2 * SH][SS_XS];
+    constexpr bool WS = std::is_same<T, float>::value;
+    constexpr int SR = SS_SL + 2 * SH, GPR = SS_XS / 4;  // staged rows per strip, 4-column groups per row
+    __shared__ __align__(16) float cs[WS ? SS_WARPS * SR * SS_XS : (SS_H + 2 * SH) * SS_XS];
     const int plane = blockIdx.z;
     const int y0 = blockIdx.y * SS_H, x0 = blockIdx.x * SS_W;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const T *in = static_cast<const T *>(a.in) + (long long)plane * a.R * a.Cc;
     T *out = static_cast<T *>(a.out) + (long long)plane * a.R * a.Cc;
-
-    // staging: (SS_H + 8) rows x 18 groups of 4 columns (periodic wrap per group)
     const int nq = a.Cc >> 2;
-    constexpr int GPR = SS_XS / 4, NG = (SS_H + 2 * SH) * GPR;
-#pragma unroll 4
-    for (int it = tid; it < NG; it += 32 * SS_WARPS) {
-        const int r = it / GPR, j = it - r * GPR;
-        const float4 v = Vec4<T>::ld(in + (long long)wrap_near(y0 + r - SH, a.R) * a.Cc +
-                                     4 * wrap_near((x0 >> 2) - 1 + j, nq));
-        *reinterpret_cast<float4 *>(&cs[r][4 * j]) = v;
-    }
-    __syncthreads();
-
     const int ys = y0 + warp * SS_SL;  // first output row of this warp's strip
-    if (ys >= a.R) return;             // whole strip past the plane (no barrier follows)
+
+    if constexpr (!WS) {
+        // staging: (SS_H + 8) rows x 18 groups of 4 columns (periodic wrap per group)
+        constexpr int NG = (SS_H + 2 * SH) * GPR;
+#pragma unroll 4
+        for (int it = tid; it < NG; it += 32 * SS_WARPS) {
+            const int r = it / GPR, j = it - r * GPR;
+            const float4 v = Vec4<T>::ld(in + (long long)wrap_near(y0 + r - SH, a.R) * a.Cc +
+                                         4 * wrap_near((x0 >> 2) - 1 + j, nq));
+            *reinterpret_cast<float4 *>(&cs[r * SS_XS + 4 * j]) = v;
+        }
+        __syncthreads();
+    }
+    if (ys >= a.R) return;  // whole strip past the plane (no barrier follows)
+    float *const wsm = WS ? cs + warp * SR * SS_XS : cs + warp * SS_SL * SS_XS;
+    if constexpr (WS) {
+        static_assert(SR % 3 == 0, "three equal row groups");
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            for (int it = lane; it < (SR / 3) * GPR; it += 32) {
+                const int r = g * (SR / 3) + it / GPR, j = it % GPR;
+                cp_async16(wsm + r * SS_XS + 4 * j, in + (long long)wrap_near(ys - SH + r, a.R) * a.Cc +
+                                                        4 * wrap_near((x0 >> 2) - 1 + j, nq));
+            }
+            cp_async_commit();
+        }
+    }
     const int gx = x0 + 2 * lane;
     const float s2 = S2DEV ? (float)a.s2_dev[1] : a.s2;
     const f2 iw1 = pk2(a.win.inv[0], a.win.inv[0]), iw2 = pk2(a.win.inv[1], a.win.inv[1]);
     const f2 iw3 = pk2(a.win.inv[2], a.win.inv[2]), iw4 = pk2(a.win.inv[3], a.win.inv[3]);
-    // staged row of strip row i: warp * SS_SL + i; lane's pairs start at column 2 lane
-    const float *base = &cs[warp * SS_SL][2 * lane];
+    // staged row of strip row i: wsm + i * SS_XS; lane's pairs start at column 2 lane
+    const float *base = wsm + 2 * lane;
     f2 R1[SS_SL + 8], R2[SS_SL + 8], R3[SS_SL + 8], R4[SS_SL + 8];
 #pragma unroll
     for (int i = 0; i < SS_SL + 8; ++i) {
+        if constexpr (WS) {  // row group i / 14 has landed (each lane waits for its copies, then the warp syncs)
+            if (i == 0) cp_async_wait<2>();
+            if (i == SR / 3) cp_async_wait<1>();
+            if (i == 2 * SR / 3) cp_async_wait<0>();
+            if (i == 0 || i == SR / 3 || i == 2 * SR / 3) __syncwarp();
+        }
         const float *row = base + i * SS_XS;
         const f2 e0 = lds2(row), e1 = lds2(row + 2), e2 = lds2(row + 4), e3 = lds2(row + 6), e4 = lds2(row + 8);
         const f2 q0 = mul2(e0, e0), q1 = mul2(e1, e1), q2 = mul2(e2, e2), q3 = mul2(e3, e3), q4 = mul2(e4, e4);
