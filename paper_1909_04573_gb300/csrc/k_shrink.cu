@@ -192,6 +192,7 @@ template <> struct Vec4<__nv_bfloat16> {
 // direct sums over the last 2d+1 rows' row sums, held in registers.  No
 // row-sum array goes through shared memory.
 constexpr int SS_W = 64, SS_WARPS = 4, SS_SL = 34;  // 544 = 4 x 136: level-1 subbands of 1088-row frames
+static_assert(SS_SL % 2 == 0, "output rows come in pairs");
 constexpr int SS_H = SS_WARPS * SS_SL;
 constexpr int SS_XS = SS_W + 2 * SH;  // 72 staged columns (float4-aligned rows)
 
@@ -277,32 +278,38 @@ __global__ void __launch_bounds__(32 * SS_WARPS) k_shrink_strip(ShrinkArgs a) {
         R2[i] = add2(R1[i], add2(q1, q3));
         R3[i] = add2(R2[i], add2(om3, op3));
         R4[i] = add2(R3[i], add2(q0, q4));
-        if (i >= 8) {
-            const int o = i - 8, c = i - 4;  // output row of the strip, its staged row (strip-relative)
-            f2 b1s = R1[c - 1], b2s = R2[c - 2], b3s = R3[c - 3], b4s = R4[c - 4];
+        // output rows in pairs (o, o+1), o = i - 9 even: their box sums of
+        // radius d share the 2d middle row sums (direct sums of the same terms)
+        if (i >= 9 && ((i - 9) & 1) == 0) {
+            const int o = i - 9, c = i - 5;  // first output row of the pair, its staged row (strip-relative)
+            f2 m1 = R1[c], m2 = R2[c - 1], m3 = R3[c - 2], m4 = R4[c - 3];
+            m1 = add2(m1, R1[c + 1]);
 #pragma unroll
-            for (int j = 0; j < 2; ++j) b1s = add2(b1s, R1[c + j]);
+            for (int j = 0; j < 3; ++j) m2 = add2(m2, R2[c + j]);
 #pragma unroll
-            for (int j = -1; j < 3; ++j) b2s = add2(b2s, R2[c + j]);
+            for (int j = -1; j < 4; ++j) m3 = add2(m3, R3[c + j]);
 #pragma unroll
-            for (int j = -2; j < 4; ++j) b3s = add2(b3s, R3[c + j]);
+            for (int j = -2; j < 5; ++j) m4 = add2(m4, R4[c + j]);
+            const f2 b[2][4] = {{add2(R1[c - 1], m1), add2(R2[c - 2], m2), add2(R3[c - 3], m3), add2(R4[c - 4], m4)},
+                                {add2(m1, R1[c + 2]), add2(m2, R2[c + 3]), add2(m3, R3[c + 4]), add2(m4, R4[c + 5])}};
 #pragma unroll
-            for (int j = -3; j < 5; ++j) b4s = add2(b4s, R4[c + j]);
-            float m1a, m1b, m2a, m2b, m3a, m3b, m4a, m4b;
-            up2(mul2(b1s, iw1), m1a, m1b);
-            up2(mul2(b2s, iw2), m2a, m2b);
-            up2(mul2(b3s, iw3), m3a, m3b);
-            up2(mul2(b4s, iw4), m4a, m4b);
-            const float mA = fminf(fminf(m1a, m2a), fminf(m3a, m4a));
-            const float mB = fminf(fminf(m1b, m2b), fminf(m3b, m4b));
-            const int gy = ys + o;
-            if (gy < a.R && gx < a.Cc) {
-                float cA, cB;
-                up2(lds2(base + c * SS_XS + 4), cA, cB);
-                const float denA = fmaxf(0.f, mA - s2) + s2, denB = fmaxf(0.f, mB - s2) + s2;
-                T *dst = out + (long long)gy * a.Cc + gx;
-                stf<T>(dst, denA > 0.f ? __fdividef(cA * s2, denA) : 0.f);
-                stf<T>(dst + 1, denB > 0.f ? __fdividef(cB * s2, denB) : 0.f);
+            for (int h = 0; h < 2; ++h) {
+                float m1a, m1b, m2a, m2b, m3a, m3b, m4a, m4b;
+                up2(mul2(b[h][0], iw1), m1a, m1b);
+                up2(mul2(b[h][1], iw2), m2a, m2b);
+                up2(mul2(b[h][2], iw3), m3a, m3b);
+                up2(mul2(b[h][3], iw4), m4a, m4b);
+                const float mA = fminf(fminf(m1a, m2a), fminf(m3a, m4a));
+                const float mB = fminf(fminf(m1b, m2b), fminf(m3b, m4b));
+                const int gy = ys + o + h;
+                if (gy < a.R && gx < a.Cc) {
+                    float cA, cB;
+                    up2(lds2(base + (c + h) * SS_XS + 4), cA, cB);
+                    const float denA = fmaxf(0.f, mA - s2) + s2, denB = fmaxf(0.f, mB - s2) + s2;
+                    T *dst = out + (long long)gy * a.Cc + gx;
+                    stf<T>(dst, denA > 0.f ? __fdividef(cA * s2, denA) : 0.f);
+                    stf<T>(dst + 1, denB > 0.f ? __fdividef(cB * s2, denB) : 0.f);
+                }
             }
         }
     }
