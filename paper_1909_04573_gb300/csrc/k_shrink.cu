@@ -184,13 +184,15 @@ template <> struct Vec4<__nv_bfloat16> {
 };
 
 // ---------------------------------------------------------------------------
-// Standard windows {3, 5, 7, 9} on subbands whose width is a multiple of 4.  A tile of 64 columns x SS_H rows is staged once (the
-// coefficients with a 4-sample periodic halo); then each thread owns two
-// adjacent columns and walks down a strip of SS_SL rows without further
-// barriers: per staged row, five aligned pair loads give the nested row sums
-// of c^2 for radii 1..4 (as float32x2), and the box sums of each radius are
-// direct sums over the last 2d+1 rows' row sums, held in registers.  No
-// row-sum array goes through shared memory.
+// Standard windows {3, 5, 7, 9} on subbands whose width is a multiple of 4.
+// A block covers 64 columns x SS_H rows; each thread owns two adjacent
+// columns and walks down a strip of SS_SL rows of the coefficients staged
+// with a 4-sample periodic halo.  Per staged row, five aligned pair loads
+// give c at columns x-4 .. x+5, and packed float32x2 operations form c^2 and
+// the nested row sums of radii 1..4; the box sum of radius d is a direct sum
+// of the last 2d+1 rows' row sums, kept in registers, and two consecutive
+// output rows share their 2d middle terms.  No row-sum array goes through
+// shared memory.
 constexpr int SS_W = 64, SS_WARPS = 4, SS_SL = 34;  // 544 = 4 x 136: level-1 subbands of 1088-row frames
 static_assert(SS_SL % 2 == 0, "output rows come in pairs");
 constexpr int SS_H = SS_WARPS * SS_SL;
