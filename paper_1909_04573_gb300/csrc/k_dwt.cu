@@ -50,11 +50,9 @@ struct Lane {
     bool fast;                // warp-uniform: columns are 2q..2q+7 directly, float2-aligned
 };
 
-// row pass of one input row: ref, s = sum_{k>=1} h_k (v_k - v_0), t = sum g_k (v_k - v_0)
+// raw samples 2q..2q+7 of one input row (high and, above level 1, low parts)
 template <bool LEVEL1>
-__device__ __forceinline__ void row_item(const AnaArgs &a, const RowIn &row, const Lane<LEVEL1> &L, int q2,
-                                         float &rh, float &rl, float &s, float &t) {
-    float v[8], w[8];
+__device__ __forceinline__ void row_load(const RowIn &row, const Lane<LEVEL1> &L, int q2, float *v, float *w) {
     if (L.fast) {
         const float2 *ph = reinterpret_cast<const float2 *>(row.h + q2);
 #pragma unroll
@@ -79,6 +77,12 @@ __device__ __forceinline__ void row_item(const AnaArgs &a, const RowIn &row, con
             if (!LEVEL1) w[k] = __ldg(row.l + L.col[k]);
         }
     }
+}
+
+// row pass of one input row: ref, s = sum_{k>=1} h_k (v_k - v_0), t = sum g_k (v_k - v_0)
+template <bool LEVEL1>
+__device__ __forceinline__ void row_math(const AnaArgs &a, const float *v, const float *w, float &rh, float &rl,
+                                         float &s, float &t) {
     float ss = 0.f, tt = 0.f;
 #pragma unroll
     for (int k = 1; k < kTaps; ++k) {
@@ -91,6 +95,28 @@ __device__ __forceinline__ void row_item(const AnaArgs &a, const RowIn &row, con
     rl = LEVEL1 ? 0.f : w[0];
     s = ss;
     t = tt;
+}
+
+template <bool LEVEL1>
+__device__ __forceinline__ void row_item(const AnaArgs &a, const RowIn &row, const Lane<LEVEL1> &L, int q2,
+                                         float &rh, float &rl, float &s, float &t) {
+    float v[8], w[8];
+    row_load<LEVEL1>(row, L, q2, v, w);
+    row_math<LEVEL1>(a, v, w, rh, rl, s, t);
+}
+
+// Level-1 input ring: interior warps stage their 72 input columns of each
+// input row in a per-warp ring of 24 rows with cp.async, 4-row chunks issued
+// 16 rows ahead of use, so the global latency overlaps the filter arithmetic.
+constexpr int kRingRows = 24, kRingCols = 72, kChunk = 4;
+__device__ __forceinline__ void ring_cp16(float *dst, const float *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void ring_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void ring_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 template <bool LEVEL1, class T, int SP, int WARPS>
@@ -128,20 +154,72 @@ __global__ void __launch_bounds__(32 * WARPS, 24 / WARPS) k_analysis_stream(AnaA
     };
     const float scale = a.scale_on ? __frcp_rn((float)a.sc.count(plane)) : 1.f;
 
-    float rh[8], rl[8], rs[8], rt[8];
+    // ring: level 1, interior warps whose 72-column window stays inside the row
+    constexpr bool RING_OK = LEVEL1 && WARPS <= 4;
+    __shared__ __align__(16) float ring[RING_OK ? WARPS : 1][RING_OK ? kRingRows : 1][RING_OK ? kRingCols : 4];
+    const bool use_ring = RING_OK && L.fast && 2 * cq0 + kRingCols <= srcW && (srcW & 3) == 0 &&
+                          ((reinterpret_cast<uintptr_t>(a.inh) & 15u) == 0);
+    float *const rbase = &ring[RING_OK ? warp : 0][0][0];
     const int y0 = 2 * p0;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) row_item<LEVEL1>(a, row_at(y0 + k), L, 2 * q, rh[k], rl[k], rs[k], rt[k]);
-
     const int pend = min(p0 + SP, R2);
-    for (int pb = p0; pb < pend; pb += 4) {
+    const int t_last = 2 * (pend - p0) + 5;  // last strip-relative input row used
+    // chunk c holds strip rows 4c .. 4c+3 (skipped past t_last; an empty group keeps the count)
+    auto issue_chunk = [&](int c) {
+        if (RING_OK && use_ring && kChunk * c <= t_last) {
+            for (int it = lane; it < kChunk * (kRingCols / 4); it += 32) {
+                const int r = kChunk * c + it / (kRingCols / 4), j = it % (kRingCols / 4);
+                ring_cp16(rbase + (r % kRingRows) * kRingCols + 4 * j, row_at(y0 + r).h + 2 * cq0 + 4 * j);
+            }
+        }
+        ring_commit();
+    };
+    auto ring_row = [&](int t, float &rh_, float &rl_, float &rs_, float &rt_) {
+        const float2 *pr = reinterpret_cast<const float2 *>(rbase + (t % kRingRows) * kRingCols + 2 * lane);
+        float v[8], w[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 u = pr[k];
+            v[2 * k] = u.x;
+            v[2 * k + 1] = u.y;
+        }
+        row_math<LEVEL1>(a, v, w, rh_, rl_, rs_, rt_);
+    };
+
+    float rh[8], rl[8], rs[8], rt[8];
+    if (use_ring) {
+        for (int c = 0; c < 4; ++c) issue_chunk(c);  // strip rows 0..15
+        ring_wait<2>();                                 // rows 0..7 have landed
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ring_row(k, rh[k], rl[k], rs[k], rt[k]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) row_item<LEVEL1>(a, row_at(y0 + k), L, 2 * q, rh[k], rl[k], rs[k], rt[k]);
+    }
+
+    for (int pb = p0, m = 0; pb < pend; pb += 4, ++m) {
+        if (use_ring) {
+            // iteration m reads strip rows 8m+6 .. 8m+13 (chunks <= 2m+3); chunks
+            // 2m+4, 2m+5 (rows 8m+16 .. 8m+23) reuse the slots of rows 8m-8 ..
+            // 8m-1, all read before this point
+            __syncwarp();
+            issue_chunk(2 * m + 4);
+            issue_chunk(2 * m + 5);
+            ring_wait<2>();
+            __syncwarp();
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int p = pb + j;
             // input rows 2p+6, 2p+7 go to slots (2j+6) mod 8, (2j+7) mod 8
             const int s6 = (2 * j + 6) & 7, s7 = (2 * j + 7) & 7;
-            row_item<LEVEL1>(a, row_at(2 * p + 6), L, 2 * q, rh[s6], rl[s6], rs[s6], rt[s6]);
-            row_item<LEVEL1>(a, row_at(2 * p + 7), L, 2 * q, rh[s7], rl[s7], rs[s7], rt[s7]);
+            if (use_ring) {
+                ring_row(2 * (p - p0) + 6, rh[s6], rl[s6], rs[s6], rt[s6]);
+                ring_row(2 * (p - p0) + 7, rh[s7], rl[s7], rs[s7], rt[s7]);
+            } else {
+                row_item<LEVEL1>(a, row_at(2 * p + 6), L, 2 * q, rh[s6], rl[s6], rs[s6], rt[s6]);
+                row_item<LEVEL1>(a, row_at(2 * p + 7), L, 2 * q, rh[s7], rl[s7], rs[s7], rt[s7]);
+            }
             // column pass over rows 2p..2p+7 = slots 2j .. 2j+7 (mod 8)
             const int b0 = (2 * j) & 7;
             const float r0h = rh[b0], r0l = rl[b0];
@@ -182,6 +260,7 @@ __global__ void __launch_bounds__(32 * WARPS, 24 / WARPS) k_analysis_stream(AnaA
             }
         }
     }
+    if (use_ring) ring_wait<0>();  // no copy outstanding at exit
 }
 
 constexpr int TP = 16, TQ = 32;                 // output tile: TP rows x TQ cols
