@@ -1,0 +1,39 @@
+"""Host logic of bench.py's kernel report (CPU): the roofline of the kernel
+with the most device time, its arithmetic against the measured peak, the
+per-kernel table and the launch count of the library's own kernels."""
+import bench
+
+
+def _prof():
+    # name: (launches, total device ms, algorithmic bytes) over 10 steps
+    return {"sda_sum": (10, 11.0, 6.72e10), "shrink": (80, 7.3, 2.0e10), "final_mle": (10, 5.0, 1.1e10),
+            "cufft_r2c": (10, 0.3, 0.0), "not_launched": (0, 0.0, 0.0)}
+
+
+def test_roofline_of_the_kernel_with_most_device_time():
+    roof, sda_roof, kern, launches = bench.kernel_report(_prof(), 10, None, None)
+    peak, _ = bench.peaks()
+    assert roof["kernel"] == "sda_sum" and roof["bound"] == "hbm" and roof["unit"] == "GB/s"
+    per_launch_s = 11.0 / 10 / 1000.0
+    assert abs(roof["achieved"] - 6.72e9 / per_launch_s / 1e9) < 1e-6
+    assert abs(roof["frac"] - roof["achieved"] / peak) < 1e-12 and roof["peak"] == peak
+    assert roof["bytes_per_launch"] == 6.72e9 and roof["launches"] == 10
+    assert roof["traffic"] is None or roof["traffic"] > 0
+    assert sda_roof["kernel"] == "sda_sum" and abs(sda_roof["frac"] - roof["frac"]) < 1e-12
+    # library kernels only (cuFFT excluded), per step figures, kernels never launched left out
+    assert launches == 100
+    assert "not_launched" not in kern
+    assert kern["shrink"]["launches_per_step"] == 8 and abs(kern["shrink"]["ms_per_step"] - 0.73) < 1e-12
+    assert abs(sum(v["share"] for v in kern.values()) - 1.0) < 1e-12
+    assert "algorithmic_GBps" not in kern["cufft_r2c"]
+
+
+def test_forced_dominant_kernel():
+    roof, _, _, _ = bench.kernel_report(_prof(), 10, None, None, dominant="final_mle")
+    assert roof["kernel"] == "final_mle" and roof["launches"] == 10
+    assert abs(roof["achieved"] - 1.1e9 / (5.0 / 10 / 1000.0) / 1e9) < 1e-6
+
+
+def test_fallback_peak_without_measured_file(monkeypatch, tmp_path):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.peaks() == (6800.0, "fallback")
