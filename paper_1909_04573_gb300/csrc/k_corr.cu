@@ -19,10 +19,12 @@
 //
 // Each 1-D transform is a Stockham autosort FFT over the factors 8, 4, 2, 9,
 // 15, 3, 5, 7 of its length (9 and 15 as register-resident composite
-// butterflies); one pass per factor, ping-ponging between two shared buffers.  Several sequences are interleaved element by element (element j of
-// sequence g at j*G + g) and consecutive threads take consecutive sequences,
-// so every shared-memory access of a pass is conflict-free.  Twiddles are
-// computed once per call in float64 (k_twiddles) and rounded to float.
+// butterflies); one pass per factor, ping-ponging between two shared
+// buffers.  Several sequences are interleaved element by element and
+// consecutive threads take consecutive sequences; rows of the interleaved
+// layout are padded (at<G>) so that the strided writes of the early passes
+// spread over the banks too.  Twiddles are computed once per call in float64
+// (k_twiddles) and rounded to float.
 #include <cuda_runtime.h>
 
 #include <algorithm>
