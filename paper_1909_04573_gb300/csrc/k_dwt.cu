@@ -33,9 +33,11 @@ constexpr float kSqrt2f = 1.41421356237309504880f;
 // input row y (ref, s, t) goes into a ring of the last 8 input rows held in
 // registers; every two new input rows complete one output row (rows
 // 2p..2p+7).  The ring slot of input row y is (y - 2p0) mod 8, so an unrolled
-// body of 4 output rows uses fixed slots.  Inputs come from global memory
-// through L1 (interior warps read four float2 per row and part); no shared
-// memory and no barriers.
+// body of 4 output rows uses fixed slots.  At level 1 the interior warps read
+// their input rows from a per-warp shared-memory ring that cp.async fills
+// ahead of use (below); the mirrored edge warps, and levels above 1, read
+// global memory through L1 (four float2 per row where aligned).  No block
+// barriers: each warp synchronises only with itself.
 // Launch shapes (output rows per strip SP, a multiple of 4, and warps per
 // block side by side in q) are template parameters; prnu_autotune picks one
 // per geometry among kStreamShapes.
