@@ -73,6 +73,25 @@ def test_wiener_dft_keeps_white_noise_and_removes_a_periodic_pattern():
     assert residual_pattern < 0.05
 
 
+def test_wiener_dft_exact_properties():
+    """A constant plane has zero noise variance, so nothing passes; the
+    filter is homogeneous of degree 1 (magnitudes and the noise variance
+    scale together: a sigma used where sigma^2 belongs breaks this); and it
+    keeps the phase of every bin it lets through."""
+    np.testing.assert_allclose(O.wiener_dft(np.full((16, 24), 3.7)), 0.0, atol=1e-12)
+    rng = np.random.default_rng(11)
+    K = rng.normal(0, 1, size=(32, 48)) + 2.0 * np.cos(2 * np.pi * 5 * np.arange(48) / 48)[None]
+    out = O.wiener_dft(K)
+    np.testing.assert_allclose(O.wiener_dft(7.3 * K), 7.3 * out, rtol=1e-10, atol=1e-12)
+    Fi, Fo = np.fft.fft2(K), np.fft.fft2(out)
+    keep = np.abs(Fo) > 1e-9 * np.abs(Fo).max()
+    assert keep.sum() > K.size // 2
+    # same direction in the complex plane: Fo / Fi is real and non-negative where kept
+    ratio = Fo[keep] / Fi[keep]
+    np.testing.assert_allclose(ratio.imag, 0.0, atol=1e-9)
+    assert (ratio.real > 0).all() and (ratio.real <= 1 + 1e-12).all()
+
+
 def _brute_correlation(X, Y):
     H, W = X.shape
     C = np.zeros((H, W))
