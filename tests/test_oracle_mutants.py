@@ -1,0 +1,75 @@
+"""The oracle's pins catch plausible mistakes.  Each mutant below plants one
+error in a copy of the oracle's C core (a wrong sign, index, radius,
+reduction, constant or dropped term); the copy is built with gcc and the pin
+files tests/test_oracle_{wavelet,denoise,sda_mle_pce}.py run against it in a
+subprocess: at least one pin must fail.  The unmutated copy, run the same way,
+must pass (so a broken harness cannot look like a caught mutant).  CPU only."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PIN_FILES = ["test_oracle_wavelet.py", "test_oracle_denoise.py", "test_oracle_sda_mle_pce.py"]
+
+# name, text in oracle/prnu_oracle.c (must occur exactly once), replacement
+MUTANTS = [
+    ("highpass taps not reversed", "* h[L - 1 - k];", "* h[k];"),
+    ("analysis index sign", "double v = x[wrap_index(2L * n + k, N) * xs];",
+     "double v = x[wrap_index(2L * n - k, N) * xs];"),
+    ("window radius off by one", "int w = windows[wi], rad = w / 2;", "int w = windows[wi], rad = w / 2 + 1;"),
+    ("max over windows instead of min", "if (mean < vmin) vmin = mean;",
+     "if (mean > vmin || vmin == INFINITY) vmin = mean;"),
+    ("sigma0 used for sigma0^2", "double s2 = sigma0 * sigma0;", "double s2 = sigma0;"),
+    ("noise details in the denoised image",
+     "rc = orc_idwt2_level(rec, cleanD[l][0], cleanD[l][1], cleanD[l][2], R, Cc, h, L, tmp);",
+     "rc = orc_idwt2_level(rec, noiseD[l][0], cleanD[l][1], cleanD[l][2], R, Cc, h, L, tmp);"),
+    ("mirror without edge repeat", "return i < n ? i : 2 * n - 1 - i;", "return i < n ? i : 2 * n - 2 - i;"),
+    ("MLE numerator W.W", "num[i] += Wr[i] * I[i];", "num[i] += Wr[i] * Wr[i];"),
+    ("ragged group divided by d", "out[(((long)i * C + c) * H + y) * W + x] = (double)s / (double)n;",
+     "out[(((long)i * C + c) * H + y) * W + x] = (double)s / (double)d;"),
+    ("LL4 dropped from the denoised image", "memcpy(rec, LLs[levels], n * sizeof(double));",
+     "memset(rec, 0, n * sizeof(double));"),
+    ("variance floor without sigma0^2", "double var = vmin - s2 > 0.0 ? vmin - s2 : 0.0;",
+     "double var = vmin > 0.0 ? vmin : 0.0;"),
+]
+
+
+def _run_pins(tmp_path, c_source: str) -> subprocess.CompletedProcess:
+    """Copy the oracle (with `c_source` as its C core), the pin files and
+    what they import into tmp_path, and run the pins there."""
+    (tmp_path / "tests").mkdir()
+    (tmp_path / "paper_1909_04573_gb300").mkdir()
+    shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle",
+                    ignore=shutil.ignore_patterns("*.so", "*.so.*", "__pycache__"))
+    (tmp_path / "oracle" / "prnu_oracle.c").write_text(c_source)
+    shutil.copytree(os.path.join(ROOT, "tests", "golden"), tmp_path / "tests" / "golden")
+    for f in ["conftest.py"] + PIN_FILES:
+        shutil.copy(os.path.join(ROOT, "tests", f), tmp_path / "tests" / f)
+    for f in ["__init__.py", "synth.py"]:
+        shutil.copy(os.path.join(ROOT, "paper_1909_04573_gb300", f), tmp_path / "paper_1909_04573_gb300" / f)
+    env = dict(os.environ, PYTHONPATH=str(tmp_path), PYTHONDONTWRITEBYTECODE="1")
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"] +
+                          [os.path.join("tests", f) for f in PIN_FILES],
+                          cwd=tmp_path, env=env, capture_output=True, text=True, timeout=600)
+
+
+def _source():
+    with open(os.path.join(ROOT, "oracle", "prnu_oracle.c")) as f:
+        return f.read()
+
+
+def test_unmutated_copy_passes_the_pins(tmp_path):
+    r = _run_pins(tmp_path, _source())
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_fails_a_pin(tmp_path, name, old, new):
+    src = _source()
+    assert src.count(old) == 1, f"mutation site of '{name}' not unique in prnu_oracle.c"
+    r = _run_pins(tmp_path, src.replace(old, new))
+    assert r.returncode == 1, f"'{name}' not caught (pytest exit {r.returncode}):\n" + r.stdout[-1500:]
+    assert "failed" in r.stdout
