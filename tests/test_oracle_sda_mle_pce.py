@@ -130,6 +130,20 @@ def test_pce_matches_brute_force_definition_32x32():
     assert r.peak == (0, 0)
 
 
+def test_pce_and_ncc_are_odd_in_the_query_residual():
+    # C -> -C when W_q -> -W_q: C(0) changes sign, the energy does not, so PCE
+    # and NCC change sign with the same magnitude (an anti-correlated query is
+    # a large negative PCE, not a match)
+    rng = np.random.default_rng(8)
+    K = rng.normal(0, 0.01, size=(32, 40))
+    Iq = rng.uniform(50, 200, size=(32, 40))
+    Wq = K * Iq + rng.normal(0, 0.5, size=(32, 40))
+    pos, neg = O.pce_match(K, Wq, Iq), O.pce_match(K, -Wq, Iq)
+    assert pos.pce > 60 and neg.pce < -60
+    assert abs(neg.pce + pos.pce) <= 1e-12 * abs(pos.pce)
+    assert abs(neg.ncc + pos.ncc) <= 1e-15
+
+
 def test_pce_of_white_signal_with_itself_is_about_n():
     # C(0) = |X|^2 ~ N, C(s != 0) ~ N(0, N): PCE ~ N = H W
     rng = np.random.default_rng(7)
