@@ -2,7 +2,8 @@
 error in a copy of the oracle (its C core or its Python finalize / PCE: a
 wrong sign, index, radius, reduction, constant or dropped term); the copy is
 built with gcc and the pin files tests/test_oracle_{wavelet,denoise,
-sda_mle_pce}.py run against it in a subprocess: at least one pin must fail.
+sda_mle_pce}.py (tests/test_oracle_grad.py for the adjoints of grad.py) run
+against it in a subprocess: at least one pin must fail.
 The unmutated copy, run the same way, must pass (so a broken harness cannot
 look like a caught mutant).  CPU only."""
 import os
@@ -14,6 +15,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PIN_FILES = ["test_oracle_wavelet.py", "test_oracle_denoise.py", "test_oracle_sda_mle_pce.py"]
+GRAD_PIN_FILES = ["test_oracle_grad.py"]
 
 # name, oracle file, text (must occur exactly once in it), replacement
 MUTANTS = [
@@ -51,6 +53,19 @@ MUTANTS = [
     ("zero-mean over rows only", "pipeline.py", "    K = K - K.mean(axis=0, keepdims=True)\n", ""),
     ("Wiener noise level as std", "pipeline.py", "sig2 = float(np.var(K))", "sig2 = float(np.std(K))"),
     ("Wiener magnitude not normalised", "pipeline.py", "M = np.abs(F) / np.sqrt(N)", "M = np.abs(F)"),
+    # adjoints (pinned by tests/test_oracle_grad.py).  Not listed: dropping the
+    # mean removal of the PCE adjoint, which is equivalent (the correlation of
+    # G with the zero-mean Y already has zero mean).
+    ("shrink adjoint without the argmin-window term", "grad.py", "gc = gc + 2.0 * c * _box_sum(a, w)",
+     "gc = gc + 0.0 * c * _box_sum(a, w)"),
+    ("shrink adjoint without d(s0^2)/d(s0)", "grad.py", "return gc, 2.0 * sigma0 * g_s2", "return gc, g_s2"),
+    ("MLE adjoint of den halved", "grad.py", "g_num[None] * Wr + 2.0 * g_den[None] * S",
+     "g_num[None] * Wr + g_den[None] * S"),
+    ("PCE adjoint correlates where it convolves", "grad.py",
+     "gYc = np.real(np.fft.ifft2(np.fft.fft2(X) * np.fft.fft2(G)))",
+     "gYc = np.real(np.fft.ifft2(np.conj(np.fft.fft2(X)) * np.fft.fft2(G)))"),
+    ("SDA weight adjoint from the wrong group", "grad.py", "float(np.sum(gS[j // d] * np.transpose",
+     "float(np.sum(gS[(j + 1) // d % gS.shape[0]] * np.transpose"),
 ]
 
 
@@ -64,13 +79,14 @@ def _run_pins(tmp_path, replace=None) -> subprocess.CompletedProcess:
     if replace:
         (tmp_path / "oracle" / replace[0]).write_text(replace[1])
     shutil.copytree(os.path.join(ROOT, "tests", "golden"), tmp_path / "tests" / "golden")
-    for f in ["conftest.py"] + PIN_FILES:
+    for f in ["conftest.py"] + PIN_FILES + GRAD_PIN_FILES:
         shutil.copy(os.path.join(ROOT, "tests", f), tmp_path / "tests" / f)
     for f in ["__init__.py", "synth.py"]:
         shutil.copy(os.path.join(ROOT, "paper_1909_04573_gb300", f), tmp_path / "paper_1909_04573_gb300" / f)
     env = dict(os.environ, PYTHONPATH=str(tmp_path), PYTHONDONTWRITEBYTECODE="1")
+    files = GRAD_PIN_FILES if replace and replace[0] == "grad.py" else PIN_FILES
     return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"] +
-                          [os.path.join("tests", f) for f in PIN_FILES],
+                          [os.path.join("tests", f) for f in files],
                           cwd=tmp_path, env=env, capture_output=True, text=True, timeout=600)
 
 
@@ -81,6 +97,10 @@ def _source(name):
 
 def test_unmutated_copy_passes_the_pins(tmp_path):
     r = _run_pins(tmp_path)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+    # and the adjoint pins, on an unchanged copy of grad.py
+    (tmp_path / "g").mkdir()
+    r = _run_pins(tmp_path / "g", ("grad.py", _source("grad.py")))
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
 
 
