@@ -274,8 +274,12 @@ prnu_status prnu_pce_match_images(prnu_ctx *ctx, const float *K, const float *im
 /* prnu_pce_match_images with its outputs left on the device: pce_dev[n],
  * ncc_dev[n] (nullable) and peak_dev[2n] (nullable) are device pointers,
  * written by the last kernel of the call.  Nothing synchronises, so the call
- * can be captured in a CUDA graph once the workspace and the cuFFT plans exist
- * (after one uncaptured call with the same geometry). */
+ * can be captured in a CUDA graph after one uncaptured call with the same
+ * geometry (which creates any cuFFT plan the geometry needs and sets the
+ * correlation kernels' shared-memory attributes).  Errors as
+ * prnu_pce_match_images (EINVAL for NULL pointers, n < 1 or a bad nbhd,
+ * ENOSPC for a short workspace, EUNSUPPORTED for 16-bit subbands), reported
+ * before anything is launched. */
 prnu_status prnu_pce_match_images_async(prnu_ctx *ctx, const float *K, const float *img_q, int n, int H, int W,
                                         int C, const prnu_params *params, int nbhd, double *pce_dev, double *ncc_dev,
                                         int *peak_dev, void *ws, size_t ws_bytes, void *stream);
