@@ -933,7 +933,10 @@ def main():
     if not args.no_perframe:
         ms_pf = timed(lambda: step(d=1, images_per_pass=100), 2, 1)
         line["perframe"] = {"value": frames_per_step / (ms_pf / 1000.0), "unit": UNIT, "ms_per_step": ms_pf,
-                            "sda_speedup": ms_pf / ms}
+                            "sda_speedup": ms_pf / ms,
+                            "paper_context": "Sec. V-B: SDA-50 29.3x and SDA-1200 52.1x faster than denoising "
+                                             "every frame of a ~1200-frame Full HD video (1407 s), one Matlab "
+                                             "thread on a Xeon E5-2687W v2, decoding and disk reads included"}
 
     # ---- end to end through the host-buffer entry point
     if not args.no_e2e:
