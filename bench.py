@@ -198,9 +198,10 @@ def kernel_report(prof, steps, ck, dev, dominant=None):
 
 
 # ------------------------------------------------------------- CPU oracle --
-def oracle_sample(frames_host, groups: int):
+def oracle_sample(frames_host, groups: int, sums: bool = False):
     """Time the FP64 oracle on `groups` SDA groups of the workload: SDA mean,
-    per-channel residual, MLE sums.  Returns (seconds, frames, cores)."""
+    per-channel residual, MLE sums.  Returns (seconds, frames, cores), and
+    with sums=True also the oracle's (num, den) [C, H, W] float64."""
     import numpy as np
 
     import oracle as O
@@ -210,7 +211,38 @@ def oracle_sample(frames_host, groups: int):
     den = np.zeros((C, H, W))
     O.fingerprint_accumulate(frames_host[: groups * D_SDA], D_SDA, num=num, den=den)
     t = time.perf_counter() - t0
+    if sums:
+        return t, groups * D_SDA, O.threads(), num, den
     return t, groups * D_SDA, O.threads()
+
+
+# Tolerances of the FP32 path against the FP64 oracle (fingerprint relative
+# L2, residual max-abs in 0..255 units); the MLE sums take the fingerprint's.
+PARITY_TOL = {"num_rel_l2": 1e-5, "den_rel_l2": 1e-5, "K_rel_l2": 1e-5, "residual_max_abs": 1e-3}
+
+
+def headline_parity(gpu, frames_host, onum, oden):
+    """Compare the timed step's fingerprint sums with the oracle's on the same
+    frames: num, den and K = num/den (no finalize flags) as relative L2, and
+    the residual of the first SDA frame (group 0) as max-abs."""
+    import numpy as np
+
+    import oracle as O
+
+    def rel(a, b):
+        return float(np.linalg.norm(a.astype(np.float64) - b) / np.linalg.norm(b))
+
+    oK = O.fingerprint_finalize(onum, oden, 0)
+    I0 = O.sda_average(frames_host[:D_SDA], D_SDA)[0]
+    ores = O.residual(I0)
+    out = {"num_rel_l2": rel(gpu["num"], onum), "den_rel_l2": rel(gpu["den"], oden),
+           "K_rel_l2": rel(gpu["K"], oK),
+           "residual_max_abs": float(np.abs(gpu["res0"].astype(np.float64) - ores).max())}
+    out["pass"] = all(out[k] <= PARITY_TOL[k] for k in PARITY_TOL)
+    out["tolerance"] = dict(PARITY_TOL)
+    out["sample"] = (f"the timed step's num/den ({len(frames_host)} frames, SDA-{D_SDA}, all groups), K = num/den, "
+                     "and the residual of the group-0 SDA frame, against the FP64 oracle on the same uint8 frames")
+    return out
 
 
 def oracle_sample_1core(frames_host):
@@ -888,6 +920,17 @@ def main():
     pos = [p for p in pces[:N_QUERY]]
     neg = [p for p in pces[N_QUERY:]]
 
+    # the timed step's fingerprint sums, kept for the parity check against the
+    # oracle (the later forms of the step reuse num / den)
+    gpu_par = None
+    if not shard_mode and not args.no_cpu and rank == 0 and world == 1:
+        K0 = ctx.fingerprint_finalize(num, den, 0)
+        res0 = ctx.denoise_residual(ctx.sda_average(frames[:D_SDA], D_SDA)[0])
+        torch.cuda.synchronize()
+        gpu_par = {"num": num.cpu().numpy(), "den": den.cpu().numpy(), "K": K0.cpu().numpy(),
+                   "res0": res0.cpu().numpy()}
+        del K0, res0
+
     roof, sda_roof, kern, launches = kernel_report(prof, args.steps, ck, dev)
     if kern_all is not None:
         kern = kern_all
@@ -995,7 +1038,9 @@ def main():
     # ---- CPU baseline: the FP64 oracle on a bounded sample, rank 0 at N = 1
     if rank == 0 and world == 1 and not args.no_cpu:
         groups = (m_frames + D_SDA - 1) // D_SDA
-        t, n, cores = oracle_sample(frames_host, groups)
+        t, n, cores, onum, oden = oracle_sample(frames_host, groups, sums=True)
+        if gpu_par is not None:
+            line["parity"] = headline_parity(gpu_par, frames_host, onum, oden)
         t1 = oracle_sample_1core(frames_host)
         line["cpu_baseline"] = {"value": n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "value_1core": 1.0 / t1,
@@ -1011,6 +1056,9 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     del np
+    if "parity" in line and not line["parity"]["pass"]:
+        sys.exit("parity against the FP64 oracle failed at the timed configuration: " +
+                 json.dumps({k: v for k, v in line["parity"].items() if k != "sample"}))
 
 
 if __name__ == "__main__":

@@ -146,16 +146,21 @@ prnu_status prnu_denoise_residual_batch(prnu_ctx *ctx, const float *img, int n, 
  * allocation, services that fix their memory footprint at start-up -- the
  * intermediates live in a fixed 64 MiB file-scope device array of the library
  * instead of a caller workspace.  The caller still passes img and
- * residual_out (same layout and meaning as prnu_denoise_residual).  Images
- * whose intermediates exceed 64 MiB (e.g. 1920x1080 RGB; 1920x1080 grey and
- * 1280x720 RGB fit) return PRNU_ENOSPC with a message and launch nothing.
- * The first call on a device resolves the array's device address
- * (cudaGetSymbolAddress, which loads the module that holds the array): make
- * that first call before any stream capture.  Every GPU on which the array's
- * module is loaded keeps the 64 MiB until the process exits.  All calls on a
- * device share the array: calls whose GPU work may overlap (other streams or
- * threads without ordering) race and corrupt each other's results; calls
- * ordered on one stream are safe, and no clearing is needed between them. */
+ * residual_out (same layout and meaning as prnu_denoise_residual).  The
+ * arguments are validated first, exactly as prnu_denoise_residual does
+ * (EINVAL, nothing resolved or launched).  Images whose intermediates exceed
+ * 64 MiB return PRNU_ENOSPC with a message and launch nothing; the need
+ * depends on the subband type: with float32 subbands 1920x1080 grey and
+ * 1280x720 RGB fit and 1920x1080 RGB does not, with float16 / bfloat16
+ * subbands 1920x1080 RGB fits.  The first call with each context resolves the
+ * array's device address on the context's device (cudaGetSymbolAddress,
+ * which loads the module that holds the array) and keeps it in the context:
+ * make that first call before any stream capture (a context created after a
+ * device reset resolves it again).  Every GPU on which the array's module is
+ * loaded keeps the 64 MiB until the process exits.  All calls on a device
+ * share the array: calls whose GPU work may overlap (other streams or threads
+ * without ordering) race and corrupt each other's results; calls ordered on
+ * one stream are safe, and no clearing is needed between them. */
 prnu_status prnu_denoise_residual_static(prnu_ctx *ctx, const float *img, int H, int W, int C,
                                          const prnu_params *params, float *residual_out, void *stream);
 

@@ -37,6 +37,9 @@ struct prnu_ctx {
     std::vector<cudaEvent_t> pool;
     // autotuned level-1 analysis shape per (padded H, padded W, subband type)
     std::map<std::tuple<int, int, int>, int> tuned;
+    // device address of the allocation-free entry point's scratch array,
+    // resolved by that entry point's first call with this context
+    void *static_scratch = nullptr;
 };
 
 namespace prnu {

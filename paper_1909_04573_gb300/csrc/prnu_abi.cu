@@ -524,7 +524,21 @@ size_t multi_layout_bytes(int H, int W, int C, const prnu_params *p, int groups)
 // Accessors for the allocation-free entry point (prnu_static.cu).
 namespace prnu {
 int ctx_device(const prnu_ctx *ctx) { return ctx->device; }
-size_t denoise_scratch_bytes(int H, int W, int C, int levels) { return make_layout(H, W, C, levels, false).end; }
+void **ctx_static_scratch(prnu_ctx *ctx) { return &ctx->static_scratch; }
+// Validates a residual request the way prnu_denoise_residual does (NULL
+// pointers, aliasing, geometry, parameters), so that nothing is resolved or
+// launched for invalid input, and returns the bytes of intermediates it
+// needs with the requested subband storage type.
+prnu_status check_residual_request(const float *img, int H, int W, int C, const prnu_params *params,
+                                   const float *residual_out, size_t *need) {
+    if (!img || !residual_out) return fail(PRNU_EINVAL, "img/residual_out is NULL");
+    if ((const void *)img == (const void *)residual_out) return fail(PRNU_EINVAL, "img and residual_out alias");
+    prnu_status s;
+    if ((s = check_geometry(H, W, C)) != PRNU_OK) return s;
+    if ((s = check_params(params, H, W, nullptr)) != PRNU_OK) return s;
+    *need = make_layout(H, W, C, params->levels, false, params->dtype).end;
+    return PRNU_OK;
+}
 prnu_status set_last_error(prnu_status s, const char *msg) { return fail(s, "%s", msg); }
 }  // namespace prnu
 

@@ -22,26 +22,31 @@
 
 namespace prnu {
 int ctx_device(const prnu_ctx *ctx);
-size_t denoise_scratch_bytes(int H, int W, int C, int levels);
+void **ctx_static_scratch(prnu_ctx *ctx);
+prnu_status check_residual_request(const float *img, int H, int W, int C, const prnu_params *params,
+                                   const float *residual_out, size_t *need);
 prnu_status set_last_error(prnu_status s, const char *msg);
 }  // namespace prnu
 
 namespace {
 
 constexpr size_t kStaticScratchBytes = 64ull << 20;  // 64 MiB
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_scratch[kStaticScratchBytes];
 
 std::mutex g_mu;
-void *g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of g_scratch on `dev`, resolved once per device with that
-// device current.  In host code the name g_scratch is only a host-side
-// stand-in, never a device address, so kernels must receive this pointer.
-cudaError_t scratch_on(int dev, void **out) {
+// Device address of g_scratch on the context's device, resolved once per
+// context with that device current and kept in the context.  In host code the
+// name g_scratch is only a host-side stand-in, never a device address, so
+// kernels must receive this pointer.  Keeping it per context (rather than per
+// process) means a context created after a device reset resolves the address
+// of the re-loaded module instead of reusing a stale one.
+cudaError_t scratch_of(prnu_ctx *ctx, void **out) {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    void **slot = prnu::ctx_static_scratch(ctx);
+    if (!*slot) {
+        const int dev = prnu::ctx_device(ctx);
         int prev = -1;
         cudaError_t e = cudaGetDevice(&prev);
         if (e != cudaSuccess) return e;
@@ -50,9 +55,9 @@ cudaError_t scratch_on(int dev, void **out) {
         e = cudaGetSymbolAddress(&p, g_scratch);
         if (prev != dev) cudaSetDevice(prev);
         if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = p;
+        *slot = p;
     }
-    *out = g_scratch_ptr[dev];
+    *out = *slot;
     return cudaSuccess;
 }
 
@@ -61,28 +66,25 @@ cudaError_t scratch_on(int dev, void **out) {
 extern "C" prnu_status prnu_denoise_residual_static(prnu_ctx *ctx, const float *img, int H, int W, int C,
                                                     const prnu_params *params, float *residual_out, void *stream) {
     if (!ctx) return prnu::set_last_error(PRNU_EINVAL, "ctx is NULL");
-    const int dev = prnu::ctx_device(ctx);
-    if (dev < 0 || dev >= kMaxDevices) return prnu::set_last_error(PRNU_EINVAL, "device index out of range");
-    if (params && H >= 1 && W >= 1 && H <= 16384 && W <= 16384 && params->levels >= 1 &&
-        params->levels <= prnu::kMaxLevels && (C == 1 || C == 3)) {
-        const size_t need = prnu::denoise_scratch_bytes(H, W, C, params->levels);
-        if (need > kStaticScratchBytes) {
-            char msg[256];
-            snprintf(msg, sizeof msg,
-                     "prnu_denoise_residual_static: a %d x %d x %d image needs %zu bytes of scratch, more than "
-                     "the %zu-byte static scratch; use prnu_denoise_residual with a workspace",
-                     H, W, C, need, kStaticScratchBytes);
-            return prnu::set_last_error(PRNU_ENOSPC, msg);
-        }
+    // the regular entry point's checks first: invalid input resolves nothing
+    // (no module load) and launches nothing
+    size_t need = 0;
+    prnu_status s = prnu::check_residual_request(img, H, W, C, params, residual_out, &need);
+    if (s != PRNU_OK) return s;
+    if (need > kStaticScratchBytes) {
+        char msg[320];
+        snprintf(msg, sizeof msg,
+                 "prnu_denoise_residual_static: a %d x %d x %d image with %s subbands needs %zu bytes of scratch, "
+                 "more than the %zu-byte static scratch; use prnu_denoise_residual with a workspace",
+                 H, W, C, params->dtype == PRNU_DTYPE_F32 ? "float32" : "16-bit", need, kStaticScratchBytes);
+        return prnu::set_last_error(PRNU_ENOSPC, msg);
     }
     void *scratch = nullptr;
-    const cudaError_t e = scratch_on(dev, &scratch);
+    const cudaError_t e = scratch_of(ctx, &scratch);
     if (e != cudaSuccess) {
         char msg[256];
         snprintf(msg, sizeof msg, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
         return prnu::set_last_error(PRNU_ECUDA, msg);
     }
-    // all further validation (NULL pointers, geometry, parameters) is the
-    // regular entry point's; it launches nothing on invalid input
     return prnu_denoise_residual(ctx, img, H, W, C, params, residual_out, scratch, kStaticScratchBytes, stream);
 }

@@ -100,3 +100,31 @@ def test_reduced_precision_subbands(ctx, data, dtype):
     n32, d32 = _acc(ctx, fr, 25, P.default_params(), (3, 192, 256))
     K32 = ctx.fingerprint_finalize(torch.as_tensor(n32).cuda(), torch.as_tensor(d32).cuda()).cpu().numpy()
     assert _rel(K32, oK) <= 1e-5 < e_K
+
+
+# bounds on the PCE error of reduced-precision subband storage (fingerprint
+# and query residual both stored at that precision), relative to the oracle's
+# PCE; the float32 path keeps the parity tolerance of 0.1 %.
+PCE_BOUNDS = {P.PRNU_DTYPE_F32: 1e-3, P.PRNU_DTYPE_F16: 5e-3, P.PRNU_DTYPE_BF16: 3e-2}
+
+
+@pytest.mark.parametrize("dtype", [P.PRNU_DTYPE_F32, P.PRNU_DTYPE_F16, P.PRNU_DTYPE_BF16])
+def test_reduced_precision_pce(ctx, data, dtype):
+    """PCE of a same-camera query (grey fingerprint, per-channel residual of
+    the query) with every stage's subbands stored at `dtype`, against the FP64
+    oracle's PCE of the same frames."""
+    fr, onum, oden = data[0], data[1], data[2]
+    cam = synth.Camera(H=192, W=256, C=3, camera_id=50, sigma_read=3.0)
+    qh = O.sda_average(synth.frames(cam, 1, stream=1).numpy(), 1)[0]
+    oK = O.fingerprint_finalize(onum, oden, O.TO_GRAY)[0]
+    opce = O.pce_match(oK, O.to_gray(O.residual(qh)), O.to_gray(qh)).pce
+    p = P.default_params(dtype=dtype)
+    n, d = _acc(ctx, fr, 25, p, (3, 192, 256))
+    K = ctx.fingerprint_finalize(torch.as_tensor(n).cuda(), torch.as_tensor(d).cuda(), P.PRNU_TO_GRAY)
+    q = torch.as_tensor(qh.astype(np.float32)).cuda()
+    wq = ctx.denoise_residual(q, params=p)
+    pce = ctx.pce_match(K[0], wq, q)[0]
+    err = abs(pce - opce) / abs(opce)
+    print(f"dtype {dtype}: PCE {pce:.3f} vs oracle {opce:.3f}, relative error {err:.3e}")
+    assert opce > 60
+    assert err <= PCE_BOUNDS[dtype]
