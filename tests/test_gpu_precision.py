@@ -108,18 +108,27 @@ def test_reduced_precision_subbands(ctx, data, dtype):
 PCE_BOUNDS = {P.PRNU_DTYPE_F32: 1e-3, P.PRNU_DTYPE_F16: 5e-3, P.PRNU_DTYPE_BF16: 3e-2}
 
 
-@pytest.mark.parametrize("dtype", [P.PRNU_DTYPE_F32, P.PRNU_DTYPE_F16, P.PRNU_DTYPE_BF16])
-def test_reduced_precision_pce(ctx, data, dtype):
-    """PCE of a same-camera query (grey fingerprint, per-channel residual of
-    the query) with every stage's subbands stored at `dtype`, against the FP64
-    oracle's PCE of the same frames."""
-    fr, onum, oden = data[0], data[1], data[2]
-    cam = synth.Camera(H=192, W=256, C=3, camera_id=50, sigma_read=3.0)
+@pytest.fixture(scope="module")
+def pce_data():
+    # 48 RGB 320x256 frames with independent scenes, sigma_read 3, SDA groups
+    # of 8, and one same-camera query: the oracle's PCE is about 2.2e3
+    cam = synth.Camera(H=256, W=320, C=3, camera_id=50, sigma_read=3.0)
+    fr = synth.frames(cam, 48).numpy()
+    onum, oden = O.fingerprint_accumulate(fr, 8)
     qh = O.sda_average(synth.frames(cam, 1, stream=1).numpy(), 1)[0]
     oK = O.fingerprint_finalize(onum, oden, O.TO_GRAY)[0]
     opce = O.pce_match(oK, O.to_gray(O.residual(qh)), O.to_gray(qh)).pce
+    return fr, qh, opce
+
+
+@pytest.mark.parametrize("dtype", [P.PRNU_DTYPE_F32, P.PRNU_DTYPE_F16, P.PRNU_DTYPE_BF16])
+def test_reduced_precision_pce(ctx, pce_data, dtype):
+    """PCE of a same-camera query (grey fingerprint, per-channel residual of
+    the query) with every stage's subbands stored at `dtype`, against the FP64
+    oracle's PCE of the same frames."""
+    fr, qh, opce = pce_data
     p = P.default_params(dtype=dtype)
-    n, d = _acc(ctx, fr, 25, p, (3, 192, 256))
+    n, d = _acc(ctx, fr, 8, p, (3, 256, 320))
     K = ctx.fingerprint_finalize(torch.as_tensor(n).cuda(), torch.as_tensor(d).cuda(), P.PRNU_TO_GRAY)
     q = torch.as_tensor(qh.astype(np.float32)).cuda()
     wq = ctx.denoise_residual(q, params=p)
