@@ -219,6 +219,47 @@ prnu_status prnu_workspace_size_multi(prnu_ctx *ctx, const prnu_camera *cams, in
 prnu_status prnu_fingerprint_accumulate_multi(prnu_ctx *ctx, const prnu_camera *cams, int ncams,
                                               const prnu_params *params, void *ws, size_t ws_bytes, void *stream);
 
+/* The MLE sums of prnu_fingerprint_accumulate_multi (Sec. III-A over the SDA
+ * frames of Sec. III-B, many cameras of uneven frame counts, resolutions and
+ * group sizes) in ONE persistent kernel launch.  Every block of the launch
+ * claims items from a device work queue -- one tile of one stage (SDA sums,
+ * analysis of a level, shrink of a level, synthesis of a level, level-1
+ * synthesis with the MLE sums) of one SDA group -- waits until the stages the
+ * item reads have completed, runs it and counts it.  The host orders the
+ * queue so that the frame reads of one group run beside the denoising of the
+ * two groups before it.  A group's intermediates live in one of `slots`
+ * workspace slots (3..64; a slot is reused by group g + slots once group g's
+ * MLE step is done); each camera's groups are added to its num/den one at a
+ * time, in order.  Every device-side wait gives up after wait_budget_ms
+ * (0 = 2000 ms) of the GPU's global timer: the launch then records
+ * PRNU_ETIMEOUT and the failing item in the workspace and ends without
+ * completing the sums; prnu_persistent_status reports it.  uint8 frames and
+ * float32 subbands (PRNU_EUNSUPPORTED otherwise); num/den as in
+ * prnu_fingerprint_accumulate (float32 [C][H][W], or compensated pairs).
+ * Same results as prnu_fingerprint_accumulate_multi up to the order of the
+ * float32 MLE additions.  Allocates nothing and synchronises nothing (one
+ * memset, a few small copy kernels and the persistent kernel), so the call can
+ * be captured in a CUDA graph; at most 8 distinct geometries per call. */
+prnu_status prnu_workspace_size_persistent(prnu_ctx *ctx, const prnu_camera *cams, int ncams,
+                                           const prnu_params *params, int slots, size_t *bytes);
+prnu_status prnu_fingerprint_accumulate_persistent(prnu_ctx *ctx, const prnu_camera *cams, int ncams,
+                                                   const prnu_params *params, int slots, double wait_budget_ms,
+                                                   void *ws, size_t ws_bytes, void *stream);
+
+/* Status of the last persistent launch whose workspace is ws: synchronises
+ * `stream`, then returns PRNU_OK, or PRNU_ETIMEOUT when one of its bounded
+ * waits gave up; fail_info (nullable, host int[3]) receives the queue item,
+ * SDA group and stage of the first wait that gave up. */
+prnu_status prnu_persistent_status(prnu_ctx *ctx, const void *ws, size_t ws_bytes, void *stream, int *fail_info);
+
+/* Diagnostic of the bounded waits (no counterpart in the paper): launches
+ * the persistent kernel on a one-item queue whose item depends on a count
+ * that nothing reaches, so its wait gives up after wait_budget_ms (0 < ms <=
+ * 1e4) and prnu_persistent_status then returns PRNU_ETIMEOUT, with the
+ * context still usable.  ws: at least 4 KiB. */
+prnu_status prnu_persistent_wait_probe(prnu_ctx *ctx, double wait_budget_ms, void *ws, size_t ws_bytes,
+                                       void *stream);
+
 /* Fingerprint from the MLE sums, Sec. III-A: K = num/den (division in
  * float64; K = 0 where den == 0), then the optional literature steps named by
  * `flags` (not defined in the paper): PRNU_TO_GRAY, PRNU_ZERO_MEAN,

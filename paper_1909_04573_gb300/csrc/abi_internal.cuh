@@ -135,6 +135,9 @@ prnu_status check_geometry(int H, int W, int C);
 // Validates params against the geometry; fills `win` (nullable).
 prnu_status check_params(const prnu_params *p, int H, int W, Win *win);
 prnu_status check_ws(void *ws, size_t ws_bytes, size_t need);
+// Frames of an accumulate call (element size fes bytes: 1 uint8, 2 float16).
+prnu_status check_frames(const uint8_t *frames, int m, int H, int W, int C, size_t frame_stride, size_t row_pitch,
+                         int d, int fes = 1);
 
 inline int padded(int n, int levels) {
     const int m = 1 << levels;

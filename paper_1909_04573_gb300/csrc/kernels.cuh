@@ -174,4 +174,62 @@ cudaError_t launch_pce_bwd_out(const float *gYraw, const float *gXraw, const flo
 void pce_unpack(const void *p, int q, double *c0, double *energy, long long *peak_idx, double *sx, double *sxx,
                 double *sy, double *syy);
 
+// k_persist.cu -- the multi-camera pipeline as one persistent launch over a
+// device work queue of (group, stage, tile) items.
+// Stages of a group with L levels: 0 SDA sums; l = 1..L analysis of level l;
+// L + l shrink of level l; 3L + 1 - l synthesis of level l (l = L..2); 3L the
+// level-1 synthesis with the MLE sums.
+constexpr int kPMaxStages = 3 * kMaxLevels + 1;
+constexpr int kPMaxGeos = 8;
+constexpr int kPProbeStage = kPMaxStages;  // a diagnostic item that waits on a count nothing reaches
+struct PGroup {
+    const uint8_t *frames;
+    long long frame_stride, row_pitch;
+    int n;     // frames in the group
+    int cam;   // index into the camera table
+    int geo;   // index into the geometry table
+    int prev;  // the camera's previous group in this launch (its MLE sums come first), or -1
+};
+struct PCam {
+    float *num, *den;
+};
+struct PGeo {
+    int H, W, C, Hp, Wp;
+    int cnt[kPMaxStages];  // work items per stage
+    // byte offsets within a slot (the single-plane-group layout of the pipeline)
+    long long X, LLh[kMaxLevels + 1], LLl[kMaxLevels + 1], Rn[kMaxLevels + 1], D[kMaxLevels + 1],
+        N[kMaxLevels + 1];
+};
+// a run of consecutive queue items of one stage of one group: queue items
+// start .. next segment's start - 1 are that stage's items first, first + 1, ...
+struct PSeg {
+    int start, group, stage, first;
+};
+struct PHeader {
+    int next;    // queue head (claimed items)
+    int status;  // PRNU_OK, or PRNU_ETIMEOUT once a wait gave up
+    int fail_item, fail_group, fail_stage, fail_blocks;
+    int pad[2];
+};
+struct PArgs {
+    PHeader *hdr;
+    const PGroup *groups;
+    const PCam *cams;
+    const PGeo *geos;
+    const PSeg *segs;
+    int *done;  // [G][NS] completed items per (group, stage)
+    char *slots;
+    long long slot_bytes;
+    int nslots, L, NS, nseg, total, G;
+    float s2;
+    Win win;
+    Filt f;
+    long long budget_ns;  // longest wait on one dependency
+};
+// template switches: compensated MLE sums, the standard 3/5/7/9 windows
+cudaError_t launch_persist(const PArgs &a, bool comp, bool std_win, int blocks, cudaStream_t st);
+int persist_blocks_per_sm(bool comp, bool std_win);
+constexpr int kPutChunk = 24576;  // bytes per by-value copy launch
+cudaError_t launch_put_bytes(const void *src, size_t n, void *dst, cudaStream_t st);
+
 }  // namespace prnu

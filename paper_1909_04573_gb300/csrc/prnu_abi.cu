@@ -305,7 +305,7 @@ prnu_status check_ws(void *ws, size_t ws_bytes, size_t need) {
 }
 
 prnu_status check_frames(const uint8_t *frames, int m, int H, int W, int C, size_t frame_stride, size_t row_pitch,
-                         int d, int fes = 1) {
+                         int d, int fes) {
     if (!frames) return fail(PRNU_EINVAL, "frames is NULL");
     if (m < 1) return fail(PRNU_EINVAL, "m must be >= 1");
     if (d < 1 || d > m) return fail(PRNU_EINVAL, "d must be in [1, m] (d=%d, m=%d)", d, m);

@@ -29,7 +29,8 @@ EXPORTS = (
     "prnu_denoise_residual_ckpt", "prnu_denoise_residual_backward", "prnu_mle_images", "prnu_mle_images_backward",
     "prnu_workspace_size_pce_backward", "prnu_pce_backward", "prnu_workspace_size_pce_images",
     "prnu_pce_match_images", "prnu_pce_match_images_async", "prnu_pce_images_prepare",
-    "prnu_pce_images_finish_async",
+    "prnu_pce_images_finish_async", "prnu_workspace_size_persistent", "prnu_fingerprint_accumulate_persistent",
+    "prnu_persistent_status", "prnu_persistent_wait_probe",
 )
 
 
@@ -93,6 +94,12 @@ def lib() -> ctypes.CDLL:
                                          _vp],
                 "prnu_workspace_size_multi": [_vp, ctypes.POINTER(prnu_camera), _i, _pp, _i, ctypes.POINTER(_sz)],
                 "prnu_fingerprint_accumulate_multi": [_vp, ctypes.POINTER(prnu_camera), _i, _pp, _vp, _sz, _vp],
+                "prnu_workspace_size_persistent": [_vp, ctypes.POINTER(prnu_camera), _i, _pp, _i,
+                                                   ctypes.POINTER(_sz)],
+                "prnu_fingerprint_accumulate_persistent": [_vp, ctypes.POINTER(prnu_camera), _i, _pp, _i,
+                                                           ctypes.c_double, _vp, _sz, _vp],
+                "prnu_persistent_status": [_vp, _vp, _sz, _vp, ctypes.POINTER(_i)],
+                "prnu_persistent_wait_probe": [_vp, ctypes.c_double, _vp, _sz, _vp],
                 "prnu_autotune": [_vp, _i, _i, _i, _pp, _i, _vp, _sz, _vp, ctypes.POINTER(_i),
                                   ctypes.POINTER(ctypes.c_float)],
                 "prnu_autotune_set": [_vp, _i, _i, _pp, _i],
@@ -264,6 +271,32 @@ def prnu_fingerprint_accumulate_multi(ctx, cams, params, ws, ws_bytes, stream):
     arr = (prnu_camera * len(cams))(*cams)
     _check(lib().prnu_fingerprint_accumulate_multi(ctx, arr, len(cams), ctypes.byref(params), ws, ws_bytes, stream),
            ctx)
+
+
+def prnu_workspace_size_persistent(ctx, cams, params, slots=4) -> int:
+    arr = (prnu_camera * len(cams))(*cams)
+    n = _sz()
+    _check(lib().prnu_workspace_size_persistent(ctx, arr, len(cams), ctypes.byref(params), slots, ctypes.byref(n)),
+           ctx)
+    return n.value
+
+
+def prnu_fingerprint_accumulate_persistent(ctx, cams, params, slots, wait_budget_ms, ws, ws_bytes, stream):
+    arr = (prnu_camera * len(cams))(*cams)
+    _check(lib().prnu_fingerprint_accumulate_persistent(ctx, arr, len(cams), ctypes.byref(params), slots,
+                                                        float(wait_budget_ms), ws, ws_bytes, stream), ctx)
+
+
+def prnu_persistent_status(ctx, ws, ws_bytes, stream):
+    """Synchronises the stream and returns (status, (item, group, stage)) of
+    the last persistent launch in ws, without raising."""
+    info = (_i * 3)()
+    st = lib().prnu_persistent_status(ctx, ws, ws_bytes, stream, info)
+    return st, (info[0], info[1], info[2])
+
+
+def prnu_persistent_wait_probe(ctx, wait_budget_ms, ws, ws_bytes, stream):
+    _check(lib().prnu_persistent_wait_probe(ctx, float(wait_budget_ms), ws, ws_bytes, stream), ctx)
 
 
 STREAM_SHAPES = [(16, 4), (32, 4), (64, 4), (32, 2), (32, 8), (64, 2)]  # (strip rows, warps per block)
@@ -523,6 +556,20 @@ class Context:
         n = ws_bytes or prnu_workspace_size_multi(self.ctx, cams, params, groups_per_pass)
         ws = self.workspace(n)
         prnu_fingerprint_accumulate_multi(self.ctx, cams, params, ws.data_ptr(), n, self._stream())
+
+    def fingerprint_accumulate_persistent(self, items, params=None, slots=4, wait_budget_ms=2000.0, check=True):
+        """items: [(frames, d, num, den)] of several cameras (any geometries),
+        in one persistent launch; with check=True the queue status is read
+        back (synchronising) and a timed-out wait raises PrnuError."""
+        params = params or default_params()
+        cams = self.cameras(items)
+        n = prnu_workspace_size_persistent(self.ctx, cams, params, slots)
+        ws = self.workspace(n)
+        prnu_fingerprint_accumulate_persistent(self.ctx, cams, params, slots, wait_budget_ms, ws.data_ptr(), n,
+                                               self._stream())
+        if check:
+            st, info = prnu_persistent_status(self.ctx, ws.data_ptr(), n, self._stream())
+            _check(st, self.ctx)
 
     def fingerprint_finalize(self, num, den, flags: int = 0, params=None):
         params = params or default_params()
