@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--cameras", type=int, default=32, help="batch config: number of cameras")
     ap.add_argument("--chunk-gb", type=float, default=96.0, help="batch config: frame buffer per chunk (GiB)")
     ap.add_argument("--groups-per-pass", type=int, default=32, help="batch config: SDA groups per pass")
+    ap.add_argument("--batch-path", default="both", choices=["persistent", "stage", "both"],
+                    help="batch config: the persistent launch (value), the per-stage launches, or both (the "
+                         "per-stage form reported beside the persistent one)")
+    ap.add_argument("--slots", type=int, default=4, help="batch config: workspace slots of the persistent launch")
     ap.add_argument("--mode", default="weak", choices=["weak", "shard"],
                     help="weak: one camera per GPU (no exchange); shard: one camera's groups split over the GPUs, "
                          "num/den summed with one all-reduce (strong scaling)")
@@ -522,9 +526,30 @@ def batch_config(args, rank, world, local):
         torch.cuda.synchronize()
         gen_s[0] += time.perf_counter() - t0
 
-    def accumulate(ci):
-        P.prnu_fingerprint_accumulate_multi(ctx.ctx, chunk_cams[ci], prm, ws.data_ptr(), ws.numel(),
-                                            ctx._stream())
+    # the persistent path: one workspace per chunk, so that every chunk's queue
+    # status can be read back after the timed steps
+    paths = ["persistent", "stage"] if args.batch_path == "both" else [args.batch_path]
+    pws = []
+    if "persistent" in paths:
+        for cc in chunk_cams:
+            nb_ = P.prnu_workspace_size_persistent(ctx.ctx, cc, prm, args.slots)
+            pws.append(torch.empty(nb_, dtype=torch.uint8, device=dev))
+
+    def accumulate(ci, path, stream=None):
+        st = stream if stream is not None else ctx._stream()
+        if path == "persistent":
+            P.prnu_fingerprint_accumulate_persistent(ctx.ctx, chunk_cams[ci], prm, args.slots, 2000.0,
+                                                     pws[ci].data_ptr(), pws[ci].numel(), st)
+        else:
+            P.prnu_fingerprint_accumulate_multi(ctx.ctx, chunk_cams[ci], prm, ws.data_ptr(), ws.numel(), st)
+
+    def queue_status():
+        bad = []
+        for ci, w in enumerate(pws):
+            st_, info = P.prnu_persistent_status(ctx.ctx, w.data_ptr(), w.numel(), ctx._stream())
+            if st_ != P.PRNU_OK:
+                bad.append({"chunk": ci, "status": st_, "item_group_stage": info})
+        return bad
 
     pce = np.zeros((ncam, ncam))
 
@@ -536,9 +561,9 @@ def batch_config(args, rank, world, local):
         for i in range(ncam):
             pce[i] = [r[0] for r in ctx.pce_match_batch(Kc[i], wq, qimg)]
 
-    graphs = [None] * len(chunks)
+    graphs = {pth: [None] * len(chunks) for pth in paths}
 
-    def run_step(use_graphs, times):
+    def run_step(path, use_graphs, times):
         for n_, d_ in zip(nums, dens):
             n_.zero_()
             d_.zero_()
@@ -547,9 +572,9 @@ def batch_config(args, rank, world, local):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             if use_graphs:
-                graphs[ci].replay()
+                graphs[path][ci].replay()
             else:
-                accumulate(ci)
+                accumulate(ci, path)
             e1.record()
             times.append((e0, e1))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -558,40 +583,51 @@ def batch_config(args, rank, world, local):
         e1.record()
         times.append((e0, e1))
 
-    # warm-up 1 (eager, also creates the cuFFT plans), then capture one graph per chunk
-    run_step(False, [])
     side = torch.cuda.Stream()
-    for ci in range(len(chunks)):
-        g = torch.cuda.CUDAGraph()
-        side.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(side):
-            with torch.cuda.graph(g, stream=side):
-                P.prnu_fingerprint_accumulate_multi(ctx.ctx, chunk_cams[ci], prm, ws.data_ptr(), ws.numel(),
-                                                    side.cuda_stream)
-        torch.cuda.current_stream().wait_stream(side)
-        graphs[ci] = g
-    for _ in range(max(0, args.warmup - 1)):
-        run_step(True, [])
-    # per-kernel profile of one eager step (the graphs replay the same launches)
-    P.prnu_profile_reset(ctx.ctx)
-    P.prnu_profile_enable(ctx.ctx, True)
-    run_step(False, [])
-    torch.cuda.synchronize()
-    P.prnu_profile_enable(ctx.ctx, False)
-    prof = P.prnu_profile_read(ctx.ctx)
-    P.prnu_profile_reset(ctx.ctx)
-    # timed steps: graph replays; only the device time between generation gaps counts
-    gen_s[0] = 0.0
-    clocks = Clocks(local)
-    clocks.start()
-    times = []
-    for _ in range(args.steps):
-        run_step(True, times)
-    torch.cuda.synchronize()
-    ck = clocks.stop()
-    total_ms = sum(a.elapsed_time(b) for a, b in times)
-    tail_ms = sum(times[i][0].elapsed_time(times[i][1]) for i in range(len(chunks), len(times), len(chunks) + 1))
-    ms = total_ms / args.steps
+    results = {}
+    for path in paths:
+        # warm-up 1 (eager, also creates the cuFFT plans), then capture one graph per chunk
+        run_step(path, False, [])
+        for ci in range(len(chunks)):
+            g = torch.cuda.CUDAGraph()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                with torch.cuda.graph(g, stream=side):
+                    accumulate(ci, path, side.cuda_stream)
+            torch.cuda.current_stream().wait_stream(side)
+            graphs[path][ci] = g
+        for _ in range(max(0, args.warmup - 1)):
+            run_step(path, True, [])
+        # per-kernel profile of one eager step (the graphs replay the same launches)
+        P.prnu_profile_reset(ctx.ctx)
+        P.prnu_profile_enable(ctx.ctx, True)
+        run_step(path, False, [])
+        torch.cuda.synchronize()
+        P.prnu_profile_enable(ctx.ctx, False)
+        prof = P.prnu_profile_read(ctx.ctx)
+        P.prnu_profile_reset(ctx.ctx)
+        # timed steps: graph replays; only the device time between generation gaps counts
+        gen_s[0] = 0.0
+        clocks = Clocks(local)
+        clocks.start()
+        times = []
+        for _ in range(args.steps):
+            run_step(path, True, times)
+        torch.cuda.synchronize()
+        ck = clocks.stop()
+        total_ms = sum(a.elapsed_time(b) for a, b in times)
+        tail_ms = sum(times[i][0].elapsed_time(times[i][1])
+                      for i in range(len(chunks), len(times), len(chunks) + 1))
+        bad = queue_status() if path == "persistent" else []
+        results[path] = {"ms": total_ms / args.steps, "tail_ms": tail_ms / args.steps, "prof": prof, "ck": ck,
+                         "pce": pce.copy(), "queue_failures": bad, "gen_s": gen_s[0] / args.steps}
+        for gs_ in graphs[path]:
+            del gs_
+        graphs[path] = [None] * len(chunks)
+        torch.cuda.synchronize()
+    main = results[paths[0]]
+    ms, tail_ms, prof, ck = main["ms"], main["tail_ms"], main["prof"], main["ck"]
+    pce[:] = main["pce"]
     roof, sda_roof, kern, launches = kernel_report(prof, 1, ck, dev)
     hbm, _ = peaks()
     diag = np.diag(pce)
@@ -608,7 +644,7 @@ def batch_config(args, rank, world, local):
                        "groups": sum((m + d - 1) // d for _, m, d in specs), "cuda_graphs": len(chunks),
                        "pce_window": f"{Wq}x{Hq}", "parallelism": f"whole batch per GPU x {world}",
                        "l2": "inputs 453 GB > 129 MB L2 (no flush)"},
-            "tail_ms_per_step": tail_ms / args.steps, "generation_s_per_step_untimed": gen_s[0] / args.steps,
+            "path": paths[0], "tail_ms_per_step": tail_ms, "generation_s_per_step_untimed": main["gen_s"],
             "frame_GBps": total_bytes / (ms / 1000.0) / 1e9,
             "frame_frac_of_peak": total_bytes / (ms / 1000.0) / 1e9 / hbm,
             "autotune": tuned, "roofline": roof, "roofline_sda_sum": sda_roof, "gpu_launches": int(launches),
@@ -616,11 +652,53 @@ def batch_config(args, rank, world, local):
             "pce_matrix": {"diag_min": float(diag.min()), "diag_median": float(np.median(diag)),
                            "offdiag_max": float(off.max()), "offdiag_max_abs": float(np.abs(off).max()),
                            "diag_above_60": int((diag > 60).sum()), "offdiag_above_60": int((off > 60).sum())}}
+    if "persistent" in results:
+        line["queue_failures"] = results["persistent"]["queue_failures"]
+    if len(paths) == 2:
+        o = results[paths[1]]
+        line["per_stage"] = {"value": world * total_frames / (o["ms"] / 1000.0), "unit": "frames/s",
+                             "ms_per_step": o["ms"], "tail_ms_per_step": o["tail_ms"],
+                             "mode": "one launch per stage per pass (prnu_fingerprint_accumulate_multi), graph per chunk",
+                             "pce_matrix_max_rel_diff": float(np.max(np.abs(o["pce"] - main["pce"]) /
+                                                                     np.maximum(np.abs(main["pce"]), 1.0)))}
+    if "persistent" in paths and rank == 0:
+        line["parity"] = batch_parity_sample(ctx, chunks, chunk_items, specs, prm, args.slots)
     if ck:
         line["clocks"] = ck
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def batch_parity_sample(ctx, chunks, chunk_items, specs, prm, slots):
+    """Per-camera parity of the persistent launch on the first chunk: the first
+    SDA group of each of its camera parts (one part per resolution, at most
+    four), run as one persistent call into fresh sums and compared with the FP64
+    oracle on the same frames."""
+    import numpy as np
+    import torch
+
+    import oracle as O
+    O.build()
+    picked, seen = [], set()
+    for p, it in zip(chunks[0], chunk_items[0]):
+        c, _, d = specs[p.cam]
+        if (c.H, c.W) in seen or len(picked) == 4:
+            continue
+        seen.add((c.H, c.W))
+        fr = it[0][: min(d, it[0].shape[0])]
+        num = torch.zeros((c.C, c.H, c.W), device=fr.device)
+        picked.append((fr, d, num, torch.zeros_like(num)))
+    ctx.fingerprint_accumulate_persistent(picked, params=prm, slots=slots)
+    out = []
+    for fr, d, num, den in picked:
+        onum, oden = O.fingerprint_accumulate(fr.cpu().numpy(), d)
+        out.append({"geometry": f"{fr.shape[2]}x{fr.shape[1]}", "frames": int(fr.shape[0]),
+                    "num_rel_l2": float(np.linalg.norm(num.cpu().numpy() - onum) / np.linalg.norm(onum)),
+                    "den_rel_l2": float(np.linalg.norm(den.cpu().numpy() - oden) / np.linalg.norm(oden))})
+    ok = all(r["num_rel_l2"] <= 1e-5 and r["den_rel_l2"] <= 1e-5 for r in out)
+    return {"pass": ok, "tolerance": 1e-5, "cameras": out,
+            "sample": "first SDA group of one camera part per resolution in the first chunk, one persistent call"}
 
 
 # ------------------------------------------------------- differentiation --
