@@ -78,8 +78,14 @@ typedef struct {
                         [2][C][H][W] float32 (the float-float pair hi, then lo, both zero-initialised by the
                         caller), accumulated with TwoSum error terms; finalize then reads both parts */
     int sda_blocks_per_sm; /* 0 (default): the SDA group-sum kernel fills every SM; 1..32: at most that many
-                              of its 1024-thread blocks per SM, leaving room for kernels that run concurrently
-                              on other streams (e.g. prnu_pce_images_prepare) */
+                              of its blocks per SM, leaving room for kernels that run concurrently on other
+                              streams (e.g. prnu_pce_images_prepare or a pipelined accumulate's denoising) */
+    int pipeline_passes;   /* prnu_fingerprint_accumulate with device frames: 0 or 1 (default): one stream,
+                              each pass's group sums then its denoising; n >= 2: the groups are split into n
+                              passes (or more, if two pass layouts of ceil(groups/n) groups do not fit the
+                              workspace) and the group sums of pass k+1 run on the context's side stream while
+                              pass k is denoised on `stream` (two pass layouts in the workspace; the sums kernel
+                              then takes at most sda_blocks_per_sm blocks per SM, 6 when that is 0) */
 } prnu_params;
 
 typedef struct prnu_ctx prnu_ctx; /* opaque; owns no per-call buffers */

@@ -175,6 +175,7 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
 prnu_status get_plan(prnu_ctx *ctx, int H, int W, cufftType type, int batch, cufftHandle *plan, size_t *work);
 
 constexpr int kRedBlocks = 512;
+constexpr int kPipeSdaBlocks = 6;  // SDA sums blocks per SM beside a pipelined accumulate's denoising
 
 // Workspace of finalize (one plane at a time) and of a PCE batch of n queries.
 struct FftLayout {

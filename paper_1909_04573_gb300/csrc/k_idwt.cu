@@ -237,18 +237,35 @@ __global__ void __launch_bounds__(256) k_final(FinalArgs a) {
 // MLE mode with float32 subbands: the same level-1 step as k_final with the
 // next image's coefficient tiles and image tile fetched by cp.async into a
 // second buffer while the current image is synthesised.
+//
+// Staging moves 16-byte chunks: a coefficient tile row is the 24 columns
+// n0-4 .. n0+19 (n0 = x0/2; the synthesis reads n0-3 .. n0+15), which start on
+// a 4-float boundary, and since the coefficient width Cc is a multiple of 8 a
+// periodic wrap never splits a chunk; image tile rows are 8 chunks (a ragged
+// right edge or a width that is not a multiple of 4 falls back to 4-byte
+// copies).  The column pass gives warp w the output row pairs of coefficient
+// rows 2w, 2w+1 with one coefficient column per lane (lanes 0..18), so its
+// shared-memory reads and writes are consecutive in a row; lo and hi share
+// rows of 48 floats (hi at +24), so the two output rows a warp reads in the
+// row pass sit 16 banks apart.
 
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+constexpr int AC_W = 24;   // staged coefficient columns per tile row (6 chunks)
+constexpr int AC_LH = 48;  // lo | hi row: lo at 0..18, hi at 24..42
 struct AsyncTile {
-    float c[2][4][CT][CT + 1];  // LL, LH, HL, HH coefficient tiles, double-buffered
-    float x[2][OT][OT];         // the image tile (group sums)
-    float lo[OT][CT + 1], hi[OT][CT + 1];
+    float c[2][4][CT][AC_W];  // LL, LH, HL, HH coefficient tiles, double-buffered
+    float x[2][OT][OT];       // the image tile (group sums)
+    float lh[OT][AC_LH];      // column-synthesised lo (0..18) and hi (24..42)
 };
 
 template <bool COMP>
@@ -262,27 +279,36 @@ __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
     const float *HL = static_cast<const float *>(a.HL), *HH = static_cast<const float *>(a.HH);
     const int nimg = a.G;
     auto plane_of = [&](int i) { return i * a.C + (int)blockIdx.z; };
-    const int sx = wrap_near((x0 >> 1) - 3 + tx, a.Cc);
+    // image tile: full 16-byte chunks when the tile's rows are whole chunks
+    const bool x16 = (a.W & 3) == 0 && x0 + OT <= a.W && (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0;
     auto issue = [&](int plane, int b) {
         const long long poff = (long long)plane * a.Rc * a.Cc;
-        if (tx < CT) {
-            for (int r = ty; r < CT; r += 8) {
-                const long long o = poff + (long long)wrap_near((y0 >> 1) - 3 + r, a.Rc) * a.Cc + sx;
-                if (LL)
-                    cp_async4(&s.c[b][0][r][tx], LL + o);
-                else
-                    s.c[b][0][r][tx] = 0.f;
-                cp_async4(&s.c[b][1][r][tx], LH + o);
-                cp_async4(&s.c[b][2][r][tx], HL + o);
-                cp_async4(&s.c[b][3][r][tx], HH + o);
+        // 4 subbands x CT rows x 6 chunks
+        for (int it = tid; it < 4 * CT * (AC_W / 4); it += 256) {
+            const int k = it / (CT * (AC_W / 4)), rem = it - k * (CT * (AC_W / 4));
+            const int r = rem / (AC_W / 4), j = rem - r * (AC_W / 4);
+            const float *src = k == 0 ? LL : k == 1 ? LH : k == 2 ? HL : HH;
+            float *dst = &s.c[b][k][r][4 * j];
+            if (!src) {
+                *reinterpret_cast<float4 *>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+                continue;
             }
+            const int row = wrap_near((y0 >> 1) - 3 + r, a.Rc);
+            const int col = wrap_near((x0 >> 1) - 4 + 4 * j, a.Cc);
+            cp_async16(dst, src + poff + (long long)row * a.Cc + col);
         }
+        const float *xp = a.X + (long long)plane * hw;
+        if (x16) {
+            const int y = tid >> 3, j = tid & 7;  // 32 rows x 8 chunks
+            if (y0 + y < a.H) cp_async16(&s.x[b][y][4 * j], xp + (long long)(y0 + y) * a.W + x0 + 4 * j);
+        } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int it = tid + 256 * k;
-            const int y = it >> 5, xx = it & 31;
-            const int gy = y0 + y, gx = x0 + xx;
-            if (gy < a.H && gx < a.W) cp_async4(&s.x[b][y][xx], a.X + (long long)plane * hw + (long long)gy * a.W + gx);
+            for (int k = 0; k < 4; ++k) {
+                const int it = tid + 256 * k;
+                const int y = it >> 5, xx = it & 31;
+                const int gy = y0 + y, gx = x0 + xx;
+                if (gy < a.H && gx < a.W) cp_async4(&s.x[b][y][xx], xp + (long long)gy * a.W + gx);
+            }
         }
     };
     float an[4], ad[4], anl[4], adl[4];
@@ -295,7 +321,7 @@ __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
         const int b = i & 1;
         const int plane = plane_of(i);
         cp_wait_all();
-        __syncthreads();  // image i landed; every reader of the other buffer and of lo/hi is done
+        __syncthreads();  // image i landed; every reader of the other buffer and of lh is done
         if (i + 1 < nimg) issue(plane_of(i + 1), b ^ 1);
         cp_commit();
         if (a.gd && a.gd[i].cam != cam) {  // block-uniform: the camera changes
@@ -304,27 +330,30 @@ __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
             for (int k = 0; k < 4; ++k) { an[k] = 0.f; ad[k] = 0.f; anl[k] = 0.f; adl[k] = 0.f; }
             cam = a.gd[i].cam;
         }
-        // column synthesis from buffer b
-        for (int it = tid; it < NPAIR * CT; it += 256) {
-            const int m = it / CT, c = it - m * CT;
-            float q[4][4];
+        // column synthesis from buffer b: warp ty, coefficient rows m = 2ty, 2ty+1, column tx
+        if (tx < CT) {
 #pragma unroll
-            for (int t = 0; t < 4; ++t)
+            for (int mm = 0; mm < 2; ++mm) {
+                const int m = 2 * ty + mm;
+                float q[4][4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) q[k][t] = s.c[b][k][m + 3 - t][c];
+                for (int t = 0; t < 4; ++t)
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                float lo = 0.f, hi = 0.f;
+                    for (int k = 0; k < 4; ++k) q[k][t] = s.c[b][k][m + 3 - t][tx + 1];
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const float hk = a.f.h[e + 2 * t], gk = a.f.g[e + 2 * t];
-                    lo = __fmaf_rn(hk, q[0][t], lo);
-                    lo = __fmaf_rn(gk, q[1][t], lo);
-                    hi = __fmaf_rn(hk, q[2][t], hi);
-                    hi = __fmaf_rn(gk, q[3][t], hi);
+                for (int e = 0; e < 2; ++e) {
+                    float lo = 0.f, hi = 0.f;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const float hk = a.f.h[e + 2 * t], gk = a.f.g[e + 2 * t];
+                        lo = __fmaf_rn(hk, q[0][t], lo);
+                        lo = __fmaf_rn(gk, q[1][t], lo);
+                        hi = __fmaf_rn(hk, q[2][t], hi);
+                        hi = __fmaf_rn(gk, q[3][t], hi);
+                    }
+                    s.lh[2 * m + e][tx] = lo;
+                    s.lh[2 * m + e][AC_W + tx] = hi;
                 }
-                s.lo[2 * m + e][c] = lo;
-                s.hi[2 * m + e][c] = hi;
             }
         }
         __syncthreads();
@@ -339,8 +368,8 @@ __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
             float l[4], h[4];
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-                l[t] = s.lo[y][n + 3 - t];
-                h[t] = s.hi[y][n + 3 - t];
+                l[t] = s.lh[y][n + 3 - t];
+                h[t] = s.lh[y][AC_W + n + 3 - t];
             }
             float w[2];
 #pragma unroll
@@ -353,8 +382,9 @@ __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
                 }
                 w[e] = v;
             }
-            const float I0 = s.x[b][y][2 * n] * inv_n;
-            const float I1 = two ? s.x[b][y][2 * n + 1] * inv_n : 0.f;
+            const float2 xv = *reinterpret_cast<const float2 *>(&s.x[b][y][2 * n]);
+            const float I0 = xv.x * inv_n;
+            const float I1 = two ? xv.y * inv_n : 0.f;
             if (COMP) {
                 ff_add(an[2 * k], anl[2 * k], w[0] * I0);
                 ff_add(ad[2 * k], adl[2 * k], I0 * I0);

@@ -132,6 +132,8 @@ prnu_status check_params(const prnu_params *p, int H, int W, Win *win) {
     if (p->compensated != 0 && p->compensated != 1) return fail(PRNU_EINVAL, "compensated must be 0 or 1");
     if (p->sda_blocks_per_sm < 0 || p->sda_blocks_per_sm > 32)
         return fail(PRNU_EINVAL, "sda_blocks_per_sm must be in 0..32");
+    if (p->pipeline_passes < 0 || p->pipeline_passes > 64)
+        return fail(PRNU_EINVAL, "pipeline_passes must be in 0..64");
     if (win) {
         win->n = p->n_windows;
         for (int i = 0; i < 4; ++i) {
@@ -447,6 +449,31 @@ prnu_status accumulate_pass(prnu_ctx *ctx, const uint8_t *frames, int m, int H, 
     return denoise_pass(ctx, m, H, W, C, d, g0, G, prm, win, num, den, ws, st);
 }
 
+// Passes of Gp2 groups through two pass layouts in ws: the group sums of
+// pass k+1 run on the context's side stream (at most sda_bps blocks per SM)
+// while pass k is denoised on st; events hand each layout back and forth.
+// Under stream capture the side stream joins the capture through the events.
+prnu_status accumulate_pipelined(prnu_ctx *ctx, const uint8_t *frames, int m, int H, int W, int C, size_t fs,
+                                 size_t rp, int d, int g, int Gp2, const prnu_params &prm, const Win &win, float *num,
+                                 float *den, char *ws, int sda_bps, cudaStream_t st) {
+    prnu_status s;
+    const size_t half = align_up(make_layout(H, W, (long long)Gp2 * C, prm.levels, true, prm.dtype).end, kAlign);
+    char *wsb[2] = {ws, ws + half};
+    cudaStream_t side = ctx->copy_stream;
+    for (int b = 0; b < 2; ++b) CU(cudaEventRecord(ctx->ev_free[b], st));  // after prior work on st
+    int k = 0;
+    for (int g0 = 0; g0 < g; g0 += Gp2, ++k) {
+        const int G = std::min(Gp2, g - g0), b = k & 1;
+        CU(cudaStreamWaitEvent(side, ctx->ev_free[b], 0));
+        if ((s = sda_pass(ctx, frames, m, H, W, C, fs, rp, d, g0, G, prm, wsb[b], side, sda_bps)) != PRNU_OK) return s;
+        CU(cudaEventRecord(ctx->ev_copied[b], side));
+        CU(cudaStreamWaitEvent(st, ctx->ev_copied[b], 0));
+        if ((s = denoise_pass(ctx, m, H, W, C, d, g0, G, prm, win, num, den, wsb[b], st)) != PRNU_OK) return s;
+        CU(cudaEventRecord(ctx->ev_free[b], st));
+    }
+    return PRNU_OK;
+}
+
 // Largest number of groups per pass whose layout fits in `bytes`.
 int groups_fitting(int H, int W, int C, int L, size_t bytes, int gmax, int sdt) {
     int lo = 0, hi = gmax;
@@ -559,6 +586,7 @@ prnu_status prnu_default_params(prnu_params *p) {
     p->frame_dtype = PRNU_FRAMES_U8;
     p->compensated = 0;
     p->sda_blocks_per_sm = 0;
+    p->pipeline_passes = 0;
     return PRNU_OK;
 }
 
@@ -714,6 +742,16 @@ prnu_status prnu_fingerprint_accumulate(prnu_ctx *ctx, const uint8_t *frames, in
     if (Gp < 1) return check_ws(ws, ws_bytes, make_layout(H, W, C, params->levels, true, params->dtype).end);
     if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(PRNU_EINVAL, "workspace must be 256-byte aligned");
     DeviceGuard gd(ctx->device);
+    if (params->pipeline_passes >= 2 && g >= 2) {
+        // two pass layouts: the sums of pass k+1 on the side stream beside the denoising of pass k
+        const int want = (g + params->pipeline_passes - 1) / params->pipeline_passes;
+        const int Gp2 = groups_fitting(H, W, C, params->levels, ws_bytes / 2 / kAlign * kAlign, want, params->dtype);
+        if (Gp2 >= 1)
+            return accumulate_pipelined(ctx, frames, m, H, W, C, frame_stride, row_pitch, d, g, Gp2, *params, win, num,
+                                        den, static_cast<char *>(ws),
+                                        params->sda_blocks_per_sm > 0 ? params->sda_blocks_per_sm : kPipeSdaBlocks,
+                                        S(stream));
+    }
     for (int g0 = 0; g0 < g; g0 += Gp) {
         const int G = std::min(Gp, g - g0);
         if ((s = accumulate_pass(ctx, frames, m, H, W, C, frame_stride, row_pitch, d, g0, G, *params, win, num, den,
@@ -751,27 +789,9 @@ prnu_status prnu_fingerprint_accumulate_host(prnu_ctx *ctx, const uint8_t *host_
             // at least four passes, so that all but the last pass's denoise hides behind the reads
             const int Gp2 = groups_fitting(H, W, C, params->levels, ws_bytes / 2 / kAlign * kAlign,
                                            std::max(1, (g + 3) / 4), params->dtype);
-            if (Gp2 >= 1 && g > Gp2) {
-                const size_t half =
-                    align_up(make_layout(H, W, (long long)Gp2 * C, params->levels, true, params->dtype).end, kAlign);
-                char *wsb[2] = {static_cast<char *>(ws), static_cast<char *>(ws) + half};
-                cudaStream_t side = ctx->copy_stream;
-                for (int b = 0; b < 2; ++b) CU(cudaEventRecord(ctx->ev_free[b], st));  // after prior work on st
-                int k = 0;
-                for (int g0 = 0; g0 < g; g0 += Gp2, ++k) {
-                    const int G = std::min(Gp2, g - g0), b = k & 1;
-                    CU(cudaStreamWaitEvent(side, ctx->ev_free[b], 0));
-                    if ((s = sda_pass(ctx, dev, m, H, W, C, frame_stride, row_pitch, d, g0, G, *params, wsb[b], side,
-                                      2)) != PRNU_OK)
-                        return s;
-                    CU(cudaEventRecord(ctx->ev_copied[b], side));
-                    CU(cudaStreamWaitEvent(st, ctx->ev_copied[b], 0));
-                    if ((s = denoise_pass(ctx, m, H, W, C, d, g0, G, *params, win, num, den, wsb[b], st)) != PRNU_OK)
-                        return s;
-                    CU(cudaEventRecord(ctx->ev_free[b], st));
-                }
-                return PRNU_OK;
-            }
+            if (Gp2 >= 1 && g > Gp2)
+                return accumulate_pipelined(ctx, dev, m, H, W, C, frame_stride, row_pitch, d, g, Gp2, *params, win,
+                                            num, den, static_cast<char *>(ws), 2, st);
             const int Gp = groups_fitting(H, W, C, params->levels, ws_bytes, g, params->dtype);
             if (Gp < 1) return check_ws(ws, ws_bytes, make_layout(H, W, C, params->levels, true, params->dtype).end);
             for (int g0 = 0; g0 < g; g0 += Gp)
