@@ -235,8 +235,9 @@ __global__ void __launch_bounds__(256) k_final(FinalArgs a) {
 
 // ---------------------------------------------------------------------------
 // MLE mode with float32 subbands: the same level-1 step as k_final with the
-// next image's coefficient tiles and image tile fetched by cp.async into a
-// second buffer while the current image is synthesised.
+// coefficient tiles and image tile of the next two images fetched by cp.async
+// into two more buffers while the current image is synthesised (a tile's
+// synthesis is too short to cover one copy latency).
 //
 // Staging moves 16-byte chunks: a coefficient tile row is the 24 columns
 // n0-4 .. n0+19 (n0 = x0/2; the synthesis reads n0-3 .. n0+15), which start on
@@ -259,13 +260,15 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 constexpr int AC_W = 24;   // staged coefficient columns per tile row (6 chunks)
 constexpr int AC_LH = 48;  // lo | hi row: lo at 0..18, hi at 24..42
+constexpr int AC_BUF = 3;  // copy stages
 struct AsyncTile {
-    float c[2][4][CT][AC_W];  // LL, LH, HL, HH coefficient tiles, double-buffered
-    float x[2][OT][OT];       // the image tile (group sums)
-    float lh[OT][AC_LH];      // column-synthesised lo (0..18) and hi (24..42)
+    float c[AC_BUF][4][CT][AC_W];  // LL, LH, HL, HH coefficient tiles
+    float x[AC_BUF][OT][OT];       // the image tile (group sums)
+    float lh[OT][AC_LH];           // column-synthesised lo (0..18) and hi (24..42)
 };
 
 template <bool COMP>
@@ -317,12 +320,14 @@ __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
     int cam = a.gd ? a.gd[0].cam : -1;
     issue(plane_of(0), 0);
     cp_commit();
+    if (nimg > 1) issue(plane_of(1), 1);
+    cp_commit();  // one group per image slot, empty past the last image
     for (int i = 0; i < nimg; ++i) {
-        const int b = i & 1;
+        const int b = i % AC_BUF;
         const int plane = plane_of(i);
-        cp_wait_all();
-        __syncthreads();  // image i landed; every reader of the other buffer and of lh is done
-        if (i + 1 < nimg) issue(plane_of(i + 1), b ^ 1);
+        cp_wait_one();
+        __syncthreads();  // image i landed; every reader of image i-1's buffer and of lh is done
+        if (i + 2 < nimg) issue(plane_of(i + 2), (i + 2) % AC_BUF);
         cp_commit();
         if (a.gd && a.gd[i].cam != cam) {  // block-uniform: the camera changes
             mle_flush<COMP>(a, a.cams[cam].num, a.cams[cam].den, an, ad, anl, adl, y0, x0, tid);
@@ -402,6 +407,7 @@ __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
             }
         }
     }
+    cp_wait_all();  // no copy in flight at exit (the trailing groups are empty)
     if (a.gd)
         mle_flush<COMP>(a, a.cams[cam].num, a.cams[cam].den, an, ad, anl, adl, y0, x0, tid);
     else

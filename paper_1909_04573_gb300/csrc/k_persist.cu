@@ -492,61 +492,83 @@ struct Dep {
     int group, stage, target;
 };
 
-// The stages item (g, s) waits for; returns how many (at most three).
-__device__ int deps_of(const PArgs &a, int g, int s, Dep *d) {
+// The stages item (g, s) waits for (every item of each); returns how many
+// (at most three).  Unused entries are set to a count that is always reached.
+__device__ __forceinline__ int deps_of(const PArgs &a, int g, int s, Dep &d0, Dep &d1, Dep &d2) {
     const int L = a.L;
-    int n = 0;
-    auto full = [&](int dg, int ds) {
-        d[n++] = Dep{dg, ds, a.geos[a.groups[dg].geo].cnt[ds]};
-    };
+    auto full = [&](int dg, int ds) { return Dep{dg, ds, a.geos[a.groups[dg].geo].cnt[ds]}; };
+    d0 = d1 = d2 = Dep{g, 0, 0};
     if (s == kPProbeStage) {  // diagnostic: a count nothing reaches
-        d[n++] = Dep{g, 0, 0x7fffffff};
-    } else if (s == 0) {
-        if (g >= a.nslots) full(g - a.nslots, 3 * L);
-    } else if (s <= L) {
-        full(g, s - 1);
-    } else if (s <= 2 * L) {
-        full(g, s - L);
-    } else if (s < 3 * L) {
+        d0 = Dep{g, 0, 0x7fffffff};
+        return 1;
+    }
+    if (s == 0) {
+        if (g < a.nslots) return 0;
+        d0 = full(g - a.nslots, 3 * L);
+        return 1;
+    }
+    if (s <= L) {
+        d0 = full(g, s - 1);
+        return 1;
+    }
+    if (s <= 2 * L) {
+        d0 = full(g, s - L);
+        return 1;
+    }
+    if (s < 3 * L) {
         const int l = 3 * L + 1 - s;
-        full(g, L + l);
-        if (l < L) full(g, s - 1);
-    } else {
-        full(g, L + 1);
-        if (L >= 2) full(g, 3 * L - 1);
-        if (a.groups[g].prev >= 0) full(a.groups[g].prev, 3 * L);
+        d0 = full(g, L + l);
+        if (l < L) {
+            d1 = full(g, s - 1);
+            return 2;
+        }
+        return 1;
+    }
+    d0 = full(g, L + 1);
+    int n = 1;
+    if (L >= 2) {
+        d1 = full(g, 3 * L - 1);
+        n = 2;
+    }
+    if (a.groups[g].prev >= 0) {
+        if (n == 1)
+            d1 = full(a.groups[g].prev, 3 * L);
+        else
+            d2 = full(a.groups[g].prev, 3 * L);
+        ++n;
     }
     return n;
 }
 
-// Thread 0 of a block: wait until every dependency of the item has completed
-// (acquire), giving up after budget_ns; returns false when the launch has
-// failed (here or in another block).
-__device__ bool wait_deps(const PArgs &a, int item, int g, int s) {
-    Dep d[3];
-    const int n = deps_of(a, g, s, d);
-    for (int i = 0; i < n; ++i) {
-        const int *cnt = a.done + (long long)d[i].group * a.NS + d[i].stage;
-        if (ld_acquire(cnt) >= d[i].target) continue;
-        const unsigned long long t0 = gtimer();
-        for (;;) {
-            __nanosleep(200);
-            if (ld_acquire(cnt) >= d[i].target) break;
-            if (ld_relaxed(&a.hdr->status) != 0) return false;
-            if (gtimer() - t0 > (unsigned long long)a.budget_ns) {
-                if (atomicCAS(&a.hdr->status, 0, (int)PRNU_ETIMEOUT) == 0) {
-                    a.hdr->fail_item = item;
-                    a.hdr->fail_group = g;
-                    a.hdr->fail_stage = s;
-                }
-                atomicAdd(&a.hdr->fail_blocks, 1);
-                return false;
+// Thread 0 of a block: wait until the completion count of d reaches its
+// target (acquire), giving up after budget_ns; returns false when the launch
+// has failed (here or in another block).
+__device__ bool wait_dep(const PArgs &a, const Dep &d, int item, int g, int s) {
+    const int *cnt = a.done + (long long)d.group * a.NS + d.stage;
+    if (ld_acquire(cnt) >= d.target) return true;
+    const unsigned long long t0 = gtimer();
+    for (;;) {
+        __nanosleep(200);
+        if (ld_acquire(cnt) >= d.target) return true;
+        if (ld_relaxed(&a.hdr->status) != 0) return false;
+        if (gtimer() - t0 > (unsigned long long)a.budget_ns) {
+            if (atomicCAS(&a.hdr->status, 0, (int)PRNU_ETIMEOUT) == 0) {
+                a.hdr->fail_item = item;
+                a.hdr->fail_group = g;
+                a.hdr->fail_stage = s;
             }
+            atomicAdd(&a.hdr->fail_blocks, 1);
+            return false;
         }
     }
-    return true;
 }
 
+__device__ __forceinline__ bool same_or_weaker(const Dep &d, const Dep &seen) {
+    return d.group == seen.group && d.stage == seen.stage && d.target <= seen.target;
+}
+
+// One queue item: tiles t*k .. t*k + k - 1 (those that exist) of stage s of
+// group g, with k the stage's tiles per item.
 template <bool COMP, bool STD>
 __device__ void run_item(const PArgs &a, int g, int s, int t, PSmem &sm, int tid) {
     const PGroup &grp = a.groups[g];
@@ -556,95 +578,128 @@ __device__ void run_item(const PArgs &a, int g, int s, int t, PSmem &sm, int tid
     auto F = [&](long long off) { return reinterpret_cast<float *>(slot + off); };
     const float scale = __frcp_rn((float)grp.n);
     if (s == 0) {
-        if (C == 3) {
-            const int nseg = (W + 1023) / 1024;
-            st_sda<3, 1024>(grp, H, W, F(ge.X), t / nseg, t % nseg, sm.sda, tid);
-        } else {
-            const int nseg = (W + 4095) / 4096;
-            st_sda<1, 4096>(grp, H, W, F(ge.X), t / nseg, t % nseg, sm.sda, tid);
+        const int nseg = C == 3 ? (W + 1023) / 1024 : (W + 4095) / 4096;
+        const int n = H * nseg;
+        for (int u = t * kPTilesSda; u < min(n, (t + 1) * kPTilesSda); ++u) {
+            if (u != t * kPTilesSda) __syncthreads();
+            if (C == 3)
+                st_sda<3, 1024>(grp, H, W, F(ge.X), u / nseg, u % nseg, sm.sda, tid);
+            else
+                st_sda<1, 4096>(grp, H, W, F(ge.X), u / nseg, u % nseg, sm.sda, tid);
         }
     } else if (s <= L) {
         const int l = s;
         const int R = Hp >> (l - 1), Cc = Wp >> (l - 1);
         const int R2 = R >> 1, C2 = Cc >> 1;
         const int tq = (C2 + ATQ - 1) / ATQ, tp = (R2 + ATP - 1) / ATP;
-        const int plane = t / (tp * tq), r = t % (tp * tq);
-        const int p0 = (r / tq) * ATP, q0 = (r % tq) * ATQ;
+        const int n = C * tp * tq;
         const long long A = (long long)R2 * C2;
-        float *LLh = l < L ? F(ge.LLh[l]) + plane * A : nullptr;
-        float *LLl = l < L ? F(ge.LLl[l]) + plane * A : nullptr;
-        float *D = F(ge.D[l]);
-        float *LH = D + plane * A, *HL = D + (C + plane) * A, *HH = D + (2 * C + plane) * A;
-        if (l == 1)
-            st_analysis<true>(F(ge.X) + (long long)plane * H * W, nullptr, R, Cc, H, W, LLh, LLl, LH, HL, HH, scale,
-                              a.f, p0, q0, sm.ana);
-        else
-            st_analysis<false>(F(ge.LLh[l - 1]) + plane * (long long)R * Cc, F(ge.LLl[l - 1]) + plane * (long long)R * Cc,
-                               R, Cc, H, W, LLh, LLl, LH, HL, HH, scale, a.f, p0, q0, sm.ana);
+        for (int u = t * kPTilesAna; u < min(n, (t + 1) * kPTilesAna); ++u) {
+            if (u != t * kPTilesAna) __syncthreads();
+            const int plane = u / (tp * tq), r = u % (tp * tq);
+            const int p0 = (r / tq) * ATP, q0 = (r % tq) * ATQ;
+            float *LLh = l < L ? F(ge.LLh[l]) + plane * A : nullptr;
+            float *LLl = l < L ? F(ge.LLl[l]) + plane * A : nullptr;
+            float *D = F(ge.D[l]);
+            float *LH = D + plane * A, *HL = D + (C + plane) * A, *HH = D + (2 * C + plane) * A;
+            if (l == 1)
+                st_analysis<true>(F(ge.X) + (long long)plane * H * W, nullptr, R, Cc, H, W, LLh, LLl, LH, HL, HH,
+                                  scale, a.f, p0, q0, sm.ana);
+            else
+                st_analysis<false>(F(ge.LLh[l - 1]) + plane * (long long)R * Cc,
+                                   F(ge.LLl[l - 1]) + plane * (long long)R * Cc, R, Cc, H, W, LLh, LLl, LH, HL, HH,
+                                   scale, a.f, p0, q0, sm.ana);
+        }
     } else if (s <= 2 * L) {
         const int l = s - L;
         const int R = Hp >> l, Cc = Wp >> l;
         const int tq = (Cc + PST - 1) / PST, tp = (R + PST - 1) / PST;
-        const int plane = t / (tp * tq), r = t % (tp * tq);
+        const int n = 3 * C * tp * tq;
         const long long A = (long long)R * Cc;
-        st_shrink<STD>(F(ge.D[l]) + plane * A, F(ge.N[l]) + plane * A, R, Cc, (r / tq) * PST, (r % tq) * PST, a.s2,
-                       a.win, sm.shr, tid);
+        for (int u = t * kPTilesShr; u < min(n, (t + 1) * kPTilesShr); ++u) {
+            if (u != t * kPTilesShr) __syncthreads();
+            const int plane = u / (tp * tq), r = u % (tp * tq);
+            st_shrink<STD>(F(ge.D[l]) + plane * A, F(ge.N[l]) + plane * A, R, Cc, (r / tq) * PST, (r % tq) * PST,
+                           a.s2, a.win, sm.shr, tid);
+        }
     } else if (s < 3 * L) {
         const int l = 3 * L + 1 - s;
         const int Rc = Hp >> l, Cc = Wp >> l;
         const int Ro = 2 * Rc, Co = 2 * Cc;
         const int tq = (Co + POT - 1) / POT, tp = (Ro + POT - 1) / POT;
-        const int plane = t / (tp * tq), r = t % (tp * tq);
+        const int n = C * tp * tq;
         const long long A = (long long)Rc * Cc;
         const float *N = F(ge.N[l]);
-        st_synthesis(l < L ? F(ge.Rn[l]) + plane * A : nullptr, N + plane * A, N + (C + plane) * A,
-                     N + (2 * C + plane) * A, Rc, Cc, F(ge.Rn[l - 1]) + plane * (long long)Ro * Co, (r / tq) * POT,
-                     (r % tq) * POT, a.f, sm.syn, tid);
+        for (int u = t * kPTilesSyn; u < min(n, (t + 1) * kPTilesSyn); ++u) {
+            if (u != t * kPTilesSyn) __syncthreads();
+            const int plane = u / (tp * tq), r = u % (tp * tq);
+            st_synthesis(l < L ? F(ge.Rn[l]) + plane * A : nullptr, N + plane * A, N + (C + plane) * A,
+                         N + (2 * C + plane) * A, Rc, Cc, F(ge.Rn[l - 1]) + plane * (long long)Ro * Co,
+                         (r / tq) * POT, (r % tq) * POT, a.f, sm.syn, tid);
+        }
     } else {
         const int Rc = Hp >> 1, Cc = Wp >> 1;
         const int tq = (W + POT - 1) / POT, tp = (H + POT - 1) / POT;
-        const int c = t / (tp * tq), r = t % (tp * tq);
+        const int n = C * tp * tq;
         const long long A = (long long)Rc * Cc, hw = (long long)H * W;
         const float *N = F(ge.N[1]);
         const PCam &cam = a.cams[grp.cam];
-        st_final<COMP>(L >= 2 ? F(ge.Rn[1]) + c * A : nullptr, N + c * A, N + (C + c) * A, N + (2 * C + c) * A, Rc,
-                       Cc, F(ge.X) + c * hw, H, W, scale, cam.num + c * hw, cam.den + c * hw, (long long)C * hw,
-                       (r / tq) * POT, (r % tq) * POT, a.f, sm.syn, tid);
+        for (int u = t * kPTilesFin; u < min(n, (t + 1) * kPTilesFin); ++u) {
+            if (u != t * kPTilesFin) __syncthreads();
+            const int c = u / (tp * tq), r = u % (tp * tq);
+            st_final<COMP>(L >= 2 ? F(ge.Rn[1]) + c * A : nullptr, N + c * A, N + (C + c) * A, N + (2 * C + c) * A,
+                           Rc, Cc, F(ge.X) + c * hw, H, W, scale, cam.num + c * hw, cam.den + c * hw,
+                           (long long)C * hw, (r / tq) * POT, (r % tq) * POT, a.f, sm.syn, tid);
+        }
     }
 }
 
+// Thread 0: the queue item index after `it` for this block (an atomic claim),
+// or -1 when the queue is empty or the launch has failed.
+__device__ __forceinline__ int claim(const PArgs &a) {
+    if (ld_relaxed(&a.hdr->status) != 0) return -1;
+    const int it = atomicAdd(&a.hdr->next, 1);
+    return it < a.total ? it : -1;
+}
+
+// Thread 0: the segment holding item `it`, walking forward from `seg`
+// (claims grow with time) or bisecting when the queue has moved far ahead.
+__device__ __forceinline__ int segment_of(const PArgs &a, int it, int seg) {
+    if (__ldg(&a.segs[seg].start) > it) seg = 0;
+    int steps = 0;
+    while (seg + 1 < a.nseg && __ldg(&a.segs[seg + 1].start) <= it && steps < 8) {
+        ++seg;
+        ++steps;
+    }
+    if (seg + 1 < a.nseg && __ldg(&a.segs[seg + 1].start) <= it) {
+        int lo = seg + 1, hi = a.nseg - 1;  // largest index with start <= it
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&a.segs[mid].start) <= it)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        seg = lo;
+    }
+    return seg;
+}
+
 template <bool COMP, bool STD>
-__global__ void __launch_bounds__(kThreads) k_persist(PArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) k_persist(PArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PSmem &sm = *reinterpret_cast<PSmem *>(smem_raw);
     __shared__ int s_item, s_seg, s_ok;
     const int tid = threadIdx.y * 32 + threadIdx.x;
-    int seg = 0;  // thread 0: the segment of the last claimed item
+    // thread 0: the segment of the last item, the item claimed ahead (so the
+    // claim's latency overlaps the current item), and the dependencies last
+    // found complete (counts only grow, so they stay complete)
+    int seg = 0, ahead = -2;
+    Dep seen0{-1, 0, 0}, seen1{-1, 0, 0}, seen2{-1, 0, 0};
     for (;;) {
         if (tid == 0) {
-            int it = -1;
-            if (ld_relaxed(&a.hdr->status) == 0) it = atomicAdd(&a.hdr->next, 1);
-            if (it >= a.total) it = -1;
-            if (it >= 0) {
-                // claims grow with time: walk forward from the last segment,
-                // or bisect when the queue has moved far ahead
-                int steps = 0;
-                while (seg + 1 < a.nseg && __ldg(&a.segs[seg + 1].start) <= it && steps < 8) {
-                    ++seg;
-                    ++steps;
-                }
-                if (seg + 1 < a.nseg && __ldg(&a.segs[seg + 1].start) <= it) {
-                    int lo = seg + 1, hi = a.nseg - 1;  // largest index with start <= it
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (__ldg(&a.segs[mid].start) <= it)
-                            lo = mid;
-                        else
-                            hi = mid - 1;
-                    }
-                    seg = lo;
-                }
-            }
+            const int it = ahead == -2 ? claim(a) : ahead;
+            if (it >= 0) seg = segment_of(a, it, seg);
             s_item = it;
             s_seg = seg;
         }
@@ -652,7 +707,28 @@ __global__ void __launch_bounds__(kThreads) k_persist(PArgs a) {
         const int it = s_item;
         if (it < 0) break;
         const PSeg sg = a.segs[s_seg];
-        if (tid == 0) s_ok = wait_deps(a, it, sg.group, sg.stage) ? 1 : 0;
+        if (tid == 0) {
+            Dep d0, d1, d2;
+            const int n = deps_of(a, sg.group, sg.stage, d0, d1, d2);
+            bool ok = true;
+            // entries past n are {g, 0, 0}: always complete
+            if (!same_or_weaker(d0, seen0)) {
+                ok = wait_dep(a, d0, it, sg.group, sg.stage);
+                if (ok) seen0 = d0;
+            }
+            if (ok && n > 1 && !same_or_weaker(d1, seen1)) {
+                ok = wait_dep(a, d1, it, sg.group, sg.stage);
+                if (ok) seen1 = d1;
+            }
+            if (ok && n > 2 && !same_or_weaker(d2, seen2)) {
+                ok = wait_dep(a, d2, it, sg.group, sg.stage);
+                if (ok) seen2 = d2;
+            }
+            // claim the next item before running this one (deadlock-free: a
+            // block's held item is always later in the queue than its running one)
+            ahead = ok ? claim(a) : -1;
+            s_ok = ok ? 1 : 0;
+        }
         __syncthreads();
         if (!s_ok) break;
         if (sg.stage != kPProbeStage) run_item<COMP, STD>(a, sg.group, sg.stage, sg.first + (it - sg.start), sm, tid);

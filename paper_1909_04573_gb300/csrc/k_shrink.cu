@@ -256,76 +256,61 @@ __global__ void __launch_bounds__(32 * SS_WARPS) k_shrink_strip(ShrinkArgs a) {
     const f2 iw3 = pk2(a.win.inv[2], a.win.inv[2]), iw4 = pk2(a.win.inv[3], a.win.inv[3]);
     // staged row of strip row i: wsm + i * SS_XS; lane's pairs start at column 2 lane
     const float *base = wsm + 2 * lane;
-    // Row sums of the last 10 staged rows in a register ring (strip row i in
-    // slot i % 10).  The walk is a rolled loop over periods of 10 rows whose
-    // body is unrolled, so every ring slot is a compile-time register and the
-    // code stays small (the fully unrolled strip overflowed the instruction
-    // cache).
-    constexpr int NR = SS_SL + 8;
-    f2 R1[10], R2[10], R3[10], R4[10];
-#pragma unroll 1
-    for (int k = 0; k < (NR + 9) / 10; ++k) {
+    f2 R1[SS_SL + 8], R2[SS_SL + 8], R3[SS_SL + 8], R4[SS_SL + 8];
 #pragma unroll
-        for (int j = 0; j < 10; ++j) {
-            const int i = 10 * k + j;
-            if (i >= NR) break;
-            if constexpr (WS) {  // row group i / 14 has landed (each lane waits for its copies, then the warp syncs)
-                if (i == 0) cp_async_wait<2>();
-                if (i == SR / 3) cp_async_wait<1>();
-                if (i == 2 * SR / 3) cp_async_wait<0>();
-                if (i == 0 || i == SR / 3 || i == 2 * SR / 3) __syncwarp();
-            }
-            const float *row = base + i * SS_XS;
-            const f2 e0 = lds2(row), e1 = lds2(row + 2), e2 = lds2(row + 4), e3 = lds2(row + 6), e4 = lds2(row + 8);
-            const f2 q0 = mul2(e0, e0), q1 = mul2(e1, e1), q2 = mul2(e2, e2), q3 = mul2(e3, e3), q4 = mul2(e4, e4);
-            float a0, a1, b0, b1, c0, c1, d0, d1, g0, g1;
-            up2(q0, a0, a1);
-            up2(q1, b0, b1);
-            up2(q2, c0, c1);
-            up2(q3, d0, d1);
-            up2(q4, g0, g1);
-            // columns (x, x+1): q_k = c^2 at (x-4+2k, x-3+2k); odd pairs straddle them
-            const f2 om3 = pk2(a1, b0), om1 = pk2(b1, c0), op1 = pk2(c1, d0), op3 = pk2(d1, g0);
-            R1[j] = add2(q2, add2(om1, op1));
-            R2[j] = add2(R1[j], add2(q1, q3));
-            R3[j] = add2(R2[j], add2(om3, op3));
-            R4[j] = add2(R3[j], add2(q0, q4));
-            // output rows in pairs (o, o+1), o = i - 9 even (i odd, so j odd):
-            // their box sums of radius d share the 2d middle row sums
-            if ((j & 1) && i >= 9) {
-                const int o = i - 9, c = i - 5;  // first output row of the pair, its staged row (strip-relative)
-#define RS(arr, t) arr[(j + 15 + (t)) % 10]  // the row sums of strip row c + t, t in -4..5
-                f2 m1 = RS(R1, 0), m2 = RS(R2, -1), m3 = RS(R3, -2), m4 = RS(R4, -3);
-                m1 = add2(m1, RS(R1, 1));
+    for (int i = 0; i < SS_SL + 8; ++i) {
+        if constexpr (WS) {  // row group i / 14 has landed (each lane waits for its copies, then the warp syncs)
+            if (i == 0) cp_async_wait<2>();
+            if (i == SR / 3) cp_async_wait<1>();
+            if (i == 2 * SR / 3) cp_async_wait<0>();
+            if (i == 0 || i == SR / 3 || i == 2 * SR / 3) __syncwarp();
+        }
+        const float *row = base + i * SS_XS;
+        const f2 e0 = lds2(row), e1 = lds2(row + 2), e2 = lds2(row + 4), e3 = lds2(row + 6), e4 = lds2(row + 8);
+        const f2 q0 = mul2(e0, e0), q1 = mul2(e1, e1), q2 = mul2(e2, e2), q3 = mul2(e3, e3), q4 = mul2(e4, e4);
+        float a0, a1, b0, b1, c0, c1, d0, d1, g0, g1;
+        up2(q0, a0, a1);
+        up2(q1, b0, b1);
+        up2(q2, c0, c1);
+        up2(q3, d0, d1);
+        up2(q4, g0, g1);
+        // columns (x, x+1): q_k = c^2 at (x-4+2k, x-3+2k); odd pairs straddle them
+        const f2 om3 = pk2(a1, b0), om1 = pk2(b1, c0), op1 = pk2(c1, d0), op3 = pk2(d1, g0);
+        R1[i] = add2(q2, add2(om1, op1));
+        R2[i] = add2(R1[i], add2(q1, q3));
+        R3[i] = add2(R2[i], add2(om3, op3));
+        R4[i] = add2(R3[i], add2(q0, q4));
+        // output rows in pairs (o, o+1), o = i - 9 even: their box sums of
+        // radius d share the 2d middle row sums (direct sums of the same terms)
+        if (i >= 9 && ((i - 9) & 1) == 0) {
+            const int o = i - 9, c = i - 5;  // first output row of the pair, its staged row (strip-relative)
+            f2 m1 = R1[c], m2 = R2[c - 1], m3 = R3[c - 2], m4 = R4[c - 3];
+            m1 = add2(m1, R1[c + 1]);
 #pragma unroll
-                for (int t = 0; t < 3; ++t) m2 = add2(m2, RS(R2, t));
+            for (int j = 0; j < 3; ++j) m2 = add2(m2, R2[c + j]);
 #pragma unroll
-                for (int t = -1; t < 4; ++t) m3 = add2(m3, RS(R3, t));
+            for (int j = -1; j < 4; ++j) m3 = add2(m3, R3[c + j]);
 #pragma unroll
-                for (int t = -2; t < 5; ++t) m4 = add2(m4, RS(R4, t));
-                const f2 b[2][4] = {{add2(RS(R1, -1), m1), add2(RS(R2, -2), m2), add2(RS(R3, -3), m3),
-                                     add2(RS(R4, -4), m4)},
-                                    {add2(m1, RS(R1, 2)), add2(m2, RS(R2, 3)), add2(m3, RS(R3, 4)),
-                                     add2(m4, RS(R4, 5))}};
-#undef RS
+            for (int j = -2; j < 5; ++j) m4 = add2(m4, R4[c + j]);
+            const f2 b[2][4] = {{add2(R1[c - 1], m1), add2(R2[c - 2], m2), add2(R3[c - 3], m3), add2(R4[c - 4], m4)},
+                                {add2(m1, R1[c + 2]), add2(m2, R2[c + 3]), add2(m3, R3[c + 4]), add2(m4, R4[c + 5])}};
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    float m1a, m1b, m2a, m2b, m3a, m3b, m4a, m4b;
-                    up2(mul2(b[h][0], iw1), m1a, m1b);
-                    up2(mul2(b[h][1], iw2), m2a, m2b);
-                    up2(mul2(b[h][2], iw3), m3a, m3b);
-                    up2(mul2(b[h][3], iw4), m4a, m4b);
-                    const float mA = fminf(fminf(m1a, m2a), fminf(m3a, m4a));
-                    const float mB = fminf(fminf(m1b, m2b), fminf(m3b, m4b));
-                    const int gy = ys + o + h;
-                    if (gy < a.R && gx < a.Cc) {
-                        float cA, cB;
-                        up2(lds2(base + (c + h) * SS_XS + 4), cA, cB);
-                        const float denA = fmaxf(0.f, mA - s2) + s2, denB = fmaxf(0.f, mB - s2) + s2;
-                        T *dst = out + (long long)gy * a.Cc + gx;
-                        stf<T>(dst, denA > 0.f ? __fdividef(cA * s2, denA) : 0.f);
-                        stf<T>(dst + 1, denB > 0.f ? __fdividef(cB * s2, denB) : 0.f);
-                    }
+            for (int h = 0; h < 2; ++h) {
+                float m1a, m1b, m2a, m2b, m3a, m3b, m4a, m4b;
+                up2(mul2(b[h][0], iw1), m1a, m1b);
+                up2(mul2(b[h][1], iw2), m2a, m2b);
+                up2(mul2(b[h][2], iw3), m3a, m3b);
+                up2(mul2(b[h][3], iw4), m4a, m4b);
+                const float mA = fminf(fminf(m1a, m2a), fminf(m3a, m4a));
+                const float mB = fminf(fminf(m1b, m2b), fminf(m3b, m4b));
+                const int gy = ys + o + h;
+                if (gy < a.R && gx < a.Cc) {
+                    float cA, cB;
+                    up2(lds2(base + (c + h) * SS_XS + 4), cA, cB);
+                    const float denA = fmaxf(0.f, mA - s2) + s2, denB = fmaxf(0.f, mB - s2) + s2;
+                    T *dst = out + (long long)gy * a.Cc + gx;
+                    stf<T>(dst, denA > 0.f ? __fdividef(cA * s2, denA) : 0.f);
+                    stf<T>(dst + 1, denB > 0.f ? __fdividef(cB * s2, denB) : 0.f);
                 }
             }
         }

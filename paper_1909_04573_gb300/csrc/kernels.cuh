@@ -182,6 +182,9 @@ void pce_unpack(const void *p, int q, double *c0, double *energy, long long *pea
 constexpr int kPMaxStages = 3 * kMaxLevels + 1;
 constexpr int kPMaxGeos = 8;
 constexpr int kPProbeStage = kPMaxStages;  // a diagnostic item that waits on a count nothing reaches
+// tiles per queue item (more work per claim, wait and count): SDA sums,
+// analysis, shrink, synthesis, level-1 synthesis + MLE
+constexpr int kPTilesSda = 1, kPTilesAna = 4, kPTilesShr = 4, kPTilesSyn = 4, kPTilesFin = 2;
 struct PGroup {
     const uint8_t *frames;
     long long frame_stride, row_pitch;

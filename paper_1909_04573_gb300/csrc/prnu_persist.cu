@@ -47,15 +47,16 @@ PGeo make_geo(int H, int W, int C, int L) {
         g.D[l] = (long long)lo.D[l];
         g.N[l] = (long long)lo.N[l];
     }
-    // items per stage; the same tilings as the device decode in k_persist.cu
-    g.cnt[0] = H * cdiv(W, sda_seg(C));
+    // items per stage: tiles (the same tilings as the device decode in
+    // k_persist.cu) grouped kPTiles* to an item
+    g.cnt[0] = cdiv((long long)H * cdiv(W, sda_seg(C)), kPTilesSda);
     for (int l = 1; l <= L; ++l) {
-        g.cnt[l] = C * cdiv(g.Hp >> l, 16) * cdiv(g.Wp >> l, 32);          // analysis: 16 x 32 outputs
-        g.cnt[L + l] = 3 * C * cdiv(g.Hp >> l, 32) * cdiv(g.Wp >> l, 32);  // shrink: 32 x 32
+        g.cnt[l] = cdiv((long long)C * cdiv(g.Hp >> l, 16) * cdiv(g.Wp >> l, 32), kPTilesAna);  // 16 x 32 outputs
+        g.cnt[L + l] = cdiv(3LL * C * cdiv(g.Hp >> l, 32) * cdiv(g.Wp >> l, 32), kPTilesShr);   // 32 x 32
     }
     for (int l = L; l >= 2; --l)
-        g.cnt[3 * L + 1 - l] = C * cdiv(g.Hp >> (l - 1), 32) * cdiv(g.Wp >> (l - 1), 32);  // synthesis
-    g.cnt[3 * L] = C * cdiv(H, 32) * cdiv(W, 32);  // level-1 synthesis + MLE
+        g.cnt[3 * L + 1 - l] = cdiv((long long)C * cdiv(g.Hp >> (l - 1), 32) * cdiv(g.Wp >> (l - 1), 32), kPTilesSyn);
+    g.cnt[3 * L] = cdiv((long long)C * cdiv(H, 32) * cdiv(W, 32), kPTilesFin);  // level-1 synthesis + MLE
     return g;
 }
 
