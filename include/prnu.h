@@ -43,7 +43,8 @@ typedef enum {
     PRNU_ENOSPC = -2,      /* workspace too small (nothing launched) */
     PRNU_ECUDA = -3,       /* CUDA runtime or cuFFT error */
     PRNU_ETIMEOUT = -4,    /* a bounded device-side wait gave up */
-    PRNU_EUNSUPPORTED = -5 /* valid but not implemented (e.g. dtype) */
+    PRNU_EUNSUPPORTED = -5, /* valid but not implemented (e.g. dtype) */
+    PRNU_EDEBUG = -6        /* debug build: a device-side index check failed */
 } prnu_status;
 
 /* Flags of prnu_fingerprint_finalize. */
@@ -436,6 +437,17 @@ prnu_status prnu_autotune(prnu_ctx *ctx, int H, int W, int C, const prnu_params 
  * padded geometry and storage type, or with shape = -1 returns it to the
  * default (32x4).  Host only; EINVAL for an index out of range. */
 prnu_status prnu_autotune_set(prnu_ctx *ctx, int H, int W, const prnu_params *params, int shape);
+
+/* Index checks (not part of the paper's method).  The debug build of the
+ * library (libprnu_debug.so, compiled with PRNU_DEBUG; same entry points)
+ * checks the global-memory indices of its kernels against the extents their
+ * arguments imply; the first failed check of each source file records the
+ * line and the index and the access is skipped (no trap).  This call
+ * synchronises the context's device, then returns PRNU_OK when no check has
+ * failed since the previous call, or PRNU_EDEBUG with "file:line index" of the
+ * first failure in *where (host buffer of where_len bytes, nullable); the
+ * records are cleared.  The release build returns PRNU_EUNSUPPORTED. */
+prnu_status prnu_debug_status(prnu_ctx *ctx, char *where, size_t where_len);
 
 /* Per-kernel profiling (not part of the paper's method).  Every kernel launch
  * is counted per kernel name.  With profiling on, each launch (and each cuFFT

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "../../include/prnu.h"
+#include "debug.cuh"
 
 namespace prnu {
 

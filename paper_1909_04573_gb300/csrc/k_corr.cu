@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(CT) k_rfft_rows(const float *__restrict__ x, f
             const float2 zk = Z[at<G>(k == M ? 0 : k, g)];
             const float2 zc = cconj(Z[at<G>(k == 0 ? 0 : M - k, g)]);
             const float2 s = cadd(zk, zc), wd = cmul(__ldg(twh + k), csub(zk, zc));
-            out[r * ldo + k] = make_float2(0.5f * (s.x + wd.y), 0.5f * (s.y - wd.x));
+            if (PRNU_DCHECK(k < ldo, k)) out[r * ldo + k] = make_float2(0.5f * (s.x + wd.y), 0.5f * (s.y - wd.x));
         }
         __syncthreads();  // cur / scr are restaged from the next iteration on
     }
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(CT) k_corr_columns(float2 *F, int n, int H, in
     for (int u = threadIdx.x; u < G * H; u += blockDim.x) {
         const int s = u % G, y = u / G, c = c0 + (s < TC ? s : s - TC);
         const float2 *src = s < TC ? FX : FY;
-        if (c < Wh)
+        if (c < Wh && PRNU_DCHECK(c < ld && q < n, c))
             cp_async8(A + at<G>(y, s), src + (long long)y * ld + c);
         else
             A[at<G>(y, s)] = make_float2(0.f, 0.f);
@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(CT) k_corr_columns(float2 *F, int n, int H, in
     const float2 *Z = fft_any<HS, TC, TC, true>(T, S, p, tw);
     for (int u = threadIdx.x; u < TC * H; u += blockDim.x) {
         const int s = u % TC, y = u / TC, c = c0 + s;
-        if (c < Wh) FX[(long long)y * ld + c] = Z[at<TC>(y, s)];
+        if (c < Wh && PRNU_DCHECK(c < ld, c)) FX[(long long)y * ld + c] = Z[at<TC>(y, s)];
     }
 }
 
@@ -546,7 +546,7 @@ __global__ void __launch_bounds__(CT) k_corr_rows(const float2 *__restrict__ Zal
         for (int g = 0; g < G; ++g) {
             const int y = y0 + g;
             for (int k = threadIdx.x; k < Wh; k += blockDim.x) {
-                if (y < H)
+                if (y < H && PRNU_DCHECK(k < ld, k))
                     cp_async8(dst + g * Wh + k, Z + (long long)y * ld + k);
                 else
                     dst[g * Wh + k] = make_float2(0.f, 0.f);

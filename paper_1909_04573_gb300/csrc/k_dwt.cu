@@ -144,11 +144,13 @@ __global__ void __launch_bounds__(32 * WARPS, 24 / WARPS) k_analysis_stream(AnaA
         for (int k = 0; k < 8; ++k) {
             const int gx = wrap_near(2 * q + k, a.Cc);
             L.col[k] = LEVEL1 ? mirror(gx, a.W) : gx;
+            if (!PRNU_DCHECK(L.col[k] >= 0 && L.col[k] < srcW, L.col[k])) L.col[k] = 0;
         }
     }
     auto row_at = [&](int y) {
         const int gy = wrap_near(y, a.R);
-        const int sy = LEVEL1 ? mirror(gy, a.H) : gy;
+        int sy = LEVEL1 ? mirror(gy, a.H) : gy;
+        if (!PRNU_DCHECK(sy >= 0 && sy < srcH, sy)) sy = 0;
         RowIn r;
         r.h = a.inh + pbase + (long long)sy * srcW;
         r.l = LEVEL1 ? nullptr : a.inl + pbase + (long long)sy * srcW;
@@ -170,6 +172,7 @@ __global__ void __launch_bounds__(32 * WARPS, 24 / WARPS) k_analysis_stream(AnaA
         if (RING_OK && use_ring && kChunk * c <= t_last) {
             for (int it = lane; it < kChunk * (kRingCols / 4); it += 32) {
                 const int r = kChunk * c + it / (kRingCols / 4), j = it % (kRingCols / 4);
+                if (!PRNU_DCHECK(2 * cq0 + 4 * j + 3 < srcW, 2 * cq0 + 4 * j)) continue;
                 ring_cp16(rbase + (r % kRingRows) * kRingCols + 4 * j, row_at(y0 + r).h + 2 * cq0 + 4 * j);
             }
         }
@@ -243,7 +246,7 @@ __global__ void __launch_bounds__(32 * WARPS, 24 / WARPS) k_analysis_stream(AnaA
                 Th = __fmaf_rn(a.f.h[k], rt[sl], Th);
                 Tg = __fmaf_rn(a.f.g[k], rt[sl], Tg);
             }
-            if (p < pend && store_q) {
+            if (p < pend && store_q && PRNU_DCHECK(p < R2 && q < C2 && plane < a.P, (long long)p * C2 + q)) {
                 const float llsmall = __fmaf_rn(kSqrt2f, A, Sh);
                 const float lh = __fmaf_rn(kSqrt2f, B, Sg);
                 const long long o = ((long long)plane * R2 + p) * C2 + q;
@@ -300,7 +303,7 @@ __global__ void __launch_bounds__(256) k_analysis(AnaArgs a) {
 #pragma unroll
         for (int k = 0; k < NCOL; ++k) {
             const int c = tx + 32 * k;
-            if (c < IC) {
+            if (c < IC && PRNU_DCHECK(sy >= 0 && sy < srcH && srcx[k] >= 0 && srcx[k] < srcW, rowoff + srcx[k])) {
                 vh[r][c] = __ldg(a.inh + rowoff + srcx[k]);
                 if (!LEVEL1) vl[r][c] = __ldg(a.inl + rowoff + srcx[k]);
             }

@@ -26,7 +26,7 @@ template <class T>
 __device__ __forceinline__ void load_coeffs(SynTile &s, const T *LL, const T *LH, const T *HL, const T *HH,
                                             long long poff, int Rc, int Cc, int y0, int x0) {
     const int tx = threadIdx.x, ty = threadIdx.y;
-    if (tx < CT) {
+    if (tx < CT && PRNU_DCHECK(wrap_near((x0 >> 1) - 3 + tx, Cc) < Cc, tx)) {
         const int sx = wrap_near((x0 >> 1) - 3 + tx, Cc);
         for (int r = ty; r < CT; r += 8) {
             const long long o = poff + (long long)wrap_near((y0 >> 1) - 3 + r, Rc) * Cc + sx;
@@ -134,7 +134,7 @@ __device__ __forceinline__ void mle_flush(const FinalArgs &a, float *num, float 
         const int gy = y0 + y, gx = x0 + 2 * n;
         if (gy >= a.H || gx >= a.W) continue;
         const long long o = (long long)blockIdx.z * hw + (long long)gy * a.W + gx;
-        const int cnt = gx + 1 < a.W ? 2 : 1;
+        const int cnt = PRNU_DCHECK((int)blockIdx.z < a.C, blockIdx.z) ? (gx + 1 < a.W ? 2 : 1) : 0;
         for (int e = 0; e < cnt; ++e) {
             const int j = 2 * k + e;
             if (COMP) {
@@ -284,26 +284,48 @@ __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
     auto plane_of = [&](int i) { return i * a.C + (int)blockIdx.z; };
     // image tile: full 16-byte chunks when the tile's rows are whole chunks
     const bool x16 = (a.W & 3) == 0 && x0 + OT <= a.W && (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0;
-    auto issue = [&](int plane, int b) {
-        const long long poff = (long long)plane * a.Rc * a.Cc;
-        // 4 subbands x CT rows x 6 chunks
-        for (int it = tid; it < 4 * CT * (AC_W / 4); it += 256) {
+    // The copies of every image have the same in-plane offsets: each thread's
+    // (at most two) coefficient chunks -- subband k, row, 4-column group -- and
+    // its image chunk are resolved once, so an image's issue is a handful of
+    // adds per copy.
+    constexpr int NCH = 4 * CT * (AC_W / 4);  // 456 coefficient chunks
+    int ck[2], coff[2], cdst[2];              // subband (-1: none), in-plane offset, float index in s.c[0]
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int it = tid + 256 * h;
+        ck[h] = -1;
+        coff[h] = 0;
+        cdst[h] = 0;
+        if (it < NCH) {
             const int k = it / (CT * (AC_W / 4)), rem = it - k * (CT * (AC_W / 4));
             const int r = rem / (AC_W / 4), j = rem - r * (AC_W / 4);
-            const float *src = k == 0 ? LL : k == 1 ? LH : k == 2 ? HL : HH;
-            float *dst = &s.c[b][k][r][4 * j];
-            if (!src) {
-                *reinterpret_cast<float4 *>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
-                continue;
-            }
             const int row = wrap_near((y0 >> 1) - 3 + r, a.Rc);
             const int col = wrap_near((x0 >> 1) - 4 + 4 * j, a.Cc);
-            cp_async16(dst, src + poff + (long long)row * a.Cc + col);
+            if (PRNU_DCHECK(row >= 0 && row < a.Rc && col >= 0 && col + 3 < a.Cc, col)) {
+                ck[h] = k;
+                coff[h] = row * a.Cc + col;
+                cdst[h] = (k * CT + r) * AC_W + 4 * j;
+            }
+        }
+    }
+    const int xy = tid >> 3, xj = tid & 7;  // x16: 32 rows x 8 chunks
+    const bool xrow = y0 + xy < a.H && PRNU_DCHECK(!x16 || x0 + 4 * xj + 3 < a.W, x0 + 4 * xj);
+    const long long xoff = (long long)(y0 + xy) * a.W + x0 + 4 * xj;
+    auto issue = [&](int plane, int b) {
+        const long long poff = (long long)plane * a.Rc * a.Cc;
+        float *cb = &s.c[b][0][0][0];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (ck[h] < 0) continue;
+            const float *src = ck[h] == 0 ? LL : ck[h] == 1 ? LH : ck[h] == 2 ? HL : HH;
+            if (src)
+                cp_async16(cb + cdst[h], src + poff + coff[h]);
+            else
+                *reinterpret_cast<float4 *>(cb + cdst[h]) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         const float *xp = a.X + (long long)plane * hw;
         if (x16) {
-            const int y = tid >> 3, j = tid & 7;  // 32 rows x 8 chunks
-            if (y0 + y < a.H) cp_async16(&s.x[b][y][4 * j], xp + (long long)(y0 + y) * a.W + x0 + 4 * j);
+            if (xrow) cp_async16(&s.x[b][xy][4 * xj], xp + xoff);
         } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -335,26 +357,29 @@ __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
             for (int k = 0; k < 4; ++k) { an[k] = 0.f; ad[k] = 0.f; anl[k] = 0.f; adl[k] = 0.f; }
             cam = a.gd[i].cam;
         }
-        // column synthesis from buffer b: warp ty, coefficient rows m = 2ty, 2ty+1, column tx
+        // column synthesis from buffer b: warp ty owns coefficient rows
+        // m = 2ty, 2ty+1 (output rows 4ty .. 4ty+3), which read tile rows
+        // 2ty .. 2ty+4 (each loaded once), lane tx one coefficient column
         if (tx < CT) {
+            float q[5][4];  // [tile row - 2ty][subband]
+#pragma unroll
+            for (int rr = 0; rr < 5; ++rr)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) q[rr][k] = s.c[b][k][2 * ty + rr][tx + 1];
 #pragma unroll
             for (int mm = 0; mm < 2; ++mm) {
                 const int m = 2 * ty + mm;
-                float q[4][4];
-#pragma unroll
-                for (int t = 0; t < 4; ++t)
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) q[k][t] = s.c[b][k][m + 3 - t][tx + 1];
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                     float lo = 0.f, hi = 0.f;
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) {
+                    for (int t = 0; t < 4; ++t) {  // coefficient row m - t is tile row m + 3 - t
                         const float hk = a.f.h[e + 2 * t], gk = a.f.g[e + 2 * t];
-                        lo = __fmaf_rn(hk, q[0][t], lo);
-                        lo = __fmaf_rn(gk, q[1][t], lo);
-                        hi = __fmaf_rn(hk, q[2][t], hi);
-                        hi = __fmaf_rn(gk, q[3][t], hi);
+                        const float *r = q[mm + 3 - t];
+                        lo = __fmaf_rn(hk, r[0], lo);
+                        lo = __fmaf_rn(gk, r[1], lo);
+                        hi = __fmaf_rn(hk, r[2], hi);
+                        hi = __fmaf_rn(gk, r[3], hi);
                     }
                     s.lh[2 * m + e][tx] = lo;
                     s.lh[2 * m + e][AC_W + tx] = hi;
@@ -449,7 +474,7 @@ __device__ __forceinline__ void stream_synth(const float *LL, const float *LH, c
         return __ldg(p + o);
     };
     auto load = [&](int m, float *d) {
-        const long long o = (long long)wrap_near(m, Rc) * Cc + nw;
+        const long long o = PRNU_DCHECK(nw >= 0 && nw < Cc, nw) ? (long long)wrap_near(m, Rc) * Cc + nw : 0;
         d[0] = LL ? __ldg(LL + o) : 0.f;
         d[1] = ld(LH, o);
         d[2] = ld(HL, o);

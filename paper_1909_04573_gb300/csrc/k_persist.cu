@@ -157,7 +157,7 @@ __device__ void st_analysis(const float *inh, const float *inl, int R, int Cc, i
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const int c = tx + 32 * k;
-            if (c < AIC) {
+            if (c < AIC && PRNU_DCHECK(sy >= 0 && sy < (LEVEL1 ? H : R) && srcx[k] >= 0 && srcx[k] < srcW, rowoff + srcx[k])) {
                 s.vh[r][c] = ldc(inh + rowoff + srcx[k]);
                 if (!LEVEL1) s.vl[r][c] = ldc(inl + rowoff + srcx[k]);
             }
@@ -597,6 +597,7 @@ __device__ void run_item(const PArgs &a, int g, int s, int t, PSmem &sm, int tid
         for (int u = t * kPTilesAna; u < min(n, (t + 1) * kPTilesAna); ++u) {
             if (u != t * kPTilesAna) __syncthreads();
             const int plane = u / (tp * tq), r = u % (tp * tq);
+            if (!PRNU_DCHECK(plane < C, u)) continue;
             const int p0 = (r / tq) * ATP, q0 = (r % tq) * ATQ;
             float *LLh = l < L ? F(ge.LLh[l]) + plane * A : nullptr;
             float *LLl = l < L ? F(ge.LLl[l]) + plane * A : nullptr;
@@ -619,6 +620,7 @@ __device__ void run_item(const PArgs &a, int g, int s, int t, PSmem &sm, int tid
         for (int u = t * kPTilesShr; u < min(n, (t + 1) * kPTilesShr); ++u) {
             if (u != t * kPTilesShr) __syncthreads();
             const int plane = u / (tp * tq), r = u % (tp * tq);
+            if (!PRNU_DCHECK(plane < 3 * C, u)) continue;
             st_shrink<STD>(F(ge.D[l]) + plane * A, F(ge.N[l]) + plane * A, R, Cc, (r / tq) * PST, (r % tq) * PST,
                            a.s2, a.win, sm.shr, tid);
         }
@@ -647,6 +649,7 @@ __device__ void run_item(const PArgs &a, int g, int s, int t, PSmem &sm, int tid
         for (int u = t * kPTilesFin; u < min(n, (t + 1) * kPTilesFin); ++u) {
             if (u != t * kPTilesFin) __syncthreads();
             const int c = u / (tp * tq), r = u % (tp * tq);
+            if (!PRNU_DCHECK(c < C, u)) continue;
             st_final<COMP>(L >= 2 ? F(ge.Rn[1]) + c * A : nullptr, N + c * A, N + (C + c) * A, N + (2 * C + c) * A,
                            Rc, Cc, F(ge.X) + c * hw, H, W, scale, cam.num + c * hw, cam.den + c * hw,
                            (long long)C * hw, (r / tq) * POT, (r % tq) * POT, a.f, sm.syn, tid);

@@ -68,7 +68,8 @@ __global__ void __launch_bounds__(SEGPX * C / 16) k_sda_sum(SdaArgs a) {
         const int x0 = seg * SEGPX;
         const int npx = min(SEGPX, a.W - x0);
         const int b0 = x0 * C + 16 * k;
-        const int nb = min(16, rowbytes - b0);
+        const int nb = PRNU_DCHECK(y < a.H && gi < a.G && j1 <= (MULTI ? a.gd[gi].n : a.m), u) ? min(16, rowbytes - b0)
+                                                                                            : 0;
         uint32_t tot[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) tot[i] = 0;
@@ -119,7 +120,8 @@ __global__ void __launch_bounds__(SEGPX * C / 16) k_sda_sum(SdaArgs a) {
         float *o = a.out + (long long)gi * C * plane + (long long)y * a.W + x0;
 #pragma unroll
         for (int c = 0; c < C; ++c)
-            for (int x = k; x < npx; x += NT) o[(long long)c * plane + x] = sbuf[x * C + c];
+            for (int x = k; x < npx; x += NT)
+                if (PRNU_DCHECK(x0 + x < a.W, x0 + x)) o[(long long)c * plane + x] = sbuf[x * C + c];
     }
 }
 

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256) k_shrink(ShrinkArgs a) {
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int c = tx + 32 * k;
-            if (c < SE) {
+            if (c < SE && PRNU_DCHECK(srcx[k] >= 0 && srcx[k] < a.Cc && rowoff < (long long)a.R * a.Cc, srcx[k])) {
                 const float v = ldf<T>(in + rowoff + srcx[k]);
                 c2[r][c] = v * v;
             }
@@ -244,6 +244,7 @@ __global__ void __launch_bounds__(32 * SS_WARPS) k_shrink_strip(ShrinkArgs a) {
         for (int g = 0; g < 3; ++g) {
             for (int it = lane; it < (SR / 3) * GPR; it += 32) {
                 const int r = g * (SR / 3) + it / GPR, j = it % GPR;
+                if (!PRNU_DCHECK(4 * wrap_near((x0 >> 2) - 1 + j, nq) + 3 < a.Cc, j)) continue;
                 cp_async16(wsm + r * SS_XS + 4 * j, in + (long long)wrap_near(ys - SH + r, a.R) * a.Cc +
                                                         4 * wrap_near((x0 >> 2) - 1 + j, nq));
             }
@@ -304,7 +305,7 @@ __global__ void __launch_bounds__(32 * SS_WARPS) k_shrink_strip(ShrinkArgs a) {
                 const float mA = fminf(fminf(m1a, m2a), fminf(m3a, m4a));
                 const float mB = fminf(fminf(m1b, m2b), fminf(m3b, m4b));
                 const int gy = ys + o + h;
-                if (gy < a.R && gx < a.Cc) {
+                if (gy < a.R && gx < a.Cc && PRNU_DCHECK(gx + 1 < a.Cc, gx)) {
                     float cA, cB;
                     up2(lds2(base + (c + h) * SS_XS + 4), cA, cB);
                     const float denA = fmaxf(0.f, mA - s2) + s2, denB = fmaxf(0.f, mB - s2) + s2;

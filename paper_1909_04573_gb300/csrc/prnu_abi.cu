@@ -548,6 +548,15 @@ size_t multi_layout_bytes(int H, int W, int C, const prnu_params *p, int groups)
 
 }  // namespace
 
+// Debug-word readers of the translation units (debug.cuh).
+namespace prnu {
+std::vector<std::pair<const char *, DebugReader>> &debug_registry() {
+    static std::vector<std::pair<const char *, DebugReader>> r;
+    return r;
+}
+void debug_register(const char *unit, DebugReader fn) { debug_registry().emplace_back(unit, fn); }
+}  // namespace prnu
+
 // Accessors for the allocation-free entry point (prnu_static.cu).
 namespace prnu {
 int ctx_device(const prnu_ctx *ctx) { return ctx->device; }
@@ -1374,6 +1383,30 @@ prnu_status prnu_autotune_set(prnu_ctx *ctx, int H, int W, const prnu_params *pa
     else
         ctx->tuned[key] = shape;
     return PRNU_OK;
+}
+
+prnu_status prnu_debug_status(prnu_ctx *ctx, char *where, size_t where_len) {
+    if (!ctx) return fail(PRNU_EINVAL, "ctx is NULL");
+    if (where && where_len) where[0] = 0;
+#ifndef PRNU_DEBUG
+    return fail(PRNU_EUNSUPPORTED, "this library was built without PRNU_DEBUG (use libprnu_debug.so)");
+#else
+    DeviceGuard g(ctx->device);
+    CU(cudaDeviceSynchronize());
+    prnu_status st = PRNU_OK;
+    for (auto &u : debug_registry()) {
+        DebugWord w{0, 0, 0};
+        CU(u.second(&w, true));
+        if (w.hit && st == PRNU_OK) {
+            const char *base = std::strrchr(u.first, '/');
+            st = fail(PRNU_EDEBUG, "index check failed at %s:%d (index %lld)", base ? base + 1 : u.first, w.line,
+                      w.index);
+            if (where && where_len) snprintf(where, where_len, "%s:%d %lld", base ? base + 1 : u.first, w.line,
+                                             w.index);
+        }
+    }
+    return st;
+#endif
 }
 
 prnu_status prnu_profile_enable(prnu_ctx *ctx, int on) {

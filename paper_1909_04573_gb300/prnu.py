@@ -14,7 +14,7 @@ import threading
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libprnu.so")
 
-PRNU_OK, PRNU_EINVAL, PRNU_ENOSPC, PRNU_ECUDA, PRNU_ETIMEOUT, PRNU_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+PRNU_OK, PRNU_EINVAL, PRNU_ENOSPC, PRNU_ECUDA, PRNU_ETIMEOUT, PRNU_EUNSUPPORTED, PRNU_EDEBUG = 0, -1, -2, -3, -4, -5, -6
 PRNU_ZERO_MEAN, PRNU_WIENER_DFT, PRNU_TO_GRAY = 1, 2, 4
 
 # every symbol declared in include/prnu.h
@@ -30,7 +30,7 @@ EXPORTS = (
     "prnu_workspace_size_pce_backward", "prnu_pce_backward", "prnu_workspace_size_pce_images",
     "prnu_pce_match_images", "prnu_pce_match_images_async", "prnu_pce_images_prepare",
     "prnu_pce_images_finish_async", "prnu_workspace_size_persistent", "prnu_fingerprint_accumulate_persistent",
-    "prnu_persistent_status", "prnu_persistent_wait_probe",
+    "prnu_persistent_status", "prnu_persistent_wait_probe", "prnu_debug_status",
 )
 
 
@@ -63,77 +63,92 @@ _vp, _sz, _i, _u = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint
 _pp = ctypes.POINTER(prnu_params)
 
 
+def _bind(path: str) -> ctypes.CDLL:
+    """Load a libprnu build and declare the signature of every entry point."""
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is not built: run __graft_entry__.build() (nvcc, sm_103a)")
+    L = ctypes.CDLL(path)
+    sig = {
+        "prnu_default_params": [_pp],
+        "prnu_create": [ctypes.POINTER(_vp), _i],
+        "prnu_destroy": [_vp],
+        "prnu_last_error": [_vp],
+        "prnu_workspace_size": [_vp, _i, _i, _i, _pp, _i, ctypes.POINTER(_sz)],
+        "prnu_workspace_size_host": [_vp, _i, _i, _i, _i, _pp, _i, ctypes.POINTER(_sz)],
+        "prnu_sda_average": [_vp, _vp, _i, _i, _i, _i, _sz, _sz, _i, _vp, _vp],
+        "prnu_denoise_residual": [_vp, _vp, _i, _i, _i, _pp, _vp, _vp, _sz, _vp],
+        "prnu_fingerprint_accumulate": [_vp, _vp, _i, _i, _i, _i, _sz, _sz, _i, _pp, _vp, _vp, _vp, _sz, _vp],
+        "prnu_fingerprint_accumulate_host": [_vp, _vp, _i, _i, _i, _i, _sz, _sz, _i, _pp, _vp, _vp, _vp,
+                                             _sz, _vp],
+        "prnu_fingerprint_finalize": [_vp, _vp, _vp, _i, _i, _i, _u, _pp, _vp, _vp, _sz, _vp],
+        "prnu_pce_match": [_vp, _vp, _vp, _vp, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _vp, _sz, _vp],
+        "prnu_denoise_residual_static": [_vp, _vp, _i, _i, _i, _pp, _vp, _vp],
+        "prnu_denoise_residual_batch": [_vp, _vp, _i, _i, _i, _i, _pp, _vp, _vp, _sz, _vp],
+        "prnu_pce_match_batch": [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _vp, _sz,
+                                 _vp],
+        "prnu_pce_match_pairs": [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _vp, _sz,
+                                 _vp],
+        "prnu_workspace_size_multi": [_vp, ctypes.POINTER(prnu_camera), _i, _pp, _i, ctypes.POINTER(_sz)],
+        "prnu_fingerprint_accumulate_multi": [_vp, ctypes.POINTER(prnu_camera), _i, _pp, _vp, _sz, _vp],
+        "prnu_workspace_size_persistent": [_vp, ctypes.POINTER(prnu_camera), _i, _pp, _i,
+                                           ctypes.POINTER(_sz)],
+        "prnu_fingerprint_accumulate_persistent": [_vp, ctypes.POINTER(prnu_camera), _i, _pp, _i,
+                                                   ctypes.c_double, _vp, _sz, _vp],
+        "prnu_persistent_status": [_vp, _vp, _sz, _vp, ctypes.POINTER(_i)],
+        "prnu_persistent_wait_probe": [_vp, ctypes.c_double, _vp, _sz, _vp],
+        "prnu_autotune": [_vp, _i, _i, _i, _pp, _i, _vp, _sz, _vp, ctypes.POINTER(_i),
+                          ctypes.POINTER(ctypes.c_float)],
+        "prnu_autotune_set": [_vp, _i, _i, _pp, _i],
+        "prnu_workspace_size_pce_images": [_vp, _i, _i, _i, _pp, _i, ctypes.POINTER(_sz)],
+        "prnu_pce_match_images_async": [_vp, _vp, _vp, _i, _i, _i, _i, _pp, _i, _vp, _vp, _vp, _vp, _sz,
+                                        _vp],
+        "prnu_pce_images_prepare": [_vp, _vp, _i, _i, _i, _i, _pp, _vp, _sz, _vp],
+        "prnu_pce_images_finish_async": [_vp, _vp, _vp, _i, _i, _i, _i, _pp, _i, _vp, _vp, _vp, _vp, _sz,
+                                         _vp],
+        "prnu_pce_match_images": [_vp, _vp, _vp, _i, _i, _i, _i, _pp, _i, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i), _vp, _sz, _vp],
+        "prnu_sda_weighted": [_vp, _vp, _i, _i, _i, _i, _sz, _sz, _i, _vp, _vp, _vp],
+        "prnu_sda_weighted_backward": [_vp, _vp, _i, _i, _i, _i, _sz, _sz, _i, _vp, _vp, _vp, _sz, _vp],
+        "prnu_workspace_size_grad": [_vp, _i, _i, _i, _pp, _i, ctypes.POINTER(_sz), ctypes.POINTER(_sz)],
+        "prnu_denoise_residual_ckpt": [_vp, _vp, _i, _i, _i, _i, _pp, _vp, _vp, _vp, _sz, _vp],
+        "prnu_denoise_residual_backward": [_vp, _vp, _i, _i, _i, _i, _pp, _vp, _vp, _vp, _vp, _sz, _vp],
+        "prnu_mle_images": [_vp, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp],
+        "prnu_mle_images_backward": [_vp, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp],
+        "prnu_workspace_size_pce_backward": [_vp, _i, _i, _i, ctypes.POINTER(_sz)],
+        "prnu_pce_backward": [_vp, _vp, _i, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _sz, _vp],
+        "prnu_debug_status": [_vp, ctypes.c_char_p, _sz],
+        "prnu_profile_enable": [_vp, _i],
+        "prnu_profile_reset": [_vp],
+        "prnu_profile_select": [_vp, ctypes.c_char_p],
+        "prnu_profile_read": [_vp, _i, ctypes.c_char_p, _sz, ctypes.POINTER(ctypes.c_longlong),
+                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = None if name == "prnu_destroy" else (ctypes.c_char_p if name == "prnu_last_error"
+                                                          else ctypes.c_int)
+    return L
+
+
 def lib() -> ctypes.CDLL:
     global _lib
     with _lock:
         if _lib is None:
-            if not os.path.exists(LIB_PATH):
-                raise ImportError(f"{LIB_PATH} is not built: run __graft_entry__.build() (nvcc, sm_103a)")
-            L = ctypes.CDLL(LIB_PATH)
-            sig = {
-                "prnu_default_params": [_pp],
-                "prnu_create": [ctypes.POINTER(_vp), _i],
-                "prnu_destroy": [_vp],
-                "prnu_last_error": [_vp],
-                "prnu_workspace_size": [_vp, _i, _i, _i, _pp, _i, ctypes.POINTER(_sz)],
-                "prnu_workspace_size_host": [_vp, _i, _i, _i, _i, _pp, _i, ctypes.POINTER(_sz)],
-                "prnu_sda_average": [_vp, _vp, _i, _i, _i, _i, _sz, _sz, _i, _vp, _vp],
-                "prnu_denoise_residual": [_vp, _vp, _i, _i, _i, _pp, _vp, _vp, _sz, _vp],
-                "prnu_fingerprint_accumulate": [_vp, _vp, _i, _i, _i, _i, _sz, _sz, _i, _pp, _vp, _vp, _vp, _sz, _vp],
-                "prnu_fingerprint_accumulate_host": [_vp, _vp, _i, _i, _i, _i, _sz, _sz, _i, _pp, _vp, _vp, _vp,
-                                                     _sz, _vp],
-                "prnu_fingerprint_finalize": [_vp, _vp, _vp, _i, _i, _i, _u, _pp, _vp, _vp, _sz, _vp],
-                "prnu_pce_match": [_vp, _vp, _vp, _vp, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_double),
-                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _vp, _sz, _vp],
-                "prnu_denoise_residual_static": [_vp, _vp, _i, _i, _i, _pp, _vp, _vp],
-                "prnu_denoise_residual_batch": [_vp, _vp, _i, _i, _i, _i, _pp, _vp, _vp, _sz, _vp],
-                "prnu_pce_match_batch": [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_double),
-                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _vp, _sz,
-                                         _vp],
-                "prnu_pce_match_pairs": [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_double),
-                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _vp, _sz,
-                                         _vp],
-                "prnu_workspace_size_multi": [_vp, ctypes.POINTER(prnu_camera), _i, _pp, _i, ctypes.POINTER(_sz)],
-                "prnu_fingerprint_accumulate_multi": [_vp, ctypes.POINTER(prnu_camera), _i, _pp, _vp, _sz, _vp],
-                "prnu_workspace_size_persistent": [_vp, ctypes.POINTER(prnu_camera), _i, _pp, _i,
-                                                   ctypes.POINTER(_sz)],
-                "prnu_fingerprint_accumulate_persistent": [_vp, ctypes.POINTER(prnu_camera), _i, _pp, _i,
-                                                           ctypes.c_double, _vp, _sz, _vp],
-                "prnu_persistent_status": [_vp, _vp, _sz, _vp, ctypes.POINTER(_i)],
-                "prnu_persistent_wait_probe": [_vp, ctypes.c_double, _vp, _sz, _vp],
-                "prnu_autotune": [_vp, _i, _i, _i, _pp, _i, _vp, _sz, _vp, ctypes.POINTER(_i),
-                                  ctypes.POINTER(ctypes.c_float)],
-                "prnu_autotune_set": [_vp, _i, _i, _pp, _i],
-                "prnu_workspace_size_pce_images": [_vp, _i, _i, _i, _pp, _i, ctypes.POINTER(_sz)],
-                "prnu_pce_match_images_async": [_vp, _vp, _vp, _i, _i, _i, _i, _pp, _i, _vp, _vp, _vp, _vp, _sz,
-                                                _vp],
-                "prnu_pce_images_prepare": [_vp, _vp, _i, _i, _i, _i, _pp, _vp, _sz, _vp],
-                "prnu_pce_images_finish_async": [_vp, _vp, _vp, _i, _i, _i, _i, _pp, _i, _vp, _vp, _vp, _vp, _sz,
-                                                 _vp],
-                "prnu_pce_match_images": [_vp, _vp, _vp, _i, _i, _i, _i, _pp, _i, ctypes.POINTER(ctypes.c_double),
-                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i), _vp, _sz, _vp],
-                "prnu_sda_weighted": [_vp, _vp, _i, _i, _i, _i, _sz, _sz, _i, _vp, _vp, _vp],
-                "prnu_sda_weighted_backward": [_vp, _vp, _i, _i, _i, _i, _sz, _sz, _i, _vp, _vp, _vp, _sz, _vp],
-                "prnu_workspace_size_grad": [_vp, _i, _i, _i, _pp, _i, ctypes.POINTER(_sz), ctypes.POINTER(_sz)],
-                "prnu_denoise_residual_ckpt": [_vp, _vp, _i, _i, _i, _i, _pp, _vp, _vp, _vp, _sz, _vp],
-                "prnu_denoise_residual_backward": [_vp, _vp, _i, _i, _i, _i, _pp, _vp, _vp, _vp, _vp, _sz, _vp],
-                "prnu_mle_images": [_vp, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp],
-                "prnu_mle_images_backward": [_vp, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp],
-                "prnu_workspace_size_pce_backward": [_vp, _i, _i, _i, ctypes.POINTER(_sz)],
-                "prnu_pce_backward": [_vp, _vp, _i, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _sz, _vp],
-                "prnu_profile_enable": [_vp, _i],
-                "prnu_profile_reset": [_vp],
-                "prnu_profile_select": [_vp, ctypes.c_char_p],
-                "prnu_profile_read": [_vp, _i, ctypes.c_char_p, _sz, ctypes.POINTER(ctypes.c_longlong),
-                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
-            }
-            for name, args in sig.items():
-                fn = getattr(L, name)
-                fn.argtypes = args
-                fn.restype = None if name == "prnu_destroy" else (ctypes.c_char_p if name == "prnu_last_error"
-                                                                  else ctypes.c_int)
-            _lib = L
+            _lib = _bind(LIB_PATH)
     return _lib
+
+
+def set_library(path: str | None) -> None:
+    """Bind the entry points of another build of the library (the debug build
+    libprnu_debug.so); None returns to the release build.  Contexts belong to
+    the build that created them: close them before switching."""
+    global _lib
+    with _lock:
+        _lib = _bind(path or LIB_PATH)
 
 
 def _check(status: int, ctx=None) -> None:
@@ -327,6 +342,14 @@ def prnu_workspace_size_pce_backward(ctx, H, W, n):
 def call(name, ctx, *args):
     """Call a status-returning entry point of libprnu; raise PrnuError on failure."""
     _check(getattr(lib(), name)(ctx, *args), ctx)
+
+
+def prnu_debug_status(ctx):
+    """(status, "file:line index") of the debug build's index checks since the
+    last call (synchronises the device; PRNU_EUNSUPPORTED in the release build)."""
+    buf = ctypes.create_string_buffer(256)
+    st = lib().prnu_debug_status(ctx, buf, 256)
+    return st, buf.value.decode()
 
 
 def prnu_profile_enable(ctx, on: bool) -> None:
