@@ -422,21 +422,38 @@ prnu_status prnu_pce_backward(prnu_ctx *ctx, const float *K, int per_query, cons
                               float *g_residual_q, void *ws, size_t ws_bytes, void *stream);
 
 /* Autotuner (not part of the paper's method): times every launch shape
- * (strip rows x warps per block) of the level-1 analysis kernel on `images`
- * images of this geometry and storage type, in the workspace (which must hold
+ * (strip rows x warps per block) of the level-1 analysis kernel, then every
+ * choice of the analysis of levels 2.., the shrink of every level and the
+ * synthesis of levels 2.. (prnu_autotune_level), on `images` images of this
+ * geometry and storage type, in the workspace (which must hold
  * prnu_workspace_size(..., images) bytes; its contents are overwritten), and
- * keeps the fastest in the context for all later calls with that geometry.
- * All shapes compute the same results.  Synchronises `stream` (not
- * capturable).  shape_out / ms_out (nullable, host) receive the chosen shape
- * index and its time per launch. */
+ * keeps the fastest of each in the context for all later calls with that
+ * geometry.  Synchronises `stream` (not capturable).  shape_out / ms_out
+ * (nullable, host) receive the chosen level-1 shape index and its time per
+ * launch. */
 prnu_status prnu_autotune(prnu_ctx *ctx, int H, int W, int C, const prnu_params *params, int images, void *ws,
                           size_t ws_bytes, void *stream, int *shape_out, float *ms_out);
 
 /* Pins the level-1 analysis launch shape (index into the tuner's list:
  * 0..5 = 16x4, 32x4, 64x4, 32x2, 32x8, 64x2 strip rows x warps) for this
- * padded geometry and storage type, or with shape = -1 returns it to the
- * default (32x4).  Host only; EINVAL for an index out of range. */
+ * padded geometry and storage type, or with shape = -1 returns it, and every
+ * per-level choice of prnu_autotune_level, to the defaults (32x4 and choice
+ * 0).  Host only; EINVAL for an index out of range. */
 prnu_status prnu_autotune_set(prnu_ctx *ctx, int H, int W, const prnu_params *params, int shape);
+
+/* The tuner's per-level launch choices (prnu_autotune times every choice of
+ * every level on its zero planes and keeps the fastest; 0 is the default
+ * rule).  kind 0: analysis of level 2..levels (0 tiled 16 x 32 outputs,
+ * 1 streaming 16 rows x 4 warps, 2 streaming 32 rows x 2 warps; all give
+ * bit-identical results); kind 1: shrink of level 1..levels (0 the register
+ * strip where the standard windows and a width that is a multiple of 4 allow
+ * it, else the tile; 1 the 32 x 32 tile; the two sum the windows in different
+ * orders); kind 2: synthesis of level 2..levels (0 streaming where its grid
+ * fills the GPU, else tiled; 1 streaming (float32 subbands); 2 tiled).
+ * choice >= 0 pins it, -1 returns it to the default, -2 only reads it;
+ * *current (nullable) receives the choice in force.  Host only. */
+prnu_status prnu_autotune_level(prnu_ctx *ctx, int H, int W, const prnu_params *params, int kind, int level,
+                                int choice, int *current);
 
 /* Index checks (not part of the paper's method).  The debug build of the
  * library (libprnu_debug.so, compiled with PRNU_DEBUG; same entry points)

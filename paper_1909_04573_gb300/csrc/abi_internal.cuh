@@ -37,6 +37,9 @@ struct prnu_ctx {
     std::vector<cudaEvent_t> pool;
     // autotuned level-1 analysis shape per (padded H, padded W, subband type)
     std::map<std::tuple<int, int, int>, int> tuned;
+    // autotuned choices of the other launches per (padded H, padded W,
+    // subband type, kind, level)
+    std::map<std::tuple<int, int, int, int, int>, int> tuned_lv;
     // device address of the allocation-free entry point's scratch array,
     // resolved by that entry point's first call with this context
     void *static_scratch = nullptr;

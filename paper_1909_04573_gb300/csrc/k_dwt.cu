@@ -394,12 +394,12 @@ __global__ void __launch_bounds__(256) k_analysis(AnaArgs a) {
     }
 }
 
-template <class T, int SP, int WARPS>
+template <class T, int SP, int WARPS, bool LEVEL1 = true>
 static void launch_stream(const AnaArgs &a, cudaStream_t st) {
     dim3 block(32 * WARPS);
     dim3 grid((unsigned)((a.Cc / 2 + 32 * WARPS - 1) / (32 * WARPS)), (unsigned)((a.R / 2 + SP - 1) / SP),
               (unsigned)a.P);
-    k_analysis_stream<true, T, SP, WARPS><<<grid, block, 0, st>>>(a);
+    k_analysis_stream<LEVEL1, T, SP, WARPS><<<grid, block, 0, st>>>(a);
 }
 
 template <class T>
@@ -413,6 +413,10 @@ static void launch_analysis_t(const AnaArgs &a, bool level1, int shape, cudaStre
             case 5: launch_stream<T, 64, 2>(a, st); break;
             default: launch_stream<T, 32, 4>(a, st); break;
         }
+    } else if (shape == 1) {
+        launch_stream<T, 16, 4, false>(a, st);
+    } else if (shape == 2) {
+        launch_stream<T, 32, 2, false>(a, st);
     } else {
         dim3 block(32, 8);
         dim3 grid((unsigned)((a.Cc / 2 + TQ - 1) / TQ), (unsigned)((a.R / 2 + TP - 1) / TP), (unsigned)a.P);

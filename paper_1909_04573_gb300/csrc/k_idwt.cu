@@ -678,8 +678,9 @@ int final_pce_blocks(int Rc, int Cc) {
     return (int)(g.x * g.y);
 }
 
-cudaError_t launch_synthesis(const SynArgs &a, cudaStream_t st) {
-    if (a.sdt == SB_F32 && (a.gray3 || stream_pays(a.Rc, a.Cc, a.P))) {
+cudaError_t launch_synthesis(const SynArgs &a, cudaStream_t st, int choice) {
+    const bool stream = choice == 1 || (choice == 0 && stream_pays(a.Rc, a.Cc, a.P));
+    if (a.sdt == SB_F32 && (a.gray3 || stream)) {
         if (a.gray3)
             k_synthesis_stream<true><<<stream_grid(a.Rc, a.Cc, a.P), 32 * FS_WARPS, 0, st>>>(a);
         else

@@ -319,11 +319,11 @@ __global__ void __launch_bounds__(32 * SS_WARPS) k_shrink_strip(ShrinkArgs a) {
 }
 
 template <class T>
-static void launch_shrink_t(const ShrinkArgs &a, cudaStream_t st) {
+static void launch_shrink_t(const ShrinkArgs &a, cudaStream_t st, int choice) {
     dim3 block(32, 8);
     dim3 grid((unsigned)((a.Cc + ST - 1) / ST), (unsigned)((a.R + ST - 1) / ST), (unsigned)a.nplanes);
     const bool std4 = a.win.n == 4 && a.win.r[0] == 1 && a.win.r[1] == 2 && a.win.r[2] == 3 && a.win.r[3] == 4;
-    if (std4 && a.Cc % 4 == 0) {  // strip path (aligned 4-wide groups)
+    if (std4 && a.Cc % 4 == 0 && choice == 0) {  // strip path (aligned 4-wide groups)
         dim3 g2((unsigned)((a.Cc + SS_W - 1) / SS_W), (unsigned)((a.R + SS_H - 1) / SS_H), (unsigned)a.nplanes);
         if (a.s2_dev)
             k_shrink_strip<true, T><<<g2, 32 * SS_WARPS, 0, st>>>(a);
@@ -339,13 +339,13 @@ static void launch_shrink_t(const ShrinkArgs &a, cudaStream_t st) {
         k_shrink<false, true, T><<<grid, block, 0, st>>>(a);
 }
 
-cudaError_t launch_shrink(const ShrinkArgs &a, cudaStream_t st) {
+cudaError_t launch_shrink(const ShrinkArgs &a, cudaStream_t st, int choice) {
     if (a.sdt == SB_F16)
-        launch_shrink_t<__half>(a, st);
+        launch_shrink_t<__half>(a, st, choice);
     else if (a.sdt == SB_BF16)
-        launch_shrink_t<__nv_bfloat16>(a, st);
+        launch_shrink_t<__nv_bfloat16>(a, st, choice);
     else
-        launch_shrink_t<float>(a, st);
+        launch_shrink_t<float>(a, st, choice);
     return cudaGetLastError();
 }
 

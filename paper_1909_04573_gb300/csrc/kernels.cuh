@@ -41,6 +41,15 @@ constexpr int kStreamShapes = 6;
 constexpr int kStreamShapeDefault = 1;  // 32 rows x 4 warps
 constexpr int kStreamShapeDims[kStreamShapes][2] = {{16, 4}, {32, 4}, {64, 4}, {32, 2}, {32, 8}, {64, 2}};
 cudaError_t launch_analysis(const AnaArgs &a, bool level1, cudaStream_t st, int shape = kStreamShapeDefault);
+// tuner choices of the other launches (0 = the default rule)
+// levels >= 2 analysis: 0 tiled 16 x 32, 1 streaming 16 rows x 4 warps, 2 streaming 32 x 2
+constexpr int kAnaChoices = 3;
+// shrink: 0 strip where it applies (standard windows, width % 4 == 0), else tiled; 1 tiled
+constexpr int kShrinkChoices = 2;
+// synthesis (levels >= 2): 0 streaming where its grid fills the GPU, else tiled; 1 streaming
+// (float32 subbands; else tiled); 2 tiled
+constexpr int kSynChoices = 3;
+enum TuneKind : int { kTuneAnalysis = 0, kTuneShrink = 1, kTuneSynthesis = 2 };
 
 // k_shrink.cu
 struct ShrinkArgs {
@@ -52,7 +61,7 @@ struct ShrinkArgs {
     const double *s2_dev;
     Win win;
 };
-cudaError_t launch_shrink(const ShrinkArgs &a, cudaStream_t st);
+cudaError_t launch_shrink(const ShrinkArgs &a, cudaStream_t st, int choice = 0);
 
 // k_idwt.cu
 struct SynArgs {
@@ -92,7 +101,7 @@ struct FinalArgs {
 };
 // blocks per query of the PCE-mode level-1 kernel (its partial-sum count)
 int final_pce_blocks(int Rc, int Cc);
-cudaError_t launch_synthesis(const SynArgs &a, cudaStream_t st);
+cudaError_t launch_synthesis(const SynArgs &a, cudaStream_t st, int choice = 0);
 cudaError_t launch_final(const FinalArgs &a, bool mle, cudaStream_t st);
 
 // k_fft.cu

@@ -190,6 +190,12 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
     const size_t es = subband_bytes(sdt);
     // typed subband k of a region holding 3 (or 1) planes groups of P planes
     auto SB = [&](size_t off, long long A, int k) { return static_cast<void *>(ws + off + (size_t)k * P * A * es); };
+    // the tuner's choice for a launch kind at level l (0: the default rule)
+    auto choice = [&](int kind, int l) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        auto it = ctx->tuned_lv.find(std::make_tuple(Hp, Wp, sdt, kind, l));
+        return it == ctx->tuned_lv.end() ? 0 : it->second;
+    };
     for (int l = 1; l <= L && phase != kDenoiseLevel1; ++l) {
         const long long A = (long long)(Hp >> l) * (Wp >> l);
         AnaArgs a{};
@@ -218,6 +224,8 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
                 std::lock_guard<std::mutex> lk(ctx->mu);
                 auto it = ctx->tuned.find(std::make_tuple(Hp, Wp, sdt));
                 if (it != ctx->tuned.end()) shape = it->second;
+            } else {
+                shape = choice(kTuneAnalysis, l);
             }
             CU(launch_analysis(a, l == 1, st, shape));
         }
@@ -250,7 +258,7 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
         s.win = win;
         {
             Launch t(ctx, "shrink", st, 1, 2.0 * s.nplanes * s.R * s.Cc * es);
-            CU(launch_shrink(s, st));
+            CU(launch_shrink(s, st, choice(kTuneShrink, l)));
         }
     }
     // PCE mode with three channels: the synthesis is linear, so levels L..1
@@ -273,7 +281,7 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
         y.f = ctx->filt;
         {
             Launch t(ctx, "synthesis", st, 1, (double)P * A * es * 3 + (double)Ps * A * es * (y.LL ? 5 : 4));
-            CU(launch_synthesis(y, st));
+            CU(launch_synthesis(y, st, choice(kTuneSynthesis, l)));
         }
     }
     if (phase == kDenoiseUpToLevel2) return PRNU_OK;
@@ -1358,14 +1366,131 @@ prnu_status prnu_autotune(prnu_ctx *ctx, int H, int W, int C, const prnu_params 
             best = shape;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
         ctx->tuned[std::make_tuple(Hp, Wp, (int)params->dtype)] = best;
     }
+    // the other launches, level by level on the pyramid of the zero planes:
+    // analysis of levels 2..L, shrink of levels 1..L, synthesis of levels L..2
+    CU(launch_analysis(a, true, st, best));  // LL_1 and the level-1 details
+    auto time_it = [&](auto &&launch, float *ms) -> prnu_status {
+        CU(launch());  // warm
+        CU(cudaEventRecord(e0, st));
+        for (int r = 0; r < 3; ++r) CU(launch());
+        CU(cudaEventRecord(e1, st));
+        CU(cudaEventSynchronize(e1));
+        CU(cudaEventElapsedTime(ms, e0, e1));
+        return PRNU_OK;
+    };
+    const int sdt = params->dtype;
+    auto keep = [&](int kind, int l, int c) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->tuned_lv[std::make_tuple(Hp, Wp, sdt, kind, l)] = c;
+    };
+    Win win;
+    if ((s = check_params(params, H, W, &win)) != PRNU_OK) return s;
+    for (int l = 1; l <= L; ++l) {
+        const long long Al = (long long)(Hp >> l) * (Wp >> l);
+        if (l >= 2) {
+            AnaArgs al = a;
+            al.inh = reinterpret_cast<const float *>(b + lo.LLh[l - 1]);
+            al.inl = reinterpret_cast<const float *>(b + lo.LLl[l - 1]);
+            al.R = Hp >> (l - 1);
+            al.Cc = Wp >> (l - 1);
+            al.LLh = l < L ? reinterpret_cast<float *>(b + lo.LLh[l]) : nullptr;
+            al.LLl = l < L ? reinterpret_cast<float *>(b + lo.LLl[l]) : nullptr;
+            al.LH = b + lo.D[l];
+            al.HL = b + lo.D[l] + (size_t)P * Al * es;
+            al.HH = b + lo.D[l] + 2 * (size_t)P * Al * es;
+            int bc = 0;
+            float bm = 1e30f;
+            for (int c = 0; c < kAnaChoices; ++c) {
+                float ms = 0.f;
+                if ((s = time_it([&] { return launch_analysis(al, false, st, c); }, &ms)) != PRNU_OK) return s;
+                if (ms < bm) {
+                    bm = ms;
+                    bc = c;
+                }
+            }
+            keep(kTuneAnalysis, l, bc);
+            CU(launch_analysis(al, false, st, bc));  // this level's outputs for the next one
+        }
+        ShrinkArgs sa{};
+        sa.in = b + lo.D[l];
+        sa.out = b + lo.N[l];
+        sa.sdt = sdt;
+        sa.R = Hp >> l;
+        sa.Cc = Wp >> l;
+        sa.nplanes = 3 * P;
+        sa.s2 = params->sigma0 * params->sigma0;
+        sa.win = win;
+        int bc = 0;
+        float bm = 1e30f;
+        for (int c = 0; c < kShrinkChoices; ++c) {
+            float ms = 0.f;
+            if ((s = time_it([&] { return launch_shrink(sa, st, c); }, &ms)) != PRNU_OK) return s;
+            if (ms < bm) {
+                bm = ms;
+                bc = c;
+            }
+        }
+        keep(kTuneShrink, l, bc);
+    }
+    for (int l = L; l >= 2; --l) {
+        const long long Al = (long long)(Hp >> l) * (Wp >> l);
+        SynArgs y{};
+        y.LL = l == L ? nullptr : b + lo.Rn[l];
+        y.LH = b + lo.N[l];
+        y.HL = b + lo.N[l] + (size_t)P * Al * es;
+        y.HH = b + lo.N[l] + 2 * (size_t)P * Al * es;
+        y.sdt = sdt;
+        y.Rc = Hp >> l;
+        y.Cc = Wp >> l;
+        y.P = P;
+        y.out = b + lo.Rn[l - 1];
+        y.f = ctx->filt;
+        int bc = 0;
+        float bm = 1e30f;
+        for (int c = 0; c < kSynChoices; ++c) {
+            float ms = 0.f;
+            if ((s = time_it([&] { return launch_synthesis(y, st, c); }, &ms)) != PRNU_OK) return s;
+            if (ms < bm) {
+                bm = ms;
+                bc = c;
+            }
+        }
+        keep(kTuneSynthesis, l, bc);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     if (shape_out) *shape_out = best;
     if (ms_out) *ms_out = best_ms;
+    return PRNU_OK;
+}
+
+prnu_status prnu_autotune_level(prnu_ctx *ctx, int H, int W, const prnu_params *params, int kind, int level,
+                                int choice, int *current) {
+    if (!ctx) return fail(PRNU_EINVAL, "ctx is NULL");
+    prnu_status s;
+    if ((s = check_geometry(H, W, 1)) != PRNU_OK) return s;
+    if ((s = check_params(params, H, W, nullptr)) != PRNU_OK) return s;
+    const int L = params->levels;
+    const int nch = kind == kTuneAnalysis ? kAnaChoices : kind == kTuneShrink ? kShrinkChoices
+                  : kind == kTuneSynthesis ? kSynChoices : 0;
+    if (nch == 0) return fail(PRNU_EINVAL, "kind must be 0 (analysis), 1 (shrink) or 2 (synthesis)");
+    const int lmin = kind == kTuneShrink ? 1 : 2;
+    if (level < lmin || level > L) return fail(PRNU_EINVAL, "level must be in [%d, %d] for this kind", lmin, L);
+    if (choice < -2 || choice >= nch) return fail(PRNU_EINVAL, "choice must be in [-2, %d)", nch);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    const auto key = std::make_tuple(padded(H, L), padded(W, L), (int)params->dtype, kind, level);
+    if (choice == -1)
+        ctx->tuned_lv.erase(key);
+    else if (choice >= 0)
+        ctx->tuned_lv[key] = choice;
+    if (current) {
+        auto it = ctx->tuned_lv.find(key);
+        *current = it == ctx->tuned_lv.end() ? 0 : it->second;
+    }
     return PRNU_OK;
 }
 
@@ -1378,10 +1503,19 @@ prnu_status prnu_autotune_set(prnu_ctx *ctx, int H, int W, const prnu_params *pa
     const int L = params->levels;
     std::lock_guard<std::mutex> lk(ctx->mu);
     const auto key = std::make_tuple(padded(H, L), padded(W, L), (int)params->dtype);
-    if (shape < 0)
+    if (shape < 0) {
         ctx->tuned.erase(key);
-    else
+        // the defaults for every level
+        for (auto it = ctx->tuned_lv.begin(); it != ctx->tuned_lv.end();) {
+            if (std::get<0>(it->first) == std::get<0>(key) && std::get<1>(it->first) == std::get<1>(key) &&
+                std::get<2>(it->first) == std::get<2>(key))
+                it = ctx->tuned_lv.erase(it);
+            else
+                ++it;
+        }
+    } else {
         ctx->tuned[key] = shape;
+    }
     return PRNU_OK;
 }
 

@@ -30,7 +30,7 @@ EXPORTS = (
     "prnu_workspace_size_pce_backward", "prnu_pce_backward", "prnu_workspace_size_pce_images",
     "prnu_pce_match_images", "prnu_pce_match_images_async", "prnu_pce_images_prepare",
     "prnu_pce_images_finish_async", "prnu_workspace_size_persistent", "prnu_fingerprint_accumulate_persistent",
-    "prnu_persistent_status", "prnu_persistent_wait_probe", "prnu_debug_status",
+    "prnu_persistent_status", "prnu_persistent_wait_probe", "prnu_debug_status", "prnu_autotune_level",
 )
 
 
@@ -102,6 +102,7 @@ def _bind(path: str) -> ctypes.CDLL:
         "prnu_autotune": [_vp, _i, _i, _i, _pp, _i, _vp, _sz, _vp, ctypes.POINTER(_i),
                           ctypes.POINTER(ctypes.c_float)],
         "prnu_autotune_set": [_vp, _i, _i, _pp, _i],
+        "prnu_autotune_level": [_vp, _i, _i, _pp, _i, _i, _i, ctypes.POINTER(_i)],
         "prnu_workspace_size_pce_images": [_vp, _i, _i, _i, _pp, _i, ctypes.POINTER(_sz)],
         "prnu_pce_match_images_async": [_vp, _vp, _vp, _i, _i, _i, _i, _pp, _i, _vp, _vp, _vp, _vp, _sz,
                                         _vp],
@@ -565,6 +566,15 @@ class Context:
     def autotune_set(self, H, W, shape, params=None):
         """Pin the level-1 analysis shape (index into STREAM_SHAPES; -1 = default)."""
         _check(lib().prnu_autotune_set(self.ctx, H, W, ctypes.byref(params or default_params()), shape), self.ctx)
+
+    def autotune_level(self, H, W, kind, level, choice=-2, params=None):
+        """Pin (choice >= 0), reset (-1) or read (-2) the tuner's choice for a
+        launch kind (0 analysis, 1 shrink, 2 synthesis) at a level; returns the
+        choice in force."""
+        cur = _i()
+        _check(lib().prnu_autotune_level(self.ctx, H, W, ctypes.byref(params or default_params()), kind, level,
+                                         choice, ctypes.byref(cur)), self.ctx)
+        return cur.value
 
     def cameras(self, items):
         """[(frames [m, H, W, C] tensor, d, num, den)] -> prnu_camera structs."""

@@ -56,3 +56,47 @@ def test_invalid_shape_is_rejected(ctx):
     assert e.value.status == P.PRNU_EINVAL
     with pytest.raises(P.PrnuError):
         ctx.autotune(64, 64, 2)                                   # C must be 1 or 3
+
+
+@pytest.mark.parametrize("H,W,C,dtype", [(200, 328, 3, P.PRNU_DTYPE_F32), (1080, 1920, 1, P.PRNU_DTYPE_F32),
+                                         (97, 250, 1, P.PRNU_DTYPE_F16)])
+def test_per_level_choices(ctx, H, W, C, dtype):
+    """Every per-level launch choice the tuner may pin: the analysis and the
+    synthesis forms give bit-identical residuals; the two shrink forms sum the
+    windows in different orders and agree to float32 rounding."""
+    prm = P.default_params(dtype=dtype)
+    img = ctx.sda_average(synth.frames(synth.Camera(H=H, W=W, C=C, camera_id=43), 3, device="cuda"), 3)[0]
+    ctx.autotune_set(H, W, -1, prm)
+    ref = ctx.denoise_residual(img, params=prm).clone()
+    for kind, levels, nch, exact in ((0, range(2, 5), 3, True), (2, range(2, 5), 3, True), (1, range(1, 5), 2, False)):
+        for level in levels:
+            for c in range(nch):
+                assert ctx.autotune_level(H, W, kind, level, c, prm) == c
+                out = ctx.denoise_residual(img, params=prm)
+                torch.cuda.synchronize()
+                if exact:
+                    assert torch.equal(out, ref), (kind, level, c)
+                else:
+                    assert float((out - ref).abs().max()) <= 1e-4 * max(1.0, float(ref.abs().max())), (kind, level, c)
+            ctx.autotune_level(H, W, kind, level, -1, prm)
+    ctx.autotune_set(H, W, -1, prm)
+
+
+def test_tuner_sets_every_level(ctx):
+    H, W, C = 272, 480, 3
+    prm = P.default_params()
+    img = ctx.sda_average(synth.frames(synth.Camera(H=H, W=W, C=C, camera_id=44), 2, device="cuda"), 2)[0]
+    ctx.autotune_set(H, W, -1, prm)
+    ref = ctx.denoise_residual(img, params=prm).clone()
+    ctx.autotune(H, W, C, prm, images=2)
+    got = {(k, l): ctx.autotune_level(H, W, k, l) for k, ls in ((0, range(2, 5)), (1, range(1, 5)), (2, range(2, 5)))
+           for l in ls}
+    assert all(0 <= v < (2 if k == 1 else 3) for (k, _), v in got.items())
+    out = ctx.denoise_residual(img, params=prm)
+    torch.cuda.synchronize()
+    assert float((out - ref).abs().max()) <= 1e-4 * max(1.0, float(ref.abs().max()))
+    with pytest.raises(P.PrnuError):
+        ctx.autotune_level(H, W, 0, 1, 0)       # no analysis choice at level 1
+    with pytest.raises(P.PrnuError):
+        ctx.autotune_level(H, W, 1, 5, 0)       # past the last level
+    ctx.autotune_set(H, W, -1, prm)
