@@ -35,7 +35,9 @@
 namespace prnu {
 namespace {
 
-constexpr int CT = 256;  // threads per block of the three kernels
+constexpr int CT = 256;    // threads per block of the inverse row pass (its registers allow no more)
+constexpr int CTW = 512;   // threads per block of the forward row and the column passes: their shared
+                           // memory allows two blocks per SM, so twice the threads double the warps
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -300,7 +302,7 @@ __device__ float2 *fft_run(float2 *a, float2 *b, const FftSteps &p, const float2
 }
 
 // The same with the length fixed at compile time: the pass sequence, strides
-// and loop trip counts are constants (the block has CT threads).
+// and loop trip counts are constants (the block has NT threads).
 struct StaticPlan {
     int np = 0;
     int r[kMaxFftPasses] = {}, ns[kMaxFftPasses] = {};
@@ -323,7 +325,7 @@ __host__ __device__ constexpr StaticPlan static_plan(int L) {
     return p;
 }
 
-template <int R, int L, int Ns, int G, int NA, bool INV>
+template <int R, int L, int Ns, int G, int NA, bool INV, int NT>
 __device__ __forceinline__ void fft_pass_s(const float2 *__restrict__ a, float2 *__restrict__ b,
                                            const float2 *__restrict__ tw) {
     constexpr int nb = L / R, step = L / (Ns * R), total = nb * NA;
@@ -333,9 +335,9 @@ __device__ __forceinline__ void fft_pass_s(const float2 *__restrict__ a, float2 
     constexpr bool st_lin = Ns % 8 == 0 || (Ns == 1 && 8 % R == 0);
     constexpr int ld_step = prow(nb), st_step = Ns == 1 ? 1 : prow(Ns);
 #pragma unroll
-    for (int it = 0; it < (total + CT - 1) / CT; ++it) {
-        const int u = (int)threadIdx.x + it * CT;
-        if (total % CT == 0 || u < total) {
+    for (int it = 0; it < (total + NT - 1) / NT; ++it) {
+        const int u = (int)threadIdx.x + it * NT;
+        if (total % NT == 0 || u < total) {
             const int g = u % NA, j = u / NA;
             const int k = Ns == 1 ? 0 : j % Ns;
             float2 v[R];
@@ -361,24 +363,24 @@ __device__ __forceinline__ void fft_pass_s(const float2 *__restrict__ a, float2 
     }
 }
 
-template <int L, int G, int NA, bool INV, int P = 0>
+template <int L, int G, int NA, bool INV, int NT, int P = 0>
 __device__ __forceinline__ float2 *fft_run_s(float2 *a, float2 *b, const float2 *tw) {
     constexpr StaticPlan pl = static_plan(L);
     static_assert(pl.np > 0, "length must factor into 2, 3, 5, 7");
     if constexpr (P == pl.np) {
         return a;
     } else {
-        fft_pass_s<pl.r[P], L, pl.ns[P], G, NA, INV>(a, b, tw);
+        fft_pass_s<pl.r[P], L, pl.ns[P], G, NA, INV, NT>(a, b, tw);
         __syncthreads();
-        return fft_run_s<L, G, NA, INV, P + 1>(b, a, tw);
+        return fft_run_s<L, G, NA, INV, NT, P + 1>(b, a, tw);
     }
 }
 
-// LS > 0: the length is LS (compile time); else p.L
-template <int LS, int G, int NA, bool INV>
+// LS > 0: the length is LS (compile time); else p.L.  NT: threads per block.
+template <int LS, int G, int NA, bool INV, int NT>
 __device__ __forceinline__ float2 *fft_any(float2 *a, float2 *b, const FftSteps &p, const float2 *tw) {
     if constexpr (LS > 0)
-        return fft_run_s<LS, G, NA, INV>(a, b, tw);
+        return fft_run_s<LS, G, NA, INV, NT>(a, b, tw);
     else
         return fft_run<G, NA, INV>(a, b, p, tw);
 }
@@ -421,8 +423,8 @@ __global__ void k_twiddles(float2 *tw, int M, int H) {
 // M + 1 bins (pitch ldo complex); G rows per block iteration.  Three buffers
 // rotate: the next rows are staged (cp.async) while the current ones are
 // transformed in the other two.
-template <int G, int MS>
-__global__ void __launch_bounds__(CT) k_rfft_rows(const float *__restrict__ x, float2 *__restrict__ out,
+template <int G, int MS, int NT>
+__global__ void __launch_bounds__(NT) k_rfft_rows(const float *__restrict__ x, float2 *__restrict__ out,
                                                   long long nrows, int W, int ldo, FftSteps p,
                                                   const float2 *__restrict__ twg) {
     extern __shared__ float2 sm[];
@@ -452,7 +454,7 @@ __global__ void __launch_bounds__(CT) k_rfft_rows(const float *__restrict__ x, f
         cp_async_commit();
         cp_async_wait<1>();  // this iteration's rows have landed
         __syncthreads();
-        const float2 *Z = fft_any<MS, G, G, false>(cur, scr, p, tw);
+        const float2 *Z = fft_any<MS, G, G, false, NT>(cur, scr, p, tw);
         // split step: X_k = (Z_k + conj Z_{M-k}) / 2 - i w_W^k (Z_k - conj Z_{M-k}) / 2
         for (int u = threadIdx.x; u < G * (M + 1); u += blockDim.x) {
             const int g = u % G, k = u / G;
@@ -471,8 +473,8 @@ __global__ void __launch_bounds__(CT) k_rfft_rows(const float *__restrict__ x, f
 // Per query q (grid y) and tile of TC spectrum columns (grid x): column FFTs
 // of X^_q and Y^_q (F + q*H*ld and F + (n+q)*H*ld, pitch ld), Z = conj(X^) Y^
 // with Z(0, 0) = 0, inverse column FFT of Z, written over X^_q.
-template <int TC, int HS>
-__global__ void __launch_bounds__(CT) k_corr_columns(float2 *F, int n, int H, int Wh, int ld, FftSteps p,
+template <int TC, int HS, int NT>
+__global__ void __launch_bounds__(NT) k_corr_columns(float2 *F, int n, int H, int Wh, int ld, FftSteps p,
                                                      const float2 *__restrict__ twg) {
     extern __shared__ float2 sm[];
     constexpr int G = 2 * TC;
@@ -492,7 +494,7 @@ __global__ void __launch_bounds__(CT) k_corr_columns(float2 *F, int n, int H, in
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    float2 *S = fft_any<HS, G, G, false>(A, B, p, tw);
+    float2 *S = fft_any<HS, G, G, false, NT>(A, B, p, tw);
     float2 *T = S == A ? B : A;
     // Z into T in its own layout of TC sequences (the inverse then touches
     // whole rows of that layout)
@@ -504,7 +506,7 @@ __global__ void __launch_bounds__(CT) k_corr_columns(float2 *F, int n, int H, in
         T[at<TC>(y, s)] = z;
     }
     __syncthreads();
-    const float2 *Z = fft_any<HS, TC, TC, true>(T, S, p, tw);
+    const float2 *Z = fft_any<HS, TC, TC, true, NT>(T, S, p, tw);
     for (int u = threadIdx.x; u < TC * H; u += blockDim.x) {
         const int s = u % TC, y = u / TC, c = c0 + s;
         if (c < Wh && PRNU_DCHECK(c < ld, c)) FX[(long long)y * ld + c] = Z[at<TC>(y, s)];
@@ -575,7 +577,7 @@ __global__ void __launch_bounds__(CT) k_corr_rows(const float2 *__restrict__ Zal
             Wk[at<G>(k, g)] = make_float2(e.x - o.y, e.y + o.x);
         }
         __syncthreads();
-        const float2 *z = fft_any<MS, G, G, true>(Wk, cur, p, tw);
+        const float2 *z = fft_any<MS, G, G, true, CT>(Wk, cur, p, tw);
         float fe = 0.f;
         for (int u = threadIdx.x; u < G * M; u += blockDim.x) {
             const int g = u % G, m = u / G, y = y0 + g;
@@ -685,11 +687,11 @@ size_t corr_twiddle_count(int H, int W) { return (size_t)(W / 2) * 2 + 1 + H; }
 int corr_pitch(int W) { return (W / 2 + 1 + 3) / 4 * 4; }
 
 namespace {
-template <auto Kern, typename... Args>
+template <auto Kern, int NT = CT, typename... Args>
 cudaError_t launch(dim3 grid, size_t smem, cudaStream_t st, Args... args) {
     cudaError_t e = smem_attr<Kern>(smem);
     if (e != cudaSuccess) return e;
-    Kern<<<grid, CT, smem, st>>>(args...);
+    Kern<<<grid, NT, smem, st>>>(args...);
     return cudaGetLastError();
 }
 // lengths with compiled-in pass plans (1920 x 1080 frames); others run the
@@ -710,19 +712,21 @@ cudaError_t launch_corr_fft(const float *XY, float2 *F, float2 *tw, int n, int H
         k_twiddles<<<(nt + 255) / 256, 256, 0, st>>>(tw, M, H);
         const long long nrows = 2LL * n * H;
         const dim3 grid((unsigned)std::min<long long>((nrows + G - 1) / G, (long long)sms * (rs <= 113 * 1024 ? 2 : 1)));
-        if (M == kStaticM) return launch<k_rfft_rows<4, kStaticM>>(grid, rs, st, XY, F, nrows, W, ld, pm, (const float2 *)tw);
-        if (G == 4) return launch<k_rfft_rows<4, 0>>(grid, rs, st, XY, F, nrows, W, ld, pm, (const float2 *)tw);
-        return launch<k_rfft_rows<2, 0>>(grid, rs, st, XY, F, nrows, W, ld, pm, (const float2 *)tw);
+        if (M == kStaticM)
+            return launch<k_rfft_rows<4, kStaticM, CTW>, CTW>(grid, rs, st, XY, F, nrows, W, ld, pm, (const float2 *)tw);
+        if (G == 4) return launch<k_rfft_rows<4, 0, CTW>, CTW>(grid, rs, st, XY, F, nrows, W, ld, pm, (const float2 *)tw);
+        return launch<k_rfft_rows<2, 0, CTW>, CTW>(grid, rs, st, XY, F, nrows, W, ld, pm, (const float2 *)tw);
     }
     if (stage == 1) {
         const int tc = cols_tile(H);
         const size_t cs = cols_smem(H, tc);
         const dim3 grid((Wh + tc - 1) / tc, n);
         const float2 *twc = tw + 2 * M + 1;
-        if (H == kStaticH && tc == 2) return launch<k_corr_columns<2, kStaticH>>(grid, cs, st, F, n, H, Wh, ld, ph, twc);
-        if (tc == 4) return launch<k_corr_columns<4, 0>>(grid, cs, st, F, n, H, Wh, ld, ph, twc);
-        if (tc == 2) return launch<k_corr_columns<2, 0>>(grid, cs, st, F, n, H, Wh, ld, ph, twc);
-        return launch<k_corr_columns<1, 0>>(grid, cs, st, F, n, H, Wh, ld, ph, twc);
+        if (H == kStaticH && tc == 2)
+            return launch<k_corr_columns<2, kStaticH, CTW>, CTW>(grid, cs, st, F, n, H, Wh, ld, ph, twc);
+        if (tc == 4) return launch<k_corr_columns<4, 0, CTW>, CTW>(grid, cs, st, F, n, H, Wh, ld, ph, twc);
+        if (tc == 2) return launch<k_corr_columns<2, 0, CTW>, CTW>(grid, cs, st, F, n, H, Wh, ld, ph, twc);
+        return launch<k_corr_columns<1, 0, CTW>, CTW>(grid, cs, st, F, n, H, Wh, ld, ph, twc);
     }
     const dim3 grid((unsigned)std::min(nb, (H + G - 1) / G), n);
     const float2 *Fc = F, *twc = tw;

@@ -1,5 +1,7 @@
-"""Level-1 analysis launch shapes: every shape the tuner may pick gives
-bit-identical results, and the tuner's choice is cached and used (GPU)."""
+"""The autotuner's launch choices: every level-1 analysis shape, every
+analysis form of levels 2.. and every synthesis form give bit-identical
+results, the two shrink forms agree to float32 rounding, and the tuner's
+choices are cached and used (GPU)."""
 import pytest
 import torch
 
@@ -46,7 +48,10 @@ def test_tuner_picks_a_shape_and_keeps_results(ctx):
     num1, den1 = torch.zeros_like(num0), torch.zeros_like(den0)
     ctx.fingerprint_accumulate(fr, 5, num1, den1)
     torch.cuda.synchronize()
-    assert torch.equal(num0, num1) and torch.equal(den0, den1)
+    # the level-1 shapes and the analysis / synthesis choices are bit-identical;
+    # a shrink choice sums the windows in another order (float32 rounding)
+    assert torch.equal(den0, den1)
+    assert float((num1 - num0).norm() / num0.norm()) <= 1e-6
     ctx.autotune_set(H, W, -1)
 
 
