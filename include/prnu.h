@@ -449,7 +449,7 @@ prnu_status prnu_autotune_set(prnu_ctx *ctx, int H, int W, const prnu_params *pa
  * strip where the standard windows and a width that is a multiple of 4 allow
  * it, else the tile; 1 the 32 x 32 tile; the two sum the windows in different
  * orders); kind 2: synthesis of level 2..levels (0 streaming where its grid
- * fills the GPU, else tiled; 1 streaming (float32 subbands); 2 tiled).
+ * fills the GPU, else tiled; 1 streaming; 2 tiled).
  * choice >= 0 pins it, -1 returns it to the default, -2 only reads it;
  * *current (nullable) receives the choice in force.  Host only. */
 prnu_status prnu_autotune_level(prnu_ctx *ctx, int H, int W, const prnu_params *params, int kind, int level,

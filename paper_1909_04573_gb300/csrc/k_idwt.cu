@@ -8,6 +8,8 @@
 // j = 2m + e (e in {0, 1}) takes k = e + 2t, n = m - t for t = 0..3.
 // Columns are synthesised first, then rows.  A 32 x 32 output tile needs a
 // 19 x 19 tile (3-coefficient halo) of each of the four subbands.
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace prnu {
@@ -254,6 +256,9 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
@@ -262,24 +267,36 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-constexpr int AC_W = 24;   // staged coefficient columns per tile row (6 chunks)
+constexpr int AC_W = 24;   // lo | hi split of a row of lh
 constexpr int AC_LH = 48;  // lo | hi row: lo at 0..18, hi at 24..42
 constexpr int AC_BUF = 3;  // copy stages
+// Staged coefficient columns per tile row for subband type T: float32 rows
+// are columns n0-4 .. n0+19 (6 chunks of 4), 16-bit rows n0-8 .. n0+23 (4
+// chunks of 8); the synthesis reads n0-3 .. n0+15 at offset ACOFF.
+template <class T> struct ACT {
+    static constexpr int EPC = 16 / (int)sizeof(T);        // elements per 16-byte chunk
+    static constexpr int W = sizeof(T) == 4 ? 24 : 32;     // staged columns
+    static constexpr int CPR = W / EPC;                    // chunks per row
+    static constexpr int START = sizeof(T) == 4 ? 4 : 8;   // first staged column is n0 - START
+    static constexpr int OFF = START - 3;                  // column of n0 - 3 in the staged row
+};
+template <class T>
 struct AsyncTile {
-    float c[AC_BUF][4][CT][AC_W];  // LL, LH, HL, HH coefficient tiles
-    float x[AC_BUF][OT][OT];       // the image tile (group sums)
-    float lh[OT][AC_LH];           // column-synthesised lo (0..18) and hi (24..42)
+    T c[AC_BUF][4][CT][ACT<T>::W];  // LL, LH, HL, HH coefficient tiles
+    float x[AC_BUF][OT][OT];        // the image tile (group sums)
+    float lh[OT][AC_LH];            // column-synthesised lo (0..18) and hi (24..42)
 };
 
-template <bool COMP>
+template <bool COMP, class T>
 __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
-    __shared__ __align__(16) AsyncTile s;
+    using At = ACT<T>;
+    __shared__ __align__(16) AsyncTile<T> s;
     const int y0 = blockIdx.y * OT, x0 = blockIdx.x * OT;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * 32 + tx;
     const long long hw = (long long)a.H * a.W;
-    const float *LL = static_cast<const float *>(a.LL), *LH = static_cast<const float *>(a.LH);
-    const float *HL = static_cast<const float *>(a.HL), *HH = static_cast<const float *>(a.HH);
+    const T *LL = static_cast<const T *>(a.LL), *LH = static_cast<const T *>(a.LH);
+    const T *HL = static_cast<const T *>(a.HL), *HH = static_cast<const T *>(a.HH);
     const int nimg = a.G;
     auto plane_of = [&](int i) { return i * a.C + (int)blockIdx.z; };
     // image tile: full 16-byte chunks when the tile's rows are whole chunks
@@ -288,8 +305,8 @@ __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
     // (at most two) coefficient chunks -- subband k, row, 4-column group -- and
     // its image chunk are resolved once, so an image's issue is a handful of
     // adds per copy.
-    constexpr int NCH = 4 * CT * (AC_W / 4);  // 456 coefficient chunks
-    int ck[2], coff[2], cdst[2];              // subband (-1: none), in-plane offset, float index in s.c[0]
+    constexpr int NCH = 4 * CT * At::CPR;  // coefficient chunks (456 float32, 304 16-bit)
+    int ck[2], coff[2], cdst[2];           // subband (-1: none), in-plane offset, element index in s.c[0]
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int it = tid + 256 * h;
@@ -297,14 +314,14 @@ __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
         coff[h] = 0;
         cdst[h] = 0;
         if (it < NCH) {
-            const int k = it / (CT * (AC_W / 4)), rem = it - k * (CT * (AC_W / 4));
-            const int r = rem / (AC_W / 4), j = rem - r * (AC_W / 4);
+            const int k = it / (CT * At::CPR), rem = it - k * (CT * At::CPR);
+            const int r = rem / At::CPR, j = rem - r * At::CPR;
             const int row = wrap_near((y0 >> 1) - 3 + r, a.Rc);
-            const int col = wrap_near((x0 >> 1) - 4 + 4 * j, a.Cc);
-            if (PRNU_DCHECK(row >= 0 && row < a.Rc && col >= 0 && col + 3 < a.Cc, col)) {
+            const int col = wrap_near((x0 >> 1) - At::START + At::EPC * j, a.Cc);
+            if (PRNU_DCHECK(row >= 0 && row < a.Rc && col >= 0 && col + At::EPC - 1 < a.Cc, col)) {
                 ck[h] = k;
                 coff[h] = row * a.Cc + col;
-                cdst[h] = (k * CT + r) * AC_W + 4 * j;
+                cdst[h] = (k * CT + r) * At::W + At::EPC * j;
             }
         }
     }
@@ -313,11 +330,11 @@ __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
     const long long xoff = (long long)(y0 + xy) * a.W + x0 + 4 * xj;
     auto issue = [&](int plane, int b) {
         const long long poff = (long long)plane * a.Rc * a.Cc;
-        float *cb = &s.c[b][0][0][0];
+        T *cb = &s.c[b][0][0][0];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             if (ck[h] < 0) continue;
-            const float *src = ck[h] == 0 ? LL : ck[h] == 1 ? LH : ck[h] == 2 ? HL : HH;
+            const T *src = ck[h] == 0 ? LL : ck[h] == 1 ? LH : ck[h] == 2 ? HL : HH;
             if (src)
                 cp_async16(cb + cdst[h], src + poff + coff[h]);
             else
@@ -365,7 +382,7 @@ __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
 #pragma unroll
             for (int rr = 0; rr < 5; ++rr)
 #pragma unroll
-                for (int k = 0; k < 4; ++k) q[rr][k] = s.c[b][k][2 * ty + rr][tx + 1];
+                for (int k = 0; k < 4; ++k) q[rr][k] = to_f(s.c[b][k][2 * ty + rr][tx + At::OFF]);
 #pragma unroll
             for (int mm = 0; mm < 2; ++mm) {
                 const int m = 2 * ty + mm;
@@ -457,10 +474,9 @@ constexpr int FS_COLS = 29;  // output coefficient columns per warp
 // offsets 0, cs, 2 cs (the synthesis is linear, so this synthesises the grey
 // combination of three channels' noise).  Each output pair (y, x), (y, x+1)
 // of the first outH x outW samples goes to epi(y, x, w0, w1, two).
-template <bool GRAY3, class Epi>
-__device__ __forceinline__ void stream_synth(const float *LL, const float *LH, const float *HL, const float *HH,
-                                             long long cs, int Rc, int Cc, const Filt &f, int cg, int m0, int outH,
-                                             int outW, Epi &epi) {
+template <bool GRAY3, class T, class Epi>
+__device__ __forceinline__ void stream_synth(const T *LL, const T *LH, const T *HL, const T *HH, long long cs, int Rc,
+                                             int Cc, const Filt &f, int cg, int m0, int outH, int outW, Epi &epi) {
     const int lane = threadIdx.x & 31;
     const int n = cg * FS_COLS - 3 + lane;  // coefficient column (unwrapped)
     const int nw = wrap_near(n, Cc);
@@ -468,14 +484,14 @@ __device__ __forceinline__ void stream_synth(const float *LL, const float *LH, c
     const int m1 = min(Rc, m0 + FS_ROWS);
     // ring slot of coefficient row m is (m - m0 + 3) & 3
     float q[4][4];  // [slot][subband]
-    auto ld = [&](const float *p, long long o) {
+    auto ld = [&](const T *p, long long o) {
         if (GRAY3)
-            return __fmaf_rn(0.114f, __ldg(p + o + 2 * cs), __fmaf_rn(0.587f, __ldg(p + o + cs), 0.299f * __ldg(p + o)));
-        return __ldg(p + o);
+            return __fmaf_rn(0.114f, ldf<T>(p + o + 2 * cs), __fmaf_rn(0.587f, ldf<T>(p + o + cs), 0.299f * ldf<T>(p + o)));
+        return ldf<T>(p + o);
     };
     auto load = [&](int m, float *d) {
         const long long o = PRNU_DCHECK(nw >= 0 && nw < Cc, nw) ? (long long)wrap_near(m, Rc) * Cc + nw : 0;
-        d[0] = LL ? __ldg(LL + o) : 0.f;
+        d[0] = LL ? ldf<T>(LL + o) : 0.f;
         d[1] = ld(LH, o);
         d[2] = ld(HL, o);
         d[3] = ld(HH, o);
@@ -534,50 +550,50 @@ __device__ __forceinline__ void stream_synth(const float *LL, const float *LH, c
     }
 }
 
-// store (ACC: add) an output pair into a row-major plane of width W
-template <bool ACC>
+// store (ACC: add) an output pair into a row-major plane of width W of type T
+template <bool ACC, class T = float>
 struct StoreEpi {
-    float *p;
+    T *p;
     int W;
     __device__ __forceinline__ void operator()(int y, int x, float w0, float w1, bool two) const {
-        float *o = p + (long long)y * W + x;
+        T *o = p + (long long)y * W + x;
         if (ACC) {
-            o[0] += w0;
-            if (two) o[1] += w1;
-        } else if (two && ((reinterpret_cast<uintptr_t>(o) & 7u) == 0)) {
+            stf<T>(o, to_f(o[0]) + w0);
+            if (two) stf<T>(o + 1, to_f(o[1]) + w1);
+        } else if (std::is_same<T, float>::value && two && ((reinterpret_cast<uintptr_t>(o) & 7u) == 0)) {
             *reinterpret_cast<float2 *>(o) = make_float2(w0, w1);
         } else {
-            o[0] = w0;
-            if (two) o[1] = w1;
+            stf<T>(o, w0);
+            if (two) stf<T>(o + 1, w1);
         }
     }
 };
 
 // Level 1, residual mode: W cropped to H x W, stored (ACC: added) at res_out[plane].
-template <bool ACC>
+template <bool ACC, class T>
 __global__ void __launch_bounds__(32 * FS_WARPS) k_final_stream(FinalArgs a) {
     const int cg = blockIdx.x * FS_WARPS + (threadIdx.x >> 5);
     if (cg * FS_COLS >= a.Cc) return;  // warp-uniform
     const long long off = (long long)blockIdx.z * a.Rc * a.Cc;
-    const float *LL = a.LL ? static_cast<const float *>(a.LL) + off : nullptr;
+    const T *LL = a.LL ? static_cast<const T *>(a.LL) + off : nullptr;
     StoreEpi<ACC> epi{a.res_out + (long long)blockIdx.z * a.H * a.W, a.W};
-    stream_synth<false>(LL, static_cast<const float *>(a.LH) + off, static_cast<const float *>(a.HL) + off,
-                        static_cast<const float *>(a.HH) + off, 0, a.Rc, a.Cc, a.f, cg, blockIdx.y * FS_ROWS, a.H,
-                        a.W, epi);
+    stream_synth<false, T>(LL, static_cast<const T *>(a.LH) + off, static_cast<const T *>(a.HL) + off,
+                           static_cast<const T *>(a.HH) + off, 0, a.Rc, a.Cc, a.f, cg, blockIdx.y * FS_ROWS, a.H,
+                           a.W, epi);
 }
 
 // Levels 2..L: the 2Rc x 2Cc noise LL of the level below (grey with gray3).
-template <bool GRAY3>
+template <bool GRAY3, class T>
 __global__ void __launch_bounds__(32 * FS_WARPS) k_synthesis_stream(SynArgs a) {
     const int cg = blockIdx.x * FS_WARPS + (threadIdx.x >> 5);
     if (cg * FS_COLS >= a.Cc) return;  // warp-uniform
     const long long A = (long long)a.Rc * a.Cc;
     const long long off = (long long)blockIdx.z * A, doff = GRAY3 ? 3 * off : off;
-    const float *LL = a.LL ? static_cast<const float *>(a.LL) + off : nullptr;
-    StoreEpi<false> epi{static_cast<float *>(a.out) + 4 * off, 2 * a.Cc};
-    stream_synth<GRAY3>(LL, static_cast<const float *>(a.LH) + doff, static_cast<const float *>(a.HL) + doff,
-                        static_cast<const float *>(a.HH) + doff, A, a.Rc, a.Cc, a.f, cg, blockIdx.y * FS_ROWS,
-                        2 * a.Rc, 2 * a.Cc, epi);
+    const T *LL = a.LL ? static_cast<const T *>(a.LL) + off : nullptr;
+    StoreEpi<false, T> epi{static_cast<T *>(a.out) + 4 * off, 2 * a.Cc};
+    stream_synth<GRAY3, T>(LL, static_cast<const T *>(a.LH) + doff, static_cast<const T *>(a.HL) + doff,
+                           static_cast<const T *>(a.HH) + doff, A, a.Rc, a.Cc, a.f, cg, blockIdx.y * FS_ROWS,
+                           2 * a.Rc, 2 * a.Cc, epi);
 }
 
 // Level 1, PCE mode: X = grey W, Y = K grey(I), and the lane's sums of X,
@@ -637,7 +653,7 @@ __global__ void __launch_bounds__(32 * FS_WARPS, 8) k_final_pce(FinalArgs a) {
     if (cg * FS_COLS < a.Cc) {  // warp-uniform
         const long long doff = (GRAY3 ? 3LL : 1LL) * z * A;
         const float *LL = a.LL ? static_cast<const float *>(a.LL) + z * A : nullptr;
-        stream_synth<GRAY3>(LL, static_cast<const float *>(a.LH) + doff, static_cast<const float *>(a.HL) + doff,
+        stream_synth<GRAY3, float>(LL, static_cast<const float *>(a.LH) + doff, static_cast<const float *>(a.HL) + doff,
                             static_cast<const float *>(a.HH) + doff, A, a.Rc, a.Cc, a.f, cg, blockIdx.y * FS_ROWS,
                             a.H, a.W, epi);
     }
@@ -678,13 +694,24 @@ int final_pce_blocks(int Rc, int Cc) {
     return (int)(g.x * g.y);
 }
 
+template <class T>
+static void launch_synthesis_stream(const SynArgs &a, cudaStream_t st) {
+    k_synthesis_stream<false, T><<<stream_grid(a.Rc, a.Cc, a.P), 32 * FS_WARPS, 0, st>>>(a);
+}
+
 cudaError_t launch_synthesis(const SynArgs &a, cudaStream_t st, int choice) {
     const bool stream = choice == 1 || (choice == 0 && stream_pays(a.Rc, a.Cc, a.P));
-    if (a.sdt == SB_F32 && (a.gray3 || stream)) {
-        if (a.gray3)
-            k_synthesis_stream<true><<<stream_grid(a.Rc, a.Cc, a.P), 32 * FS_WARPS, 0, st>>>(a);
+    if (a.gray3) {  // float32 only (checked by the caller)
+        k_synthesis_stream<true, float><<<stream_grid(a.Rc, a.Cc, a.P), 32 * FS_WARPS, 0, st>>>(a);
+        return cudaGetLastError();
+    }
+    if (stream) {
+        if (a.sdt == SB_F16)
+            launch_synthesis_stream<__half>(a, st);
+        else if (a.sdt == SB_BF16)
+            launch_synthesis_stream<__nv_bfloat16>(a, st);
         else
-            k_synthesis_stream<false><<<stream_grid(a.Rc, a.Cc, a.P), 32 * FS_WARPS, 0, st>>>(a);
+            launch_synthesis_stream<float>(a, st);
         return cudaGetLastError();
     }
     dim3 block(32, 8);
@@ -710,18 +737,33 @@ static void launch_final_t(const FinalArgs &a, bool mle, cudaStream_t st) {
         k_final<true, T, false><<<grid, block, 0, st>>>(a);
 }
 
+// MLE mode: the copy-pipelined kernel for every subband type
+template <class T>
 static void launch_final_async_mle(const FinalArgs &a, cudaStream_t st) {
     dim3 block(32, 8);
     dim3 grid((unsigned)((a.W + OT - 1) / OT), (unsigned)((a.H + OT - 1) / OT), (unsigned)a.C);
     if (a.compensated)
-        k_final_async<true><<<grid, block, 0, st>>>(a);
+        k_final_async<true, T><<<grid, block, 0, st>>>(a);
     else
-        k_final_async<false><<<grid, block, 0, st>>>(a);
+        k_final_async<false, T><<<grid, block, 0, st>>>(a);
+}
+
+template <class T>
+static void launch_final_stream(const FinalArgs &a, cudaStream_t st) {
+    if (a.accumulate)
+        k_final_stream<true, T><<<stream_grid(a.Rc, a.Cc, a.C * a.G), 32 * FS_WARPS, 0, st>>>(a);
+    else
+        k_final_stream<false, T><<<stream_grid(a.Rc, a.Cc, a.C * a.G), 32 * FS_WARPS, 0, st>>>(a);
 }
 
 cudaError_t launch_final(const FinalArgs &a, bool mle, cudaStream_t st) {
-    if (a.sdt == SB_F32 && mle) {
-        launch_final_async_mle(a, st);
+    if (mle) {
+        if (a.sdt == SB_F16)
+            launch_final_async_mle<__half>(a, st);
+        else if (a.sdt == SB_BF16)
+            launch_final_async_mle<__nv_bfloat16>(a, st);
+        else
+            launch_final_async_mle<float>(a, st);
         return cudaGetLastError();
     }
     if (a.pce) {  // float32 subbands only (checked by the caller)
@@ -731,11 +773,13 @@ cudaError_t launch_final(const FinalArgs &a, bool mle, cudaStream_t st) {
             k_final_pce<false><<<stream_grid(a.Rc, a.Cc, a.G), 32 * FS_WARPS, 0, st>>>(a);
         return cudaGetLastError();
     }
-    if (a.sdt == SB_F32 && stream_pays(a.Rc, a.Cc, a.C * a.G)) {
-        if (a.accumulate)
-            k_final_stream<true><<<stream_grid(a.Rc, a.Cc, a.C * a.G), 32 * FS_WARPS, 0, st>>>(a);
+    if (stream_pays(a.Rc, a.Cc, a.C * a.G)) {
+        if (a.sdt == SB_F16)
+            launch_final_stream<__half>(a, st);
+        else if (a.sdt == SB_BF16)
+            launch_final_stream<__nv_bfloat16>(a, st);
         else
-            k_final_stream<false><<<stream_grid(a.Rc, a.Cc, a.C * a.G), 32 * FS_WARPS, 0, st>>>(a);
+            launch_final_stream<float>(a, st);
         return cudaGetLastError();
     }
     if (a.sdt == SB_F16)

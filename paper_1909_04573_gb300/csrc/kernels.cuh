@@ -46,8 +46,7 @@ cudaError_t launch_analysis(const AnaArgs &a, bool level1, cudaStream_t st, int 
 constexpr int kAnaChoices = 3;
 // shrink: 0 strip where it applies (standard windows, width % 4 == 0), else tiled; 1 tiled
 constexpr int kShrinkChoices = 2;
-// synthesis (levels >= 2): 0 streaming where its grid fills the GPU, else tiled; 1 streaming
-// (float32 subbands; else tiled); 2 tiled
+// synthesis (levels >= 2): 0 streaming where its grid fills the GPU, else tiled; 1 streaming; 2 tiled
 constexpr int kSynChoices = 3;
 enum TuneKind : int { kTuneAnalysis = 0, kTuneShrink = 1, kTuneSynthesis = 2 };
 
