@@ -1050,6 +1050,25 @@ def main():
                                       "mode": "queries denoised on a second stream during the extraction "
                                               "(prnu_pce_images_prepare / _finish_async), one graph replay"}
 
+    # ---- extraction alone (accumulate + finalize of the fingerprint, no
+    # queries): its frame bytes against the copy peak
+    if use_graph:
+        def extract():
+            num.zero_()
+            den.zero_()
+            ctx.fingerprint_accumulate(frames, D_SDA, num, den)
+            ctx.fingerprint_finalize(num, den, flags)
+        g_ex = capture(None, fn=extract, profile=False)
+        ms_ex = timed(g_ex.replay, 1, 0) / args.steps
+        del g_ex
+        torch.cuda.synchronize()
+        P.prnu_profile_reset(ctx.ctx)
+        ex_gbps = step_bytes / (ms_ex / 1000.0) / 1e9
+        line["extraction"] = {"value": frames_per_step / (ms_ex / 1000.0), "unit": UNIT, "ms_per_step": ms_ex,
+                              "frame_GBps": ex_gbps, "frame_frac_of_peak": ex_gbps / hbm,
+                              "mode": "accumulate (SDA-50 sums, denoise, MLE) + finalize (grey, zero-mean, DFT "
+                                      "Wiener) of the step's fingerprint, without the queries; one graph replay"}
+
     # ---- per-frame (ALL-FE) comparison: d = 1, 1000 denoise passes x 3 channels
     if not args.no_perframe:
         ms_pf = timed(lambda: step(d=1, images_per_pass=100), 2, 1)

@@ -532,7 +532,7 @@ __device__ __forceinline__ double block_sum_d(double v, double *sh) {
 // staged (cp.async) into one of two buffers while the previous ones are
 // transformed in the work buffer and the other.
 template <int G, int MS>
-__global__ void __launch_bounds__(CT) k_corr_rows(const float2 *__restrict__ Zall, int H, int W, int ld, int r,
+__global__ void __launch_bounds__(CT, 3) k_corr_rows(const float2 *__restrict__ Zall, int H, int W, int ld, int r,
                                                   FftSteps p, const float2 *__restrict__ twg, double *part_e,
                                                   float *part_v, long long *part_i, float *c0) {
     extern __shared__ float2 sm[];
@@ -647,12 +647,16 @@ cudaError_t smem_attr(size_t bytes) {
 }
 
 int rows_per_block(int M) { return M <= 1024 ? 4 : 2; }
+// the inverse row pass takes two rows per block, so that three of its blocks
+// (80 registers, 256 threads) fit an SM's shared memory
+constexpr int kInvRows = 2;
 // twiddles (M) and three buffers of G padded rows
-size_t rows_buf(int M) { return (size_t)rows_per_block(M) * padded_len(M + 1); }
+size_t rows_buf(int M, int G) { return (size_t)G * padded_len(M + 1); }
 // (k_corr_rows reuses its work buffer as 3328 bytes of reduction scratch)
-size_t rows_smem(int M) {
-    return std::max(((size_t)M + 3 * rows_buf(M)) * sizeof(float2), (size_t)M * sizeof(float2) + 3328);
+size_t rows_smem(int M, int G) {
+    return std::max(((size_t)M + 3 * rows_buf(M, G)) * sizeof(float2), (size_t)M * sizeof(float2) + 3328);
 }
+size_t rows_smem(int M) { return rows_smem(M, rows_per_block(M)); }
 size_t cols_smem(int H, int tc) { return ((size_t)H + 2 * 2 * tc * (size_t)padded_len(H)) * sizeof(float2); }
 // widest column tile whose block still fits twice per SM, else once
 int cols_tile(int H) {
@@ -728,14 +732,15 @@ cudaError_t launch_corr_fft(const float *XY, float2 *F, float2 *tw, int n, int H
         if (tc == 2) return launch<k_corr_columns<2, 0, CTW>, CTW>(grid, cs, st, F, n, H, Wh, ld, ph, twc);
         return launch<k_corr_columns<1, 0, CTW>, CTW>(grid, cs, st, F, n, H, Wh, ld, ph, twc);
     }
-    const dim3 grid((unsigned)std::min(nb, (H + G - 1) / G), n);
+    const dim3 grid((unsigned)corr_rows_blocks(H, W, nb), n);
+    const size_t ri = rows_smem(M, kInvRows);
     const float2 *Fc = F, *twc = tw;
     if (M == kStaticM)
-        return launch<k_corr_rows<4, kStaticM>>(grid, rs, st, Fc, H, W, ld, r, pm, twc, part_e, part_v, part_i, c0);
-    if (G == 4) return launch<k_corr_rows<4, 0>>(grid, rs, st, Fc, H, W, ld, r, pm, twc, part_e, part_v, part_i, c0);
-    return launch<k_corr_rows<2, 0>>(grid, rs, st, Fc, H, W, ld, r, pm, twc, part_e, part_v, part_i, c0);
+        return launch<k_corr_rows<kInvRows, kStaticM>>(grid, ri, st, Fc, H, W, ld, r, pm, twc, part_e, part_v, part_i,
+                                                        c0);
+    return launch<k_corr_rows<kInvRows, 0>>(grid, ri, st, Fc, H, W, ld, r, pm, twc, part_e, part_v, part_i, c0);
 }
 
-int corr_rows_blocks(int H, int W, int nb) { return std::min(nb, (H + rows_per_block(W / 2) - 1) / rows_per_block(W / 2)); }
+int corr_rows_blocks(int H, int W, int nb) { return std::min(nb, (H + kInvRows - 1) / kInvRows); }
 
 }  // namespace prnu

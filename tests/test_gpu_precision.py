@@ -104,8 +104,10 @@ def test_reduced_precision_subbands(ctx, data, dtype):
 
 # bounds on the PCE error of reduced-precision subband storage (fingerprint
 # and query residual both stored at that precision), relative to the oracle's
-# PCE; the float32 path keeps the parity tolerance of 0.1 %.
-PCE_BOUNDS = {P.PRNU_DTYPE_F32: 1e-3, P.PRNU_DTYPE_F16: 5e-3, P.PRNU_DTYPE_BF16: 3e-2}
+# PCE; the float32 path keeps the parity tolerance of 0.1 %.  Measured on
+# GB300 for this data: float32 4.3e-8, float16 1.2e-5, bfloat16 1.1e-5 (at the
+# 4032x3024 precision workload: 6.7e-8, 5.3e-5, 7.6e-4).
+PCE_BOUNDS = {P.PRNU_DTYPE_F32: 1e-3, P.PRNU_DTYPE_F16: 2e-4, P.PRNU_DTYPE_BF16: 5e-4}
 
 
 @pytest.fixture(scope="module")
