@@ -26,9 +26,6 @@
  * - Limits: 16 <= H, W; H, W <= 16384; C in {1, 3}; 1 <= levels <= 6 with
  *   H, W >= 2^levels; windows odd in [1, 9]; 1 <= d <= m; d <= 65793 (so that
  *   a group sum of uint8 frames is an exact float32 integer).
- * - A context holds one side stream and its events (used by the host-frame
- *   accumulate and the pipelined accumulate): issue the calls of one context
- *   from one host thread at a time; use one context per thread otherwise.
  */
 #ifndef PRNU_H
 #define PRNU_H

@@ -17,12 +17,6 @@
 // The correlation plane itself is never written.  All transforms are
 // unnormalised (the result is H*W times the correlation), like cuFFT's.
 //
-// The half spectra between the passes are stored column-major: bin (y, k) of
-// plane p at p*(W/2+1)*ldh + k*ldh + y, ldh = H rounded up to 4.  The column
-// pass then reads and writes contiguous columns, and the row passes, which
-// handle four (forward) or two (inverse) consecutive rows per block, move
-// 32- or 16-byte pieces of each column.
-//
 // Each 1-D transform is a Stockham autosort FFT over the factors 8, 4, 2, 9,
 // 15, 3, 5, 7 of its length (9 and 15 as register-resident composite
 // butterflies); one pass per factor, ping-ponging between two shared
@@ -431,7 +425,7 @@ __global__ void k_twiddles(float2 *tw, int M, int H) {
 // transformed in the other two.
 template <int G, int MS, int NT>
 __global__ void __launch_bounds__(NT) k_rfft_rows(const float *__restrict__ x, float2 *__restrict__ out,
-                                                  long long nrows, int H, int W, int ldh, FftSteps p,
+                                                  long long nrows, int W, int ldo, FftSteps p,
                                                   const float2 *__restrict__ twg) {
     extern __shared__ float2 sm[];
     const int M = MS > 0 ? MS : W >> 1;
@@ -469,9 +463,7 @@ __global__ void __launch_bounds__(NT) k_rfft_rows(const float *__restrict__ x, f
             const float2 zk = Z[at<G>(k == M ? 0 : k, g)];
             const float2 zc = cconj(Z[at<G>(k == 0 ? 0 : M - k, g)]);
             const float2 s = cadd(zk, zc), wd = cmul(__ldg(twh + k), csub(zk, zc));
-            const long long pl = r / H, y = r - pl * H;  // plane, row
-            if (PRNU_DCHECK(y < ldh, y))
-                out[pl * (M + 1) * ldh + (long long)k * ldh + y] = make_float2(0.5f * (s.x + wd.y), 0.5f * (s.y - wd.x));
+            if (PRNU_DCHECK(k < ldo, k)) out[r * ldo + k] = make_float2(0.5f * (s.x + wd.y), 0.5f * (s.y - wd.x));
         }
         __syncthreads();  // cur / scr are restaged from the next iteration on
     }
@@ -482,20 +474,20 @@ __global__ void __launch_bounds__(NT) k_rfft_rows(const float *__restrict__ x, f
 // of X^_q and Y^_q (F + q*H*ld and F + (n+q)*H*ld, pitch ld), Z = conj(X^) Y^
 // with Z(0, 0) = 0, inverse column FFT of Z, written over X^_q.
 template <int TC, int HS, int NT>
-__global__ void __launch_bounds__(NT) k_corr_columns(float2 *F, int n, int H, int Wh, int ldh, FftSteps p,
+__global__ void __launch_bounds__(NT) k_corr_columns(float2 *F, int n, int H, int Wh, int ld, FftSteps p,
                                                      const float2 *__restrict__ twg) {
     extern __shared__ float2 sm[];
     constexpr int G = 2 * TC;
     float2 *tw = sm, *A = sm + H, *B = A + G * padded_len(H);
     const int q = blockIdx.y, c0 = blockIdx.x * TC;
-    float2 *FX = F + (long long)q * Wh * ldh;
-    const float2 *FY = F + (long long)(n + q) * Wh * ldh;
+    float2 *FX = F + (long long)q * H * ld;
+    const float2 *FY = F + (long long)(n + q) * H * ld;
     load_table(tw, twg, H);
     for (int u = threadIdx.x; u < G * H; u += blockDim.x) {
         const int s = u % G, y = u / G, c = c0 + (s < TC ? s : s - TC);
         const float2 *src = s < TC ? FX : FY;
-        if (c < Wh && PRNU_DCHECK(y < ldh && q < n, y))
-            cp_async8(A + at<G>(y, s), src + (long long)c * ldh + y);
+        if (c < Wh && PRNU_DCHECK(c < ld && q < n, c))
+            cp_async8(A + at<G>(y, s), src + (long long)y * ld + c);
         else
             A[at<G>(y, s)] = make_float2(0.f, 0.f);
     }
@@ -517,7 +509,7 @@ __global__ void __launch_bounds__(NT) k_corr_columns(float2 *F, int n, int H, in
     const float2 *Z = fft_any<HS, TC, TC, true, NT>(T, S, p, tw);
     for (int u = threadIdx.x; u < TC * H; u += blockDim.x) {
         const int s = u % TC, y = u / TC, c = c0 + s;
-        if (c < Wh && PRNU_DCHECK(y < ldh, y)) FX[(long long)c * ldh + y] = Z[at<TC>(y, s)];
+        if (c < Wh && PRNU_DCHECK(c < ld, c)) FX[(long long)y * ld + c] = Z[at<TC>(y, s)];
     }
 }
 
@@ -540,7 +532,7 @@ __device__ __forceinline__ double block_sum_d(double v, double *sh) {
 // staged (cp.async) into one of two buffers while the previous ones are
 // transformed in the work buffer and the other.
 template <int G, int MS>
-__global__ void __launch_bounds__(CT, 3) k_corr_rows(const float2 *__restrict__ Zall, int H, int W, int ldh, int r,
+__global__ void __launch_bounds__(CT, 3) k_corr_rows(const float2 *__restrict__ Zall, int H, int W, int ld, int r,
                                                   FftSteps p, const float2 *__restrict__ twg, double *part_e,
                                                   float *part_v, long long *part_i, float *c0) {
     extern __shared__ float2 sm[];
@@ -550,16 +542,17 @@ __global__ void __launch_bounds__(CT, 3) k_corr_rows(const float2 *__restrict__ 
     const int BS = G * padded_len(Wh);
     float2 *const S0 = Wk + BS;  // two staging buffers of BS (G raw rows of Wh bins)
     const int q = blockIdx.y;
-    const float2 *Z = Zall + (long long)q * Wh * ldh;
+    const float2 *Z = Zall + (long long)q * H * ld;
     load_table(tw, twg, M);
     auto stage = [&](int y0, float2 *dst) {
-        // consecutive threads take the G rows of one column, then the next column
-        for (int u = threadIdx.x; u < G * Wh; u += blockDim.x) {
-            const int g = u % G, k = u / G, y = y0 + g;
-            if (y < H && PRNU_DCHECK(y < ldh, y))
-                cp_async8(dst + g * Wh + k, Z + (long long)k * ldh + y);
-            else
-                dst[g * Wh + k] = make_float2(0.f, 0.f);
+        for (int g = 0; g < G; ++g) {
+            const int y = y0 + g;
+            for (int k = threadIdx.x; k < Wh; k += blockDim.x) {
+                if (y < H && PRNU_DCHECK(k < ld, k))
+                    cp_async8(dst + g * Wh + k, Z + (long long)y * ld + k);
+                else
+                    dst[g * Wh + k] = make_float2(0.f, 0.f);
+            }
         }
     };
     double acc = 0.0;
@@ -695,8 +688,7 @@ bool corr_fft_supported(int H, int W) {
 }
 
 size_t corr_twiddle_count(int H, int W) { return (size_t)(W / 2) * 2 + 1 + H; }
-int corr_col_pitch(int H) { return (H + 3) / 4 * 4; }
-long long corr_plane(int H, int W) { return (long long)(W / 2 + 1) * corr_col_pitch(H); }
+int corr_pitch(int W) { return (W / 2 + 1 + 3) / 4 * 4; }
 
 namespace {
 template <auto Kern, int NT = CT, typename... Args>
@@ -714,7 +706,7 @@ constexpr int kStaticM = 960, kStaticH = 1080;
 cudaError_t launch_corr_fft(const float *XY, float2 *F, float2 *tw, int n, int H, int W, int r, int nb,
                             double *part_e, float *part_v, long long *part_i, float *c0, int sms, cudaStream_t st,
                             int stage) {
-    const int M = W / 2, Wh = M + 1, ld = corr_col_pitch(H);
+    const int M = W / 2, Wh = M + 1, ld = corr_pitch(W);
     FftSteps pm, ph;
     if (!fft_steps(M, &pm) || !fft_steps(H, &ph)) return cudaErrorInvalidValue;
     const int G = rows_per_block(M);
@@ -725,11 +717,9 @@ cudaError_t launch_corr_fft(const float *XY, float2 *F, float2 *tw, int n, int H
         const long long nrows = 2LL * n * H;
         const dim3 grid((unsigned)std::min<long long>((nrows + G - 1) / G, (long long)sms * (rs <= 113 * 1024 ? 2 : 1)));
         if (M == kStaticM)
-            return launch<k_rfft_rows<4, kStaticM, CTW>, CTW>(grid, rs, st, XY, F, nrows, H, W, ld, pm,
-                                                               (const float2 *)tw);
-        if (G == 4)
-            return launch<k_rfft_rows<4, 0, CTW>, CTW>(grid, rs, st, XY, F, nrows, H, W, ld, pm, (const float2 *)tw);
-        return launch<k_rfft_rows<2, 0, CTW>, CTW>(grid, rs, st, XY, F, nrows, H, W, ld, pm, (const float2 *)tw);
+            return launch<k_rfft_rows<4, kStaticM, CTW>, CTW>(grid, rs, st, XY, F, nrows, W, ld, pm, (const float2 *)tw);
+        if (G == 4) return launch<k_rfft_rows<4, 0, CTW>, CTW>(grid, rs, st, XY, F, nrows, W, ld, pm, (const float2 *)tw);
+        return launch<k_rfft_rows<2, 0, CTW>, CTW>(grid, rs, st, XY, F, nrows, W, ld, pm, (const float2 *)tw);
     }
     if (stage == 1) {
         const int tc = cols_tile(H);

@@ -143,8 +143,7 @@ bool fft_steps(int L, FftSteps *p);
 // shared-memory limits of the kernels
 bool corr_fft_supported(int H, int W);
 size_t corr_twiddle_count(int H, int W);  // float2 entries
-int corr_col_pitch(int H);                // complex bins per stored spectrum column (H, padded to 4)
-long long corr_plane(int H, int W);       // complex bins per stored half-spectrum plane
+int corr_pitch(int W);                    // complex bins per half-spectrum row (W/2 + 1, padded to 4)
 int corr_rows_blocks(int H, int W, int nb);
 // stage 0: twiddles + row FFTs of the 2n planes XY into F; 1: column FFTs,
 // cross spectrum and inverse column FFTs (in place over the X half of F);

@@ -369,7 +369,7 @@ prnu_status fft_layout(prnu_ctx *ctx, int H, int W, int n, FftLayout *out) {
     f.nb = (int)std::min<size_t>(256, std::max<size_t>(1, hw / (256 * 16)));
     f.nbm = f.nb;
     f.own_fft = corr_fft_supported(H, W);
-    const size_t nh_pce = f.own_fft ? (size_t)corr_plane(H, W) : nh;  // padded columns for the own FFT
+    const size_t nh_pce = f.own_fft ? (size_t)H * corr_pitch(W) : nh;  // padded rows for the own FFT
     f.cplx = take(2 * (size_t)std::max(n, 1) * std::max(nh, nh_pce) * sizeof(cufftComplex));
     f.real = take(2 * (size_t)std::max(n, 1) * hw * sizeof(float));
     f.colmean = take((size_t)W * sizeof(double));
