@@ -78,9 +78,10 @@ typedef struct {
     int compensated; /* 0: num/den are float32 [C][H][W];  1: compensated sums, num and den each point to
                         [2][C][H][W] float32 (the float-float pair hi, then lo, both zero-initialised by the
                         caller), accumulated with TwoSum error terms; finalize then reads both parts */
-    int sda_blocks_per_sm; /* 0 (default): the SDA group-sum kernel fills every SM; 1..32: at most that many
-                              of its blocks per SM, leaving room for kernels that run concurrently on other
-                              streams (e.g. prnu_pce_images_prepare or a pipelined accumulate's denoising) */
+    int sda_blocks_per_sm; /* 0 (default): the SDA group-sum kernel fills every SM (2 blocks per SM when it
+                              reads page-locked host frames); 1..32: at most that many of its blocks per SM,
+                              leaving room for kernels that run concurrently on other streams (e.g.
+                              prnu_pce_images_prepare or a pipelined accumulate's denoising) */
     int pipeline_passes;   /* prnu_fingerprint_accumulate with device frames: 0 or 1 (default): one stream,
                               each pass's group sums then its denoising; n >= 2: the groups are split into n
                               passes (or more, if two pass layouts of ceil(groups/n) groups do not fit the

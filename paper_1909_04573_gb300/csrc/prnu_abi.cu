@@ -808,7 +808,8 @@ prnu_status prnu_fingerprint_accumulate_host(prnu_ctx *ctx, const uint8_t *host_
                                            std::max(1, (g + 3) / 4), params->dtype);
             if (Gp2 >= 1 && g > Gp2)
                 return accumulate_pipelined(ctx, dev, m, H, W, C, frame_stride, row_pitch, d, g, Gp2, *params, win,
-                                            num, den, static_cast<char *>(ws), 2, st);
+                                            num, den, static_cast<char *>(ws),
+                                            params->sda_blocks_per_sm > 0 ? params->sda_blocks_per_sm : 2, st);
             const int Gp = groups_fitting(H, W, C, params->levels, ws_bytes, g, params->dtype);
             if (Gp < 1) return check_ws(ws, ws_bytes, make_layout(H, W, C, params->levels, true, params->dtype).end);
             for (int g0 = 0; g0 < g; g0 += Gp)

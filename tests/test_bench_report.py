@@ -37,3 +37,28 @@ def test_forced_dominant_kernel():
 def test_fallback_peak_without_measured_file(monkeypatch, tmp_path):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.peaks() == (6800.0, "fallback")
+
+
+def test_headline_parity_host_logic(monkeypatch):
+    """The parity block of the video bench: relative L2 of num / den / K and the
+    max-abs of the group-0 residual against the oracle, pass / fail at the
+    stated tolerances (small frames; the oracle computes both sides here, one
+    of them perturbed)."""
+    import numpy as np
+
+    import oracle as O
+    from paper_1909_04573_gb300 import synth
+    monkeypatch.setattr(bench, "D_SDA", 4)
+    fr = synth.frames(synth.Camera(H=32, W=48, C=3, camera_id=77), 8).numpy()
+    onum, oden = O.fingerprint_accumulate(fr, 4)
+    res0 = O.residual(O.sda_average(fr[:4], 4)[0])
+    good = {"num": onum.astype(np.float32), "den": oden.astype(np.float32),
+            "K": O.fingerprint_finalize(onum, oden).astype(np.float32), "res0": res0.astype(np.float32)}
+    out = bench.headline_parity(good, fr, onum, oden)
+    assert out["pass"] and out["num_rel_l2"] < 1e-6 and out["residual_max_abs"] < 1e-4
+    bad = dict(good, res0=good["res0"] + 2e-3)             # a residual off by more than 1e-3
+    out = bench.headline_parity(bad, fr, onum, oden)
+    assert not out["pass"] and out["residual_max_abs"] > 1e-3
+    bad = dict(good, num=good["num"] * (1 + 1e-4))          # sums off by 1e-4 relative
+    out = bench.headline_parity(bad, fr, onum, oden)
+    assert not out["pass"] and abs(out["num_rel_l2"] - 1e-4) < 1e-5

@@ -135,6 +135,43 @@ def test_multipass_accumulate_and_determinism(ctx):
     assert _rel(n2, n1) <= 1e-6 and _rel(d2, d1) <= 1e-6
 
 
+@pytest.mark.parametrize("passes", [2, 3, 8])
+def test_pipelined_accumulate_equals_one_stream_and_replays(ctx, passes):
+    """prnu_params.pipeline_passes: the group sums of the next pass on the
+    context's side stream beside the current pass's denoising (two pass
+    layouts, events); eager and captured in a CUDA graph, it gives the sums of
+    the one-stream call."""
+    fr = torch.as_tensor(_frames(64, 96, 3, 37, seed=8)).cuda()
+    C, H, W = 3, 64, 96
+    ref_n, ref_d = torch.zeros((C, H, W), device="cuda"), torch.zeros((C, H, W), device="cuda")
+    ctx.fingerprint_accumulate(fr, 4, ref_n, ref_d)
+    prm = P.default_params(pipeline_passes=passes)
+    num, den = torch.zeros_like(ref_n), torch.zeros_like(ref_d)
+    ctx.fingerprint_accumulate(fr, 4, num, den, params=prm)
+    torch.cuda.synchronize()
+    assert _rel(num.cpu().numpy(), ref_n.cpu().numpy()) <= 1e-6
+    assert torch.equal(den, ref_d)
+    f, m, Hh, Ww, Cc, fs, rp = ctx._frames_geometry(fr)
+    nb = P.prnu_workspace_size(ctx.ctx, H, W, C, prm, 10)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            num.zero_()
+            den.zero_()
+            P.prnu_fingerprint_accumulate(ctx.ctx, f.data_ptr(), m, H, W, C, fs, rp, 4, prm, num.data_ptr(),
+                                          den.data_ptr(), ws.data_ptr(), nb, side.cuda_stream)
+    torch.cuda.current_stream().wait_stream(side)
+    for _ in range(2):
+        num.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        assert _rel(num.cpu().numpy(), ref_n.cpu().numpy()) <= 1e-6
+        assert torch.equal(den, ref_d)
+
+
 @pytest.mark.parametrize("pinned", [True, False])
 def test_accumulate_host_equals_device(ctx, pinned):
     """Page-locked frames are read in place (zero copy), pageable ones are
