@@ -624,6 +624,207 @@ __global__ void __launch_bounds__(CT, 3) k_corr_rows(const float2 *__restrict__ 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-per-row forms of the two row passes for rows of 1920 samples (M = 960
+// complex points, 960 = 32 x 30).  Lane n1 takes the 30-point DFT of
+// z[n1 + 32 n2] (n2 = 0..29) in registers (radix 2 over two 15-point DFTs,
+// those by the prime-factor map) and multiplies it by w_960^{n1 k2}; one
+// transpose through the warp's own shared buffer; lane k2 (0..29) then takes
+// the 32-point DFT (8 x 4) over n1, which gives Z[k2 + 30 k1].  A warp owns
+// its row and synchronises only with itself: no block barrier, one shared-
+// memory exchange per transform instead of three Stockham passes.
+constexpr int RM = 960, RP = 32, RQ = 30;  // M = RP * RQ
+constexpr int RTS = RP + 1;                 // transpose row stride (float2): at most 2-way conflicts
+constexpr int RBUF = RQ * RTS;              // 990 float2 per warp (also holds the 960 results)
+
+__device__ __forceinline__ float2 twm(const float2 *__restrict__ tw, int i) { return __ldg(tw + i); }  // w_960^i
+
+// 30-point DFT (forward) of v[0..29] in place
+__device__ __forceinline__ void dft30(float2 *v, const float2 *__restrict__ tw) {
+    float2 e[15], o[15];
+#pragma unroll
+    for (int j = 0; j < 15; ++j) {
+        e[j] = v[2 * j];
+        o[j] = v[2 * j + 1];
+    }
+    Dft<15>::run(e);
+    Dft<15>::run(o);
+#pragma unroll
+    for (int k = 0; k < 15; ++k) {
+        const float2 t = k == 0 ? o[0] : cmul(o[k], twm(tw, 32 * k));  // w_30^k = w_960^{32 k}
+        v[k] = cadd(e[k], t);
+        v[k + 15] = csub(e[k], t);
+    }
+}
+
+// 32-point DFT (forward) of u[0..31] in place: 8 x 4
+__device__ __forceinline__ void dft32(float2 *u, const float2 *__restrict__ tw) {
+    float2 t[8][4];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) t[b][j] = u[b + 8 * j];
+        Dft<4>::run(t[b]);
+#pragma unroll
+        for (int k2 = 1; k2 < 4; ++k2)
+            if (b) t[b][k2] = cmul(t[b][k2], twm(tw, 30 * b * k2));  // w_32^{b k2} = w_960^{30 b k2}
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) {
+        float2 sv[8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) sv[b] = t[b][k2];
+        Dft<8>::run(sv);
+#pragma unroll
+        for (int k1 = 0; k1 < 8; ++k1) u[k2 + 4 * k1] = sv[k1];
+    }
+}
+
+// The 960-point transform of a warp's row, lane n1 holding v[n2] = z[n1 + 32 n2]
+// (unnormalised; INV: exponent sign +1, as conj(DFT(conj z))); the result
+// Z[0..959] is left in buf, visible to the whole warp.
+template <bool INV>
+__device__ __forceinline__ void fft960_warp(float2 *v, float2 *buf, const float2 *__restrict__ tw, int lane) {
+    if (INV) {
+#pragma unroll
+        for (int n2 = 0; n2 < RQ; ++n2) v[n2] = cconj(v[n2]);
+    }
+    dft30(v, tw);
+#pragma unroll
+    for (int k2 = 0; k2 < RQ; ++k2) buf[k2 * RTS + lane] = (k2 && lane) ? cmul(v[k2], twm(tw, lane * k2)) : v[k2];
+    __syncwarp();
+    float2 u[RP];
+    if (lane < RQ) {
+#pragma unroll
+        for (int n1 = 0; n1 < RP; ++n1) u[n1] = buf[lane * RTS + n1];
+    }
+    __syncwarp();
+    if (lane < RQ) {
+        dft32(u, tw);
+#pragma unroll
+        for (int k1 = 0; k1 < RP; ++k1) buf[lane + RQ * k1] = INV ? cconj(u[k1]) : u[k1];
+    }
+    __syncwarp();
+}
+
+// Forward row pass, rows of 2 * 960 real samples: half spectra of 961 bins
+// (pitch ldo), each warp a row at a time.  Bounded to 128 registers (four
+// blocks per SM; a few spilled values): 0.19 ms per video step against
+// 0.27 ms at 168 registers and three blocks.
+template <int NW>
+__global__ void __launch_bounds__(32 * NW, 4) k_rfft_rows_w(const float *__restrict__ x, float2 *__restrict__ out,
+                                                         long long nrows, int ldo, const float2 *__restrict__ twg) {
+    __shared__ __align__(16) float2 sbuf[NW][RBUF];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float2 *buf = sbuf[warp];
+    const float2 *__restrict__ twh = twg + RM;  // w_1920^k, k <= 960
+    for (long long r = (long long)blockIdx.x * NW + warp; r < nrows; r += (long long)gridDim.x * NW) {
+        const float2 *z = reinterpret_cast<const float2 *>(x + r * (2 * RM));
+        float2 v[RQ];
+#pragma unroll
+        for (int n2 = 0; n2 < RQ; ++n2) v[n2] = __ldg(z + lane + RP * n2);
+        fft960_warp<false>(v, buf, twg, lane);
+        // split step: X_k = (Z_k + conj Z_{M-k}) / 2 - i w_W^k (Z_k - conj Z_{M-k}) / 2
+        for (int k = lane; k <= RM; k += 32) {
+            const float2 zk = buf[k == RM ? 0 : k];
+            const float2 zc = cconj(buf[k == 0 ? 0 : RM - k]);
+            const float2 sm2 = cadd(zk, zc), wd = cmul(__ldg(twh + k), csub(zk, zc));
+            if (PRNU_DCHECK(k < ldo, k)) out[r * ldo + k] = make_float2(0.5f * (sm2.x + wd.y), 0.5f * (sm2.y - wd.x));
+        }
+        __syncwarp();  // buf is rewritten by the warp's next row
+    }
+}
+
+// Inverse row pass and PCE partials (as k_corr_rows), each warp a row at a
+// time; three blocks per SM (168 registers, no spill: 0.15 ms per video step
+// against 0.17 ms under the 128-register bound).
+template <int NW>
+__global__ void __launch_bounds__(32 * NW, 3) k_corr_rows_w(const float2 *__restrict__ Zall, int H, int W, int ld, int r,
+                                                         const float2 *__restrict__ twg, double *part_e,
+                                                         float *part_v, long long *part_i, float *c0) {
+    __shared__ __align__(16) float2 sbuf[NW][RBUF];
+    __shared__ double she[NW];
+    __shared__ float shv[NW];
+    __shared__ long long shi[NW];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float2 *buf = sbuf[warp];
+    const int q = blockIdx.y;
+    const float2 *Z = Zall + (long long)q * H * ld;
+    const float2 *__restrict__ twh = twg + RM;
+    double acc = 0.0;
+    float bv = -__int_as_float(0x7f800000);
+    long long bi = LLONG_MAX;
+    for (int y = blockIdx.x * NW + warp; y < H; y += gridDim.x * NW) {
+        const float2 *row = Z + (long long)y * ld;
+        // split step: Z'_k = E_k + i O_k, E_k = X_k + conj X_{M-k},
+        // O_k = (X_k - conj X_{M-k}) e^{+2 pi i k / W}  (gives W * x after the inverse)
+        float2 v[RQ];
+#pragma unroll
+        for (int n2 = 0; n2 < RQ; ++n2) {
+            const int k = lane + RP * n2;
+            if (!PRNU_DCHECK(RM - k < ld, k)) continue;
+            const float2 a = __ldg(row + k), b = cconj(__ldg(row + RM - k));
+            const float2 e = cadd(a, b), o = cmul(csub(a, b), cconj(__ldg(twh + k)));
+            v[n2] = make_float2(e.x - o.y, e.y + o.x);
+        }
+        fft960_warp<true>(v, buf, twg, lane);
+        float fe = 0.f;
+        const bool ynear = min(y, H - y) <= r;
+        for (int m = lane; m < RM; m += 32) {
+            const float2 val = buf[m];  // C(y, 2m), C(y, 2m + 1)
+            const int x0 = 2 * m, x1 = 2 * m + 1;
+            if (!(ynear && min(x0, W - x0) <= r)) fe = __fmaf_rn(val.x, val.x, fe);
+            if (!(ynear && min(x1, W - x1) <= r)) fe = __fmaf_rn(val.y, val.y, fe);
+            const long long i0 = (long long)y * W + x0;
+            if (val.x > bv || (val.x == bv && i0 < bi)) {
+                bv = val.x;
+                bi = i0;
+            }
+            if (val.y > bv || (val.y == bv && i0 + 1 < bi)) {
+                bv = val.y;
+                bi = i0 + 1;
+            }
+            if (y == 0 && m == 0) c0[q] = val.x;
+        }
+        acc += (double)fe;
+        __syncwarp();  // buf is rewritten by the warp's next row
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_down_sync(0xffffffffu, acc, o);
+        const float ov = __shfl_down_sync(0xffffffffu, bv, o);
+        const long long oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) {
+            bv = ov;
+            bi = oi;
+        }
+    }
+    if (lane == 0) {
+        she[warp] = acc;
+        shv[warp] = bv;
+        shi[warp] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double e = 0.0;
+        float v0 = shv[0];
+        long long i0 = shi[0];
+        for (int w = 0; w < NW; ++w) {
+            e += she[w];
+            if (shv[w] > v0 || (shv[w] == v0 && shi[w] < i0)) {
+                v0 = shv[w];
+                i0 = shi[w];
+            }
+        }
+        const long long o = (long long)q * gridDim.x + blockIdx.x;
+        part_e[o] = e;
+        part_v[o] = v0;
+        part_i[o] = i0;
+    }
+}
+
+constexpr int kRowWarps = 4;  // warps (rows in flight) per block of the warp-per-row passes
+
 // Opts each kernel instance, once per device, into the largest dynamic shared
 // memory the device allows next to its static shared memory (a host-side
 // attribute; each launch still asks only for what it uses, checked against
@@ -716,6 +917,11 @@ cudaError_t launch_corr_fft(const float *XY, float2 *F, float2 *tw, int n, int H
         k_twiddles<<<(nt + 255) / 256, 256, 0, st>>>(tw, M, H);
         const long long nrows = 2LL * n * H;
         const dim3 grid((unsigned)std::min<long long>((nrows + G - 1) / G, (long long)sms * (rs <= 113 * 1024 ? 2 : 1)));
+        if (M == RM) {
+            const dim3 gw((unsigned)std::min<long long>((nrows + kRowWarps - 1) / kRowWarps, (long long)sms * 8));
+            k_rfft_rows_w<kRowWarps><<<gw, 32 * kRowWarps, 0, st>>>(XY, F, nrows, ld, (const float2 *)tw);
+            return cudaGetLastError();
+        }
         if (M == kStaticM)
             return launch<k_rfft_rows<4, kStaticM, CTW>, CTW>(grid, rs, st, XY, F, nrows, W, ld, pm, (const float2 *)tw);
         if (G == 4) return launch<k_rfft_rows<4, 0, CTW>, CTW>(grid, rs, st, XY, F, nrows, W, ld, pm, (const float2 *)tw);
@@ -735,12 +941,19 @@ cudaError_t launch_corr_fft(const float *XY, float2 *F, float2 *tw, int n, int H
     const dim3 grid((unsigned)corr_rows_blocks(H, W, nb), n);
     const size_t ri = rows_smem(M, kInvRows);
     const float2 *Fc = F, *twc = tw;
+    if (M == RM) {
+        k_corr_rows_w<kRowWarps><<<grid, 32 * kRowWarps, 0, st>>>(Fc, H, W, ld, r, twc, part_e, part_v, part_i, c0);
+        return cudaGetLastError();
+    }
     if (M == kStaticM)
         return launch<k_corr_rows<kInvRows, kStaticM>>(grid, ri, st, Fc, H, W, ld, r, pm, twc, part_e, part_v, part_i,
                                                         c0);
     return launch<k_corr_rows<kInvRows, 0>>(grid, ri, st, Fc, H, W, ld, r, pm, twc, part_e, part_v, part_i, c0);
 }
 
-int corr_rows_blocks(int H, int W, int nb) { return std::min(nb, (H + kInvRows - 1) / kInvRows); }
+int corr_rows_blocks(int H, int W, int nb) {
+    const int rows = W / 2 == RM ? kRowWarps : kInvRows;  // rows per block iteration
+    return std::min(nb, (H + rows - 1) / rows);
+}
 
 }  // namespace prnu
