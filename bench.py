@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="video config: time eager launches, not a CUDA graph")
+    ap.add_argument("--sda-fusion", type=int, default=0,
+                    help="video config: prnu_params.sda_fusion of the fingerprint (0: fused group sums + level-1 "
+                         "analysis where it applies, -1: separate kernels, n >= 1: fused with n row strips)")
     ap.add_argument("--frames", type=int, default=M_FRAMES,
                     help="frames of the workload (default 1000; smaller values are for profiling captures)")
     ap.add_argument("--config", default="video", choices=["video", "precision", "depth", "batch", "grad"],
@@ -84,6 +87,7 @@ FP32_LANES_PER_SM = 128
 
 # profiler name -> kernel symbol in the ncu captures (profiles/)
 NCU_NAME = {"shrink": "k_shrink_strip<0, float>", "sda_sum": "k_sda_sum<3, 1024, 0>",
+            "sda_dwt": "k_sda_dwt<3, 2, float>",
             "analysis_l1": "k_analysis_stream<1, float, 32, 2>", "analysis": "k_analysis<0, float>",
             "synthesis": "k_synthesis_stream<0, float>", "final_mle": "k_final_async<0, float>",
             "final_pce": "k_final_pce<1>", "pce_fft_rows": "k_rfft_rows_w<4>",
@@ -194,12 +198,13 @@ def kernel_report(prof, steps, ck, dev, dominant=None):
             roof = {"kernel": dom, "bound": "hbm", "achieved": gbps, "peak": hbm, "unit": "GB/s",
                     "frac": gbps / hbm, "peak_kind": f"{peak_kind} copy bandwidth", "traffic": traffic,
                     "bytes_per_launch": dom_b / dom_n, "launches": dom_n, "ms_per_launch": dom_t / dom_n}
-    sda_roof = None
-    if "sda_sum" in own and own["sda_sum"][1] > 0:
-        n_, t_, b_ = own["sda_sum"]
+    sda_roof = None  # the group-sum kernel: fused with the level-1 analysis, or alone
+    sk = next((k for k in ("sda_dwt", "sda_sum") if k in own and own[k][1] > 0), None)
+    if sk:
+        n_, t_, b_ = own[sk]
         g_ = (b_ / n_) / (t_ / n_ / 1000.0) / 1e9
-        sda_roof = {"kernel": "sda_sum", "bound": "hbm", "achieved": g_, "peak": hbm, "unit": "GB/s",
-                    "frac": g_ / hbm, "traffic": dram_traffic(NCU_NAME["sda_sum"]), "bytes_per_launch": b_ / n_}
+        sda_roof = {"kernel": sk, "bound": "hbm", "achieved": g_, "peak": hbm, "unit": "GB/s",
+                    "frac": g_ / hbm, "traffic": dram_traffic(NCU_NAME[sk]), "bytes_per_launch": b_ / n_}
     return roof, sda_roof, kern, launches
 
 
@@ -875,15 +880,18 @@ def main():
 
     from paper_1909_04573_gb300 import shard
 
+    prm = P.default_params(sda_fusion=args.sda_fusion)
+
     def step(d=D_SDA, images_per_pass=None):
         num.zero_()
         den.zero_()
         if shard_mode:
             shard.accumulate_sharded(
-                lambda f, dd, a, b: ctx.fingerprint_accumulate(f, dd, a, b, images_per_pass=images_per_pass),
+                lambda f, dd, a, b: ctx.fingerprint_accumulate(f, dd, a, b, params=prm,
+                                                               images_per_pass=images_per_pass),
                 frames, d, num, den, rank, world)
         else:
-            ctx.fingerprint_accumulate(frames, d, num, den, images_per_pass=images_per_pass)
+            ctx.fingerprint_accumulate(frames, d, num, den, params=prm, images_per_pass=images_per_pass)
         K = ctx.fingerprint_finalize(num, den, flags)
         ctx.pce_match_images_async(K[0], qimg, out=pout)
 
@@ -900,7 +908,7 @@ def main():
             qctx.pce_images_prepare(qimg)
         num.zero_()
         den.zero_()
-        ctx.fingerprint_accumulate(frames, D_SDA, num, den)
+        ctx.fingerprint_accumulate(frames, D_SDA, num, den, params=prm)
         K = ctx.fingerprint_finalize(num, den, flags)
         torch.cuda.current_stream().wait_stream(side)
         qctx.pce_images_finish_async(K[0], qimg, out=pout)
@@ -1055,21 +1063,30 @@ def main():
     # ---- extraction alone (accumulate + finalize of the fingerprint, no
     # queries): its frame bytes against the copy peak
     if use_graph:
-        def extract():
-            num.zero_()
-            den.zero_()
-            ctx.fingerprint_accumulate(frames, D_SDA, num, den)
-            ctx.fingerprint_finalize(num, den, flags)
-        g_ex = capture(None, fn=extract, profile=False)
-        ms_ex = timed(g_ex.replay, 1, 0) / args.steps
-        del g_ex
-        torch.cuda.synchronize()
-        P.prnu_profile_reset(ctx.ctx)
+        def extraction_ms(p):
+            def extract():
+                num.zero_()
+                den.zero_()
+                ctx.fingerprint_accumulate(frames, D_SDA, num, den, params=p)
+                ctx.fingerprint_finalize(num, den, flags)
+            g_ex = capture(None, fn=extract, profile=False)
+            ms_ = timed(g_ex.replay, 1, 0) / args.steps
+            del g_ex
+            torch.cuda.synchronize()
+            P.prnu_profile_reset(ctx.ctx)
+            return ms_
+        ms_ex = extraction_ms(prm)
         ex_gbps = step_bytes / (ms_ex / 1000.0) / 1e9
         line["extraction"] = {"value": frames_per_step / (ms_ex / 1000.0), "unit": UNIT, "ms_per_step": ms_ex,
                               "frame_GBps": ex_gbps, "frame_frac_of_peak": ex_gbps / hbm,
+                              "sda_fusion": args.sda_fusion,
                               "mode": "accumulate (SDA-50 sums, denoise, MLE) + finalize (grey, zero-mean, DFT "
                                       "Wiener) of the step's fingerprint, without the queries; one graph replay"}
+        # A/B: the same extraction with the other form of the group sums
+        alt = P.PRNU_SDA_SEPARATE if args.sda_fusion != P.PRNU_SDA_SEPARATE else 0
+        ms_alt = extraction_ms(P.default_params(sda_fusion=alt))
+        line["extraction"]["other_sda_form"] = {"sda_fusion": alt, "ms_per_step": ms_alt,
+                                                "value": frames_per_step / (ms_alt / 1000.0)}
 
     # ---- per-frame (ALL-FE) comparison: d = 1, 1000 denoise passes x 3 channels
     if not args.no_perframe:

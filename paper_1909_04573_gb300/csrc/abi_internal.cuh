@@ -166,8 +166,12 @@ Layout make_layout(int H, int W, long long P, int L, bool withX, int sdt = SB_F3
 // fin.res_out) the gradient of the input; dL/dsigma0 is added to *g_sigma.
 // run_denoise phases: everything; analysis, shrink and synthesis down to
 // level 2 only; the level-1 synthesis (and its epilogue) only, from subbands a
-// kDenoiseUpToLevel2 call left in the same workspace.
-constexpr int kDenoiseAll = 0, kDenoiseUpToLevel2 = 1, kDenoiseLevel1 = 2;
+// kDenoiseUpToLevel2 call left in the same workspace; everything but the
+// level-1 analysis, whose outputs the fused group-sum kernel left in the layout.
+constexpr int kDenoiseAll = 0, kDenoiseUpToLevel2 = 1, kDenoiseLevel1 = 2, kDenoiseAfterL1Analysis = 3;
+// Arguments of the level-l analysis of P planes of the layout lo in ws.
+AnaArgs analysis_args(const prnu_ctx *ctx, const float *in, int H, int W, int P, const prnu_params &prm,
+                      PlaneScale sc, int scale_on, char *ws, const Layout &lo, int l);
 prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, const prnu_params &prm, const Win &win,
                         PlaneScale sc, int scale_on, char *ws, const Layout &lo, FinalArgs fin, bool mle,
                         cudaStream_t st, const float *ckpt = nullptr, double *g_sigma = nullptr,

@@ -22,11 +22,9 @@
 // Two launch shapes: level 1 (the full-resolution planes) streams down strips
 // with the row pass held in registers; levels >= 2 (a quarter of the samples
 // or fewer, too few strips to keep the GPU busy) use shared-memory tiles.
-#include "kernels.cuh"
+#include "dwt_rows.cuh"
 
 namespace prnu {
-
-constexpr float kSqrt2f = 1.41421356237309504880f;
 
 // Streaming layout: a warp owns 32 consecutive output columns q and a strip
 // of SP output rows; each lane walks down its column.  The row pass of an
@@ -81,30 +79,12 @@ __device__ __forceinline__ void row_load(const RowIn &row, const Lane<LEVEL1> &L
     }
 }
 
-// row pass of one input row: ref, s = sum_{k>=1} h_k (v_k - v_0), t = sum g_k (v_k - v_0)
-template <bool LEVEL1>
-__device__ __forceinline__ void row_math(const AnaArgs &a, const float *v, const float *w, float &rh, float &rl,
-                                         float &s, float &t) {
-    float ss = 0.f, tt = 0.f;
-#pragma unroll
-    for (int k = 1; k < kTaps; ++k) {
-        float dlt = __fsub_rn(v[k], v[0]);
-        if (!LEVEL1) dlt = __fadd_rn(dlt, __fsub_rn(w[k], w[0]));
-        ss = __fmaf_rn(a.f.h[k], dlt, ss);
-        tt = __fmaf_rn(a.f.g[k], dlt, tt);
-    }
-    rh = v[0];
-    rl = LEVEL1 ? 0.f : w[0];
-    s = ss;
-    t = tt;
-}
-
 template <bool LEVEL1>
 __device__ __forceinline__ void row_item(const AnaArgs &a, const RowIn &row, const Lane<LEVEL1> &L, int q2,
                                          float &rh, float &rl, float &s, float &t) {
     float v[8], w[8];
     row_load<LEVEL1>(row, L, q2, v, w);
-    row_math<LEVEL1>(a, v, w, rh, rl, s, t);
+    row_math<LEVEL1>(a.f, v, w, rh, rl, s, t);
 }
 
 // Level-1 input ring: interior warps stage their 72 input columns of each
@@ -187,7 +167,7 @@ __global__ void __launch_bounds__(32 * WARPS, 24 / WARPS) k_analysis_stream(AnaA
             v[2 * k] = u.x;
             v[2 * k + 1] = u.y;
         }
-        row_math<LEVEL1>(a, v, w, rh_, rl_, rs_, rt_);
+        row_math<LEVEL1>(a.f, v, w, rh_, rl_, rs_, rt_);
     };
 
     float rh[8], rl[8], rs[8], rt[8];
@@ -226,43 +206,8 @@ __global__ void __launch_bounds__(32 * WARPS, 24 / WARPS) k_analysis_stream(AnaA
                 row_item<LEVEL1>(a, row_at(2 * p + 7), L, 2 * q, rh[s7], rl[s7], rs[s7], rt[s7]);
             }
             // column pass over rows 2p..2p+7 = slots 2j .. 2j+7 (mod 8)
-            const int b0 = (2 * j) & 7;
-            const float r0h = rh[b0], r0l = rl[b0];
-            float A = 0.f, B = 0.f;
-#pragma unroll
-            for (int k = 1; k < kTaps; ++k) {
-                const int sl = (b0 + k) & 7;
-                float D = __fsub_rn(rh[sl], r0h);
-                if (!LEVEL1) D = __fadd_rn(D, __fsub_rn(rl[sl], r0l));
-                A = __fmaf_rn(a.f.h[k], D, A);
-                B = __fmaf_rn(a.f.g[k], D, B);
-            }
-            float Sh = 0.f, Sg = 0.f, Th = 0.f, Tg = 0.f;
-#pragma unroll
-            for (int k = 0; k < kTaps; ++k) {
-                const int sl = (b0 + k) & 7;
-                Sh = __fmaf_rn(a.f.h[k], rs[sl], Sh);
-                Sg = __fmaf_rn(a.f.g[k], rs[sl], Sg);
-                Th = __fmaf_rn(a.f.h[k], rt[sl], Th);
-                Tg = __fmaf_rn(a.f.g[k], rt[sl], Tg);
-            }
-            if (p < pend && store_q && PRNU_DCHECK(p < R2 && q < C2 && plane < a.P, (long long)p * C2 + q)) {
-                const float llsmall = __fmaf_rn(kSqrt2f, A, Sh);
-                const float lh = __fmaf_rn(kSqrt2f, B, Sg);
-                const long long o = ((long long)plane * R2 + p) * C2 + q;
-                if (a.LLh) {
-                    float sh, se;
-                    two_sum(2.f * r0h, llsmall, sh, se);
-                    const float lo = __fadd_rn(2.f * r0l, se);
-                    float hh, ll;
-                    fast_two_sum(sh, lo, hh, ll);
-                    a.LLh[o] = hh;
-                    a.LLl[o] = ll;
-                }
-                stf<T>(static_cast<T *>(a.LH) + o, lh * scale);
-                stf<T>(static_cast<T *>(a.HL) + o, Th * scale);
-                stf<T>(static_cast<T *>(a.HH) + o, Tg * scale);
-            }
+            if (p < pend && store_q && PRNU_DCHECK(p < R2 && q < C2 && plane < a.P, (long long)p * C2 + q))
+                col_store<LEVEL1, T>(a, rh, rl, rs, rt, (2 * j) & 7, ((long long)plane * R2 + p) * C2 + q, scale);
         }
     }
     if (use_ring) ring_wait<0>();  // no copy outstanding at exit

@@ -134,6 +134,8 @@ prnu_status check_params(const prnu_params *p, int H, int W, Win *win) {
         return fail(PRNU_EINVAL, "sda_blocks_per_sm must be in 0..32");
     if (p->pipeline_passes < 0 || p->pipeline_passes > 64)
         return fail(PRNU_EINVAL, "pipeline_passes must be in 0..64");
+    if (p->sda_fusion < PRNU_SDA_SEPARATE || p->sda_fusion > 256)
+        return fail(PRNU_EINVAL, "sda_fusion must be PRNU_SDA_SEPARATE (-1), 0 or a strip count in 1..256");
     if (win) {
         win->n = p->n_windows;
         for (int i = 0; i < 4; ++i) {
@@ -177,8 +179,40 @@ Layout make_layout(int H, int W, long long P, int L, bool withX, int sdt) {
     return lo;
 }
 
+// Arguments of the level-l analysis of P planes of the layout lo in ws
+// (level 1 reads `in`).
+AnaArgs analysis_args(const prnu_ctx *ctx, const float *in, int H, int W, int P, const prnu_params &prm,
+                      PlaneScale sc, int scale_on, char *ws, const Layout &lo, int l) {
+    const int L = prm.levels;
+    const int Hp = padded(H, L), Wp = padded(W, L);
+    auto F = [&](size_t off) { return reinterpret_cast<float *>(ws + off); };
+    const long long A = (long long)(Hp >> l) * (Wp >> l);
+    const size_t es = subband_bytes(prm.dtype);
+    auto SB = [&](size_t off, int k) { return static_cast<void *>(ws + off + (size_t)k * P * A * es); };
+    AnaArgs a{};
+    a.inh = l == 1 ? in : F(lo.LLh[l - 1]);
+    a.inl = l == 1 ? nullptr : F(lo.LLl[l - 1]);
+    a.R = Hp >> (l - 1);
+    a.Cc = Wp >> (l - 1);
+    a.H = H;
+    a.W = W;
+    a.P = P;
+    a.LLh = l < L ? F(lo.LLh[l]) : nullptr;
+    a.LLl = l < L ? F(lo.LLl[l]) : nullptr;
+    a.LH = SB(lo.D[l], 0);
+    a.HL = SB(lo.D[l], 1);
+    a.HH = SB(lo.D[l], 2);
+    a.sdt = prm.dtype;
+    a.sc = sc;
+    a.scale_on = scale_on;
+    a.f = ctx->filt;
+    return a;
+}
+
 // Analysis, shrink and synthesis of P planes; the level-1 step (residual or
 // MLE) is described by `fin`, whose coefficient pointers are filled here.
+// Phase kDenoiseAfterL1Analysis starts at the level-1 shrink: the level-1
+// analysis outputs are already in the layout (the fused group-sum kernel).
 prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, const prnu_params &prm, const Win &win,
                         PlaneScale sc, int scale_on, char *ws, const Layout &lo, FinalArgs fin, bool mle,
                         cudaStream_t st, const float *ckpt, double *g_sigma, int phase) {
@@ -198,24 +232,8 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
     };
     for (int l = 1; l <= L && phase != kDenoiseLevel1; ++l) {
         const long long A = (long long)(Hp >> l) * (Wp >> l);
-        AnaArgs a{};
-        a.inh = l == 1 ? in : F(lo.LLh[l - 1]);
-        a.inl = l == 1 ? nullptr : F(lo.LLl[l - 1]);
-        a.R = Hp >> (l - 1);
-        a.Cc = Wp >> (l - 1);
-        a.H = H;
-        a.W = W;
-        a.P = P;
-        a.LLh = l < L ? F(lo.LLh[l]) : nullptr;
-        a.LLl = l < L ? F(lo.LLl[l]) : nullptr;
-        a.LH = SB(lo.D[l], A, 0);
-        a.HL = SB(lo.D[l], A, 1);
-        a.HH = SB(lo.D[l], A, 2);
-        a.sdt = sdt;
-        a.sc = sc;
-        a.scale_on = scale_on;
-        a.f = ctx->filt;
-        {
+        const AnaArgs a = analysis_args(ctx, in, H, W, P, prm, sc, scale_on, ws, lo, l);
+        if (!(l == 1 && phase == kDenoiseAfterL1Analysis)) {
             const double in_b = l == 1 ? (double)P * H * W * 4 : (double)P * a.R * a.Cc * 8;
             const double out_b = (double)P * A * (3.0 * es + (l < L ? 8 : 0));
             Launch t(ctx, l == 1 ? "analysis_l1" : "analysis", st, 1, in_b + out_b);
@@ -405,11 +423,9 @@ prnu_status fft_layout(prnu_ctx *ctx, int H, int W, int n, FftLayout *out) {
 }
 
 
-// Group sums of groups g0 .. g0+G-1 of `frames` into the pass layout's X.
-prnu_status sda_pass(prnu_ctx *ctx, const uint8_t *frames, int m, int H, int W, int C, size_t fs, size_t rp, int d,
-                     int g0, int G, const prnu_params &prm, char *ws, cudaStream_t st, int blocks_per_sm = 0) {
-    const int P = G * C;
-    const Layout lo = make_layout(H, W, P, prm.levels, true, prm.dtype);
+// Group-sum arguments of groups g0 .. g0+G-1 of `frames` into X.
+SdaArgs sda_args(const uint8_t *frames, int m, int H, int W, int C, size_t fs, size_t rp, int d, int g0, int G,
+                 const prnu_params &prm, float *X, int blocks_per_sm) {
     SdaArgs sa{};
     sa.frames = frames;
     sa.frame_stride = (long long)fs;
@@ -421,12 +437,26 @@ prnu_status sda_pass(prnu_ctx *ctx, const uint8_t *frames, int m, int H, int W, 
     sa.d = d;
     sa.g0 = g0;
     sa.G = G;
-    sa.out = reinterpret_cast<float *>(ws + lo.X);
+    sa.out = X;
     sa.mean = 0;
     sa.frame_half = prm.frame_dtype == PRNU_FRAMES_F16;
     sa.blocks_per_sm = blocks_per_sm > 0 ? blocks_per_sm : prm.sda_blocks_per_sm;
-    const double fr = (double)(std::min(m, (g0 + G) * d) - g0 * d) * H * W * C *
-                      (prm.frame_dtype == PRNU_FRAMES_F16 ? 2 : 1);
+    return sa;
+}
+
+// Frame bytes the groups g0 .. g0+G-1 read.
+double group_frame_bytes(int m, int H, int W, int C, int d, int g0, int G, const prnu_params &prm) {
+    return (double)(std::min(m, (g0 + G) * d) - g0 * d) * H * W * C * (prm.frame_dtype == PRNU_FRAMES_F16 ? 2 : 1);
+}
+
+// Group sums of groups g0 .. g0+G-1 of `frames` into the pass layout's X.
+prnu_status sda_pass(prnu_ctx *ctx, const uint8_t *frames, int m, int H, int W, int C, size_t fs, size_t rp, int d,
+                     int g0, int G, const prnu_params &prm, char *ws, cudaStream_t st, int blocks_per_sm = 0) {
+    const int P = G * C;
+    const Layout lo = make_layout(H, W, P, prm.levels, true, prm.dtype);
+    const SdaArgs sa = sda_args(frames, m, H, W, C, fs, rp, d, g0, G, prm, reinterpret_cast<float *>(ws + lo.X),
+                                blocks_per_sm);
+    const double fr = group_frame_bytes(m, H, W, C, d, g0, G, prm);
     Launch t(ctx, "sda_sum", st, 1, fr + (double)P * H * W * 4);
     CU(launch_sda(sa, ctx->sms, st));
     return PRNU_OK;
@@ -434,7 +464,8 @@ prnu_status sda_pass(prnu_ctx *ctx, const uint8_t *frames, int m, int H, int W, 
 
 // Denoise + MLE of the G group sums in the pass layout's X into num/den.
 prnu_status denoise_pass(prnu_ctx *ctx, int m, int H, int W, int C, int d, int g0, int G, const prnu_params &prm,
-                         const Win &win, float *num, float *den, char *ws, cudaStream_t st) {
+                         const Win &win, float *num, float *den, char *ws, cudaStream_t st,
+                         int phase = kDenoiseAll) {
     const int P = G * C;
     const Layout lo = make_layout(H, W, P, prm.levels, true, prm.dtype);
     const PlaneScale sc{d, m, g0, C, nullptr};
@@ -445,13 +476,32 @@ prnu_status denoise_pass(prnu_ctx *ctx, int m, int H, int W, int C, int d, int g
     fin.sc = sc;
     fin.num = num;
     fin.den = den;
-    return run_denoise(ctx, reinterpret_cast<const float *>(ws + lo.X), H, W, P, prm, win, sc, 1, ws, lo, fin, true, st);
+    return run_denoise(ctx, reinterpret_cast<const float *>(ws + lo.X), H, W, P, prm, win, sc, 1, ws, lo, fin, true, st,
+                       nullptr, nullptr, phase);
 }
 
-// Process groups g0 .. g0+G-1 of `frames` (device) into num/den.
+// Process groups g0 .. g0+G-1 of `frames` into num/den.  Frames in device
+// memory (fuse_ok) take the fused group-sum + level-1 analysis kernel where it
+// applies, unless prm.sda_fusion asks for the separate kernels.
 prnu_status accumulate_pass(prnu_ctx *ctx, const uint8_t *frames, int m, int H, int W, int C, size_t fs, size_t rp,
                             int d, int g0, int G, const prnu_params &prm, const Win &win, float *num, float *den,
-                            char *ws, cudaStream_t st) {
+                            char *ws, cudaStream_t st, bool fuse_ok = true) {
+    if (fuse_ok && prm.sda_fusion != PRNU_SDA_SEPARATE) {
+        const int P = G * C;
+        const Layout lo = make_layout(H, W, P, prm.levels, true, prm.dtype);
+        float *X = reinterpret_cast<float *>(ws + lo.X);
+        const SdaArgs sa = sda_args(frames, m, H, W, C, fs, rp, d, g0, G, prm, X, 0);
+        const AnaArgs a = analysis_args(ctx, X, H, W, P, prm, PlaneScale{d, m, g0, C, nullptr}, 1, ws, lo, 1);
+        if (sda_dwt_applies(sa, a)) {
+            {
+                const double l1 = (double)P * (a.R / 2) * (a.Cc / 2) * (3.0 * subband_bytes(prm.dtype) +
+                                                                      (prm.levels > 1 ? 8 : 0));
+                Launch t(ctx, "sda_dwt", st, 1, group_frame_bytes(m, H, W, C, d, g0, G, prm) + (double)P * H * W * 4 + l1);
+                CU(launch_sda_dwt(sa, a, ctx->sms, st, prm.sda_fusion > 0 ? prm.sda_fusion : 0));
+            }
+            return denoise_pass(ctx, m, H, W, C, d, g0, G, prm, win, num, den, ws, st, kDenoiseAfterL1Analysis);
+        }
+    }
     prnu_status s = sda_pass(ctx, frames, m, H, W, C, fs, rp, d, g0, G, prm, ws, st);
     if (s != PRNU_OK) return s;
     return denoise_pass(ctx, m, H, W, C, d, g0, G, prm, win, num, den, ws, st);
@@ -604,6 +654,7 @@ prnu_status prnu_default_params(prnu_params *p) {
     p->compensated = 0;
     p->sda_blocks_per_sm = 0;
     p->pipeline_passes = 0;
+    p->sda_fusion = 0;
     return PRNU_OK;
 }
 
@@ -814,7 +865,7 @@ prnu_status prnu_fingerprint_accumulate_host(prnu_ctx *ctx, const uint8_t *host_
             if (Gp < 1) return check_ws(ws, ws_bytes, make_layout(H, W, C, params->levels, true, params->dtype).end);
             for (int g0 = 0; g0 < g; g0 += Gp)
                 if ((s = accumulate_pass(ctx, dev, m, H, W, C, frame_stride, row_pitch, d, g0, std::min(Gp, g - g0),
-                                         *params, win, num, den, static_cast<char *>(ws), st)) != PRNU_OK)
+                                         *params, win, num, den, static_cast<char *>(ws), st, false)) != PRNU_OK)
                     return s;
             return PRNU_OK;
         }

@@ -42,13 +42,14 @@ class PrnuError(RuntimeError):
 
 PRNU_DTYPE_F32, PRNU_DTYPE_F16, PRNU_DTYPE_BF16 = 0, 1, 2
 PRNU_FRAMES_U8, PRNU_FRAMES_F16 = 0, 1
+PRNU_SDA_SEPARATE = -1
 
 
 class prnu_params(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("sigma0", ctypes.c_float), ("n_windows", ctypes.c_int),
                 ("windows", ctypes.c_int * 4), ("pad_mode", ctypes.c_int), ("dtype", ctypes.c_int),
                 ("frame_dtype", ctypes.c_int), ("compensated", ctypes.c_int), ("sda_blocks_per_sm", ctypes.c_int),
-                ("pipeline_passes", ctypes.c_int)]
+                ("pipeline_passes", ctypes.c_int), ("sda_fusion", ctypes.c_int)]
 
 
 class prnu_camera(ctypes.Structure):
@@ -159,7 +160,7 @@ def _check(status: int, ctx=None) -> None:
 
 
 def default_params(levels=4, sigma0=3.0, windows=(3, 5, 7, 9), dtype=PRNU_DTYPE_F32, frame_dtype=PRNU_FRAMES_U8,
-                   compensated=False, sda_blocks_per_sm=0, pipeline_passes=0) -> prnu_params:
+                   compensated=False, sda_blocks_per_sm=0, pipeline_passes=0, sda_fusion=0) -> prnu_params:
     p = prnu_params()
     _check(lib().prnu_default_params(ctypes.byref(p)))
     p.dtype = dtype
@@ -167,6 +168,7 @@ def default_params(levels=4, sigma0=3.0, windows=(3, 5, 7, 9), dtype=PRNU_DTYPE_
     p.compensated = 1 if compensated else 0
     p.sda_blocks_per_sm = sda_blocks_per_sm
     p.pipeline_passes = pipeline_passes
+    p.sda_fusion = sda_fusion
     p.levels = levels
     p.sigma0 = sigma0
     p.n_windows = len(windows)

@@ -90,10 +90,10 @@ def test_residual(lib_ctx, H, W, C):
     assert out.intact()
 
 
-@pytest.mark.parametrize("pipeline", [0, 2])
-def test_accumulate_and_finalize(lib_ctx, pipeline):
+@pytest.mark.parametrize("pipeline,H,W", [(0, 40, 52), (2, 40, 52), (0, 48, 64)])  # 48 x 64: fused group sums
+def test_accumulate_and_finalize(lib_ctx, pipeline, H, W):
     lib, ctx = lib_ctx
-    H, W, C, m, d = 40, 52, 3, 17, 5
+    C, m, d = 3, 17, 5
     fr = synth.frames(synth.Camera(H=H, W=W, C=C, camera_id=5), m, drift_px=1.0)
     num, den = Guarded((C, H, W), fill=0.0), Guarded((C, H, W), fill=0.0)
     prm = P.default_params(pipeline_passes=pipeline)
