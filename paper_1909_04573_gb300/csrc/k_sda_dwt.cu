@@ -80,8 +80,23 @@ __global__ void __launch_bounds__(FusedGeo<C, QG>::NT, 2) k_sda_dwt(SdaArgs s, A
     const int p0 = blockIdx.z * spr, pend = min(p0 + spr, R2);
     const int npr = pend - p0;
     const int rowbytes = s.W * C;
-    const int j0 = (s.g0 + gi) * s.d, j1 = min(s.m, j0 + s.d);
-    const long long fstride = s.frame_stride, rpitch = s.row_pitch;
+    // the group's frames: consecutive groups of d frames of one sequence, or
+    // (multi-camera pass) the group's own descriptor
+    const uint8_t *frames = s.frames;
+    long long fstride = s.frame_stride, rpitch = s.row_pitch;
+    int j0, j1, jmax;
+    if (s.gd) {
+        const GroupDesc &gdesc = s.gd[gi];
+        frames = gdesc.frames;
+        fstride = gdesc.frame_stride;
+        rpitch = gdesc.row_pitch;
+        j0 = 0;
+        j1 = jmax = gdesc.n;
+    } else {
+        j0 = (s.g0 + gi) * s.d;
+        j1 = min(s.m, j0 + s.d);
+        jmax = s.m;
+    }
     // owned bytes of this block (a multiple of 16) and the source of its halo:
     // the next bytes of the row, or the row start past the last column
     const int seg0 = 2 * cq0 * C;
@@ -114,10 +129,10 @@ __global__ void __launch_bounds__(FusedGeo<C, QG>::NT, 2) k_sda_dwt(SdaArgs s, A
     auto issue_slice = [&](int k) {       // one commit group per slice (empty past the last)
         if (k < nslices && uoff >= 0) {
             const int sg = k / nb, f0 = (k - sg * nb) * fb, fn = min(fb, nfr - f0);
-            const uint8_t *p = s.frames + (long long)(j0 + f0 + sub) * fstride +
+            const uint8_t *p = frames + (long long)(j0 + f0 + sub) * fstride +
                                (long long)src_row(2 * sg + urow) * rpitch + uoff;
             uint4 *dst = stg + ((k & 1) * fb + sub) * FG::NU + unit;
-            const int fe = PRNU_DCHECK(uoff + 16 <= rowbytes && j0 + f0 + fn <= s.m, uoff) ? fn : 0;
+            const int fe = PRNU_DCHECK(uoff + 16 <= rowbytes && j0 + f0 + fn <= jmax, uoff) ? fn : 0;
             for (int f = sub; f < fe; f += FG::NSUB, p += fstep, dst += FG::NSUB * FG::NU) cp16(dst, p);
         }
         cp_commit();
@@ -232,7 +247,7 @@ __global__ void __launch_bounds__(FusedGeo<C, QG>::NT, 2) k_sda_dwt(SdaArgs s, A
 }
 
 template <int C, int QG, class T>
-void launch_t(const SdaArgs &s, const AnaArgs &a, int num_sms, int strips, cudaStream_t st) {
+void launch_t(const SdaArgs &s, const AnaArgs &a, int num_sms, int strips, int max_n, cudaStream_t st) {
     using FG = FusedGeo<C, QG>;
     const int R2 = a.R >> 1, C2 = a.Cc >> 1;
     const int ncb = (C2 + 32 * QG - 1) / (32 * QG);
@@ -242,7 +257,7 @@ void launch_t(const SdaArgs &s, const AnaArgs &a, int num_sms, int strips, cudaS
         strips = std::min(strips, std::max(1, R2 / 16));
     }
     const int spr = (R2 + strips - 1) / strips;
-    const int fb = std::min(s.d, kMaxSlice);
+    const int fb = std::min(max_n, kMaxSlice);
     const size_t smem = (size_t)2 * fb * FG::NU * 16;
     cudaFuncSetAttribute(k_sda_dwt<C, QG, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const dim3 grid((unsigned)ncb, (unsigned)s.G, (unsigned)((R2 + spr - 1) / spr));
@@ -250,31 +265,44 @@ void launch_t(const SdaArgs &s, const AnaArgs &a, int num_sms, int strips, cudaS
 }
 
 template <class T>
-void launch_c(const SdaArgs &s, const AnaArgs &a, int num_sms, int strips, cudaStream_t st) {
+void launch_c(const SdaArgs &s, const AnaArgs &a, int num_sms, int strips, int max_n, cudaStream_t st) {
     if (s.C == 3)
-        launch_t<3, 2, T>(s, a, num_sms, strips, st);
+        launch_t<3, 2, T>(s, a, num_sms, strips, max_n, st);
     else
-        launch_t<1, 4, T>(s, a, num_sms, strips, st);
+        launch_t<1, 4, T>(s, a, num_sms, strips, max_n, st);
 }
 
 }  // namespace
 
-bool sda_dwt_applies(const SdaArgs &s, const AnaArgs &a) {
-    if (s.frame_half || s.gd || (s.C != 1 && s.C != 3) || s.d < 1 || s.d > 257) return false;
-    if (a.Cc != s.W || a.W != s.W || a.H != s.H || a.R < s.H || a.P != s.G * s.C) return false;
-    if (((reinterpret_cast<uintptr_t>(s.frames) | (uintptr_t)s.frame_stride | (uintptr_t)s.row_pitch) & 15u) != 0)
+bool sda_dwt_applies(const SdaArgs &s, const AnaArgs &a, const PassDesc *pd) {
+    if (s.frame_half || (s.C != 1 && s.C != 3) || (s.gd != nullptr) != (pd != nullptr)) return false;
+    if (a.Cc != s.W || a.W != s.W || a.H != s.H || a.R < s.H || a.P != s.G * s.C || (s.W * s.C) % 16 != 0)
         return false;
-    return (s.W * s.C) % 16 == 0;
+    auto aligned = [](const uint8_t *f, long long fs, long long rp) {
+        return ((reinterpret_cast<uintptr_t>(f) | (uintptr_t)fs | (uintptr_t)rp) & 15u) == 0;
+    };
+    if (!pd) return s.d >= 1 && s.d <= 257 && aligned(s.frames, s.frame_stride, s.row_pitch);
+    if (pd->G != s.G) return false;
+    for (int i = 0; i < pd->G; ++i)
+        if (pd->g[i].n < 1 || pd->g[i].n > 257 || !aligned(pd->g[i].frames, pd->g[i].frame_stride, pd->g[i].row_pitch))
+            return false;
+    return true;
 }
 
-cudaError_t launch_sda_dwt(const SdaArgs &s, const AnaArgs &a, int num_sms, cudaStream_t st, int strips) {
-    if (!sda_dwt_applies(s, a)) return cudaErrorInvalidValue;
+cudaError_t launch_sda_dwt(const SdaArgs &s, const AnaArgs &a, const PassDesc *pd, int num_sms, cudaStream_t st,
+                           int strips) {
+    if (!sda_dwt_applies(s, a, pd)) return cudaErrorInvalidValue;
+    int max_n = s.d;
+    if (pd) {
+        max_n = 1;
+        for (int i = 0; i < pd->G; ++i) max_n = std::max(max_n, pd->g[i].n);
+    }
     if (a.sdt == SB_F16)
-        launch_c<__half>(s, a, num_sms, strips, st);
+        launch_c<__half>(s, a, num_sms, strips, max_n, st);
     else if (a.sdt == SB_BF16)
-        launch_c<__nv_bfloat16>(s, a, num_sms, strips, st);
+        launch_c<__nv_bfloat16>(s, a, num_sms, strips, max_n, st);
     else
-        launch_c<float>(s, a, num_sms, strips, st);
+        launch_c<float>(s, a, num_sms, strips, max_n, st);
     return cudaGetLastError();
 }
 

@@ -44,11 +44,14 @@ cudaError_t launch_analysis(const AnaArgs &a, bool level1, cudaStream_t st, int 
 
 // k_sda_dwt.cu: the group sums of s (into s.out, exact sums) and the level-1
 // analysis of a (a.inh unused) in one kernel, where sda_dwt_applies: uint8
-// frames of one camera, C = 1 or 3, padded width == W, W*C a multiple of 16,
-// 16-byte aligned frames and strides, d <= 257.  strips: output-row strips
-// per column (0: about four blocks per SM).
-bool sda_dwt_applies(const SdaArgs &s, const AnaArgs &a);
-cudaError_t launch_sda_dwt(const SdaArgs &s, const AnaArgs &a, int num_sms, cudaStream_t st, int strips = 0);
+// frames, C = 1 or 3, padded width == W, W*C a multiple of 16, 16-byte
+// aligned frames and strides, groups of 1..257 frames.  A multi-camera pass
+// (s.gd set) passes the host copy of its descriptor as pd (nullptr
+// otherwise).  strips: output-row strips per column (0: about two blocks per
+// SM).
+bool sda_dwt_applies(const SdaArgs &s, const AnaArgs &a, const PassDesc *pd);
+cudaError_t launch_sda_dwt(const SdaArgs &s, const AnaArgs &a, const PassDesc *pd, int num_sms, cudaStream_t st,
+                           int strips = 0);
 // tuner choices of the other launches (0 = the default rule)
 // levels >= 2 analysis: 0 tiled 16 x 32, 1 streaming 16 rows x 4 warps, 2 streaming 32 x 2
 constexpr int kAnaChoices = 3;

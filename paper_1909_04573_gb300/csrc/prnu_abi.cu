@@ -492,12 +492,12 @@ prnu_status accumulate_pass(prnu_ctx *ctx, const uint8_t *frames, int m, int H, 
         float *X = reinterpret_cast<float *>(ws + lo.X);
         const SdaArgs sa = sda_args(frames, m, H, W, C, fs, rp, d, g0, G, prm, X, 0);
         const AnaArgs a = analysis_args(ctx, X, H, W, P, prm, PlaneScale{d, m, g0, C, nullptr}, 1, ws, lo, 1);
-        if (sda_dwt_applies(sa, a)) {
+        if (sda_dwt_applies(sa, a, nullptr)) {
             {
                 const double l1 = (double)P * (a.R / 2) * (a.Cc / 2) * (3.0 * subband_bytes(prm.dtype) +
                                                                       (prm.levels > 1 ? 8 : 0));
                 Launch t(ctx, "sda_dwt", st, 1, group_frame_bytes(m, H, W, C, d, g0, G, prm) + (double)P * H * W * 4 + l1);
-                CU(launch_sda_dwt(sa, a, ctx->sms, st, prm.sda_fusion > 0 ? prm.sda_fusion : 0));
+                CU(launch_sda_dwt(sa, a, nullptr, ctx->sms, st, prm.sda_fusion > 0 ? prm.sda_fusion : 0));
             }
             return denoise_pass(ctx, m, H, W, C, d, g0, G, prm, win, num, den, ws, st, kDenoiseAfterL1Analysis);
         }
@@ -572,13 +572,22 @@ prnu_status accumulate_pass_multi(prnu_ctx *ctx, const PassDesc &pd, int H, int 
     sa.mean = 0;
     sa.frame_half = prm.frame_dtype == PRNU_FRAMES_F16;
     sa.gd = dpd->g;
-    {
-        double fr = 0.0;
-        for (int i = 0; i < G; ++i) fr += (double)pd.g[i].n;
-        Launch t(ctx, "sda_sum", st, 1, fr * H * W * C * (sa.frame_half ? 2 : 1) + (double)P * H * W * 4);
+    const PlaneScale sc{1, 1, 0, C, dpd->g};
+    double fr = 0.0;
+    for (int i = 0; i < G; ++i) fr += (double)pd.g[i].n;
+    fr *= (double)H * W * C * (sa.frame_half ? 2 : 1);
+    // the group sums with the level-1 analysis in one kernel where it applies
+    const AnaArgs a1 = analysis_args(ctx, sa.out, H, W, P, prm, sc, 1, ws, lo, 1);
+    const bool fused = prm.sda_fusion != PRNU_SDA_SEPARATE && sda_dwt_applies(sa, a1, &pd);
+    if (fused) {
+        const double l1 = (double)P * (a1.R / 2) * (a1.Cc / 2) * (3.0 * subband_bytes(prm.dtype) +
+                                                                (prm.levels > 1 ? 8 : 0));
+        Launch t(ctx, "sda_dwt", st, 1, fr + (double)P * H * W * 4 + l1);
+        CU(launch_sda_dwt(sa, a1, &pd, ctx->sms, st, prm.sda_fusion > 0 ? prm.sda_fusion : 0));
+    } else {
+        Launch t(ctx, "sda_sum", st, 1, fr + (double)P * H * W * 4);
         CU(launch_sda(sa, ctx->sms, st));
     }
-    const PlaneScale sc{1, 1, 0, C, dpd->g};
     FinalArgs fin{};
     fin.C = C;
     fin.G = G;
@@ -587,7 +596,7 @@ prnu_status accumulate_pass_multi(prnu_ctx *ctx, const PassDesc &pd, int H, int 
     fin.gd = dpd->g;
     fin.cams = dpd->cam;
     return run_denoise(ctx, reinterpret_cast<const float *>(ws + lo.X), H, W, P, prm, win, sc, 1, ws, lo, fin, true,
-                       st);
+                       st, nullptr, nullptr, fused ? kDenoiseAfterL1Analysis : kDenoiseAll);
 }
 
 prnu_status check_camera(const prnu_camera &c, const prnu_params *params) {

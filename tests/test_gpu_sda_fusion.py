@@ -132,3 +132,27 @@ def test_invalid_fusion_setting(ctx):
         with pytest.raises(P.PrnuError) as e:
             ctx.fingerprint_accumulate(fr, 2, num, den, params=P.default_params(sda_fusion=bad))
         assert e.value.status == P.PRNU_EINVAL
+
+
+def test_fused_in_multi_camera_passes(ctx):
+    """prnu_fingerprint_accumulate_multi: groups of several cameras in one
+    pass (per-group frame descriptors, ragged counts), the geometries the
+    fused kernel serves and one it does not (W = 52): the same sums as the
+    separate kernels, bit for bit, and the oracle's."""
+    specs = [(64, 96, 3, 13, 4), (64, 96, 3, 9, 9), (48, 128, 1, 11, 3), (40, 52, 3, 7, 2), (64, 96, 3, 20, 7)]
+    frames = [synth.frames(synth.Camera(H=H, W=W, C=C, camera_id=900 + i), m, drift_px=0.3)
+              for i, (H, W, C, m, d) in enumerate(specs)]
+    res = {}
+    for fusion in (0, P.PRNU_SDA_SEPARATE):
+        items = []
+        for fr, (H, W, C, m, d) in zip(frames, specs):
+            items.append((fr.cuda(), d, torch.zeros((C, H, W), device="cuda"), torch.zeros((C, H, W), device="cuda")))
+        ctx.fingerprint_accumulate_multi(items, params=P.default_params(sda_fusion=fusion), groups_per_pass=5)
+        torch.cuda.synchronize()
+        res[fusion] = [(n.cpu().numpy(), dd.cpu().numpy()) for _, _, n, dd in items]
+    for (nf, df), (ns, ds) in zip(res[0], res[P.PRNU_SDA_SEPARATE]):
+        np.testing.assert_array_equal(nf, ns)
+        np.testing.assert_array_equal(df, ds)
+    for fr, (H, W, C, m, d), (nf, df) in zip(frames, specs, res[0]):
+        onum, oden = O.fingerprint_accumulate(fr.numpy(), d)
+        assert _rel(nf, onum) <= K_TOL and _rel(df, oden) <= K_TOL
