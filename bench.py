@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="video config: time eager launches, not a CUDA graph")
     ap.add_argument("--sda-fusion", type=int, default=0,
-                    help="video config: prnu_params.sda_fusion of the fingerprint (0: fused group sums + level-1 "
+                    help="video and batch configs: prnu_params.sda_fusion of the fingerprints (0: fused group sums + level-1 "
                          "analysis where it applies, -1: separate kernels, n >= 1: fused with n row strips)")
     ap.add_argument("--frames", type=int, default=M_FRAMES,
                     help="frames of the workload (default 1000; smaller values are for profiling captures)")
@@ -491,7 +491,7 @@ def batch_config(args, rank, world, local):
                       dtype=torch.uint8, device=dev)
     nums = [torch.zeros((c.C, c.H, c.W), device=dev) for c, _, _ in specs]
     dens = [torch.zeros_like(n) for n in nums]
-    prm = P.default_params()
+    prm = P.default_params(sda_fusion=args.sda_fusion)
     gpp = args.groups_per_pass
 
     def items_of(ch):

@@ -88,14 +88,15 @@ typedef struct {
                               workspace) and the group sums of pass k+1 run on the context's side stream while
                               pass k is denoised on `stream` (two pass layouts in the workspace; the sums kernel
                               then takes at most sda_blocks_per_sm blocks per SM, 6 when that is 0) */
-    int sda_fusion;        /* prnu_fingerprint_accumulate with device frames (one stream) and
-                              prnu_fingerprint_accumulate_multi: 0 (default): each pass's group sums and their
-                              level-1 analysis run as one kernel (Sec. III-B averaging + the first DWT level;
-                              the SDA frame still goes to the workspace for the MLE step) where that applies
-                              -- uint8 frames, C = 1 or 3, W a multiple of 2^levels with W*C a multiple of 16,
-                              16-byte aligned frames and strides, groups of at most 257 frames -- else the
-                              separate kernels; PRNU_SDA_SEPARATE: always the separate group-sum and analysis
-                              kernels; n >= 1 (at most 256): fused, with n row strips per column */
+    int sda_fusion;        /* the group sums and their level-1 analysis as one kernel (Sec. III-B averaging +
+                              the first DWT level; the SDA frame still goes to the workspace for the MLE step)
+                              where that applies -- uint8 frames, C = 1 or 3, W a multiple of 2^levels with
+                              W*C a multiple of 16, 16-byte aligned frames and strides, groups of at most 257
+                              frames -- else the separate kernels.  0 (default): fused in
+                              prnu_fingerprint_accumulate with device frames (one stream), separate in
+                              prnu_fingerprint_accumulate_multi (groups of different sizes balance better
+                              there); PRNU_SDA_SEPARATE: always separate; n >= 1 (at most 256): fused in both,
+                              with n row strips per column */
 } prnu_params;
 #define PRNU_SDA_SEPARATE (-1)
 

@@ -576,9 +576,11 @@ prnu_status accumulate_pass_multi(prnu_ctx *ctx, const PassDesc &pd, int H, int 
     double fr = 0.0;
     for (int i = 0; i < G; ++i) fr += (double)pd.g[i].n;
     fr *= (double)H * W * C * (sa.frame_half ? 2 : 1);
-    // the group sums with the level-1 analysis in one kernel where it applies
+    // the group sums with the level-1 analysis in one kernel when asked for
+    // (sda_fusion >= 1) and it applies; by default the separate kernels, which
+    // balance groups of different sizes better (measured on mixed passes)
     const AnaArgs a1 = analysis_args(ctx, sa.out, H, W, P, prm, sc, 1, ws, lo, 1);
-    const bool fused = prm.sda_fusion != PRNU_SDA_SEPARATE && sda_dwt_applies(sa, a1, &pd);
+    const bool fused = prm.sda_fusion >= 1 && sda_dwt_applies(sa, a1, &pd);
     if (fused) {
         const double l1 = (double)P * (a1.R / 2) * (a1.Cc / 2) * (3.0 * subband_bytes(prm.dtype) +
                                                                 (prm.levels > 1 ? 8 : 0));
