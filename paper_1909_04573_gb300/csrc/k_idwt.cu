@@ -503,6 +503,7 @@ __device__ __forceinline__ void stream_synth(const T *LL, const T *LH, const T *
         for (int j = 0; j < 4; ++j) {
             const int m = mb + j;
             if (m >= m1) break;
+            epi.prefetch(2 * m, 2 * n, out_lane, outH, outW);  // the epilogue's inputs, beside the row's loads
             load(m, q[(j + 3) & 3]);
             // column synthesis: rows 2m + e of lo (LL, LH) and hi (HL, HH)
             float lo[2], hi[2];
@@ -555,6 +556,7 @@ template <bool ACC, class T = float>
 struct StoreEpi {
     T *p;
     int W;
+    __device__ __forceinline__ void prefetch(int, int, bool, int, int) {}
     __device__ __forceinline__ void operator()(int y, int x, float w0, float w1, bool two) const {
         T *o = p + (long long)y * W + x;
         if (ACC) {
@@ -605,6 +607,7 @@ struct PceEpi {
     int W, C;
     bool vec;  // W even and every base 8-byte aligned: pairs move as float2
     float m[4] = {0.f, 0.f, 0.f, 0.f}, mlo[4] = {0.f, 0.f, 0.f, 0.f};
+    float2 pi[2][3], pk[2];  // output rows 2m, 2m+1: image channels and K at (y, x), (y, x+1)
     __device__ __forceinline__ float2 ld2(const float *p, bool two) const {
         if (vec && two) return __ldg(reinterpret_cast<const float2 *>(p));
         return make_float2(__ldg(p), two ? __ldg(p + 1) : 0.f);
@@ -617,15 +620,34 @@ struct PceEpi {
             if (two) p[1] = b;
         }
     }
+    // loads of output rows y0, y0+1 at columns x, x+1, issued one coefficient
+    // row ahead of their use so their latency overlaps the synthesis
+    __device__ __forceinline__ void prefetch(int y0, int x, bool lane_ok, int outH, int outW) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int y = y0 + e;
+            if (lane_ok && y < outH && x < outW) {
+                const bool two = x + 1 < outW;
+                const long long o = (long long)y * W + x;
+                pi[e][0] = ld2(I + o, two);
+                if (C == 3) {
+                    pi[e][1] = ld2(I + hw + o, two);
+                    pi[e][2] = ld2(I + 2 * hw + o, two);
+                }
+                pk[e] = ld2(K + o, two);
+            }
+        }
+    }
     __device__ __forceinline__ void operator()(int y, int x, float w0, float w1, bool two) {
         const long long o = (long long)y * W + x;
-        float2 g = ld2(I + o, two);
+        const int e = y & 1;
+        float2 g = pi[e][0];
         if (C == 3) {
-            const float2 i1 = ld2(I + hw + o, two), i2 = ld2(I + 2 * hw + o, two);
+            const float2 i1 = pi[e][1], i2 = pi[e][2];
             g.x = __fmaf_rn(0.114f, i2.x, __fmaf_rn(0.587f, i1.x, 0.299f * g.x));
             g.y = __fmaf_rn(0.114f, i2.y, __fmaf_rn(0.587f, i1.y, 0.299f * g.y));
         }
-        const float2 k = ld2(K + o, two);
+        const float2 k = pk[e];
         const float y0 = k.x * g.x, y1 = two ? k.y * g.y : 0.f;
         if (!two) w1 = 0.f;
         st2(X + o, w0, w1, two);
@@ -638,7 +660,7 @@ struct PceEpi {
 };
 
 template <bool GRAY3>
-__global__ void __launch_bounds__(32 * FS_WARPS, 8) k_final_pce(FinalArgs a) {
+__global__ void __launch_bounds__(32 * FS_WARPS, 5) k_final_pce(FinalArgs a) {
     __shared__ double sh[FS_WARPS][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cg = blockIdx.x * FS_WARPS + warp;
