@@ -461,7 +461,9 @@ __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
 // Residual mode with float32 subbands, streaming: a warp owns 32 coefficient
 // columns n0 .. n0+31 of one plane and walks a strip of coefficient rows,
 // keeping the last four rows of the four subbands in a register ring for the
-// column synthesis.  Lanes 3..31 produce output columns 2n, 2n+1; lanes 0..2
+// column synthesis; the loads of the next coefficient row (and the
+// epilogue's inputs of this row, where it has any) are issued before this
+// row's arithmetic, so their latency overlaps it.  Lanes 3..31 produce output columns 2n, 2n+1; lanes 0..2
 // only supply the row synthesis' left neighbours (taken with shuffles), so
 // consecutive warps start 29 columns apart.  Three rows above the strip prime
 // the ring.
@@ -484,27 +486,46 @@ __device__ __forceinline__ void stream_synth(const T *LL, const T *LH, const T *
     const int m1 = min(Rc, m0 + FS_ROWS);
     // ring slot of coefficient row m is (m - m0 + 3) & 3
     float q[4][4];  // [slot][subband]
-    auto ld = [&](const T *p, long long o) {
-        if (GRAY3)
-            return __fmaf_rn(0.114f, ldf<T>(p + o + 2 * cs), __fmaf_rn(0.587f, ldf<T>(p + o + cs), 0.299f * ldf<T>(p + o)));
-        return ldf<T>(p + o);
-    };
-    auto load = [&](int m, float *d) {
+    // raw loads of one coefficient row (LL, then each detail subband's one or
+    // three channel values), fetched one row ahead of their use
+    constexpr int NR = GRAY3 ? 10 : 4;
+    auto fetch = [&](int m, float *r) {
         const long long o = PRNU_DCHECK(nw >= 0 && nw < Cc, nw) ? (long long)wrap_near(m, Rc) * Cc + nw : 0;
-        d[0] = LL ? ldf<T>(LL + o) : 0.f;
-        d[1] = ld(LH, o);
-        d[2] = ld(HL, o);
-        d[3] = ld(HH, o);
-    };
+        r[0] = LL ? ldf<T>(LL + o) : 0.f;
+        const T *sb[3] = {LH, HL, HH};
 #pragma unroll
-    for (int t = 1; t <= 3; ++t) load(m0 - t, q[(3 - t) & 3]);
+        for (int k = 0; k < 3; ++k) {
+            if (GRAY3) {
+                r[1 + 3 * k] = ldf<T>(sb[k] + o);
+                r[2 + 3 * k] = ldf<T>(sb[k] + o + cs);
+                r[3 + 3 * k] = ldf<T>(sb[k] + o + 2 * cs);
+            } else {
+                r[1 + k] = ldf<T>(sb[k] + o);
+            }
+        }
+    };
+    auto combine = [&](const float *r, float *d) {
+        d[0] = r[0];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            d[1 + k] = GRAY3 ? __fmaf_rn(0.114f, r[3 + 3 * k], __fmaf_rn(0.587f, r[2 + 3 * k], 0.299f * r[1 + 3 * k]))
+                             : r[1 + k];
+    };
+    float nx[NR];
+#pragma unroll
+    for (int t = 1; t <= 3; ++t) {
+        fetch(m0 - t, nx);
+        combine(nx, q[(3 - t) & 3]);
+    }
+    fetch(m0, nx);
     for (int mb = m0; mb < m1; mb += 4) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int m = mb + j;
             if (m >= m1) break;
-            epi.prefetch(2 * m, 2 * n, out_lane, outH, outW);  // the epilogue's inputs, beside the row's loads
-            load(m, q[(j + 3) & 3]);
+            combine(nx, q[(j + 3) & 3]);
+            if (m + 1 < m1) fetch(m + 1, nx);  // the next row's loads overlap this row's synthesis
+            epi.prefetch(2 * m, 2 * n, out_lane, outH, outW);  // the epilogue's inputs, beside them
             // column synthesis: rows 2m + e of lo (LL, LH) and hi (HL, HH)
             float lo[2], hi[2];
 #pragma unroll
@@ -660,7 +681,7 @@ struct PceEpi {
 };
 
 template <bool GRAY3>
-__global__ void __launch_bounds__(32 * FS_WARPS, 5) k_final_pce(FinalArgs a) {
+__global__ void __launch_bounds__(32 * FS_WARPS, 4) k_final_pce(FinalArgs a) {
     __shared__ double sh[FS_WARPS][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cg = blockIdx.x * FS_WARPS + warp;
