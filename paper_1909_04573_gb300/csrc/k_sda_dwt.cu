@@ -251,10 +251,21 @@ void launch_t(const SdaArgs &s, const AnaArgs &a, int num_sms, int strips, int m
     using FG = FusedGeo<C, QG>;
     const int R2 = a.R >> 1, C2 = a.Cc >> 1;
     const int ncb = (C2 + 32 * QG - 1) / (32 * QG);
-    if (strips <= 0) {  // about two blocks per SM, strips of at least 16 output rows
-        const long long base = (long long)ncb * s.G;
-        strips = (int)std::max<long long>(1, (2LL * num_sms + base / 2) / base);
-        strips = std::min(strips, std::max(1, R2 / 16));
+    if (strips <= 0) {
+        // Every block walks its strip at about the same pace, two blocks per SM:
+        // the launch takes (waves of blocks) x (stages of a strip, its 3-stage
+        // halo included).  Pick the strip count (strips of at least 16 output
+        // rows) that minimises that product.
+        const long long slots = 2LL * num_sms, base = (long long)ncb * s.G;
+        long long best = -1;
+        for (int k = 1; k <= std::max(1, R2 / 16); ++k) {
+            const long long waves = (base * k + slots - 1) / slots;
+            const long long cost = waves * ((R2 + k - 1) / k + 3);
+            if (best < 0 || cost < best) {
+                best = cost;
+                strips = k;
+            }
+        }
     }
     const int spr = (R2 + strips - 1) / strips;
     const int fb = std::min(max_n, kMaxSlice);

@@ -134,8 +134,9 @@ prnu_status check_params(const prnu_params *p, int H, int W, Win *win) {
         return fail(PRNU_EINVAL, "sda_blocks_per_sm must be in 0..32");
     if (p->pipeline_passes < 0 || p->pipeline_passes > 64)
         return fail(PRNU_EINVAL, "pipeline_passes must be in 0..64");
-    if (p->sda_fusion < PRNU_SDA_SEPARATE || p->sda_fusion > 256)
-        return fail(PRNU_EINVAL, "sda_fusion must be PRNU_SDA_SEPARATE (-1), 0 or a strip count in 1..256");
+    if (p->sda_fusion < PRNU_SDA_FUSED || p->sda_fusion > 256)
+        return fail(PRNU_EINVAL, "sda_fusion must be PRNU_SDA_FUSED (-2), PRNU_SDA_SEPARATE (-1), 0 or a strip "
+                                 "count in 1..256");
     if (win) {
         win->n = p->n_windows;
         for (int i = 0; i < 4; ++i) {
@@ -482,11 +483,16 @@ prnu_status denoise_pass(prnu_ctx *ctx, int m, int H, int W, int C, int d, int g
 
 // Process groups g0 .. g0+G-1 of `frames` into num/den.  Frames in device
 // memory (fuse_ok) take the fused group-sum + level-1 analysis kernel where it
-// applies, unless prm.sda_fusion asks for the separate kernels.
+// applies: by default for groups of at least kFuseMinGroup frames (shorter
+// groups leave the fused kernel's per-stage hand-off and analysis too little
+// summing to hide behind; measured), always with PRNU_SDA_FUSED or a strip
+// count, never with PRNU_SDA_SEPARATE.
+constexpr int kFuseMinGroup = 16;
 prnu_status accumulate_pass(prnu_ctx *ctx, const uint8_t *frames, int m, int H, int W, int C, size_t fs, size_t rp,
                             int d, int g0, int G, const prnu_params &prm, const Win &win, float *num, float *den,
                             char *ws, cudaStream_t st, bool fuse_ok = true) {
-    if (fuse_ok && prm.sda_fusion != PRNU_SDA_SEPARATE) {
+    if (fuse_ok && (prm.sda_fusion >= 1 || prm.sda_fusion == PRNU_SDA_FUSED ||
+                    (prm.sda_fusion == 0 && d >= kFuseMinGroup))) {
         const int P = G * C;
         const Layout lo = make_layout(H, W, P, prm.levels, true, prm.dtype);
         float *X = reinterpret_cast<float *>(ws + lo.X);
@@ -577,10 +583,10 @@ prnu_status accumulate_pass_multi(prnu_ctx *ctx, const PassDesc &pd, int H, int 
     for (int i = 0; i < G; ++i) fr += (double)pd.g[i].n;
     fr *= (double)H * W * C * (sa.frame_half ? 2 : 1);
     // the group sums with the level-1 analysis in one kernel when asked for
-    // (sda_fusion >= 1) and it applies; by default the separate kernels, which
+    // (PRNU_SDA_FUSED or a strip count) and it applies; by default the separate kernels, which
     // balance groups of different sizes better (measured on mixed passes)
     const AnaArgs a1 = analysis_args(ctx, sa.out, H, W, P, prm, sc, 1, ws, lo, 1);
-    const bool fused = prm.sda_fusion >= 1 && sda_dwt_applies(sa, a1, &pd);
+    const bool fused = (prm.sda_fusion >= 1 || prm.sda_fusion == PRNU_SDA_FUSED) && sda_dwt_applies(sa, a1, &pd);
     if (fused) {
         const double l1 = (double)P * (a1.R / 2) * (a1.Cc / 2) * (3.0 * subband_bytes(prm.dtype) +
                                                                 (prm.levels > 1 ? 8 : 0));

@@ -42,7 +42,7 @@ class PrnuError(RuntimeError):
 
 PRNU_DTYPE_F32, PRNU_DTYPE_F16, PRNU_DTYPE_BF16 = 0, 1, 2
 PRNU_FRAMES_U8, PRNU_FRAMES_F16 = 0, 1
-PRNU_SDA_SEPARATE = -1
+PRNU_SDA_SEPARATE, PRNU_SDA_FUSED = -1, -2
 
 
 class prnu_params(ctypes.Structure):

@@ -96,7 +96,7 @@ def test_accumulate_and_finalize(lib_ctx, pipeline, H, W):
     C, m, d = 3, 17, 5
     fr = synth.frames(synth.Camera(H=H, W=W, C=C, camera_id=5), m, drift_px=1.0)
     num, den = Guarded((C, H, W), fill=0.0), Guarded((C, H, W), fill=0.0)
-    prm = P.default_params(pipeline_passes=pipeline)
+    prm = P.default_params(pipeline_passes=pipeline, sda_fusion=P.PRNU_SDA_FUSED if W == 64 else 0)
     ctx.fingerprint_accumulate(fr.cuda(), d, num.t, den.t, params=prm, images_per_pass=2)
     _check(lib, ctx)
     onum, oden = O.fingerprint_accumulate(fr.numpy(), d)
@@ -126,8 +126,8 @@ def test_multi_camera_and_persistent(lib_ctx):
             items.append((fr, d, num.t, den.t))
         if persistent:
             ctx.fingerprint_accumulate_persistent(items)
-        else:
-            ctx.fingerprint_accumulate_multi(items)
+        else:  # the fused group-sum kernel where a geometry allows it
+            ctx.fingerprint_accumulate_multi(items, params=P.default_params(sda_fusion=P.PRNU_SDA_FUSED))
         _check(lib, ctx)
         for fr, d, n, dd in items:
             onum, oden = O.fingerprint_accumulate(fr.cpu().numpy(), d)

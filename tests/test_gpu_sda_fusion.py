@@ -48,24 +48,25 @@ def _accumulate(ctx, fr, d, fusion, dtype=P.PRNU_DTYPE_F32):
     return num.cpu().numpy(), den.cpu().numpy()
 
 
-# (H, W, C, m, d, strips): strips 0 = the default rule
+# (H, W, C, m, d, fusion): PRNU_SDA_FUSED = fused with the strips chosen per launch,
+# n >= 1 = fused with n row strips, 0 = the default rule (fused for d >= 16)
 CASES = [
-    (64, 128, 3, 13, 5, 0),     # whole column blocks, ragged last group (3 frames)
-    (48, 1008, 3, 9, 4, 0),     # partial last column block (504 output columns)
-    (37, 48, 1, 12, 5, 0),      # one channel, one partial block, mirrored rows (padded height 48)
+    (64, 128, 3, 13, 5, P.PRNU_SDA_FUSED),     # whole column blocks, ragged last group (3 frames)
+    (48, 1008, 3, 9, 4, P.PRNU_SDA_FUSED),     # partial last column block (504 output columns)
+    (37, 48, 1, 12, 5, P.PRNU_SDA_FUSED),      # one channel, one partial block, mirrored rows (padded height 48)
     (100, 160, 3, 20, 10, 3),   # three row strips (re-summed 6-row halos)
     (30, 64, 3, 17, 17, 7),     # strips of 3 output rows: more strips than full iterations
-    (32, 64, 3, 300, 257, 0),   # the longest group the 16-bit lanes hold, then a group of 43
-    (1080, 1920, 3, 100, 50, 0),  # full HD, two SDA-50 groups
+    (32, 64, 3, 300, 257, 0),   # the longest group the 16-bit lanes hold, then a group of 43 (default rule)
+    (1080, 1920, 3, 100, 50, 0),  # full HD, two SDA-50 groups (default rule)
 ]
 
 
-@pytest.mark.parametrize("H,W,C,m,d,strips", CASES)
-def test_fused_equals_separate_bit_for_bit_and_matches_oracle(ctx, H, W, C, m, d, strips):
+@pytest.mark.parametrize("H,W,C,m,d,fusion", CASES)
+def test_fused_equals_separate_bit_for_bit_and_matches_oracle(ctx, H, W, C, m, d, fusion):
     fr = synth.frames(synth.Camera(H=H, W=W, C=C, camera_id=H + W + m), m, drift_px=0.5)
     dev = fr.cuda()
     n_sep, d_sep = _accumulate(ctx, dev, d, P.PRNU_SDA_SEPARATE)
-    n_fus, d_fus = _accumulate(ctx, dev, d, strips)
+    n_fus, d_fus = _accumulate(ctx, dev, d, fusion)
     np.testing.assert_array_equal(n_fus, n_sep)
     np.testing.assert_array_equal(d_fus, d_sep)
     if H * W <= 200_000:
@@ -73,7 +74,7 @@ def test_fused_equals_separate_bit_for_bit_and_matches_oracle(ctx, H, W, C, m, d
         assert _rel(n_fus, onum) <= K_TOL and _rel(d_fus, oden) <= K_TOL
     else:  # full HD: the first group against the oracle
         onum, oden = O.fingerprint_accumulate(fr.numpy()[:d], d)
-        n1, d1 = _accumulate(ctx, dev[:d].contiguous(), d, strips)
+        n1, d1 = _accumulate(ctx, dev[:d].contiguous(), d, fusion)
         assert _rel(n1, onum) <= K_TOL and _rel(d1, oden) <= K_TOL
 
 
@@ -81,7 +82,7 @@ def test_fused_equals_separate_bit_for_bit_and_matches_oracle(ctx, H, W, C, m, d
 def test_fused_with_16bit_subbands(ctx, dtype):
     fr = synth.frames(synth.Camera(H=64, W=96, C=3, camera_id=31), 12).cuda()
     n_sep, d_sep = _accumulate(ctx, fr, 6, P.PRNU_SDA_SEPARATE, dtype)
-    n_fus, d_fus = _accumulate(ctx, fr, 6, 0, dtype)
+    n_fus, d_fus = _accumulate(ctx, fr, 6, P.PRNU_SDA_FUSED, dtype)
     np.testing.assert_array_equal(n_fus, n_sep)
     np.testing.assert_array_equal(d_fus, d_sep)
 
@@ -89,9 +90,9 @@ def test_fused_with_16bit_subbands(ctx, dtype):
 @pytest.mark.parametrize("H,W,C,m,d", [(40, 52, 3, 9, 4), (32, 64, 3, 260, 258)])
 def test_outside_the_fused_conditions(ctx, H, W, C, m, d):
     """W = 52 (rows not whole 16-byte chunks) and groups of 258 frames take
-    the separate kernels under the default setting: same sums as forcing them."""
+    the separate kernels even when fusion is asked for: same sums as forcing them."""
     fr = synth.frames(synth.Camera(H=H, W=W, C=C, camera_id=7), m).cuda()
-    n0, d0 = _accumulate(ctx, fr, d, 0)
+    n0, d0 = _accumulate(ctx, fr, d, P.PRNU_SDA_FUSED)
     n1, d1 = _accumulate(ctx, fr, d, P.PRNU_SDA_SEPARATE)
     np.testing.assert_array_equal(n0, n1)
     np.testing.assert_array_equal(d0, d1)
@@ -101,8 +102,8 @@ def test_fused_in_a_cuda_graph(ctx):
     """The fused pass replays from a CUDA graph with the eager result."""
     H, W, C, m, d = 64, 128, 3, 20, 5
     fr = synth.frames(synth.Camera(H=H, W=W, C=C, camera_id=3), m).cuda()
-    ref_n, ref_d = _accumulate(ctx, fr, d, 0)
-    prm = P.default_params()
+    ref_n, ref_d = _accumulate(ctx, fr, d, P.PRNU_SDA_FUSED)
+    prm = P.default_params(sda_fusion=P.PRNU_SDA_FUSED)
     f, mm, Hh, Ww, Cc, fs, rp = ctx._frames_geometry(fr)
     nb = P.prnu_workspace_size(ctx.ctx, H, W, C, prm, 4)
     ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
@@ -128,7 +129,7 @@ def test_fused_in_a_cuda_graph(ctx):
 def test_invalid_fusion_setting(ctx):
     fr = synth.frames(synth.Camera(H=32, W=64, C=3, camera_id=1), 4).cuda()
     num, den = torch.zeros((3, 32, 64), device="cuda"), torch.zeros((3, 32, 64), device="cuda")
-    for bad in (-2, 257):
+    for bad in (-3, 257):
         with pytest.raises(P.PrnuError) as e:
             ctx.fingerprint_accumulate(fr, 2, num, den, params=P.default_params(sda_fusion=bad))
         assert e.value.status == P.PRNU_EINVAL
@@ -143,16 +144,16 @@ def test_fused_in_multi_camera_passes(ctx):
     frames = [synth.frames(synth.Camera(H=H, W=W, C=C, camera_id=900 + i), m, drift_px=0.3)
               for i, (H, W, C, m, d) in enumerate(specs)]
     res = {}
-    for fusion in (2, P.PRNU_SDA_SEPARATE):  # multi-camera passes fuse only when asked (n >= 1 row strips)
+    for fusion in (P.PRNU_SDA_FUSED, P.PRNU_SDA_SEPARATE):  # multi-camera passes fuse only when asked
         items = []
         for fr, (H, W, C, m, d) in zip(frames, specs):
             items.append((fr.cuda(), d, torch.zeros((C, H, W), device="cuda"), torch.zeros((C, H, W), device="cuda")))
         ctx.fingerprint_accumulate_multi(items, params=P.default_params(sda_fusion=fusion), groups_per_pass=5)
         torch.cuda.synchronize()
         res[fusion] = [(n.cpu().numpy(), dd.cpu().numpy()) for _, _, n, dd in items]
-    for (nf, df), (ns, ds) in zip(res[2], res[P.PRNU_SDA_SEPARATE]):
+    for (nf, df), (ns, ds) in zip(res[P.PRNU_SDA_FUSED], res[P.PRNU_SDA_SEPARATE]):
         np.testing.assert_array_equal(nf, ns)
         np.testing.assert_array_equal(df, ds)
-    for fr, (H, W, C, m, d), (nf, df) in zip(frames, specs, res[2]):
+    for fr, (H, W, C, m, d), (nf, df) in zip(frames, specs, res[P.PRNU_SDA_FUSED]):
         onum, oden = O.fingerprint_accumulate(fr.numpy(), d)
         assert _rel(nf, onum) <= K_TOL and _rel(df, oden) <= K_TOL
