@@ -93,9 +93,9 @@ typedef struct {
                               where that applies -- uint8 frames, C = 1 or 3, W a multiple of 2^levels with
                               W*C a multiple of 16, 16-byte aligned frames and strides, groups of at most 257
                               frames -- else the separate kernels.  0 (default): fused in
-                              prnu_fingerprint_accumulate with device frames (one stream) for d >= 16,
-                              separate for shorter groups and in prnu_fingerprint_accumulate_multi (groups of
-                              different sizes balance better there); PRNU_SDA_SEPARATE: always separate;
+                              prnu_fingerprint_accumulate with device frames (one stream) for d >= 16 and in
+                              a pass of prnu_fingerprint_accumulate_multi whose groups average 16 frames or
+                              more, separate for shorter groups; PRNU_SDA_SEPARATE: always separate;
                               PRNU_SDA_FUSED: fused in both wherever it applies, row strips chosen per launch;
                               n >= 1 (at most 256): the same with n row strips per column */
 } prnu_params;
