@@ -219,7 +219,7 @@ constexpr int ICS = IC + 2;                      // even row stride: float2-alig
 constexpr int NCOL = (IC + 31) / 32;             // input columns per thread
 
 template <bool LEVEL1, class T>
-__global__ void __launch_bounds__(256) k_analysis(AnaArgs a) {
+__global__ void __launch_bounds__(256, 5) k_analysis(AnaArgs a) {
     __shared__ __align__(16) float vh[IR][ICS];
     __shared__ __align__(16) float vl[LEVEL1 ? 1 : IR][LEVEL1 ? 2 : ICS];
     __shared__ float rh[IR][TQ + 1], rl[LEVEL1 ? 1 : IR][LEVEL1 ? 1 : TQ + 1];
@@ -241,16 +241,34 @@ __global__ void __launch_bounds__(256) k_analysis(AnaArgs a) {
         srcx[k] = LEVEL1 ? mirror(gx, a.W) : gx;
     }
     const int srcH = LEVEL1 ? a.H : a.R, srcW = LEVEL1 ? a.W : a.Cc;
-    for (int r = ty; r < IR; r += 8) {
-        const int gy = wrap_near(2 * p0 + r, a.R);
-        const int sy = LEVEL1 ? mirror(gy, a.H) : gy;
-        const long long rowoff = ((long long)plane * srcH + sy) * srcW;
+    // above level 1, tiles whose ICS columns lie inside the row (no wrap)
+    // arrive as 16-byte copies of both parts
+    const bool chunks = !LEVEL1 && (srcW & 3) == 0 && 2 * q0 + ICS <= srcW &&
+                        ((reinterpret_cast<uintptr_t>(a.inh) | reinterpret_cast<uintptr_t>(a.inl)) & 15u) == 0;
+    if (chunks) {
+        const int tid = ty * 32 + tx;
+        for (int it = tid; it < IR * (ICS / 4); it += 256) {
+            const int r = it / (ICS / 4), j = it - r * (ICS / 4);
+            const int sy = wrap_near(2 * p0 + r, a.R);
+            const long long off = ((long long)plane * srcH + sy) * srcW + 2 * q0 + 4 * j;
+            if (!PRNU_DCHECK(sy >= 0 && sy < srcH && 2 * q0 + 4 * j + 3 < srcW, off)) continue;
+            ring_cp16(&vh[r][4 * j], a.inh + off);
+            if (!LEVEL1) ring_cp16(&vl[r][4 * j], a.inl + off);
+        }
+        ring_commit();
+        ring_wait<0>();
+    } else {
+        for (int r = ty; r < IR; r += 8) {
+            const int gy = wrap_near(2 * p0 + r, a.R);
+            const int sy = LEVEL1 ? mirror(gy, a.H) : gy;
+            const long long rowoff = ((long long)plane * srcH + sy) * srcW;
 #pragma unroll
-        for (int k = 0; k < NCOL; ++k) {
-            const int c = tx + 32 * k;
-            if (c < IC && PRNU_DCHECK(sy >= 0 && sy < srcH && srcx[k] >= 0 && srcx[k] < srcW, rowoff + srcx[k])) {
-                vh[r][c] = __ldg(a.inh + rowoff + srcx[k]);
-                if (!LEVEL1) vl[r][c] = __ldg(a.inl + rowoff + srcx[k]);
+            for (int k = 0; k < NCOL; ++k) {
+                const int c = tx + 32 * k;
+                if (c < IC && PRNU_DCHECK(sy >= 0 && sy < srcH && srcx[k] >= 0 && srcx[k] < srcW, rowoff + srcx[k])) {
+                    vh[r][c] = __ldg(a.inh + rowoff + srcx[k]);
+                    if (!LEVEL1) vl[r][c] = __ldg(a.inl + rowoff + srcx[k]);
+                }
             }
         }
     }
@@ -294,32 +312,42 @@ __global__ void __launch_bounds__(256) k_analysis(AnaArgs a) {
     }
     __syncthreads();
 
-    // 3) column pass
+    // 3) column pass: thread (tx, ty) owns output rows 2ty, 2ty+1 of column q =
+    //    tx, which read input rows 4ty .. 4ty+9 (six of them shared), each read
+    //    once from shared memory
     const float scale = a.scale_on ? __frcp_rn((float)a.sc.count(plane)) : 1.f;
-    const int q = tx;
+    const int q = tx, qq = q0 + q;
+    float ch[10], cl[10], cs[10], ct[10];
 #pragma unroll
-    for (int pl = ty; pl < TP; pl += 8) {
-        const int p = p0 + pl, qq = q0 + q;
+    for (int j = 0; j < 10; ++j) {
+        const int y = 4 * ty + j;
+        ch[j] = rh[y][q];
+        cl[j] = LEVEL1 ? 0.f : rl[y][q];
+        cs[j] = ss[y][q];
+        ct[j] = tt[y][q];
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int p = p0 + 2 * ty + e;
         if (p >= R2 || qq >= C2) continue;
-        const int y0 = 2 * pl;
-        const float r0h = rh[y0][q];
-        const float r0l = LEVEL1 ? 0.f : rl[y0][q];
+        const float r0h = ch[2 * e];
+        const float r0l = cl[2 * e];
         float A = 0.f, B = 0.f;
 #pragma unroll
         for (int j = 1; j < kTaps; ++j) {
-            float D = __fsub_rn(rh[y0 + j][q], r0h);
-            if (!LEVEL1) D = __fadd_rn(D, __fsub_rn(rl[y0 + j][q], r0l));
+            float D = __fsub_rn(ch[2 * e + j], r0h);
+            if (!LEVEL1) D = __fadd_rn(D, __fsub_rn(cl[2 * e + j], r0l));
             A = __fmaf_rn(a.f.h[j], D, A);
             B = __fmaf_rn(a.f.g[j], D, B);
         }
         float Sh = 0.f, Sg = 0.f, Th = 0.f, Tg = 0.f;
 #pragma unroll
         for (int j = 0; j < kTaps; ++j) {
-            const float s = ss[y0 + j][q], t = tt[y0 + j][q];
-            Sh = __fmaf_rn(a.f.h[j], s, Sh);
-            Sg = __fmaf_rn(a.f.g[j], s, Sg);
-            Th = __fmaf_rn(a.f.h[j], t, Th);
-            Tg = __fmaf_rn(a.f.g[j], t, Tg);
+            const float sv = cs[2 * e + j], tv = ct[2 * e + j];
+            Sh = __fmaf_rn(a.f.h[j], sv, Sh);
+            Sg = __fmaf_rn(a.f.g[j], sv, Sg);
+            Th = __fmaf_rn(a.f.h[j], tv, Th);
+            Tg = __fmaf_rn(a.f.g[j], tv, Tg);
         }
         const float llsmall = __fmaf_rn(kSqrt2f, A, Sh);
         const float lh = __fmaf_rn(kSqrt2f, B, Sg);
