@@ -18,9 +18,42 @@ constexpr int kMaxRadius = 4;  // windows up to 9 x 9
 // Filter bank in float32, passed by value to kernels (kernel parameters live
 // in the constant bank).  g[k] = (-1)^k h[7-k].
 struct Filt {
-    float h[kTaps];
-    float g[kTaps];
+    __align__(8) float h[kTaps];
+    __align__(8) float g[kTaps];
+    __align__(8) float hg[kTaps][2];  // (h[k], g[k]) side by side, for packed float32x2 arithmetic
 };
+
+// ---- packed float32x2 FMA (Blackwell): two independent round-to-nearest
+// FMAs in one instruction, so the bits equal those of two scalar __fmaf_rn.
+using pf2 = unsigned long long;  // {lo lane, hi lane}
+__device__ __forceinline__ pf2 pf2_of(float a, float b) {
+    pf2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void pf2_split(pf2 v, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ pf2 pf2_fma(pf2 a, pf2 b, pf2 c) {
+    pf2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ pf2 pf2_at(const float *p) { return *reinterpret_cast<const pf2 *>(p); }  // 8-byte aligned
+// analysis: the low- and high-pass accumulators of one output advance together,
+// {x, y} += {h_k, g_k} * {d, d}
+__device__ __forceinline__ pf2 hg_of(const Filt &f, int k) { return pf2_at(&f.hg[k][0]); }
+// synthesis of an output pair: v_e = sum_{t=0..3} h[e+2t] x[t] + g[e+2t] y[t]
+// (in that order) for e = 0, 1, as {v_0, v_1} += {h[2t], h[2t+1]} * {x[t], x[t]}, ...
+__device__ __forceinline__ void synth_pair2(const Filt &f, const float *x, const float *y, float &v0, float &v1) {
+    pf2 acc = pf2_of(0.f, 0.f);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        acc = pf2_fma(pf2_at(&f.h[2 * t]), pf2_of(x[t], x[t]), acc);
+        acc = pf2_fma(pf2_at(&f.g[2 * t]), pf2_of(y[t], y[t]), acc);
+    }
+    pf2_split(acc, v0, v1);
+}
 
 // Local-variance windows.
 struct Win {

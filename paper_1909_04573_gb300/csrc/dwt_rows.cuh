@@ -16,18 +16,16 @@ constexpr float kSqrt2f = 1.41421356237309504880f;
 template <bool LEVEL1>
 __device__ __forceinline__ void row_math(const Filt &f, const float *v, const float *w, float &rh, float &rl,
                                          float &s, float &t) {
-    float ss = 0.f, tt = 0.f;
+    pf2 st = pf2_of(0.f, 0.f);  // {s, t}
 #pragma unroll
     for (int k = 1; k < kTaps; ++k) {
         float dlt = __fsub_rn(v[k], v[0]);
         if (!LEVEL1) dlt = __fadd_rn(dlt, __fsub_rn(w[k], w[0]));
-        ss = __fmaf_rn(f.h[k], dlt, ss);
-        tt = __fmaf_rn(f.g[k], dlt, tt);
+        st = pf2_fma(hg_of(f, k), pf2_of(dlt, dlt), st);
     }
     rh = v[0];
     rl = LEVEL1 ? 0.f : w[0];
-    s = ss;
-    t = tt;
+    pf2_split(st, s, t);
 }
 
 // Column pass over the row-pass results of input rows 2p..2p+7, held in an
@@ -38,24 +36,24 @@ template <bool LEVEL1, class T>
 __device__ __forceinline__ void col_store(const AnaArgs &a, const float *rh, const float *rl, const float *rs,
                                           const float *rt, int b0, long long o, float scale) {
     const float r0h = rh[b0], r0l = rl[b0];
-    float A = 0.f, B = 0.f;
+    pf2 AB = pf2_of(0.f, 0.f), S = pf2_of(0.f, 0.f), Tp = pf2_of(0.f, 0.f);  // {A, B}, {Sh, Sg}, {Th, Tg}
 #pragma unroll
     for (int k = 1; k < kTaps; ++k) {
         const int sl = (b0 + k) & 7;
         float D = __fsub_rn(rh[sl], r0h);
         if (!LEVEL1) D = __fadd_rn(D, __fsub_rn(rl[sl], r0l));
-        A = __fmaf_rn(a.f.h[k], D, A);
-        B = __fmaf_rn(a.f.g[k], D, B);
+        AB = pf2_fma(hg_of(a.f, k), pf2_of(D, D), AB);
     }
-    float Sh = 0.f, Sg = 0.f, Th = 0.f, Tg = 0.f;
 #pragma unroll
     for (int k = 0; k < kTaps; ++k) {
         const int sl = (b0 + k) & 7;
-        Sh = __fmaf_rn(a.f.h[k], rs[sl], Sh);
-        Sg = __fmaf_rn(a.f.g[k], rs[sl], Sg);
-        Th = __fmaf_rn(a.f.h[k], rt[sl], Th);
-        Tg = __fmaf_rn(a.f.g[k], rt[sl], Tg);
+        S = pf2_fma(hg_of(a.f, k), pf2_of(rs[sl], rs[sl]), S);
+        Tp = pf2_fma(hg_of(a.f, k), pf2_of(rt[sl], rt[sl]), Tp);
     }
+    float A, B, Sh, Sg, Th, Tg;
+    pf2_split(AB, A, B);
+    pf2_split(S, Sh, Sg);
+    pf2_split(Tp, Th, Tg);
     const float llsmall = __fmaf_rn(kSqrt2f, A, Sh);
     const float lh = __fmaf_rn(kSqrt2f, B, Sg);
     if (a.LLh) {

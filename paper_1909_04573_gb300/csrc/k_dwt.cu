@@ -296,16 +296,10 @@ __global__ void __launch_bounds__(256, 5) k_analysis(AnaArgs a) {
                     w[2 * j + 1] = t.y;
                 }
             }
-            float s = 0.f, t = 0.f;
-#pragma unroll
-            for (int k = 1; k < kTaps; ++k) {
-                float dlt = __fsub_rn(v[k], v[0]);
-                if (!LEVEL1) dlt = __fadd_rn(dlt, __fsub_rn(w[k], w[0]));
-                s = __fmaf_rn(a.f.h[k], dlt, s);
-                t = __fmaf_rn(a.f.g[k], dlt, t);
-            }
-            rh[r][q] = v[0];
-            if (!LEVEL1) rl[r][q] = w[0];
+            float h0, l0, s, t;
+            row_math<LEVEL1>(a.f, v, w, h0, l0, s, t);
+            rh[r][q] = h0;
+            if (!LEVEL1) rl[r][q] = l0;
             ss[r][q] = s;
             tt[r][q] = t;
         }
@@ -332,23 +326,23 @@ __global__ void __launch_bounds__(256, 5) k_analysis(AnaArgs a) {
         if (p >= R2 || qq >= C2) continue;
         const float r0h = ch[2 * e];
         const float r0l = cl[2 * e];
-        float A = 0.f, B = 0.f;
+        pf2 AB = pf2_of(0.f, 0.f), S = pf2_of(0.f, 0.f), Tp = pf2_of(0.f, 0.f);  // {A, B}, {Sh, Sg}, {Th, Tg}
 #pragma unroll
         for (int j = 1; j < kTaps; ++j) {
             float D = __fsub_rn(ch[2 * e + j], r0h);
             if (!LEVEL1) D = __fadd_rn(D, __fsub_rn(cl[2 * e + j], r0l));
-            A = __fmaf_rn(a.f.h[j], D, A);
-            B = __fmaf_rn(a.f.g[j], D, B);
+            AB = pf2_fma(hg_of(a.f, j), pf2_of(D, D), AB);
         }
-        float Sh = 0.f, Sg = 0.f, Th = 0.f, Tg = 0.f;
 #pragma unroll
         for (int j = 0; j < kTaps; ++j) {
             const float sv = cs[2 * e + j], tv = ct[2 * e + j];
-            Sh = __fmaf_rn(a.f.h[j], sv, Sh);
-            Sg = __fmaf_rn(a.f.g[j], sv, Sg);
-            Th = __fmaf_rn(a.f.h[j], tv, Th);
-            Tg = __fmaf_rn(a.f.g[j], tv, Tg);
+            S = pf2_fma(hg_of(a.f, j), pf2_of(sv, sv), S);
+            Tp = pf2_fma(hg_of(a.f, j), pf2_of(tv, tv), Tp);
         }
+        float A, B, Sh, Sg, Th, Tg;
+        pf2_split(AB, A, B);
+        pf2_split(S, Sh, Sg);
+        pf2_split(Tp, Th, Tg);
         const float llsmall = __fmaf_rn(kSqrt2f, A, Sh);
         const float lh = __fmaf_rn(kSqrt2f, B, Sg);
         const long long o = ((long long)plane * R2 + p) * C2 + qq;

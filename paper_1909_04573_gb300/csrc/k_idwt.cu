@@ -53,20 +53,13 @@ __device__ __forceinline__ void synth_cols(SynTile &s, const Filt &f, int tid) {
             u[t] = s.c[2][m + 3 - t][c];
             v[t] = s.c[3][m + 3 - t][c];
         }
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            float lo = 0.f, hi = 0.f;
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const float hk = f.h[e + 2 * t], gk = f.g[e + 2 * t];
-                lo = __fmaf_rn(hk, a[t], lo);
-                lo = __fmaf_rn(gk, b[t], lo);
-                hi = __fmaf_rn(hk, u[t], hi);
-                hi = __fmaf_rn(gk, v[t], hi);
-            }
-            s.lo[2 * m + e][c] = lo;
-            s.hi[2 * m + e][c] = hi;
-        }
+        float lo0, lo1, hi0, hi1;
+        synth_pair2(f, a, b, lo0, lo1);
+        synth_pair2(f, u, v, hi0, hi1);
+        s.lo[2 * m][c] = lo0;
+        s.lo[2 * m + 1][c] = lo1;
+        s.hi[2 * m][c] = hi0;
+        s.hi[2 * m + 1][c] = hi1;
     }
 }
 
@@ -78,18 +71,9 @@ __device__ __forceinline__ float2 synth_pair(const SynTile &s, const Filt &f, in
         l[t] = s.lo[y][n + 3 - t];
         h[t] = s.hi[y][n + 3 - t];
     }
-    float o[2];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        float v = 0.f;
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            v = __fmaf_rn(f.h[e + 2 * t], l[t], v);
-            v = __fmaf_rn(f.g[e + 2 * t], h[t], v);
-        }
-        o[e] = v;
-    }
-    return make_float2(o[0], o[1]);
+    float o0, o1;
+    synth_pair2(f, l, h, o0, o1);
+    return make_float2(o0, o1);
 }
 
 template <class T>
@@ -386,21 +370,21 @@ __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
 #pragma unroll
             for (int mm = 0; mm < 2; ++mm) {
                 const int m = 2 * ty + mm;
+                float c0[4], c1[4], c2[4], c3[4];  // coefficient row m - t is tile row m + 3 - t
 #pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    float lo = 0.f, hi = 0.f;
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {  // coefficient row m - t is tile row m + 3 - t
-                        const float hk = a.f.h[e + 2 * t], gk = a.f.g[e + 2 * t];
-                        const float *r = q[mm + 3 - t];
-                        lo = __fmaf_rn(hk, r[0], lo);
-                        lo = __fmaf_rn(gk, r[1], lo);
-                        hi = __fmaf_rn(hk, r[2], hi);
-                        hi = __fmaf_rn(gk, r[3], hi);
-                    }
-                    s.lh[2 * m + e][tx] = lo;
-                    s.lh[2 * m + e][AC_W + tx] = hi;
+                for (int t = 0; t < 4; ++t) {
+                    c0[t] = q[mm + 3 - t][0];
+                    c1[t] = q[mm + 3 - t][1];
+                    c2[t] = q[mm + 3 - t][2];
+                    c3[t] = q[mm + 3 - t][3];
                 }
+                float lo0, lo1, hi0, hi1;
+                synth_pair2(a.f, c0, c1, lo0, lo1);
+                synth_pair2(a.f, c2, c3, hi0, hi1);
+                s.lh[2 * m][tx] = lo0;
+                s.lh[2 * m + 1][tx] = lo1;
+                s.lh[2 * m][AC_W + tx] = hi0;
+                s.lh[2 * m + 1][AC_W + tx] = hi1;
             }
         }
         __syncthreads();
@@ -419,16 +403,7 @@ __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
                 h[t] = s.lh[y][AC_W + n + 3 - t];
             }
             float w[2];
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                float v = 0.f;
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    v = __fmaf_rn(a.f.h[e + 2 * t], l[t], v);
-                    v = __fmaf_rn(a.f.g[e + 2 * t], h[t], v);
-                }
-                w[e] = v;
-            }
+            synth_pair2(a.f, l, h, w[0], w[1]);
             const float2 xv = *reinterpret_cast<const float2 *>(&s.x[b][y][2 * n]);
             const float I0 = xv.x * inv_n;
             const float I1 = two ? xv.y * inv_n : 0.f;
@@ -528,20 +503,18 @@ __device__ __forceinline__ void stream_synth(const T *LL, const T *LH, const T *
             epi.prefetch(2 * m, 2 * n, out_lane, outH, outW);  // the epilogue's inputs, beside them
             // column synthesis: rows 2m + e of lo (LL, LH) and hi (HL, HH)
             float lo[2], hi[2];
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                float l = 0.f, h = 0.f;
+            {
+                float c0[4], c1[4], c2[4], c3[4];  // coefficient row m - t
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     const float *r = q[(j + 3 - t) & 3];
-                    const float hk = f.h[e + 2 * t], gk = f.g[e + 2 * t];
-                    l = __fmaf_rn(hk, r[0], l);
-                    l = __fmaf_rn(gk, r[1], l);
-                    h = __fmaf_rn(hk, r[2], h);
-                    h = __fmaf_rn(gk, r[3], h);
+                    c0[t] = r[0];
+                    c1[t] = r[1];
+                    c2[t] = r[2];
+                    c3[t] = r[3];
                 }
-                lo[e] = l;
-                hi[e] = h;
+                synth_pair2(f, c0, c1, lo[0], lo[1]);
+                synth_pair2(f, c2, c3, hi[0], hi[1]);
             }
             // row synthesis of output rows 2m + e, columns 2n + f
 #pragma unroll
@@ -555,16 +528,7 @@ __device__ __forceinline__ void stream_synth(const T *LL, const T *LH, const T *
                     Hh[t] = __shfl_up_sync(0xffffffffu, hi[e], t);
                 }
                 float w[2];
-#pragma unroll
-                for (int fi = 0; fi < 2; ++fi) {
-                    float v = 0.f;
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        v = __fmaf_rn(f.h[fi + 2 * t], L[t], v);
-                        v = __fmaf_rn(f.g[fi + 2 * t], Hh[t], v);
-                    }
-                    w[fi] = v;
-                }
+                synth_pair2(f, L, Hh, w[0], w[1]);
                 const int y = 2 * m + e, x = 2 * n;
                 if (out_lane && y < outH && x < outW) epi(y, x, w[0], w[1], x + 1 < outW);
             }

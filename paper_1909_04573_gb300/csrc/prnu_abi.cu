@@ -697,6 +697,8 @@ prnu_status prnu_create(prnu_ctx **out, int device) {
     for (int k = 0; k < kTaps; ++k) {
         c->filt.h[k] = (float)c->h64[k];
         c->filt.g[k] = (float)((k % 2 ? -1.0 : 1.0) * c->h64[kTaps - 1 - k]);
+        c->filt.hg[k][0] = c->filt.h[k];
+        c->filt.hg[k][1] = c->filt.g[k];
     }
     if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
         delete c;
