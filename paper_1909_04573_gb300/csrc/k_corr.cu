@@ -39,10 +39,28 @@ constexpr int CT = 256;    // threads per block of the inverse row pass (its reg
 constexpr int CTW = 512;   // threads per block of the forward row and the column passes: their shared
                            // memory allows two blocks per SM, so twice the threads double the warps
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// complex arithmetic on {re, im} as packed float32x2 (each lane round-to-nearest)
+__device__ __forceinline__ pf2 pk(float2 a) { return pf2_of(a.x, a.y); }
+__device__ __forceinline__ float2 upk(pf2 v) {
+    float2 r;
+    pf2_split(v, r.x, r.y);
+    return r;
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+    pf2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk(a)), "l"(pk(b)));
+    return upk(r);
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+    pf2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk(a)), "l"(pk(b)));
+    return upk(r);
+}
+// a b = {a.x b.x - a.y b.y, a.x b.y + a.y b.x}: {-a.y b.y, a.y b.x}, then one packed FMA
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(__fmaf_rn(a.x, b.x, -a.y * b.y), __fmaf_rn(a.x, b.y, a.y * b.x));
+    pf2 p;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(p) : "l"(pf2_of(-a.y, a.y)), "l"(pf2_of(b.y, b.x)));
+    return upk(pf2_fma(pf2_of(a.x, a.x), pk(b), p));
 }
 __device__ __forceinline__ float2 cmi(float2 a) { return make_float2(a.y, -a.x); }  // -i a
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
