@@ -503,18 +503,20 @@ __device__ __forceinline__ void stream_synth(const T *LL, const T *LH, const T *
             epi.prefetch(2 * m, 2 * n, out_lane, outH, outW);  // the epilogue's inputs, beside them
             // column synthesis: rows 2m + e of lo (LL, LH) and hi (HL, HH)
             float lo[2], hi[2];
-            {
-                float c0[4], c1[4], c2[4], c3[4];  // coefficient row m - t
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                float l = 0.f, h = 0.f;
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     const float *r = q[(j + 3 - t) & 3];
-                    c0[t] = r[0];
-                    c1[t] = r[1];
-                    c2[t] = r[2];
-                    c3[t] = r[3];
+                    const float hk = f.h[e + 2 * t], gk = f.g[e + 2 * t];
+                    l = __fmaf_rn(hk, r[0], l);
+                    l = __fmaf_rn(gk, r[1], l);
+                    h = __fmaf_rn(hk, r[2], h);
+                    h = __fmaf_rn(gk, r[3], h);
                 }
-                synth_pair2(f, c0, c1, lo[0], lo[1]);
-                synth_pair2(f, c2, c3, hi[0], hi[1]);
+                lo[e] = l;
+                hi[e] = h;
             }
             // row synthesis of output rows 2m + e, columns 2n + f
 #pragma unroll
