@@ -36,6 +36,8 @@ namespace prnu {
 namespace {
 
 constexpr int CT = 256;    // threads per block of the inverse row pass (its registers allow no more)
+constexpr int CTH = 544;   // threads of the column pass of 1080-point columns: its first (radix-8)
+                           // pass over two columns of X^ and Y^ has 540 butterflies, one per thread
 constexpr int CTW = 512;   // threads per block of the forward row and the column passes: their shared
                            // memory allows two blocks per SM, so twice the threads double the warps
 
@@ -951,7 +953,7 @@ cudaError_t launch_corr_fft(const float *XY, float2 *F, float2 *tw, int n, int H
         const dim3 grid((Wh + tc - 1) / tc, n);
         const float2 *twc = tw + 2 * M + 1;
         if (H == kStaticH && tc == 2)
-            return launch<k_corr_columns<2, kStaticH, CTW>, CTW>(grid, cs, st, F, n, H, Wh, ld, ph, twc);
+            return launch<k_corr_columns<2, kStaticH, CTH>, CTH>(grid, cs, st, F, n, H, Wh, ld, ph, twc);
         if (tc == 4) return launch<k_corr_columns<4, 0, CTW>, CTW>(grid, cs, st, F, n, H, Wh, ld, ph, twc);
         if (tc == 2) return launch<k_corr_columns<2, 0, CTW>, CTW>(grid, cs, st, F, n, H, Wh, ld, ph, twc);
         return launch<k_corr_columns<1, 0, CTW>, CTW>(grid, cs, st, F, n, H, Wh, ld, ph, twc);
