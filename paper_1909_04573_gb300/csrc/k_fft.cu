@@ -31,16 +31,19 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 
 // ---------------------------------------------------------------- finalize --
 // K = num/den to float64 accuracy in float32 arithmetic (GB300's float64 rate
-// is a small fraction of its float32 rate): q0 is the float32 IEEE quotient,
-// r = num - q0 den is exact (one FMA), and q0 + r/den is carried as an
-// unevaluated float-float pair (hi, lo), accurate to O(2^-46) relative.
+// is a small fraction of its float32 rate): q0 = num * (1/den) is within about
+// an ulp of the quotient, so r = num - q0 den is exact (one FMA), and
+// q0 + r/den is carried as an unevaluated float-float pair (hi, lo), accurate
+// to O(2^-44) relative; q0 need not be the correctly rounded quotient, the
+// residual carries its error.
 struct FF {
     float hi, lo;
 };
 __device__ __forceinline__ FF div_ff(float n, float d) {
-    const float q0 = __fdiv_rn(n, d);
+    const float rd = __frcp_rn(d);
+    const float q0 = __fmul_rn(n, rd);
     const float r = __fmaf_rn(-q0, d, n);
-    return FF{q0, __fmul_rn(r, __frcp_rn(d))};
+    return FF{q0, __fmul_rn(r, rd)};
 }
 // a * (hi, lo) + (s, t) in float-float: TwoProd by FMA, then TwoSum
 __device__ __forceinline__ FF ff_fma(float a, FF x, FF acc) {
@@ -197,8 +200,10 @@ __global__ void k_moments(const float *v, long long n, const double *center, dou
     }
 }
 
-// stage 2: out[0] = center + mean, out[1] = sum of squares about center / n
-__global__ void k_moments_final(const double *part, int nb, long long n, const double *center, double *out) {
+// stage 2: out[0] = center + mean, out[1] = sum of squares about center / n,
+// less the squared mean of the deviations when `central` (one pass about 0)
+__global__ void k_moments_final(const double *part, int nb, long long n, const double *center, double *out,
+                                int central) {
     __shared__ double sh[32];
     double s = 0.0, q = 0.0;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
@@ -209,8 +214,9 @@ __global__ void k_moments_final(const double *part, int nb, long long n, const d
     q = block_sum(q, sh);
     if (threadIdx.x == 0) {
         const double c = center ? center[0] : 0.0;
-        out[0] = c + s / (double)n;
-        out[1] = q / (double)n;
+        const double m = s / (double)n;
+        out[0] = c + m;
+        out[1] = central ? q / (double)n - m * m : q / (double)n;
     }
 }
 
@@ -458,13 +464,19 @@ cudaError_t launch_zero_mean(float *K, int H, int W, double *colmean, double *ro
     return cudaGetLastError();
 }
 
-// out[0] = mean, out[1] = variance (population); two passes about the mean
+// out[0] = mean, out[1] = variance (population).  Two passes about the mean;
+// one pass (sum and sum of squares about 0, less the squared mean) for a
+// plane whose mean is known to be near zero (zero_mean), where nothing cancels.
 cudaError_t launch_mean_var(const float *v, long long n, double *part, int nb, double *tmp, double *out,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool zero_mean) {
     k_moments<<<nb, RB, 0, st>>>(v, n, nullptr, part);
-    k_moments_final<<<1, RB, 0, st>>>(part, nb, n, nullptr, tmp);
+    if (zero_mean) {
+        k_moments_final<<<1, RB, 0, st>>>(part, nb, n, nullptr, out, 1);
+        return cudaGetLastError();
+    }
+    k_moments_final<<<1, RB, 0, st>>>(part, nb, n, nullptr, tmp, 0);
     k_moments<<<nb, RB, 0, st>>>(v, n, tmp, part);
-    k_moments_final<<<1, RB, 0, st>>>(part, nb, n, tmp, out);
+    k_moments_final<<<1, RB, 0, st>>>(part, nb, n, tmp, out, 0);
     // out[0] = tmp[0] + mean of deviations (a refinement of the mean)
     return cudaGetLastError();
 }

@@ -120,7 +120,7 @@ cudaError_t launch_divide(const float *num, const float *den, const float *num_l
 cudaError_t launch_zero_mean(float *K, int H, int W, double *colmean, double *rowmean, double *part, int sms,
                              cudaStream_t st);
 cudaError_t launch_mean_var(const float *v, long long n, double *part, int nb, double *tmp, double *out,
-                            cudaStream_t st);
+                            cudaStream_t st, bool zero_mean = false);
 cudaError_t launch_magnitude_half(const cufftComplex *Fh, int H, int W, float inv_sqrt_n, float *M, int sms,
                                   cudaStream_t st);
 cudaError_t launch_apply_ratio_half(cufftComplex *Fh, const float *M, const float *Mn, int H, int W, float scale,

@@ -220,7 +220,6 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
     size_t ckpt_off = 0;  // floats of the levels before l in the checkpoint
     const int L = prm.levels;
     const int Hp = padded(H, L), Wp = padded(W, L);
-    auto F = [&](size_t off) { return reinterpret_cast<float *>(ws + off); };
     const int sdt = prm.dtype;
     const size_t es = subband_bytes(sdt);
     // typed subband k of a region holding 3 (or 1) planes groups of P planes
@@ -988,9 +987,10 @@ prnu_status prnu_fingerprint_finalize(prnu_ctx *ctx, const float *num, const flo
             float *Mn = M + hw;
             double *mom = reinterpret_cast<double *>(b + f.mom0);
             {
-                Launch t(ctx, "mean_var", st, 4);
+                const bool centred = (flags & PRNU_ZERO_MEAN) != 0;  // K's mean was just removed
+                Launch t(ctx, "mean_var", st, centred ? 2 : 4);
                 CU(launch_mean_var(K, hw, reinterpret_cast<double *>(b + f.part), kRedBlocks,
-                                   reinterpret_cast<double *>(b + f.tmp), mom, st));
+                                   reinterpret_cast<double *>(b + f.tmp), mom, st, centred));
             }
             {
                 Launch t(ctx, "cufft_r2c", st, 1);
