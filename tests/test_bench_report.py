@@ -62,3 +62,18 @@ def test_headline_parity_host_logic(monkeypatch):
     bad = dict(good, num=good["num"] * (1 + 1e-4))          # sums off by 1e-4 relative
     out = bench.headline_parity(bad, fr, onum, oden)
     assert not out["pass"] and abs(out["num_rel_l2"] - 1e-4) < 1e-5
+
+
+def test_group_sum_roofline_follows_the_fused_kernel():
+    """With the group sums fused into the level-1 analysis the group-sum
+    roofline is that kernel's (sda_dwt); with the separate kernels it is the
+    sums kernel's (sda_sum)."""
+    prof = {"sda_dwt": (10, 11.8, 7.345e10), "shrink": (80, 7.3, 2.0e10), "analysis_l1": (10, 2.8, 1.1e10)}
+    roof, sda_roof, kern, _ = bench.kernel_report(prof, 10, None, None)
+    assert roof["kernel"] == "sda_dwt" and sda_roof["kernel"] == "sda_dwt"
+    assert abs(sda_roof["bytes_per_launch"] - 7.345e9) < 1.0
+    assert abs(sda_roof["achieved"] - 7.345e9 / (11.8 / 10 / 1000.0) / 1e9) < 1e-6
+    _, sda_roof, _, _ = bench.kernel_report(_prof(), 10, None, None)
+    assert sda_roof["kernel"] == "sda_sum"
+    _, sda_roof, _, _ = bench.kernel_report({"final_mle": (1, 1.0, 1e9)}, 1, None, None)
+    assert sda_roof is None
