@@ -578,15 +578,15 @@ prnu_status accumulate_pass_multi(prnu_ctx *ctx, const PassDesc &pd, int H, int 
     sa.frame_half = prm.frame_dtype == PRNU_FRAMES_F16;
     sa.gd = dpd->g;
     const PlaneScale sc{1, 1, 0, C, dpd->g};
-    double fr = 0.0;  // frames of the pass, then their bytes
-    for (int i = 0; i < G; ++i) fr += (double)pd.g[i].n;
+    long long nfr = 0;  // frames of the pass
+    for (int i = 0; i < G; ++i) nfr += pd.g[i].n;
+    const double fr = (double)nfr * H * W * C * (sa.frame_half ? 2 : 1);  // their bytes
     // the group sums with the level-1 analysis in one kernel where it applies:
     // by default when the pass's groups average kFuseMinGroup frames or more
     const AnaArgs a1 = analysis_args(ctx, sa.out, H, W, P, prm, sc, 1, ws, lo, 1);
     const bool want = prm.sda_fusion >= 1 || prm.sda_fusion == PRNU_SDA_FUSED ||
-                      (prm.sda_fusion == 0 && fr >= (double)kFuseMinGroup * G);
+                      (prm.sda_fusion == 0 && nfr >= (long long)kFuseMinGroup * G);
     const bool fused = want && sda_dwt_applies(sa, a1, &pd);
-    fr *= (double)H * W * C * (sa.frame_half ? 2 : 1);
     if (fused) {
         const double l1 = (double)P * (a1.R / 2) * (a1.Cc / 2) * (3.0 * subband_bytes(prm.dtype) +
                                                                 (prm.levels > 1 ? 8 : 0));
