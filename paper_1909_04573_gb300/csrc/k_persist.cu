@@ -64,6 +64,7 @@ __device__ __forceinline__ float ldc(const float *p) { return __ldcg(p); }
 // Exact per-group byte sums of one row segment (as k_sda_sum: 16-byte
 // streaming loads, two 16-bit lanes per 32-bit register, flushed every 256
 // frames), transposed through shared memory into the planar X.
+constexpr int kSdaPrefetch = 8;  // frames ahead of the group sums' loads that L2 is asked for
 template <int C, int SEG>
 __device__ void st_sda(const PGroup &g, int H, int W, float *X, int y, int seg, float *sbuf, int tid) {
     constexpr int NT = SEG * C / 16;
@@ -83,12 +84,21 @@ __device__ void st_sda(const PGroup &g, int H, int W, float *X, int y, int seg, 
         const uint8_t *base = fr + (long long)y * rp + b0;
         const bool al16 = ((reinterpret_cast<uintptr_t>(fr) | (uintptr_t)fs | (uintptr_t)rp) & 15u) == 0;
         if (al16 && nb == 16) {
+            // thread 0 asks L2 for the row segment kSdaPrefetch frames ahead (bulk
+            // prefetch, fire and forget), so the 16-byte loads find it in L2
+            const uint8_t *segp = fr + (long long)y * rp + (long long)x0 * C;
+            const unsigned segb = (unsigned)(min(SEG * C, rowbytes - x0 * C) & ~15);
             for (int jb = 0; jb < g.n; jb += 256) {
                 const int je = min(g.n, jb + 256);
                 uint32_t ev[4] = {0, 0, 0, 0}, od[4] = {0, 0, 0, 0};
                 const uint8_t *p = base + (long long)jb * fs;
 #pragma unroll 4
                 for (int j = jb; j < je; ++j, p += fs) {
+                    if (tid == 0 && j + kSdaPrefetch < g.n && segb)
+                        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(
+                                         segp + (long long)(j + kSdaPrefetch) * fs),
+                                     "r"(segb)
+                                     : "memory");
                     const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(p));
                     const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
