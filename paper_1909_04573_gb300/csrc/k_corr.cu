@@ -533,6 +533,137 @@ __global__ void __launch_bounds__(NT) k_corr_columns(float2 *F, int n, int H, in
     }
 }
 
+// ------------------------------------------ 1080-point columns, four-step ---
+// The column pass of 1080-row planes as a four-step transform held in
+// registers, 1080 = 40 x 27 (n = 27 n1 + n2, k = k1 + 40 k2):
+//   A[n2][k1] = sum_{n1} x[27 n1 + n2] w_40^{n1 k1}    one thread per n2: a 40-point DFT
+//   X[k1 + 40 k2] = sum_{n2} A[n2][k1] w_1080^{n2 k1} w_27^{n2 k2}   one thread per k1: a 27-point DFT
+// with one shared-memory transpose between them (the Stockham form moves
+// every sample through shared memory once per radix pass, three times).
+// The thread of k1 forms both X^ and Y^ there, so the cross spectrum
+// Z = conj(X^) Y^ (DC bin zeroed) is made in registers, and it starts the
+// inverse right away: with m = k1 + 40 m1, j = j1 + 27 j2,
+//   C[k1][j1] = sum_{m1} Z[k1 + 40 m1] w_27^{-m1 j1} w_1080^{-k1 j1}   (27-point, same thread)
+//   y[j1 + 27 j2] = sum_{k1} C[k1][j1] w_40^{-k1 j2}                  one thread per j1: 40-point
+// The result (unnormalised, as every transform here) replaces X^.
+constexpr int K4_N1 = 40, K4_N2 = 27, K4_L = 1080;
+constexpr int K4_COLS = 2;                     // spectrum columns per block (4: 0.264 ms, 8: 0.290 ms per
+                                               // video step against 0.256 ms; three blocks per SM here)
+constexpr int K4_NT = 128;                     // threads: the first step has 2 x 27 x 2 = 108 items
+constexpr int K4_SS = K4_N1 * K4_COLS + 4;     // float2 stride of an n2 (or j1) row of the buffers
+
+// 40-point DFT in place, 8 x 5 prime-factor (no twiddles): input index
+// (5 a + 8 b) mod 40 -> output index (25 k1 + 16 k2) mod 40
+__device__ __forceinline__ void dft40(float2 *v) {
+    float2 u[5][8];
+#pragma unroll
+    for (int b = 0; b < 5; ++b)
+#pragma unroll
+        for (int a = 0; a < 8; ++a) u[b][a] = v[(5 * a + 8 * b) % 40];
+#pragma unroll
+    for (int b = 0; b < 5; ++b) Dft<8>::run(u[b]);
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) {
+        float2 t[5];
+#pragma unroll
+        for (int b = 0; b < 5; ++b) t[b] = u[b][k1];
+        Dft<5>::run(t);
+#pragma unroll
+        for (int k2 = 0; k2 < 5; ++k2) v[(25 * k1 + 16 * k2) % 40] = t[k2];
+    }
+}
+
+// 27-point DFT in place, 3 x 9 with twiddles w_27^m = w_1080^{40 m}
+__device__ __forceinline__ void dft27(float2 *v, const float2 *__restrict__ tw) {
+    float2 y[3][9];
+#pragma unroll
+    for (int b = 0; b < 9; ++b) {
+        float2 t[3] = {v[b], v[9 + b], v[18 + b]};
+        Dft<3>::run(t);
+#pragma unroll
+        for (int k1 = 0; k1 < 3; ++k1) y[k1][b] = (k1 * b == 0) ? t[k1] : cmul(t[k1], __ldg(tw + 40 * k1 * b));
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1) {
+        Dft<9>::run(y[k1]);
+#pragma unroll
+        for (int k2 = 0; k2 < 9; ++k2) v[k1 + 3 * k2] = y[k1][k2];
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void conj_all(float2 *v) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i].y = -v[i].y;
+}
+
+__global__ void __launch_bounds__(K4_NT) k_corr_columns_4s(float2 *F, int n, int Wh, int ld,
+                                                           const float2 *__restrict__ tw) {
+    extern __shared__ __align__(16) float2 sm4[];
+    float2 *S = sm4;                                 // [2][27][K4_SS]: A of X^ and Y^ after the first step
+    float2 *T = sm4 + 2 * K4_N2 * K4_SS;             // [27][K4_SS]: C after the first inverse step
+    const int q = blockIdx.y, c0 = blockIdx.x * K4_COLS, tid = threadIdx.x;
+    float2 *FX = F + (long long)q * K4_L * ld;
+    const float2 *FY = F + (long long)(n + q) * K4_L * ld;
+
+    // forward step 1: item (sequence, n2, column)
+    if (tid < 2 * K4_N2 * K4_COLS) {
+        const int col = tid % K4_COLS, r = tid / K4_COLS, n2 = r % K4_N2, sq = r / K4_N2;
+        const int c = c0 + col;
+        const float2 *src = (sq ? FY : FX) + c;
+        float2 v[K4_N1];
+#pragma unroll
+        for (int n1 = 0; n1 < K4_N1; ++n1)
+            v[n1] = (c < Wh && PRNU_DCHECK(c < ld && q < n, c)) ? src[(long long)(27 * n1 + n2) * ld]
+                                                                : make_float2(0.f, 0.f);
+        dft40(v);
+        float2 *dst = S + (sq * K4_N2 + n2) * K4_SS + col;
+#pragma unroll
+        for (int k1 = 0; k1 < K4_N1; ++k1)
+            dst[k1 * K4_COLS] = (k1 == 0 || n2 == 0) ? v[k1] : cmul(v[k1], __ldg(tw + n2 * k1));
+    }
+    __syncthreads();
+    // forward step 2 and the first inverse step: item (k1, column)
+    if (tid < K4_N1 * K4_COLS) {
+        const int col = tid % K4_COLS, k1 = tid / K4_COLS;
+        float2 a[K4_N2], b[K4_N2];
+#pragma unroll
+        for (int n2 = 0; n2 < K4_N2; ++n2) {
+            a[n2] = S[n2 * K4_SS + k1 * K4_COLS + col];
+            b[n2] = S[(K4_N2 + n2) * K4_SS + k1 * K4_COLS + col];
+        }
+        dft27(a, tw);  // X^[k1 + 40 k2] = a[k2]
+        dft27(b, tw);
+#pragma unroll
+        for (int k2 = 0; k2 < K4_N2; ++k2) {  // Z = conj(X^) Y^, conjugated for the inverse by conjugation
+            const float2 x = a[k2], y = b[k2];
+            a[k2] = make_float2(__fmaf_rn(x.x, y.x, x.y * y.y), -__fmaf_rn(x.x, y.y, -x.y * y.x));
+        }
+        if (c0 + col == 0 && k1 == 0) a[0] = make_float2(0.f, 0.f);
+        dft27(a, tw);  // conj C (before the inverse twiddle)
+        float2 *dst = T + k1 * K4_COLS + col;
+#pragma unroll
+        for (int j1 = 0; j1 < K4_N2; ++j1) {
+            const float2 cj = cconj(a[j1]);
+            dst[j1 * K4_SS] = (k1 == 0 || j1 == 0) ? cj : cmul(cj, cconj(__ldg(tw + k1 * j1)));
+        }
+    }
+    __syncthreads();
+    // inverse step 2: item (j1, column)
+    if (tid < K4_N2 * K4_COLS) {
+        const int col = tid % K4_COLS, j1 = tid / K4_COLS;
+        const int c = c0 + col;
+        float2 v[K4_N1];
+#pragma unroll
+        for (int k1 = 0; k1 < K4_N1; ++k1) v[k1] = cconj(T[j1 * K4_SS + k1 * K4_COLS + col]);
+        dft40(v);
+        if (c < Wh && PRNU_DCHECK(c < ld, c)) {
+#pragma unroll
+            for (int j2 = 0; j2 < K4_N1; ++j2) FX[(long long)(j1 + 27 * j2) * ld + c] = cconj(v[j2]);
+        }
+    }
+}
+
 __device__ __forceinline__ double block_sum_d(double v, double *sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -952,6 +1083,11 @@ cudaError_t launch_corr_fft(const float *XY, float2 *F, float2 *tw, int n, int H
         const size_t cs = cols_smem(H, tc);
         const dim3 grid((Wh + tc - 1) / tc, n);
         const float2 *twc = tw + 2 * M + 1;
+        if (H == K4_L) {  // four-step form, K4_COLS columns per block
+            const size_t s4 = (size_t)3 * K4_N2 * K4_SS * sizeof(float2);
+            const dim3 g4((Wh + K4_COLS - 1) / K4_COLS, n);
+            return launch<k_corr_columns_4s, K4_NT>(g4, s4, st, F, n, Wh, ld, twc);
+        }
         if (H == kStaticH && tc == 2)
             return launch<k_corr_columns<2, kStaticH, CTH>, CTH>(grid, cs, st, F, n, H, Wh, ld, ph, twc);
         if (tc == 4) return launch<k_corr_columns<4, 0, CTW>, CTW>(grid, cs, st, F, n, H, Wh, ld, ph, twc);
