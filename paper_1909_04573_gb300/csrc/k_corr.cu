@@ -919,24 +919,35 @@ __global__ void __launch_bounds__(32 * NW, 3) k_corr_rows_w(const float2 *__rest
             v[n2] = make_float2(e.x - o.y, e.y + o.x);
         }
         fft960_warp<true>(v, buf, twg, lane);
-        float fe = 0.f;
+        // energy outside the neighbourhood of zero shift (only the rows within r
+        // of row 0 test columns), the row's first maximum in this lane, C(0, 0)
+        float fe = 0.f, rv = -__int_as_float(0x7f800000);
+        int rx = 0;
         const bool ynear = min(y, H - y) <= r;
-        for (int m = lane; m < RM; m += 32) {
-            const float2 val = buf[m];  // C(y, 2m), C(y, 2m + 1)
-            const int x0 = 2 * m, x1 = 2 * m + 1;
-            if (!(ynear && min(x0, W - x0) <= r)) fe = __fmaf_rn(val.x, val.x, fe);
-            if (!(ynear && min(x1, W - x1) <= r)) fe = __fmaf_rn(val.y, val.y, fe);
-            const long long i0 = (long long)y * W + x0;
-            if (val.x > bv || (val.x == bv && i0 < bi)) {
-                bv = val.x;
-                bi = i0;
+        if (ynear) {
+            for (int m = lane; m < RM; m += 32) {
+                const float2 val = buf[m];  // C(y, 2m), C(y, 2m + 1)
+                const int x0 = 2 * m, x1 = 2 * m + 1;
+                if (min(x0, W - x0) > r) fe = __fmaf_rn(val.x, val.x, fe);
+                if (min(x1, W - x1) > r) fe = __fmaf_rn(val.y, val.y, fe);
+                if (val.x > rv) { rv = val.x; rx = x0; }
+                if (val.y > rv) { rv = val.y; rx = x1; }
             }
-            if (val.y > bv || (val.y == bv && i0 + 1 < bi)) {
-                bv = val.y;
-                bi = i0 + 1;
+        } else {
+            for (int m = lane; m < RM; m += 32) {
+                const float2 val = buf[m];
+                fe = __fmaf_rn(val.x, val.x, fe);
+                fe = __fmaf_rn(val.y, val.y, fe);
+                if (val.x > rv) { rv = val.x; rx = 2 * m; }
+                if (val.y > rv) { rv = val.y; rx = 2 * m + 1; }
             }
-            if (y == 0 && m == 0) c0[q] = val.x;
         }
+        // rows come in increasing order per lane, so a tie keeps the earlier (smaller) index
+        if (rv > bv) {
+            bv = rv;
+            bi = (long long)y * W + rx;
+        }
+        if (y == 0 && lane == 0) c0[q] = buf[0].x;
         acc += (double)fe;
         __syncwarp();  // buf is rewritten by the warp's next row
     }
