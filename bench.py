@@ -91,7 +91,7 @@ NCU_NAME = {"shrink": "k_shrink_strip<0, float>", "sda_sum": "k_sda_sum<3, 1024,
             "analysis_l1": "k_analysis_stream<1, float, 32, 2>", "analysis": "k_analysis<0, float>",
             "synthesis": "k_synthesis_stream<0, float>", "final_mle": "k_final_async<0, float>",
             "final_pce": "k_final_pce<1>", "pce_fft_rows": "k_rfft_rows_w<4>",
-            "pce_fft_columns": "k_corr_columns<2, 1080, 544>", "pce_fft_rows_inverse": "k_corr_rows_w<4>",
+            "pce_fft_columns": "k_corr_columns_4s", "pce_fft_rows_inverse": "k_corr_rows_w<4>",
             "pce_outputs": "k_pce_outputs"}
 
 def dram_traffic(kernel_symbol):
