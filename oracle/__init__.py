@@ -14,8 +14,11 @@ Contents:
   grad.py          FP64 vector-Jacobian products of weighted SDA, residual,
                    MLE and PCE, and of the whole chain (mean PCE of queries)
 
-Parity unpinned: the exact denoiser output on natural-looking content is fixed
-only by this literal restatement; the tests pin every invariant around it.
+Pins: tests/test_oracle_*.py hold every function to textbook values, closed
+forms, invariants or brute force; the exact denoiser output on natural-looking
+content is held to an independent computation of the definition (explicit
+orthogonal level matrices from the published taps, a library periodic box
+filter, the transposed matrices as the inverse).
 """
 from .pipeline import (DEFAULT, TO_GRAY, WIENER_DFT, ZERO_MEAN, Params, PCEResult,  # noqa: F401
                        cross_correlation, denoise_plane, dwt2_level, fingerprint_accumulate,

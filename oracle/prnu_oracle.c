@@ -25,8 +25,11 @@
  *   MLE (Sec. III-A equation for K-hat, and its SDA form in Sec. III-B):
  *       num += W.I, den += I.I accumulated over the frames (or SDA frames).
  *
- * The parity-unpinned part (the exact denoiser output on natural-looking
- * content) is checked only through the invariants in tests/test_oracle_*.py.
+ * Pins (tests/test_oracle_*.py) hold these loops to textbook values,
+ * invariants and brute force; the exact denoiser output on natural-looking
+ * content is held to an independent computation of the same definition
+ * (explicit orthogonal level matrices from the published taps, a library box
+ * filter for the window means, the transposed matrices for the inverse).
  */
 #include <stdint.h>
 #include <stdlib.h>

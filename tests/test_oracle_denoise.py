@@ -1,4 +1,6 @@
 """Pins of the oracle's denoiser F and residual W = I - F(I) (CPU only)."""
+import os
+
 import numpy as np
 import pytest
 from scipy import ndimage
@@ -112,3 +114,79 @@ def test_residual_is_small_on_smooth_content_and_carries_white_noise():
     # most of the white noise lands in the residual, little of the scene does
     assert np.corrcoef(w.ravel(), noise.ravel())[0, 1] > 0.8
     assert np.std(w - noise) < 1.0
+
+
+# ---- the whole denoiser by an independent route ----------------------------
+# The residual of a natural-looking image computed without the oracle's code:
+# the taps from the published table (Daubechies 1992, Table 6.1, N = 4), the
+# highpass by the quadrature-mirror relation, each periodised analysis level as
+# an explicit orthogonal matrix (its rows circular shifts of the taps by 2n),
+# the four levels applied to the rows and columns, numpy's symmetric padding,
+# the window means by scipy's periodic box filter, the shrink
+# n = c s0^2 / (max(0, min_w mean_w - s0^2) + s0^2) of every detail subband, and
+# the inverse as the transposed matrices applied to (0, n) -- the noise form of
+# W = I - F(I) (the residual of Sec. II-A with the denoiser's reading).
+
+def _golden_taps():
+    path = os.path.join(os.path.dirname(__file__), "golden", "daubechies_n4_lowpass.txt")
+    with open(path) as f:
+        return np.array([float(t) for t in (ln.strip() for ln in f) if t and not t.startswith("#")])
+
+
+def _level_matrix(N, h):
+    L = len(h)
+    g = np.array([(-1.0) ** k * h[L - 1 - k] for k in range(L)])
+    base_h, base_g = np.zeros(N), np.zeros(N)
+    for k in range(L):  # taps wrap when N < L
+        base_h[k % N] += h[k]
+        base_g[k % N] += g[k]
+    return np.vstack([np.roll(base_h, 2 * n) for n in range(N // 2)] +
+                     [np.roll(base_g, 2 * n) for n in range(N // 2)])
+
+
+def _residual_by_matrices(img, s0=3.0, levels=4, windows=(3, 5, 7, 9)):
+    H, W = img.shape
+    step = 2 ** levels
+    Hp, Wp = -(-H // step) * step, -(-W // step) * step
+    x = np.pad(img, ((0, Hp - H), (0, Wp - W)), mode="symmetric")
+    h = _golden_taps()
+    mats, noise = [], []
+    for lv in range(levels):
+        R, C = Hp >> lv, Wp >> lv
+        Ar, Ac = _level_matrix(R, h), _level_matrix(C, h)
+        y = Ar @ x @ Ac.T              # quadrants: [lo-lo, lo-hi; hi-lo, hi-hi]
+        r, c = R // 2, C // 2
+        n = np.zeros_like(y)
+        for sl in ((slice(0, r), slice(c, C)), (slice(r, R), slice(0, c)), (slice(r, R), slice(c, C))):
+            d = y[sl]
+            m = np.min([ndimage.uniform_filter(d * d, size=w, mode="wrap") for w in windows], axis=0)
+            n[sl] = d * s0 * s0 / (np.maximum(0.0, m - s0 * s0) + s0 * s0)
+        mats.append((Ar, Ac))
+        noise.append(n)
+        x = y[:r, :c]
+    z = np.zeros((Hp >> levels, Wp >> levels))   # the noise form keeps no lowpass
+    for lv in reversed(range(levels)):
+        Ar, Ac = mats[lv]
+        n = noise[lv]
+        r, c = z.shape
+        n[:r, :c] = z
+        z = Ar.T @ n @ Ac
+    return z[:H, :W]
+
+
+@pytest.mark.parametrize("shape,seed", [((37, 50), 21), ((64, 96), 22), ((80, 48), 23)])
+def test_residual_equals_the_matrix_route(shape, seed):
+    img = _scene(*shape, seed)
+    ref = _residual_by_matrices(img)
+    got = O.residual(img)
+    # the table's 12 printed decimals bound the agreement
+    assert np.abs(got - ref).max() <= 1e-8 * np.abs(img).max()
+    assert np.abs(ref).max() > 0.5       # a non-trivial residual
+
+
+def test_matrix_route_with_other_parameters():
+    img = _scene(48, 64, 24, noise=5.0)
+    for s0, wins in ((1.0, (3, 5, 7, 9)), (5.0, (3,)), (3.0, (5, 9))):
+        ref = _residual_by_matrices(img, s0=s0, windows=wins)
+        got = O.residual(img, O.Params(sigma0=s0, windows=wins))
+        assert np.abs(got - ref).max() <= 1e-8 * np.abs(img).max(), (s0, wins)
