@@ -92,6 +92,34 @@ def test_wiener_dft_exact_properties():
     assert (ratio.real > 0).all() and (ratio.real <= 1 + 1e-12).all()
 
 
+def test_wiener_dft_equals_an_independent_route():
+    """The whole DFT Wiener step computed without the oracle's code: the 2-D
+    DFT as explicit matrices exp(-2 pi i k n / N), the magnitude scaled by
+    1/sqrt(HW), the window means of its square by scipy's periodic box filter,
+    the shrink n = M s^2 / (max(0, min_w mean_w - s^2) + s^2) with s^2 the
+    plane's variance, and the inverse DFT (conjugate matrices / HW) of the
+    spectrum scaled by n / M."""
+    from scipy import ndimage
+    rng = np.random.default_rng(12)
+    H, W = 24, 40
+    yy, xx = np.mgrid[0:H, 0:W]
+    K = (rng.normal(0, 1, size=(H, W)) + 1.5 * np.cos(2 * np.pi * 3 * xx / W)
+         + 0.8 * np.sin(2 * np.pi * (2 * yy / H + 5 * xx / W)))
+    K = K - K.mean(axis=0, keepdims=True)
+    K = K - K.mean(axis=1, keepdims=True)
+    EH = np.exp(-2j * np.pi * np.outer(np.arange(H), np.arange(H)) / H)
+    EW = np.exp(-2j * np.pi * np.outer(np.arange(W), np.arange(W)) / W)
+    F = EH @ K @ EW.T
+    M = np.abs(F) / np.sqrt(H * W)
+    s2 = float(np.mean((K - K.mean()) ** 2))
+    m = np.min([ndimage.uniform_filter(M * M, size=w, mode="wrap") for w in (3, 5, 7, 9)], axis=0)
+    n = M * s2 / (np.maximum(0.0, m - s2) + s2)
+    ref = np.real(EH.conj() @ (F * np.where(M > 0, n / np.where(M > 0, M, 1.0), 0.0)) @ EW.conj().T) / (H * W)
+    out = O.wiener_dft(K)
+    np.testing.assert_allclose(out, ref, atol=1e-11 * np.abs(K).max(), rtol=0)
+    assert np.linalg.norm(out - K) > 0.05 * np.linalg.norm(K)   # the filter does something here
+
+
 def _brute_correlation(X, Y):
     H, W = X.shape
     C = np.zeros((H, W))
