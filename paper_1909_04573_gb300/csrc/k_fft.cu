@@ -10,6 +10,8 @@
 #include <cufft.h>
 
 #include <algorithm>
+#include <climits>
+#include <cmath>
 
 #include "kernels.cuh"
 
@@ -68,29 +70,43 @@ __global__ void k_divide(const float *num, const float *den, const float *num_lo
                          int C, int gray, float *K) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < hw;
          i += (long long)gridDim.x * blockDim.x) {
+        // every load of the pixel first, so their latencies overlap (no load
+        // waits on a value loaded before it)
+        float dv[3] = {0.f, 0.f, 0.f}, nv[3] = {0.f, 0.f, 0.f}, dlv[3] = {0.f, 0.f, 0.f}, nlv[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (c < C) {
+                const long long o = c * hw + i;
+                dv[c] = den[o];
+                nv[c] = num[o];
+                if (num_lo) {
+                    dlv[c] = den_lo[o];
+                    nlv[c] = num_lo[o];
+                }
+            }
+        }
         FF k[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             if (c >= C) break;
-            const long long o = c * hw + i;
-            const float d = den[o];
+            const float d = dv[c];
             if (num_lo) {
                 // (n + nl) / (d + dl): q0 from the high parts, then the exact residual of the pair
-                const float dl = den_lo[o];
+                const float dl = dlv[c];
                 if (d == 0.f && dl == 0.f) {
                     k[c] = FF{0.f, 0.f};
                     continue;
                 }
                 float dh, dlo;
                 fast_two_sum(d, dl, dh, dlo);
-                const float n = num[o], nl = num_lo[o];
+                const float n = nv[c], nl = nlv[c];
                 const float q0 = __fdiv_rn(__fadd_rn(n, nl), dh);
                 // r = (n + nl) - q0 (dh + dlo), accurate to the float-float level
                 const float p = __fmul_rn(q0, dh), pe = __fmaf_rn(q0, dh, -p);
                 const float r = __fadd_rn(__fadd_rn(__fsub_rn(n, p), nl), -__fmaf_rn(q0, dlo, pe));
                 k[c] = FF{q0, __fmul_rn(r, __frcp_rn(dh))};
             } else {
-                k[c] = d != 0.f ? div_ff(num[o], d) : FF{0.f, 0.f};
+                k[c] = d != 0.f ? div_ff(nv[c], d) : FF{0.f, 0.f};
             }
         }
         if (gray) {
@@ -134,7 +150,8 @@ __global__ void k_colsum_part(const float *K, int H, int W, double *part) {
     if (x >= W) return;
     const int y0 = band * CM_BAND, y1 = min(H, y0 + CM_BAND);
     FF s{0.f, 0.f};
-    for (int y = y0; y < y1; ++y) ffa(s, K[(long long)y * W + x]);
+#pragma unroll 8
+    for (int y = y0; y < y1; ++y) ffa(s, K[(long long)y * W + x]);  // loads of 8 rows in flight
     part[(long long)band * W + x] = ffd(s);
 }
 
@@ -153,7 +170,8 @@ __global__ void k_rowmean(const float *K, int H, int W, const FF *colmean, FF *r
     __shared__ double sh[32];
     const int y = blockIdx.x;
     FF acc{0.f, 0.f};
-    for (int x = threadIdx.x; x < W; x += blockDim.x) {
+#pragma unroll 4
+    for (int x = threadIdx.x; x < W; x += blockDim.x) {  // four columns' loads in flight
         const FF d = ff_sub(K[(long long)y * W + x], colmean[x]);
         ffa(acc, d.hi);
         ffa(acc, d.lo);
@@ -163,10 +181,14 @@ __global__ void k_rowmean(const float *K, int H, int W, const FF *colmean, FF *r
 }
 
 // K - colmean - rowmean, rounded once; rows over blocks, columns over threads
-__global__ void k_sub_means(float *K, int H, int W, const FF *colmean, const FF *rowmean) {
+// (the means are separate buffers, so a column's loads need not wait for the
+// previous column's store)
+__global__ void k_sub_means(float *__restrict__ K, int H, int W, const FF *__restrict__ colmean,
+                            const FF *__restrict__ rowmean) {
     for (int y = blockIdx.x; y < H; y += gridDim.x) {
         const FF rm = rowmean[y];
         float *row = K + (long long)y * W;
+#pragma unroll 4
         for (int x = threadIdx.x; x < W; x += blockDim.x) {
             const FF cm = colmean[x];
             const FF a = ff_sub(row[x], cm);  // a.hi + a.lo = K - colmean
@@ -182,8 +204,9 @@ __global__ void k_moments(const float *v, long long n, const double *center, dou
     __shared__ double sh[32];
     const FF c = ff_of(center ? center[0] : 0.0);
     FF s{0.f, 0.f}, q{0.f, 0.f};
+#pragma unroll 4
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
+         i += (long long)gridDim.x * blockDim.x) {  // four loads in flight
         const FF d = ff_sub(v[i], c);
         ffa(s, d.hi);
         ffa(s, d.lo);
@@ -422,14 +445,32 @@ __global__ void k_pce_final(const float *c0, long long c0_stride, const double *
         for (int k = 0; k < 4; ++k) m[k] += part_m[((long long)q * nbm + i) * 4 + k];
     e = block_sum(e, sh);
     for (int k = 0; k < 4; ++k) m[k] = block_sum(m[k], sh);
+    // the peak: the largest block maximum, the smallest pixel index among
+    // equal ones (a strict order on the distinct (value, index) pairs, so the
+    // threads' strided scans and their merge find the same pair a scan in
+    // order does)
+    __shared__ float wv[32];
+    __shared__ long long wi[32];
+    float bv = -INFINITY;
+    long long bi = LLONG_MAX;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        const float v = part_v[(long long)q * nb + i];
+        const long long ix = part_i[(long long)q * nb + i];
+        if (v > bv || (v == bv && ix < bi)) { bv = v; bi = ix; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const float v = __shfl_down_sync(0xffffffffu, bv, o);
+        const long long ix = __shfl_down_sync(0xffffffffu, bi, o);
+        if (v > bv || (v == bv && ix < bi)) { bv = v; bi = ix; }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        wv[threadIdx.x >> 5] = bv;
+        wi[threadIdx.x >> 5] = bi;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        float bv = part_v[(long long)q * nb];
-        long long bi = part_i[(long long)q * nb];
-        for (int i = 1; i < nb; ++i) {
-            const float v = part_v[(long long)q * nb + i];
-            const long long ix = part_i[(long long)q * nb + i];
-            if (v > bv || (v == bv && ix < bi)) { bv = v; bi = ix; }
-        }
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (wv[w] > bv || (wv[w] == bv && wi[w] < bi)) { bv = wv[w]; bi = wi[w]; }
         out[q].c0 = (double)c0[(long long)q * c0_stride];
         out[q].energy = e;
         out[q].peak_idx = bi;
