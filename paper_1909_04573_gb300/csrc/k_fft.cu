@@ -471,6 +471,7 @@ __global__ void k_pce_final(const float *c0, long long c0_stride, const double *
     if (threadIdx.x == 0) {
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
             if (wv[w] > bv || (wv[w] == bv && wi[w] < bi)) { bv = wv[w]; bi = wi[w]; }
+        if (bi == LLONG_MAX) bi = part_i[(long long)q * nb];  // every maximum NaN: the first block's pixel
         out[q].c0 = (double)c0[(long long)q * c0_stride];
         out[q].energy = e;
         out[q].peak_idx = bi;
