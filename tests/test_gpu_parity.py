@@ -328,6 +328,39 @@ def test_invalid_arguments_are_rejected(ctx):
     assert e.value.status == P.PRNU_ENOSPC
 
 
+def test_empty_inputs_and_out_of_range_group_sizes_are_rejected(ctx):
+    """No frames, no queries, and SDA group sizes outside [1, m] (Sec. III-B
+    groups d consecutive frames of the m given) are rejected with EINVAL
+    before anything is launched: num / den keep their contents."""
+    H, W, C = 32, 64, 3
+    fr = synth.frames(synth.Camera(H=H, W=W, C=C, camera_id=5), 4).cuda()
+    p = P.default_params()
+    n = P.prnu_workspace_size(ctx.ctx, H, W, C, p, 4)
+    ws = torch.empty(n, dtype=torch.uint8, device="cuda")
+    num = torch.full((C, H, W), 7.0, device="cuda")
+    den = torch.full_like(num, 3.0)
+    fs, rp = H * W * C, W * C
+    for m, d in ((0, 1), (0, 0), (4, 0), (4, 5)):
+        with pytest.raises(P.PrnuError) as e:
+            P.prnu_fingerprint_accumulate(ctx.ctx, fr.data_ptr(), m, H, W, C, fs, rp, d, p, num.data_ptr(),
+                                          den.data_ptr(), ws.data_ptr(), n, ctx._stream())
+        assert e.value.status == P.PRNU_EINVAL, (m, d)
+    out = torch.zeros((1, C, H, W), device="cuda")
+    with pytest.raises(P.PrnuError) as e:
+        P.prnu_sda_average(ctx.ctx, fr.data_ptr(), 0, H, W, C, fs, rp, 1, out.data_ptr(), ctx._stream())
+    assert e.value.status == P.PRNU_EINVAL
+    K = torch.zeros((H, W), device="cuda")
+    q = torch.zeros((1, C, H, W), device="cuda")
+    nq = P.prnu_workspace_size_pce_images(ctx.ctx, H, W, C, p, 1)
+    wq = torch.empty(nq, dtype=torch.uint8, device="cuda")
+    with pytest.raises(P.PrnuError) as e:
+        P.prnu_pce_match_images(ctx.ctx, K.data_ptr(), q.data_ptr(), 0, H, W, C, p, 11, wq.data_ptr(), nq,
+                                ctx._stream())
+    assert e.value.status == P.PRNU_EINVAL
+    torch.cuda.synchronize()
+    assert bool((num == 7.0).all()) and bool((den == 3.0).all())
+
+
 # --------------------------------------------------------------- batches ----
 def test_denoise_residual_batch_matches_oracle(ctx):
     imgs = np.stack([_frames(72, 104, 3, 1, seed=40 + i)[0].transpose(2, 0, 1) for i in range(5)]).astype(np.float32)
