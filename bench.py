@@ -89,7 +89,7 @@ FP32_LANES_PER_SM = 128
 NCU_NAME = {"shrink": "k_shrink_strip<0, float>", "sda_sum": "k_sda_sum<3, 1024, 0>",
             "sda_dwt": "k_sda_dwt<3, 2, float>",
             "analysis_l1": "k_analysis_stream<1, float, 32, 2>", "analysis": "k_analysis<0, float>",
-            "synthesis": "k_synthesis_stream<0, float>", "final_mle": "k_final_async<0, float>",
+            "synthesis": "k_synthesis_stream<0, float>", "final_mle": "k_final_async_w<0, 2>",
             "final_pce": "k_final_pce<1>", "pce_fft_rows": "k_rfft_rows_w<4>",
             "pce_fft_columns": "k_corr_columns_4s", "pce_fft_rows_inverse": "k_corr_rows_w<4>",
             "pce_outputs": "k_pce_outputs"}

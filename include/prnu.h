@@ -455,14 +455,17 @@ prnu_status prnu_autotune(prnu_ctx *ctx, int H, int W, int C, const prnu_params 
 prnu_status prnu_autotune_set(prnu_ctx *ctx, int H, int W, const prnu_params *params, int shape);
 
 /* The tuner's per-level launch choices (prnu_autotune times every choice of
- * every level on its zero planes and keeps the fastest; 0 is the default
- * rule).  kind 0: analysis of level 2..levels (0 tiled 16 x 32 outputs,
+ * kinds 0-2 at every level on its zero planes and keeps the fastest; 0 is the
+ * default rule).  kind 0: analysis of level 2..levels (0 tiled 16 x 32 outputs,
  * 1 streaming 16 rows x 4 warps, 2 streaming 32 rows x 2 warps; all give
  * bit-identical results); kind 1: shrink of level 1..levels (0 the register
  * strip where the standard windows and a width that is a multiple of 4 allow
  * it, else the tile; 1 the 32 x 32 tile; the two sum the windows in different
  * orders); kind 2: synthesis of level 2..levels (0 streaming where its grid
- * fills the GPU, else tiled; 1 streaming; 2 tiled).
+ * fills the GPU, else tiled; 1 streaming; 2 tiled); kind 3: the level-1 MLE
+ * step of the accumulate calls, level 1 only (0 and 1 the 58 x 32 output tile
+ * where it applies -- float32 subbands, even W -- else the 32 x 32 tile; 2 the
+ * 32 x 32 tile; both give bit-identical sums).
  * choice >= 0 pins it, -1 returns it to the default, -2 only reads it;
  * *current (nullable) receives the choice in force.  Host only. */
 prnu_status prnu_autotune_level(prnu_ctx *ctx, int H, int W, const prnu_params *params, int kind, int level,

@@ -432,6 +432,241 @@ __global__ void __launch_bounds__(256, 5) k_final_async(FinalArgs a) {
 }
 
 
+// Wide-tile form of the MLE step for float32 subbands: a 58 x 32 output tile
+// needs exactly 32 coefficient columns (29 + the 3-column halo), one per
+// lane, so the column synthesis keeps every lane busy (the 32 x 32 tile's 19
+// columns leave 13 of 32 idle); in the row synthesis warp w takes output rows
+// 4w .. 4w+3 and lane n the output pair 2n, 2n+1 (29 of 32 lanes).  The
+// copies of image i+2 are in flight while image i is synthesised, as in
+// k_final_async, and every output takes the same operations in the same order
+// (column synthesis, row synthesis, then W I and I I image by image), so the
+// sums are identical.  Needs W even, Cc a multiple of 4, 16-byte aligned
+// subbands and 8-byte aligned group sums (the launcher checks).
+constexpr int AW_OW = 58, AW_OH = 32;  // output tile
+constexpr int AW_PAIRS = AW_OW / 2;    // output pairs per tile row
+constexpr int AW_CW = 32, AW_CH = 19;  // coefficient tile: columns n0-3 .. n0+28, rows m0-3 .. m0+15
+constexpr int AW_SW = 36;              // staged columns: 9 aligned 4-column chunks from (n0-3) rounded down
+template <int BUF>
+struct AsyncTileW {
+    float c[BUF][4][AW_CH][AW_SW];  // LL, LH, HL, HH
+    float x[BUF][AW_OH][AW_OW];     // the image tile (group sums)
+    float lh[AW_OH][2 * AW_CW];     // column-synthesised lo (0..31) and hi (32..63)
+};
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+template <bool COMP, int BUF>
+__global__ void __launch_bounds__(256, BUF == 2 ? 4 : 3) k_final_async_w(FinalArgs a) {
+    extern __shared__ __align__(16) unsigned char aw_smem[];
+    AsyncTileW<BUF> &s = *reinterpret_cast<AsyncTileW<BUF> *>(aw_smem);
+    const int y0 = blockIdx.y * AW_OH, x0 = blockIdx.x * AW_OW;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long hw = (long long)a.H * a.W;
+    const float *LL = static_cast<const float *>(a.LL), *LH = static_cast<const float *>(a.LH);
+    const float *HL = static_cast<const float *>(a.HL), *HH = static_cast<const float *>(a.HH);
+    const int nimg = a.G;
+    auto plane_of = [&](int i) { return i * a.C + (int)blockIdx.z; };
+    const int n0 = x0 >> 1, m0 = y0 >> 1;
+    const int cs = (n0 - 3) & ~3;    // first staged column (a multiple of 4; -4 for the first tile)
+    const int coff0 = (n0 - 3) - cs;  // staged column of n0 - 3
+    // each thread's (at most three) coefficient chunks -- subband, row, chunk -- and
+    // (at most four) image pairs, resolved once: an image's issue is a few adds per copy
+    constexpr int NCH = 4 * AW_CH * (AW_SW / 4);  // 684
+    int ck[3], coff[3], cdst[3];
+#pragma unroll
+    for (int h = 0; h < 3; ++h) {
+        const int it = tid + 256 * h;
+        ck[h] = -1;
+        coff[h] = 0;
+        cdst[h] = 0;
+        if (it < NCH) {
+            const int k = it / (AW_CH * (AW_SW / 4)), rem = it - k * (AW_CH * (AW_SW / 4));
+            const int r = rem / (AW_SW / 4), j = rem - r * (AW_SW / 4);
+            const int row = wrap_near(m0 - 3 + r, a.Rc);
+            const int col = wrap_near(cs + 4 * j, a.Cc);
+            if (PRNU_DCHECK(row >= 0 && row < a.Rc && col >= 0 && col + 3 < a.Cc, col)) {
+                ck[h] = k;
+                coff[h] = row * a.Cc + col;
+                cdst[h] = (k * AW_CH + r) * AW_SW + 4 * j;
+            }
+        }
+    }
+    long long xoff[4];
+    int xdst[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const int it = tid + 256 * h;
+        xdst[h] = -1;
+        xoff[h] = 0;
+        if (it < AW_OH * AW_PAIRS) {
+            const int yy = it / AW_PAIRS, pp = it - yy * AW_PAIRS;
+            const int gy = y0 + yy, gx = x0 + 2 * pp;
+            if (gy < a.H && PRNU_DCHECK(gx + 1 < a.W || gx >= a.W, gx) && gx < a.W) {
+                xdst[h] = yy * AW_OW + 2 * pp;
+                xoff[h] = (long long)gy * a.W + gx;
+            }
+        }
+    }
+    auto issue = [&](int plane, int b) {
+        const long long poff = (long long)plane * a.Rc * a.Cc;
+        float *cb = &s.c[b][0][0][0];
+#pragma unroll
+        for (int h = 0; h < 3; ++h) {
+            if (ck[h] < 0) continue;
+            const float *src = ck[h] == 0 ? LL : ck[h] == 1 ? LH : ck[h] == 2 ? HL : HH;
+            if (src)
+                cp_async16(cb + cdst[h], src + poff + coff[h]);
+            else
+                *reinterpret_cast<float4 *>(cb + cdst[h]) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const float *xp = a.X + (long long)plane * hw;
+        float *xb = &s.x[b][0][0];
+#pragma unroll
+        for (int h = 0; h < 4; ++h)
+            if (xdst[h] >= 0) cp_async8(xb + xdst[h], xp + xoff[h]);
+    };
+    float an[4][2], ad[4][2], anl[4][2], adl[4][2];  // [output row 4w + r][column 2n + c]
+    auto reset = [&] {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                an[r][c] = 0.f;
+                ad[r][c] = 0.f;
+                anl[r][c] = 0.f;
+                adl[r][c] = 0.f;
+            }
+    };
+    // add the thread's sums into num/den (float-float pairs with COMP)
+    auto flush = [&](float *num, float *den) {
+        if (lane >= AW_PAIRS) return;
+        const long long chw = (long long)a.C * hw;  // offset of the low parts when COMP
+        const int gx = x0 + 2 * lane;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int gy = y0 + 4 * warp + r;
+            if (gy >= a.H || gx >= a.W || !PRNU_DCHECK((int)blockIdx.z < a.C, blockIdx.z)) continue;
+            const long long o = (long long)blockIdx.z * hw + (long long)gy * a.W + gx;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                if (COMP) {
+                    float h = num[o + c], l = num[chw + o + c];
+                    ff_add(h, l, an[r][c]);
+                    l = __fadd_rn(l, anl[r][c]);
+                    num[o + c] = h;
+                    num[chw + o + c] = l;
+                    h = den[o + c];
+                    l = den[chw + o + c];
+                    ff_add(h, l, ad[r][c]);
+                    l = __fadd_rn(l, adl[r][c]);
+                    den[o + c] = h;
+                    den[chw + o + c] = l;
+                } else {
+                    num[o + c] += an[r][c];
+                    den[o + c] += ad[r][c];
+                }
+            }
+        }
+    };
+    reset();
+    int cam = a.gd ? a.gd[0].cam : -1;
+    // BUF == 3: images i+1 and i+2 in flight while image i is synthesised;
+    // BUF == 2: image i+1
+    issue(plane_of(0), 0);
+    cp_commit();
+    if (BUF == 3) {
+        if (nimg > 1) issue(plane_of(1), 1);
+        cp_commit();  // one group per image slot, empty past the last image
+    }
+    for (int i = 0; i < nimg; ++i) {
+        const int b = i % BUF;
+        const int plane = plane_of(i);
+        if (BUF == 2) {
+            cp_wait_all();    // image i landed
+            __syncthreads();  // every reader of image i-1's buffer and of lh is done
+            if (i + 1 < nimg) issue(plane_of(i + 1), (i + 1) % BUF);
+            cp_commit();
+        } else {
+            cp_wait_one();
+            __syncthreads();  // image i landed; every reader of image i-1's buffer and of lh is done
+            if (i + 2 < nimg) issue(plane_of(i + 2), (i + 2) % BUF);
+            cp_commit();
+        }
+        if (a.gd && a.gd[i].cam != cam) {  // block-uniform: the camera changes
+            flush(a.cams[cam].num, a.cams[cam].den);
+            reset();
+            cam = a.gd[i].cam;
+        }
+        // column synthesis from buffer b: warp w owns coefficient rows m = 2w, 2w+1
+        // (output rows 4w .. 4w+3), which read tile rows 2w .. 2w+4; lane = tile column
+        {
+            float q[5][4];  // [tile row - 2w][subband]
+#pragma unroll
+            for (int rr = 0; rr < 5; ++rr)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) q[rr][k] = s.c[b][k][2 * warp + rr][lane + coff0];
+#pragma unroll
+            for (int mm = 0; mm < 2; ++mm) {
+                const int m = 2 * warp + mm;
+                float c0[4], c1[4], c2[4], c3[4];  // coefficient row m - t is tile row m + 3 - t
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    c0[t] = q[mm + 3 - t][0];
+                    c1[t] = q[mm + 3 - t][1];
+                    c2[t] = q[mm + 3 - t][2];
+                    c3[t] = q[mm + 3 - t][3];
+                }
+                float lo0, lo1, hi0, hi1;
+                synth_pair2(a.f, c0, c1, lo0, lo1);
+                synth_pair2(a.f, c2, c3, hi0, hi1);
+                s.lh[2 * m][lane] = lo0;
+                s.lh[2 * m + 1][lane] = lo1;
+                s.lh[2 * m][AW_CW + lane] = hi0;
+                s.lh[2 * m + 1][AW_CW + lane] = hi1;
+            }
+        }
+        __syncthreads();
+        const float inv_n = __frcp_rn((float)a.sc.count(plane));
+        if (lane < AW_PAIRS) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int y = 4 * warp + r;
+                const int gy = y0 + y, gx = x0 + 2 * lane;
+                if (gy >= a.H || gx >= a.W) continue;
+                float l[4], h[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    l[t] = s.lh[y][lane + 3 - t];
+                    h[t] = s.lh[y][AW_CW + lane + 3 - t];
+                }
+                float w[2];
+                synth_pair2(a.f, l, h, w[0], w[1]);
+                const float2 xv = *reinterpret_cast<const float2 *>(&s.x[b][y][2 * lane]);
+                const float I0 = xv.x * inv_n, I1 = xv.y * inv_n;
+                if (COMP) {
+                    ff_add(an[r][0], anl[r][0], w[0] * I0);
+                    ff_add(ad[r][0], adl[r][0], I0 * I0);
+                    ff_add(an[r][1], anl[r][1], w[1] * I1);
+                    ff_add(ad[r][1], adl[r][1], I1 * I1);
+                } else {
+                    an[r][0] = __fmaf_rn(w[0], I0, an[r][0]);
+                    ad[r][0] = __fmaf_rn(I0, I0, ad[r][0]);
+                    an[r][1] = __fmaf_rn(w[1], I1, an[r][1]);
+                    ad[r][1] = __fmaf_rn(I1, I1, ad[r][1]);
+                }
+            }
+        }
+    }
+    cp_wait_all();  // no copy in flight at exit (the trailing groups are empty)
+    if (a.gd)
+        flush(a.cams[cam].num, a.cams[cam].den);
+    else
+        flush(a.num, a.den);
+}
+
 // ---------------------------------------------------------------------------
 // Residual mode with float32 subbands, streaming: a warp owns 32 coefficient
 // columns n0 .. n0+31 of one plane and walks a strip of coefficient rows,
@@ -746,6 +981,25 @@ static void launch_final_t(const FinalArgs &a, bool mle, cudaStream_t st) {
         k_final<true, T, false><<<grid, block, 0, st>>>(a);
 }
 
+// MLE mode, wide tile: float32 subbands (16-byte aligned, Cc a multiple of 4
+// so no staged chunk straddles the periodic wrap), even W and 8-byte aligned
+// group sums
+constexpr int kFinalWideBuf = 2;
+static bool final_wide_ok(const FinalArgs &a) {
+    const uintptr_t sb = (a.LL ? reinterpret_cast<uintptr_t>(a.LL) : 0) | reinterpret_cast<uintptr_t>(a.LH) |
+                         reinterpret_cast<uintptr_t>(a.HL) | reinterpret_cast<uintptr_t>(a.HH);
+    return a.sdt == SB_F32 && a.Cc % 4 == 0 && a.W % 2 == 0 && (sb & 15u) == 0 &&
+           (reinterpret_cast<uintptr_t>(a.X) & 7u) == 0;
+}
+template <bool COMP>
+static void launch_final_wide(const FinalArgs &a, cudaStream_t st) {
+    constexpr int BUF = kFinalWideBuf;
+    const size_t smem = sizeof(AsyncTileW<BUF>);
+    cudaFuncSetAttribute(k_final_async_w<COMP, BUF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const dim3 grid((unsigned)((a.W + AW_OW - 1) / AW_OW), (unsigned)((a.H + AW_OH - 1) / AW_OH), (unsigned)a.C);
+    k_final_async_w<COMP, BUF><<<grid, 256, smem, st>>>(a);
+}
+
 // MLE mode: the copy-pipelined kernel for every subband type
 template <class T>
 static void launch_final_async_mle(const FinalArgs &a, cudaStream_t st) {
@@ -765,7 +1019,14 @@ static void launch_final_stream(const FinalArgs &a, cudaStream_t st) {
         k_final_stream<false, T><<<stream_grid(a.Rc, a.Cc, a.C * a.G), 32 * FS_WARPS, 0, st>>>(a);
 }
 
-cudaError_t launch_final(const FinalArgs &a, bool mle, cudaStream_t st) {
+cudaError_t launch_final(const FinalArgs &a, bool mle, cudaStream_t st, int choice) {
+    if (mle && choice != 2 && final_wide_ok(a)) {
+        if (a.compensated)
+            launch_final_wide<true>(a, st);
+        else
+            launch_final_wide<false>(a, st);
+        return cudaGetLastError();
+    }
     if (mle) {
         if (a.sdt == SB_F16)
             launch_final_async_mle<__half>(a, st);

@@ -59,7 +59,10 @@ constexpr int kAnaChoices = 3;
 constexpr int kShrinkChoices = 2;
 // synthesis (levels >= 2): 0 streaming where its grid fills the GPU, else tiled; 1 streaming; 2 tiled
 constexpr int kSynChoices = 3;
-enum TuneKind : int { kTuneAnalysis = 0, kTuneShrink = 1, kTuneSynthesis = 2 };
+// level-1 MLE step: 0 and 1 the 58 x 32 wide tile where it applies (float32 subbands, even W), else
+// the 32 x 32 tile; 2 the 32 x 32 tile
+constexpr int kFinalChoices = 3;
+enum TuneKind : int { kTuneAnalysis = 0, kTuneShrink = 1, kTuneSynthesis = 2, kTuneFinal = 3 };
 
 // k_shrink.cu
 struct ShrinkArgs {
@@ -112,7 +115,7 @@ struct FinalArgs {
 // blocks per query of the PCE-mode level-1 kernel (its partial-sum count)
 int final_pce_blocks(int Rc, int Cc);
 cudaError_t launch_synthesis(const SynArgs &a, cudaStream_t st, int choice = 0);
-cudaError_t launch_final(const FinalArgs &a, bool mle, cudaStream_t st);
+cudaError_t launch_final(const FinalArgs &a, bool mle, cudaStream_t st, int choice = 0);
 
 // k_fft.cu
 cudaError_t launch_divide(const float *num, const float *den, const float *num_lo, const float *den_lo, long long hw,

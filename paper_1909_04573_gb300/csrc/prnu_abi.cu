@@ -321,7 +321,7 @@ prnu_status run_denoise(prnu_ctx *ctx, const float *in, int H, int W, int P, con
                         : fin.pce ? (double)fin.G * H * W * 4 * (fin.C + 3)
                                   : (double)P * H * W * 4 * (fin.accumulate ? 2 : 1);
         Launch t(ctx, mle ? "final_mle" : fin.pce ? "final_pce" : "final_residual", st, 1, cin + io);
-        CU(launch_final(fin, mle, st));
+        CU(launch_final(fin, mle, st, mle ? choice(kTuneFinal, 1) : 0));
     }
     return PRNU_OK;
 }
@@ -1548,10 +1548,12 @@ prnu_status prnu_autotune_level(prnu_ctx *ctx, int H, int W, const prnu_params *
     if ((s = check_params(params, H, W, nullptr)) != PRNU_OK) return s;
     const int L = params->levels;
     const int nch = kind == kTuneAnalysis ? kAnaChoices : kind == kTuneShrink ? kShrinkChoices
-                  : kind == kTuneSynthesis ? kSynChoices : 0;
-    if (nch == 0) return fail(PRNU_EINVAL, "kind must be 0 (analysis), 1 (shrink) or 2 (synthesis)");
-    const int lmin = kind == kTuneShrink ? 1 : 2;
-    if (level < lmin || level > L) return fail(PRNU_EINVAL, "level must be in [%d, %d] for this kind", lmin, L);
+                  : kind == kTuneSynthesis ? kSynChoices : kind == kTuneFinal ? kFinalChoices : 0;
+    if (nch == 0)
+        return fail(PRNU_EINVAL, "kind must be 0 (analysis), 1 (shrink), 2 (synthesis) or 3 (level-1 MLE step)");
+    const int lmin = kind == kTuneShrink || kind == kTuneFinal ? 1 : 2;
+    const int lmax = kind == kTuneFinal ? 1 : L;
+    if (level < lmin || level > lmax) return fail(PRNU_EINVAL, "level must be in [%d, %d] for this kind", lmin, lmax);
     if (choice < -2 || choice >= nch) return fail(PRNU_EINVAL, "choice must be in [-2, %d)", nch);
     std::lock_guard<std::mutex> lk(ctx->mu);
     const auto key = std::make_tuple(padded(H, L), padded(W, L), (int)params->dtype, kind, level);

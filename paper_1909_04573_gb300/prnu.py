@@ -571,8 +571,8 @@ class Context:
 
     def autotune_level(self, H, W, kind, level, choice=-2, params=None):
         """Pin (choice >= 0), reset (-1) or read (-2) the tuner's choice for a
-        launch kind (0 analysis, 1 shrink, 2 synthesis) at a level; returns the
-        choice in force."""
+        launch kind (0 analysis, 1 shrink, 2 synthesis, 3 the level-1 MLE step)
+        at a level; returns the choice in force."""
         cur = _i()
         _check(lib().prnu_autotune_level(self.ctx, H, W, ctypes.byref(params or default_params()), kind, level,
                                          choice, ctypes.byref(cur)), self.ctx)
